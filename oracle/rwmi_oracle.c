@@ -1,0 +1,1223 @@
+/*
+ * rwmi_oracle.c -- plain, slow FP64 CPU reference ("the oracle") for one timestep of the
+ * RW-MI-DELBM fluid-solute update (arXiv 2308.05007).
+ *
+ * TEST INFRASTRUCTURE ONLY. The test-suite, the package smoke check and the benchmark's CPU
+ * baseline leg are the only users of this library; the product path never loads it. It shares
+ * no code, header, table or helper with the CUDA library: the lattice tables, the counter-based
+ * generator, the metaball function and every step below are written out here on their own.
+ *
+ * One timestep t -> t+1, in the order the oracle runs it:
+ *   1. rigid particle poses at t and t+1: the DEM of Eq. 4 is held to prescribed trajectories;
+ *   2. solid fraction per cell from the metaball function of Eq. 3 (4x4x4 sub-samples);
+ *   3. lattice Boltzmann pull-stream and collide, Eqs. 12-15 (D3Q19 as in Section 2.3, or
+ *      D3Q15), with partially-saturated-cell solid coupling and Guo body forcing;
+ *   4. random-walk advance of every solute walker, Eq. 2, with the four walker/particle
+ *      relations of Section 2.4.2: free motion (I, III), Dirichlet refill (II), and the
+ *      no-flux rule (IV) by Algorithm 1 (bisection) and Algorithm 2 (specular reflection);
+ *   5. on request: concentration binning (Eq. 16), walker moments, mass/momentum, forces.
+ *
+ * Precision: FP64 throughout, except the two places where floating point decides an integer
+ * that the GPU must reproduce exactly -- the sub-sample inside test of the solid fraction and
+ * the accept/reject test of walker seeding. Those evaluate Eq. 3 in IEEE binary32 with a fixed
+ * operation order (no contraction; build with -ffp-contract=off), which is the kernel's
+ * precision. Readings of passages the paper leaves open are marked "Reading" below.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_API __attribute__((visibility("default")))
+
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
+
+/* ------------------------------------------------------------------------------------------
+ * Counter-based generator: Philox4x32 with 10 rounds (Salmon, Moraes, Dror and Shaw,
+ * "Parallel random numbers: as easy as 1, 2, 3", SC'11). The paper only asks for a Gaussian
+ * vector of zero mean and unit variance in Eq. 2; a counter-based generator keyed by
+ * (walker id, step) makes every walker's noise independent of execution order.
+ * ------------------------------------------------------------------------------------------ */
+static void philox4x32_10(uint32_t k0, uint32_t k1, const uint32_t ctr[4], uint32_t out[4])
+{
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    for (int round = 0; round < 10; ++round) {
+        /* S-box: two 32x32 -> 64-bit products, hi halves mixed with the other words and key */
+        uint64_t prod0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+        uint64_t prod1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+        uint32_t n0 = (uint32_t)(prod1 >> 32) ^ c1 ^ k0;
+        uint32_t n1 = (uint32_t)prod1;
+        uint32_t n2 = (uint32_t)(prod0 >> 32) ^ c3 ^ k1;
+        uint32_t n3 = (uint32_t)prod0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+        /* key schedule: Weyl sequence with the golden-ratio and sqrt(3)-1 constants */
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* U = ((r >> 8) + 1/2) 2^-24: 24-bit uniform strictly inside (0, 1), exact in FP32 and FP64 */
+static double u24(uint32_t r) { return ((double)(r >> 8) + 0.5) * 5.9604644775390625e-08; }
+
+/* Box-Muller transform of two uniforms into two independent standard normals */
+static void box_muller(double ua, double ub, double* za, double* zb)
+{
+    double rad = sqrt(-2.0 * log(ua));
+    double ang = 2.0 * M_PI * ub;
+    *za = rad * cos(ang);
+    if (zb) *zb = rad * sin(ang);
+}
+
+/* ------------------------------------------------------------------------------------------
+ * Lattice velocity sets. Section 2.3 names D3Q19 (the sums of Eqs. 14-15 run over 19
+ * directions); D3Q15 is offered as well. Weights and c_s^2 = 1/3 are the standard ones of
+ * Qian, d'Humieres and Lallemand (1992). Directions come in opposite pairs (2m-1, 2m).
+ * ------------------------------------------------------------------------------------------ */
+static const int E15[15][3] = {
+    {0, 0, 0},
+    {1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0}, {0, 0, 1}, {0, 0, -1},
+    {1, 1, 1}, {-1, -1, -1}, {1, 1, -1}, {-1, -1, 1},
+    {1, -1, 1}, {-1, 1, -1}, {-1, 1, 1}, {1, -1, -1}};
+static const int E19[19][3] = {
+    {0, 0, 0},
+    {1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0}, {0, 0, 1}, {0, 0, -1},
+    {1, 1, 0}, {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0},
+    {1, 0, 1}, {-1, 0, -1}, {1, 0, -1}, {-1, 0, 1},
+    {0, 1, 1}, {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
+
+static double lattice_weight(int q, int i)
+{
+    if (q == 15) return i == 0 ? 2.0 / 9.0 : (i <= 6 ? 1.0 / 9.0 : 1.0 / 72.0);
+    return i == 0 ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
+}
+static const int* lattice_e(int q, int i) { return q == 15 ? E15[i] : E19[i]; }
+static int opposite(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+
+/* ------------------------------------------------------------------------------------------
+ * State
+ * ------------------------------------------------------------------------------------------ */
+typedef struct {
+    int n[3];
+    long long ncell;
+    int q;
+    double tau, D;
+    uint32_t key0, key1;
+    int wall[3];             /* no-slip walls on the two faces normal to this axis */
+    double F0[3], Fperiod;   /* body force density F(t) = F0 sin(2 pi t / Fperiod), or F0 */
+    double rho0, u_init[3];
+
+    /* metaball particles (Eq. 3), rigid, prescribed motion */
+    int P, Nc;
+    int* coff;               /* [P+1] */
+    double* cbody;           /* [3 Nc] body-frame control points */
+    double* kc;              /* [Nc] */
+    float* kc32;             /* [Nc] the same weights as given (binary32) */
+    double *org, *amp, *per, *pha, *omg;   /* [3P] [3P] [P] [P] [3P] */
+    double* Rb;              /* [P] bound: f_p < 1 farther than Rb from the origin */
+
+    /* fluid */
+    double *f, *fn;          /* [q ncell], direction-major; f holds post-collision of t-1 */
+    double *u, *rho;         /* [3 ncell], [ncell] of the last LBM step */
+    int *cnt, *own;          /* solid sub-sample count 0..64 and owner per cell, time t */
+    long long solid_time;
+    double mass, mom[3];     /* sums over cells of rho and sum_i f_i e_i, last LBM step */
+    double *Fp, *Tp;         /* [3P] hydrodynamic force and torque, last LBM step */
+
+    /* walkers */
+    long long nw;
+    double *x, *x0;          /* [3 nw] unwrapped positions and start positions */
+
+    long long t;
+    long long cnt_type[4], bisect_fail, refill_fail, wall_fail, seed_fail;
+} orc_t;
+
+static long long cell_index(const orc_t* o, long long i, long long j, long long k)
+{
+    return (k * o->n[1] + j) * o->n[0] + i;
+}
+
+static long long wrapll(long long a, long long n) { a %= n; return a < 0 ? a + n : a; }
+
+/* ------------------------------------------------------------------------------------------
+ * Prescribed particle motion (stand-in for Eq. 4; Eq. 37 drives the oscillator case with a
+ * sinusoid). Origin o(t) = o0 + A sin(2 pi t / T + phi), velocity its time derivative,
+ * constant spin omega: the body frame turns by |omega| t about omega/|omega| (Rodrigues).
+ * ------------------------------------------------------------------------------------------ */
+static void particle_pose(const orc_t* o, long long t, int p, double org[3], double vel[3],
+                          double R[3][3])
+{
+    double s = 0.0, cdt = 0.0;
+    if (o->per[p] > 0.0) {
+        double th = 2.0 * M_PI * (double)t / o->per[p] + o->pha[p];
+        s = sin(th);
+        cdt = cos(th) * 2.0 * M_PI / o->per[p];
+    }
+    for (int a = 0; a < 3; ++a) {
+        org[a] = o->org[3 * p + a] + o->amp[3 * p + a] * s;
+        vel[a] = o->amp[3 * p + a] * cdt;
+    }
+    double w[3] = {o->omg[3 * p], o->omg[3 * p + 1], o->omg[3 * p + 2]};
+    double wn = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) R[a][b] = (a == b) ? 1.0 : 0.0;
+    if (wn > 0.0) {
+        double ax[3] = {w[0] / wn, w[1] / wn, w[2] / wn};
+        double ang = wn * (double)t, ca = cos(ang), sa = sin(ang);
+        /* R = cos I + sin [n]x + (1 - cos) n n^T */
+        double K[3][3] = {{0, -ax[2], ax[1]}, {ax[2], 0, -ax[0]}, {-ax[1], ax[0], 0}};
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b)
+                R[a][b] = (a == b ? ca : 0.0) + sa * K[a][b] + (1.0 - ca) * ax[a] * ax[b];
+    }
+}
+
+/* Origin wrapped into the box on periodic axes */
+static void wrap_point(const orc_t* o, double x[3])
+{
+    for (int a = 0; a < 3; ++a)
+        if (!o->wall[a]) x[a] -= (double)o->n[a] * floor(x[a] / (double)o->n[a]);
+}
+
+/* World positions of all control points at time t (wrapped on periodic axes), plus each
+ * particle's wrapped origin and velocity, in FP64 and rounded to binary32. */
+typedef struct {
+    double* c;    /* [3 Nc] */
+    float* c32;   /* [3 Nc] */
+    double* o;    /* [3 P] wrapped origin */
+    double* v;    /* [3 P] */
+    double* w;    /* [3 P] spin */
+} frame_t;
+
+static void frame_alloc(const orc_t* o, frame_t* fr)
+{
+    fr->c = (double*)calloc(3 * (size_t)o->Nc + 3, sizeof(double));
+    fr->c32 = (float*)calloc(3 * (size_t)o->Nc + 3, sizeof(float));
+    fr->o = (double*)calloc(3 * (size_t)o->P + 3, sizeof(double));
+    fr->v = (double*)calloc(3 * (size_t)o->P + 3, sizeof(double));
+    fr->w = (double*)calloc(3 * (size_t)o->P + 3, sizeof(double));
+}
+static void frame_free(frame_t* fr) { free(fr->c); free(fr->c32); free(fr->o); free(fr->v); free(fr->w); }
+
+static void frame_at(const orc_t* o, long long t, frame_t* fr)
+{
+    for (int p = 0; p < o->P; ++p) {
+        double org[3], vel[3], R[3][3];
+        particle_pose(o, t, p, org, vel, R);
+        for (int i = o->coff[p]; i < o->coff[p + 1]; ++i) {
+            double cw[3];
+            for (int a = 0; a < 3; ++a)
+                cw[a] = org[a] + R[a][0] * o->cbody[3 * i] + R[a][1] * o->cbody[3 * i + 1]
+                        + R[a][2] * o->cbody[3 * i + 2];
+            wrap_point(o, cw);
+            for (int a = 0; a < 3; ++a) { fr->c[3 * i + a] = cw[a]; fr->c32[3 * i + a] = (float)cw[a]; }
+        }
+        wrap_point(o, org);
+        for (int a = 0; a < 3; ++a) {
+            fr->o[3 * p + a] = org[a];
+            fr->v[3 * p + a] = vel[a];
+            fr->w[3 * p + a] = o->omg[3 * p + a];
+        }
+    }
+}
+
+/* Minimum-image displacement on periodic axes (Reading: a metaball near a periodic face acts
+ * through it, as the fluid and walkers do). Both arguments lie in [0, n). */
+static double min_image(const orc_t* o, int a, double d)
+{
+    if (!o->wall[a]) {
+        double n = (double)o->n[a];
+        if (d > 0.5 * n) d -= n;
+        else if (d < -0.5 * n) d += n;
+    }
+    return d;
+}
+
+/* Eq. 3, f(x) = sum_i k_i / |x - x_i|^2, and its gradient, Eq. 17,
+ * grad f = sum_i -2 k_i (x - x_i) / |x - x_i|^4, for particle p; x wrapped into the box. */
+static double metaball64(const orc_t* o, const frame_t* fr, int p, const double x[3], double g[3])
+{
+    double f = 0.0;
+    if (g) g[0] = g[1] = g[2] = 0.0;
+    for (int i = o->coff[p]; i < o->coff[p + 1]; ++i) {
+        double d[3];
+        for (int a = 0; a < 3; ++a) d[a] = min_image(o, a, x[a] - fr->c[3 * i + a]);
+        double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        f += o->kc[i] / r2;
+        if (g) {
+            double s = -2.0 * o->kc[i] / (r2 * r2);
+            for (int a = 0; a < 3; ++a) g[a] += s * d[a];
+        }
+    }
+    return f;
+}
+
+/* Eq. 3 in binary32 with a fixed operation order: the inside test that decides sub-sample
+ * counts and seeding accept/reject. d = x - c, one minimum-image correction by +-n, then
+ * r2 = (dx*dx + dy*dy) + dz*dz and f = ((k_0/r2_0) + k_1/r2_1) + ... */
+static float metaball32(const orc_t* o, const frame_t* fr, int p, const float x[3])
+{
+    float f = 0.0f;
+    for (int i = o->coff[p]; i < o->coff[p + 1]; ++i) {
+        float d[3];
+        for (int a = 0; a < 3; ++a) {
+            float da = x[a] - fr->c32[3 * i + a];
+            if (!o->wall[a]) {
+                float n = (float)o->n[a];
+                float h = 0.5f * n;
+                if (da > h) da = da - n;
+                else if (da < -h) da = da + n;
+            }
+            d[a] = da;
+        }
+        float xx = d[0] * d[0];
+        float yy = d[1] * d[1];
+        float zz = d[2] * d[2];
+        float r2 = xx + yy;
+        r2 = r2 + zz;
+        float term = o->kc32[i] / r2;
+        f = f + term;
+    }
+    return f;
+}
+
+/* Distance from x (wrapped) to particle p's wrapped origin, minimum image */
+static double origin_distance(const orc_t* o, const frame_t* fr, int p, const double x[3])
+{
+    double s = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        double d = min_image(o, a, x[a] - fr->o[3 * p + a]);
+        s += d * d;
+    }
+    return sqrt(s);
+}
+
+/* Bound on a particle's extent. With r = |x - o| and |x - x_i| >= r - |c_i| for every
+ * control point, f(x) <= sum_i k_i / (r - |c_i|)^2 once r > max |c_i|; the right side falls
+ * monotonically, so beyond its unit crossing Rb every point has f < 1 (Eq. 3 is exact here,
+ * the bound only lets a cell or walker skip a particle it cannot touch). */
+static double bound_radius(const orc_t* o, int p)
+{
+    double cmax = 0.0, ksum = 0.0;
+    for (int i = o->coff[p]; i < o->coff[p + 1]; ++i) {
+        double c = sqrt(o->cbody[3 * i] * o->cbody[3 * i] + o->cbody[3 * i + 1] * o->cbody[3 * i + 1]
+                        + o->cbody[3 * i + 2] * o->cbody[3 * i + 2]);
+        if (c > cmax) cmax = c;
+        ksum += o->kc[i];
+    }
+    double lo = cmax, hi = cmax + sqrt(ksum) + 1e-9;
+    for (int it = 0; it < 200; ++it) {
+        double mid = 0.5 * (lo + hi), s = 0.0;
+        for (int i = o->coff[p]; i < o->coff[p + 1]; ++i) {
+            double c = sqrt(o->cbody[3 * i] * o->cbody[3 * i] + o->cbody[3 * i + 1] * o->cbody[3 * i + 1]
+                            + o->cbody[3 * i + 2] * o->cbody[3 * i + 2]);
+            s += o->kc[i] / ((mid - c) * (mid - c));
+        }
+        if (s > 1.0) lo = mid; else hi = mid;
+    }
+    return hi;
+}
+
+/* Lowest-index particle whose metaball reaches 1 at x (FP64); -1 if x is in the fluid */
+static int inside_any64(const orc_t* o, const frame_t* fr, const double xin[3])
+{
+    double x[3] = {xin[0], xin[1], xin[2]};
+    wrap_point(o, x);
+    for (int p = 0; p < o->P; ++p) {
+        if (origin_distance(o, fr, p, x) > o->Rb[p] + 1e-6) continue;
+        if (metaball64(o, fr, p, x, NULL) >= 1.0) return p;
+    }
+    return -1;
+}
+
+/* The same test in binary32 (seeding accept/reject) */
+static int inside_any32(const orc_t* o, const frame_t* fr, const float x[3])
+{
+    double xd[3] = {x[0], x[1], x[2]};
+    for (int p = 0; p < o->P; ++p) {
+        if (origin_distance(o, fr, p, xd) > o->Rb[p] + 0.5) continue;
+        if (metaball32(o, fr, p, x) >= 1.0f) return p;
+    }
+    return -1;
+}
+
+/* ------------------------------------------------------------------------------------------
+ * Solid fraction per cell. The partially-saturated-cells method is named in Section 1; the
+ * paper gives no formula for the fraction. Reading: node at the cell centre, cell
+ * [i, i+1) x [j, j+1) x [k, k+1); 4x4x4 sub-samples at i + (a + 1/2)/4 etc.; a sub-sample is
+ * solid when some particle's Eq. 3 value is >= 1 there; the count n (0..64) gives
+ * epsilon = n / 64. Owner: the particle holding the most sub-samples, lowest index on ties.
+ * Every sub-sample of every cell is tested; a particle is skipped for a cell only when the
+ * cell lies wholly beyond its bound radius, where Eq. 3 stays below 1.
+ * ------------------------------------------------------------------------------------------ */
+static void rasterize(orc_t* o, long long t)
+{
+    frame_t fr;
+    frame_alloc(o, &fr);
+    frame_at(o, t, &fr);
+    int* cand = (int*)malloc(sizeof(int) * (size_t)(o->P + 1));
+    int* npart = (int*)calloc((size_t)o->P + 1, sizeof(int));
+    for (long long k = 0; k < o->n[2]; ++k)
+        for (long long j = 0; j < o->n[1]; ++j)
+            for (long long i = 0; i < o->n[0]; ++i) {
+                long long c = cell_index(o, i, j, k);
+                double xc[3] = {i + 0.5, j + 0.5, k + 0.5};
+                int nc = 0;
+                for (int p = 0; p < o->P; ++p)
+                    if (origin_distance(o, &fr, p, xc) <= o->Rb[p] + 1.0) { cand[nc++] = p; npart[p] = 0; }
+                int count = 0;
+                if (nc > 0) {
+                    for (int cz = 0; cz < 4; ++cz)
+                        for (int cy = 0; cy < 4; ++cy)
+                            for (int cx = 0; cx < 4; ++cx) {
+                                float xs[3] = {(float)i + (0.125f + 0.25f * (float)cx),
+                                               (float)j + (0.125f + 0.25f * (float)cy),
+                                               (float)k + (0.125f + 0.25f * (float)cz)};
+                                int solid = 0;
+                                for (int m = 0; m < nc; ++m)
+                                    if (metaball32(o, &fr, cand[m], xs) >= 1.0f) { npart[cand[m]]++; solid = 1; }
+                                count += solid;
+                            }
+                }
+                int owner = -1, best = 0;
+                for (int m = 0; m < nc; ++m)
+                    if (npart[cand[m]] > best) { best = npart[cand[m]]; owner = cand[m]; }
+                o->cnt[c] = count;
+                o->own[c] = count > 0 ? owner : -1;
+            }
+    free(cand);
+    free(npart);
+    frame_free(&fr);
+    o->solid_time = t;
+}
+
+/* Body force density at step t (Reading: a force density F, as rho0 g with rho0 = 1) */
+static void body_force(const orc_t* o, long long t, double F[3])
+{
+    double s = 1.0;
+    if (o->Fperiod > 0.0) s = sin(2.0 * M_PI * (double)t / o->Fperiod);
+    for (int a = 0; a < 3; ++a) F[a] = o->F0[a] * s;
+}
+
+/* Eq. 13: second-order equilibrium with c_s^2 = 1/3 */
+static double feq(int q, int i, double rho, const double u[3])
+{
+    const int* e = lattice_e(q, i);
+    double eu = e[0] * u[0] + e[1] * u[1] + e[2] * u[2];
+    double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    return lattice_weight(q, i) * rho * (1.0 + 3.0 * eu + 4.5 * eu * eu - 1.5 * uu);
+}
+
+/* Post-collision populations of one cell at step t from the pulled populations fi.
+ *  - Eqs. 14-15 moments; velocity with half the body force (Guo, Zheng and Shi 2002):
+ *    u = (sum_i f_i e_i + F/2) / rho.
+ *  - Eq. 12 BGK relaxation towards Eq. 13, weighted by the fluid share (1 - B).
+ *  - Partially saturated cells (Noble and Torczynski 1998): B = eps (tau - 1/2) /
+ *    ((1 - eps) + (tau - 1/2)), solid term Omega_i = f_opp(i) - feq_opp(i)(rho, u)
+ *    - f_i + feq_i(rho, u_s), with u_s = v_p + omega_p x (x - o_p) of the owner particle.
+ *  - Guo source S_i = (1 - 1/(2 tau)) w_i [3 (e_i - u) + 9 (e_i . u) e_i] . F, weighted by
+ *    (1 - B).
+ * Returns the momentum the solid term puts into the fluid, B sum_i Omega_i e_i, in dp. */
+static void collide_cell(const orc_t* o, const frame_t* fr, long long t, long long i, long long j,
+                         long long k, int count, int owner, const double fi[19], const double F[3],
+                         double fout[19], double u[3], double* rho_out, double dp[3])
+{
+    int q = o->q;
+    double tau = o->tau;
+    double rho = 0.0, jm[3] = {0.0, 0.0, 0.0};
+    for (int m = 0; m < q; ++m) {
+        const int* e = lattice_e(q, m);
+        rho += fi[m];
+        for (int a = 0; a < 3; ++a) jm[a] += fi[m] * e[a];
+    }
+    for (int a = 0; a < 3; ++a) u[a] = (jm[a] + 0.5 * F[a]) / rho;
+    *rho_out = rho;
+    double eps = count / 64.0;
+    double B = eps * (tau - 0.5) / ((1.0 - eps) + (tau - 0.5));
+    double us[3] = {0.0, 0.0, 0.0};
+    if (B > 0.0 && owner >= 0) {
+        double r[3];
+        double xn[3] = {i + 0.5, j + 0.5, k + 0.5};
+        for (int a = 0; a < 3; ++a) r[a] = min_image(o, a, xn[a] - fr->o[3 * owner + a]);
+        const double* v = fr->v + 3 * owner;
+        const double* w = fr->w + 3 * owner;
+        us[0] = v[0] + w[1] * r[2] - w[2] * r[1];
+        us[1] = v[1] + w[2] * r[0] - w[0] * r[2];
+        us[2] = v[2] + w[0] * r[1] - w[1] * r[0];
+    }
+    dp[0] = dp[1] = dp[2] = 0.0;
+    double guo = 1.0 - 0.5 / tau;
+    for (int m = 0; m < q; ++m) {
+        const int* e = lattice_e(q, m);
+        double w = lattice_weight(q, m);
+        double eu = e[0] * u[0] + e[1] * u[1] + e[2] * u[2];
+        double S = 0.0;
+        for (int a = 0; a < 3; ++a) S += (3.0 * (e[a] - u[a]) + 9.0 * eu * e[a]) * F[a];
+        S *= guo * w;
+        double fe = feq(q, m, rho, u);
+        double om = 0.0;
+        if (B > 0.0) {
+            int mo = opposite(m);
+            om = fi[mo] - feq(q, mo, rho, u) - fi[m] + feq(q, m, rho, us);
+            for (int a = 0; a < 3; ++a) dp[a] += B * om * e[a];
+        }
+        fout[m] = fi[m] - (1.0 - B) * (fi[m] - fe) / tau + B * om + (1.0 - B) * S;
+    }
+    (void)t;
+}
+
+/* Pull streaming, Eq. 12 left side: f_i(x, t) = f+_i(x - e_i, t - 1) with periodic wrap;
+ * where x - e_i lies beyond a wall the half-way bounce-back f_i(x, t) = f+_opp(i)(x, t - 1)
+ * applies (the wall sits on the cell face, at rest). */
+static void pull_cell(const orc_t* o, long long i, long long j, long long k, double fi[19])
+{
+    long long c = cell_index(o, i, j, k);
+    for (int m = 0; m < o->q; ++m) {
+        const int* e = lattice_e(o->q, m);
+        long long s[3] = {i - e[0], j - e[1], k - e[2]};
+        int blocked = 0;
+        for (int a = 0; a < 3; ++a) {
+            if (o->wall[a]) {
+                if (s[a] < 0 || s[a] >= o->n[a]) blocked = 1;
+            } else {
+                s[a] = wrapll(s[a], o->n[a]);
+            }
+        }
+        if (blocked) fi[m] = o->f[(size_t)opposite(m) * o->ncell + c];
+        else fi[m] = o->f[(size_t)m * o->ncell + cell_index(o, s[0], s[1], s[2])];
+    }
+}
+
+static void lbm_step(orc_t* o, long long t)
+{
+    if (o->solid_time != t) rasterize(o, t);
+    frame_t fr;
+    frame_alloc(o, &fr);
+    frame_at(o, t, &fr);
+    double F[3];
+    body_force(o, t, F);
+    o->mass = 0.0;
+    o->mom[0] = o->mom[1] = o->mom[2] = 0.0;
+    for (int m = 0; m < 3 * o->P; ++m) { o->Fp[m] = 0.0; o->Tp[m] = 0.0; }
+    for (long long k = 0; k < o->n[2]; ++k)
+        for (long long j = 0; j < o->n[1]; ++j)
+            for (long long i = 0; i < o->n[0]; ++i) {
+                long long c = cell_index(o, i, j, k);
+                double fi[19], fo[19], u[3], rho, dp[3];
+                pull_cell(o, i, j, k, fi);
+                collide_cell(o, &fr, t, i, j, k, o->cnt[c], o->own[c], fi, F, fo, u, &rho, dp);
+                for (int m = 0; m < o->q; ++m) o->fn[(size_t)m * o->ncell + c] = fo[m];
+                for (int a = 0; a < 3; ++a) o->u[3 * c + a] = u[a];
+                o->rho[c] = rho;
+                o->mass += rho;
+                for (int m = 0; m < o->q; ++m) {
+                    const int* e = lattice_e(o->q, m);
+                    for (int a = 0; a < 3; ++a) o->mom[a] += fi[m] * e[a];
+                }
+                int p = o->own[c];
+                if (o->cnt[c] > 0 && p >= 0) {
+                    /* force on the particle: the opposite of what the solid term gives the
+                     * fluid; torque about the particle origin (minimum image) */
+                    double Fc[3] = {-dp[0], -dp[1], -dp[2]}, r[3];
+                    double xn[3] = {i + 0.5, j + 0.5, k + 0.5};
+                    for (int a = 0; a < 3; ++a) r[a] = min_image(o, a, xn[a] - fr.o[3 * p + a]);
+                    for (int a = 0; a < 3; ++a) o->Fp[3 * p + a] += Fc[a];
+                    o->Tp[3 * p + 0] += r[1] * Fc[2] - r[2] * Fc[1];
+                    o->Tp[3 * p + 1] += r[2] * Fc[0] - r[0] * Fc[2];
+                    o->Tp[3 * p + 2] += r[0] * Fc[1] - r[1] * Fc[0];
+                }
+            }
+    double* tmp = o->f;
+    o->f = o->fn;
+    o->fn = tmp;
+    frame_free(&fr);
+}
+
+/* ------------------------------------------------------------------------------------------
+ * Random-walk method, Section 2.4
+ * ------------------------------------------------------------------------------------------ */
+
+/* Section 2.4.1: the walker takes the fluid velocity by linear interpolation from the LBM
+ * grid. Reading: trilinear over the eight nodes (cell centres) around x, periodic wrap on
+ * periodic axes; on a walled axis the wall plane carries u = 0 and the half cell between the
+ * wall and the first node interpolates linearly to it. */
+static void axis_stencil(const orc_t* o, int a, double xa, long long idx[2], double wt[2])
+{
+    long long n = o->n[a];
+    if (!o->wall[a]) {
+        double s = xa - 0.5;
+        double fl = floor(s);
+        double w = s - fl;
+        long long i0 = (long long)fl;
+        idx[0] = wrapll(i0, n);
+        idx[1] = wrapll(i0 + 1, n);
+        wt[0] = 1.0 - w;
+        wt[1] = w;
+        return;
+    }
+    if (xa < 0.0) xa = 0.0;
+    if (xa > (double)n) xa = (double)n;
+    if (xa < 0.5) {                       /* wall at 0 (value 0) .. node 0 at 0.5 */
+        idx[0] = -1; idx[1] = 0;
+        wt[1] = xa / 0.5; wt[0] = 1.0 - wt[1];
+    } else if (xa >= (double)n - 0.5) {   /* node n-1 at n-0.5 .. wall at n (value 0) */
+        idx[0] = n - 1; idx[1] = -1;
+        wt[1] = (xa - ((double)n - 0.5)) / 0.5; wt[0] = 1.0 - wt[1];
+    } else {
+        double s = xa - 0.5;
+        double fl = floor(s);
+        double w = s - fl;
+        idx[0] = (long long)fl;
+        idx[1] = idx[0] + 1;
+        if (idx[1] > n - 1) idx[1] = n - 1;
+        wt[0] = 1.0 - w;
+        wt[1] = w;
+    }
+}
+
+static void trilinear(const orc_t* o, const double* ufield, const double x[3], double u[3])
+{
+    long long ix[2], iy[2], iz[2];
+    double wx[2], wy[2], wz[2];
+    axis_stencil(o, 0, x[0], ix, wx);
+    axis_stencil(o, 1, x[1], iy, wy);
+    axis_stencil(o, 2, x[2], iz, wz);
+    u[0] = u[1] = u[2] = 0.0;
+    for (int c = 0; c < 2; ++c)
+        for (int b = 0; b < 2; ++b)
+            for (int a = 0; a < 2; ++a) {
+                if (ix[a] < 0 || iy[b] < 0 || iz[c] < 0) continue;   /* wall value 0 */
+                double w = wx[a] * wy[b] * wz[c];
+                long long cell = cell_index(o, ix[a], iy[b], iz[c]);
+                for (int d = 0; d < 3; ++d) u[d] += w * ufield[3 * cell + d];
+            }
+}
+
+/* Specular reflection at the no-slip walls (the walls bound the solute too). Returns 0 if
+ * the point could not be brought back inside [0, n] on a walled axis. */
+static int wall_reflect(const orc_t* o, double x[3])
+{
+    int ok = 1;
+    for (int a = 0; a < 3; ++a) {
+        if (!o->wall[a]) continue;
+        double n = (double)o->n[a];
+        for (int it = 0; it < 8; ++it) {
+            if (x[a] < 0.0) x[a] = -x[a];
+            else if (x[a] > n) x[a] = 2.0 * n - x[a];
+            else break;
+        }
+        if (x[a] < 0.0 || x[a] > n) {
+            ok = 0;
+            x[a] = x[a] < 0.0 ? 0.0 : n;
+        }
+    }
+    return ok;
+}
+
+static int beyond_wall(const orc_t* o, const double x[3])
+{
+    for (int a = 0; a < 3; ++a)
+        if (o->wall[a] && (x[a] < 0.0 || x[a] > (double)o->n[a])) return 1;
+    return 0;
+}
+
+static double f_at(const orc_t* o, const frame_t* fr, int p, const double xin[3], double g[3])
+{
+    double x[3] = {xin[0], xin[1], xin[2]};
+    wrap_point(o, x);
+    return metaball64(o, fr, p, x, g);
+}
+
+/* Algorithm 1: bisection on the segment from an outside point a (f < 1) to an inside point
+ * b (f >= 1) of particle p. Convergence when |f(mid) - 1| < 1e-3; at most 200 iterations;
+ * on f(mid) < 1 the outside end moves to mid, otherwise the inside end does. Returns 1 and
+ * the point in xi on success, 0 when no such point was found (the error of Algorithm 1).
+ * a_out receives the final outside end of the bracket. */
+static int bisect(const orc_t* o, const frame_t* fr, int p, const double a_in[3], const double b_in[3],
+                  double xi[3], double a_out[3])
+{
+    double a[3] = {a_in[0], a_in[1], a_in[2]}, b[3] = {b_in[0], b_in[1], b_in[2]};
+    int found = 0;
+    for (int it = 1; it <= 200; ++it) {
+        double mid[3];
+        for (int d = 0; d < 3; ++d) mid[d] = 0.5 * (a[d] + b[d]);
+        double fm = f_at(o, fr, p, mid, NULL);
+        if (fabs(fm - 1.0) < 1e-3) {
+            for (int d = 0; d < 3; ++d) xi[d] = mid[d];
+            found = 1;
+            break;
+        } else if (fm < 1.0) {
+            for (int d = 0; d < 3; ++d) a[d] = mid[d];
+        } else {
+            for (int d = 0; d < 3; ++d) b[d] = mid[d];
+        }
+    }
+    if (a_out) for (int d = 0; d < 3; ++d) a_out[d] = a[d];
+    return found;
+}
+
+/* Algorithm 2 / Eqs. 18-22: t_o = x_int - x_p, t_i = x_f - x_int, n = grad f(x_int),
+ * t_r = t_i - 2 (t_i . n) n. Reading: n is normalised (Eq. 22 is a mirror only for unit n).
+ * Returns the reflected end point x_int + t_r. */
+static void reflect(const orc_t* o, const frame_t* fr, int p, const double xint[3], const double xf[3],
+                    double xnew[3])
+{
+    double g[3];
+    f_at(o, fr, p, xint, g);
+    double gn = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+    double n[3] = {g[0] / gn, g[1] / gn, g[2] / gn};
+    double ti[3] = {xf[0] - xint[0], xf[1] - xint[1], xf[2] - xint[2]};
+    double tn = ti[0] * n[0] + ti[1] * n[1] + ti[2] * n[2];
+    for (int d = 0; d < 3; ++d) xnew[d] = xint[d] + (ti[d] - 2.0 * tn * n[d]);
+}
+
+/* Section 2.4.2 Dirichlet "refill" of a type-II walker at x inside particle p. Reading:
+ *  1. s = -grad f / |grad f| at x (outward: Eq. 3 falls away from the control points);
+ *  2. step out along s by h = 1/2, 1, 2, ..., 64 until f < 1 (bracket), then Algorithm 1 on
+ *     [outside point, x] gives the surface point x_s;
+ *  3. place the walker uniformly in the ball of radius sqrt(2 D dt) about x_s, from three
+ *     uniforms of Philox counter (id, t, 1, 0): cos(theta) = 2U0 - 1, phi = 2 pi U1,
+ *     r = R U2^(1/3); walls reflect it;
+ *  4. if that point is inside a particle, mirror it across the tangent plane at x_s (outward
+ *     normal of step 1 at x_s); if still inside, use the bracket's final outside end.
+ * Returns 0 when step 2 or the final point failed (counted as a refill failure). */
+static int refill(orc_t* o, const frame_t* fr, int p, const double x[3], uint32_t id, uint32_t t,
+                  double xnew[3])
+{
+    double g[3];
+    f_at(o, fr, p, x, g);
+    double gn = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+    double s[3] = {1.0, 0.0, 0.0};
+    if (gn > 0.0 && isfinite(gn)) for (int d = 0; d < 3; ++d) s[d] = -g[d] / gn;
+    double xo[3];
+    int out = 0;
+    for (double h = 0.5; h <= 64.0; h *= 2.0) {
+        for (int d = 0; d < 3; ++d) xo[d] = x[d] + h * s[d];
+        if (f_at(o, fr, p, xo, NULL) < 1.0) { out = 1; break; }
+    }
+    if (!out) { for (int d = 0; d < 3; ++d) xnew[d] = x[d]; return 0; }
+    double xs[3], aend[3];
+    if (!bisect(o, fr, p, xo, x, xs, aend)) {
+        for (int d = 0; d < 3; ++d) xs[d] = aend[d];
+    }
+    double gs[3];
+    f_at(o, fr, p, xs, gs);
+    double gsn = sqrt(gs[0] * gs[0] + gs[1] * gs[1] + gs[2] * gs[2]);
+    double nout[3] = {-gs[0] / gsn, -gs[1] / gsn, -gs[2] / gsn};
+    uint32_t ctr[4] = {id, t, 1u, 0u}, r[4];
+    philox4x32_10(o->key0, o->key1, ctr, r);
+    double ct = 2.0 * u24(r[0]) - 1.0;
+    double st = sqrt(fmax(0.0, 1.0 - ct * ct));
+    double ph = 2.0 * M_PI * u24(r[1]);
+    double rad = sqrt(2.0 * o->D) * cbrt(u24(r[2]));
+    double xr[3] = {xs[0] + rad * st * cos(ph), xs[1] + rad * st * sin(ph), xs[2] + rad * ct};
+    wall_reflect(o, xr);
+    if (inside_any64(o, fr, xr) >= 0) {
+        double dn = (xr[0] - xs[0]) * nout[0] + (xr[1] - xs[1]) * nout[1] + (xr[2] - xs[2]) * nout[2];
+        if (dn < 0.0) for (int d = 0; d < 3; ++d) xr[d] -= 2.0 * dn * nout[d];
+        wall_reflect(o, xr);
+        if (inside_any64(o, fr, xr) >= 0) {
+            for (int d = 0; d < 3; ++d) xr[d] = aend[d];
+            if (inside_any64(o, fr, xr) >= 0) {
+                for (int d = 0; d < 3; ++d) xnew[d] = xr[d];
+                return 0;
+            }
+        }
+    }
+    for (int d = 0; d < 3; ++d) xnew[d] = xr[d];
+    return 1;
+}
+
+/* One walker, step t -> t+1 (Eq. 2 with dt = 1, then the rules of Section 2.4.2), velocity
+ * field ufield of step t, particle frame fr1 at t+1. Types: I out/out and III in/out move
+ * freely; II in/in is refilled; IV out/in is reflected by Algorithms 1 and 2, and a
+ * reflected point that lands inside a particle or beyond a wall returns the walker to x
+ * ("multiple reflections" in Section 2.4.2). */
+static void walker_advance(orc_t* o, const frame_t* fr1, const double* ufield, uint32_t id, uint32_t t,
+                           const double x[3], double xnew[3])
+{
+    double u[3];
+    trilinear(o, ufield, x, u);
+    uint32_t ctr[4] = {id, t, 0u, 0u}, r[4];
+    philox4x32_10(o->key0, o->key1, ctr, r);
+    double z[3];
+    box_muller(u24(r[0]), u24(r[1]), &z[0], &z[1]);
+    box_muller(u24(r[2]), u24(r[3]), &z[2], NULL);
+    double amp = sqrt(2.0 * o->D * 1.0);
+    double xf[3];
+    for (int d = 0; d < 3; ++d) xf[d] = x[d] + u[d] * 1.0 + amp * z[d];
+    if (!wall_reflect(o, xf)) o->wall_fail++;
+    int pin = o->P ? inside_any64(o, fr1, x) : -1;
+    int qin = o->P ? inside_any64(o, fr1, xf) : -1;
+    if (pin >= 0 && qin >= 0) {                 /* type II: Dirichlet refill */
+        o->cnt_type[1]++;
+        if (!refill(o, fr1, pin, x, id, t, xnew)) o->refill_fail++;
+    } else if (pin >= 0) {                      /* type III: moves out freely */
+        o->cnt_type[2]++;
+        for (int d = 0; d < 3; ++d) xnew[d] = xf[d];
+    } else if (qin >= 0) {                      /* type IV: no-flux reflection */
+        o->cnt_type[3]++;
+        double xi[3], tr[3];
+        if (!bisect(o, fr1, qin, x, xf, xi, NULL)) {
+            o->bisect_fail++;                   /* Reading: the walker stays where it was */
+            for (int d = 0; d < 3; ++d) xnew[d] = x[d];
+            return;
+        }
+        reflect(o, fr1, qin, xi, xf, tr);
+        if (beyond_wall(o, tr) || inside_any64(o, fr1, tr) >= 0) {
+            for (int d = 0; d < 3; ++d) xnew[d] = x[d];
+        } else {
+            for (int d = 0; d < 3; ++d) xnew[d] = tr[d];
+        }
+    } else {                                    /* type I */
+        o->cnt_type[0]++;
+        for (int d = 0; d < 3; ++d) xnew[d] = xf[d];
+    }
+}
+
+static void walkers_step(orc_t* o, long long t)
+{
+    if (o->nw == 0) return;
+    frame_t fr1;
+    frame_alloc(o, &fr1);
+    frame_at(o, t + 1, &fr1);
+    for (long long w = 0; w < o->nw; ++w) {
+        double xn[3];
+        walker_advance(o, &fr1, o->u, (uint32_t)w, (uint32_t)t, o->x + 3 * w, xn);
+        for (int d = 0; d < 3; ++d) o->x[3 * w + d] = xn[d];
+    }
+    frame_free(&fr1);
+}
+
+/* Eq. 16 bins walkers by the cell that holds them: n_s(x, t). Positions are unwrapped;
+ * periodic axes wrap, walled axes clamp x = n into the last cell. */
+static long long walker_cell(const orc_t* o, const double x[3])
+{
+    long long c[3];
+    for (int a = 0; a < 3; ++a) {
+        long long i = (long long)floor(x[a]);
+        if (o->wall[a]) { if (i < 0) i = 0; if (i > o->n[a] - 1) i = o->n[a] - 1; }
+        else i = wrapll(i, o->n[a]);
+        c[a] = i;
+    }
+    return cell_index(o, c[0], c[1], c[2]);
+}
+
+/* ------------------------------------------------------------------------------------------
+ * Exported API (ctypes). All arrays are host arrays owned by the caller.
+ * ------------------------------------------------------------------------------------------ */
+ORC_API void* orc_create(const int dims[3], int q, double tau, double D, uint64_t seed,
+                         int wall_mask, const double F0[3], double Fperiod, double rho0,
+                         const double u_init[3])
+{
+    if (q != 15 && q != 19) return NULL;
+    orc_t* o = (orc_t*)calloc(1, sizeof(orc_t));
+    for (int a = 0; a < 3; ++a) {
+        o->n[a] = dims[a];
+        o->wall[a] = (wall_mask >> a) & 1;
+        o->F0[a] = F0[a];
+        o->u_init[a] = u_init[a];
+    }
+    o->ncell = (long long)dims[0] * dims[1] * dims[2];
+    o->q = q; o->tau = tau; o->D = D;
+    o->key0 = (uint32_t)seed; o->key1 = (uint32_t)(seed >> 32);
+    o->Fperiod = Fperiod; o->rho0 = rho0;
+    o->f = (double*)malloc(sizeof(double) * (size_t)q * o->ncell);
+    o->fn = (double*)malloc(sizeof(double) * (size_t)q * o->ncell);
+    o->u = (double*)calloc(3 * (size_t)o->ncell, sizeof(double));
+    o->rho = (double*)calloc((size_t)o->ncell, sizeof(double));
+    o->cnt = (int*)calloc((size_t)o->ncell, sizeof(int));
+    o->own = (int*)malloc(sizeof(int) * (size_t)o->ncell);
+    for (long long c = 0; c < o->ncell; ++c) o->own[c] = -1;
+    o->solid_time = -1;
+    /* initial state: equilibrium at rho0 and u_init (post-collision of step -1) */
+    for (int m = 0; m < q; ++m) {
+        double fe = feq(q, m, rho0, u_init);
+        for (long long c = 0; c < o->ncell; ++c) o->f[(size_t)m * o->ncell + c] = fe;
+    }
+    for (long long c = 0; c < o->ncell; ++c) {
+        o->rho[c] = rho0;
+        for (int a = 0; a < 3; ++a) o->u[3 * c + a] = u_init[a];
+    }
+    o->coff = (int*)calloc(1, sizeof(int));
+    return o;
+}
+
+ORC_API void orc_destroy(void* h)
+{
+    orc_t* o = (orc_t*)h;
+    if (!o) return;
+    free(o->f); free(o->fn); free(o->u); free(o->rho); free(o->cnt); free(o->own);
+    free(o->coff); free(o->cbody); free(o->kc); free(o->kc32);
+    free(o->org); free(o->amp); free(o->per); free(o->pha); free(o->omg); free(o->Rb);
+    free(o->Fp); free(o->Tp); free(o->x); free(o->x0);
+    free(o);
+}
+
+ORC_API int orc_set_metaballs(void* h, int P, const int* coff, const float* cbody, const float* k,
+                              const double* origin, const double* amp, const double* per,
+                              const double* pha, const double* omega)
+{
+    orc_t* o = (orc_t*)h;
+    free(o->coff); free(o->cbody); free(o->kc); free(o->kc32);
+    free(o->org); free(o->amp); free(o->per); free(o->pha); free(o->omg); free(o->Rb);
+    free(o->Fp); free(o->Tp);
+    o->P = P;
+    o->Nc = coff[P];
+    o->coff = (int*)malloc(sizeof(int) * (size_t)(P + 1));
+    memcpy(o->coff, coff, sizeof(int) * (size_t)(P + 1));
+    o->cbody = (double*)malloc(sizeof(double) * 3 * (size_t)o->Nc + 8);
+    o->kc = (double*)malloc(sizeof(double) * (size_t)o->Nc + 8);
+    o->kc32 = (float*)malloc(sizeof(float) * (size_t)o->Nc + 8);
+    for (int i = 0; i < o->Nc; ++i) {
+        for (int a = 0; a < 3; ++a) o->cbody[3 * i + a] = (double)cbody[3 * i + a];
+        o->kc[i] = (double)k[i];
+        o->kc32[i] = k[i];
+    }
+    size_t p3 = sizeof(double) * 3 * (size_t)P + 8, p1 = sizeof(double) * (size_t)P + 8;
+    o->org = (double*)malloc(p3); o->amp = (double*)malloc(p3); o->omg = (double*)malloc(p3);
+    o->per = (double*)malloc(p1); o->pha = (double*)malloc(p1); o->Rb = (double*)malloc(p1);
+    o->Fp = (double*)calloc(3 * (size_t)P + 1, sizeof(double));
+    o->Tp = (double*)calloc(3 * (size_t)P + 1, sizeof(double));
+    for (int p = 0; p < P; ++p) {
+        for (int a = 0; a < 3; ++a) {
+            o->org[3 * p + a] = origin[3 * p + a];
+            o->amp[3 * p + a] = amp[3 * p + a];
+            o->omg[3 * p + a] = omega ? omega[3 * p + a] : 0.0;
+        }
+        o->per[p] = per[p];
+        o->pha[p] = pha[p];
+    }
+    for (int p = 0; p < P; ++p) o->Rb[p] = bound_radius(o, p);
+    o->solid_time = -1;
+    return 0;
+}
+
+/* Seeding: walker w tries Philox counters (w, a, 2, 0), a = 0, 1, ..., taking three uniforms
+ * as a point lo + U (hi - lo) of the seed box (FP64, rounded to binary32), and keeps the
+ * first point outside every particle at the current time (binary32 test). Walkers that start
+ * inside a particle are removed at the first step in Section 2.4.2; drawing again keeps the
+ * requested count exact. Returns the number of walkers that found no free point. */
+ORC_API long long orc_seed_walkers(void* h, long long n, const double lo[3], const double hi[3],
+                                   int max_attempts)
+{
+    orc_t* o = (orc_t*)h;
+    free(o->x); free(o->x0);
+    o->nw = n;
+    o->x = (double*)malloc(sizeof(double) * 3 * (size_t)n + 8);
+    o->x0 = (double*)malloc(sizeof(double) * 3 * (size_t)n + 8);
+    frame_t fr;
+    frame_alloc(o, &fr);
+    frame_at(o, o->t, &fr);
+    long long fails = 0;
+    for (long long w = 0; w < n; ++w) {
+        float xs[3] = {0.0f, 0.0f, 0.0f};
+        int ok = 0;
+        for (int a = 0; a < max_attempts && !ok; ++a) {
+            uint32_t ctr[4] = {(uint32_t)w, (uint32_t)a, 2u, 0u}, r[4];
+            philox4x32_10(o->key0, o->key1, ctr, r);
+            for (int d = 0; d < 3; ++d) {
+                volatile double span = hi[d] - lo[d];
+                volatile double off = u24(r[d]) * span;
+                xs[d] = (float)(lo[d] + off);
+            }
+            ok = (o->P == 0) || inside_any32(o, &fr, xs) < 0;
+        }
+        if (!ok) fails++;
+        for (int d = 0; d < 3; ++d) o->x[3 * w + d] = o->x0[3 * w + d] = (double)xs[d];
+    }
+    frame_free(&fr);
+    o->seed_fail += fails;
+    return fails;
+}
+
+ORC_API void orc_set_walkers(void* h, long long n, const double* x, const double* x0)
+{
+    orc_t* o = (orc_t*)h;
+    free(o->x); free(o->x0);
+    o->nw = n;
+    o->x = (double*)malloc(sizeof(double) * 3 * (size_t)n + 8);
+    o->x0 = (double*)malloc(sizeof(double) * 3 * (size_t)n + 8);
+    memcpy(o->x, x, sizeof(double) * 3 * (size_t)n);
+    memcpy(o->x0, x0 ? x0 : x, sizeof(double) * 3 * (size_t)n);
+}
+
+/* n timesteps: solid fraction at t, LBM at t, walkers t -> t+1 with the particles at t+1 */
+ORC_API void orc_step(void* h, long long nsteps)
+{
+    orc_t* o = (orc_t*)h;
+    for (long long s = 0; s < nsteps; ++s) {
+        rasterize(o, o->t);
+        lbm_step(o, o->t);
+        walkers_step(o, o->t);
+        o->t++;
+    }
+}
+
+/* LBM only (walkers frozen): used to spin up a flow before walkers are released */
+ORC_API void orc_step_fluid(void* h, long long nsteps)
+{
+    orc_t* o = (orc_t*)h;
+    for (long long s = 0; s < nsteps; ++s) {
+        rasterize(o, o->t);
+        lbm_step(o, o->t);
+        o->t++;
+    }
+}
+
+ORC_API long long orc_time(void* h) { return ((orc_t*)h)->t; }
+ORC_API void orc_set_time(void* h, long long t) { ((orc_t*)h)->t = t; ((orc_t*)h)->solid_time = -1; }
+
+ORC_API void orc_velocity(void* h, double* out)
+{
+    orc_t* o = (orc_t*)h;
+    memcpy(out, o->u, sizeof(double) * 3 * (size_t)o->ncell);
+}
+ORC_API void orc_density(void* h, double* out)
+{
+    orc_t* o = (orc_t*)h;
+    memcpy(out, o->rho, sizeof(double) * (size_t)o->ncell);
+}
+/* Post-collision populations f+(t-1) held at the start of step t, direction-major */
+ORC_API void orc_populations(void* h, double* out)
+{
+    orc_t* o = (orc_t*)h;
+    memcpy(out, o->f, sizeof(double) * (size_t)o->q * o->ncell);
+}
+ORC_API void orc_set_populations(void* h, const double* f)
+{
+    orc_t* o = (orc_t*)h;
+    memcpy(o->f, f, sizeof(double) * (size_t)o->q * o->ncell);
+}
+ORC_API void orc_set_velocity(void* h, const double* u)
+{
+    orc_t* o = (orc_t*)h;
+    memcpy(o->u, u, sizeof(double) * 3 * (size_t)o->ncell);
+}
+ORC_API void orc_solid(void* h, long long t, int* count, int* owner)
+{
+    orc_t* o = (orc_t*)h;
+    if (o->solid_time != t) rasterize(o, t);
+    memcpy(count, o->cnt, sizeof(int) * (size_t)o->ncell);
+    memcpy(owner, o->own, sizeof(int) * (size_t)o->ncell);
+}
+ORC_API void orc_walkers(void* h, double* x, double* x0)
+{
+    orc_t* o = (orc_t*)h;
+    memcpy(x, o->x, sizeof(double) * 3 * (size_t)o->nw);
+    if (x0) memcpy(x0, o->x0, sizeof(double) * 3 * (size_t)o->nw);
+}
+
+/* Eq. 16 with m_s = 1 and dx = 1: the count of walkers per cell (Reading: the solid fraction
+ * named beside Eq. 16 is reported separately, not folded in). */
+ORC_API void orc_concentration(void* h, uint32_t* out)
+{
+    orc_t* o = (orc_t*)h;
+    memset(out, 0, sizeof(uint32_t) * (size_t)o->ncell);
+    for (long long w = 0; w < o->nw; ++w) out[walker_cell(o, o->x + 3 * w)]++;
+}
+
+/* Binning of caller-given binary32 positions (the exactness check of the cell assignment) */
+ORC_API void orc_bin_positions(void* h, long long n, const float* pos, int64_t* cell)
+{
+    orc_t* o = (orc_t*)h;
+    for (long long w = 0; w < n; ++w) {
+        double x[3] = {pos[3 * w], pos[3 * w + 1], pos[3 * w + 2]};
+        cell[w] = walker_cell(o, x);
+    }
+}
+
+/* Walker moments: out = {N, mean(x - x0)[3], var(x - x0)[3], mean(x)[3], var(x)[3]}
+ * (population variances, two passes). Section 4 fits the z-variance against time (Eq. 38). */
+ORC_API void orc_moments(void* h, double out[13])
+{
+    orc_t* o = (orc_t*)h;
+    for (int m = 0; m < 13; ++m) out[m] = 0.0;
+    out[0] = (double)o->nw;
+    if (o->nw == 0) return;
+    double md[3] = {0, 0, 0}, mx[3] = {0, 0, 0};
+    for (long long w = 0; w < o->nw; ++w)
+        for (int a = 0; a < 3; ++a) {
+            md[a] += o->x[3 * w + a] - o->x0[3 * w + a];
+            mx[a] += o->x[3 * w + a];
+        }
+    for (int a = 0; a < 3; ++a) { md[a] /= (double)o->nw; mx[a] /= (double)o->nw; }
+    double vd[3] = {0, 0, 0}, vx[3] = {0, 0, 0};
+    for (long long w = 0; w < o->nw; ++w)
+        for (int a = 0; a < 3; ++a) {
+            double d = o->x[3 * w + a] - o->x0[3 * w + a] - md[a];
+            double e = o->x[3 * w + a] - mx[a];
+            vd[a] += d * d;
+            vx[a] += e * e;
+        }
+    for (int a = 0; a < 3; ++a) {
+        out[1 + a] = md[a];
+        out[4 + a] = vd[a] / (double)o->nw;
+        out[7 + a] = mx[a];
+        out[10 + a] = vx[a] / (double)o->nw;
+    }
+}
+
+/* {sum rho, sum_i f_i e_i (3)} over all cells at the last LBM step (pre-collision) */
+ORC_API void orc_mass_momentum(void* h, double out[4])
+{
+    orc_t* o = (orc_t*)h;
+    out[0] = o->mass;
+    for (int a = 0; a < 3; ++a) out[1 + a] = o->mom[a];
+}
+
+/* {F_p (3), T_p (3)} per particle at the last LBM step */
+ORC_API void orc_forces(void* h, double* out)
+{
+    orc_t* o = (orc_t*)h;
+    for (int p = 0; p < o->P; ++p)
+        for (int a = 0; a < 3; ++a) {
+            out[6 * p + a] = o->Fp[3 * p + a];
+            out[6 * p + 3 + a] = o->Tp[3 * p + a];
+        }
+}
+
+/* {type I, II, III, IV counts, bisection failures, refill failures, wall failures, seed failures} */
+ORC_API void orc_counters(void* h, long long out[8])
+{
+    orc_t* o = (orc_t*)h;
+    for (int m = 0; m < 4; ++m) out[m] = o->cnt_type[m];
+    out[4] = o->bisect_fail; out[5] = o->refill_fail; out[6] = o->wall_fail; out[7] = o->seed_fail;
+}
+
+/* Sampled checks at full size: the step-t update of chosen cells from the populations now
+ * held (f+(t-1)), without changing the state. fout [q n] direction-major, uout [3 n]. */
+ORC_API void orc_lbm_cells(void* h, long long n, const int64_t* cells, double* fout, double* uout,
+                           double* rhoout)
+{
+    orc_t* o = (orc_t*)h;
+    if (o->solid_time != o->t) rasterize(o, o->t);
+    frame_t fr;
+    frame_alloc(o, &fr);
+    frame_at(o, o->t, &fr);
+    double F[3];
+    body_force(o, o->t, F);
+    for (long long m = 0; m < n; ++m) {
+        long long c = cells[m];
+        long long i = c % o->n[0], j = (c / o->n[0]) % o->n[1], k = c / ((long long)o->n[0] * o->n[1]);
+        double fi[19], fo[19], u[3], rho, dp[3];
+        pull_cell(o, i, j, k, fi);
+        collide_cell(o, &fr, o->t, i, j, k, o->cnt[c], o->own[c], fi, F, fo, u, &rho, dp);
+        for (int d = 0; d < o->q; ++d) fout[(size_t)d * n + m] = fo[d];
+        for (int a = 0; a < 3; ++a) uout[3 * m + a] = u[a];
+        if (rhoout) rhoout[m] = rho;
+    }
+    frame_free(&fr);
+}
+
+/* Sampled walker checks: advance caller-given walkers (positions x [3n], ids) by one step at
+ * the current time t with the velocity field now held (set with orc_set_velocity). */
+ORC_API void orc_walkers_advance(void* h, long long n, const double* x, const uint32_t* ids, double* xout)
+{
+    orc_t* o = (orc_t*)h;
+    frame_t fr1;
+    frame_alloc(o, &fr1);
+    frame_at(o, o->t + 1, &fr1);
+    for (long long w = 0; w < n; ++w) walker_advance(o, &fr1, o->u, ids[w], (uint32_t)o->t, x + 3 * w, xout + 3 * w);
+    frame_free(&fr1);
+}
+
+/* ---- single-function entry points for the CPU pins ---- */
+ORC_API void orc_philox(uint64_t seed, const uint32_t ctr[4], uint32_t out[4])
+{
+    philox4x32_10((uint32_t)seed, (uint32_t)(seed >> 32), ctr, out);
+}
+
+/* The three step normals of walker id at step t (counter (id, t, 0, 0)) */
+ORC_API void orc_step_normals(uint64_t seed, uint32_t id, uint32_t t, double z[3])
+{
+    uint32_t ctr[4] = {id, t, 0u, 0u}, r[4];
+    philox4x32_10((uint32_t)seed, (uint32_t)(seed >> 32), ctr, r);
+    box_muller(u24(r[0]), u24(r[1]), &z[0], &z[1]);
+    box_muller(u24(r[2]), u24(r[3]), &z[2], NULL);
+}
+
+ORC_API double orc_metaball(void* h, long long t, int p, const double x[3], double g[3])
+{
+    orc_t* o = (orc_t*)h;
+    frame_t fr;
+    frame_alloc(o, &fr);
+    frame_at(o, t, &fr);
+    double f = f_at(o, &fr, p, x, g);
+    frame_free(&fr);
+    return f;
+}
+
+ORC_API float orc_metaball32(void* h, long long t, int p, const float x[3])
+{
+    orc_t* o = (orc_t*)h;
+    frame_t fr;
+    frame_alloc(o, &fr);
+    frame_at(o, t, &fr);
+    float f = metaball32(o, &fr, p, x);
+    frame_free(&fr);
+    return f;
+}
+
+ORC_API double orc_bound_radius(void* h, int p) { return ((orc_t*)h)->Rb[p]; }
+
+ORC_API int orc_inside(void* h, long long t, const double x[3])
+{
+    orc_t* o = (orc_t*)h;
+    frame_t fr;
+    frame_alloc(o, &fr);
+    frame_at(o, t, &fr);
+    int p = inside_any64(o, &fr, x);
+    frame_free(&fr);
+    return p;
+}
+
+ORC_API int orc_bisect(void* h, long long t, int p, const double a[3], const double b[3], double xi[3])
+{
+    orc_t* o = (orc_t*)h;
+    frame_t fr;
+    frame_alloc(o, &fr);
+    frame_at(o, t, &fr);
+    int ok = bisect(o, &fr, p, a, b, xi, NULL);
+    frame_free(&fr);
+    return ok;
+}
+
+ORC_API void orc_reflect(void* h, long long t, int p, const double xint[3], const double xf[3], double xnew[3])
+{
+    orc_t* o = (orc_t*)h;
+    frame_t fr;
+    frame_alloc(o, &fr);
+    frame_at(o, t, &fr);
+    reflect(o, &fr, p, xint, xf, xnew);
+    frame_free(&fr);
+}
+
+ORC_API int orc_refill(void* h, long long t, int p, const double x[3], uint32_t id, double xnew[3])
+{
+    orc_t* o = (orc_t*)h;
+    frame_t fr;
+    frame_alloc(o, &fr);
+    frame_at(o, t + 1, &fr);
+    int ok = refill(o, &fr, p, x, id, (uint32_t)t, xnew);
+    frame_free(&fr);
+    return ok;
+}
+
+ORC_API void orc_trilinear(void* h, const double x[3], double u[3]) { trilinear((orc_t*)h, ((orc_t*)h)->u, x, u); }
+
+ORC_API void orc_pose(void* h, long long t, int p, double org[3], double vel[3])
+{
+    double R[3][3];
+    particle_pose((orc_t*)h, t, p, org, vel, R);
+}
+
+ORC_API void orc_lattice(int q, int* e, double* w)
+{
+    for (int i = 0; i < q; ++i) {
+        for (int a = 0; a < 3; ++a) e[3 * i + a] = lattice_e(q, i)[a];
+        w[i] = lattice_weight(q, i);
+    }
+}
