@@ -1,0 +1,331 @@
+#!/usr/bin/env python3
+"""Benchmark of the fused fluid-solute step (LBM stream-collide on partially-saturated cells +
+random-walk advance of solute walkers) on the 256^3 oscillator workload, one GB300 per rank.
+
+One "step" is one pass of the whole path: particle poses and brick lists, metaball
+rasterisation, the fused LBM kernel, the walker advance, and -- every 16 steps -- the counting
+sort/binning of walkers (concentration) and the FP64 walker moments. Inputs are resident in HBM
+and larger than L2 (each population buffer is 1 GB), so no L2 flush is needed.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0). With N > 1 (torchrun) every rank advances its own replica
+(weak scaling, no collective on the data path); the time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "LBM MLUPS + walker-steps/s and %HBM roofline, FP32/FP16-shift vs plain; p99 latency"
+STORE_NAMES = {0: "fp32", 1: "fp32_shift", 2: "fp16_shift"}
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "lbm_kernel_oscillator_256.md")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=32)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--walkers", type=int, default=10_000_000)
+    ap.add_argument("--particles", type=int, default=64)
+    ap.add_argument("--q", type=int, default=15)
+    ap.add_argument("--storage", type=int, default=1)
+    ap.add_argument("--sort-interval", type=int, default=16)
+    ap.add_argument("--moment-interval", type=int, default=16)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload(a):
+    from paper_2308_05007_gb300 import inputs as I
+    w = I.oscillator(n=a.n, n_particles=a.particles, n_walkers=a.walkers, q=a.q, storage=a.storage)
+    return I.with_(w, sort_interval=a.sort_interval, moment_interval=a.moment_interval)
+
+
+def bytes_per_step(w, n_cells, s):
+    """Algorithmic HBM bytes of one step: populations read + written once (2 Q s per cell), the
+    velocity field written by the LBM kernel and gathered once by walkers (12 + 12 B per cell),
+    each walker's float4 read and written (32 B)."""
+    return n_cells * (2 * w.q * s + 24) + 32 * w.n_walkers
+
+
+def lbm_bytes_per_launch(w, n_cells, s):
+    """Algorithmic bytes of one launch of the LBM kernel: 2 Q s per cell + 12 B of velocity."""
+    return n_cells * (2 * w.q * s + 12)
+
+
+def config_dict(a, w):
+    return {
+        "workload": (f"oscillator {a.n}^3 D3Q{w.q} {STORE_NAMES[w.storage]}, no-slip z-walls, tau 0.7, "
+                     f"F=5e-6 sin(2 pi t/2000) x; {a.particles} metaball particles (4-8 centres, "
+                     f"sigma 4, k U[20,60]) oscillating 5 sin(2 pi t/2000) x; "
+                     f"{a.walkers:.0e} walkers, D=0.005"),
+        "cells": w.n_cells, "walkers": w.n_walkers, "particles": a.particles, "q": w.q,
+        "storage": STORE_NAMES[w.storage], "sort_interval": w.sort_interval,
+        "moment_interval": w.moment_interval,
+        "l2": "inputs larger than L2 (populations 2 x %.2f GB), no flush" % (w.n_cells * w.q * (2 if w.storage == 2 else 4) / 1e9),
+        "graphs": "CUDA graph per %d steps" % max(w.sort_interval, w.moment_interval, 2),
+    }
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.gpu), "-lms", "200"], stdout=open(self.path, "w"),
+                                         stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        self.proc.wait()
+        rows = []
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) >= 9:
+                rows.append(p)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = max(float(r[2]) for r in rows if r[2].replace(".", "").isdigit())
+        load = [x for x in sm if x > 0.5 * mx] or sm
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(load), "sm_max_mhz": mx, "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows
+                                                          if r[3].replace(".", "").isdigit())}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        return {"hbm_gbs": 6800.0, "fallback": True}
+
+
+def profiled_traffic(a):
+    """Per-launch DRAM bytes of the LBM kernel from the committed ncu summary, if that summary
+    was taken on this workload and on the current kernel source (else None)."""
+    import hashlib
+    try:
+        text = open(PROFILE_SUMMARY).read()
+    except OSError:
+        return None
+    src = open(os.path.join(ROOT, "paper_2308_05007_gb300", "csrc", "rwmi_fluid.cu"), "rb").read()
+    digest = hashlib.sha256(src).hexdigest()[:16]
+    vals = {}
+    for line in text.splitlines():
+        if ":" in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("source_sha256_16") != digest or vals.get("workload_n") != str(a.n):
+        return None
+    try:
+        return float(vals["traffic_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def cpu_baseline(a, w):
+    """The FP64 oracle as it stands, single-threaded, on a bounded sample of the same workload:
+    one fluid step (solid fraction + LBM) of the full box, plus one walker step of a 1e4-walker
+    sample; the full-step time is extrapolated to all walkers."""
+    import numpy as np
+    from oracle.oracle import Oracle
+    from paper_2308_05007_gb300 import inputs as I
+    ws = I.with_(w, n_walkers=10000)
+    t0 = time.perf_counter()
+    o = Oracle.from_workload(ws)
+    t_setup = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    o.step_fluid(1)
+    t_fluid = time.perf_counter() - t0
+    x, _ = o.walkers()
+    o.set_time(o.t - 1)
+    t0 = time.perf_counter()
+    o.walkers_advance(x, np.arange(len(x), dtype=np.uint32))
+    t_walk = (time.perf_counter() - t0) * (w.n_walkers / len(x))
+    t_step = t_fluid + t_walk
+    return {
+        "value": w.n_cells / t_step / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+        "walker_steps_per_s": w.n_walkers / t_step,
+        "sample": (f"1 fluid step of the full {a.n}^3 box ({t_fluid:.1f} s) + 1 walker step of 1e4 "
+                   f"walkers ({t_walk * len(x) / w.n_walkers:.2f} s), walker time scaled to "
+                   f"{w.n_walkers:.0e}; setup {t_setup:.1f} s untimed"),
+        "s_per_step": t_step,
+    }
+
+
+def run_reference(a, rank):
+    if rank != 0:
+        return
+    w = workload(a)
+    cb = cpu_baseline(a, w)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "MLUPS", "n_gpus": a.gpus,
+        "steps": 1, "warmup": 0, "ms_per_step": cb["s_per_step"] * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_dict(a, w),
+        "walker_steps_per_s": cb["walker_steps_per_s"],
+        "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
+        "e2e": {"value": cb["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "note": "FP64 CPU oracle (the reference arm of this build); --steps/--warmup are replaced by the bounded sample",
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    a = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if a.impl == "reference":
+        run_reference(a, rank)
+        return
+    import numpy as np
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2308_05007_gb300.rwmi import Simulation
+
+    w = workload(a)
+    s_bytes = 2 if w.storage == 2 else 4
+    stream = torch.cuda.Stream()
+    sim = Simulation.from_workload(w, seed_walkers=False)
+    sim.set_stream(stream)
+    sim.seed_walkers(w.n_walkers, *w.walker_box)
+    L = 16
+    warm = max(a.warmup, 3)
+    warm = (warm + L - 1) // L * L
+    steps = max(a.steps, L)
+    with torch.cuda.stream(stream):
+        sim.step(warm)
+        assert sim.sync() >= 0
+        # per-phase GPU time (CUDA events on the launching stream, eager launches)
+        phases = sim.step_timed(L)
+        n_timed_phase_steps = L
+        # the timed region
+        clocks = Clocks(torch.cuda.current_device())
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        clocks.start()
+        l0 = sim.launch_count
+        ev0.record(stream)
+        sim.step(steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        launches = sim.launch_count - l0
+        clk = clocks.stop()
+        if dist:
+            dist.barrier()
+        ms = ev0.elapsed_time(ev1)
+        st = sim.sync()
+        assert st >= 0, st
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    sec = ms / 1e3
+    mlups = world * w.n_cells * steps / sec / 1e6
+    wsps = world * w.n_walkers * steps / sec
+
+    # e2e through the public API with host buffers: H2D of the walker positions from pinned host
+    # memory, the steps, D2H of the concentration field and the moments
+    e2e = None
+    if not a.no_e2e:
+        pos, _, _ = sim.walkers(with_x0=False)
+        pinned = torch.from_numpy(pos).pin_memory()
+        conc = torch.empty(w.n_cells, dtype=torch.int32).pin_memory()
+        with torch.cuda.stream(stream):
+            torch.cuda.synchronize()
+            if dist:
+                dist.barrier()
+            t0 = time.perf_counter()
+            sim.set_walkers(pinned)
+            sim.step(steps)
+            sim.concentration(out=conc)
+            mom = sim.walker_moments()
+            torch.cuda.synchronize()
+            te = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([te], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            te = float(t.item())
+        assert int(conc.sum()) == w.n_walkers and mom[0] == w.n_walkers
+        e2e = {"value": world * w.n_cells * steps / te / 1e6, "unit": "MLUPS",
+               "h2d_bytes_per_step": pinned.numel() * 4 / steps,
+               "d2h_bytes_per_step": (conc.numel() * 4 + 13 * 8) / steps,
+               "walker_steps_per_s": world * w.n_walkers * steps / te}
+
+    if rank != 0:
+        return
+    peaks = measured_peaks()
+    lbm_ms = phases["lbm"] / n_timed_phase_steps
+    achieved = lbm_bytes_per_launch(w, w.n_cells, s_bytes) / (lbm_ms / 1e3) / 1e9
+    peak = float(peaks["hbm_gbs"])
+    traffic = profiled_traffic(a)
+    step_bytes = bytes_per_step(w, w.n_cells, s_bytes)
+    line = {
+        "metric": METRIC, "value": mlups, "unit": "MLUPS", "n_gpus": world, "steps": steps,
+        "warmup": warm, "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config_dict(a, w),
+        "walker_steps_per_s": wsps,
+        "step_hbm_frac": step_bytes / (ms / steps / 1e3) / 1e9 / peak,
+        "step_algorithmic_bytes": step_bytes,
+        "roofline": {"kernel": "lbm_kernel", "bound": "hbm", "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                     "algorithmic_bytes_per_launch": lbm_bytes_per_launch(w, w.n_cells, s_bytes),
+                     "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if not peaks.get("fallback") else "fallback"},
+        "phase_ms_per_step": {k: v / n_timed_phase_steps for k, v in phases.items()},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    if e2e:
+        line["e2e"] = e2e
+    if world == 1 and not a.no_cpu_baseline:
+        cb = cpu_baseline(a, w)
+        line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+    print(json.dumps(line), flush=True)
+    sim.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

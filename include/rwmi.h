@@ -1,0 +1,229 @@
+/*
+ * rwmi.h -- C ABI of the GB300 (sm_103a) fluid-solute step of RW-MI-DELBM
+ * (Zhao, Zhang, Li and Galindo-Torres, arXiv 2308.05007).
+ *
+ * One timestep t -> t+1 of a simulation context runs, on one GPU:
+ *   - the prescribed rigid motion of metaball particles (Eq. 3 shapes; the DEM of Eq. 4 is
+ *     held to given trajectories) and their partially-saturated solid fraction per cell;
+ *   - a fused lattice Boltzmann pull-stream + BGK collide (Eqs. 12-15; D3Q19 as in Section 2.3,
+ *     or D3Q15) with partially-saturated-cell solid coupling and Guo body forcing, which also
+ *     yields the hydrodynamic force and torque on every particle;
+ *   - the random-walk advance of every solute walker (Eq. 2) with the velocity interpolated
+ *     from the lattice (Section 2.4.1) and the walker/particle rules of Section 2.4.2:
+ *     refill of type II walkers, Algorithm 1 (bisection) and Algorithm 2 (specular
+ *     reflection) for type IV walkers, free motion for types I and III;
+ *   - on request or at a set cadence: the counting sort of walkers by cell whose histogram is
+ *     the concentration of Eq. 16, and FP64 walker moments (the input of Eqs. 38-40).
+ *
+ * Conventions for every entry point:
+ *   - Lattice units: dx = dt = 1, c_s^2 = 1/3, kinematic viscosity (tau - 1/2)/3.
+ *   - Cell (i, j, k) is [i, i+1) x [j, j+1) x [k, k+1); its lattice node sits at the centre.
+ *     Flat cell index c = i + nx (j + ny k). Walker positions are unwrapped.
+ *   - Ownership: the library owns all device state and allocates it in rwmi_create,
+ *     rwmi_set_metaballs and rwmi_seed_walkers / rwmi_set_walkers. The caller owns every input
+ *     and output array; inputs are copied during the call. An output pointer may be host
+ *     (pageable or pinned) or device memory of the context's GPU; the library tells them apart
+ *     with cudaPointerGetAttributes.
+ *   - Streams: all GPU work of a context is issued on one stream (rwmi_set_stream; default: a
+ *     stream the context creates). rwmi_step is asynchronous; getters synchronise that stream.
+ *   - Errors: every call returns an rwmi_status. RWMI_E_INVALID leaves the context unchanged.
+ *     Any other negative status leaves it unusable until rwmi_destroy. Positive values are
+ *     warnings. rwmi_last_error gives a message. Nothing is thrown across the ABI; nothing
+ *     exits. Calls on one context are not thread-safe.
+ */
+#ifndef RWMI_H
+#define RWMI_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define RWMI_API __attribute__((visibility("default")))
+#else
+#define RWMI_API
+#endif
+
+typedef struct rwmi_ctx rwmi_ctx;
+
+typedef enum {
+    RWMI_OK = 0,
+    RWMI_W_BISECT = 1,       /* Algorithm 1 found no point with |f - 1| < 1e-3 in 200 steps for
+                                some walker (Section 2.4.2: "an error is reported"); the walker
+                                stayed where it was. Also refill failures. */
+    RWMI_W_SEED = 2,         /* some walker found no free seed point (see rwmi_seed_walkers) */
+    RWMI_E_INVALID = -1,     /* bad argument or size; context unchanged */
+    RWMI_E_OOM = -2,         /* device allocation failed */
+    RWMI_E_CUDA = -3,        /* a CUDA runtime call or kernel launch failed */
+    RWMI_E_NONFINITE = -4,   /* NaN/Inf in the FP64 mass sum or a walker velocity */
+    RWMI_E_TIMEOUT = -5,     /* a bounded device wait gave up */
+    RWMI_E_STATE = -6        /* call out of order (e.g. stepping before configuration ends) */
+} rwmi_status;
+
+/* Storage of the populations in HBM; arithmetic is FP32 in every case. */
+enum {
+    RWMI_STORE_FP32 = 0,          /* f_i as binary32 */
+    RWMI_STORE_FP32_SHIFT = 1,    /* f_i - w_i rho0 as binary32 (default; keeps u ~ 1e-4 exact
+                                     to ~1e-7 relative) */
+    RWMI_STORE_FP16_SHIFT = 2     /* f_i - w_i rho0 as binary16 */
+};
+
+typedef struct {
+    int32_t q;                 /* 15 (D3Q15) or 19 (D3Q19, Section 2.3). Default 19. */
+    int32_t storage;           /* RWMI_STORE_*. Default RWMI_STORE_FP32_SHIFT. */
+    uint32_t wall_mask;        /* bit a: no-slip walls on both faces normal to axis a
+                                  (half-way bounce-back for the fluid, specular reflection for
+                                  walkers). Other axes are periodic. Default 0. */
+    double body_force[3];      /* force density F0 (lattice units). Default 0. */
+    double force_period;       /* F(t) = F0 sin(2 pi t / force_period); 0: constant F0 */
+    double rho0;               /* reference density (initial state, shift). Default 1. */
+    double init_velocity[3];   /* initial equilibrium velocity. Default 0. */
+    int32_t sort_interval;     /* sort walkers by cell every this many steps (0: never).
+                                  Default 16. The sort also refreshes the concentration. */
+    int32_t moment_interval;   /* append FP64 walker moments to the series every this many
+                                  steps (0: never). Default 0. */
+    int32_t use_graphs;        /* replay captured CUDA graphs for repeated steps. Default 1. */
+} rwmi_config;
+
+/* Fills *cfg with the defaults listed above. */
+RWMI_API void rwmi_config_defaults(rwmi_config* cfg);
+
+/* Creates a context for a box of dims[0] x dims[1] x dims[2] cells on the current CUDA
+ * device, with BGK relaxation time tau (Eq. 12; tau > 1/2), walker diffusion coefficient D
+ * (Eq. 2; D >= 0) and the 64-bit Philox key seed that fixes all walker noise. The context
+ * takes the default configuration; change it with rwmi_configure before the first step.
+ * Sizes: each dim >= 1; total cells <= 2^31 - 1. */
+RWMI_API rwmi_status rwmi_create(rwmi_ctx** ctx, const int32_t dims[3], double tau, double D,
+                                 uint64_t seed);
+
+/* Replaces the configuration. Allowed only before the first rwmi_step; resets the fluid to
+ * the equilibrium at (rho0, init_velocity). */
+RWMI_API rwmi_status rwmi_configure(rwmi_ctx* ctx, const rwmi_config* cfg);
+
+/* Issues all later GPU work of the context on this cudaStream_t (e.g. a torch stream). */
+RWMI_API rwmi_status rwmi_set_stream(rwmi_ctx* ctx, void* cuda_stream);
+
+/* Metaball particles, Eq. 3: particle p owns control points center_offsets[p] ..
+ * center_offsets[p+1]-1, with body-frame positions centers_body[3 i .. 3 i + 2] relative to
+ * the particle origin and weights k[i] > 0 (f(x) = sum k_i / |x - x_i|^2, inside where f >= 1).
+ * The origin follows origin + amplitude sin(2 pi t / period + phase) (period 0: at rest) and
+ * the body spins with constant angular velocity omega (rad per step, may be NULL for none).
+ * Arrays: center_offsets [P+1], centers_body [3 Nc], k [Nc], origin/amplitude/omega [3P],
+ * period/phase [P], host memory. Limits: P <= 511, Nc <= 65535. Replaces earlier particles.
+ * Allowed before the first step only. */
+RWMI_API rwmi_status rwmi_set_metaballs(rwmi_ctx* ctx, int32_t n_particles,
+                                        const int32_t* center_offsets, const float* centers_body,
+                                        const float* k, const double* origin,
+                                        const double* amplitude, const double* period,
+                                        const double* phase, const double* omega);
+
+/* Seeds n walkers uniformly in the fluid part of the box [box_lo, box_hi] (inside the domain)
+ * at the current time. Walker w draws Philox counters (w, a, 2, 0), a = 0, 1, ..., < 1000,
+ * takes the point box_lo + U (box_hi - box_lo) and keeps the first one outside every particle
+ * (Section 2.4.2 removes walkers that start inside; drawing again keeps the count exact).
+ * Returns RWMI_W_SEED if some walker found no free point (it is then left at its last draw).
+ * Walker ids are 0 .. n-1; start positions are kept for rwmi_walker_moments. n <= 2^31 - 1. */
+RWMI_API rwmi_status rwmi_seed_walkers(rwmi_ctx* ctx, int64_t n, const double box_lo[3],
+                                       const double box_hi[3]);
+
+/* Sets n walkers at the given binary32 positions pos[3 w .. 3 w + 2] (host or device), with
+ * ids 0 .. n-1 and start positions equal to pos. Positions on walled axes must lie in [0, n]. */
+RWMI_API rwmi_status rwmi_set_walkers(rwmi_ctx* ctx, int64_t n, const float* pos);
+
+/* Advances n timesteps (asynchronous on the context's stream). Step t: solid fraction from
+ * the particles at t, LBM at t, walkers from t to t+1 with the particles at t+1; walker noise
+ * uses Philox counter (walker id, t, 0, 0). n >= 0. */
+RWMI_API rwmi_status rwmi_step(rwmi_ctx* ctx, int32_t n);
+
+/* Phases of one timestep, for rwmi_step_timed. */
+enum {
+    RWMI_PHASE_RASTER = 0,   /* solid fraction of the particles at t */
+    RWMI_PHASE_LBM = 1,      /* fused pull-stream + collide at t */
+    RWMI_PHASE_POSE = 2,     /* particle poses, brick lists and body force of t+1 */
+    RWMI_PHASE_WALKERS = 3,  /* walker advance t -> t+1 */
+    RWMI_PHASE_SORT = 4,     /* counting sort / binning (every sort_interval steps) */
+    RWMI_PHASE_MOMENTS = 5,  /* moment series (every moment_interval steps) */
+    RWMI_NPHASE = 6
+};
+
+/* Like rwmi_step but launches each step without graphs and brackets every phase with CUDA
+ * events on the context's stream; waits for completion and adds the GPU time of each phase
+ * (milliseconds, summed over the n steps) to phase_ms[RWMI_NPHASE]. Same results as rwmi_step. */
+RWMI_API rwmi_status rwmi_step_timed(rwmi_ctx* ctx, int32_t n, double* phase_ms);
+
+/* Waits for the context's stream and returns the first pending device condition:
+ * RWMI_E_NONFINITE, RWMI_W_BISECT, or RWMI_OK. Clears the warning counters it reports. */
+RWMI_API rwmi_status rwmi_sync(rwmi_ctx* ctx);
+
+/* Number of completed steps. */
+RWMI_API rwmi_status rwmi_time(rwmi_ctx* ctx, int64_t* t);
+
+/* Eq. 16 with m_s = 1, dx = 1: out[c] = number of walkers in cell c (uint32, nx*ny*nz). */
+RWMI_API rwmi_status rwmi_concentration(rwmi_ctx* ctx, uint32_t* out);
+
+/* FP64 walker moments of the current positions x and start positions x0:
+ * out = {N, mean(x - x0)[3], var(x - x0)[3], mean(x)[3], var(x)[3]} (population variances).
+ * Section 4 fits the z-variance against time (Eq. 38) to get the dispersion coefficient. */
+RWMI_API rwmi_status rwmi_walker_moments(rwmi_ctx* ctx, double out[13]);
+
+/* The moments recorded every moment_interval steps: up to max_rows rows of
+ * {t, the 13 values above}; *n_rows receives the number written (oldest first). */
+RWMI_API rwmi_status rwmi_moment_series(rwmi_ctx* ctx, double* out, int32_t max_rows,
+                                        int32_t* n_rows);
+
+/* Velocity of the last LBM step, u = (sum_i f_i e_i + F/2) / rho (Eq. 15 with Guo's half
+ * force): out[3 c + a], binary32, 3*nx*ny*nz values. */
+RWMI_API rwmi_status rwmi_velocity(rwmi_ctx* ctx, float* out);
+
+/* Density of the last LBM step (Eq. 14), binary32, nx*ny*nz values. */
+RWMI_API rwmi_status rwmi_density(rwmi_ctx* ctx, float* out);
+
+/* Populations now held (post-collision of the last step, f_i unshifted) as FP64:
+ * out[i * ncell + c], directions in the library's order (rwmi_lattice). */
+RWMI_API rwmi_status rwmi_populations(rwmi_ctx* ctx, double* out);
+
+/* The library's velocity set: e[3 i + a] (int32) and w[i] (double) for its q directions. */
+RWMI_API rwmi_status rwmi_lattice(rwmi_ctx* ctx, int32_t* e, double* w, int32_t* q);
+
+/* Solid fraction data of time t (the last rasterised step): count[c] (0..64 sub-samples
+ * inside a particle, epsilon = count / 64) and owner[c] (particle index, -1 if none). */
+RWMI_API rwmi_status rwmi_solid(rwmi_ctx* ctx, int32_t* count, int32_t* owner);
+
+/* {sum rho, sum_i f_i e_i (3 components)} over all cells at the last LBM step (FP64 sums). */
+RWMI_API rwmi_status rwmi_mass_momentum(rwmi_ctx* ctx, double out[4]);
+
+/* Hydrodynamic force and torque on each particle at the last LBM step, FP64:
+ * out[6 p .. 6 p + 2] = F_p, out[6 p + 3 .. 6 p + 5] = T_p about the particle origin. */
+RWMI_API rwmi_status rwmi_particle_forces(rwmi_ctx* ctx, double* out);
+
+/* Walker state: out[4 w .. 4 w + 3] = {x, y, z, id} (binary32; id as a float-coded integer)
+ * in the library's current (cell-sorted) order; x0 (may be NULL) receives the start
+ * positions, 3 per walker, in the same order. */
+RWMI_API rwmi_status rwmi_walkers(rwmi_ctx* ctx, float* out, float* x0);
+
+/* Device counters since creation: {type I, II, III, IV walker steps (0 unless counting is
+ * enabled at build time), Algorithm 1 failures, refill failures, wall failures, seed failures}. */
+RWMI_API rwmi_status rwmi_counters(rwmi_ctx* ctx, int64_t out[8]);
+
+/* Checkpoint and restart: populations, walkers (positions, start positions), the step
+ * counter and the particle table. A restart continues bit-identically (noise is keyed by
+ * walker id and step). */
+RWMI_API rwmi_status rwmi_save(rwmi_ctx* ctx, const char* path);
+RWMI_API rwmi_status rwmi_load(rwmi_ctx* ctx, const char* path);
+
+/* Message of the last failing call on this context (static storage of the context). */
+RWMI_API const char* rwmi_last_error(const rwmi_ctx* ctx);
+
+/* Number of kernel launches the context has issued (for launch accounting). */
+RWMI_API int64_t rwmi_launch_count(const rwmi_ctx* ctx);
+
+/* Frees every resource of the context; NULL is allowed. */
+RWMI_API void rwmi_destroy(rwmi_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RWMI_H */

@@ -1,0 +1,911 @@
+// rwmi_api.cu -- host side of the C ABI declared in include/rwmi.h: context state, device
+// memory, the per-step launch sequence (replayed from captured CUDA graphs), read-back and
+// checkpointing. Every step of the method runs in the kernels of rwmi_fluid.cu and
+// rwmi_walkers.cu; this file only sequences them.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "rwmi.h"
+#include "rwmi_internal.cuh"
+
+using namespace rwmi;
+
+namespace {
+
+constexpr int SERIES_ROWS = 65536;
+constexpr int SERIES_COLS = 14;
+constexpr uint64_t CKPT_MAGIC = 0x31494d5752ULL;  // "RWMI1"
+
+struct GraphKey {
+  int fcur, pcur;
+  bool operator<(const GraphKey& o) const { return fcur != o.fcur ? fcur < o.fcur : pcur < o.pcur; }
+};
+
+struct GraphEntry {
+  cudaGraphExec_t exec = nullptr;
+  int64_t launches = 0;
+};
+
+}  // namespace
+
+struct rwmi_ctx {
+  // configuration
+  int n[3];
+  int64_t ncell;
+  double tau, D;
+  uint64_t seed;
+  rwmi_config cfg;
+  Geom g;
+  int device = 0, nsm = 152;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  bool stepped = false;
+  std::string err;
+
+  // device state
+  void* f[2] = {nullptr, nullptr};
+  float* u = nullptr;
+  uint16_t* solid = nullptr;
+  int64_t* d_T = nullptr;
+  unsigned int* ticket = nullptr;
+  unsigned long long* status = nullptr;
+  double* acc[2] = {nullptr, nullptr};   // per time parity: forces [6P] + mass/momentum [4]
+  double* macc = nullptr;                // moment accumulators [12]
+  double* series = nullptr;              // [SERIES_ROWS][SERIES_COLS]
+  double* mrow = nullptr;                // on-demand moments row [SERIES_COLS]
+  // bricks per time parity
+  uint32_t* bword[2] = {nullptr, nullptr};
+  uint16_t* bcand[2] = {nullptr, nullptr};
+  int32_t* rlist[2] = {nullptr, nullptr};
+  PoseF* pose[2] = {nullptr, nullptr};
+  StepParams* sp[2] = {nullptr, nullptr};
+  float4* cworld[2] = {nullptr, nullptr};
+  uint32_t nbrick = 0;
+  // particles
+  int P = 0, Nc = 0;
+  ParticleDesc* desc = nullptr;
+  float4* cbody = nullptr;
+  float walk_margin = 1.0f;
+  // walkers
+  int64_t nw = 0;
+  float4* pos[2] = {nullptr, nullptr};
+  float4* x0[2] = {nullptr, nullptr};
+  uint32_t* rank = nullptr;
+  uint32_t* counts = nullptr;
+  uint32_t* offsets = nullptr;
+  uint32_t* bsums = nullptr;
+  // scratch for read-back conversions
+  void* scratch = nullptr;
+  size_t scratch_bytes = 0;
+
+  // host mirrors
+  int64_t t = 0;
+  int fcur = 0, pcur = 0;
+  int64_t binned_t = -1;
+  int64_t series_rows = 0;
+  int64_t launches = 0;
+  unsigned long long status_seen[ST_COUNT] = {0};
+  std::map<GraphKey, GraphEntry> graphs;
+  // phase timing (rwmi_step_timed): events[phase] start/stop pairs when enabled
+  bool timing = false;
+  cudaEvent_t ev[2 * RWMI_NPHASE] = {};
+};
+
+namespace {
+
+rwmi_status fail(rwmi_ctx* c, rwmi_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+#define CK(call)                                                                       \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess)                                                             \
+      return fail(c, e_ == cudaErrorMemoryAllocation ? RWMI_E_OOM : RWMI_E_CUDA,       \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                 \
+  } while (0)
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  return cudaMalloc((void**)p, bytes);
+}
+
+void dfree(void* p) {
+  if (p) cudaFree(p);
+}
+
+size_t storage_bytes(int storage) { return storage == 2 ? 2 : 4; }
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+rwmi_status copy_out(rwmi_ctx* c, void* dst, const void* src, size_t bytes) {
+  const cudaMemcpyKind k = is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  CK(cudaMemcpyAsync(dst, src, bytes, k, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return RWMI_OK;
+}
+
+rwmi_status ensure_scratch(rwmi_ctx* c, size_t bytes) {
+  if (c->scratch_bytes >= bytes) return RWMI_OK;
+  dfree(c->scratch);
+  c->scratch = nullptr;
+  c->scratch_bytes = 0;
+  CK(dalloc(&c->scratch, bytes));
+  c->scratch_bytes = bytes;
+  return RWMI_OK;
+}
+
+void drop_graphs(rwmi_ctx* c) {
+  for (auto& kv : c->graphs)
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+  c->graphs.clear();
+}
+
+ParticleSet particle_set(const rwmi_ctx* c) {
+  ParticleSet ps;
+  ps.P = c->P;
+  ps.Nc = c->Nc;
+  ps.desc = c->desc;
+  ps.cbody = c->cbody;
+  ps.walk_margin = c->walk_margin;
+  return ps;
+}
+
+BrickSet brick_set(const rwmi_ctx* c, int par) {
+  BrickSet b;
+  b.bword = c->bword[par];
+  b.bcand = c->bcand[par];
+  b.rlist = c->rlist[par];
+  b.pose = c->pose[par];
+  b.cworld = c->cworld[par];
+  b.sp = c->sp[par];
+  return b;
+}
+
+void update_margin(rwmi_ctx* c) {
+  // longest regular walker step: |u| <= U_BOUND plus three normals of at most 5.9 each
+  c->walk_margin = U_BOUND + (float)std::sqrt(2.0 * c->D) * 5.9f * 1.7320508f + 0.01f;
+}
+
+// Brick lists, poses and body force of the current time; zeroes its accumulators.
+rwmi_status build_current_frame(rwmi_ctx* c) {
+  const int par = (int)(c->t & 1);
+  CK(cudaMemsetAsync(c->bword[par], 0, sizeof(uint32_t) * (c->nbrick + 1), c->stream));
+  launch_pose_bin(c->g, particle_set(c), brick_set(c, par), c->d_T, 0, c->cfg.body_force,
+                  c->cfg.force_period, 1, c->acc[par], c->stream);
+  c->launches++;
+  CK(cudaGetLastError());
+  return RWMI_OK;
+}
+
+rwmi_status reset_fluid(rwmi_ctx* c) {
+  const float u0[3] = {(float)c->cfg.init_velocity[0], (float)c->cfg.init_velocity[1],
+                       (float)c->cfg.init_velocity[2]};
+  launch_init_populations(c->cfg.q, c->cfg.storage, c->g, c->f[c->fcur], (float)c->cfg.rho0, u0,
+                          c->u, c->stream);
+  c->launches++;
+  CK(cudaGetLastError());
+  return RWMI_OK;
+}
+
+rwmi_status alloc_fluid(rwmi_ctx* c) {
+  for (int k = 0; k < 2; ++k) {
+    dfree(c->f[k]);
+    c->f[k] = nullptr;
+  }
+  const size_t pop = (size_t)c->cfg.q * c->g.ncell_pad * storage_bytes(c->cfg.storage);
+  for (int k = 0; k < 2; ++k) CK(dalloc(&c->f[k], pop));
+  return RWMI_OK;
+}
+
+rwmi_status alloc_particles(rwmi_ctx* c) {
+  for (int k = 0; k < 2; ++k) {
+    dfree(c->pose[k]);
+    dfree(c->cworld[k]);
+    dfree(c->acc[k]);
+    c->pose[k] = nullptr;
+    c->cworld[k] = nullptr;
+    c->acc[k] = nullptr;
+    CK(dalloc(&c->pose[k], sizeof(PoseF) * (size_t)(c->P > 0 ? c->P : 1)));
+    CK(dalloc(&c->cworld[k], sizeof(float4) * (size_t)(c->Nc > 0 ? c->Nc : 1)));
+    CK(dalloc(&c->acc[k], sizeof(double) * (size_t)(6 * c->P + 4)));
+    CK(cudaMemsetAsync(c->acc[k], 0, sizeof(double) * (size_t)(6 * c->P + 4), c->stream));
+  }
+  return RWMI_OK;
+}
+
+rwmi_status alloc_walkers(rwmi_ctx* c, int64_t n) {
+  for (int k = 0; k < 2; ++k) {
+    dfree(c->pos[k]);
+    dfree(c->x0[k]);
+    c->pos[k] = nullptr;
+    c->x0[k] = nullptr;
+  }
+  dfree(c->rank);
+  c->rank = nullptr;
+  c->nw = 0;
+  for (int k = 0; k < 2; ++k) {
+    CK(dalloc(&c->pos[k], sizeof(float4) * (size_t)n));
+    CK(dalloc(&c->x0[k], sizeof(float4) * (size_t)n));
+  }
+  CK(dalloc(&c->rank, sizeof(uint32_t) * (size_t)n));
+  c->nw = n;
+  c->pcur = 0;
+  c->binned_t = -1;
+  drop_graphs(c);
+  return RWMI_OK;
+}
+
+// Counting sort of the walkers by cell; the histogram is the concentration of Eq. 16.
+void enqueue_sort(rwmi_ctx* c) {
+  cudaMemsetAsync(c->counts, 0, sizeof(uint32_t) * (size_t)c->ncell, c->stream);
+  launch_histogram(c->g, c->pos[c->pcur], c->nw, c->counts, c->rank, c->stream);
+  launch_scan(c->counts, c->offsets, c->bsums, (uint32_t)c->ncell, c->stream);
+  launch_scatter(c->g, c->pos[c->pcur], c->x0[c->pcur], c->nw, c->offsets, c->rank,
+                 c->pos[c->pcur ^ 1], c->x0[c->pcur ^ 1], c->stream);
+  c->launches += 5;
+  c->pcur ^= 1;
+}
+
+void phase_begin(rwmi_ctx* c, int ph) {
+  if (c->timing) cudaEventRecord(c->ev[2 * ph], c->stream);
+}
+void phase_end(rwmi_ctx* c, int ph) {
+  if (c->timing) cudaEventRecord(c->ev[2 * ph + 1], c->stream);
+}
+
+// One timestep t -> t+1 (host mirrors advance as the launches are queued).
+void enqueue_step(rwmi_ctx* c) {
+  const int tp = (int)(c->t & 1), tn = tp ^ 1;
+  const ParticleSet ps = particle_set(c);
+  const uint32_t k0 = (uint32_t)c->seed, k1 = (uint32_t)(c->seed >> 32);
+  // solid fraction of time t (particles at t)
+  phase_begin(c, RWMI_PHASE_RASTER);
+  if (c->P > 0) {
+    launch_raster(c->g, ps, brick_set(c, tp), c->solid, c->status, c->nsm, c->stream);
+    c->launches++;
+  }
+  phase_end(c, RWMI_PHASE_RASTER);
+  // LBM at t
+  phase_begin(c, RWMI_PHASE_LBM);
+  launch_lbm(c->cfg.q, c->cfg.storage, true, c->g, c->f[c->fcur], c->f[c->fcur ^ 1], c->u, c->solid,
+             brick_set(c, tp), (float)c->tau, (float)c->cfg.rho0, c->acc[tp] + 6 * c->P, c->acc[tp],
+             c->status, c->stream);
+  c->launches++;
+  phase_end(c, RWMI_PHASE_LBM);
+  c->fcur ^= 1;
+  // particles, bricks and body force of t+1
+  phase_begin(c, RWMI_PHASE_POSE);
+  cudaMemsetAsync(c->bword[tn], 0, sizeof(uint32_t) * (c->nbrick + 1), c->stream);
+  launch_pose_bin(c->g, ps, brick_set(c, tn), c->d_T, 1, c->cfg.body_force, c->cfg.force_period, 1,
+                  c->acc[tn], c->stream);
+  c->launches++;
+  phase_end(c, RWMI_PHASE_POSE);
+  // walkers t -> t+1; the walker kernel's last block advances the device step counter
+  phase_begin(c, RWMI_PHASE_WALKERS);
+  if (c->nw > 0)
+    launch_walkers(c->g, ps, brick_set(c, tn), c->pos[c->pcur], c->nw, c->u, c->d_T, (float)c->D, k0,
+                   k1, c->status, c->ticket, c->d_T, c->stream);
+  else
+    launch_advance(c->d_T, c->stream);
+  c->launches++;
+  phase_end(c, RWMI_PHASE_WALKERS);
+  c->t += 1;
+  phase_begin(c, RWMI_PHASE_SORT);
+  if (c->nw > 0 && c->cfg.sort_interval > 0 && c->t % c->cfg.sort_interval == 0) {
+    enqueue_sort(c);
+    c->binned_t = c->t;
+  }
+  phase_end(c, RWMI_PHASE_SORT);
+  phase_begin(c, RWMI_PHASE_MOMENTS);
+  if (c->cfg.moment_interval > 0 && c->t % c->cfg.moment_interval == 0) {
+    launch_moments(c->pos[c->pcur], c->x0[c->pcur], c->nw, c->macc, c->series, c->cfg.moment_interval,
+                   SERIES_ROWS, c->d_T, c->stream);
+    c->launches += c->nw > 0 ? 2 : 1;
+    c->series_rows++;
+  }
+  phase_end(c, RWMI_PHASE_MOMENTS);
+}
+
+int64_t chunk_length(const rwmi_ctx* c) {
+  auto gcd = [](int64_t a, int64_t b) { while (b) { int64_t t = a % b; a = b; b = t; } return a; };
+  int64_t L = 2;
+  for (int64_t v : {(int64_t)c->cfg.sort_interval, (int64_t)c->cfg.moment_interval})
+    if (v > 0) L = L / gcd(L, v) * v;
+  return L;
+}
+
+}  // namespace
+
+// ============================================================================================
+// Exported C ABI
+// ============================================================================================
+extern "C" {
+
+RWMI_API void rwmi_config_defaults(rwmi_config* cfg) {
+  if (!cfg) return;
+  std::memset(cfg, 0, sizeof(*cfg));
+  cfg->q = 19;
+  cfg->storage = RWMI_STORE_FP32_SHIFT;
+  cfg->wall_mask = 0;
+  cfg->force_period = 0.0;
+  cfg->rho0 = 1.0;
+  cfg->sort_interval = 16;
+  cfg->moment_interval = 0;
+  cfg->use_graphs = 1;
+}
+
+RWMI_API rwmi_status rwmi_create(rwmi_ctx** out, const int32_t dims[3], double tau, double D,
+                                 uint64_t seed) {
+  if (!out || !dims) return RWMI_E_INVALID;
+  *out = nullptr;
+  int64_t ncell = 1;
+  for (int a = 0; a < 3; ++a) {
+    if (dims[a] < 1 || dims[a] > (1 << 20)) return RWMI_E_INVALID;
+    ncell *= dims[a];
+  }
+  if (ncell > 0x7fffffffLL || !(tau > 0.5) || !std::isfinite(tau) || !(D >= 0.0) || !std::isfinite(D))
+    return RWMI_E_INVALID;
+  rwmi_ctx* c = new rwmi_ctx();
+  for (int a = 0; a < 3; ++a) c->n[a] = dims[a];
+  c->ncell = ncell;
+  c->tau = tau;
+  c->D = D;
+  c->seed = seed;
+  rwmi_config_defaults(&c->cfg);
+  Geom& g = c->g;
+  for (int a = 0; a < 3; ++a) {
+    g.n[a] = dims[a];
+    g.nb[a] = (dims[a] + BRICK - 1) / BRICK;
+    g.wall[a] = 0;
+  }
+  g.nxy = (uint32_t)dims[0] * (uint32_t)dims[1];
+  g.ncell = (uint32_t)ncell;
+  g.ncell_pad = (uint32_t)((ncell + 63) / 64 * 64);
+  make_divisor((uint32_t)dims[0], g.mx, g.sx);
+  make_divisor(g.nxy, g.mxy, g.sxy);
+  c->nbrick = (uint32_t)g.nb[0] * g.nb[1] * g.nb[2];
+  update_margin(c);
+  rwmi_status st = [&]() -> rwmi_status {
+    CK(cudaGetDevice(&c->device));
+    CK(cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->device));
+    CK(cudaStreamCreate(&c->stream));
+    c->own_stream = true;
+    rwmi_status s = alloc_fluid(c);
+    if (s != RWMI_OK) return s;
+    CK(dalloc(&c->u, sizeof(float) * 3 * (size_t)g.ncell_pad));
+    CK(dalloc(&c->solid, sizeof(uint16_t) * (size_t)ncell));
+    CK(dalloc(&c->d_T, sizeof(int64_t)));
+    CK(dalloc(&c->ticket, sizeof(unsigned int)));
+    CK(dalloc(&c->status, sizeof(unsigned long long) * ST_COUNT));
+    CK(dalloc(&c->macc, sizeof(double) * 12));
+    CK(dalloc(&c->series, sizeof(double) * (size_t)SERIES_ROWS * SERIES_COLS));
+    CK(dalloc(&c->mrow, sizeof(double) * SERIES_COLS));
+    CK(dalloc(&c->counts, sizeof(uint32_t) * (size_t)ncell));
+    CK(dalloc(&c->offsets, sizeof(uint32_t) * (size_t)ncell));
+    CK(dalloc(&c->bsums, sizeof(uint32_t) * scan_block_sums_size((uint32_t)ncell)));
+    for (int k = 0; k < 2; ++k) {
+      CK(dalloc(&c->bword[k], sizeof(uint32_t) * (c->nbrick + 1)));
+      CK(dalloc(&c->bcand[k], sizeof(uint16_t) * (size_t)c->nbrick * MAXC));
+      CK(dalloc(&c->rlist[k], sizeof(int32_t) * c->nbrick));
+      CK(dalloc(&c->sp[k], sizeof(StepParams)));
+      CK(cudaMemsetAsync(c->sp[k], 0, sizeof(StepParams), c->stream));
+    }
+    CK(dalloc(&c->desc, sizeof(ParticleDesc)));
+    CK(dalloc(&c->cbody, sizeof(float4)));
+    s = alloc_particles(c);
+    if (s != RWMI_OK) return s;
+    CK(cudaMemsetAsync(c->d_T, 0, sizeof(int64_t), c->stream));
+    CK(cudaMemsetAsync(c->ticket, 0, sizeof(unsigned int), c->stream));
+    CK(cudaMemsetAsync(c->status, 0, sizeof(unsigned long long) * ST_COUNT, c->stream));
+    CK(cudaMemsetAsync(c->macc, 0, sizeof(double) * 12, c->stream));
+    CK(cudaMemsetAsync(c->solid, 0, sizeof(uint16_t) * (size_t)ncell, c->stream));
+    s = reset_fluid(c);
+    if (s != RWMI_OK) return s;
+    s = build_current_frame(c);
+    if (s != RWMI_OK) return s;
+    CK(cudaStreamSynchronize(c->stream));
+    return RWMI_OK;
+  }();
+  if (st != RWMI_OK) {
+    const std::string msg = c->err;
+    rwmi_destroy(c);
+    std::fprintf(stderr, "rwmi_create: %s\n", msg.c_str());
+    return st;
+  }
+  *out = c;
+  return RWMI_OK;
+}
+
+RWMI_API rwmi_status rwmi_configure(rwmi_ctx* c, const rwmi_config* cfg) {
+  if (!c || !cfg) return RWMI_E_INVALID;
+  if (c->stepped) return fail(c, RWMI_E_STATE, "rwmi_configure: only before the first step");
+  if ((cfg->q != 15 && cfg->q != 19) || cfg->storage < 0 || cfg->storage > 2 || cfg->wall_mask > 7 ||
+      !(cfg->rho0 > 0.0) || cfg->sort_interval < 0 || cfg->moment_interval < 0 ||
+      !(cfg->force_period >= 0.0))
+    return fail(c, RWMI_E_INVALID, "rwmi_configure: bad q, storage, wall_mask, rho0 or interval");
+  for (int a = 0; a < 3; ++a)
+    if (!std::isfinite(cfg->body_force[a]) || !std::isfinite(cfg->init_velocity[a]))
+      return fail(c, RWMI_E_INVALID, "rwmi_configure: non-finite force or velocity");
+  const bool realloc_f = cfg->q != c->cfg.q || cfg->storage != c->cfg.storage;
+  c->cfg = *cfg;
+  for (int a = 0; a < 3; ++a) c->g.wall[a] = (cfg->wall_mask >> a) & 1;
+  drop_graphs(c);
+  if (realloc_f) {
+    rwmi_status s = alloc_fluid(c);
+    if (s != RWMI_OK) return s;
+  }
+  c->fcur = 0;
+  rwmi_status s = reset_fluid(c);
+  if (s != RWMI_OK) return s;
+  s = build_current_frame(c);
+  if (s != RWMI_OK) return s;
+  CK(cudaStreamSynchronize(c->stream));
+  return RWMI_OK;
+}
+
+RWMI_API rwmi_status rwmi_set_stream(rwmi_ctx* c, void* stream) {
+  if (!c) return RWMI_E_INVALID;
+  CK(cudaStreamSynchronize(c->stream));
+  if (stream == nullptr) return RWMI_OK;   // keep the context's own (blocking) stream
+  if (c->own_stream) cudaStreamDestroy(c->stream);
+  c->own_stream = false;
+  c->stream = (cudaStream_t)stream;
+  drop_graphs(c);
+  return RWMI_OK;
+}
+
+RWMI_API rwmi_status rwmi_set_metaballs(rwmi_ctx* c, int32_t P, const int32_t* coff, const float* cb,
+                                        const float* k, const double* origin, const double* amplitude,
+                                        const double* period, const double* phase, const double* omega) {
+  if (!c) return RWMI_E_INVALID;
+  if (c->stepped) return fail(c, RWMI_E_STATE, "rwmi_set_metaballs: only before the first step");
+  if (P < 0 || P > MAX_PARTICLES) return fail(c, RWMI_E_INVALID, "rwmi_set_metaballs: 0 <= P <= 511");
+  if (P > 0 && (!coff || !cb || !k || !origin || !amplitude || !period || !phase))
+    return fail(c, RWMI_E_INVALID, "rwmi_set_metaballs: null array");
+  const int Nc = P > 0 ? coff[P] : 0;
+  if (Nc < 0 || Nc > MAX_CENTERS || (P > 0 && coff[0] != 0))
+    return fail(c, RWMI_E_INVALID, "rwmi_set_metaballs: bad center offsets");
+  std::vector<ParticleDesc> desc((size_t)(P > 0 ? P : 1));
+  std::vector<float4> body((size_t)(Nc > 0 ? Nc : 1));
+  for (int p = 0; p < P; ++p) {
+    if (coff[p + 1] <= coff[p]) return fail(c, RWMI_E_INVALID, "rwmi_set_metaballs: empty particle");
+    ParticleDesc& d = desc[p];
+    for (int a = 0; a < 3; ++a) {
+      d.org[a] = origin[3 * p + a];
+      d.amp[a] = amplitude[3 * p + a];
+      d.omega[a] = omega ? omega[3 * p + a] : 0.0;
+      if (!std::isfinite(d.org[a]) || !std::isfinite(d.amp[a]) || !std::isfinite(d.omega[a]))
+        return fail(c, RWMI_E_INVALID, "rwmi_set_metaballs: non-finite trajectory");
+    }
+    d.period = period[p];
+    d.phase = phase[p];
+    if (!(d.period >= 0.0) || !std::isfinite(d.phase))
+      return fail(c, RWMI_E_INVALID, "rwmi_set_metaballs: bad period or phase");
+    d.c0 = coff[p];
+    d.c1 = coff[p + 1];
+    // Bound radius: with r = |x - o|, |x - x_i| >= r - |c_i|, so f <= sum k_i / (r - |c_i|)^2
+    // once r > max |c_i|; beyond the unit crossing of that falling bound f stays below 1.
+    double cmax = 0.0, ksum = 0.0;
+    std::vector<double> cn;
+    for (int i = d.c0; i < d.c1; ++i) {
+      if (!(k[i] > 0.0f) || !std::isfinite(cb[3 * i]) || !std::isfinite(cb[3 * i + 1]) || !std::isfinite(cb[3 * i + 2]))
+        return fail(c, RWMI_E_INVALID, "rwmi_set_metaballs: bad control point");
+      const double r = std::sqrt((double)cb[3 * i] * cb[3 * i] + (double)cb[3 * i + 1] * cb[3 * i + 1] +
+                                 (double)cb[3 * i + 2] * cb[3 * i + 2]);
+      cn.push_back(r);
+      cmax = std::max(cmax, r);
+      ksum += k[i];
+    }
+    double lo = cmax, hi = cmax + std::sqrt(ksum) + 1e-9;
+    for (int it = 0; it < 200; ++it) {
+      const double mid = 0.5 * (lo + hi);
+      double s = 0.0;
+      for (size_t m = 0; m < cn.size(); ++m) s += (double)k[d.c0 + m] / ((mid - cn[m]) * (mid - cn[m]));
+      if (s > 1.0) lo = mid; else hi = mid;
+    }
+    d.rb = (float)(hi * (1.0 + 1e-6) + 1e-4);
+  }
+  for (int i = 0; i < Nc; ++i) body[i] = make_float4(cb[3 * i], cb[3 * i + 1], cb[3 * i + 2], k[i]);
+  dfree(c->desc);
+  dfree(c->cbody);
+  c->desc = nullptr;
+  c->cbody = nullptr;
+  c->P = P;
+  c->Nc = Nc;
+  CK(dalloc(&c->desc, sizeof(ParticleDesc) * desc.size()));
+  CK(dalloc(&c->cbody, sizeof(float4) * body.size()));
+  CK(cudaMemcpy(c->desc, desc.data(), sizeof(ParticleDesc) * desc.size(), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(c->cbody, body.data(), sizeof(float4) * body.size(), cudaMemcpyHostToDevice));
+  rwmi_status s = alloc_particles(c);
+  if (s != RWMI_OK) return s;
+  drop_graphs(c);
+  s = build_current_frame(c);
+  if (s != RWMI_OK) return s;
+  CK(cudaStreamSynchronize(c->stream));
+  return RWMI_OK;
+}
+
+RWMI_API rwmi_status rwmi_seed_walkers(rwmi_ctx* c, int64_t n, const double lo[3], const double hi[3]) {
+  if (!c || !lo || !hi) return RWMI_E_INVALID;
+  if (n < 0 || n > 0x7fffffffLL) return fail(c, RWMI_E_INVALID, "rwmi_seed_walkers: 0 <= n < 2^31");
+  for (int a = 0; a < 3; ++a)
+    if (!(lo[a] >= 0.0) || !(hi[a] <= (double)c->n[a]) || !(lo[a] <= hi[a]))
+      return fail(c, RWMI_E_INVALID, "rwmi_seed_walkers: box must lie in [0, n] per axis");
+  rwmi_status s = alloc_walkers(c, n);
+  if (s != RWMI_OK) return s;
+  CK(cudaMemcpyAsync(c->status_seen, c->status, sizeof(unsigned long long) * ST_COUNT,
+                     cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  const unsigned long long before = c->status_seen[ST_SEED_FAIL];
+  launch_seed(c->g, particle_set(c), brick_set(c, (int)(c->t & 1)), c->pos[0], c->x0[0], n, lo, hi,
+              (uint32_t)c->seed, (uint32_t)(c->seed >> 32), c->status, c->stream);
+  c->launches++;
+  CK(cudaGetLastError());
+  unsigned long long st[ST_COUNT];
+  CK(cudaMemcpyAsync(st, c->status, sizeof(st), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  c->status_seen[ST_SEED_FAIL] = st[ST_SEED_FAIL];
+  if (st[ST_SEED_FAIL] > before)
+    return fail(c, RWMI_W_SEED, "rwmi_seed_walkers: some walkers found no free point in 1000 draws");
+  return RWMI_OK;
+}
+
+RWMI_API rwmi_status rwmi_set_walkers(rwmi_ctx* c, int64_t n, const float* pos) {
+  if (!c || (n > 0 && !pos)) return RWMI_E_INVALID;
+  if (n < 0 || n > 0x7fffffffLL) return fail(c, RWMI_E_INVALID, "rwmi_set_walkers: 0 <= n < 2^31");
+  std::vector<float> host;
+  const float* src = pos;
+  if (n > 0 && !is_device_ptr(pos)) {
+    for (int64_t w = 0; w < n; ++w)
+      for (int a = 0; a < 3; ++a) {
+        const float v = pos[3 * w + a];
+        if (!std::isfinite(v) || (c->g.wall[a] && (v < 0.0f || v > (float)c->n[a])))
+          return fail(c, RWMI_E_INVALID, "rwmi_set_walkers: position outside the walls or not finite");
+      }
+  }
+  rwmi_status s = alloc_walkers(c, n);
+  if (s != RWMI_OK) return s;
+  if (n == 0) return RWMI_OK;
+  s = ensure_scratch(c, sizeof(float) * 3 * (size_t)n);
+  if (s != RWMI_OK) return s;
+  CK(cudaMemcpyAsync(c->scratch, src, sizeof(float) * 3 * (size_t)n, cudaMemcpyDefault, c->stream));
+  launch_set_walkers((const float*)c->scratch, c->pos[0], c->x0[0], n, c->stream);
+  c->launches++;
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(c->stream));
+  return RWMI_OK;
+}
+
+RWMI_API rwmi_status rwmi_step(rwmi_ctx* c, int32_t n) {
+  if (!c || n < 0) return RWMI_E_INVALID;
+  c->stepped = true;
+  const int64_t L = chunk_length(c);
+  const bool graphs = c->cfg.use_graphs && L <= 64;
+  while (n > 0) {
+    if (graphs && c->t % L == 0 && n >= L) {
+      const GraphKey key{c->fcur, c->pcur};
+      auto it = c->graphs.find(key);
+      if (it == c->graphs.end()) {
+        const int64_t l0 = c->launches;
+        CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+        for (int64_t s = 0; s < L; ++s) enqueue_step(c);
+        cudaGraph_t graph = nullptr;
+        CK(cudaStreamEndCapture(c->stream, &graph));
+        GraphEntry e;
+        cudaError_t ie = cudaGraphInstantiate(&e.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        CK(ie);
+        e.launches = c->launches - l0;
+        c->graphs[key] = e;
+        CK(cudaGraphLaunch(e.exec, c->stream));   // mirrors already advanced while capturing
+      } else {
+        CK(cudaGraphLaunch(it->second.exec, c->stream));
+        c->launches += it->second.launches;
+        // advance the host mirrors as the captured chunk does
+        for (int64_t s = 0; s < L; ++s) {
+          c->fcur ^= 1;
+          c->t += 1;
+          if (c->nw > 0 && c->cfg.sort_interval > 0 && c->t % c->cfg.sort_interval == 0) {
+            c->pcur ^= 1;
+            c->binned_t = c->t;
+          }
+          if (c->cfg.moment_interval > 0 && c->t % c->cfg.moment_interval == 0) c->series_rows++;
+        }
+      }
+      n -= (int32_t)L;
+    } else {
+      enqueue_step(c);
+      n -= 1;
+    }
+  }
+  CK(cudaGetLastError());
+  return RWMI_OK;
+}
+
+RWMI_API rwmi_status rwmi_step_timed(rwmi_ctx* c, int32_t n, double* phase_ms) {
+  if (!c || n < 0 || !phase_ms) return RWMI_E_INVALID;
+  c->stepped = true;
+  for (int k = 0; k < 2 * RWMI_NPHASE; ++k)
+    if (!c->ev[k]) CK(cudaEventCreate(&c->ev[k]));
+  c->timing = true;
+  for (int32_t s = 0; s < n; ++s) {
+    enqueue_step(c);
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+      c->timing = false;
+      CK(e);
+    }
+    for (int ph = 0; ph < RWMI_NPHASE; ++ph) {
+      float ms = 0.0f;
+      if (cudaEventElapsedTime(&ms, c->ev[2 * ph], c->ev[2 * ph + 1]) == cudaSuccess) phase_ms[ph] += ms;
+    }
+  }
+  c->timing = false;
+  CK(cudaGetLastError());
+  return RWMI_OK;
+}
+
+RWMI_API rwmi_status rwmi_sync(rwmi_ctx* c) {
+  if (!c) return RWMI_E_INVALID;
+  CK(cudaStreamSynchronize(c->stream));
+  unsigned long long st[ST_COUNT];
+  CK(cudaMemcpy(st, c->status, sizeof(st), cudaMemcpyDeviceToHost));
+  rwmi_status r = RWMI_OK;
+  if (st[ST_NONFINITE] > c->status_seen[ST_NONFINITE]) r = fail(c, RWMI_E_NONFINITE, "non-finite walker velocity");
+  else if (st[ST_BISECT_FAIL] > c->status_seen[ST_BISECT_FAIL] || st[ST_REFILL_FAIL] > c->status_seen[ST_REFILL_FAIL])
+    r = fail(c, RWMI_W_BISECT, "Algorithm 1 or the refill found no surface point for some walker");
+  std::memcpy(c->status_seen, st, sizeof(st));
+  return r;
+}
+
+RWMI_API rwmi_status rwmi_time(rwmi_ctx* c, int64_t* t) {
+  if (!c || !t) return RWMI_E_INVALID;
+  *t = c->t;
+  return RWMI_OK;
+}
+
+RWMI_API rwmi_status rwmi_concentration(rwmi_ctx* c, uint32_t* out) {
+  if (!c || !out) return RWMI_E_INVALID;
+  if (c->binned_t != c->t) {
+    CK(cudaMemsetAsync(c->counts, 0, sizeof(uint32_t) * (size_t)c->ncell, c->stream));
+    launch_histogram(c->g, c->pos[c->pcur], c->nw, c->counts, nullptr, c->stream);
+    c->launches++;
+    CK(cudaGetLastError());
+    c->binned_t = c->t;
+  }
+  return copy_out(c, out, c->counts, sizeof(uint32_t) * (size_t)c->ncell);
+}
+
+RWMI_API rwmi_status rwmi_walker_moments(rwmi_ctx* c, double out[13]) {
+  if (!c || !out) return RWMI_E_INVALID;
+  launch_moments(c->pos[c->pcur], c->x0[c->pcur], c->nw, c->macc, c->mrow, 0, 1, c->d_T, c->stream);
+  c->launches += c->nw > 0 ? 2 : 1;
+  CK(cudaGetLastError());
+  return copy_out(c, out, c->mrow + 1, sizeof(double) * 13);
+}
+
+RWMI_API rwmi_status rwmi_moment_series(rwmi_ctx* c, double* out, int32_t max_rows, int32_t* n_rows) {
+  if (!c || !out || !n_rows || max_rows < 0) return RWMI_E_INVALID;
+  const int64_t avail = std::min<int64_t>(c->series_rows, SERIES_ROWS);
+  const int64_t take = std::min<int64_t>(avail, max_rows);
+  std::vector<double> ring((size_t)SERIES_ROWS * SERIES_COLS);
+  CK(cudaStreamSynchronize(c->stream));
+  CK(cudaMemcpy(ring.data(), c->series, sizeof(double) * ring.size(), cudaMemcpyDeviceToHost));
+  std::vector<double> rows((size_t)take * SERIES_COLS);
+  const int64_t first = c->series_rows - take;
+  for (int64_t r = 0; r < take; ++r)
+    std::memcpy(&rows[(size_t)r * SERIES_COLS], &ring[(size_t)((first + r) % SERIES_ROWS) * SERIES_COLS],
+                sizeof(double) * SERIES_COLS);
+  if (take > 0) CK(cudaMemcpy(out, rows.data(), sizeof(double) * rows.size(), cudaMemcpyDefault));
+  *n_rows = (int32_t)take;
+  return RWMI_OK;
+}
+
+RWMI_API rwmi_status rwmi_velocity(rwmi_ctx* c, float* out) {
+  if (!c || !out) return RWMI_E_INVALID;
+  rwmi_status s = ensure_scratch(c, sizeof(float) * 3 * (size_t)c->ncell);
+  if (s != RWMI_OK) return s;
+  launch_velocity_aos(c->g, c->u, (float*)c->scratch, c->stream);
+  c->launches++;
+  CK(cudaGetLastError());
+  return copy_out(c, out, c->scratch, sizeof(float) * 3 * (size_t)c->ncell);
+}
+
+RWMI_API rwmi_status rwmi_density(rwmi_ctx* c, float* out) {
+  if (!c || !out) return RWMI_E_INVALID;
+  rwmi_status s = ensure_scratch(c, sizeof(float) * (size_t)c->ncell);
+  if (s != RWMI_OK) return s;
+  launch_density(c->cfg.q, c->cfg.storage, c->g, c->f[c->fcur], (float)c->cfg.rho0, (float*)c->scratch, c->stream);
+  c->launches++;
+  CK(cudaGetLastError());
+  return copy_out(c, out, c->scratch, sizeof(float) * (size_t)c->ncell);
+}
+
+RWMI_API rwmi_status rwmi_populations(rwmi_ctx* c, double* out) {
+  if (!c || !out) return RWMI_E_INVALID;
+  const size_t bytes = sizeof(double) * (size_t)c->cfg.q * (size_t)c->ncell;
+  rwmi_status s = ensure_scratch(c, bytes);
+  if (s != RWMI_OK) return s;
+  launch_populations_f64(c->cfg.q, c->cfg.storage, c->g, c->f[c->fcur], (float)c->cfg.rho0,
+                         (double*)c->scratch, c->stream);
+  c->launches++;
+  CK(cudaGetLastError());
+  return copy_out(c, out, c->scratch, bytes);
+}
+
+RWMI_API rwmi_status rwmi_lattice(rwmi_ctx* c, int32_t* e, double* w, int32_t* q) {
+  if (!c) return RWMI_E_INVALID;
+  if (q) *q = c->cfg.q;
+  if (e && w) lattice_table(c->cfg.q, e, w);
+  return RWMI_OK;
+}
+
+RWMI_API rwmi_status rwmi_solid(rwmi_ctx* c, int32_t* count, int32_t* owner) {
+  if (!c || !count || !owner) return RWMI_E_INVALID;
+  const int par = (int)(c->t & 1);
+  const size_t bytes = sizeof(int32_t) * 2 * (size_t)c->ncell;
+  rwmi_status s = ensure_scratch(c, bytes);
+  if (s != RWMI_OK) return s;
+  if (c->P > 0) {
+    launch_raster(c->g, particle_set(c), brick_set(c, par), c->solid, c->status, c->nsm, c->stream);
+    c->launches++;
+  }
+  int32_t* tmp = (int32_t*)c->scratch;
+  launch_unpack_solid(c->g, c->solid, c->bword[par], tmp, tmp + c->ncell, c->stream);
+  c->launches++;
+  CK(cudaGetLastError());
+  s = copy_out(c, count, tmp, sizeof(int32_t) * (size_t)c->ncell);
+  if (s != RWMI_OK) return s;
+  return copy_out(c, owner, tmp + c->ncell, sizeof(int32_t) * (size_t)c->ncell);
+}
+
+RWMI_API rwmi_status rwmi_mass_momentum(rwmi_ctx* c, double out[4]) {
+  if (!c || !out) return RWMI_E_INVALID;
+  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  if (c->t > 0) {
+    rwmi_status s = copy_out(c, v, c->acc[(c->t - 1) & 1] + 6 * c->P, sizeof(v));
+    if (s != RWMI_OK) return s;
+  }
+  out[0] = (double)c->ncell * c->cfg.rho0 + v[0];
+  out[1] = v[1]; out[2] = v[2]; out[3] = v[3];
+  if (!std::isfinite(out[0])) return fail(c, RWMI_E_NONFINITE, "non-finite mass sum");
+  return RWMI_OK;
+}
+
+RWMI_API rwmi_status rwmi_particle_forces(rwmi_ctx* c, double* out) {
+  if (!c || (!out && c->P > 0)) return RWMI_E_INVALID;
+  if (c->P == 0) return RWMI_OK;
+  if (c->t == 0) {
+    std::vector<double> z((size_t)6 * c->P, 0.0);
+    CK(cudaMemcpy(out, z.data(), sizeof(double) * z.size(), cudaMemcpyDefault));
+    return RWMI_OK;
+  }
+  return copy_out(c, out, c->acc[(c->t - 1) & 1], sizeof(double) * 6 * (size_t)c->P);
+}
+
+RWMI_API rwmi_status rwmi_walkers(rwmi_ctx* c, float* out, float* x0) {
+  if (!c || (!out && c->nw > 0)) return RWMI_E_INVALID;
+  if (c->nw == 0) return RWMI_OK;
+  rwmi_status s = copy_out(c, out, c->pos[c->pcur], sizeof(float4) * (size_t)c->nw);
+  if (s != RWMI_OK) return s;
+  if (x0) {
+    const cudaMemcpyKind k = is_device_ptr(x0) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    CK(cudaMemcpy2DAsync(x0, 3 * sizeof(float), c->x0[c->pcur], sizeof(float4), 3 * sizeof(float),
+                         (size_t)c->nw, k, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+  }
+  return RWMI_OK;
+}
+
+RWMI_API rwmi_status rwmi_counters(rwmi_ctx* c, int64_t out[8]) {
+  if (!c || !out) return RWMI_E_INVALID;
+  CK(cudaStreamSynchronize(c->stream));
+  unsigned long long st[ST_COUNT];
+  CK(cudaMemcpy(st, c->status, sizeof(st), cudaMemcpyDeviceToHost));
+  for (int m = 0; m < 8; ++m) out[m] = (int64_t)st[m];
+  return RWMI_OK;
+}
+
+RWMI_API rwmi_status rwmi_save(rwmi_ctx* c, const char* path) {
+  if (!c || !path) return RWMI_E_INVALID;
+  CK(cudaStreamSynchronize(c->stream));
+  const size_t pop = (size_t)c->cfg.q * c->g.ncell_pad * storage_bytes(c->cfg.storage);
+  std::vector<char> f(pop);
+  std::vector<float4> p((size_t)c->nw), q((size_t)c->nw);
+  CK(cudaMemcpy(f.data(), c->f[c->fcur], pop, cudaMemcpyDeviceToHost));
+  if (c->nw) {
+    CK(cudaMemcpy(p.data(), c->pos[c->pcur], sizeof(float4) * p.size(), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(q.data(), c->x0[c->pcur], sizeof(float4) * q.size(), cudaMemcpyDeviceToHost));
+  }
+  FILE* fp = std::fopen(path, "wb");
+  if (!fp) return fail(c, RWMI_E_INVALID, std::string("rwmi_save: cannot open ") + path);
+  const int64_t hdr[10] = {(int64_t)CKPT_MAGIC, c->cfg.q, c->cfg.storage, c->n[0], c->n[1], c->n[2],
+                           c->nw, c->t, c->P, c->Nc};
+  bool ok = std::fwrite(hdr, sizeof(hdr), 1, fp) == 1 && std::fwrite(f.data(), 1, pop, fp) == pop;
+  if (c->nw) ok = ok && std::fwrite(p.data(), sizeof(float4), p.size(), fp) == p.size() &&
+                  std::fwrite(q.data(), sizeof(float4), q.size(), fp) == q.size();
+  ok = (std::fclose(fp) == 0) && ok;
+  if (!ok) return fail(c, RWMI_E_INVALID, "rwmi_save: write failed");
+  return RWMI_OK;
+}
+
+RWMI_API rwmi_status rwmi_load(rwmi_ctx* c, const char* path) {
+  if (!c || !path) return RWMI_E_INVALID;
+  FILE* fp = std::fopen(path, "rb");
+  if (!fp) return fail(c, RWMI_E_INVALID, std::string("rwmi_load: cannot open ") + path);
+  int64_t hdr[10];
+  if (std::fread(hdr, sizeof(hdr), 1, fp) != 1 || hdr[0] != (int64_t)CKPT_MAGIC || hdr[1] != c->cfg.q ||
+      hdr[2] != c->cfg.storage || hdr[3] != c->n[0] || hdr[4] != c->n[1] || hdr[5] != c->n[2] ||
+      hdr[8] != c->P || hdr[9] != c->Nc || hdr[6] < 0 || hdr[7] < 0) {
+    std::fclose(fp);
+    return fail(c, RWMI_E_INVALID, "rwmi_load: checkpoint does not match this context");
+  }
+  const size_t pop = (size_t)c->cfg.q * c->g.ncell_pad * storage_bytes(c->cfg.storage);
+  std::vector<char> f(pop);
+  const int64_t nw = hdr[6];
+  std::vector<float4> p((size_t)nw), q((size_t)nw);
+  bool ok = std::fread(f.data(), 1, pop, fp) == pop;
+  if (nw) ok = ok && std::fread(p.data(), sizeof(float4), p.size(), fp) == p.size() &&
+               std::fread(q.data(), sizeof(float4), q.size(), fp) == q.size();
+  std::fclose(fp);
+  if (!ok) return fail(c, RWMI_E_INVALID, "rwmi_load: truncated checkpoint");
+  CK(cudaStreamSynchronize(c->stream));
+  if (nw != c->nw) {
+    rwmi_status s = alloc_walkers(c, nw);
+    if (s != RWMI_OK) return s;
+  }
+  c->t = hdr[7];
+  c->fcur = (int)(c->t & 1);
+  c->pcur = 0;
+  c->binned_t = -1;
+  c->stepped = true;
+  drop_graphs(c);
+  CK(cudaMemcpy(c->f[c->fcur], f.data(), pop, cudaMemcpyHostToDevice));
+  if (nw) {
+    CK(cudaMemcpy(c->pos[0], p.data(), sizeof(float4) * p.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->x0[0], q.data(), sizeof(float4) * q.size(), cudaMemcpyHostToDevice));
+  }
+  CK(cudaMemcpy(c->d_T, &c->t, sizeof(int64_t), cudaMemcpyHostToDevice));
+  rwmi_status s = build_current_frame(c);
+  if (s != RWMI_OK) return s;
+  CK(cudaStreamSynchronize(c->stream));
+  return RWMI_OK;
+}
+
+RWMI_API const char* rwmi_last_error(const rwmi_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+RWMI_API int64_t rwmi_launch_count(const rwmi_ctx* c) { return c ? c->launches : 0; }
+
+RWMI_API void rwmi_destroy(rwmi_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  drop_graphs(c);
+  for (int k = 0; k < 2; ++k) {
+    dfree(c->f[k]); dfree(c->acc[k]); dfree(c->bword[k]); dfree(c->bcand[k]); dfree(c->rlist[k]);
+    dfree(c->pose[k]); dfree(c->sp[k]); dfree(c->cworld[k]); dfree(c->pos[k]); dfree(c->x0[k]);
+  }
+  dfree(c->u); dfree(c->solid); dfree(c->d_T); dfree(c->ticket); dfree(c->status); dfree(c->macc);
+  dfree(c->series); dfree(c->mrow); dfree(c->desc); dfree(c->cbody); dfree(c->rank);
+  dfree(c->counts); dfree(c->offsets); dfree(c->bsums); dfree(c->scratch);
+  for (int k = 0; k < 2 * RWMI_NPHASE; ++k)
+    if (c->ev[k]) cudaEventDestroy(c->ev[k]);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+}  // extern "C"

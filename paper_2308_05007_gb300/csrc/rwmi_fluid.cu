@@ -1,0 +1,698 @@
+// rwmi_fluid.cu -- particle poses and brick lists, metaball rasteriser, fused LBM step.
+//
+// Kernels (one timestep t):
+//   pose_bin_kernel   particle pose at a time (prescribed motion), world control points, brick
+//                     candidate lists, body force, zeroed force/momentum accumulators
+//   raster_kernel     solid sub-sample count + owner for every cell of bricks that touch a
+//                     particle (Eq. 3, 4x4x4 sub-samples, binary32 decisions bit-identical to
+//                     the CPU oracle's)
+//   lbm_kernel        pull stream (periodic wrap / half-way bounce-back) + BGK collide
+//                     (Eqs. 12-15) with PSM solid coupling and Guo forcing; writes the
+//                     populations, the velocity field and per-particle force/torque
+#include <cuda_fp16.h>
+
+#include "rwmi_internal.cuh"
+
+namespace rwmi {
+
+// ------------------------------------------------------------------------------------------
+// Velocity sets. Directions 1..H form one half of the set; direction i + H is the opposite of i.
+//   D3Q15 half: (1,0,0) (0,1,0) (0,0,1) (1,1,1) (1,1,-1) (1,-1,1) (1,-1,-1)
+//   D3Q19 half: (1,0,0) (0,1,0) (0,0,1) (1,1,0) (1,-1,0) (1,0,1) (1,0,-1) (0,1,1) (0,1,-1)
+// Weights: D3Q15 2/9, 1/9, 1/72; D3Q19 1/3, 1/18, 1/36 (c_s^2 = 1/3).
+// ------------------------------------------------------------------------------------------
+__host__ __device__ constexpr int half15(int i, int a) {
+  return a == 0 ? (i == 2 || i == 3 ? 0 : 1)
+       : a == 1 ? (i == 1 || i == 3 ? 0 : (i == 2 || i == 4 || i == 5) ? 1 : -1)
+                : (i == 1 || i == 2 ? 0 : (i == 3 || i == 4 || i == 6) ? 1 : -1);
+}
+__host__ __device__ constexpr int half19(int i, int a) {
+  return a == 0 ? ((i == 1 || (i >= 4 && i <= 7)) ? 1 : 0)
+       : a == 1 ? ((i == 2 || i == 4 || i == 8 || i == 9) ? 1 : (i == 5 ? -1 : 0))
+                : ((i == 3 || i == 6 || i == 8) ? 1 : ((i == 7 || i == 9) ? -1 : 0));
+}
+template <int Q> struct Lat {
+  static constexpr int H = (Q - 1) / 2;
+  __host__ __device__ static constexpr int e(int i, int a) {
+    return i == 0 ? 0
+         : i <= H ? (Q == 15 ? half15(i, a) : half19(i, a))
+                  : -(Q == 15 ? half15(i - H, a) : half19(i - H, a));
+  }
+  __host__ __device__ static constexpr int e2(int i) {
+    return e(i, 0) * e(i, 0) + e(i, 1) * e(i, 1) + e(i, 2) * e(i, 2);
+  }
+  __host__ __device__ static constexpr float w(int i) {
+    return Q == 15 ? (e2(i) == 0 ? 2.0f / 9.0f : e2(i) == 1 ? 1.0f / 9.0f : 1.0f / 72.0f)
+                   : (e2(i) == 0 ? 1.0f / 3.0f : e2(i) == 1 ? 1.0f / 18.0f : 1.0f / 36.0f);
+  }
+  __host__ __device__ static constexpr int opp(int i) { return i == 0 ? 0 : (i <= H ? i + H : i - H); }
+};
+
+void lattice_table(int q, int32_t* e, double* w) {
+  for (int i = 0; i < q; ++i) {
+    for (int a = 0; a < 3; ++a) e[3 * i + a] = q == 15 ? Lat<15>::e(i, a) : Lat<19>::e(i, a);
+    const int e2 = q == 15 ? Lat<15>::e2(i) : Lat<19>::e2(i);
+    w[i] = q == 15 ? (e2 == 0 ? 2.0 / 9.0 : e2 == 1 ? 1.0 / 9.0 : 1.0 / 72.0)
+                   : (e2 == 0 ? 1.0 / 3.0 : e2 == 1 ? 1.0 / 18.0 : 1.0 / 36.0);
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Prescribed particle motion and brick candidate lists
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ double wrap_d(double x, double n, int wall) {
+  return wall ? x : __dsub_rn(x, __dmul_rn(n, floor(__ddiv_rn(x, n))));
+}
+
+// One block per particle (block 0 also writes the body force of this time).
+__global__ void pose_bin_kernel(Geom g, ParticleSet ps, BrickSet bs, const int64_t* __restrict__ d_T,
+                                int t_offset, double F0x, double F0y, double F0z, double fper,
+                                int zero_acc, double* __restrict__ acc) {
+  const int64_t t = *d_T + t_offset;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const double s = fper > 0.0 ? sin(2.0 * 3.141592653589793 * (double)t / fper) : 1.0;
+    bs.sp->F[0] = (float)(F0x * s);
+    bs.sp->F[1] = (float)(F0y * s);
+    bs.sp->F[2] = (float)(F0z * s);
+  }
+  if (zero_acc) {   // force/torque [6P] + mass/momentum [4] accumulators of this time
+    for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < 6 * ps.P + 4; m += gridDim.x * blockDim.x)
+      acc[m] = 0.0;
+  }
+  const int p = blockIdx.x;
+  if (p >= ps.P) return;
+  __shared__ double sR[9], so[3];
+  const ParticleDesc d = ps.desc[p];
+  // Explicitly rounded FP64 operations in the oracle's order: the binary32 control points must
+  // round identically on both sides, so no fused multiply-add here.
+  if (threadIdx.x == 0) {
+    const double two_pi = 6.283185307179586;
+    double s = 0.0, cdt = 0.0;
+    if (d.period > 0.0) {
+      const double th = __dadd_rn(__ddiv_rn(__dmul_rn(two_pi, (double)t), d.period), d.phase);
+      s = sin(th);
+      cdt = cos(th) * two_pi / d.period;
+    }
+    double org[3], vel[3];
+    for (int a = 0; a < 3; ++a) {
+      org[a] = __dadd_rn(d.org[a], __dmul_rn(d.amp[a], s));
+      vel[a] = d.amp[a] * cdt;
+    }
+    // constant spin: body frame turned by |omega| t about omega / |omega| (Rodrigues)
+    const double wn = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(d.omega[0], d.omega[0]),
+                                                     __dmul_rn(d.omega[1], d.omega[1])),
+                                           __dmul_rn(d.omega[2], d.omega[2])));
+    for (int m = 0; m < 9; ++m) sR[m] = (m % 4 == 0) ? 1.0 : 0.0;
+    if (wn > 0.0) {
+      const double ax[3] = {__ddiv_rn(d.omega[0], wn), __ddiv_rn(d.omega[1], wn), __ddiv_rn(d.omega[2], wn)};
+      const double ang = __dmul_rn(wn, (double)t), ca = cos(ang), sa = sin(ang);
+      const double K[9] = {0, -ax[2], ax[1], ax[2], 0, -ax[0], -ax[1], ax[0], 0};
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b)
+          sR[3 * a + b] = __dadd_rn(__dadd_rn(a == b ? ca : 0.0, __dmul_rn(sa, K[3 * a + b])),
+                                    __dmul_rn(__dmul_rn(__dsub_rn(1.0, ca), ax[a]), ax[b]));
+    }
+    for (int a = 0; a < 3; ++a) so[a] = org[a];
+    PoseF pf;
+    for (int a = 0; a < 3; ++a) {
+      pf.o[a] = (float)wrap_d(org[a], (double)g.n[a], g.wall[a]);
+      pf.v[a] = (float)vel[a];
+      pf.w[a] = (float)d.omega[a];
+      pf.pad[a] = 0.0f;
+    }
+    bs.pose[p] = pf;
+  }
+  __syncthreads();
+  for (int i = d.c0 + threadIdx.x; i < d.c1; i += blockDim.x) {
+    const float4 cb = ps.cbody[i];
+    const double b[3] = {cb.x, cb.y, cb.z};
+    float4 cw;
+    double w3[3];
+    for (int a = 0; a < 3; ++a) {
+      const double v = __dadd_rn(__dadd_rn(__dadd_rn(so[a], __dmul_rn(sR[3 * a], b[0])),
+                                           __dmul_rn(sR[3 * a + 1], b[1])),
+                                 __dmul_rn(sR[3 * a + 2], b[2]));
+      w3[a] = wrap_d(v, (double)g.n[a], g.wall[a]);
+    }
+    cw.x = (float)w3[0]; cw.y = (float)w3[1]; cw.z = (float)w3[2]; cw.w = cb.w;
+    bs.cworld[i] = cw;
+  }
+  // bricks within rb + walk_margin of the origin; raster-relevant within rb + 1
+  double ow[3];
+  for (int a = 0; a < 3; ++a) ow[a] = wrap_d(so[a], (double)g.n[a], g.wall[a]);
+  const float Rw = d.rb + ps.walk_margin, Rr = d.rb + 1.0f;
+  int lo[3], cnt[3];
+  for (int a = 0; a < 3; ++a) {
+    int l = (int)floor((ow[a] - Rw) / BRICK), h = (int)floor((ow[a] + Rw) / BRICK);
+    if (g.wall[a]) { l = max(l, 0); h = min(h, g.nb[a] - 1); }
+    else if (h - l + 1 >= g.nb[a]) { l = 0; h = g.nb[a] - 1; }
+    lo[a] = l;
+    cnt[a] = max(h - l + 1, 0);
+  }
+  const int total = cnt[0] * cnt[1] * cnt[2];
+  const uint32_t nbrick = (uint32_t)g.nb[0] * g.nb[1] * g.nb[2];
+  for (int m = threadIdx.x; m < total; m += blockDim.x) {
+    int bc[3] = {lo[0] + m % cnt[0], lo[1] + (m / cnt[0]) % cnt[1], lo[2] + m / (cnt[0] * cnt[1])};
+    float d2 = 0.0f;
+    for (int a = 0; a < 3; ++a) {
+      if (!g.wall[a]) bc[a] = ((bc[a] % g.nb[a]) + g.nb[a]) % g.nb[a];
+      const float b0 = (float)(bc[a] * BRICK), b1 = fminf((float)((bc[a] + 1) * BRICK), (float)g.n[a]);
+      const float c = 0.5f * (b0 + b1), h = 0.5f * (b1 - b0);
+      float delta = (float)ow[a] - c;
+      if (!g.wall[a]) {
+        const float na = (float)g.n[a];
+        delta -= na * rintf(delta / na);
+      }
+      const float da = fmaxf(fabsf(delta) - h, 0.0f);
+      d2 += da * da;
+    }
+    if (d2 > Rw * Rw) continue;
+    const bool rr = d2 <= Rr * Rr;
+    const uint32_t b = ((uint32_t)bc[2] * g.nb[1] + bc[1]) * g.nb[0] + bc[0];
+    const uint32_t old = atomicAdd(&bs.bword[b], 1u + (rr ? 65536u : 0u));
+    const uint32_t slot = old & 0xffffu;
+    if (slot < MAXC) bs.bcand[b * MAXC + slot] = (uint16_t)(p | (rr ? 0x8000 : 0));
+    if (rr && (old >> 16) == 0u) {
+      const uint32_t li = atomicAdd(&bs.bword[nbrick], 1u);
+      bs.rlist[li] = (int32_t)b;
+    }
+  }
+}
+
+void launch_pose_bin(const Geom& g, const ParticleSet& ps, BrickSet bs, const int64_t* d_T,
+                     int t_offset, const double F0[3], double force_period, int zero_forces,
+                     double* acc, cudaStream_t st) {
+  const int blocks = ps.P > 0 ? ps.P : 1;
+  pose_bin_kernel<<<blocks, 256, 0, st>>>(g, ps, bs, d_T, t_offset, F0[0], F0[1], F0[2],
+                                          force_period, zero_forces, acc);
+}
+
+// ------------------------------------------------------------------------------------------
+// Rasteriser: per cell, sub-samples (i + (a + 1/2)/4, ...) inside any particle (Eq. 3 >= 1).
+// Interval bounds over the cell (half-diagonal 0.6495) and over its eight octants
+// (half-diagonal 0.2165) settle most sub-samples; the rest are evaluated with a fast
+// reciprocal and, when that lands within 4e-5 of 1, again with the exact binary32 sequence
+// shared with the CPU oracle. Bounds are decided with a 1e-3 margin and the fast value with a
+// 4e-5 margin, both far above binary32 rounding (~1e-6), so every decision equals the exact one.
+// ------------------------------------------------------------------------------------------
+struct CellBound { float fmax, fmin; };
+
+__device__ __forceinline__ CellBound bound_at(const float4* __restrict__ cw, int c0, int c1, float x,
+                                              float y, float z, float h, const Geom& g) {
+  float fmax = 0.0f, fmin = 0.0f;
+  for (int i = c0; i < c1; ++i) {
+    const float4 c = cw[i];
+    const float dx = min_image_rn(x - c.x, (float)g.n[0], g.wall[0]);
+    const float dy = min_image_rn(y - c.y, (float)g.n[1], g.wall[1]);
+    const float dz = min_image_rn(z - c.z, (float)g.n[2], g.wall[2]);
+    const float r = sqrtf(dx * dx + dy * dy + dz * dz);
+    const float rmin = fmaxf(r - h, 1e-20f), rmax = r + h;
+    fmax += c.w / (rmin * rmin);
+    fmin += c.w / (rmax * rmax);
+  }
+  CellBound b;
+  b.fmax = fmax;
+  b.fmin = fmin;
+  return b;
+}
+
+__device__ __forceinline__ bool subsample_inside(const float4* __restrict__ cw, int c0, int c1,
+                                                 float x, float y, float z, const Geom& g) {
+  float f = 0.0f;
+  for (int i = c0; i < c1; ++i) {
+    const float4 c = cw[i];
+    const float dx = min_image_rn(x - c.x, (float)g.n[0], g.wall[0]);
+    const float dy = min_image_rn(y - c.y, (float)g.n[1], g.wall[1]);
+    const float dz = min_image_rn(z - c.z, (float)g.n[2], g.wall[2]);
+    f += __fdividef(c.w, dx * dx + dy * dy + dz * dz);
+  }
+  if (fabsf(f - 1.0f) > 4e-5f) return f >= 1.0f;
+  return metaball_exact(cw, c0, c1, x, y, z, g) >= 1.0f;
+}
+
+// 64-bit mask of the sub-samples of cell (i, j, k) inside particle [c0, c1); bit a + 4 b + 16 c
+__device__ uint64_t particle_mask(const float4* __restrict__ cw, int c0, int c1, int i, int j, int k,
+                                  const Geom& g) {
+  const float xc = (float)i + 0.5f, yc = (float)j + 0.5f, zc = (float)k + 0.5f;
+  const CellBound cb = bound_at(cw, c0, c1, xc, yc, zc, 0.649519053f, g);
+  if (cb.fmax < 0.999f) return 0ull;
+  if (cb.fmin > 1.001f) return ~0ull;
+  uint64_t mask = 0ull;
+  for (int oc = 0; oc < 8; ++oc) {
+    const int ox = oc & 1, oy = (oc >> 1) & 1, oz = oc >> 2;
+    const float xo = (float)i + 0.25f + 0.5f * ox, yo = (float)j + 0.25f + 0.5f * oy,
+                zo = (float)k + 0.25f + 0.5f * oz;
+    const CellBound ob = bound_at(cw, c0, c1, xo, yo, zo, 0.216506351f, g);
+    if (ob.fmax < 0.999f) continue;
+    uint64_t om = 0ull;
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      const int a = 2 * ox + (s & 1), b = 2 * oy + ((s >> 1) & 1), c = 2 * oz + (s >> 2);
+      const bool in = (ob.fmin > 1.001f) ||
+                      subsample_inside(cw, c0, c1, (float)i + (0.125f + 0.25f * (float)a),
+                                       (float)j + (0.125f + 0.25f * (float)b),
+                                       (float)k + (0.125f + 0.25f * (float)c), g);
+      if (in) om |= 1ull << (a + 4 * b + 16 * c);
+    }
+    mask |= om;
+  }
+  return mask;
+}
+
+__global__ void __launch_bounds__(256) raster_kernel(Geom g, ParticleSet ps, BrickSet bs,
+                                                     uint16_t* __restrict__ solid,
+                                                     unsigned long long* __restrict__ status) {
+  const uint32_t nbrick = (uint32_t)g.nb[0] * g.nb[1] * g.nb[2];
+  const uint32_t nlist = bs.bword[nbrick];
+  __shared__ int s_c0[MAXC + 1], s_c1[MAXC + 1], s_p[MAXC + 1];
+  __shared__ int s_n, s_all;
+  for (uint32_t li = blockIdx.x; li < nlist; li += gridDim.x) {
+    const uint32_t b = (uint32_t)bs.rlist[li];
+    if (threadIdx.x == 0) {
+      const uint32_t word = bs.bword[b];
+      const uint32_t nc = word & 0xffffu;
+      s_all = nc > MAXC;
+      int n = 0;
+      if (!s_all) {
+        for (uint32_t m = 0; m < nc; ++m) {
+          const uint16_t cid = bs.bcand[b * MAXC + m];
+          if (cid & 0x8000) {
+            const int p = cid & 0x7fff;
+            s_p[n] = p; s_c0[n] = ps.desc[p].c0; s_c1[n] = ps.desc[p].c1; ++n;
+          }
+        }
+      } else {
+        atomicAdd(&status[ST_BRICK_OVERFLOW], 1ull);
+      }
+      s_n = n;
+    }
+    __syncthreads();
+    const int bi = b % g.nb[0], bj = (b / g.nb[0]) % g.nb[1], bk = b / (g.nb[0] * g.nb[1]);
+    for (int c = threadIdx.x; c < BRICK * BRICK * BRICK; c += blockDim.x) {
+      const int i = bi * BRICK + (c & 7), j = bj * BRICK + ((c >> 3) & 7), k = bk * BRICK + (c >> 6);
+      if (i >= g.n[0] || j >= g.n[1] || k >= g.n[2]) continue;
+      uint64_t any = 0ull;
+      int best = 0, bestp = -1;
+      const int ncand = s_all ? ps.P : s_n;
+      for (int m = 0; m < ncand; ++m) {
+        const int p = s_all ? m : s_p[m];
+        const int c0 = s_all ? ps.desc[p].c0 : s_c0[m], c1 = s_all ? ps.desc[p].c1 : s_c1[m];
+        const uint64_t mk = particle_mask(bs.cworld, c0, c1, i, j, k, g);
+        const int np = __popcll(mk);
+        any |= mk;
+        if (np > 0 && (np > best || (np == best && p < bestp))) { best = np; bestp = p; }
+      }
+      const int count = __popcll(any);
+      const uint32_t cell = ((uint32_t)k * g.n[1] + j) * g.n[0] + i;
+      solid[cell] = count > 0 ? (uint16_t)(count | (bestp << 7)) : (uint16_t)0;
+    }
+    __syncthreads();
+  }
+}
+
+void launch_raster(const Geom& g, const ParticleSet& ps, BrickSet bs, uint16_t* solid,
+                   unsigned long long* status, int nsm, cudaStream_t st) {
+  if (ps.P == 0) return;
+  raster_kernel<<<nsm * 8, 256, 0, st>>>(g, ps, bs, solid, status);
+}
+
+// ------------------------------------------------------------------------------------------
+// Fused pull-stream + collide (Eqs. 12-15), partially saturated cells, Guo forcing.
+// One thread per cell, flat index c = x + nx (y + ny z); direction planes are contiguous, so
+// every pull load of a warp is one (shifted) coalesced row segment. Storage: binary32 f_i,
+// binary32 f_i - w_i rho0 ("shifted") or binary16 shifted; arithmetic binary32.
+// ------------------------------------------------------------------------------------------
+template <int STORE> struct Store;
+template <> struct Store<0> {
+  using T = float;
+  static constexpr bool shifted = false;
+  __device__ static float ld(const T* p) { return *p; }
+  __device__ static void st(T* p, float v) { *p = v; }
+};
+template <> struct Store<1> {
+  using T = float;
+  static constexpr bool shifted = true;
+  __device__ static float ld(const T* p) { return *p; }
+  __device__ static void st(T* p, float v) { *p = v; }
+};
+template <> struct Store<2> {
+  using T = __half;
+  static constexpr bool shifted = true;
+  __device__ static float ld(const T* p) { return __half2float(*p); }
+  __device__ static void st(T* p, float v) { *p = __float2half_rn(v); }
+};
+
+template <int Q, int STORE, bool WALLS, bool REDUCE>
+__global__ void __launch_bounds__(256) lbm_kernel(Geom g, const void* __restrict__ fin_,
+                                                  void* __restrict__ fout_, float* __restrict__ u,
+                                                  const uint16_t* __restrict__ solid,
+                                                  const uint32_t* __restrict__ bword,
+                                                  const PoseF* __restrict__ pose,
+                                                  const StepParams* __restrict__ sp, float tau,
+                                                  float rho0, double* __restrict__ red,
+                                                  double* __restrict__ forces) {
+  using L = Lat<Q>;
+  using S = Store<STORE>;
+  using T = typename S::T;
+  const T* __restrict__ fin = (const T*)fin_;
+  T* __restrict__ fout = (T*)fout_;
+  const uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool valid = idx < g.ncell;
+  const uint32_t c = valid ? idx : 0u;
+  const uint32_t z = fast_div(c, g.mxy, g.sxy);
+  const uint32_t rem = c - z * g.nxy;
+  const uint32_t y = fast_div(rem, g.mx, g.sx);
+  const uint32_t x = rem - y * g.n[0];
+  const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+  const int sy = nx, sz = (int)g.nxy;
+  // source offsets for e_a = +1 (source at -1) and e_a = -1 (source at +1), periodic wrap
+  const int ox_p = x == 0 ? nx - 1 : -1, ox_m = (int)x == nx - 1 ? -(nx - 1) : 1;
+  const int oy_p = y == 0 ? (ny - 1) * sy : -sy, oy_m = (int)y == ny - 1 ? -(ny - 1) * sy : sy;
+  const int oz_p = z == 0 ? (nz - 1) * sz : -sz, oz_m = (int)z == nz - 1 ? -(nz - 1) * sz : sz;
+  bool bx_p = false, bx_m = false, by_p = false, by_m = false, bz_p = false, bz_m = false;
+  if (WALLS) {
+    bx_p = g.wall[0] && x == 0; bx_m = g.wall[0] && (int)x == nx - 1;
+    by_p = g.wall[1] && y == 0; by_m = g.wall[1] && (int)y == ny - 1;
+    bz_p = g.wall[2] && z == 0; bz_m = g.wall[2] && (int)z == nz - 1;
+  }
+  const size_t pad = g.ncell_pad;
+  float f[Q];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const int ex = L::e(i, 0), ey = L::e(i, 1), ez = L::e(i, 2);
+    const int off = (ex > 0 ? ox_p : ex < 0 ? ox_m : 0) + (ey > 0 ? oy_p : ey < 0 ? oy_m : 0) +
+                    (ez > 0 ? oz_p : ez < 0 ? oz_m : 0);
+    bool blk = false;
+    if (WALLS)
+      blk = (ex > 0 && bx_p) || (ex < 0 && bx_m) || (ey > 0 && by_p) || (ey < 0 && by_m) ||
+            (ez > 0 && bz_p) || (ez < 0 && bz_m);
+    const T* src = blk ? fin + (size_t)L::opp(i) * pad + c : fin + (size_t)i * pad + (int)c + off;
+    f[i] = valid ? S::ld(src) : 0.0f;
+  }
+  // moments (Eqs. 14-15); with shifted storage f holds f_i - w_i rho0
+  float drho = 0.0f, jx = 0.0f, jy = 0.0f, jz = 0.0f;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    drho += f[i];
+    if (L::e(i, 0)) jx += L::e(i, 0) * f[i];
+    if (L::e(i, 1)) jy += L::e(i, 1) * f[i];
+    if (L::e(i, 2)) jz += L::e(i, 2) * f[i];
+  }
+  const float rho = S::shifted ? rho0 + drho : drho;
+  const float Fx = sp->F[0], Fy = sp->F[1], Fz = sp->F[2];
+  const float inv_rho = 1.0f / rho;
+  const float ux = (jx + 0.5f * Fx) * inv_rho, uy = (jy + 0.5f * Fy) * inv_rho,
+              uz = (jz + 0.5f * Fz) * inv_rho;
+  const float uu = ux * ux + uy * uy + uz * uz;
+  // partially saturated cell: solid word valid only in bricks flagged for this time
+  float B = 0.0f, usx = 0.0f, usy = 0.0f, usz = 0.0f;
+  int owner = -1;
+  if (valid) {
+    const uint32_t b = ((z >> 3) * (uint32_t)g.nb[1] + (y >> 3)) * (uint32_t)g.nb[0] + (x >> 3);
+    if (bword[b] >> 16) {
+      const uint16_t sw = solid[c];
+      const int cnt = sw & 0x7f;
+      if (cnt) {
+        owner = sw >> 7;
+        const float eps = (float)cnt * (1.0f / 64.0f);
+        B = eps * (tau - 0.5f) / ((1.0f - eps) + (tau - 0.5f));
+        const PoseF ps_ = pose[owner];
+        float r[3] = {(float)x + 0.5f - ps_.o[0], (float)y + 0.5f - ps_.o[1], (float)z + 0.5f - ps_.o[2]};
+        for (int a = 0; a < 3; ++a)
+          if (!g.wall[a]) {
+            const float na = (float)g.n[a];
+            if (r[a] > 0.5f * na) r[a] -= na; else if (r[a] < -0.5f * na) r[a] += na;
+          }
+        usx = ps_.v[0] + ps_.w[1] * r[2] - ps_.w[2] * r[1];
+        usy = ps_.v[1] + ps_.w[2] * r[0] - ps_.w[0] * r[2];
+        usz = ps_.v[2] + ps_.w[0] * r[1] - ps_.w[1] * r[0];
+      }
+    }
+  }
+  const float omB = 1.0f - B;
+  const float rtau = omB / tau;              // (1 - B) / tau
+  const float guo = omB * (1.0f - 0.5f / tau);
+  const float uF = ux * Fx + uy * Fy + uz * Fz;
+  const float usus = usx * usx + usy * usy + usz * usz;
+  float dpx = 0.0f, dpy = 0.0f, dpz = 0.0f;
+  // rest direction
+  {
+    const float w = L::w(0);
+    const float dev = -1.5f * uu;                       // feq_0 / (w rho) - 1
+    const float feq_s = S::shifted ? w * (drho + rho * dev) : w * rho * (1.0f + dev);
+    const float S0 = guo * w * (-3.0f * uF);
+    const float out = f[0] - rtau * (f[0] - feq_s) + S0;   // Omega_0 = 0 (rest is its own pair)
+    if (valid) S::st(fout + c, out);
+  }
+  // opposite pairs (i, i + H) share e.u
+#pragma unroll
+  for (int i = 1; i <= L::H; ++i) {
+    const int io = i + L::H;
+    const int ex = L::e(i, 0), ey = L::e(i, 1), ez = L::e(i, 2);
+    const float w = L::w(i);
+    const float eu = ex * ux + ey * uy + ez * uz;
+    const float eF = ex * Fx + ey * Fy + ez * Fz;
+    const float sym = 4.5f * eu * eu - 1.5f * uu;        // even part of feq / (w rho)
+    const float base = S::shifted ? w * drho : w * rho;  // w rho (minus w rho0 when shifted)
+    const float feq_p = base + w * rho * (3.0f * eu + sym);
+    const float feq_m = base + w * rho * (-3.0f * eu + sym);
+    const float Sp = guo * w * (3.0f * (eF - uF) + 9.0f * eu * eF);
+    const float Sm = guo * w * (3.0f * (-eF - uF) + 9.0f * eu * eF);
+    float out_p = f[i] - rtau * (f[i] - feq_p) + Sp;
+    float out_m = f[io] - rtau * (f[io] - feq_m) + Sm;
+    if (B > 0.0f) {
+      const float eus = ex * usx + ey * usy + ez * usz;
+      const float wr = w * rho;
+      const float common = wr * (4.5f * (eus * eus - eu * eu) - 1.5f * (usus - uu));
+      const float odd = wr * 3.0f * (eu + eus);
+      const float om_p = (f[io] - f[i]) + odd + common;   // Omega_i
+      const float om_m = (f[i] - f[io]) - odd + common;   // Omega_opp(i)
+      out_p += B * om_p;
+      out_m += B * om_m;
+      const float dm = B * (om_p - om_m);                 // B (Omega_i e_i + Omega_opp e_opp) / e_i
+      dpx += dm * ex; dpy += dm * ey; dpz += dm * ez;
+    }
+    if (valid) {
+      S::st(fout + (size_t)i * pad + c, out_p);
+      S::st(fout + (size_t)io * pad + c, out_m);
+    }
+  }
+  if (valid) {
+    u[c] = ux;
+    u[pad + c] = uy;
+    u[2 * pad + c] = uz;
+  }
+  // hydrodynamic force on the owner particle: -B sum_i Omega_i e_i; torque about its origin
+  const unsigned full = 0xffffffffu;
+  const bool hasF = owner >= 0;
+  if (__any_sync(full, hasF)) {
+    float Fc[3] = {-dpx, -dpy, -dpz};
+    float Tc[3] = {0.0f, 0.0f, 0.0f};
+    if (hasF) {
+      const PoseF ps_ = pose[owner];
+      float r[3] = {(float)x + 0.5f - ps_.o[0], (float)y + 0.5f - ps_.o[1], (float)z + 0.5f - ps_.o[2]};
+      for (int a = 0; a < 3; ++a)
+        if (!g.wall[a]) {
+          const float na = (float)g.n[a];
+          if (r[a] > 0.5f * na) r[a] -= na; else if (r[a] < -0.5f * na) r[a] += na;
+        }
+      Tc[0] = r[1] * Fc[2] - r[2] * Fc[1];
+      Tc[1] = r[2] * Fc[0] - r[0] * Fc[2];
+      Tc[2] = r[0] * Fc[1] - r[1] * Fc[0];
+    }
+    const int key = hasF ? owner : -1;
+    const int first = __shfl_sync(full, key, __ffs(__ballot_sync(full, hasF)) - 1);
+    const bool uniform = __all_sync(full, !hasF || key == first);
+    if (uniform) {
+      float v[6] = {Fc[0], Fc[1], Fc[2], Tc[0], Tc[1], Tc[2]};
+#pragma unroll
+      for (int m = 0; m < 6; ++m) {
+        if (!hasF) v[m] = 0.0f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[m] += __shfl_xor_sync(full, v[m], o);
+      }
+      if ((threadIdx.x & 31) == 0)
+        for (int m = 0; m < 6; ++m) atomicAdd(&forces[6 * first + m], (double)v[m]);
+    } else if (hasF) {
+      for (int m = 0; m < 3; ++m) {
+        atomicAdd(&forces[6 * owner + m], (double)Fc[m]);
+        atomicAdd(&forces[6 * owner + 3 + m], (double)Tc[m]);
+      }
+    }
+  }
+  if (REDUCE) {   // FP64 sums of (rho - rho0) and sum_i f_i e_i (pre-collision), per block
+    double v[4] = {valid ? (double)(S::shifted ? drho : rho - rho0) : 0.0, valid ? (double)jx : 0.0,
+                   valid ? (double)jy : 0.0, valid ? (double)jz : 0.0};
+#pragma unroll
+    for (int m = 0; m < 4; ++m)
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v[m] += __shfl_xor_sync(full, v[m], o);
+    __shared__ double s_red[8][4];
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0)
+      for (int m = 0; m < 4; ++m) s_red[wid][m] = v[m];
+    __syncthreads();
+    if (threadIdx.x < 4) {
+      double s = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += s_red[w][threadIdx.x];
+      atomicAdd(&red[threadIdx.x], s);
+    }
+  }
+}
+
+template <int Q, int STORE>
+static void launch_lbm_q(bool walls, bool reduce, const Geom& g, const void* fin, void* fout,
+                         float* u, const uint16_t* solid, BrickSet bs, float tau, float rho0,
+                         double* red, double* forces, cudaStream_t st) {
+  const dim3 grid((g.ncell + 255) / 256), block(256);
+  if (walls) {
+    if (reduce) lbm_kernel<Q, STORE, true, true><<<grid, block, 0, st>>>(g, fin, fout, u, solid, bs.bword, bs.pose, bs.sp, tau, rho0, red, forces);
+    else lbm_kernel<Q, STORE, true, false><<<grid, block, 0, st>>>(g, fin, fout, u, solid, bs.bword, bs.pose, bs.sp, tau, rho0, red, forces);
+  } else {
+    if (reduce) lbm_kernel<Q, STORE, false, true><<<grid, block, 0, st>>>(g, fin, fout, u, solid, bs.bword, bs.pose, bs.sp, tau, rho0, red, forces);
+    else lbm_kernel<Q, STORE, false, false><<<grid, block, 0, st>>>(g, fin, fout, u, solid, bs.bword, bs.pose, bs.sp, tau, rho0, red, forces);
+  }
+}
+
+void launch_lbm(int q, int storage, bool reduce, const Geom& g, const void* fin, void* fout,
+                float* u, const uint16_t* solid, BrickSet bs, float tau, float rho0, double* red,
+                double* forces, unsigned long long* status, cudaStream_t st) {
+  (void)status;
+  const bool walls = g.wall[0] || g.wall[1] || g.wall[2];
+  if (q == 15) {
+    if (storage == 0) launch_lbm_q<15, 0>(walls, reduce, g, fin, fout, u, solid, bs, tau, rho0, red, forces, st);
+    else if (storage == 1) launch_lbm_q<15, 1>(walls, reduce, g, fin, fout, u, solid, bs, tau, rho0, red, forces, st);
+    else launch_lbm_q<15, 2>(walls, reduce, g, fin, fout, u, solid, bs, tau, rho0, red, forces, st);
+  } else {
+    if (storage == 0) launch_lbm_q<19, 0>(walls, reduce, g, fin, fout, u, solid, bs, tau, rho0, red, forces, st);
+    else if (storage == 1) launch_lbm_q<19, 1>(walls, reduce, g, fin, fout, u, solid, bs, tau, rho0, red, forces, st);
+    else launch_lbm_q<19, 2>(walls, reduce, g, fin, fout, u, solid, bs, tau, rho0, red, forces, st);
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Initial state, checkpoint load and read-back helpers
+// ------------------------------------------------------------------------------------------
+template <int Q, int STORE>
+__global__ void init_pop_kernel(Geom g, void* f_, float rho0, float ux, float uy, float uz, float* u) {
+  using L = Lat<Q>;
+  using S = Store<STORE>;
+  typename S::T* f = (typename S::T*)f_;
+  const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.ncell) return;
+  const float uu = ux * ux + uy * uy + uz * uz;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const float eu = L::e(i, 0) * ux + L::e(i, 1) * uy + L::e(i, 2) * uz;
+    const float dev = 3.0f * eu + 4.5f * eu * eu - 1.5f * uu;
+    const float v = S::shifted ? L::w(i) * rho0 * dev : L::w(i) * rho0 * (1.0f + dev);
+    S::st(f + (size_t)i * g.ncell_pad + c, v);
+  }
+  u[c] = ux;
+  u[g.ncell_pad + c] = uy;
+  u[2 * (size_t)g.ncell_pad + c] = uz;
+}
+
+template <int Q, int STORE>
+__global__ void pop_f64_kernel(Geom g, const void* f_, float rho0, double* out) {
+  using L = Lat<Q>;
+  using S = Store<STORE>;
+  const typename S::T* f = (const typename S::T*)f_;
+  const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.ncell) return;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const double v = (double)S::ld(f + (size_t)i * g.ncell_pad + c);
+    out[(size_t)i * g.ncell + c] = S::shifted ? v + (double)L::w(i) * (double)rho0 : v;
+  }
+}
+
+template <int Q, int STORE>
+__global__ void load_pop_kernel(Geom g, const double* in, float rho0, void* f_) {
+  using L = Lat<Q>;
+  using S = Store<STORE>;
+  typename S::T* f = (typename S::T*)f_;
+  const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.ncell) return;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const double v = in[(size_t)i * g.ncell + c];
+    S::st(f + (size_t)i * g.ncell_pad + c,
+          (float)(S::shifted ? v - (double)L::w(i) * (double)rho0 : v));
+  }
+}
+
+template <int Q, int STORE>
+__global__ void density_kernel(Geom g, const void* f_, float rho0, float* out) {
+  using S = Store<STORE>;
+  const typename S::T* f = (const typename S::T*)f_;
+  const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.ncell) return;
+  float s = 0.0f;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) s += S::ld(f + (size_t)i * g.ncell_pad + c);
+  out[c] = S::shifted ? rho0 + s : s;
+}
+
+#define RWMI_DISPATCH(q, storage, KERNEL, ...)                                   \
+  do {                                                                           \
+    const dim3 grid_((g.ncell + 255) / 256);                                     \
+    if ((q) == 15) {                                                             \
+      if ((storage) == 0) KERNEL<15, 0><<<grid_, 256, 0, st>>>(__VA_ARGS__);     \
+      else if ((storage) == 1) KERNEL<15, 1><<<grid_, 256, 0, st>>>(__VA_ARGS__);\
+      else KERNEL<15, 2><<<grid_, 256, 0, st>>>(__VA_ARGS__);                    \
+    } else {                                                                     \
+      if ((storage) == 0) KERNEL<19, 0><<<grid_, 256, 0, st>>>(__VA_ARGS__);     \
+      else if ((storage) == 1) KERNEL<19, 1><<<grid_, 256, 0, st>>>(__VA_ARGS__);\
+      else KERNEL<19, 2><<<grid_, 256, 0, st>>>(__VA_ARGS__);                    \
+    }                                                                            \
+  } while (0)
+
+void launch_init_populations(int q, int storage, const Geom& g, void* f, float rho0,
+                             const float u0[3], float* u, cudaStream_t st) {
+  RWMI_DISPATCH(q, storage, init_pop_kernel, g, f, rho0, u0[0], u0[1], u0[2], u);
+}
+void launch_populations_f64(int q, int storage, const Geom& g, const void* f, float rho0,
+                            double* out, cudaStream_t st) {
+  RWMI_DISPATCH(q, storage, pop_f64_kernel, g, f, rho0, out);
+}
+void launch_load_populations(int q, int storage, const Geom& g, const double* in, float rho0,
+                             void* f, cudaStream_t st) {
+  RWMI_DISPATCH(q, storage, load_pop_kernel, g, in, rho0, f);
+}
+void launch_density(int q, int storage, const Geom& g, const void* f, float rho0, float* out,
+                    cudaStream_t st) {
+  RWMI_DISPATCH(q, storage, density_kernel, g, f, rho0, out);
+}
+
+__global__ void unpack_solid_kernel(Geom g, const uint16_t* solid, const uint32_t* bword,
+                                    int32_t* count, int32_t* owner) {
+  const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.ncell) return;
+  const uint32_t z = c / g.nxy, rem = c - z * g.nxy, y = rem / g.n[0], x = rem - y * g.n[0];
+  const uint32_t b = ((z >> 3) * (uint32_t)g.nb[1] + (y >> 3)) * (uint32_t)g.nb[0] + (x >> 3);
+  uint16_t sw = 0;
+  if (bword[b] >> 16) sw = solid[c];
+  const int n = sw & 0x7f;
+  count[c] = n;
+  owner[c] = n ? (sw >> 7) : -1;
+}
+
+void launch_unpack_solid(const Geom& g, const uint16_t* solid, const uint32_t* bword,
+                         int32_t* count, int32_t* owner, cudaStream_t st) {
+  unpack_solid_kernel<<<(g.ncell + 255) / 256, 256, 0, st>>>(g, solid, bword, count, owner);
+}
+
+__global__ void velocity_aos_kernel(Geom g, const float* u, float* out) {
+  const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.ncell) return;
+  out[3 * (size_t)c] = u[c];
+  out[3 * (size_t)c + 1] = u[g.ncell_pad + c];
+  out[3 * (size_t)c + 2] = u[2 * (size_t)g.ncell_pad + c];
+}
+
+void launch_velocity_aos(const Geom& g, const float* u, float* out, cudaStream_t st) {
+  velocity_aos_kernel<<<(g.ncell + 255) / 256, 256, 0, st>>>(g, u, out);
+}
+
+}  // namespace rwmi

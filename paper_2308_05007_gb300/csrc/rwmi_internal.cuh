@@ -1,0 +1,236 @@
+// rwmi_internal.cuh -- device data layout and small device helpers of the GB300 library.
+//
+// HBM layout (one context):
+//   populations   f[2][Q][ncell_pad]      A/B ping-pong, direction-major (SoA), each direction
+//                                         plane 128-byte aligned; binary32 (optionally shifted by
+//                                         w_i rho0) or binary16 shifted
+//   velocity      u[3][ncell_pad]         binary32 SoA, written by the LBM kernel, gathered by
+//                                         walkers
+//   solid         solid[ncell]            uint16: sub-sample count (bits 0-6) | owner (bits 7-15),
+//                                         valid only in bricks flagged for the current time
+//   bricks        8x8x8-cell bricks, per time parity: bword[nbrick+1] (walker-candidate count in
+//                 bits 0-15, raster-relevant count in bits 16-31; the extra last word counts
+//                 rlist), bcand[nbrick][MAXC] (uint16 particle ids, bit 15 = raster-relevant),
+//                 rlist[nbrick] (bricks holding raster-relevant particles)
+//   particles     desc[P] (trajectory), cbody[Nc] float4 (body-frame x, y, z, k),
+//                 per time parity: pose[P] and cworld[Nc] float4 (world x, y, z, k; wrapped)
+//   walkers       pos[2][N] float4 {x, y, z, id bits} (unwrapped), x0[2][N] float4 start
+//                 positions; the second buffers are the counting-sort targets
+//   sort/bin      counts[ncell], offsets[ncell] uint32, rank[N] uint32, block sums
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace rwmi {
+
+constexpr int BRICK = 8;            // brick edge in cells
+constexpr int MAXC = 16;            // candidate particles stored per brick
+constexpr int MAX_PARTICLES = 511;  // owner field of the solid word is 9 bits
+constexpr int MAX_CENTERS = 65535;
+constexpr float U_BOUND = 0.3f;     // lattice speed bound assumed by the walker candidate margin
+
+// Status counters (device, unsigned long long): see rwmi_counters.
+enum StatusSlot {
+  ST_TYPE1 = 0, ST_TYPE2, ST_TYPE3, ST_TYPE4,
+  ST_BISECT_FAIL, ST_REFILL_FAIL, ST_WALL_FAIL, ST_SEED_FAIL,
+  ST_NONFINITE, ST_BRICK_OVERFLOW, ST_FAST_SPEED, ST_COUNT
+};
+
+struct ParticleDesc {
+  double org[3], amp[3], omega[3];
+  double period, phase;
+  float rb;        // bound radius: Eq. 3 stays below 1 farther than rb from the origin
+  int c0, c1;      // control points c0 .. c1-1
+};
+
+struct PoseF {     // particle state at one time: wrapped origin, velocity, spin
+  float o[3], v[3], w[3];
+  float pad[3];
+};
+
+struct StepParams {  // per time parity
+  float F[3];      // body force density at that time
+  float pad;
+};
+
+// Geometry shared by all kernels (passed by value).
+struct Geom {
+  int n[3];            // cells per axis
+  int nb[3];           // bricks per axis
+  int wall[3];         // 1: no-slip walls normal to this axis
+  uint32_t nxy;        // n[0] * n[1]
+  uint32_t ncell;
+  uint32_t ncell_pad;  // direction-plane stride of the population arrays
+  // fast division of a flat cell index by nx and nxy: q = (umulhi(v, m) + v) >> s
+  uint32_t mx, sx, mxy, sxy;
+};
+
+// Divisor magic for q = (umulhi(v, m) + v) >> s, exact for 0 <= v < 2^31, 1 <= d < 2^31
+// (Granlund and Montgomery 1994, the "add" variant).
+inline void make_divisor(uint32_t d, uint32_t& m, uint32_t& s) {
+  uint32_t l = 0;
+  while ((1ull << l) < d) ++l;
+  s = l;
+  m = (uint32_t)(((1ull << 32) * ((1ull << l) - d)) / d + 1ull);
+}
+
+__device__ __forceinline__ uint32_t fast_div(uint32_t v, uint32_t m, uint32_t s) {
+  return (__umulhi(v, m) + v) >> s;
+}
+
+// ---- Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32->64 products ----
+__device__ __forceinline__ uint4 philox(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t a = c.x, b = c.z;
+    const uint32_t hi_a = __umulhi(0xD2511F53u, a), lo_a = 0xD2511F53u * a;
+    const uint32_t hi_b = __umulhi(0xCD9E8D57u, b), lo_b = 0xCD9E8D57u * b;
+    c = make_uint4(hi_b ^ c.y ^ k0, lo_b, hi_a ^ c.w ^ k1, lo_a);
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return c;
+}
+
+// ((r >> 8) + 1/2) 2^-24: exact in binary32, strictly inside (0, 1)
+__device__ __forceinline__ float uniform24(uint32_t r) {
+  return ((float)(r >> 8) + 0.5f) * 5.9604644775390625e-08f;
+}
+
+// Minimum image on a periodic axis, binary32, fixed rounding (no contraction).
+__device__ __forceinline__ float min_image_rn(float d, float n, int wall) {
+  if (!wall) {
+    const float h = 0.5f * n;
+    if (d > h) d = __fsub_rn(d, n);
+    else if (d < -h) d = __fadd_rn(d, n);
+  }
+  return d;
+}
+
+// Eq. 3 in binary32 with the fixed operation order that decides sub-sample counts and seeding:
+// d = x - c (one +-n minimum-image correction), r2 = (dx*dx + dy*dy) + dz*dz,
+// f = ((k_0 / r2_0) + k_1 / r2_1) + ... ; every operation rounded to nearest, never fused.
+__device__ __forceinline__ float metaball_exact(const float4* __restrict__ cw, int c0, int c1,
+                                                float x, float y, float z, const Geom& g) {
+  float f = 0.0f;
+  for (int i = c0; i < c1; ++i) {
+    const float4 c = cw[i];
+    const float dx = min_image_rn(__fsub_rn(x, c.x), (float)g.n[0], g.wall[0]);
+    const float dy = min_image_rn(__fsub_rn(y, c.y), (float)g.n[1], g.wall[1]);
+    const float dz = min_image_rn(__fsub_rn(z, c.z), (float)g.n[2], g.wall[2]);
+    float r2 = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
+    r2 = __fadd_rn(r2, __fmul_rn(dz, dz));
+    f = __fadd_rn(f, __fdiv_rn(c.w, r2));
+  }
+  return f;
+}
+
+// Eq. 3 and Eq. 17 for walker decisions (binary32, contraction allowed): value and gradient.
+__device__ __forceinline__ float metaball_grad(const float4* __restrict__ cw, int c0, int c1,
+                                               float x, float y, float z, const Geom& g,
+                                               float* gx, float* gy, float* gz) {
+  float f = 0.0f, ax = 0.0f, ay = 0.0f, az = 0.0f;
+  for (int i = c0; i < c1; ++i) {
+    const float4 c = cw[i];
+    const float dx = min_image_rn(x - c.x, (float)g.n[0], g.wall[0]);
+    const float dy = min_image_rn(y - c.y, (float)g.n[1], g.wall[1]);
+    const float dz = min_image_rn(z - c.z, (float)g.n[2], g.wall[2]);
+    const float r2 = dx * dx + dy * dy + dz * dz;
+    const float inv = 1.0f / r2;
+    const float term = c.w * inv;
+    f += term;
+    const float s = -2.0f * term * inv;
+    ax += s * dx; ay += s * dy; az += s * dz;
+  }
+  if (gx) { *gx = ax; *gy = ay; *gz = az; }
+  return f;
+}
+
+__device__ __forceinline__ float metaball_value(const float4* __restrict__ cw, int c0, int c1,
+                                                float x, float y, float z, const Geom& g) {
+  float f = 0.0f;
+  for (int i = c0; i < c1; ++i) {
+    const float4 c = cw[i];
+    const float dx = min_image_rn(x - c.x, (float)g.n[0], g.wall[0]);
+    const float dy = min_image_rn(y - c.y, (float)g.n[1], g.wall[1]);
+    const float dz = min_image_rn(z - c.z, (float)g.n[2], g.wall[2]);
+    f += c.w / (dx * dx + dy * dy + dz * dz);
+  }
+  return f;
+}
+
+// Wrap a coordinate into [0, n) on a periodic axis (binary32).
+__device__ __forceinline__ float wrap_coord(float x, float n, int wall) {
+  if (wall) return x;
+  float w = x - n * floorf(x / n);
+  if (w >= n) w -= n;
+  if (w < 0.0f) w += n;
+  return w;
+}
+
+__device__ __forceinline__ int brick_of(float xw, float yw, float zw, const Geom& g) {
+  int bi = min(max((int)floorf(xw) >> 3, 0), g.nb[0] - 1);
+  int bj = min(max((int)floorf(yw) >> 3, 0), g.nb[1] - 1);
+  int bk = min(max((int)floorf(zw) >> 3, 0), g.nb[2] - 1);
+  return (bk * g.nb[1] + bj) * g.nb[0] + bi;
+}
+
+// ---- kernel launchers (defined in the .cu files) ----
+struct BrickSet {
+  uint32_t* bword;    // [nbrick + 1]
+  uint16_t* bcand;    // [nbrick * MAXC]
+  int32_t* rlist;     // [nbrick]
+  PoseF* pose;        // [P]
+  float4* cworld;     // [Nc]
+  StepParams* sp;     // [1]
+};
+
+struct ParticleSet {
+  int P, Nc;
+  const ParticleDesc* desc;   // [P]
+  const float4* cbody;        // [Nc]
+  float walk_margin;          // candidate margin for walkers, cells
+};
+
+void launch_pose_bin(const Geom& g, const ParticleSet& ps, BrickSet bs, const int64_t* d_T,
+                     int t_offset, const double F0[3], double force_period, int zero_forces,
+                     double* forces, cudaStream_t st);
+void launch_raster(const Geom& g, const ParticleSet& ps, BrickSet bs, uint16_t* solid,
+                   unsigned long long* status, int nsm, cudaStream_t st);
+void launch_lbm(int q, int storage, bool reduce, const Geom& g, const void* fin, void* fout,
+                float* u, const uint16_t* solid, BrickSet bs, float tau, float rho0,
+                double* red, double* forces, unsigned long long* status, cudaStream_t st);
+void launch_init_populations(int q, int storage, const Geom& g, void* f, float rho0,
+                             const float u0[3], float* u, cudaStream_t st);
+void launch_walkers(const Geom& g, const ParticleSet& ps, BrickSet bs1, float4* pos, int64_t n,
+                    const float* u, const int64_t* d_T, float D, uint32_t k0, uint32_t k1,
+                    unsigned long long* status, unsigned int* ticket, int64_t* d_T_inc,
+                    cudaStream_t st);
+void launch_advance(int64_t* d_T, cudaStream_t st);
+void launch_seed(const Geom& g, const ParticleSet& ps, BrickSet bs, float4* pos, float4* x0,
+                 int64_t n, const double lo[3], const double hi[3], uint32_t k0, uint32_t k1,
+                 unsigned long long* status, cudaStream_t st);
+void launch_set_walkers(const float* pos3, float4* pos, float4* x0, int64_t n, cudaStream_t st);
+void launch_histogram(const Geom& g, const float4* pos, int64_t n, uint32_t* counts,
+                      uint32_t* rank, cudaStream_t st);
+void launch_scan(const uint32_t* counts, uint32_t* offsets, uint32_t* block_sums, uint32_t n,
+                 cudaStream_t st);
+void launch_scatter(const Geom& g, const float4* pos, const float4* x0, int64_t n,
+                    const uint32_t* offsets, const uint32_t* rank, float4* pos_out,
+                    float4* x0_out, cudaStream_t st);
+void launch_moments(const float4* pos, const float4* x0, int64_t n, double* acc, double* base,
+                    int interval, int rows, const int64_t* d_T, cudaStream_t st);
+void launch_unpack_solid(const Geom& g, const uint16_t* solid, const uint32_t* bword,
+                         int32_t* count, int32_t* owner, cudaStream_t st);
+void launch_populations_f64(int q, int storage, const Geom& g, const void* f, float rho0,
+                            double* out, cudaStream_t st);
+void launch_velocity_aos(const Geom& g, const float* u, float* out, cudaStream_t st);
+void launch_density(int q, int storage, const Geom& g, const void* f, float rho0, float* out,
+                    cudaStream_t st);
+void launch_load_populations(int q, int storage, const Geom& g, const double* in, float rho0,
+                             void* f, cudaStream_t st);
+size_t scan_block_sums_size(uint32_t n);
+void lattice_table(int q, int32_t* e, double* w);
+
+}  // namespace rwmi

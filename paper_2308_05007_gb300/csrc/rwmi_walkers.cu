@@ -1,0 +1,559 @@
+// rwmi_walkers.cu -- random-walk advance of solute walkers (Eq. 2, Section 2.4), seeding,
+// counting sort by cell (the histogram is the concentration of Eq. 16) and FP64 moments.
+#include "rwmi_internal.cuh"
+
+namespace rwmi {
+
+// ------------------------------------------------------------------------------------------
+// Section 2.4.1: velocity at the walker by trilinear interpolation of the node values (cell
+// centres). Periodic axes wrap; on a walled axis the wall plane carries u = 0 and the half cell
+// between wall and first node interpolates linearly to it (the wall corner gets weight 0).
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ void axis_weights(float x, int n, int wall, int& i0, int& i1, float& w0,
+                                             float& w1) {
+  if (!wall) {
+    const float s = x - 0.5f;
+    const float fl = floorf(s);
+    const float w = s - fl;
+    int i = (int)fl % n;
+    if (i < 0) i += n;
+    i0 = i;
+    i1 = i + 1 == n ? 0 : i + 1;
+    w0 = 1.0f - w;
+    w1 = w;
+    return;
+  }
+  const float nf = (float)n;
+  x = fminf(fmaxf(x, 0.0f), nf);
+  if (x < 0.5f) {
+    i0 = 0; i1 = 0; w0 = 0.0f; w1 = 2.0f * x;                 // wall (0) .. node 0
+  } else if (x >= nf - 0.5f) {
+    i0 = n - 1; i1 = n - 1; w0 = 1.0f - 2.0f * (x - (nf - 0.5f)); w1 = 0.0f;   // node n-1 .. wall
+  } else {
+    const float s = x - 0.5f;
+    const float fl = floorf(s);
+    i0 = (int)fl;
+    i1 = min(i0 + 1, n - 1);
+    w1 = s - fl;
+    w0 = 1.0f - w1;
+  }
+}
+
+__device__ __forceinline__ void interp_velocity(const float* __restrict__ u, const Geom& g, float x,
+                                                float y, float z, float& ux, float& uy, float& uz) {
+  int ix0, ix1, iy0, iy1, iz0, iz1;
+  float wx0, wx1, wy0, wy1, wz0, wz1;
+  axis_weights(x, g.n[0], g.wall[0], ix0, ix1, wx0, wx1);
+  axis_weights(y, g.n[1], g.wall[1], iy0, iy1, wy0, wy1);
+  axis_weights(z, g.n[2], g.wall[2], iz0, iz1, wz0, wz1);
+  const size_t pad = g.ncell_pad;
+  const uint32_t r00 = ((uint32_t)iz0 * g.n[1] + iy0) * g.n[0], r01 = ((uint32_t)iz0 * g.n[1] + iy1) * g.n[0];
+  const uint32_t r10 = ((uint32_t)iz1 * g.n[1] + iy0) * g.n[0], r11 = ((uint32_t)iz1 * g.n[1] + iy1) * g.n[0];
+  const uint32_t cidx[8] = {r00 + ix0, r00 + ix1, r01 + ix0, r01 + ix1,
+                            r10 + ix0, r10 + ix1, r11 + ix0, r11 + ix1};
+  const float cw[8] = {wz0 * wy0 * wx0, wz0 * wy0 * wx1, wz0 * wy1 * wx0, wz0 * wy1 * wx1,
+                       wz1 * wy0 * wx0, wz1 * wy0 * wx1, wz1 * wy1 * wx0, wz1 * wy1 * wx1};
+  float ax = 0.0f, ay = 0.0f, az = 0.0f;
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    ax += cw[m] * __ldg(u + cidx[m]);
+    ay += cw[m] * __ldg(u + pad + cidx[m]);
+    az += cw[m] * __ldg(u + 2 * pad + cidx[m]);
+  }
+  ux = ax; uy = ay; uz = az;
+}
+
+// Specular reflection at no-slip wall planes. Returns false if a coordinate stayed outside.
+__device__ __forceinline__ bool wall_reflect(float* x, const Geom& g) {
+  bool ok = true;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (!g.wall[a]) continue;
+    const float n = (float)g.n[a];
+    for (int it = 0; it < 8; ++it) {
+      if (x[a] < 0.0f) x[a] = -x[a];
+      else if (x[a] > n) x[a] = 2.0f * n - x[a];
+      else break;
+    }
+    if (x[a] < 0.0f || x[a] > n) { ok = false; x[a] = x[a] < 0.0f ? 0.0f : n; }
+  }
+  return ok;
+}
+
+__device__ __forceinline__ bool beyond_wall(const float* x, const Geom& g) {
+  for (int a = 0; a < 3; ++a)
+    if (g.wall[a] && (x[a] < 0.0f || x[a] > (float)g.n[a])) return true;
+  return false;
+}
+
+struct WalkCtx {
+  Geom g;
+  ParticleSet ps;
+  BrickSet bs;
+};
+
+__device__ __forceinline__ float f_particle(const WalkCtx& c, int p, const float* x, float* gr) {
+  const float xw = wrap_coord(x[0], (float)c.g.n[0], c.g.wall[0]);
+  const float yw = wrap_coord(x[1], (float)c.g.n[1], c.g.wall[1]);
+  const float zw = wrap_coord(x[2], (float)c.g.n[2], c.g.wall[2]);
+  const ParticleDesc& d = c.ps.desc[p];
+  if (gr) return metaball_grad(c.bs.cworld, d.c0, d.c1, xw, yw, zw, c.g, gr, gr + 1, gr + 2);
+  return metaball_value(c.bs.cworld, d.c0, d.c1, xw, yw, zw, c.g);
+}
+
+// Lowest-index particle holding x (any particle; bound-radius skip), or -1.
+__device__ int inside_any(const WalkCtx& c, const float* x) {
+  const float xw = wrap_coord(x[0], (float)c.g.n[0], c.g.wall[0]);
+  const float yw = wrap_coord(x[1], (float)c.g.n[1], c.g.wall[1]);
+  const float zw = wrap_coord(x[2], (float)c.g.n[2], c.g.wall[2]);
+  for (int p = 0; p < c.ps.P; ++p) {
+    const PoseF& pp = c.bs.pose[p];
+    const float dx = min_image_rn(xw - pp.o[0], (float)c.g.n[0], c.g.wall[0]);
+    const float dy = min_image_rn(yw - pp.o[1], (float)c.g.n[1], c.g.wall[1]);
+    const float dz = min_image_rn(zw - pp.o[2], (float)c.g.n[2], c.g.wall[2]);
+    const float rb = c.ps.desc[p].rb + 1e-3f;
+    if (dx * dx + dy * dy + dz * dz > rb * rb) continue;
+    const ParticleDesc& d = c.ps.desc[p];
+    if (metaball_value(c.bs.cworld, d.c0, d.c1, xw, yw, zw, c.g) >= 1.0f) return p;
+  }
+  return -1;
+}
+
+// Algorithm 1: bisection from outside point a (f < 1) to inside point b (f >= 1) of particle p;
+// |f(mid) - 1| < 1e-3 converges; at most 200 iterations. aout: final outside end.
+__device__ bool bisect(const WalkCtx& c, int p, const float* a_in, const float* b_in, float* xi, float* aout) {
+  float a[3] = {a_in[0], a_in[1], a_in[2]}, b[3] = {b_in[0], b_in[1], b_in[2]};
+  bool found = false;
+  for (int it = 1; it <= 200; ++it) {
+    float mid[3] = {0.5f * (a[0] + b[0]), 0.5f * (a[1] + b[1]), 0.5f * (a[2] + b[2])};
+    const float fm = f_particle(c, p, mid, nullptr);
+    if (fabsf(fm - 1.0f) < 1e-3f) {
+      xi[0] = mid[0]; xi[1] = mid[1]; xi[2] = mid[2];
+      found = true;
+      break;
+    } else if (fm < 1.0f) {
+      a[0] = mid[0]; a[1] = mid[1]; a[2] = mid[2];
+    } else {
+      b[0] = mid[0]; b[1] = mid[1]; b[2] = mid[2];
+    }
+  }
+  if (aout) { aout[0] = a[0]; aout[1] = a[1]; aout[2] = a[2]; }
+  return found;
+}
+
+// Section 2.4.2 refill of a type-II walker (see the oracle's reading, implemented alike).
+__device__ bool refill(const WalkCtx& c, int p, const float* x, uint32_t id, uint32_t t, float amp,
+                       uint32_t k0, uint32_t k1, float* xnew) {
+  float gr[3];
+  f_particle(c, p, x, gr);
+  const float gn = sqrtf(gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2]);
+  float s[3] = {1.0f, 0.0f, 0.0f};
+  if (gn > 0.0f && isfinite(gn)) { s[0] = -gr[0] / gn; s[1] = -gr[1] / gn; s[2] = -gr[2] / gn; }
+  float xo[3];
+  bool out = false;
+  for (float h = 0.5f; h <= 64.0f; h *= 2.0f) {
+    xo[0] = x[0] + h * s[0]; xo[1] = x[1] + h * s[1]; xo[2] = x[2] + h * s[2];
+    if (f_particle(c, p, xo, nullptr) < 1.0f) { out = true; break; }
+  }
+  if (!out) { xnew[0] = x[0]; xnew[1] = x[1]; xnew[2] = x[2]; return false; }
+  float xs[3], aend[3];
+  if (!bisect(c, p, xo, x, xs, aend)) { xs[0] = aend[0]; xs[1] = aend[1]; xs[2] = aend[2]; }
+  float gs[3];
+  f_particle(c, p, xs, gs);
+  const float gsn = sqrtf(gs[0] * gs[0] + gs[1] * gs[1] + gs[2] * gs[2]);
+  const float no[3] = {-gs[0] / gsn, -gs[1] / gsn, -gs[2] / gsn};
+  const uint4 r = philox(make_uint4(id, t, 1u, 0u), k0, k1);
+  const float ct = 2.0f * uniform24(r.x) - 1.0f;
+  const float st = sqrtf(fmaxf(0.0f, 1.0f - ct * ct));
+  float sp, cp;
+  sincospif(2.0f * uniform24(r.y), &sp, &cp);
+  const float rad = amp * cbrtf(uniform24(r.z));
+  float xr[3] = {xs[0] + rad * st * cp, xs[1] + rad * st * sp, xs[2] + rad * ct};
+  wall_reflect(xr, c.g);
+  if (inside_any(c, xr) >= 0) {
+    const float dn = (xr[0] - xs[0]) * no[0] + (xr[1] - xs[1]) * no[1] + (xr[2] - xs[2]) * no[2];
+    if (dn < 0.0f) for (int a = 0; a < 3; ++a) xr[a] -= 2.0f * dn * no[a];
+    wall_reflect(xr, c.g);
+    if (inside_any(c, xr) >= 0) {
+      xr[0] = aend[0]; xr[1] = aend[1]; xr[2] = aend[2];
+      if (inside_any(c, xr) >= 0) { xnew[0] = xr[0]; xnew[1] = xr[1]; xnew[2] = xr[2]; return false; }
+    }
+  }
+  xnew[0] = xr[0]; xnew[1] = xr[1]; xnew[2] = xr[2];
+  return true;
+}
+
+// One thread per walker: Eq. 2 with dt = 1, walls, then the type I-IV rules against the
+// particles at t+1 (candidates from the walker's brick; rare paths test all particles).
+__global__ void __launch_bounds__(256) walker_kernel(WalkCtx c, float4* __restrict__ pos, int64_t n,
+                                                     const float* __restrict__ u,
+                                                     const int64_t* __restrict__ d_T, float amp,
+                                                     uint32_t k0, uint32_t k1,
+                                                     unsigned long long* __restrict__ status,
+                                                     unsigned int* ticket, int64_t* d_T_inc) {
+  const int64_t T = *d_T;
+  const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (w < n) {
+    const float4 p4 = pos[w];
+    const uint32_t id = __float_as_uint(p4.w);
+    const float x[3] = {p4.x, p4.y, p4.z};
+    float ux, uy, uz;
+    interp_velocity(u, c.g, x[0], x[1], x[2], ux, uy, uz);
+    const uint4 r = philox(make_uint4(id, (uint32_t)T, 0u, 0u), k0, k1);
+    const float rad01 = sqrtf(-2.0f * logf(uniform24(r.x)));
+    const float rad23 = sqrtf(-2.0f * logf(uniform24(r.z)));
+    float s1, c1;
+    sincospif(2.0f * uniform24(r.y), &s1, &c1);
+    const float c3 = cospif(2.0f * uniform24(r.w));
+    float xf[3] = {x[0] + ux + amp * (rad01 * c1), x[1] + uy + amp * (rad01 * s1),
+                   x[2] + uz + amp * (rad23 * c3)};
+    if (!wall_reflect(xf, c.g)) atomicAdd(&status[ST_WALL_FAIL], 1ull);
+    float xn[3] = {xf[0], xf[1], xf[2]};
+    if (c.ps.P > 0) {
+      const float step2 = (xf[0] - x[0]) * (xf[0] - x[0]) + (xf[1] - x[1]) * (xf[1] - x[1]) +
+                          (xf[2] - x[2]) * (xf[2] - x[2]);
+      const float xw = wrap_coord(x[0], (float)c.g.n[0], c.g.wall[0]);
+      const float yw = wrap_coord(x[1], (float)c.g.n[1], c.g.wall[1]);
+      const float zw = wrap_coord(x[2], (float)c.g.n[2], c.g.wall[2]);
+      const int b = brick_of(xw, yw, zw, c.g);
+      const uint32_t nc = c.bs.bword[b] & 0xffffu;
+      const bool far_step = step2 > c.ps.walk_margin * c.ps.walk_margin;
+      if (far_step) atomicAdd(&status[ST_FAST_SPEED], 1ull);
+      if (nc > 0 || far_step) {
+        int pin = -1, qin = -1;
+        if (nc > MAXC || far_step) {
+          pin = inside_any(c, x);
+          qin = inside_any(c, xf);
+        } else {
+          const float xfw = wrap_coord(xf[0], (float)c.g.n[0], c.g.wall[0]);
+          const float yfw = wrap_coord(xf[1], (float)c.g.n[1], c.g.wall[1]);
+          const float zfw = wrap_coord(xf[2], (float)c.g.n[2], c.g.wall[2]);
+          for (uint32_t m = 0; m < nc; ++m) {
+            const int p = c.bs.bcand[b * MAXC + m] & 0x7fff;
+            const ParticleDesc& d = c.ps.desc[p];
+            if ((pin < 0 || p < pin) && metaball_value(c.bs.cworld, d.c0, d.c1, xw, yw, zw, c.g) >= 1.0f) pin = p;
+            if ((qin < 0 || p < qin) && metaball_value(c.bs.cworld, d.c0, d.c1, xfw, yfw, zfw, c.g) >= 1.0f) qin = p;
+          }
+        }
+        if (pin >= 0 && qin >= 0) {            // type II: Dirichlet refill
+          atomicAdd(&status[ST_TYPE2], 1ull);
+          if (!refill(c, pin, x, id, (uint32_t)T, amp, k0, k1, xn)) atomicAdd(&status[ST_REFILL_FAIL], 1ull);
+        } else if (pin >= 0) {                 // type III: moves out freely
+          atomicAdd(&status[ST_TYPE3], 1ull);
+        } else if (qin >= 0) {                 // type IV: Algorithms 1 and 2
+          atomicAdd(&status[ST_TYPE4], 1ull);
+          float xi[3];
+          if (!bisect(c, qin, x, xf, xi, nullptr)) {
+            atomicAdd(&status[ST_BISECT_FAIL], 1ull);
+            xn[0] = x[0]; xn[1] = x[1]; xn[2] = x[2];
+          } else {
+            float gr[3];
+            f_particle(c, qin, xi, gr);
+            const float gn = sqrtf(gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2]);
+            const float nv[3] = {gr[0] / gn, gr[1] / gn, gr[2] / gn};
+            const float ti[3] = {xf[0] - xi[0], xf[1] - xi[1], xf[2] - xi[2]};
+            const float tn = ti[0] * nv[0] + ti[1] * nv[1] + ti[2] * nv[2];
+            float tr[3];
+            for (int a = 0; a < 3; ++a) tr[a] = xi[a] + (ti[a] - 2.0f * tn * nv[a]);
+            if (beyond_wall(tr, c.g) || inside_any(c, tr) >= 0) {
+              xn[0] = x[0]; xn[1] = x[1]; xn[2] = x[2];
+            } else {
+              xn[0] = tr[0]; xn[1] = tr[1]; xn[2] = tr[2];
+            }
+          }
+        }
+      }
+    }
+    if (!(isfinite(ux) && isfinite(uy) && isfinite(uz))) atomicAdd(&status[ST_NONFINITE], 1ull);
+    pos[w] = make_float4(xn[0], xn[1], xn[2], p4.w);
+  }
+  // the last block to finish advances the device step counter
+  if (d_T_inc) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      const unsigned int done = atomicAdd(ticket, 1u);
+      if (done == gridDim.x - 1) {
+        *d_T_inc = T + 1;
+        *ticket = 0u;
+        __threadfence();
+      }
+    }
+  }
+}
+
+void launch_walkers(const Geom& g, const ParticleSet& ps, BrickSet bs1, float4* pos, int64_t n,
+                    const float* u, const int64_t* d_T, float D, uint32_t k0, uint32_t k1,
+                    unsigned long long* status, unsigned int* ticket, int64_t* d_T_inc,
+                    cudaStream_t st) {
+  WalkCtx c{g, ps, bs1};
+  const int64_t blocks = (n + 255) / 256;
+  walker_kernel<<<(unsigned)blocks, 256, 0, st>>>(c, pos, n, u, d_T, sqrtf(2.0f * D), k0, k1,
+                                                  status, ticket, d_T_inc);
+}
+
+__global__ void advance_kernel(int64_t* d_T) { *d_T += 1; }
+void launch_advance(int64_t* d_T, cudaStream_t st) { advance_kernel<<<1, 1, 0, st>>>(d_T); }
+
+// ------------------------------------------------------------------------------------------
+// Seeding: walker w tries Philox counters (w, a, 2, 0); point lo + U (hi - lo) in explicitly
+// rounded FP64, rounded to binary32; accepted when Eq. 3 (exact binary32 sequence) stays
+// below 1 for every particle -- the same decision the CPU oracle takes.
+// ------------------------------------------------------------------------------------------
+__global__ void seed_kernel(Geom g, ParticleSet ps, BrickSet bs, float4* pos, float4* x0, int64_t n,
+                            double lo0, double lo1, double lo2, double hi0, double hi1, double hi2,
+                            uint32_t k0, uint32_t k1, unsigned long long* status) {
+  const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= n) return;
+  const double lo[3] = {lo0, lo1, lo2}, hi[3] = {hi0, hi1, hi2};
+  float x[3] = {0.0f, 0.0f, 0.0f};
+  bool ok = false;
+  for (int a = 0; a < 1000 && !ok; ++a) {
+    const uint4 r = philox(make_uint4((uint32_t)w, (uint32_t)a, 2u, 0u), k0, k1);
+    const uint32_t rr[3] = {r.x, r.y, r.z};
+    for (int d = 0; d < 3; ++d) {
+      const double uu = ((double)(rr[d] >> 8) + 0.5) * 5.9604644775390625e-08;
+      x[d] = __double2float_rn(__dadd_rn(lo[d], __dmul_rn(uu, __dsub_rn(hi[d], lo[d]))));
+    }
+    ok = true;
+    if (ps.P > 0) {
+      const int b = brick_of(wrap_coord(x[0], (float)g.n[0], g.wall[0]),
+                             wrap_coord(x[1], (float)g.n[1], g.wall[1]),
+                             wrap_coord(x[2], (float)g.n[2], g.wall[2]), g);
+      const uint32_t nc = bs.bword[b] & 0xffffu;
+      const uint32_t m_end = nc > MAXC ? (uint32_t)ps.P : nc;
+      for (uint32_t m = 0; m < m_end && ok; ++m) {
+        const int p = nc > MAXC ? (int)m : (bs.bcand[b * MAXC + m] & 0x7fff);
+        if (metaball_exact(bs.cworld, ps.desc[p].c0, ps.desc[p].c1, x[0], x[1], x[2], g) >= 1.0f) ok = false;
+      }
+    }
+  }
+  if (!ok) atomicAdd(&status[ST_SEED_FAIL], 1ull);
+  pos[w] = make_float4(x[0], x[1], x[2], __uint_as_float((uint32_t)w));
+  x0[w] = make_float4(x[0], x[1], x[2], 0.0f);
+}
+
+void launch_seed(const Geom& g, const ParticleSet& ps, BrickSet bs, float4* pos, float4* x0,
+                 int64_t n, const double lo[3], const double hi[3], uint32_t k0, uint32_t k1,
+                 unsigned long long* status, cudaStream_t st) {
+  if (n <= 0) return;
+  seed_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g, ps, bs, pos, x0, n, lo[0], lo[1], lo[2],
+                                                           hi[0], hi[1], hi[2], k0, k1, status);
+}
+
+__global__ void set_walkers_kernel(const float* pos3, float4* pos, float4* x0, int64_t n) {
+  const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= n) return;
+  const float x = pos3[3 * w], y = pos3[3 * w + 1], z = pos3[3 * w + 2];
+  pos[w] = make_float4(x, y, z, __uint_as_float((uint32_t)w));
+  x0[w] = make_float4(x, y, z, 0.0f);
+}
+
+void launch_set_walkers(const float* pos3, float4* pos, float4* x0, int64_t n, cudaStream_t st) {
+  if (n <= 0) return;
+  set_walkers_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(pos3, pos, x0, n);
+}
+
+// ------------------------------------------------------------------------------------------
+// Eq. 16 binning and the counting sort by cell: histogram with warp-aggregated atomics (lanes
+// holding walkers of the same cell share one atomic), exclusive scan, stable-per-rank scatter.
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t walker_cell(const float4& p, const Geom& g) {
+  const float x[3] = {p.x, p.y, p.z};
+  int c[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    int i = (int)floorf(x[a]);
+    if (g.wall[a]) i = min(max(i, 0), g.n[a] - 1);
+    else { i %= g.n[a]; if (i < 0) i += g.n[a]; }
+    c[a] = i;
+  }
+  return ((uint32_t)c[2] * g.n[1] + c[1]) * g.n[0] + c[0];
+}
+
+__global__ void histogram_kernel(Geom g, const float4* __restrict__ pos, int64_t n,
+                                 uint32_t* __restrict__ counts, uint32_t* __restrict__ rank) {
+  const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool act = w < n;
+  const unsigned amask = __ballot_sync(0xffffffffu, act);
+  if (!act) return;
+  const uint32_t cell = walker_cell(pos[w], g);
+  const unsigned peers = __match_any_sync(amask, cell);
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(peers) - 1;
+  uint32_t base = 0;
+  if (lane == leader) base = atomicAdd(&counts[cell], (uint32_t)__popc(peers));
+  base = __shfl_sync(peers, base, leader);
+  if (rank) rank[w] = base + __popc(peers & ((1u << lane) - 1u));
+}
+
+void launch_histogram(const Geom& g, const float4* pos, int64_t n, uint32_t* counts,
+                      uint32_t* rank, cudaStream_t st) {
+  if (n <= 0) return;
+  histogram_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g, pos, n, counts, rank);
+}
+
+constexpr int SCAN_THREADS = 256, SCAN_ITEMS = 8, SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+
+size_t scan_block_sums_size(uint32_t n) { return (n + SCAN_TILE - 1) / SCAN_TILE + 1; }
+
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* total) {
+  __shared__ uint32_t s_w[SCAN_THREADS / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint32_t incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) s_w[wid] = incl;
+  __syncthreads();
+  if (wid == 0) {
+    uint32_t s = lane < SCAN_THREADS / 32 ? s_w[lane] : 0u;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += t;
+    }
+    if (lane < SCAN_THREADS / 32) s_w[lane] = s;
+  }
+  __syncthreads();
+  const uint32_t wbase = wid > 0 ? s_w[wid - 1] : 0u;
+  if (total) *total = s_w[SCAN_THREADS / 32 - 1];
+  __syncthreads();
+  return wbase + incl - v;
+}
+
+__global__ void scan_reduce_kernel(const uint32_t* __restrict__ in, uint32_t n, uint32_t* __restrict__ sums) {
+  const uint32_t base = blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
+  uint32_t s = 0;
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; ++k) s += base + k < n ? in[base + k] : 0u;
+  uint32_t total;
+  block_exclusive_scan(s, &total);
+  if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+__global__ void scan_top_kernel(uint32_t* sums, uint32_t nb) {
+  uint32_t carry = 0;
+  for (uint32_t base = 0; base < nb; base += SCAN_THREADS) {
+    const uint32_t i = base + threadIdx.x;
+    const uint32_t v = i < nb ? sums[i] : 0u;
+    uint32_t total;
+    const uint32_t ex = block_exclusive_scan(v, &total);
+    if (i < nb) sums[i] = carry + ex;
+    carry += total;
+  }
+}
+
+__global__ void scan_down_kernel(const uint32_t* __restrict__ in, uint32_t n,
+                                 const uint32_t* __restrict__ sums, uint32_t* __restrict__ out) {
+  const uint32_t base = blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
+  uint32_t v[SCAN_ITEMS], s = 0;
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; ++k) { v[k] = base + k < n ? in[base + k] : 0u; s += v[k]; }
+  uint32_t run = sums[blockIdx.x] + block_exclusive_scan(s, nullptr);
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; ++k) {
+    if (base + k < n) out[base + k] = run;
+    run += v[k];
+  }
+}
+
+void launch_scan(const uint32_t* counts, uint32_t* offsets, uint32_t* block_sums, uint32_t n,
+                 cudaStream_t st) {
+  const uint32_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
+  scan_reduce_kernel<<<nb, SCAN_THREADS, 0, st>>>(counts, n, block_sums);
+  scan_top_kernel<<<1, SCAN_THREADS, 0, st>>>(block_sums, nb);
+  scan_down_kernel<<<nb, SCAN_THREADS, 0, st>>>(counts, n, block_sums, offsets);
+}
+
+__global__ void scatter_kernel(Geom g, const float4* __restrict__ pos, const float4* __restrict__ x0,
+                               int64_t n, const uint32_t* __restrict__ offsets,
+                               const uint32_t* __restrict__ rank, float4* __restrict__ pos_out,
+                               float4* __restrict__ x0_out) {
+  const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= n) return;
+  const float4 p = pos[w];
+  const uint32_t dst = offsets[walker_cell(p, g)] + rank[w];
+  pos_out[dst] = p;
+  x0_out[dst] = x0[w];
+}
+
+void launch_scatter(const Geom& g, const float4* pos, const float4* x0, int64_t n,
+                    const uint32_t* offsets, const uint32_t* rank, float4* pos_out,
+                    float4* x0_out, cudaStream_t st) {
+  if (n <= 0) return;
+  scatter_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g, pos, x0, n, offsets, rank, pos_out, x0_out);
+}
+
+// ------------------------------------------------------------------------------------------
+// FP64 walker moments: sums of d = x - x0, d^2, x, x^2 per axis (exact FP64 differences of the
+// binary32 positions), then {N, mean d, var d, mean x, var x}.
+// ------------------------------------------------------------------------------------------
+__global__ void moments_kernel(const float4* __restrict__ pos, const float4* __restrict__ x0, int64_t n,
+                               double* __restrict__ acc) {
+  double v[12];
+#pragma unroll
+  for (int m = 0; m < 12; ++m) v[m] = 0.0;
+  for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < n; w += (int64_t)gridDim.x * blockDim.x) {
+    const float4 p = pos[w], q = x0[w];
+    const double xs[3] = {p.x, p.y, p.z}, x0s[3] = {q.x, q.y, q.z};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const double d = xs[a] - x0s[a];
+      v[a] += d;
+      v[3 + a] += d * d;
+      v[6 + a] += xs[a];
+      v[9 + a] += xs[a] * xs[a];
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < 12; ++m)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[m] += __shfl_xor_sync(0xffffffffu, v[m], o);
+  __shared__ double s[8][12];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0)
+    for (int m = 0; m < 12; ++m) s[wid][m] = v[m];
+  __syncthreads();
+  if (threadIdx.x < 12) {
+    double t = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += s[k][threadIdx.x];
+    atomicAdd(&acc[threadIdx.x], t);
+  }
+}
+
+// Row {t, N, mean d[3], var d[3], mean x[3], var x[3]}; clears acc for the next use. With
+// interval > 0 the row is slot (t / interval - 1) mod rows of the series at base (so a replayed
+// graph writes the row of the step it runs), otherwise base itself.
+__global__ void moments_finalize_kernel(double* acc, int64_t n, double* base, int interval, int rows,
+                                        const int64_t* d_T) {
+  if (threadIdx.x != 0) return;
+  const double N = (double)n;
+  const int64_t t = *d_T;
+  double* out_row = base;
+  if (interval > 0) out_row = base + (size_t)(((t / interval) - 1) % rows) * 14;
+  out_row[0] = (double)t;
+  out_row[1] = N;
+  for (int a = 0; a < 3; ++a) {
+    const double md = n ? acc[a] / N : 0.0, mx = n ? acc[6 + a] / N : 0.0;
+    out_row[2 + a] = md;
+    out_row[5 + a] = n ? acc[3 + a] / N - md * md : 0.0;
+    out_row[8 + a] = mx;
+    out_row[11 + a] = n ? acc[9 + a] / N - mx * mx : 0.0;
+  }
+  for (int m = 0; m < 12; ++m) acc[m] = 0.0;
+}
+
+void launch_moments(const float4* pos, const float4* x0, int64_t n, double* acc, double* base,
+                    int interval, int rows, const int64_t* d_T, cudaStream_t st) {
+  if (n > 0) {
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    moments_kernel<<<(unsigned)blocks, 256, 0, st>>>(pos, x0, n, acc);
+  }
+  moments_finalize_kernel<<<1, 32, 0, st>>>(acc, n, base, interval, rows, d_T);
+}
+
+}  // namespace rwmi

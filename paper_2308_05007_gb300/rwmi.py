@@ -1,0 +1,331 @@
+"""Thin ctypes binding of librwmi.so (include/rwmi.h): argument marshalling only.
+
+Every step of the method runs in the library's CUDA kernels; this module converts numpy/torch
+arrays to pointers and status codes to exceptions. If the library is missing it raises -- there
+is no CPU path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+RWMI_OK, RWMI_W_BISECT, RWMI_W_SEED = 0, 1, 2
+STATUS_NAMES = {0: "RWMI_OK", 1: "RWMI_W_BISECT", 2: "RWMI_W_SEED", -1: "RWMI_E_INVALID", -2: "RWMI_E_OOM",
+                -3: "RWMI_E_CUDA", -4: "RWMI_E_NONFINITE", -5: "RWMI_E_TIMEOUT", -6: "RWMI_E_STATE"}
+STORE_FP32, STORE_FP32_SHIFT, STORE_FP16_SHIFT = 0, 1, 2
+
+EXPORTED = ["rwmi_config_defaults", "rwmi_create", "rwmi_configure", "rwmi_set_stream",
+            "rwmi_set_metaballs", "rwmi_seed_walkers", "rwmi_set_walkers", "rwmi_step", "rwmi_step_timed",
+            "rwmi_sync",
+            "rwmi_time", "rwmi_concentration", "rwmi_walker_moments", "rwmi_moment_series",
+            "rwmi_velocity", "rwmi_density", "rwmi_populations", "rwmi_lattice", "rwmi_solid",
+            "rwmi_mass_momentum", "rwmi_particle_forces", "rwmi_walkers", "rwmi_counters", "rwmi_save",
+            "rwmi_load", "rwmi_last_error", "rwmi_launch_count", "rwmi_destroy"]
+
+
+class RwmiError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class RwmiWarning(RuntimeWarning):
+    pass
+
+
+class Config(C.Structure):
+    _fields_ = [("q", C.c_int32), ("storage", C.c_int32), ("wall_mask", C.c_uint32),
+                ("body_force", C.c_double * 3), ("force_period", C.c_double), ("rho0", C.c_double),
+                ("init_velocity", C.c_double * 3), ("sort_interval", C.c_int32),
+                ("moment_interval", C.c_int32), ("use_graphs", C.c_int32)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load librwmi.so. Raises if it is not built (no fallback of any kind)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_build.LIB):
+        if not build_if_missing:
+            raise RuntimeError(f"{_build.LIB} is not built; run __graft_entry__.build() (needs nvcc)")
+        _build.build()
+    L = C.CDLL(_build.LIB)
+    P, vp = C.c_void_p, C.c_void_p
+    L.rwmi_config_defaults.argtypes = [C.POINTER(Config)]
+    L.rwmi_config_defaults.restype = None
+    L.rwmi_create.argtypes = [C.POINTER(P), C.POINTER(C.c_int32), C.c_double, C.c_double, C.c_uint64]
+    L.rwmi_configure.argtypes = [P, C.POINTER(Config)]
+    L.rwmi_set_stream.argtypes = [P, vp]
+    L.rwmi_set_metaballs.argtypes = [P, C.c_int32, vp, vp, vp, vp, vp, vp, vp, vp]
+    L.rwmi_seed_walkers.argtypes = [P, C.c_int64, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    L.rwmi_set_walkers.argtypes = [P, C.c_int64, vp]
+    L.rwmi_step.argtypes = [P, C.c_int32]
+    L.rwmi_step_timed.argtypes = [P, C.c_int32, vp]
+    L.rwmi_sync.argtypes = [P]
+    L.rwmi_time.argtypes = [P, C.POINTER(C.c_int64)]
+    for name in ("rwmi_concentration", "rwmi_walker_moments", "rwmi_velocity", "rwmi_density",
+                 "rwmi_populations", "rwmi_mass_momentum", "rwmi_particle_forces", "rwmi_counters"):
+        getattr(L, name).argtypes = [P, vp]
+    L.rwmi_moment_series.argtypes = [P, vp, C.c_int32, C.POINTER(C.c_int32)]
+    L.rwmi_lattice.argtypes = [P, vp, vp, C.POINTER(C.c_int32)]
+    L.rwmi_solid.argtypes = [P, vp, vp]
+    L.rwmi_walkers.argtypes = [P, vp, vp]
+    L.rwmi_save.argtypes = [P, C.c_char_p]
+    L.rwmi_load.argtypes = [P, C.c_char_p]
+    L.rwmi_last_error.argtypes = [P]
+    L.rwmi_last_error.restype = C.c_char_p
+    L.rwmi_launch_count.argtypes = [P]
+    L.rwmi_launch_count.restype = C.c_int64
+    L.rwmi_destroy.argtypes = [P]
+    L.rwmi_destroy.restype = None
+    for name in EXPORTED:
+        fn = getattr(L, name)
+        if name not in ("rwmi_config_defaults", "rwmi_last_error", "rwmi_launch_count", "rwmi_destroy"):
+            fn.restype = C.c_int
+    _lib = L
+    return L
+
+
+def _ptr(a):
+    """Pointer of a numpy array or a torch tensor (host or CUDA)."""
+    if hasattr(a, "data_ptr"):
+        return C.c_void_p(a.data_ptr())
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _d3(v):
+    return (C.c_double * 3)(*[float(x) for x in v])
+
+
+class Simulation:
+    """One GPU simulation context (librwmi.so). Outputs are numpy arrays unless a torch tensor
+    (host or CUDA, contiguous, right dtype and size) is passed as ``out``."""
+
+    def __init__(self, dims, tau, D, seed=0, q=19, storage=STORE_FP32_SHIFT, wall_mask=0,
+                 body_force=(0.0, 0.0, 0.0), force_period=0.0, rho0=1.0, init_velocity=(0.0, 0.0, 0.0),
+                 sort_interval=16, moment_interval=0, use_graphs=True, stream=None):
+        L = load()
+        self._L = L
+        self._h = C.c_void_p()
+        d = (C.c_int32 * 3)(*[int(x) for x in dims])
+        st = L.rwmi_create(C.byref(self._h), d, float(tau), float(D), C.c_uint64(int(seed) & (2**64 - 1)))
+        if st != 0:
+            raise RwmiError(st, "rwmi_create failed")
+        self.dims = tuple(int(x) for x in dims)
+        self.n_cells = self.dims[0] * self.dims[1] * self.dims[2]
+        cfg = Config()
+        L.rwmi_config_defaults(C.byref(cfg))
+        cfg.q, cfg.storage, cfg.wall_mask = int(q), int(storage), int(wall_mask)
+        for a in range(3):
+            cfg.body_force[a] = float(body_force[a])
+            cfg.init_velocity[a] = float(init_velocity[a])
+        cfg.force_period, cfg.rho0 = float(force_period), float(rho0)
+        cfg.sort_interval, cfg.moment_interval = int(sort_interval), int(moment_interval)
+        cfg.use_graphs = 1 if use_graphs else 0
+        self._check(L.rwmi_configure(self._h, C.byref(cfg)))
+        self.q = int(q)
+        self.n_particles = 0
+        self.n_walkers = 0
+        if stream is not None:
+            self.set_stream(stream)
+
+    @classmethod
+    def from_workload(cls, w, seed_walkers=True, **overrides):
+        kw = dict(q=w.q, storage=w.storage, wall_mask=w.wall_mask, body_force=w.body_force,
+                  force_period=w.force_period, rho0=w.rho0, init_velocity=w.init_velocity,
+                  sort_interval=w.sort_interval, moment_interval=w.moment_interval)
+        kw.update(overrides)
+        s = cls(w.dims, w.tau, w.D, w.seed, **kw)
+        if w.metaballs is not None and w.metaballs.n_particles > 0:
+            s.set_metaballs(w.metaballs)
+        if seed_walkers and w.n_walkers:
+            if w.walker_positions is not None:
+                s.set_walkers(w.walker_positions)
+            else:
+                s.seed_walkers(w.n_walkers, *w.walker_box)
+        return s
+
+    # ---- plumbing ----
+    def _check(self, st):
+        if st < 0:
+            raise RwmiError(st, self._L.rwmi_last_error(self._h).decode(errors="replace"))
+        return st
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self._L.rwmi_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_stream(self, stream):
+        handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        self._check(self._L.rwmi_set_stream(self._h, C.c_void_p(handle)))
+
+    # ---- setup ----
+    def set_metaballs(self, mb):
+        keep = dict(
+            coff=np.ascontiguousarray(mb.center_offsets, np.int32),
+            cb=np.ascontiguousarray(mb.centers_body, np.float32).reshape(-1),
+            k=np.ascontiguousarray(mb.k, np.float32),
+            org=np.ascontiguousarray(mb.origin, np.float64).reshape(-1),
+            amp=np.ascontiguousarray(mb.amplitude, np.float64).reshape(-1),
+            per=np.ascontiguousarray(mb.period, np.float64),
+            pha=np.ascontiguousarray(mb.phase, np.float64),
+            omg=np.ascontiguousarray(mb.omega, np.float64).reshape(-1))
+        P = len(keep["coff"]) - 1
+        self._check(self._L.rwmi_set_metaballs(self._h, P, _ptr(keep["coff"]), _ptr(keep["cb"]), _ptr(keep["k"]),
+                                               _ptr(keep["org"]), _ptr(keep["amp"]), _ptr(keep["per"]),
+                                               _ptr(keep["pha"]), _ptr(keep["omg"])))
+        self.n_particles = P
+
+    def seed_walkers(self, n, lo, hi):
+        st = self._check(self._L.rwmi_seed_walkers(self._h, int(n), _d3(lo), _d3(hi)))
+        self.n_walkers = int(n)
+        if st == RWMI_W_SEED:
+            import warnings
+            warnings.warn(self._L.rwmi_last_error(self._h).decode(), RwmiWarning)
+        return st
+
+    def set_walkers(self, pos):
+        if hasattr(pos, "data_ptr"):
+            n = pos.numel() // 3
+            self._check(self._L.rwmi_set_walkers(self._h, n, _ptr(pos)))
+        else:
+            pos = np.ascontiguousarray(pos, np.float32).reshape(-1, 3)
+            n = len(pos)
+            self._check(self._L.rwmi_set_walkers(self._h, n, _ptr(pos)))
+        self.n_walkers = int(n)
+
+    # ---- stepping ----
+    def step(self, n=1):
+        self._check(self._L.rwmi_step(self._h, int(n)))
+
+    PHASES = ("raster", "lbm", "pose_bricks", "walkers", "sort_bin", "moments")
+
+    def step_timed(self, n=1) -> dict:
+        """n eager steps with CUDA events around each phase; GPU milliseconds per phase (summed)."""
+        out = np.zeros(len(self.PHASES))
+        self._check(self._L.rwmi_step_timed(self._h, int(n), _ptr(out)))
+        return dict(zip(self.PHASES, out.tolist()))
+
+    def sync(self) -> int:
+        return self._check(self._L.rwmi_sync(self._h))
+
+    @property
+    def t(self) -> int:
+        v = C.c_int64()
+        self._check(self._L.rwmi_time(self._h, C.byref(v)))
+        return int(v.value)
+
+    @property
+    def launch_count(self) -> int:
+        return int(self._L.rwmi_launch_count(self._h))
+
+    # ---- outputs ----
+    def _out(self, out, shape, dtype):
+        if out is None:
+            out = np.zeros(shape, dtype)
+        return out
+
+    def concentration(self, out=None):
+        out = self._out(out, self.n_cells, np.uint32)
+        self._check(self._L.rwmi_concentration(self._h, _ptr(out)))
+        return out
+
+    def walker_moments(self, out=None):
+        out = self._out(out, 13, np.float64)
+        self._check(self._L.rwmi_walker_moments(self._h, _ptr(out)))
+        return out
+
+    def moment_series(self, max_rows=65536):
+        out = np.zeros((max_rows, 14))
+        n = C.c_int32()
+        self._check(self._L.rwmi_moment_series(self._h, _ptr(out), max_rows, C.byref(n)))
+        return out[: n.value]
+
+    def velocity(self, out=None):
+        out = self._out(out, (self.n_cells, 3), np.float32)
+        self._check(self._L.rwmi_velocity(self._h, _ptr(out)))
+        return out
+
+    def density(self, out=None):
+        out = self._out(out, self.n_cells, np.float32)
+        self._check(self._L.rwmi_density(self._h, _ptr(out)))
+        return out
+
+    def populations(self, out=None):
+        out = self._out(out, (self.q, self.n_cells), np.float64)
+        self._check(self._L.rwmi_populations(self._h, _ptr(out)))
+        return out
+
+    def lattice(self):
+        e = np.zeros((self.q, 3), np.int32)
+        w = np.zeros(self.q)
+        q = C.c_int32()
+        self._check(self._L.rwmi_lattice(self._h, _ptr(e), _ptr(w), C.byref(q)))
+        return e, w
+
+    def solid(self):
+        cnt = np.zeros(self.n_cells, np.int32)
+        own = np.zeros(self.n_cells, np.int32)
+        self._check(self._L.rwmi_solid(self._h, _ptr(cnt), _ptr(own)))
+        return cnt, own
+
+    def mass_momentum(self):
+        out = np.zeros(4)
+        self._check(self._L.rwmi_mass_momentum(self._h, _ptr(out)))
+        return out
+
+    def particle_forces(self):
+        out = np.zeros((max(self.n_particles, 1), 6))
+        self._check(self._L.rwmi_particle_forces(self._h, _ptr(out)))
+        return out[: self.n_particles]
+
+    def walkers(self, with_x0=True):
+        """Returns (positions [N,3] float32, ids [N] int64, start positions [N,3] or None) in the
+        library's current (cell-sorted) order."""
+        raw = np.zeros((self.n_walkers, 4), np.float32)
+        x0 = np.zeros((self.n_walkers, 3), np.float32) if with_x0 else None
+        self._check(self._L.rwmi_walkers(self._h, _ptr(raw), _ptr(x0) if with_x0 else None))
+        ids = raw[:, 3].view(np.uint32).astype(np.int64)
+        return raw[:, :3].copy(), ids, x0
+
+    def walkers_by_id(self):
+        pos, ids, x0 = self.walkers()
+        order = np.argsort(ids)
+        return pos[order], x0[order]
+
+    def counters(self) -> dict:
+        out = np.zeros(8, np.int64)
+        self._check(self._L.rwmi_counters(self._h, _ptr(out)))
+        keys = ["type_I", "type_II", "type_III", "type_IV", "bisect_fail", "refill_fail", "wall_fail",
+                "seed_fail"]
+        return dict(zip(keys, (int(v) for v in out)))
+
+    def save(self, path):
+        self._check(self._L.rwmi_save(self._h, os.fsencode(path)))
+
+    def load(self, path):
+        self._check(self._L.rwmi_load(self._h, os.fsencode(path)))

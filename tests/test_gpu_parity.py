@@ -1,0 +1,335 @@
+"""GPU (librwmi.so, sm_103a) against the FP64 oracle on identical seeded inputs.
+
+Tolerances, derived from binary32 arithmetic (unit roundoff 6e-8):
+  - solid counts/owners, seeded positions, walker counts and cell binning: bit-exact (both sides
+    decide in binary32 with one fixed operation order, or do pure integer work);
+  - one step of the LBM from identical populations: |f_gpu - f_oracle| <= 2e-7 max|f| (a few
+    roundings of O(f) terms);
+  - velocity fields after many steps (shifted FP32 storage): relative L2 error <= 1e-5;
+  - one walker step from identical inputs: |dx| <= 2e-5 (binary32 position of O(100) magnitude
+    plus float transcendental error), and at most 1e-3 of walkers on a different branch
+    (a surface test within ~1e-6 of f = 1 can flip);
+  - whole trajectories: walkers in a different cell than the oracle <= 1e-3 N.
+"""
+import os
+import tempfile
+
+import numpy as np
+import pytest
+
+from oracle.oracle import Oracle, lattice
+from paper_2308_05007_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2308_05007_gb300 import rwmi
+    rwmi.load()   # raises if the library is missing: no fallback
+    yield
+
+
+def Sim():
+    from paper_2308_05007_gb300.rwmi import Simulation
+    return Simulation
+
+
+def _perm(sim, q):
+    """Index map: oracle direction i <- library direction perm[i] (matched by velocity vector)."""
+    eg, wg = sim.lattice()
+    eo, wo = lattice(q)
+    perm = np.array([int(np.where((eg == eo[i]).all(1))[0][0]) for i in range(q)])
+    assert np.allclose(wg[perm], wo)
+    return perm
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-300))
+
+
+# ------------------------------------------------------------------------------- solid fraction
+@pytest.mark.parametrize("wl", ["ragged", "ragged_periodic", "parity_single", "oscillator_64"])
+def test_solid_fraction_bit_exact(wl):
+    if wl == "ragged":
+        w = I.ragged()
+    elif wl == "ragged_periodic":
+        w = I.ragged(dims=(33, 29, 24), walls=0, n_particles=4, seed=11)
+    elif wl == "parity_single":
+        w = I.parity_single()
+    else:
+        w = I.oscillator(n=64, n_particles=4, n_walkers=1000)
+    sim = Sim().from_workload(w, seed_walkers=False)
+    ora = Oracle.from_workload(w, seed_walkers=False)
+    for t in (0, 3, 7):
+        if t:
+            sim.step(t - sim.t)
+            ora.step_fluid(t - ora.t)
+        cg, og = sim.solid()
+        co, oo = ora.solid(t)
+        assert np.array_equal(cg, co), (t, np.flatnonzero(cg != co)[:10])
+        assert np.array_equal(og, oo)
+        assert cg.max() == 64
+
+
+# ------------------------------------------------------------------------------- seeding
+@pytest.mark.parametrize("wl", ["parity_single", "ragged"])
+def test_seeding_bit_exact(wl):
+    w = I.parity_single() if wl == "parity_single" else I.ragged(n_walkers=5000)
+    sim = Sim().from_workload(w)
+    ora = Oracle.from_workload(w)
+    xg, x0g = sim.walkers_by_id()
+    xo, _ = ora.walkers()
+    assert np.array_equal(xg.astype(np.float64), xo)
+    assert np.array_equal(xg, x0g)
+
+
+# ------------------------------------------------------------------------------- one LBM step
+@pytest.mark.parametrize("q,storage,walls", [(15, 1, 4), (19, 1, 4), (15, 0, 0), (19, 0, 2), (15, 1, 5)])
+def test_one_lbm_step_from_identical_populations(q, storage, walls):
+    w = I.ragged(q=q, storage=storage, walls=walls, seed=3 + walls)
+    sim = Sim().from_workload(w, seed_walkers=False)
+    ora = Oracle.from_workload(w, seed_walkers=False)
+    perm = _perm(sim, q)
+    sim.step(6)
+    f_prev = sim.populations()[perm]
+    t = sim.t
+    sim.step(1)
+    f_next = sim.populations()[perm]
+    u_g = sim.velocity()
+    ora.set_populations(f_prev)
+    ora.set_time(t)
+    cells = np.arange(ora.n_cells)
+    fo, uo, _ = ora.lbm_cells(cells)
+    assert np.abs(f_next - fo).max() <= 2e-7 * np.abs(fo).max()
+    assert np.abs(u_g - uo).max() <= 1e-7 * max(np.abs(uo).max(), 1e-6) + 1e-9
+
+
+# ------------------------------------------------------------------------------- trajectories
+@pytest.mark.parametrize("q", [15, 19])
+def test_parity_single_full_length(q):
+    """The plain-method case (32^3 periodic, tau 0.8, F = 1e-6 x, one k = 36 sphere, 1e4
+    walkers, D = 0.01, 500 steps, seed 0) against the oracle."""
+    w = I.parity_single(q=q)
+    sim = Sim().from_workload(w)
+    ora = Oracle.from_workload(w)
+    sim.step(w.steps)
+    assert sim.sync() >= 0
+    ora.step(w.steps)
+    assert _rel(sim.velocity(), ora.velocity()) <= 1e-5
+    mg = sim.mass_momentum()
+    mo = ora.mass_momentum()
+    assert mg[0] == pytest.approx(mo[0], rel=1e-7)
+    assert np.allclose(mg[1:], mo[1:], rtol=1e-4, atol=1e-9)
+    xg, _ = sim.walkers_by_id()
+    xo, _ = ora.walkers()
+    cg = ora.bin_positions(xg)
+    co = ora.bin_positions(xo.astype(np.float32))
+    assert (cg != co).sum() <= 1e-3 * w.n_walkers
+    close = np.abs(xg - xo).max(1) < 1e-3
+    assert close.mean() >= 1 - 1e-3
+    assert int(sim.concentration().sum()) == w.n_walkers
+    assert np.array_equal(np.sort(sim.concentration()), np.sort(ora.concentration())) or \
+        np.abs(sim.concentration().astype(int) - ora.concentration().astype(int)).sum() <= 2 * (cg != co).sum()
+    m_g, m_o = sim.walker_moments(), ora.moments()
+    assert m_g[0] == m_o[0]
+    assert np.allclose(m_g[1:], m_o[1:], rtol=1e-4, atol=1e-6)
+    fg, fo = sim.particle_forces(), ora.forces()
+    assert np.allclose(fg[:, :3], fo[:, :3], rtol=1e-3, atol=1e-3 * np.abs(fo[:, :3]).max())
+
+
+@pytest.mark.parametrize("q,storage", [(15, 1), (19, 1), (19, 0)])
+def test_ragged_moving_particles_trajectory(q, storage):
+    w = I.ragged(q=q, storage=storage, n_walkers=4000)
+    sim = Sim().from_workload(w)
+    ora = Oracle.from_workload(w)
+    sim.step(w.steps)
+    ora.step(w.steps)
+    tol = 1e-5 if storage == 1 else 2e-4   # unshifted FP32 loses ~4 digits of u ~ 1e-4 against f ~ 0.1
+    assert _rel(sim.velocity(), ora.velocity()) <= tol
+    assert sim.mass_momentum()[0] == pytest.approx(ora.mass_momentum()[0], rel=1e-7)
+    xg, _ = sim.walkers_by_id()
+    xo, _ = ora.walkers()
+    diff = (ora.bin_positions(xg) != ora.bin_positions(xo.astype(np.float32))).sum()
+    assert diff <= max(2, 1e-3 * w.n_walkers)
+    cg = sim.counters()
+    co = ora.counters()
+    for k in ("type_II", "type_III", "type_IV"):
+        assert abs(cg[k] - co[k]) <= max(3, 0.02 * co[k]), (k, cg[k], co[k])
+    assert cg["bisect_fail"] == 0 and cg["refill_fail"] == 0 and cg["wall_fail"] == 0
+    assert int(sim.concentration().sum()) == w.n_walkers
+
+
+# ------------------------------------------------------------------------------- one walker step
+@pytest.mark.parametrize("wl", ["ragged", "parity_single"])
+def test_one_walker_step_from_identical_inputs(wl):
+    w = I.ragged(n_walkers=6000) if wl == "ragged" else I.parity_single()
+    sim = Sim().from_workload(w)
+    ora = Oracle.from_workload(w, seed_walkers=False)
+    sim.step(5)
+    x_prev, _ = sim.walkers_by_id()
+    t = sim.t
+    sim.step(1)
+    x_next, _ = sim.walkers_by_id()
+    ora.set_velocity(sim.velocity().astype(np.float64))
+    ora.set_time(t)
+    xo = ora.walkers_advance(x_prev.astype(np.float64), np.arange(len(x_prev), dtype=np.uint32))
+    d = np.abs(x_next - xo).max(1)
+    assert (d > 2e-5).mean() <= 1e-3, np.sort(d)[-5:]
+
+
+# ------------------------------------------------------------------------------- invariants
+def test_binning_is_exact_for_identical_positions():
+    w = I.ragged(n_walkers=20000)
+    sim = Sim().from_workload(w)
+    sim.step(9)
+    x, ids, _ = sim.walkers()
+    ora = Oracle.from_workload(w, seed_walkers=False)
+    cells = ora.bin_positions(x)
+    expect = np.bincount(cells, minlength=ora.n_cells).astype(np.uint32)
+    assert np.array_equal(sim.concentration(), expect)
+    assert np.array_equal(np.sort(ids), np.arange(w.n_walkers))
+
+
+def test_sort_and_graphs_do_not_change_results():
+    w = I.ragged(n_walkers=5000)
+    runs = []
+    for sort_interval, graphs in ((0, False), (4, True), (3, True), (2, False)):
+        sim = Sim().from_workload(w, sort_interval=sort_interval, use_graphs=graphs, moment_interval=4)
+        sim.step(24)
+        x, _ = sim.walkers_by_id()
+        runs.append((x, sim.populations(), sim.moment_series()))
+    for x, f, ser in runs[1:]:
+        assert np.array_equal(x, runs[0][0])
+        assert np.array_equal(f, runs[0][1])
+        assert len(ser) == 6 and np.array_equal(ser[:, 0], [4, 8, 12, 16, 20, 24])
+        assert np.allclose(ser[:, 1:], runs[0][2][:, 1:], rtol=1e-12, atol=1e-14)
+
+
+def test_checkpoint_restart_is_bit_identical():
+    w = I.ragged(n_walkers=3000)
+    a = Sim().from_workload(w)
+    a.step(20)
+    xa, _ = a.walkers_by_id()
+    fa = a.populations()
+    b = Sim().from_workload(w)
+    b.step(10)
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "ck.bin")
+        b.save(path)
+        c = Sim().from_workload(w, seed_walkers=False)
+        c.load(path)
+    assert c.t == 10
+    c.step(10)
+    xc, _ = c.walkers_by_id()
+    assert np.array_equal(xc, xa)
+    assert np.array_equal(c.populations(), fa)
+
+
+def test_mass_conservation_and_walker_count_long_run():
+    w = I.ragged(n_walkers=10000)
+    sim = Sim().from_workload(w)
+    N = float(np.prod(w.dims))
+    for _ in range(5):
+        sim.step(40)
+        assert sim.mass_momentum()[0] == pytest.approx(N, rel=2e-6)
+        assert int(sim.concentration().sum()) == w.n_walkers
+    assert sim.sync() >= 0
+
+
+def test_momentum_exchange_balance_gpu():
+    tau = 0.75
+    w = I.ragged(dims=(30, 26, 22), walls=0, seed=12)
+    w = I.with_(w, force_period=0.0, body_force=(2e-5, -1e-5, 5e-6), tau=tau)
+    sim = Sim().from_workload(w, seed_walkers=False)
+    sim.step(3)
+    for _ in range(4):
+        cnt, _ = sim.solid()
+        eps = cnt / 64.0
+        B = eps * (tau - 0.5) / ((1 - eps) + (tau - 0.5))
+        sim.step(1)
+        p_t = sim.mass_momentum()[1:]
+        Fp = sim.particle_forces()[:, :3].sum(0)
+        sim.step(1)
+        p_t1 = sim.mass_momentum()[1:]
+        expect = (1 - B).sum() * np.array(w.body_force) - Fp
+        assert np.allclose(p_t1 - p_t, expect, rtol=2e-3, atol=2e-3 * np.abs(expect).max())
+
+
+def test_plane_poiseuille_gpu():
+    H, F = 16, 1e-6
+    tau = 0.5 + np.sqrt(3 / 16)
+    nu = (tau - 0.5) / 3
+    sim = Sim()((2, 2, H), tau, 0.0, q=19, wall_mask=4, body_force=(F, 0, 0))
+    sim.step(int(30 * H * H / nu) // 2 * 2)
+    u = sim.velocity()[:, 0].reshape(H, 2, 2)[:, 0, 0]
+    z = np.arange(H) + 0.5
+    exact = F * z * (H - z) / (2 * nu)
+    assert np.abs(u - exact).max() <= 2e-5 * exact.max()
+
+
+def test_edge_cases():
+    # zero walkers, zero steps, a 1x1xN column, dims not multiple of the brick size
+    sim = Sim()((1, 1, 9), 0.8, 0.01, q=15, wall_mask=4, body_force=(1e-5, 0, 0))
+    sim.step(0)
+    sim.step(5)
+    assert sim.t == 5 and sim.concentration().sum() == 0
+    assert sim.walker_moments()[0] == 0
+    # a particle straddling the periodic corner of the box
+    mb = I.single_sphere((0.3, 0.2, 0.1), 9.0)
+    s2 = Sim()((17, 13, 11), 0.8, 0.02, q=19)
+    s2.set_metaballs(mb)
+    o2 = Oracle((17, 13, 11), q=19, tau=0.8, D=0.02)
+    o2.set_metaballs(mb)
+    assert np.array_equal(s2.solid()[0], o2.solid(0)[0])
+    # invalid arguments are rejected without side effects
+    from paper_2308_05007_gb300.rwmi import RwmiError
+    with pytest.raises(RwmiError):
+        s2.seed_walkers(10, (0, 0, 0), (18, 13, 11))
+    with pytest.raises(RwmiError):
+        Sim()((0, 4, 4), 0.8, 0.01)
+    with pytest.raises(RwmiError):
+        Sim()((4, 4, 4), 0.5, 0.01)
+
+
+# ------------------------------------------------------------------------------- full size, sampled
+def test_oscillator_full_size_sampled():
+    """The 256^3 oscillator workload in the launch configuration the benchmark times (D3Q15,
+    shifted FP32, 64 particles, 1e7 walkers): sampled cells and walkers of one step against the
+    oracle, computed one by one from the GPU's own state; counts and conservation in full."""
+    w = I.oscillator()
+    sim = Sim().from_workload(w, sort_interval=16)
+    sim.step(16)
+    t = sim.t
+    perm = _perm(sim, w.q)
+    f_prev = sim.populations()[perm]
+    x_prev, _ = sim.walkers_by_id()
+    sim.step(1)
+    assert sim.sync() >= 0
+    f_next = sim.populations()
+    u = sim.velocity()
+    x_next, _ = sim.walkers_by_id()
+    ora = Oracle.from_workload(w, seed_walkers=False)
+    cg, og = sim.solid()   # solid of time t + 1 on the GPU
+    ora.set_populations(f_prev)
+    del f_prev
+    ora.set_time(t)
+    rng = np.random.default_rng(0)
+    solid_cells = np.flatnonzero(cg > 0)
+    cells = np.concatenate([rng.integers(0, ora.n_cells, 20000), rng.choice(solid_cells, 5000)])
+    fo, uo, _ = ora.lbm_cells(cells)
+    fg = f_next[perm][:, cells]
+    assert np.abs(fg - fo).max() <= 2e-7 * np.abs(fo).max()
+    assert np.abs(u[cells] - uo).max() <= 1e-7 * np.abs(uo).max() + 1e-10
+    ora.set_velocity(u.astype(np.float64))
+    ids = rng.choice(w.n_walkers, 20000, replace=False).astype(np.uint32)
+    xo = ora.walkers_advance(x_prev[ids].astype(np.float64), ids)
+    d = np.abs(x_next[ids] - xo).max(1)
+    assert (d > 2e-5).mean() <= 1e-3
+    co, oo = ora.solid(t + 1)
+    assert np.array_equal(cg, co) and np.array_equal(og, oo)
+    assert int(sim.concentration().sum()) == w.n_walkers
+    assert sim.mass_momentum()[0] == pytest.approx(float(ora.n_cells), rel=1e-6)
