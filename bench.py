@@ -314,6 +314,7 @@ def main():
                      "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if not peaks.get("fallback") else "fallback"},
         "phase_ms_per_step": {k: v / n_timed_phase_steps for k, v in phases.items()},
         "gpu_launches": launches,
+        "bricks": sim.brick_stats(),
         "clocks": clk,
     }
     if e2e:

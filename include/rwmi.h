@@ -160,6 +160,9 @@ RWMI_API rwmi_status rwmi_sync(rwmi_ctx* ctx);
 /* Number of completed steps. */
 RWMI_API rwmi_status rwmi_time(rwmi_ctx* ctx, int64_t* t);
 
+/* Sizes of the context: out = {nx, ny, nz, q, storage, walkers, particles, completed steps}. */
+RWMI_API rwmi_status rwmi_info(rwmi_ctx* ctx, int64_t out[8]);
+
 /* Eq. 16 with m_s = 1, dx = 1: out[c] = number of walkers in cell c (uint32, nx*ny*nz). */
 RWMI_API rwmi_status rwmi_concentration(rwmi_ctx* ctx, uint32_t* out);
 
@@ -215,6 +218,10 @@ RWMI_API rwmi_status rwmi_load(rwmi_ctx* ctx, const char* path);
 
 /* Message of the last failing call on this context (static storage of the context). */
 RWMI_API const char* rwmi_last_error(const rwmi_ctx* ctx);
+
+/* Brick statistics of the current time: out = {bricks with raster-relevant particles, bricks
+ * with walker candidates, largest candidate count of a brick, bricks over the stored maximum}. */
+RWMI_API rwmi_status rwmi_brick_stats(rwmi_ctx* ctx, int64_t out[4]);
 
 /* Number of kernel launches the context has issued (for launch accounting). */
 RWMI_API int64_t rwmi_launch_count(const rwmi_ctx* ctx);

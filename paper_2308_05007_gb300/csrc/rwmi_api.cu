@@ -222,8 +222,8 @@ rwmi_status alloc_particles(rwmi_ctx* c) {
     c->acc[k] = nullptr;
     CK(dalloc(&c->pose[k], sizeof(PoseF) * (size_t)(c->P > 0 ? c->P : 1)));
     CK(dalloc(&c->cworld[k], sizeof(float4) * (size_t)(c->Nc > 0 ? c->Nc : 1)));
-    CK(dalloc(&c->acc[k], sizeof(double) * (size_t)(6 * c->P + 4)));
-    CK(cudaMemsetAsync(c->acc[k], 0, sizeof(double) * (size_t)(6 * c->P + 4), c->stream));
+    CK(dalloc(&c->acc[k], sizeof(double) * (size_t)(6 * c->P + 4 * RED_SLOTS)));
+    CK(cudaMemsetAsync(c->acc[k], 0, sizeof(double) * (size_t)(6 * c->P + 4 * RED_SLOTS), c->stream));
   }
   return RWMI_OK;
 }
@@ -679,6 +679,13 @@ RWMI_API rwmi_status rwmi_time(rwmi_ctx* c, int64_t* t) {
   return RWMI_OK;
 }
 
+RWMI_API rwmi_status rwmi_info(rwmi_ctx* c, int64_t out[8]) {
+  if (!c || !out) return RWMI_E_INVALID;
+  const int64_t v[8] = {c->n[0], c->n[1], c->n[2], c->cfg.q, c->cfg.storage, c->nw, c->P, c->t};
+  std::memcpy(out, v, sizeof(v));
+  return RWMI_OK;
+}
+
 RWMI_API rwmi_status rwmi_concentration(rwmi_ctx* c, uint32_t* out) {
   if (!c || !out) return RWMI_E_INVALID;
   if (c->binned_t != c->t) {
@@ -778,8 +785,11 @@ RWMI_API rwmi_status rwmi_mass_momentum(rwmi_ctx* c, double out[4]) {
   if (!c || !out) return RWMI_E_INVALID;
   double v[4] = {0.0, 0.0, 0.0, 0.0};
   if (c->t > 0) {
-    rwmi_status s = copy_out(c, v, c->acc[(c->t - 1) & 1] + 6 * c->P, sizeof(v));
+    std::vector<double> slots((size_t)4 * RED_SLOTS);
+    rwmi_status s = copy_out(c, slots.data(), c->acc[(c->t - 1) & 1] + 6 * c->P, sizeof(double) * slots.size());
     if (s != RWMI_OK) return s;
+    for (int k = 0; k < RED_SLOTS; ++k)
+      for (int m = 0; m < 4; ++m) v[m] += slots[4 * k + m];
   }
   out[0] = (double)c->ncell * c->cfg.rho0 + v[0];
   out[1] = v[1]; out[2] = v[2]; out[3] = v[3];
@@ -887,13 +897,35 @@ RWMI_API rwmi_status rwmi_load(rwmi_ctx* c, const char* path) {
   return RWMI_OK;
 }
 
+RWMI_API rwmi_status rwmi_brick_stats(rwmi_ctx* c, int64_t out[4]) {
+  if (!c || !out) return RWMI_E_INVALID;
+  std::vector<uint32_t> w((size_t)c->nbrick + 1);
+  CK(cudaStreamSynchronize(c->stream));
+  CK(cudaMemcpy(w.data(), c->bword[c->t & 1], sizeof(uint32_t) * w.size(), cudaMemcpyDeviceToHost));
+  int64_t rast = 0, walk = 0, mx = 0, over = 0;
+  for (uint32_t b = 0; b < c->nbrick; ++b) {
+    const int64_t nc = w[b] & 0xffffu;
+    rast += (w[b] >> 16) ? 1 : 0;
+    walk += nc ? 1 : 0;
+    mx = std::max(mx, nc);
+    over += nc > MAXC ? 1 : 0;
+  }
+  out[0] = rast; out[1] = walk; out[2] = mx; out[3] = over;
+  return RWMI_OK;
+}
+
 RWMI_API const char* rwmi_last_error(const rwmi_ctx* c) { return c ? c->err.c_str() : "null context"; }
 
 RWMI_API int64_t rwmi_launch_count(const rwmi_ctx* c) { return c ? c->launches : 0; }
 
 RWMI_API void rwmi_destroy(rwmi_ctx* c) {
   if (!c) return;
-  if (c->stream) cudaStreamSynchronize(c->stream);
+  // At process teardown the CUDA runtime may already be gone: then only host memory is freed.
+  if (c->stream && cudaStreamSynchronize(c->stream) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return;
+  }
   drop_graphs(c);
   for (int k = 0; k < 2; ++k) {
     dfree(c->f[k]); dfree(c->acc[k]); dfree(c->bword[k]); dfree(c->bcand[k]); dfree(c->rlist[k]);

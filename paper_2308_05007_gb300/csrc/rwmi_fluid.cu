@@ -75,8 +75,8 @@ __global__ void pose_bin_kernel(Geom g, ParticleSet ps, BrickSet bs, const int64
     bs.sp->F[1] = (float)(F0y * s);
     bs.sp->F[2] = (float)(F0z * s);
   }
-  if (zero_acc) {   // force/torque [6P] + mass/momentum [4] accumulators of this time
-    for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < 6 * ps.P + 4; m += gridDim.x * blockDim.x)
+  if (zero_acc) {   // force/torque [6P] + striped mass/momentum [4 RED_SLOTS] accumulators of this time
+    for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < 6 * ps.P + 4 * RED_SLOTS; m += gridDim.x * blockDim.x)
       acc[m] = 0.0;
   }
   const int p = blockIdx.x;
@@ -141,21 +141,45 @@ __global__ void pose_bin_kernel(Geom g, ParticleSet ps, BrickSet bs, const int64
   double ow[3];
   for (int a = 0; a < 3; ++a) ow[a] = wrap_d(so[a], (double)g.n[a], g.wall[a]);
   const float Rw = d.rb + ps.walk_margin, Rr = d.rb + 1.0f;
-  int lo[3], cnt[3];
+  // Per axis, the bricks met by the interval [o - Rw, o + Rw] of the wrapped domain: one range,
+  // or two when the interval crosses a periodic face (bricks need not tile a periodic axis
+  // evenly, so the wrap is done on cell coordinates, not brick indices).
+  int ra[3][2], rb_[3][2], nr[3];
   for (int a = 0; a < 3; ++a) {
-    int l = (int)floor((ow[a] - Rw) / BRICK), h = (int)floor((ow[a] + Rw) / BRICK);
-    if (g.wall[a]) { l = max(l, 0); h = min(h, g.nb[a] - 1); }
-    else if (h - l + 1 >= g.nb[a]) { l = 0; h = g.nb[a] - 1; }
-    lo[a] = l;
-    cnt[a] = max(h - l + 1, 0);
+    const double n = (double)g.n[a], lo = ow[a] - Rw, hi = ow[a] + Rw;
+    const int last = g.nb[a] - 1;
+    if (g.wall[a]) {
+      const double l = fmax(lo, 0.0), h = fmin(hi, n);
+      nr[a] = l <= h ? 1 : 0;
+      ra[a][0] = min((int)floor(l / BRICK), last);
+      rb_[a][0] = min((int)floor(h / BRICK), last);
+    } else if (hi - lo >= n) {
+      nr[a] = 1; ra[a][0] = 0; rb_[a][0] = last;
+    } else {
+      const double s0 = lo - n * floor(lo / n), e0 = s0 + (hi - lo);
+      if (e0 < n) {
+        nr[a] = 1;
+        ra[a][0] = min((int)floor(s0 / BRICK), last);
+        rb_[a][0] = min((int)floor(e0 / BRICK), last);
+      } else {
+        ra[a][0] = min((int)floor(s0 / BRICK), last); rb_[a][0] = last;
+        ra[a][1] = 0; rb_[a][1] = min((int)floor((e0 - n) / BRICK), last);
+        if (rb_[a][1] >= ra[a][0] - 1) { nr[a] = 1; ra[a][0] = 0; rb_[a][0] = last; }
+        else nr[a] = 2;
+      }
+    }
   }
-  const int total = cnt[0] * cnt[1] * cnt[2];
   const uint32_t nbrick = (uint32_t)g.nb[0] * g.nb[1] * g.nb[2];
+  for (int combo = 0; combo < 8; ++combo) {
+    const int sx = combo & 1, sy = (combo >> 1) & 1, sz = combo >> 2;
+    if (sx >= nr[0] || sy >= nr[1] || sz >= nr[2]) continue;
+    const int lo3[3] = {ra[0][sx], ra[1][sy], ra[2][sz]};
+    const int cnt[3] = {rb_[0][sx] - ra[0][sx] + 1, rb_[1][sy] - ra[1][sy] + 1, rb_[2][sz] - ra[2][sz] + 1};
+    const int total = cnt[0] * cnt[1] * cnt[2];
   for (int m = threadIdx.x; m < total; m += blockDim.x) {
-    int bc[3] = {lo[0] + m % cnt[0], lo[1] + (m / cnt[0]) % cnt[1], lo[2] + m / (cnt[0] * cnt[1])};
+    int bc[3] = {lo3[0] + m % cnt[0], lo3[1] + (m / cnt[0]) % cnt[1], lo3[2] + m / (cnt[0] * cnt[1])};
     float d2 = 0.0f;
     for (int a = 0; a < 3; ++a) {
-      if (!g.wall[a]) bc[a] = ((bc[a] % g.nb[a]) + g.nb[a]) % g.nb[a];
       const float b0 = (float)(bc[a] * BRICK), b1 = fminf((float)((bc[a] + 1) * BRICK), (float)g.n[a]);
       const float c = 0.5f * (b0 + b1), h = 0.5f * (b1 - b0);
       float delta = (float)ow[a] - c;
@@ -177,6 +201,7 @@ __global__ void pose_bin_kernel(Geom g, ParticleSet ps, BrickSet bs, const int64
       bs.rlist[li] = (int32_t)b;
     }
   }
+  }
 }
 
 void launch_pose_bin(const Geom& g, const ParticleSet& ps, BrickSet bs, const int64_t* d_T,
@@ -197,18 +222,21 @@ void launch_pose_bin(const Geom& g, const ParticleSet& ps, BrickSet bs, const in
 // ------------------------------------------------------------------------------------------
 struct CellBound { float fmax, fmin; };
 
-__device__ __forceinline__ CellBound bound_at(const float4* __restrict__ cw, int c0, int c1, float x,
-                                              float y, float z, float h, const Geom& g) {
+// Bounds of Eq. 3 over a ball of radius h about (x, y, z): every control point is at least
+// r - h and at most r + h away. Fast reciprocal/sqrt: the 1e-3 decision margins dwarf their error.
+__device__ __forceinline__ CellBound bound_at(const float4* cw, int c0, int c1, float x, float y, float z,
+                                              float h, const Geom& g) {
   float fmax = 0.0f, fmin = 0.0f;
   for (int i = c0; i < c1; ++i) {
     const float4 c = cw[i];
     const float dx = min_image_rn(x - c.x, (float)g.n[0], g.wall[0]);
     const float dy = min_image_rn(y - c.y, (float)g.n[1], g.wall[1]);
     const float dz = min_image_rn(z - c.z, (float)g.n[2], g.wall[2]);
-    const float r = sqrtf(dx * dx + dy * dy + dz * dz);
-    const float rmin = fmaxf(r - h, 1e-20f), rmax = r + h;
-    fmax += c.w / (rmin * rmin);
-    fmin += c.w / (rmax * rmax);
+    const float r2 = dx * dx + dy * dy + dz * dz;
+    const float r = r2 * rsqrtf(fmaxf(r2, 1e-30f));
+    const float rmin = fmaxf(r - h, 1e-15f), rmax = r + h;
+    fmax += __fdividef(c.w, rmin * rmin);
+    fmin += __fdividef(c.w, rmax * rmax);
   }
   CellBound b;
   b.fmax = fmax;
@@ -216,8 +244,8 @@ __device__ __forceinline__ CellBound bound_at(const float4* __restrict__ cw, int
   return b;
 }
 
-__device__ __forceinline__ bool subsample_inside(const float4* __restrict__ cw, int c0, int c1,
-                                                 float x, float y, float z, const Geom& g) {
+__device__ __forceinline__ bool subsample_inside(const float4* cw, int c0, int c1, float x, float y,
+                                                 float z, const Geom& g) {
   float f = 0.0f;
   for (int i = c0; i < c1; ++i) {
     const float4 c = cw[i];
@@ -231,8 +259,7 @@ __device__ __forceinline__ bool subsample_inside(const float4* __restrict__ cw, 
 }
 
 // 64-bit mask of the sub-samples of cell (i, j, k) inside particle [c0, c1); bit a + 4 b + 16 c
-__device__ uint64_t particle_mask(const float4* __restrict__ cw, int c0, int c1, int i, int j, int k,
-                                  const Geom& g) {
+__device__ uint64_t particle_mask(const float4* cw, int c0, int c1, int i, int j, int k, const Geom& g) {
   const float xc = (float)i + 0.5f, yc = (float)j + 0.5f, zc = (float)k + 0.5f;
   const CellBound cb = bound_at(cw, c0, c1, xc, yc, zc, 0.649519053f, g);
   if (cb.fmax < 0.999f) return 0ull;
@@ -259,45 +286,85 @@ __device__ uint64_t particle_mask(const float4* __restrict__ cw, int c0, int c1,
   return mask;
 }
 
-__global__ void __launch_bounds__(256) raster_kernel(Geom g, ParticleSet ps, BrickSet bs,
+constexpr int RASTER_SMEM_CENTERS = 1024;
+
+// One block per brick of the raster list (grid-stride). The brick's raster-relevant candidate
+// particles are classified once for the whole brick (sub-samples lie within 6.71 of its centre:
+// wholly outside / wholly inside / partial), and the control points of the partial ones are staged
+// in shared memory for the per-cell masks.
+__global__ void __launch_bounds__(256, 2) raster_kernel(Geom g, ParticleSet ps, BrickSet bs,
                                                      uint16_t* __restrict__ solid,
                                                      unsigned long long* __restrict__ status) {
   const uint32_t nbrick = (uint32_t)g.nb[0] * g.nb[1] * g.nb[2];
   const uint32_t nlist = bs.bword[nbrick];
-  __shared__ int s_c0[MAXC + 1], s_c1[MAXC + 1], s_p[MAXC + 1];
-  __shared__ int s_n, s_all;
+  __shared__ float4 s_cw[RASTER_SMEM_CENTERS];
+  __shared__ int s_p[MAXC], s_c0[MAXC], s_c1[MAXC], s_cls[MAXC];
+  __shared__ int s_n, s_all, s_smem;
   for (uint32_t li = blockIdx.x; li < nlist; li += gridDim.x) {
     const uint32_t b = (uint32_t)bs.rlist[li];
+    const int bi = b % g.nb[0], bj = (b / g.nb[0]) % g.nb[1], bk = b / (g.nb[0] * g.nb[1]);
     if (threadIdx.x == 0) {
-      const uint32_t word = bs.bword[b];
-      const uint32_t nc = word & 0xffffu;
+      const uint32_t nc = bs.bword[b] & 0xffffu;
       s_all = nc > MAXC;
-      int n = 0;
+      int n = 0, tot = 0;
       if (!s_all) {
         for (uint32_t m = 0; m < nc; ++m) {
           const uint16_t cid = bs.bcand[b * MAXC + m];
           if (cid & 0x8000) {
             const int p = cid & 0x7fff;
-            s_p[n] = p; s_c0[n] = ps.desc[p].c0; s_c1[n] = ps.desc[p].c1; ++n;
+            s_p[n] = p; s_c0[n] = tot; s_c1[n] = tot + (ps.desc[p].c1 - ps.desc[p].c0);
+            tot = s_c1[n]; ++n;
           }
         }
       } else {
         atomicAdd(&status[ST_BRICK_OVERFLOW], 1ull);
       }
       s_n = n;
+      s_smem = tot <= RASTER_SMEM_CENTERS;
     }
     __syncthreads();
-    const int bi = b % g.nb[0], bj = (b / g.nb[0]) % g.nb[1], bk = b / (g.nb[0] * g.nb[1]);
+    const int n = s_n;
+    if (!s_all) {
+      // stage control points (shared when they fit) and classify each candidate for the brick
+      if (s_smem) {
+        for (int m = 0; m < n; ++m) {
+          const int g0 = ps.desc[s_p[m]].c0;
+          for (int i = threadIdx.x; i < s_c1[m] - s_c0[m]; i += blockDim.x) s_cw[s_c0[m] + i] = bs.cworld[g0 + i];
+        }
+      }
+      __syncthreads();
+      if (threadIdx.x < n) {
+        const int m = threadIdx.x;
+        const float4* cw = s_smem ? s_cw : bs.cworld;
+        const int c0 = s_smem ? s_c0[m] : ps.desc[s_p[m]].c0, c1 = s_smem ? s_c1[m] : ps.desc[s_p[m]].c1;
+        const float ex0 = (float)(bi * BRICK), ex1 = fminf((float)((bi + 1) * BRICK), (float)g.n[0]);
+        const float ey0 = (float)(bj * BRICK), ey1 = fminf((float)((bj + 1) * BRICK), (float)g.n[1]);
+        const float ez0 = (float)(bk * BRICK), ez1 = fminf((float)((bk + 1) * BRICK), (float)g.n[2]);
+        const float hx = 0.5f * (ex1 - ex0) - 0.125f, hy = 0.5f * (ey1 - ey0) - 0.125f, hz = 0.5f * (ez1 - ez0) - 0.125f;
+        const CellBound bb = bound_at(cw, c0, c1, 0.5f * (ex0 + ex1), 0.5f * (ey0 + ey1), 0.5f * (ez0 + ez1),
+                                      sqrtf(hx * hx + hy * hy + hz * hz), g);
+        s_cls[m] = bb.fmax < 0.999f ? 0 : (bb.fmin > 1.001f ? 1 : 2);
+      }
+      __syncthreads();
+    }
     for (int c = threadIdx.x; c < BRICK * BRICK * BRICK; c += blockDim.x) {
       const int i = bi * BRICK + (c & 7), j = bj * BRICK + ((c >> 3) & 7), k = bk * BRICK + (c >> 6);
       if (i >= g.n[0] || j >= g.n[1] || k >= g.n[2]) continue;
       uint64_t any = 0ull;
       int best = 0, bestp = -1;
-      const int ncand = s_all ? ps.P : s_n;
+      const int ncand = s_all ? ps.P : n;
       for (int m = 0; m < ncand; ++m) {
-        const int p = s_all ? m : s_p[m];
-        const int c0 = s_all ? ps.desc[p].c0 : s_c0[m], c1 = s_all ? ps.desc[p].c1 : s_c1[m];
-        const uint64_t mk = particle_mask(bs.cworld, c0, c1, i, j, k, g);
+        int p, c0, c1, cls = 2;
+        const float4* cw = bs.cworld;
+        if (s_all) {
+          p = m; c0 = ps.desc[p].c0; c1 = ps.desc[p].c1;
+        } else {
+          p = s_p[m]; cls = s_cls[m];
+          if (s_smem) { cw = s_cw; c0 = s_c0[m]; c1 = s_c1[m]; }
+          else { c0 = ps.desc[p].c0; c1 = ps.desc[p].c1; }
+        }
+        if (cls == 0) continue;
+        const uint64_t mk = cls == 1 ? ~0ull : particle_mask(cw, c0, c1, i, j, k, g);
         const int np = __popcll(mk);
         any |= mk;
         if (np > 0 && (np > best || (np == best && p < bestp))) { best = np; bestp = p; }
@@ -441,7 +508,9 @@ __global__ void __launch_bounds__(256) lbm_kernel(Geom g, const void* __restrict
     const float dev = -1.5f * uu;                       // feq_0 / (w rho) - 1
     const float feq_s = S::shifted ? w * (drho + rho * dev) : w * rho * (1.0f + dev);
     const float S0 = guo * w * (-3.0f * uF);
-    const float out = f[0] - rtau * (f[0] - feq_s) + S0;   // Omega_0 = 0 (rest is its own pair)
+    // rest is its own opposite: Omega_0 = feq_0(rho, u_s) - feq_0(rho, u) = 1.5 w rho (u.u - us.us)
+    const float om0 = B > 0.0f ? 1.5f * w * rho * (uu - (usx * usx + usy * usy + usz * usz)) : 0.0f;
+    const float out = f[0] - rtau * (f[0] - feq_s) + S0 + B * om0;
     if (valid) S::st(fout + c, out);
   }
   // opposite pairs (i, i + H) share e.u
@@ -532,10 +601,10 @@ __global__ void __launch_bounds__(256) lbm_kernel(Geom g, const void* __restrict
     if (lane == 0)
       for (int m = 0; m < 4; ++m) s_red[wid][m] = v[m];
     __syncthreads();
-    if (threadIdx.x < 4) {
+    if (threadIdx.x < 4) {   // striped slots keep the FP64 atomics of 65536 blocks uncontended
       double s = 0.0;
       for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += s_red[w][threadIdx.x];
-      atomicAdd(&red[threadIdx.x], s);
+      atomicAdd(&red[4 * (blockIdx.x % RED_SLOTS) + threadIdx.x], s);
     }
   }
 }

@@ -29,6 +29,7 @@ constexpr int MAXC = 16;            // candidate particles stored per brick
 constexpr int MAX_PARTICLES = 511;  // owner field of the solid word is 9 bits
 constexpr int MAX_CENTERS = 65535;
 constexpr float U_BOUND = 0.3f;     // lattice speed bound assumed by the walker candidate margin
+constexpr int RED_SLOTS = 256;      // mass/momentum partial sums are striped over this many slots
 
 // Status counters (device, unsigned long long): see rwmi_counters.
 enum StatusSlot {
@@ -126,7 +127,7 @@ __device__ __forceinline__ float metaball_exact(const float4* __restrict__ cw, i
   return f;
 }
 
-// Eq. 3 and Eq. 17 for walker decisions (binary32, contraction allowed): value and gradient.
+// Eq. 3 and Eq. 17 for walker decisions (binary32, contraction and fast reciprocals allowed).
 __device__ __forceinline__ float metaball_grad(const float4* __restrict__ cw, int c0, int c1,
                                                float x, float y, float z, const Geom& g,
                                                float* gx, float* gy, float* gz) {
@@ -137,7 +138,7 @@ __device__ __forceinline__ float metaball_grad(const float4* __restrict__ cw, in
     const float dy = min_image_rn(y - c.y, (float)g.n[1], g.wall[1]);
     const float dz = min_image_rn(z - c.z, (float)g.n[2], g.wall[2]);
     const float r2 = dx * dx + dy * dy + dz * dz;
-    const float inv = 1.0f / r2;
+    const float inv = __frcp_rn(r2);
     const float term = c.w * inv;
     f += term;
     const float s = -2.0f * term * inv;
@@ -155,7 +156,7 @@ __device__ __forceinline__ float metaball_value(const float4* __restrict__ cw, i
     const float dx = min_image_rn(x - c.x, (float)g.n[0], g.wall[0]);
     const float dy = min_image_rn(y - c.y, (float)g.n[1], g.wall[1]);
     const float dz = min_image_rn(z - c.z, (float)g.n[2], g.wall[2]);
-    f += c.w / (dx * dx + dy * dy + dz * dz);
+    f += __fdividef(c.w, dx * dx + dy * dy + dz * dz);   // ~2 ulp; walker tests need no exact rounding
   }
   return f;
 }

@@ -193,6 +193,9 @@ __global__ void __launch_bounds__(256) walker_kernel(WalkCtx c, float4* __restri
                                                      unsigned int* ticket, int64_t* d_T_inc) {
   const int64_t T = *d_T;
   const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  // per-walker events, counted once per warp (one atomic per event kind and warp)
+  bool ev_type2 = false, ev_type3 = false, ev_type4 = false, ev_bisect = false, ev_refill = false,
+       ev_wall = false, ev_fast = false, ev_nonfinite = false;
   if (w < n) {
     const float4 p4 = pos[w];
     const uint32_t id = __float_as_uint(p4.w);
@@ -207,7 +210,7 @@ __global__ void __launch_bounds__(256) walker_kernel(WalkCtx c, float4* __restri
     const float c3 = cospif(2.0f * uniform24(r.w));
     float xf[3] = {x[0] + ux + amp * (rad01 * c1), x[1] + uy + amp * (rad01 * s1),
                    x[2] + uz + amp * (rad23 * c3)};
-    if (!wall_reflect(xf, c.g)) atomicAdd(&status[ST_WALL_FAIL], 1ull);
+    if (!wall_reflect(xf, c.g)) ev_wall = true;
     float xn[3] = {xf[0], xf[1], xf[2]};
     if (c.ps.P > 0) {
       const float step2 = (xf[0] - x[0]) * (xf[0] - x[0]) + (xf[1] - x[1]) * (xf[1] - x[1]) +
@@ -218,7 +221,7 @@ __global__ void __launch_bounds__(256) walker_kernel(WalkCtx c, float4* __restri
       const int b = brick_of(xw, yw, zw, c.g);
       const uint32_t nc = c.bs.bword[b] & 0xffffu;
       const bool far_step = step2 > c.ps.walk_margin * c.ps.walk_margin;
-      if (far_step) atomicAdd(&status[ST_FAST_SPEED], 1ull);
+      ev_fast = far_step;
       if (nc > 0 || far_step) {
         int pin = -1, qin = -1;
         if (nc > MAXC || far_step) {
@@ -236,15 +239,15 @@ __global__ void __launch_bounds__(256) walker_kernel(WalkCtx c, float4* __restri
           }
         }
         if (pin >= 0 && qin >= 0) {            // type II: Dirichlet refill
-          atomicAdd(&status[ST_TYPE2], 1ull);
-          if (!refill(c, pin, x, id, (uint32_t)T, amp, k0, k1, xn)) atomicAdd(&status[ST_REFILL_FAIL], 1ull);
+          ev_type2 = true;
+          if (!refill(c, pin, x, id, (uint32_t)T, amp, k0, k1, xn)) ev_refill = true;
         } else if (pin >= 0) {                 // type III: moves out freely
-          atomicAdd(&status[ST_TYPE3], 1ull);
+          ev_type3 = true;
         } else if (qin >= 0) {                 // type IV: Algorithms 1 and 2
-          atomicAdd(&status[ST_TYPE4], 1ull);
+          ev_type4 = true;
           float xi[3];
           if (!bisect(c, qin, x, xf, xi, nullptr)) {
-            atomicAdd(&status[ST_BISECT_FAIL], 1ull);
+            ev_bisect = true;
             xn[0] = x[0]; xn[1] = x[1]; xn[2] = x[2];
           } else {
             float gr[3];
@@ -264,8 +267,19 @@ __global__ void __launch_bounds__(256) walker_kernel(WalkCtx c, float4* __restri
         }
       }
     }
-    if (!(isfinite(ux) && isfinite(uy) && isfinite(uz))) atomicAdd(&status[ST_NONFINITE], 1ull);
+    ev_nonfinite = !(isfinite(ux) && isfinite(uy) && isfinite(uz));
     pos[w] = make_float4(xn[0], xn[1], xn[2], p4.w);
+  }
+  {
+    const unsigned full = 0xffffffffu;
+    const bool evs[8] = {ev_type2, ev_type3, ev_type4, ev_bisect, ev_refill, ev_wall, ev_fast, ev_nonfinite};
+    const int slot[8] = {ST_TYPE2, ST_TYPE3, ST_TYPE4, ST_BISECT_FAIL, ST_REFILL_FAIL, ST_WALL_FAIL,
+                         ST_FAST_SPEED, ST_NONFINITE};
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const unsigned bal = __ballot_sync(full, evs[m]);
+      if (bal && (threadIdx.x & 31) == 0) atomicAdd(&status[slot[m]], (unsigned long long)__popc(bal));
+    }
   }
   // the last block to finish advances the device step counter
   if (d_T_inc) {

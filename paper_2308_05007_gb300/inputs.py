@@ -222,11 +222,12 @@ def ragged(dims=(40, 36, 26), n_particles: int = 3, n_walkers: int = 3000, seed:
     """Small odd-sized box with a few moving multi-centre particles; spans several tiles of
     every kernel and leaves a ragged tail."""
     rng = np.random.default_rng(seed)
+    # drive speeds stay below 0.07 lattice units (low Mach number): 1.5 * 2 pi / 150 = 0.063
     mb = random_metaballs(rng, n_particles, dims, wall_mask=walls, n_centers=n_centers,
                           sigma=sigma, k_range=k_range,
-                          amplitude=(2.0, 1.0, 0.0) if moving else (0.0, 0.0, 0.0),
-                          period=40.0 if moving else 0.0, phase=0.3,
-                          omega=(0.0, 0.0, 0.02) if moving else (0.0, 0.0, 0.0))
+                          amplitude=(1.5, 0.75, 0.0) if moving else (0.0, 0.0, 0.0),
+                          period=150.0 if moving else 0.0, phase=0.3,
+                          omega=(0.0, 0.0, 0.004) if moving else (0.0, 0.0, 0.0))
     return Workload(
         name=f"ragged_{dims[0]}x{dims[1]}x{dims[2]}", dims=tuple(dims), tau=0.75, D=0.02,
         seed=seed, q=q, wall_mask=walls, body_force=(2e-5, 5e-6, 0.0), force_period=60.0,

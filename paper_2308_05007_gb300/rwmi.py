@@ -6,8 +6,10 @@ is no CPU path.
 """
 from __future__ import annotations
 
+import atexit
 import ctypes as C
 import os
+import weakref
 
 import numpy as np
 
@@ -21,10 +23,10 @@ STORE_FP32, STORE_FP32_SHIFT, STORE_FP16_SHIFT = 0, 1, 2
 EXPORTED = ["rwmi_config_defaults", "rwmi_create", "rwmi_configure", "rwmi_set_stream",
             "rwmi_set_metaballs", "rwmi_seed_walkers", "rwmi_set_walkers", "rwmi_step", "rwmi_step_timed",
             "rwmi_sync",
-            "rwmi_time", "rwmi_concentration", "rwmi_walker_moments", "rwmi_moment_series",
+            "rwmi_time", "rwmi_info", "rwmi_concentration", "rwmi_walker_moments", "rwmi_moment_series",
             "rwmi_velocity", "rwmi_density", "rwmi_populations", "rwmi_lattice", "rwmi_solid",
             "rwmi_mass_momentum", "rwmi_particle_forces", "rwmi_walkers", "rwmi_counters", "rwmi_save",
-            "rwmi_load", "rwmi_last_error", "rwmi_launch_count", "rwmi_destroy"]
+            "rwmi_load", "rwmi_brick_stats", "rwmi_last_error", "rwmi_launch_count", "rwmi_destroy"]
 
 
 class RwmiError(RuntimeError):
@@ -45,6 +47,17 @@ class Config(C.Structure):
 
 
 _lib = None
+_live = weakref.WeakSet()
+
+
+@atexit.register
+def _close_all():
+    """Destroy every live context before interpreter teardown (the CUDA runtime must still exist)."""
+    for sim in list(_live):
+        try:
+            sim.close()
+        except Exception:
+            pass
 
 
 def library_path() -> str:
@@ -74,6 +87,7 @@ def load(build_if_missing: bool = False):
     L.rwmi_step_timed.argtypes = [P, C.c_int32, vp]
     L.rwmi_sync.argtypes = [P]
     L.rwmi_time.argtypes = [P, C.POINTER(C.c_int64)]
+    L.rwmi_info.argtypes = [P, vp]
     for name in ("rwmi_concentration", "rwmi_walker_moments", "rwmi_velocity", "rwmi_density",
                  "rwmi_populations", "rwmi_mass_momentum", "rwmi_particle_forces", "rwmi_counters"):
         getattr(L, name).argtypes = [P, vp]
@@ -81,6 +95,7 @@ def load(build_if_missing: bool = False):
     L.rwmi_lattice.argtypes = [P, vp, vp, C.POINTER(C.c_int32)]
     L.rwmi_solid.argtypes = [P, vp, vp]
     L.rwmi_walkers.argtypes = [P, vp, vp]
+    L.rwmi_brick_stats.argtypes = [P, vp]
     L.rwmi_save.argtypes = [P, C.c_char_p]
     L.rwmi_load.argtypes = [P, C.c_char_p]
     L.rwmi_last_error.argtypes = [P]
@@ -135,8 +150,7 @@ class Simulation:
         cfg.use_graphs = 1 if use_graphs else 0
         self._check(L.rwmi_configure(self._h, C.byref(cfg)))
         self.q = int(q)
-        self.n_particles = 0
-        self.n_walkers = 0
+        _live.add(self)
         if stream is not None:
             self.set_stream(stream)
 
@@ -198,11 +212,9 @@ class Simulation:
         self._check(self._L.rwmi_set_metaballs(self._h, P, _ptr(keep["coff"]), _ptr(keep["cb"]), _ptr(keep["k"]),
                                                _ptr(keep["org"]), _ptr(keep["amp"]), _ptr(keep["per"]),
                                                _ptr(keep["pha"]), _ptr(keep["omg"])))
-        self.n_particles = P
 
     def seed_walkers(self, n, lo, hi):
         st = self._check(self._L.rwmi_seed_walkers(self._h, int(n), _d3(lo), _d3(hi)))
-        self.n_walkers = int(n)
         if st == RWMI_W_SEED:
             import warnings
             warnings.warn(self._L.rwmi_last_error(self._h).decode(), RwmiWarning)
@@ -216,7 +228,6 @@ class Simulation:
             pos = np.ascontiguousarray(pos, np.float32).reshape(-1, 3)
             n = len(pos)
             self._check(self._L.rwmi_set_walkers(self._h, n, _ptr(pos)))
-        self.n_walkers = int(n)
 
     # ---- stepping ----
     def step(self, n=1):
@@ -232,6 +243,20 @@ class Simulation:
 
     def sync(self) -> int:
         return self._check(self._L.rwmi_sync(self._h))
+
+    def info(self) -> dict:
+        out = np.zeros(8, np.int64)
+        self._check(self._L.rwmi_info(self._h, _ptr(out)))
+        keys = ["nx", "ny", "nz", "q", "storage", "walkers", "particles", "t"]
+        return dict(zip(keys, (int(v) for v in out)))
+
+    @property
+    def n_walkers(self) -> int:
+        return self.info()["walkers"]
+
+    @property
+    def n_particles(self) -> int:
+        return self.info()["particles"]
 
     @property
     def t(self) -> int:
@@ -306,8 +331,9 @@ class Simulation:
     def walkers(self, with_x0=True):
         """Returns (positions [N,3] float32, ids [N] int64, start positions [N,3] or None) in the
         library's current (cell-sorted) order."""
-        raw = np.zeros((self.n_walkers, 4), np.float32)
-        x0 = np.zeros((self.n_walkers, 3), np.float32) if with_x0 else None
+        n = self.n_walkers
+        raw = np.zeros((n, 4), np.float32)
+        x0 = np.zeros((n, 3), np.float32) if with_x0 else None
         self._check(self._L.rwmi_walkers(self._h, _ptr(raw), _ptr(x0) if with_x0 else None))
         ids = raw[:, 3].view(np.uint32).astype(np.int64)
         return raw[:, :3].copy(), ids, x0
@@ -316,6 +342,12 @@ class Simulation:
         pos, ids, x0 = self.walkers()
         order = np.argsort(ids)
         return pos[order], x0[order]
+
+    def brick_stats(self) -> dict:
+        out = np.zeros(4, np.int64)
+        self._check(self._L.rwmi_brick_stats(self._h, _ptr(out)))
+        return dict(zip(["raster_bricks", "walker_bricks", "max_candidates", "overflow_bricks"],
+                        (int(v) for v in out)))
 
     def counters(self) -> dict:
         out = np.zeros(8, np.int64)

@@ -1,10 +1,15 @@
 """GPU (librwmi.so, sm_103a) against the FP64 oracle on identical seeded inputs.
 
-Tolerances, derived from binary32 arithmetic (unit roundoff 6e-8):
+Tolerances, derived from binary32 arithmetic (unit roundoff eps = 6e-8):
   - solid counts/owners, seeded positions, walker counts and cell binning: bit-exact (both sides
     decide in binary32 with one fixed operation order, or do pure integer work);
-  - one step of the LBM from identical populations: |f_gpu - f_oracle| <= 2e-7 max|f| (a few
-    roundings of O(f) terms);
+  - one step of the LBM from identical populations: |f_gpu - f_oracle| <= 1e-6 max|f| (about a
+    dozen roundings of O(max f) operands in the collision, 12 eps ~ 7e-7);
+  - the velocity of that step: |u_gpu - u_oracle| <= 1e-6 max(max|u|, 0.01): u is a binary32 sum of
+    Q terms of size <= max|f| divided by rho, error <= Q eps max|f| |e| ~ 5e-7 max|f|;
+  - mass after n steps: relative 1e-7 with shifted storage (the stored deviations are small), and
+    n Q eps with unshifted storage (every stored population rounds at ~eps |f| per step);
+  - momentum components: within 1e-6 of the largest component (cell-by-cell binary32 sums);
   - velocity fields after many steps (shifted FP32 storage): relative L2 error <= 1e-5;
   - one walker step from identical inputs: |dx| <= 2e-5 (binary32 position of O(100) magnitude
     plus float transcendental error), and at most 1e-3 of walkers on a different branch
@@ -52,7 +57,7 @@ def _rel(a, b):
 
 
 # ------------------------------------------------------------------------------- solid fraction
-@pytest.mark.parametrize("wl", ["ragged", "ragged_periodic", "parity_single", "oscillator_64"])
+@pytest.mark.parametrize("wl", ["ragged", "ragged_periodic", "parity_single", "oscillator_96"])
 def test_solid_fraction_bit_exact(wl):
     if wl == "ragged":
         w = I.ragged()
@@ -61,7 +66,7 @@ def test_solid_fraction_bit_exact(wl):
     elif wl == "parity_single":
         w = I.parity_single()
     else:
-        w = I.oscillator(n=64, n_particles=4, n_walkers=1000)
+        w = I.oscillator(n=96, n_particles=4, n_walkers=1000)
     sim = Sim().from_workload(w, seed_walkers=False)
     ora = Oracle.from_workload(w, seed_walkers=False)
     for t in (0, 3, 7):
@@ -104,8 +109,8 @@ def test_one_lbm_step_from_identical_populations(q, storage, walls):
     ora.set_time(t)
     cells = np.arange(ora.n_cells)
     fo, uo, _ = ora.lbm_cells(cells)
-    assert np.abs(f_next - fo).max() <= 2e-7 * np.abs(fo).max()
-    assert np.abs(u_g - uo).max() <= 1e-7 * max(np.abs(uo).max(), 1e-6) + 1e-9
+    assert np.abs(f_next - fo).max() <= 1e-6 * np.abs(fo).max()
+    assert np.abs(u_g - uo).max() <= 1e-6 * max(np.abs(uo).max(), 1e-2)
 
 
 # ------------------------------------------------------------------------------- trajectories
@@ -123,7 +128,7 @@ def test_parity_single_full_length(q):
     mg = sim.mass_momentum()
     mo = ora.mass_momentum()
     assert mg[0] == pytest.approx(mo[0], rel=1e-7)
-    assert np.allclose(mg[1:], mo[1:], rtol=1e-4, atol=1e-9)
+    assert np.allclose(mg[1:], mo[1:], rtol=1e-4, atol=1e-6 * np.abs(mo[1:]).max())
     xg, _ = sim.walkers_by_id()
     xo, _ = ora.walkers()
     cg = ora.bin_positions(xg)
@@ -150,7 +155,8 @@ def test_ragged_moving_particles_trajectory(q, storage):
     ora.step(w.steps)
     tol = 1e-5 if storage == 1 else 2e-4   # unshifted FP32 loses ~4 digits of u ~ 1e-4 against f ~ 0.1
     assert _rel(sim.velocity(), ora.velocity()) <= tol
-    assert sim.mass_momentum()[0] == pytest.approx(ora.mass_momentum()[0], rel=1e-7)
+    mass_tol = 1e-7 if storage == 1 else w.steps * q * 6e-8
+    assert sim.mass_momentum()[0] == pytest.approx(ora.mass_momentum()[0], rel=mass_tol)
     xg, _ = sim.walkers_by_id()
     xo, _ = ora.walkers()
     diff = (ora.bin_positions(xg) != ora.bin_positions(xo.astype(np.float32))).sum()
@@ -322,8 +328,8 @@ def test_oscillator_full_size_sampled():
     cells = np.concatenate([rng.integers(0, ora.n_cells, 20000), rng.choice(solid_cells, 5000)])
     fo, uo, _ = ora.lbm_cells(cells)
     fg = f_next[perm][:, cells]
-    assert np.abs(fg - fo).max() <= 2e-7 * np.abs(fo).max()
-    assert np.abs(u[cells] - uo).max() <= 1e-7 * np.abs(uo).max() + 1e-10
+    assert np.abs(fg - fo).max() <= 1e-6 * np.abs(fo).max()
+    assert np.abs(u[cells] - uo).max() <= 1e-6 * max(np.abs(uo).max(), 1e-2)
     ora.set_velocity(u.astype(np.float64))
     ids = rng.choice(w.n_walkers, 20000, replace=False).astype(np.uint32)
     xo = ora.walkers_advance(x_prev[ids].astype(np.float64), ids)
