@@ -190,11 +190,13 @@ RWMI_API rwmi_status rwmi_populations(rwmi_ctx* ctx, double* out);
 /* The library's velocity set: e[3 i + a] (int32) and w[i] (double) for its q directions. */
 RWMI_API rwmi_status rwmi_lattice(rwmi_ctx* ctx, int32_t* e, double* w, int32_t* q);
 
-/* Solid fraction data of time t (the last rasterised step): count[c] (0..64 sub-samples
- * inside a particle, epsilon = count / 64) and owner[c] (particle index, -1 if none). */
+/* Solid fraction data of the current time t (rasterised by the last step or at set-up):
+ * count[c] (0..64 sub-samples inside a particle, epsilon = count / 64) and owner[c] (particle
+ * index, -1 if none). */
 RWMI_API rwmi_status rwmi_solid(rwmi_ctx* ctx, int32_t* count, int32_t* owner);
 
-/* {sum rho, sum_i f_i e_i (3 components)} over all cells at the last LBM step (FP64 sums). */
+/* {sum rho, sum_i f_i e_i (3 components)} over all cells at the last LBM step (FP64 sums;
+ * formed on the last step of every rwmi_step call). */
 RWMI_API rwmi_status rwmi_mass_momentum(rwmi_ctx* ctx, double out[4]);
 
 /* Hydrodynamic force and torque on each particle at the last LBM step, FP64:

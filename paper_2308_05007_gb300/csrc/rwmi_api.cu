@@ -57,7 +57,8 @@ struct rwmi_ctx {
   double* macc = nullptr;                // moment accumulators [12]
   double* series = nullptr;              // [SERIES_ROWS][SERIES_COLS]
   double* mrow = nullptr;                // on-demand moments row [SERIES_COLS]
-  // bricks per time parity
+  // bricks per time parity (the walker masks are rewritten by every raster)
+  uint64_t* wmask = nullptr;
   uint32_t* bword[2] = {nullptr, nullptr};
   uint16_t* bcand[2] = {nullptr, nullptr};
   int32_t* rlist[2] = {nullptr, nullptr};
@@ -167,6 +168,7 @@ ParticleSet particle_set(const rwmi_ctx* c) {
 
 BrickSet brick_set(const rwmi_ctx* c, int par) {
   BrickSet b;
+  b.wmask = c->wmask;
   b.bword = c->bword[par];
   b.bcand = c->bcand[par];
   b.rlist = c->rlist[par];
@@ -181,13 +183,17 @@ void update_margin(rwmi_ctx* c) {
   c->walk_margin = U_BOUND + (float)std::sqrt(2.0 * c->D) * 5.9f * 1.7320508f + 0.01f;
 }
 
-// Brick lists, poses and body force of the current time; zeroes its accumulators.
+// Brick lists, poses, body force and solid fraction of the current time; zeroes its accumulators.
 rwmi_status build_current_frame(rwmi_ctx* c) {
   const int par = (int)(c->t & 1);
   CK(cudaMemsetAsync(c->bword[par], 0, sizeof(uint32_t) * (c->nbrick + 1), c->stream));
   launch_pose_bin(c->g, particle_set(c), brick_set(c, par), c->d_T, 0, c->cfg.body_force,
                   c->cfg.force_period, 1, c->acc[par], c->stream);
   c->launches++;
+  if (c->P > 0) {
+    launch_raster(c->g, particle_set(c), brick_set(c, par), c->solid, c->status, c->nsm, c->stream);
+    c->launches++;
+  }
   CK(cudaGetLastError());
   return RWMI_OK;
 }
@@ -268,21 +274,17 @@ void phase_end(rwmi_ctx* c, int ph) {
   if (c->timing) cudaEventRecord(c->ev[2 * ph + 1], c->stream);
 }
 
-// One timestep t -> t+1 (host mirrors advance as the launches are queued).
-void enqueue_step(rwmi_ctx* c) {
+// One timestep t -> t+1 (host mirrors advance as the launches are queued). The solid fraction of
+// time t was rasterised at the end of the previous step (or at set-up); this step rasterises t+1
+// before the walkers, whose mini-brick masks come from that raster. `reduce`: also form the FP64
+// mass/momentum sums of this step.
+void enqueue_step(rwmi_ctx* c, bool reduce) {
   const int tp = (int)(c->t & 1), tn = tp ^ 1;
   const ParticleSet ps = particle_set(c);
   const uint32_t k0 = (uint32_t)c->seed, k1 = (uint32_t)(c->seed >> 32);
-  // solid fraction of time t (particles at t)
-  phase_begin(c, RWMI_PHASE_RASTER);
-  if (c->P > 0) {
-    launch_raster(c->g, ps, brick_set(c, tp), c->solid, c->status, c->nsm, c->stream);
-    c->launches++;
-  }
-  phase_end(c, RWMI_PHASE_RASTER);
   // LBM at t
   phase_begin(c, RWMI_PHASE_LBM);
-  launch_lbm(c->cfg.q, c->cfg.storage, true, c->g, c->f[c->fcur], c->f[c->fcur ^ 1], c->u, c->solid,
+  launch_lbm(c->cfg.q, c->cfg.storage, reduce, c->g, c->f[c->fcur], c->f[c->fcur ^ 1], c->u, c->solid,
              brick_set(c, tp), (float)c->tau, (float)c->cfg.rho0, c->acc[tp] + 6 * c->P, c->acc[tp],
              c->status, c->stream);
   c->launches++;
@@ -295,7 +297,14 @@ void enqueue_step(rwmi_ctx* c) {
                   c->acc[tn], c->stream);
   c->launches++;
   phase_end(c, RWMI_PHASE_POSE);
-  // walkers t -> t+1; the walker kernel's last block advances the device step counter
+  // solid fraction of t+1 (used by the LBM of the next step) and the walkers' masks
+  phase_begin(c, RWMI_PHASE_RASTER);
+  if (c->P > 0) {
+    launch_raster(c->g, ps, brick_set(c, tn), c->solid, c->status, c->nsm, c->stream);
+    c->launches++;
+  }
+  phase_end(c, RWMI_PHASE_RASTER);
+  // walkers t -> t+1; the walker kernel's last warp advances the device step counter
   phase_begin(c, RWMI_PHASE_WALKERS);
   if (c->nw > 0)
     launch_walkers(c->g, ps, brick_set(c, tn), c->pos[c->pcur], c->nw, c->u, c->d_T, (float)c->D, k0,
@@ -387,7 +396,7 @@ RWMI_API rwmi_status rwmi_create(rwmi_ctx** out, const int32_t dims[3], double t
     c->own_stream = true;
     rwmi_status s = alloc_fluid(c);
     if (s != RWMI_OK) return s;
-    CK(dalloc(&c->u, sizeof(float) * 3 * (size_t)g.ncell_pad));
+    CK(dalloc(&c->u, sizeof(float4) * (size_t)g.ncell_pad));   // (u, rho) per cell
     CK(dalloc(&c->solid, sizeof(uint16_t) * (size_t)ncell));
     CK(dalloc(&c->d_T, sizeof(int64_t)));
     CK(dalloc(&c->ticket, sizeof(unsigned int)));
@@ -396,6 +405,7 @@ RWMI_API rwmi_status rwmi_create(rwmi_ctx** out, const int32_t dims[3], double t
     CK(dalloc(&c->series, sizeof(double) * (size_t)SERIES_ROWS * SERIES_COLS));
     CK(dalloc(&c->mrow, sizeof(double) * SERIES_COLS));
     CK(dalloc(&c->counts, sizeof(uint32_t) * (size_t)ncell));
+    CK(dalloc(&c->wmask, sizeof(uint64_t) * c->nbrick));
     CK(dalloc(&c->offsets, sizeof(uint32_t) * (size_t)ncell));
     CK(dalloc(&c->bsums, sizeof(uint32_t) * scan_block_sums_size((uint32_t)ncell)));
     for (int k = 0; k < 2; ++k) {
@@ -603,7 +613,7 @@ RWMI_API rwmi_status rwmi_step(rwmi_ctx* c, int32_t n) {
       if (it == c->graphs.end()) {
         const int64_t l0 = c->launches;
         CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-        for (int64_t s = 0; s < L; ++s) enqueue_step(c);
+        for (int64_t s = 0; s < L; ++s) enqueue_step(c, s == L - 1);   // sums on the chunk's last step
         cudaGraph_t graph = nullptr;
         CK(cudaStreamEndCapture(c->stream, &graph));
         GraphEntry e;
@@ -629,7 +639,7 @@ RWMI_API rwmi_status rwmi_step(rwmi_ctx* c, int32_t n) {
       }
       n -= (int32_t)L;
     } else {
-      enqueue_step(c);
+      enqueue_step(c, true);
       n -= 1;
     }
   }
@@ -644,7 +654,7 @@ RWMI_API rwmi_status rwmi_step_timed(rwmi_ctx* c, int32_t n, double* phase_ms) {
     if (!c->ev[k]) CK(cudaEventCreate(&c->ev[k]));
   c->timing = true;
   for (int32_t s = 0; s < n; ++s) {
-    enqueue_step(c);
+    enqueue_step(c, s == n - 1);   // as in a replayed chunk: the sums on the last step only
     cudaError_t e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
       c->timing = false;
@@ -768,11 +778,7 @@ RWMI_API rwmi_status rwmi_solid(rwmi_ctx* c, int32_t* count, int32_t* owner) {
   const size_t bytes = sizeof(int32_t) * 2 * (size_t)c->ncell;
   rwmi_status s = ensure_scratch(c, bytes);
   if (s != RWMI_OK) return s;
-  if (c->P > 0) {
-    launch_raster(c->g, particle_set(c), brick_set(c, par), c->solid, c->status, c->nsm, c->stream);
-    c->launches++;
-  }
-  int32_t* tmp = (int32_t*)c->scratch;
+  int32_t* tmp = (int32_t*)c->scratch;   // the current time was rasterised by the last step / set-up
   launch_unpack_solid(c->g, c->solid, c->bword[par], tmp, tmp + c->ncell, c->stream);
   c->launches++;
   CK(cudaGetLastError());
@@ -933,7 +939,7 @@ RWMI_API void rwmi_destroy(rwmi_ctx* c) {
   }
   dfree(c->u); dfree(c->solid); dfree(c->d_T); dfree(c->ticket); dfree(c->status); dfree(c->macc);
   dfree(c->series); dfree(c->mrow); dfree(c->desc); dfree(c->cbody); dfree(c->rank);
-  dfree(c->counts); dfree(c->offsets); dfree(c->bsums); dfree(c->scratch);
+  dfree(c->counts); dfree(c->offsets); dfree(c->bsums); dfree(c->scratch); dfree(c->wmask);
   for (int k = 0; k < 2 * RWMI_NPHASE; ++k)
     if (c->ev[k]) cudaEventDestroy(c->ev[k]);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);

@@ -140,7 +140,9 @@ __global__ void pose_bin_kernel(Geom g, ParticleSet ps, BrickSet bs, const int64
   // bricks within rb + walk_margin of the origin; raster-relevant within rb + 1
   double ow[3];
   for (int a = 0; a < 3; ++a) ow[a] = wrap_d(so[a], (double)g.n[a], g.wall[a]);
-  const float Rw = d.rb + ps.walk_margin, Rr = d.rb + 1.0f;
+  // walker candidates and raster candidates coincide: the raster also writes the walkers'
+  // mini-brick masks, which must cover every particle within the walker margin
+  const float Rw = d.rb + ps.walk_margin, Rr = Rw;
   // Per axis, the bricks met by the interval [o - Rw, o + Rw] of the wrapped domain: one range,
   // or two when the interval crosses a periodic face (bricks need not tile a periodic axis
   // evenly, so the wrap is done on cell coordinates, not brick indices).
@@ -258,48 +260,45 @@ __device__ __forceinline__ bool subsample_inside(const float4* cw, int c0, int c
   return metaball_exact(cw, c0, c1, x, y, z, g) >= 1.0f;
 }
 
-// 64-bit mask of the sub-samples of cell (i, j, k) inside particle [c0, c1); bit a + 4 b + 16 c
-__device__ uint64_t particle_mask(const float4* cw, int c0, int c1, int i, int j, int k, const Geom& g) {
-  const float xc = (float)i + 0.5f, yc = (float)j + 0.5f, zc = (float)k + 0.5f;
-  const CellBound cb = bound_at(cw, c0, c1, xc, yc, zc, 0.649519053f, g);
-  if (cb.fmax < 0.999f) return 0ull;
-  if (cb.fmin > 1.001f) return ~0ull;
-  uint64_t mask = 0ull;
-  for (int oc = 0; oc < 8; ++oc) {
-    const int ox = oc & 1, oy = (oc >> 1) & 1, oz = oc >> 2;
-    const float xo = (float)i + 0.25f + 0.5f * ox, yo = (float)j + 0.25f + 0.5f * oy,
-                zo = (float)k + 0.25f + 0.5f * oz;
-    const CellBound ob = bound_at(cw, c0, c1, xo, yo, zo, 0.216506351f, g);
-    if (ob.fmax < 0.999f) continue;
-    uint64_t om = 0ull;
-#pragma unroll
-    for (int s = 0; s < 8; ++s) {
-      const int a = 2 * ox + (s & 1), b = 2 * oy + ((s >> 1) & 1), c = 2 * oz + (s >> 2);
-      const bool in = (ob.fmin > 1.001f) ||
-                      subsample_inside(cw, c0, c1, (float)i + (0.125f + 0.25f * (float)a),
-                                       (float)j + (0.125f + 0.25f * (float)b),
-                                       (float)k + (0.125f + 0.25f * (float)c), g);
-      if (in) om |= 1ull << (a + 4 * b + 16 * c);
-    }
-    mask |= om;
-  }
-  return mask;
+// Sub-sample s (bit s = a + 4 b + 16 c) of cell (i, j, k) inside particle [c0, c1)?
+__device__ __forceinline__ bool subsample_bit(const float4* cw, int c0, int c1, int i, int j, int k, int s,
+                                              const Geom& g) {
+  const int a = s & 3, b = (s >> 2) & 3, cc = s >> 4;
+  return subsample_inside(cw, c0, c1, (float)i + (0.125f + 0.25f * (float)a),
+                          (float)j + (0.125f + 0.25f * (float)b), (float)k + (0.125f + 0.25f * (float)cc), g);
+}
+
+// Whole-cell mask evaluated by one thread (fallback when the shared queue is full).
+__device__ uint64_t particle_mask_serial(const float4* cw, int c0, int c1, int i, int j, int k, const Geom& g) {
+  uint64_t m = 0ull;
+  for (int s = 0; s < 64; ++s)
+    if (subsample_bit(cw, c0, c1, i, j, k, s, g)) m |= 1ull << s;
+  return m;
 }
 
 constexpr int RASTER_SMEM_CENTERS = 1024;
+constexpr int RASTER_QUEUE = 1024;      // (cell, candidate) pairs whose cell straddles the surface
+constexpr int RASTER_PER_THREAD = 4;    // queued pairs one thread can remember
 
-// One block per brick of the raster list (grid-stride). The brick's raster-relevant candidate
-// particles are classified once for the whole brick (sub-samples lie within 6.71 of its centre:
-// wholly outside / wholly inside / partial), and the control points of the partial ones are staged
-// in shared memory for the per-cell masks.
-__global__ void __launch_bounds__(256, 2) raster_kernel(Geom g, ParticleSet ps, BrickSet bs,
+// One block (256 threads, 2 cells each) per brick of the raster list (grid-stride).
+//  1. the brick's raster-relevant candidates are classified once for the whole brick (outside /
+//     wholly inside / partial) and their control points staged in shared memory;
+//  2. each thread bounds Eq. 3 over its cells (half-diagonal 0.65): outside -> no sub-sample,
+//     inside -> all 64, otherwise the (cell, candidate) pair joins a shared queue;
+//  3. whole warps evaluate queued pairs, 32 sub-samples per instruction (ballot into the mask);
+//  4. each thread combines its cells' masks: count = popcount(OR), owner = most sub-samples,
+//     lowest index on ties.
+__global__ void __launch_bounds__(256) raster_kernel(Geom g, ParticleSet ps, BrickSet bs,
                                                      uint16_t* __restrict__ solid,
                                                      unsigned long long* __restrict__ status) {
   const uint32_t nbrick = (uint32_t)g.nb[0] * g.nb[1] * g.nb[2];
   const uint32_t nlist = bs.bword[nbrick];
   __shared__ float4 s_cw[RASTER_SMEM_CENTERS];
+  __shared__ uint32_t s_q[RASTER_QUEUE];
+  __shared__ unsigned long long s_qm[RASTER_QUEUE];
   __shared__ int s_p[MAXC], s_c0[MAXC], s_c1[MAXC], s_cls[MAXC];
-  __shared__ int s_n, s_all, s_smem;
+  __shared__ int s_n, s_all, s_smem, s_qn;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   for (uint32_t li = blockIdx.x; li < nlist; li += gridDim.x) {
     const uint32_t b = (uint32_t)bs.rlist[li];
     const int bi = b % g.nb[0], bj = (b / g.nb[0]) % g.nb[1], bk = b / (g.nb[0] * g.nb[1]);
@@ -321,11 +320,11 @@ __global__ void __launch_bounds__(256, 2) raster_kernel(Geom g, ParticleSet ps, 
       }
       s_n = n;
       s_smem = tot <= RASTER_SMEM_CENTERS;
+      s_qn = 0;
     }
     __syncthreads();
     const int n = s_n;
     if (!s_all) {
-      // stage control points (shared when they fit) and classify each candidate for the brick
       if (s_smem) {
         for (int m = 0; m < n; ++m) {
           const int g0 = ps.desc[s_p[m]].c0;
@@ -347,12 +346,33 @@ __global__ void __launch_bounds__(256, 2) raster_kernel(Geom g, ParticleSet ps, 
       }
       __syncthreads();
     }
-    for (int c = threadIdx.x; c < BRICK * BRICK * BRICK; c += blockDim.x) {
-      const int i = bi * BRICK + (c & 7), j = bj * BRICK + ((c >> 3) & 7), k = bk * BRICK + (c >> 6);
+    // walker mask: mini-brick m (cells 2a..2a+1 etc. of the brick) needs tests unless Eq. 3 stays
+    // below 1 for every candidate within sqrt(3) (the mini-brick) + the walker step margin of its
+    // centre (rigorous bound with a 1e-3 margin, as above)
+    if (threadIdx.x < 64) {
+      const int mb = threadIdx.x;
+      const float xm = (float)(bi * BRICK + 2 * (mb & 3)) + 1.0f, ym = (float)(bj * BRICK + 2 * ((mb >> 2) & 3)) + 1.0f,
+                  zm = (float)(bk * BRICK + 2 * (mb >> 4)) + 1.0f;
+      bool need = s_all != 0;
+      for (int m = 0; m < n && !need; ++m) {
+        const float4* cw = s_smem ? s_cw : bs.cworld;
+        const int c0 = s_smem ? s_c0[m] : ps.desc[s_p[m]].c0, c1 = s_smem ? s_c1[m] : ps.desc[s_p[m]].c1;
+        need = bound_at(cw, c0, c1, xm, ym, zm, 1.7320508f + ps.walk_margin, g).fmax >= 0.999f;
+      }
+      const unsigned bal = __ballot_sync(0xffffffffu, need);
+      if ((threadIdx.x & 31) == 0) reinterpret_cast<unsigned*>(bs.wmask + b)[threadIdx.x >> 5] = bal;
+    }
+    // 2. per-thread classification of its two cells
+    uint64_t any[2] = {0ull, 0ull};
+    int best[2] = {0, 0}, bestp[2] = {-1, -1};
+    int qidx[RASTER_PER_THREAD], qm[RASTER_PER_THREAD], qcell[RASTER_PER_THREAD];
+    int nq = 0;
+    const int ncand = s_all ? ps.P : n;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int cl = threadIdx.x + h * 256;
+      const int i = bi * BRICK + (cl & 7), j = bj * BRICK + ((cl >> 3) & 7), k = bk * BRICK + (cl >> 6);
       if (i >= g.n[0] || j >= g.n[1] || k >= g.n[2]) continue;
-      uint64_t any = 0ull;
-      int best = 0, bestp = -1;
-      const int ncand = s_all ? ps.P : n;
       for (int m = 0; m < ncand; ++m) {
         int p, c0, c1, cls = 2;
         const float4* cw = bs.cworld;
@@ -364,14 +384,65 @@ __global__ void __launch_bounds__(256, 2) raster_kernel(Geom g, ParticleSet ps, 
           else { c0 = ps.desc[p].c0; c1 = ps.desc[p].c1; }
         }
         if (cls == 0) continue;
-        const uint64_t mk = cls == 1 ? ~0ull : particle_mask(cw, c0, c1, i, j, k, g);
+        uint64_t mk = 0ull;
+        if (cls == 1) {
+          mk = ~0ull;
+        } else {
+          const CellBound cb = bound_at(cw, c0, c1, (float)i + 0.5f, (float)j + 0.5f, (float)k + 0.5f,
+                                        0.649519053f, g);
+          if (cb.fmax < 0.999f) continue;
+          if (cb.fmin > 1.001f) {
+            mk = ~0ull;
+          } else {
+            int slot = -1;
+            if (!s_all && nq < RASTER_PER_THREAD) {
+              slot = atomicAdd(&s_qn, 1);
+              if (slot >= RASTER_QUEUE) slot = -1;
+            }
+            if (slot >= 0) {   // the warps evaluate it below
+              s_q[slot] = ((uint32_t)cl << 8) | (uint32_t)m;
+              qidx[nq] = slot; qm[nq] = m; qcell[nq] = h; ++nq;
+              continue;
+            }
+            mk = particle_mask_serial(cw, c0, c1, i, j, k, g);
+          }
+        }
         const int np = __popcll(mk);
-        any |= mk;
-        if (np > 0 && (np > best || (np == best && p < bestp))) { best = np; bestp = p; }
+        any[h] |= mk;
+        if (np > 0 && (np > best[h] || (np == best[h] && p < bestp[h]))) { best[h] = np; bestp[h] = p; }
       }
-      const int count = __popcll(any);
+    }
+    __syncthreads();
+    // 3. warps evaluate the queued (cell, candidate) pairs, two rounds of 32 sub-samples
+    const int qn = min(s_qn, RASTER_QUEUE);
+    for (int e = warp; e < qn; e += nwarps) {
+      const uint32_t ent = s_q[e];
+      const int cl = ent >> 8, m = ent & 0xff;
+      const int i = bi * BRICK + (cl & 7), j = bj * BRICK + ((cl >> 3) & 7), k = bk * BRICK + (cl >> 6);
+      const float4* cw = s_smem ? s_cw : bs.cworld;
+      const int c0 = s_smem ? s_c0[m] : ps.desc[s_p[m]].c0, c1 = s_smem ? s_c1[m] : ps.desc[s_p[m]].c1;
+      const unsigned lo = __ballot_sync(0xffffffffu, subsample_bit(cw, c0, c1, i, j, k, lane, g));
+      const unsigned hi = __ballot_sync(0xffffffffu, subsample_bit(cw, c0, c1, i, j, k, lane + 32, g));
+      if (lane == 0) s_qm[e] = ((unsigned long long)hi << 32) | lo;
+    }
+    __syncthreads();
+    // 4. combine and write the solid words
+    for (int t = 0; t < nq; ++t) {
+      const int h = qcell[t];
+      const uint64_t mk = s_qm[qidx[t]];
+      const int p = s_p[qm[t]];
+      const int np = __popcll(mk);
+      any[h] |= mk;
+      if (np > 0 && (np > best[h] || (np == best[h] && p < bestp[h]))) { best[h] = np; bestp[h] = p; }
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int cl = threadIdx.x + h * 256;
+      const int i = bi * BRICK + (cl & 7), j = bj * BRICK + ((cl >> 3) & 7), k = bk * BRICK + (cl >> 6);
+      if (i >= g.n[0] || j >= g.n[1] || k >= g.n[2]) continue;
+      const int count = __popcll(any[h]);
       const uint32_t cell = ((uint32_t)k * g.n[1] + j) * g.n[0] + i;
-      solid[cell] = count > 0 ? (uint16_t)(count | (bestp << 7)) : (uint16_t)0;
+      solid[cell] = count > 0 ? (uint16_t)(count | (bestp[h] << 7)) : (uint16_t)0;
     }
     __syncthreads();
   }
@@ -380,7 +451,7 @@ __global__ void __launch_bounds__(256, 2) raster_kernel(Geom g, ParticleSet ps, 
 void launch_raster(const Geom& g, const ParticleSet& ps, BrickSet bs, uint16_t* solid,
                    unsigned long long* status, int nsm, cudaStream_t st) {
   if (ps.P == 0) return;
-  raster_kernel<<<nsm * 8, 256, 0, st>>>(g, ps, bs, solid, status);
+  raster_kernel<<<nsm * 4, 256, 0, st>>>(g, ps, bs, solid, status);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -409,9 +480,16 @@ template <> struct Store<2> {
   __device__ static void st(T* p, float v) { *p = __float2half_rn(v); }
 };
 
+// Base pointers of the Q direction planes (kernel parameters: constant-bank operands, so each
+// access is one address multiply-add).
+template <int Q, typename T> struct Planes {
+  const T* in[Q];
+  T* out[Q];
+};
+
 template <int Q, int STORE, bool WALLS, bool REDUCE>
-__global__ void __launch_bounds__(256) lbm_kernel(Geom g, const void* __restrict__ fin_,
-                                                  void* __restrict__ fout_, float* __restrict__ u,
+__global__ void __launch_bounds__(256, 4) lbm_kernel(Geom g, Planes<Q, typename Store<STORE>::T> pl,
+                                                  float4* __restrict__ u4,
                                                   const uint16_t* __restrict__ solid,
                                                   const uint32_t* __restrict__ bword,
                                                   const PoseF* __restrict__ pose,
@@ -420,14 +498,11 @@ __global__ void __launch_bounds__(256) lbm_kernel(Geom g, const void* __restrict
                                                   double* __restrict__ forces) {
   using L = Lat<Q>;
   using S = Store<STORE>;
-  using T = typename S::T;
-  const T* __restrict__ fin = (const T*)fin_;
-  T* __restrict__ fout = (T*)fout_;
   const uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x;
   const bool valid = idx < g.ncell;
-  const uint32_t c = valid ? idx : 0u;
-  const uint32_t z = fast_div(c, g.mxy, g.sxy);
-  const uint32_t rem = c - z * g.nxy;
+  const int c = (int)(valid ? idx : g.ncell - 1);   // tail lanes recompute the last cell, store nothing
+  const uint32_t z = fast_div((uint32_t)c, g.mxy, g.sxy);
+  const uint32_t rem = (uint32_t)c - z * g.nxy;
   const uint32_t y = fast_div(rem, g.mx, g.sx);
   const uint32_t x = rem - y * g.n[0];
   const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
@@ -436,25 +511,32 @@ __global__ void __launch_bounds__(256) lbm_kernel(Geom g, const void* __restrict
   const int ox_p = x == 0 ? nx - 1 : -1, ox_m = (int)x == nx - 1 ? -(nx - 1) : 1;
   const int oy_p = y == 0 ? (ny - 1) * sy : -sy, oy_m = (int)y == ny - 1 ? -(ny - 1) * sy : sy;
   const int oz_p = z == 0 ? (nz - 1) * sz : -sz, oz_m = (int)z == nz - 1 ? -(nz - 1) * sz : sz;
-  bool bx_p = false, bx_m = false, by_p = false, by_m = false, bz_p = false, bz_m = false;
-  if (WALLS) {
-    bx_p = g.wall[0] && x == 0; bx_m = g.wall[0] && (int)x == nx - 1;
-    by_p = g.wall[1] && y == 0; by_m = g.wall[1] && (int)y == ny - 1;
-    bz_p = g.wall[2] && z == 0; bz_m = g.wall[2] && (int)z == nz - 1;
-  }
-  const size_t pad = g.ncell_pad;
   float f[Q];
+  bool wall_cell = false;
+  if (WALLS)
+    wall_cell = (g.wall[0] && (x == 0 || (int)x == nx - 1)) || (g.wall[1] && (y == 0 || (int)y == ny - 1)) ||
+                (g.wall[2] && (z == 0 || (int)z == nz - 1));
+  if (!wall_cell) {
 #pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    const int ex = L::e(i, 0), ey = L::e(i, 1), ez = L::e(i, 2);
-    const int off = (ex > 0 ? ox_p : ex < 0 ? ox_m : 0) + (ey > 0 ? oy_p : ey < 0 ? oy_m : 0) +
-                    (ez > 0 ? oz_p : ez < 0 ? oz_m : 0);
-    bool blk = false;
-    if (WALLS)
-      blk = (ex > 0 && bx_p) || (ex < 0 && bx_m) || (ey > 0 && by_p) || (ey < 0 && by_m) ||
-            (ez > 0 && bz_p) || (ez < 0 && bz_m);
-    const T* src = blk ? fin + (size_t)L::opp(i) * pad + c : fin + (size_t)i * pad + (int)c + off;
-    f[i] = valid ? S::ld(src) : 0.0f;
+    for (int i = 0; i < Q; ++i) {
+      const int ex = L::e(i, 0), ey = L::e(i, 1), ez = L::e(i, 2);
+      const int off = (ex > 0 ? ox_p : ex < 0 ? ox_m : 0) + (ey > 0 ? oy_p : ey < 0 ? oy_m : 0) +
+                      (ez > 0 ? oz_p : ez < 0 ? oz_m : 0);
+      f[i] = S::ld(pl.in[i] + (c + off));
+    }
+  } else {   // half-way bounce-back where x - e_i lies beyond a wall: f_i(x) = f+_opp(i)(x)
+    const bool bx_p = g.wall[0] && x == 0, bx_m = g.wall[0] && (int)x == nx - 1;
+    const bool by_p = g.wall[1] && y == 0, by_m = g.wall[1] && (int)y == ny - 1;
+    const bool bz_p = g.wall[2] && z == 0, bz_m = g.wall[2] && (int)z == nz - 1;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const int ex = L::e(i, 0), ey = L::e(i, 1), ez = L::e(i, 2);
+      const int off = (ex > 0 ? ox_p : ex < 0 ? ox_m : 0) + (ey > 0 ? oy_p : ey < 0 ? oy_m : 0) +
+                      (ez > 0 ? oz_p : ez < 0 ? oz_m : 0);
+      const bool blk = (ex > 0 && bx_p) || (ex < 0 && bx_m) || (ey > 0 && by_p) || (ey < 0 && by_m) ||
+                       (ez > 0 && bz_p) || (ez < 0 && bz_m);
+      f[i] = blk ? S::ld(pl.in[L::opp(i)] + c) : S::ld(pl.in[i] + (c + off));
+    }
   }
   // moments (Eqs. 14-15); with shifted storage f holds f_i - w_i rho0
   float drho = 0.0f, jx = 0.0f, jy = 0.0f, jz = 0.0f;
@@ -474,12 +556,12 @@ __global__ void __launch_bounds__(256) lbm_kernel(Geom g, const void* __restrict
   // partially saturated cell: solid word valid only in bricks flagged for this time
   float B = 0.0f, usx = 0.0f, usy = 0.0f, usz = 0.0f;
   int owner = -1;
-  if (valid) {
+  {
     const uint32_t b = ((z >> 3) * (uint32_t)g.nb[1] + (y >> 3)) * (uint32_t)g.nb[0] + (x >> 3);
     if (bword[b] >> 16) {
       const uint16_t sw = solid[c];
       const int cnt = sw & 0x7f;
-      if (cnt) {
+      if (cnt && valid) {
         owner = sw >> 7;
         const float eps = (float)cnt * (1.0f / 64.0f);
         B = eps * (tau - 0.5f) / ((1.0f - eps) + (tau - 0.5f));
@@ -502,16 +584,13 @@ __global__ void __launch_bounds__(256) lbm_kernel(Geom g, const void* __restrict
   const float uF = ux * Fx + uy * Fy + uz * Fz;
   const float usus = usx * usx + usy * usy + usz * usz;
   float dpx = 0.0f, dpy = 0.0f, dpz = 0.0f;
-  // rest direction
-  {
+  float out[Q];
+  {  // rest direction; its own opposite: Omega_0 = feq_0(rho, u_s) - feq_0(rho, u)
     const float w = L::w(0);
-    const float dev = -1.5f * uu;                       // feq_0 / (w rho) - 1
+    const float dev = -1.5f * uu;
     const float feq_s = S::shifted ? w * (drho + rho * dev) : w * rho * (1.0f + dev);
-    const float S0 = guo * w * (-3.0f * uF);
-    // rest is its own opposite: Omega_0 = feq_0(rho, u_s) - feq_0(rho, u) = 1.5 w rho (u.u - us.us)
-    const float om0 = B > 0.0f ? 1.5f * w * rho * (uu - (usx * usx + usy * usy + usz * usz)) : 0.0f;
-    const float out = f[0] - rtau * (f[0] - feq_s) + S0 + B * om0;
-    if (valid) S::st(fout + c, out);
+    const float om0 = B > 0.0f ? 1.5f * w * rho * (uu - usus) : 0.0f;
+    out[0] = f[0] - rtau * (f[0] - feq_s) + guo * w * (-3.0f * uF) + B * om0;
   }
   // opposite pairs (i, i + H) share e.u
 #pragma unroll
@@ -523,33 +602,28 @@ __global__ void __launch_bounds__(256) lbm_kernel(Geom g, const void* __restrict
     const float eF = ex * Fx + ey * Fy + ez * Fz;
     const float sym = 4.5f * eu * eu - 1.5f * uu;        // even part of feq / (w rho)
     const float base = S::shifted ? w * drho : w * rho;  // w rho (minus w rho0 when shifted)
-    const float feq_p = base + w * rho * (3.0f * eu + sym);
-    const float feq_m = base + w * rho * (-3.0f * eu + sym);
-    const float Sp = guo * w * (3.0f * (eF - uF) + 9.0f * eu * eF);
-    const float Sm = guo * w * (3.0f * (-eF - uF) + 9.0f * eu * eF);
-    float out_p = f[i] - rtau * (f[i] - feq_p) + Sp;
-    float out_m = f[io] - rtau * (f[io] - feq_m) + Sm;
+    const float wr = w * rho;
+    const float feq_p = base + wr * (3.0f * eu + sym);
+    const float feq_m = base + wr * (-3.0f * eu + sym);
+    const float gw = guo * w;
+    out[i] = f[i] - rtau * (f[i] - feq_p) + gw * (3.0f * (eF - uF) + 9.0f * eu * eF);
+    out[io] = f[io] - rtau * (f[io] - feq_m) + gw * (3.0f * (-eF - uF) + 9.0f * eu * eF);
     if (B > 0.0f) {
       const float eus = ex * usx + ey * usy + ez * usz;
-      const float wr = w * rho;
       const float common = wr * (4.5f * (eus * eus - eu * eu) - 1.5f * (usus - uu));
       const float odd = wr * 3.0f * (eu + eus);
       const float om_p = (f[io] - f[i]) + odd + common;   // Omega_i
       const float om_m = (f[i] - f[io]) - odd + common;   // Omega_opp(i)
-      out_p += B * om_p;
-      out_m += B * om_m;
+      out[i] += B * om_p;
+      out[io] += B * om_m;
       const float dm = B * (om_p - om_m);                 // B (Omega_i e_i + Omega_opp e_opp) / e_i
       dpx += dm * ex; dpy += dm * ey; dpz += dm * ez;
     }
-    if (valid) {
-      S::st(fout + (size_t)i * pad + c, out_p);
-      S::st(fout + (size_t)io * pad + c, out_m);
-    }
   }
   if (valid) {
-    u[c] = ux;
-    u[pad + c] = uy;
-    u[2 * pad + c] = uz;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) S::st(pl.out[i] + c, out[i]);
+    u4[c] = make_float4(ux, uy, uz, rho);
   }
   // hydrodynamic force on the owner particle: -B sum_i Omega_i e_i; torque about its origin
   const unsigned full = 0xffffffffu;
@@ -589,37 +663,45 @@ __global__ void __launch_bounds__(256) lbm_kernel(Geom g, const void* __restrict
       }
     }
   }
-  if (REDUCE) {   // FP64 sums of (rho - rho0) and sum_i f_i e_i (pre-collision), per block
-    double v[4] = {valid ? (double)(S::shifted ? drho : rho - rho0) : 0.0, valid ? (double)jx : 0.0,
-                   valid ? (double)jy : 0.0, valid ? (double)jz : 0.0};
+  if (REDUCE) {   // sums of (rho - rho0) and sum_i f_i e_i (pre-collision): binary32 within the
+                  // block (256 small deviations), FP64 across blocks (GB300's FP64 pipe is narrow)
+    float v[4] = {valid ? (S::shifted ? drho : rho - rho0) : 0.0f, valid ? jx : 0.0f,
+                  valid ? jy : 0.0f, valid ? jz : 0.0f};
 #pragma unroll
     for (int m = 0; m < 4; ++m)
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) v[m] += __shfl_xor_sync(full, v[m], o);
-    __shared__ double s_red[8][4];
+    __shared__ float s_red[8][4];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (lane == 0)
       for (int m = 0; m < 4; ++m) s_red[wid][m] = v[m];
     __syncthreads();
     if (threadIdx.x < 4) {   // striped slots keep the FP64 atomics of 65536 blocks uncontended
-      double s = 0.0;
+      float s = 0.0f;
       for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += s_red[w][threadIdx.x];
-      atomicAdd(&red[4 * (blockIdx.x % RED_SLOTS) + threadIdx.x], s);
+      atomicAdd(&red[4 * (blockIdx.x % RED_SLOTS) + threadIdx.x], (double)s);
     }
   }
 }
 
 template <int Q, int STORE>
-static void launch_lbm_q(bool walls, bool reduce, const Geom& g, const void* fin, void* fout,
-                         float* u, const uint16_t* solid, BrickSet bs, float tau, float rho0,
-                         double* red, double* forces, cudaStream_t st) {
+static void launch_lbm_q(bool walls, bool reduce, const Geom& g, const void* fin, void* fout, float* u,
+                         const uint16_t* solid, BrickSet bs, float tau, float rho0, double* red,
+                         double* forces, cudaStream_t st) {
+  using T = typename Store<STORE>::T;
+  Planes<Q, T> pl;
+  for (int i = 0; i < Q; ++i) {
+    pl.in[i] = (const T*)fin + (size_t)i * g.ncell_pad;
+    pl.out[i] = (T*)fout + (size_t)i * g.ncell_pad;
+  }
+  float4* u4 = reinterpret_cast<float4*>(u);
   const dim3 grid((g.ncell + 255) / 256), block(256);
   if (walls) {
-    if (reduce) lbm_kernel<Q, STORE, true, true><<<grid, block, 0, st>>>(g, fin, fout, u, solid, bs.bword, bs.pose, bs.sp, tau, rho0, red, forces);
-    else lbm_kernel<Q, STORE, true, false><<<grid, block, 0, st>>>(g, fin, fout, u, solid, bs.bword, bs.pose, bs.sp, tau, rho0, red, forces);
+    if (reduce) lbm_kernel<Q, STORE, true, true><<<grid, block, 0, st>>>(g, pl, u4, solid, bs.bword, bs.pose, bs.sp, tau, rho0, red, forces);
+    else lbm_kernel<Q, STORE, true, false><<<grid, block, 0, st>>>(g, pl, u4, solid, bs.bword, bs.pose, bs.sp, tau, rho0, red, forces);
   } else {
-    if (reduce) lbm_kernel<Q, STORE, false, true><<<grid, block, 0, st>>>(g, fin, fout, u, solid, bs.bword, bs.pose, bs.sp, tau, rho0, red, forces);
-    else lbm_kernel<Q, STORE, false, false><<<grid, block, 0, st>>>(g, fin, fout, u, solid, bs.bword, bs.pose, bs.sp, tau, rho0, red, forces);
+    if (reduce) lbm_kernel<Q, STORE, false, true><<<grid, block, 0, st>>>(g, pl, u4, solid, bs.bword, bs.pose, bs.sp, tau, rho0, red, forces);
+    else lbm_kernel<Q, STORE, false, false><<<grid, block, 0, st>>>(g, pl, u4, solid, bs.bword, bs.pose, bs.sp, tau, rho0, red, forces);
   }
 }
 
@@ -657,9 +739,7 @@ __global__ void init_pop_kernel(Geom g, void* f_, float rho0, float ux, float uy
     const float v = S::shifted ? L::w(i) * rho0 * dev : L::w(i) * rho0 * (1.0f + dev);
     S::st(f + (size_t)i * g.ncell_pad + c, v);
   }
-  u[c] = ux;
-  u[g.ncell_pad + c] = uy;
-  u[2 * (size_t)g.ncell_pad + c] = uz;
+  reinterpret_cast<float4*>(u)[c] = make_float4(ux, uy, uz, rho0);
 }
 
 template <int Q, int STORE>
@@ -755,9 +835,10 @@ void launch_unpack_solid(const Geom& g, const uint16_t* solid, const uint32_t* b
 __global__ void velocity_aos_kernel(Geom g, const float* u, float* out) {
   const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= g.ncell) return;
-  out[3 * (size_t)c] = u[c];
-  out[3 * (size_t)c + 1] = u[g.ncell_pad + c];
-  out[3 * (size_t)c + 2] = u[2 * (size_t)g.ncell_pad + c];
+  const float4 v = reinterpret_cast<const float4*>(u)[c];
+  out[3 * (size_t)c] = v.x;
+  out[3 * (size_t)c + 1] = v.y;
+  out[3 * (size_t)c + 2] = v.z;
 }
 
 void launch_velocity_aos(const Geom& g, const float* u, float* out, cudaStream_t st) {

@@ -4,14 +4,15 @@
 //   populations   f[2][Q][ncell_pad]      A/B ping-pong, direction-major (SoA), each direction
 //                                         plane 128-byte aligned; binary32 (optionally shifted by
 //                                         w_i rho0) or binary16 shifted
-//   velocity      u[3][ncell_pad]         binary32 SoA, written by the LBM kernel, gathered by
-//                                         walkers
+//   velocity      u[ncell] float4          (ux, uy, uz, rho) per cell, written by the LBM kernel
+//                                         with one 16-byte store, gathered by walkers (8 loads)
 //   solid         solid[ncell]            uint16: sub-sample count (bits 0-6) | owner (bits 7-15),
 //                                         valid only in bricks flagged for the current time
 //   bricks        8x8x8-cell bricks, per time parity: bword[nbrick+1] (walker-candidate count in
 //                 bits 0-15, raster-relevant count in bits 16-31; the extra last word counts
 //                 rlist), bcand[nbrick][MAXC] (uint16 particle ids, bit 15 = raster-relevant),
-//                 rlist[nbrick] (bricks holding raster-relevant particles)
+//                 rlist[nbrick] (bricks holding raster-relevant particles); wmask[nbrick] 64-bit
+//                 masks of 2^3-cell mini-bricks where walkers must test particles
 //   particles     desc[P] (trajectory), cbody[Nc] float4 (body-frame x, y, z, k),
 //                 per time parity: pose[P] and cworld[Nc] float4 (world x, y, z, k; wrapped)
 //   walkers       pos[2][N] float4 {x, y, z, id bits} (unwrapped), x0[2][N] float4 start
@@ -179,6 +180,8 @@ __device__ __forceinline__ int brick_of(float xw, float yw, float zw, const Geom
 
 // ---- kernel launchers (defined in the .cu files) ----
 struct BrickSet {
+  uint64_t* wmask;    // [nbrick] per brick: bit m set when mini-brick m (2^3 cells) may need a
+                      // metaball test by walkers (written by the raster of this time)
   uint32_t* bword;    // [nbrick + 1]
   uint16_t* bcand;    // [nbrick * MAXC]
   int32_t* rlist;     // [nbrick]

@@ -46,19 +46,22 @@ __device__ __forceinline__ void interp_velocity(const float* __restrict__ u, con
   axis_weights(x, g.n[0], g.wall[0], ix0, ix1, wx0, wx1);
   axis_weights(y, g.n[1], g.wall[1], iy0, iy1, wy0, wy1);
   axis_weights(z, g.n[2], g.wall[2], iz0, iz1, wz0, wz1);
-  const size_t pad = g.ncell_pad;
+  const float4* __restrict__ u4 = reinterpret_cast<const float4*>(u);
   const uint32_t r00 = ((uint32_t)iz0 * g.n[1] + iy0) * g.n[0], r01 = ((uint32_t)iz0 * g.n[1] + iy1) * g.n[0];
   const uint32_t r10 = ((uint32_t)iz1 * g.n[1] + iy0) * g.n[0], r11 = ((uint32_t)iz1 * g.n[1] + iy1) * g.n[0];
   const uint32_t cidx[8] = {r00 + ix0, r00 + ix1, r01 + ix0, r01 + ix1,
                             r10 + ix0, r10 + ix1, r11 + ix0, r11 + ix1};
   const float cw[8] = {wz0 * wy0 * wx0, wz0 * wy0 * wx1, wz0 * wy1 * wx0, wz0 * wy1 * wx1,
                        wz1 * wy0 * wx0, wz1 * wy0 * wx1, wz1 * wy1 * wx0, wz1 * wy1 * wx1};
+  float4 v[8];
+#pragma unroll
+  for (int m = 0; m < 8; ++m) v[m] = __ldg(u4 + cidx[m]);   // (u, rho) of the 8 nodes
   float ax = 0.0f, ay = 0.0f, az = 0.0f;
 #pragma unroll
   for (int m = 0; m < 8; ++m) {
-    ax += cw[m] * __ldg(u + cidx[m]);
-    ay += cw[m] * __ldg(u + pad + cidx[m]);
-    az += cw[m] * __ldg(u + 2 * pad + cidx[m]);
+    ax += cw[m] * v[m].x;
+    ay += cw[m] * v[m].y;
+    az += cw[m] * v[m].z;
   }
   ux = ax; uy = ay; uz = az;
 }
@@ -219,7 +222,13 @@ __global__ void __launch_bounds__(256) walker_kernel(WalkCtx c, float4* __restri
       const float yw = wrap_coord(x[1], (float)c.g.n[1], c.g.wall[1]);
       const float zw = wrap_coord(x[2], (float)c.g.n[2], c.g.wall[2]);
       const int b = brick_of(xw, yw, zw, c.g);
-      const uint32_t nc = c.bs.bword[b] & 0xffffu;
+      uint32_t nc = c.bs.bword[b] & 0xffffu;
+      if (nc > 0 && nc <= MAXC) {   // mini-brick of x: cells (2a, 2a+1) along each axis of the brick
+        const int ix = min(max((int)floorf(xw), 0), c.g.n[0] - 1), iy = min(max((int)floorf(yw), 0), c.g.n[1] - 1),
+                  iz = min(max((int)floorf(zw), 0), c.g.n[2] - 1);
+        const int mb = ((ix & 7) >> 1) + 4 * ((iy & 7) >> 1) + 16 * ((iz & 7) >> 1);
+        if (!((c.bs.wmask[b] >> mb) & 1ull)) nc = 0;   // no particle can be met within the step
+      }
       const bool far_step = step2 > c.ps.walk_margin * c.ps.walk_margin;
       ev_fast = far_step;
       if (nc > 0 || far_step) {
@@ -281,17 +290,15 @@ __global__ void __launch_bounds__(256) walker_kernel(WalkCtx c, float4* __restri
       if (bal && (threadIdx.x & 31) == 0) atomicAdd(&status[slot[m]], (unsigned long long)__popc(bal));
     }
   }
-  // the last block to finish advances the device step counter
-  if (d_T_inc) {
-    __syncthreads();
-    if (threadIdx.x == 0) {
+  // the last warp to finish advances the device step counter (every warp has read T by then)
+  if (d_T_inc && (threadIdx.x & 31) == 0) {
+    __threadfence();
+    const unsigned int nwarps = gridDim.x * (blockDim.x >> 5);
+    const unsigned int done = atomicAdd(ticket, 1u);
+    if (done == nwarps - 1) {
+      *d_T_inc = T + 1;
+      *ticket = 0u;
       __threadfence();
-      const unsigned int done = atomicAdd(ticket, 1u);
-      if (done == gridDim.x - 1) {
-        *d_T_inc = T + 1;
-        *ticket = 0u;
-        __threadfence();
-      }
     }
   }
 }
