@@ -76,6 +76,8 @@ struct rwmi_ctx {
   float4* pos[2] = {nullptr, nullptr};
   float4* x0[2] = {nullptr, nullptr};
   uint32_t* rank = nullptr;
+  float4* wlist = nullptr;            // walkers flagged for the particle-resolution pass
+  unsigned int* wlist_n = nullptr;
   uint32_t* counts = nullptr;
   uint32_t* offsets = nullptr;
   uint32_t* bsums = nullptr;
@@ -242,13 +244,16 @@ rwmi_status alloc_walkers(rwmi_ctx* c, int64_t n) {
     c->x0[k] = nullptr;
   }
   dfree(c->rank);
+  dfree(c->wlist);
   c->rank = nullptr;
+  c->wlist = nullptr;
   c->nw = 0;
   for (int k = 0; k < 2; ++k) {
     CK(dalloc(&c->pos[k], sizeof(float4) * (size_t)n));
     CK(dalloc(&c->x0[k], sizeof(float4) * (size_t)n));
   }
   CK(dalloc(&c->rank, sizeof(uint32_t) * (size_t)n));
+  CK(dalloc(&c->wlist, 2 * sizeof(float4) * (size_t)n));
   c->nw = n;
   c->pcur = 0;
   c->binned_t = -1;
@@ -306,12 +311,14 @@ void enqueue_step(rwmi_ctx* c, bool reduce) {
   phase_end(c, RWMI_PHASE_RASTER);
   // walkers t -> t+1; the walker kernel's last warp advances the device step counter
   phase_begin(c, RWMI_PHASE_WALKERS);
-  if (c->nw > 0)
+  if (c->nw > 0) {
     launch_walkers(c->g, ps, brick_set(c, tn), c->pos[c->pcur], c->nw, c->u, c->d_T, (float)c->D, k0,
-                   k1, c->status, c->ticket, c->d_T, c->stream);
-  else
+                   k1, c->status, c->ticket, c->d_T, c->wlist, c->wlist_n, c->nsm, c->stream);
+    c->launches += 2;
+  } else {
     launch_advance(c->d_T, c->stream);
-  c->launches++;
+    c->launches++;
+  }
   phase_end(c, RWMI_PHASE_WALKERS);
   c->t += 1;
   phase_begin(c, RWMI_PHASE_SORT);
@@ -385,6 +392,7 @@ RWMI_API rwmi_status rwmi_create(rwmi_ctx** out, const int32_t dims[3], double t
   g.nxy = (uint32_t)dims[0] * (uint32_t)dims[1];
   g.ncell = (uint32_t)ncell;
   g.ncell_pad = (uint32_t)((ncell + 63) / 64 * 64);
+  for (int a = 0; a < 3; ++a) g.inv_n[a] = 1.0f / (float)dims[a];
   make_divisor((uint32_t)dims[0], g.mx, g.sx);
   make_divisor(g.nxy, g.mxy, g.sxy);
   c->nbrick = (uint32_t)g.nb[0] * g.nb[1] * g.nb[2];
@@ -400,6 +408,8 @@ RWMI_API rwmi_status rwmi_create(rwmi_ctx** out, const int32_t dims[3], double t
     CK(dalloc(&c->solid, sizeof(uint16_t) * (size_t)ncell));
     CK(dalloc(&c->d_T, sizeof(int64_t)));
     CK(dalloc(&c->ticket, sizeof(unsigned int)));
+    CK(dalloc(&c->wlist_n, sizeof(unsigned int)));
+    CK(cudaMemsetAsync(c->wlist_n, 0, sizeof(unsigned int), c->stream));
     CK(dalloc(&c->status, sizeof(unsigned long long) * ST_COUNT));
     CK(dalloc(&c->macc, sizeof(double) * 12));
     CK(dalloc(&c->series, sizeof(double) * (size_t)SERIES_ROWS * SERIES_COLS));
@@ -937,6 +947,7 @@ RWMI_API void rwmi_destroy(rwmi_ctx* c) {
     dfree(c->f[k]); dfree(c->acc[k]); dfree(c->bword[k]); dfree(c->bcand[k]); dfree(c->rlist[k]);
     dfree(c->pose[k]); dfree(c->sp[k]); dfree(c->cworld[k]); dfree(c->pos[k]); dfree(c->x0[k]);
   }
+  dfree(c->wlist); dfree(c->wlist_n);
   dfree(c->u); dfree(c->solid); dfree(c->d_T); dfree(c->ticket); dfree(c->status); dfree(c->macc);
   dfree(c->series); dfree(c->mrow); dfree(c->desc); dfree(c->cbody); dfree(c->rank);
   dfree(c->counts); dfree(c->offsets); dfree(c->bsums); dfree(c->scratch); dfree(c->wmask);

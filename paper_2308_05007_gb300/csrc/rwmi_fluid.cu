@@ -224,16 +224,20 @@ void launch_pose_bin(const Geom& g, const ParticleSet& ps, BrickSet bs, const in
 // ------------------------------------------------------------------------------------------
 struct CellBound { float fmax, fmin; };
 
+// Displacement x - c: with mi, the minimum image on periodic axes; without, the plain difference
+// (control points staged at the brick's nearest image, valid for every point of the brick).
+__device__ __forceinline__ float disp(float x, float c, int a, bool mi, const Geom& g) {
+  return mi ? min_image_rn(x - c, (float)g.n[a], g.wall[a]) : x - c;
+}
+
 // Bounds of Eq. 3 over a ball of radius h about (x, y, z): every control point is at least
 // r - h and at most r + h away. Fast reciprocal/sqrt: the 1e-3 decision margins dwarf their error.
 __device__ __forceinline__ CellBound bound_at(const float4* cw, int c0, int c1, float x, float y, float z,
-                                              float h, const Geom& g) {
+                                              float h, const Geom& g, bool mi = true) {
   float fmax = 0.0f, fmin = 0.0f;
   for (int i = c0; i < c1; ++i) {
     const float4 c = cw[i];
-    const float dx = min_image_rn(x - c.x, (float)g.n[0], g.wall[0]);
-    const float dy = min_image_rn(y - c.y, (float)g.n[1], g.wall[1]);
-    const float dz = min_image_rn(z - c.z, (float)g.n[2], g.wall[2]);
+    const float dx = disp(x, c.x, 0, mi, g), dy = disp(y, c.y, 1, mi, g), dz = disp(z, c.z, 2, mi, g);
     const float r2 = dx * dx + dy * dy + dz * dz;
     const float r = r2 * rsqrtf(fmaxf(r2, 1e-30f));
     const float rmin = fmaxf(r - h, 1e-15f), rmax = r + h;
@@ -246,33 +250,53 @@ __device__ __forceinline__ CellBound bound_at(const float4* cw, int c0, int c1, 
   return b;
 }
 
-__device__ __forceinline__ bool subsample_inside(const float4* cw, int c0, int c1, float x, float y,
+// Upper/lower bounds over a ball of radius h1 and the upper bound over radius h2 (one pass).
+struct Bound2 { float fmax1, fmin1, fmax2; };
+__device__ __forceinline__ Bound2 bound_two(const float4* cw, int c0, int c1, float x, float y, float z,
+                                            float h1, float h2, const Geom& g, bool mi) {
+  Bound2 b{0.0f, 0.0f, 0.0f};
+  for (int i = c0; i < c1; ++i) {
+    const float4 c = cw[i];
+    const float dx = disp(x, c.x, 0, mi, g), dy = disp(y, c.y, 1, mi, g), dz = disp(z, c.z, 2, mi, g);
+    const float r2 = dx * dx + dy * dy + dz * dz;
+    const float r = r2 * rsqrtf(fmaxf(r2, 1e-30f));
+    const float a = fmaxf(r - h1, 1e-15f), bb = r + h1, cc = fmaxf(r - h2, 1e-15f);
+    b.fmax1 += __fdividef(c.w, a * a);
+    b.fmin1 += __fdividef(c.w, bb * bb);
+    b.fmax2 += __fdividef(c.w, cc * cc);
+  }
+  return b;
+}
+
+// Sub-sample inside test: fast value from the staged control points; within 4e-5 of 1 the
+// exact binary32 sequence shared with the CPU oracle decides, on the original wrapped points.
+__device__ __forceinline__ bool subsample_inside(const float4* cw, int c0, int c1, bool mi,
+                                                 const float4* cw_exact, int e0, int e1, float x, float y,
                                                  float z, const Geom& g) {
   float f = 0.0f;
   for (int i = c0; i < c1; ++i) {
     const float4 c = cw[i];
-    const float dx = min_image_rn(x - c.x, (float)g.n[0], g.wall[0]);
-    const float dy = min_image_rn(y - c.y, (float)g.n[1], g.wall[1]);
-    const float dz = min_image_rn(z - c.z, (float)g.n[2], g.wall[2]);
+    const float dx = disp(x, c.x, 0, mi, g), dy = disp(y, c.y, 1, mi, g), dz = disp(z, c.z, 2, mi, g);
     f += __fdividef(c.w, dx * dx + dy * dy + dz * dz);
   }
   if (fabsf(f - 1.0f) > 4e-5f) return f >= 1.0f;
-  return metaball_exact(cw, c0, c1, x, y, z, g) >= 1.0f;
+  return metaball_exact(cw_exact, e0, e1, x, y, z, g) >= 1.0f;
 }
 
-// Sub-sample s (bit s = a + 4 b + 16 c) of cell (i, j, k) inside particle [c0, c1)?
-__device__ __forceinline__ bool subsample_bit(const float4* cw, int c0, int c1, int i, int j, int k, int s,
-                                              const Geom& g) {
+// Sub-sample s (bit s = a + 4 b + 16 c) of cell (i, j, k) inside the particle?
+__device__ __forceinline__ bool subsample_bit(const float4* cw, int c0, int c1, bool mi, const float4* cw_exact,
+                                              int e0, int e1, int i, int j, int k, int s, const Geom& g) {
   const int a = s & 3, b = (s >> 2) & 3, cc = s >> 4;
-  return subsample_inside(cw, c0, c1, (float)i + (0.125f + 0.25f * (float)a),
+  return subsample_inside(cw, c0, c1, mi, cw_exact, e0, e1, (float)i + (0.125f + 0.25f * (float)a),
                           (float)j + (0.125f + 0.25f * (float)b), (float)k + (0.125f + 0.25f * (float)cc), g);
 }
 
 // Whole-cell mask evaluated by one thread (fallback when the shared queue is full).
-__device__ uint64_t particle_mask_serial(const float4* cw, int c0, int c1, int i, int j, int k, const Geom& g) {
+__device__ uint64_t particle_mask_serial(const float4* cw, int c0, int c1, bool mi, const float4* cw_exact, int e0,
+                                         int e1, int i, int j, int k, const Geom& g) {
   uint64_t m = 0ull;
   for (int s = 0; s < 64; ++s)
-    if (subsample_bit(cw, c0, c1, i, j, k, s, g)) m |= 1ull << s;
+    if (subsample_bit(cw, c0, c1, mi, cw_exact, e0, e1, i, j, k, s, g)) m |= 1ull << s;
   return m;
 }
 
@@ -288,7 +312,7 @@ constexpr int RASTER_PER_THREAD = 4;    // queued pairs one thread can remember
 //  3. whole warps evaluate queued pairs, 32 sub-samples per instruction (ballot into the mask);
 //  4. each thread combines its cells' masks: count = popcount(OR), owner = most sub-samples,
 //     lowest index on ties.
-__global__ void __launch_bounds__(256) raster_kernel(Geom g, ParticleSet ps, BrickSet bs,
+__global__ void __launch_bounds__(256, 4) raster_kernel(Geom g, ParticleSet ps, BrickSet bs,
                                                      uint16_t* __restrict__ solid,
                                                      unsigned long long* __restrict__ status) {
   const uint32_t nbrick = (uint32_t)g.nb[0] * g.nb[1] * g.nb[2];
@@ -297,8 +321,15 @@ __global__ void __launch_bounds__(256) raster_kernel(Geom g, ParticleSet ps, Bri
   __shared__ uint32_t s_q[RASTER_QUEUE];
   __shared__ unsigned long long s_qm[RASTER_QUEUE];
   __shared__ int s_p[MAXC], s_c0[MAXC], s_c1[MAXC], s_cls[MAXC];
-  __shared__ int s_n, s_all, s_smem, s_qn;
+  __shared__ unsigned char s_mcls[MAXC][64];   // per candidate and mini-brick: class | walker bit << 2
+  __shared__ int s_n, s_all, s_smem, s_qn, s_mi;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  // candidate m's control points for the fast tests (staged, nearest image) and for the exact one
+#define RC_FAST(m, cw, c0, c1, mi)                                                                   \
+  const float4* cw = s_smem ? s_cw : bs.cworld;                                                      \
+  const int c0 = s_smem ? s_c0[m] : ps.desc[s_p[m]].c0, c1 = s_smem ? s_c1[m] : ps.desc[s_p[m]].c1; \
+  const bool mi = s_smem ? (s_mi != 0) : true;
+#define RC_EXACT(m, e0, e1) const int e0 = ps.desc[s_p[m]].c0, e1 = ps.desc[s_p[m]].c1;
   for (uint32_t li = blockIdx.x; li < nlist; li += gridDim.x) {
     const uint32_t b = (uint32_t)bs.rlist[li];
     const int bi = b % g.nb[0], bj = (b / g.nb[0]) % g.nb[1], bk = b / (g.nb[0] * g.nb[1]);
@@ -321,44 +352,81 @@ __global__ void __launch_bounds__(256) raster_kernel(Geom g, ParticleSet ps, Bri
       s_n = n;
       s_smem = tot <= RASTER_SMEM_CENTERS;
       s_qn = 0;
+      s_mi = 0;
     }
     __syncthreads();
     const int n = s_n;
     if (!s_all) {
       if (s_smem) {
+        // stage each control point at its image nearest the brick centre; if some point lies near
+        // the half-box distance (small boxes), the fast tests keep the per-point minimum image
+        const float bcx = (float)(bi * BRICK) + 4.0f, bcy = (float)(bj * BRICK) + 4.0f, bcz = (float)(bk * BRICK) + 4.0f;
+        const float H = 6.0f + ps.walk_margin;
+        int near_half = 0;
         for (int m = 0; m < n; ++m) {
           const int g0 = ps.desc[s_p[m]].c0;
-          for (int i = threadIdx.x; i < s_c1[m] - s_c0[m]; i += blockDim.x) s_cw[s_c0[m] + i] = bs.cworld[g0 + i];
+          for (int i = threadIdx.x; i < s_c1[m] - s_c0[m]; i += blockDim.x) {
+            float4 cc = bs.cworld[g0 + i];
+            float* v[3] = {&cc.x, &cc.y, &cc.z};
+            const float bc[3] = {bcx, bcy, bcz};
+            for (int a = 0; a < 3; ++a) {
+              if (g.wall[a]) continue;
+              const float na = (float)g.n[a];
+              float d = *v[a] - bc[a];
+              if (d > 0.5f * na) *v[a] -= na; else if (d < -0.5f * na) *v[a] += na;
+              d = *v[a] - bc[a];
+              if (fabsf(d) > 0.5f * na - H) near_half = 1;
+            }
+            s_cw[s_c0[m] + i] = cc;
+          }
         }
+        if (near_half) atomicOr(&s_mi, 1);
       }
       __syncthreads();
       if (threadIdx.x < n) {
         const int m = threadIdx.x;
-        const float4* cw = s_smem ? s_cw : bs.cworld;
-        const int c0 = s_smem ? s_c0[m] : ps.desc[s_p[m]].c0, c1 = s_smem ? s_c1[m] : ps.desc[s_p[m]].c1;
+        RC_FAST(m, cw, c0, c1, mi)
         const float ex0 = (float)(bi * BRICK), ex1 = fminf((float)((bi + 1) * BRICK), (float)g.n[0]);
         const float ey0 = (float)(bj * BRICK), ey1 = fminf((float)((bj + 1) * BRICK), (float)g.n[1]);
         const float ez0 = (float)(bk * BRICK), ez1 = fminf((float)((bk + 1) * BRICK), (float)g.n[2]);
         const float hx = 0.5f * (ex1 - ex0) - 0.125f, hy = 0.5f * (ey1 - ey0) - 0.125f, hz = 0.5f * (ez1 - ez0) - 0.125f;
         const CellBound bb = bound_at(cw, c0, c1, 0.5f * (ex0 + ex1), 0.5f * (ey0 + ey1), 0.5f * (ez0 + ez1),
-                                      sqrtf(hx * hx + hy * hy + hz * hz), g);
+                                      sqrtf(hx * hx + hy * hy + hz * hz), g, mi);
         s_cls[m] = bb.fmax < 0.999f ? 0 : (bb.fmin > 1.001f ? 1 : 2);
       }
       __syncthreads();
     }
-    // walker mask: mini-brick m (cells 2a..2a+1 etc. of the brick) needs tests unless Eq. 3 stays
-    // below 1 for every candidate within sqrt(3) (the mini-brick) + the walker step margin of its
-    // centre (rigorous bound with a 1e-3 margin, as above)
-    if (threadIdx.x < 64) {
-      const int mb = threadIdx.x;
-      const float xm = (float)(bi * BRICK + 2 * (mb & 3)) + 1.0f, ym = (float)(bj * BRICK + 2 * ((mb >> 2) & 3)) + 1.0f,
-                  zm = (float)(bk * BRICK + 2 * (mb >> 4)) + 1.0f;
-      bool need = s_all != 0;
-      for (int m = 0; m < n && !need; ++m) {
-        const float4* cw = s_smem ? s_cw : bs.cworld;
-        const int c0 = s_smem ? s_c0[m] : ps.desc[s_p[m]].c0, c1 = s_smem ? s_c1[m] : ps.desc[s_p[m]].c1;
-        need = bound_at(cw, c0, c1, xm, ym, zm, 1.7320508f + ps.walk_margin, g).fmax >= 0.999f;
+    // Mini-bricks (2^3 cells; sub-samples within 1.5155 of the centre): one pass per (mini-brick,
+    // candidate) classifies it for the raster (outside / inside / partial) and bounds Eq. 3 within
+    // sqrt(3) + the walker step margin, which sets the walkers' mask bit (rigorous bounds with a
+    // 1e-3 margin, as above).
+    const int ncand = s_all ? ps.P : n;
+    if (!s_all) {
+      for (int pr = threadIdx.x; pr < 64 * n; pr += blockDim.x) {
+        const int mb = pr & 63, m = pr >> 6;
+        int cls = s_cls[m];
+        bool need = cls != 0;
+        if (cls == 2) {
+          const float xm = (float)(bi * BRICK + 2 * (mb & 3)) + 1.0f, ym = (float)(bj * BRICK + 2 * ((mb >> 2) & 3)) + 1.0f,
+                      zm = (float)(bk * BRICK + 2 * (mb >> 4)) + 1.0f;
+          RC_FAST(m, cw, c0, c1, mi)
+          const Bound2 b2 = bound_two(cw, c0, c1, xm, ym, zm, 1.5155444f, 1.7320508f + ps.walk_margin, g, mi);
+          cls = b2.fmax1 < 0.999f ? 0 : (b2.fmin1 > 1.001f ? 1 : 2);
+          need = b2.fmax2 >= 0.999f;
+        } else if (cls == 0) {
+          need = false;   // outside over the whole brick; the walker margin is checked below
+          const float xm = (float)(bi * BRICK + 2 * (mb & 3)) + 1.0f, ym = (float)(bj * BRICK + 2 * ((mb >> 2) & 3)) + 1.0f,
+                      zm = (float)(bk * BRICK + 2 * (mb >> 4)) + 1.0f;
+          RC_FAST(m, cw, c0, c1, mi)
+          need = bound_at(cw, c0, c1, xm, ym, zm, 1.7320508f + ps.walk_margin, g, mi).fmax >= 0.999f;
+        }
+        s_mcls[m][mb] = (unsigned char)(cls | (need ? 4 : 0));
       }
+    }
+    __syncthreads();
+    if (threadIdx.x < 64) {
+      bool need = s_all != 0;
+      for (int m = 0; m < n && !need; ++m) need = (s_mcls[m][threadIdx.x] & 4) != 0;
       const unsigned bal = __ballot_sync(0xffffffffu, need);
       if ((threadIdx.x & 31) == 0) reinterpret_cast<unsigned*>(bs.wmask + b)[threadIdx.x >> 5] = bal;
     }
@@ -367,21 +435,24 @@ __global__ void __launch_bounds__(256) raster_kernel(Geom g, ParticleSet ps, Bri
     int best[2] = {0, 0}, bestp[2] = {-1, -1};
     int qidx[RASTER_PER_THREAD], qm[RASTER_PER_THREAD], qcell[RASTER_PER_THREAD];
     int nq = 0;
-    const int ncand = s_all ? ps.P : n;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int cl = threadIdx.x + h * 256;
-      const int i = bi * BRICK + (cl & 7), j = bj * BRICK + ((cl >> 3) & 7), k = bk * BRICK + (cl >> 6);
+      const int li_x = cl & 7, li_y = (cl >> 3) & 7, li_z = cl >> 6;
+      const int i = bi * BRICK + li_x, j = bj * BRICK + li_y, k = bk * BRICK + li_z;
       if (i >= g.n[0] || j >= g.n[1] || k >= g.n[2]) continue;
+      const int mb = (li_x >> 1) + 4 * (li_y >> 1) + 16 * (li_z >> 1);
       for (int m = 0; m < ncand; ++m) {
-        int p, c0, c1, cls = 2;
+        int p, c0, c1, e0, e1, cls = 2;
+        bool mi = true;
         const float4* cw = bs.cworld;
         if (s_all) {
-          p = m; c0 = ps.desc[p].c0; c1 = ps.desc[p].c1;
+          p = m; c0 = e0 = ps.desc[p].c0; c1 = e1 = ps.desc[p].c1;
         } else {
-          p = s_p[m]; cls = s_cls[m];
-          if (s_smem) { cw = s_cw; c0 = s_c0[m]; c1 = s_c1[m]; }
-          else { c0 = ps.desc[p].c0; c1 = ps.desc[p].c1; }
+          p = s_p[m]; cls = s_mcls[m][mb] & 3;
+          e0 = ps.desc[p].c0; e1 = ps.desc[p].c1;
+          if (s_smem) { cw = s_cw; c0 = s_c0[m]; c1 = s_c1[m]; mi = s_mi != 0; }
+          else { c0 = e0; c1 = e1; }
         }
         if (cls == 0) continue;
         uint64_t mk = 0ull;
@@ -389,7 +460,7 @@ __global__ void __launch_bounds__(256) raster_kernel(Geom g, ParticleSet ps, Bri
           mk = ~0ull;
         } else {
           const CellBound cb = bound_at(cw, c0, c1, (float)i + 0.5f, (float)j + 0.5f, (float)k + 0.5f,
-                                        0.649519053f, g);
+                                        0.649519053f, g, mi);
           if (cb.fmax < 0.999f) continue;
           if (cb.fmin > 1.001f) {
             mk = ~0ull;
@@ -404,7 +475,7 @@ __global__ void __launch_bounds__(256) raster_kernel(Geom g, ParticleSet ps, Bri
               qidx[nq] = slot; qm[nq] = m; qcell[nq] = h; ++nq;
               continue;
             }
-            mk = particle_mask_serial(cw, c0, c1, i, j, k, g);
+            mk = particle_mask_serial(cw, c0, c1, mi, bs.cworld, e0, e1, i, j, k, g);
           }
         }
         const int np = __popcll(mk);
@@ -419,10 +490,10 @@ __global__ void __launch_bounds__(256) raster_kernel(Geom g, ParticleSet ps, Bri
       const uint32_t ent = s_q[e];
       const int cl = ent >> 8, m = ent & 0xff;
       const int i = bi * BRICK + (cl & 7), j = bj * BRICK + ((cl >> 3) & 7), k = bk * BRICK + (cl >> 6);
-      const float4* cw = s_smem ? s_cw : bs.cworld;
-      const int c0 = s_smem ? s_c0[m] : ps.desc[s_p[m]].c0, c1 = s_smem ? s_c1[m] : ps.desc[s_p[m]].c1;
-      const unsigned lo = __ballot_sync(0xffffffffu, subsample_bit(cw, c0, c1, i, j, k, lane, g));
-      const unsigned hi = __ballot_sync(0xffffffffu, subsample_bit(cw, c0, c1, i, j, k, lane + 32, g));
+      RC_FAST(m, cw, c0, c1, mi)
+      RC_EXACT(m, e0, e1)
+      const unsigned lo = __ballot_sync(0xffffffffu, subsample_bit(cw, c0, c1, mi, bs.cworld, e0, e1, i, j, k, lane, g));
+      const unsigned hi = __ballot_sync(0xffffffffu, subsample_bit(cw, c0, c1, mi, bs.cworld, e0, e1, i, j, k, lane + 32, g));
       if (lane == 0) s_qm[e] = ((unsigned long long)hi << 32) | lo;
     }
     __syncthreads();
@@ -446,6 +517,8 @@ __global__ void __launch_bounds__(256) raster_kernel(Geom g, ParticleSet ps, Bri
     }
     __syncthreads();
   }
+#undef RC_FAST
+#undef RC_EXACT
 }
 
 void launch_raster(const Geom& g, const ParticleSet& ps, BrickSet bs, uint16_t* solid,

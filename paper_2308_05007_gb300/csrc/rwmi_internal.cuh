@@ -18,6 +18,7 @@
 //   walkers       pos[2][N] float4 {x, y, z, id bits} (unwrapped), x0[2][N] float4 start
 //                 positions; the second buffers are the counting-sort targets
 //   sort/bin      counts[ncell], offsets[ncell] uint32, rank[N] uint32, block sums
+//   walker list   2 float4 per walker {x, id}, {x_f, slot}: walkers the second pass resolves
 #pragma once
 
 #include <cstdint>
@@ -66,6 +67,7 @@ struct Geom {
   uint32_t ncell_pad;  // direction-plane stride of the population arrays
   // fast division of a flat cell index by nx and nxy: q = (umulhi(v, m) + v) >> s
   uint32_t mx, sx, mxy, sxy;
+  float inv_n[3];      // 1 / n per axis (wrapping; the result is corrected to [0, n))
 };
 
 // Divisor magic for q = (umulhi(v, m) + v) >> s, exact for 0 <= v < 2^31, 1 <= d < 2^31
@@ -162,13 +164,17 @@ __device__ __forceinline__ float metaball_value(const float4* __restrict__ cw, i
   return f;
 }
 
-// Wrap a coordinate into [0, n) on a periodic axis (binary32).
-__device__ __forceinline__ float wrap_coord(float x, float n, int wall) {
+// Wrap a coordinate into [0, n) on a periodic axis (binary32; inv_n = 1/n rounded, the result is
+// corrected once on either side so it always lands in [0, n)).
+__device__ __forceinline__ float wrap_coord(float x, float n, int wall, float inv_n) {
   if (wall) return x;
-  float w = x - n * floorf(x / n);
+  float w = x - n * floorf(x * inv_n);
   if (w >= n) w -= n;
   if (w < 0.0f) w += n;
   return w;
+}
+__device__ __forceinline__ float wrap_coord(float x, float n, int wall) {
+  return wrap_coord(x, n, wall, 1.0f / n);
 }
 
 __device__ __forceinline__ int brick_of(float xw, float yw, float zw, const Geom& g) {
@@ -210,7 +216,7 @@ void launch_init_populations(int q, int storage, const Geom& g, void* f, float r
 void launch_walkers(const Geom& g, const ParticleSet& ps, BrickSet bs1, float4* pos, int64_t n,
                     const float* u, const int64_t* d_T, float D, uint32_t k0, uint32_t k1,
                     unsigned long long* status, unsigned int* ticket, int64_t* d_T_inc,
-                    cudaStream_t st);
+                    float4* list, unsigned int* list_n, int nsm, cudaStream_t st);
 void launch_advance(int64_t* d_T, cudaStream_t st);
 void launch_seed(const Geom& g, const ParticleSet& ps, BrickSet bs, float4* pos, float4* x0,
                  int64_t n, const double lo[3], const double hi[3], uint32_t k0, uint32_t k1,

@@ -9,22 +9,22 @@ namespace rwmi {
 // centres). Periodic axes wrap; on a walled axis the wall plane carries u = 0 and the half cell
 // between wall and first node interpolates linearly to it (the wall corner gets weight 0).
 // ------------------------------------------------------------------------------------------
-__device__ __forceinline__ void axis_weights(float x, int n, int wall, int& i0, int& i1, float& w0,
+// xw: the coordinate wrapped into [0, n) on a periodic axis (unwrapped on a walled axis).
+__device__ __forceinline__ void axis_weights(float xw, int n, int wall, int& i0, int& i1, float& w0,
                                              float& w1) {
   if (!wall) {
-    const float s = x - 0.5f;
+    const float s = xw - 0.5f;
     const float fl = floorf(s);
-    const float w = s - fl;
-    int i = (int)fl % n;
+    w1 = s - fl;
+    w0 = 1.0f - w1;
+    int i = (int)fl;          // -1 .. n-1
     if (i < 0) i += n;
     i0 = i;
     i1 = i + 1 == n ? 0 : i + 1;
-    w0 = 1.0f - w;
-    w1 = w;
     return;
   }
   const float nf = (float)n;
-  x = fminf(fmaxf(x, 0.0f), nf);
+  const float x = fminf(fmaxf(xw, 0.0f), nf);
   if (x < 0.5f) {
     i0 = 0; i1 = 0; w0 = 0.0f; w1 = 2.0f * x;                 // wall (0) .. node 0
   } else if (x >= nf - 0.5f) {
@@ -96,9 +96,9 @@ struct WalkCtx {
 };
 
 __device__ __forceinline__ float f_particle(const WalkCtx& c, int p, const float* x, float* gr) {
-  const float xw = wrap_coord(x[0], (float)c.g.n[0], c.g.wall[0]);
-  const float yw = wrap_coord(x[1], (float)c.g.n[1], c.g.wall[1]);
-  const float zw = wrap_coord(x[2], (float)c.g.n[2], c.g.wall[2]);
+  const float xw = wrap_coord(x[0], (float)c.g.n[0], c.g.wall[0], c.g.inv_n[0]);
+  const float yw = wrap_coord(x[1], (float)c.g.n[1], c.g.wall[1], c.g.inv_n[1]);
+  const float zw = wrap_coord(x[2], (float)c.g.n[2], c.g.wall[2], c.g.inv_n[2]);
   const ParticleDesc& d = c.ps.desc[p];
   if (gr) return metaball_grad(c.bs.cworld, d.c0, d.c1, xw, yw, zw, c.g, gr, gr + 1, gr + 2);
   return metaball_value(c.bs.cworld, d.c0, d.c1, xw, yw, zw, c.g);
@@ -106,9 +106,9 @@ __device__ __forceinline__ float f_particle(const WalkCtx& c, int p, const float
 
 // Lowest-index particle holding x (any particle; bound-radius skip), or -1.
 __device__ int inside_any(const WalkCtx& c, const float* x) {
-  const float xw = wrap_coord(x[0], (float)c.g.n[0], c.g.wall[0]);
-  const float yw = wrap_coord(x[1], (float)c.g.n[1], c.g.wall[1]);
-  const float zw = wrap_coord(x[2], (float)c.g.n[2], c.g.wall[2]);
+  const float xw = wrap_coord(x[0], (float)c.g.n[0], c.g.wall[0], c.g.inv_n[0]);
+  const float yw = wrap_coord(x[1], (float)c.g.n[1], c.g.wall[1], c.g.inv_n[1]);
+  const float zw = wrap_coord(x[2], (float)c.g.n[2], c.g.wall[2], c.g.inv_n[2]);
   for (int p = 0; p < c.ps.P; ++p) {
     const PoseF& pp = c.bs.pose[p];
     const float dx = min_image_rn(xw - pp.o[0], (float)c.g.n[0], c.g.wall[0]);
@@ -186,119 +186,188 @@ __device__ bool refill(const WalkCtx& c, int p, const float* x, uint32_t id, uin
   return true;
 }
 
-// One thread per walker: Eq. 2 with dt = 1, walls, then the type I-IV rules against the
-// particles at t+1 (candidates from the walker's brick; rare paths test all particles).
-__global__ void __launch_bounds__(256) walker_kernel(WalkCtx c, float4* __restrict__ pos, int64_t n,
-                                                     const float* __restrict__ u,
-                                                     const int64_t* __restrict__ d_T, float amp,
-                                                     uint32_t k0, uint32_t k1,
-                                                     unsigned long long* __restrict__ status,
-                                                     unsigned int* ticket, int64_t* d_T_inc) {
+// Rare path of a walker step (kept out of line so the common path keeps its registers): types
+// II-IV against the particles at t+1 (candidates of the walker's brick, or all particles when the
+// list overflowed or the step was unusually long). Returns event bits: 1 II, 2 III, 4 IV,
+// 8 Algorithm 1 failure, 16 refill failure; writes the new position to xn.
+__device__ __noinline__ unsigned resolve_particles(const WalkCtx& c, const float* x, const float* xf, float xw,
+                                                   float yw, float zw, int b, uint32_t nc, bool far_step,
+                                                   uint32_t id, uint32_t T, float amp, uint32_t k0, uint32_t k1,
+                                                   float* xn) {
+  unsigned ev = 0u;
+  int pin = -1, qin = -1;
+  if (nc > MAXC || far_step) {
+    pin = inside_any(c, x);
+    qin = inside_any(c, xf);
+  } else {
+    const float xfw = wrap_coord(xf[0], (float)c.g.n[0], c.g.wall[0], c.g.inv_n[0]);
+    const float yfw = wrap_coord(xf[1], (float)c.g.n[1], c.g.wall[1], c.g.inv_n[1]);
+    const float zfw = wrap_coord(xf[2], (float)c.g.n[2], c.g.wall[2], c.g.inv_n[2]);
+    for (uint32_t m = 0; m < nc; ++m) {
+      const int p = c.bs.bcand[b * MAXC + m] & 0x7fff;
+      const ParticleDesc& d = c.ps.desc[p];
+      if ((pin < 0 || p < pin) && metaball_value(c.bs.cworld, d.c0, d.c1, xw, yw, zw, c.g) >= 1.0f) pin = p;
+      if ((qin < 0 || p < qin) && metaball_value(c.bs.cworld, d.c0, d.c1, xfw, yfw, zfw, c.g) >= 1.0f) qin = p;
+    }
+  }
+  if (pin >= 0 && qin >= 0) {            // type II: Dirichlet refill
+    ev |= 1u;
+    if (!refill(c, pin, x, id, T, amp, k0, k1, xn)) ev |= 16u;
+  } else if (pin >= 0) {                 // type III: moves out freely
+    ev |= 2u;
+  } else if (qin >= 0) {                 // type IV: Algorithms 1 and 2
+    ev |= 4u;
+    float xi[3];
+    if (!bisect(c, qin, x, xf, xi, nullptr)) {
+      ev |= 8u;
+      xn[0] = x[0]; xn[1] = x[1]; xn[2] = x[2];
+    } else {
+      float gr[3];
+      f_particle(c, qin, xi, gr);
+      const float gn = sqrtf(gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2]);
+      const float nv[3] = {gr[0] / gn, gr[1] / gn, gr[2] / gn};
+      const float ti[3] = {xf[0] - xi[0], xf[1] - xi[1], xf[2] - xi[2]};
+      const float tn = ti[0] * nv[0] + ti[1] * nv[1] + ti[2] * nv[2];
+      float tr[3];
+      for (int a = 0; a < 3; ++a) tr[a] = xi[a] + (ti[a] - 2.0f * tn * nv[a]);
+      if (beyond_wall(tr, c.g) || inside_any(c, tr) >= 0) {
+        xn[0] = x[0]; xn[1] = x[1]; xn[2] = x[2];
+      } else {
+        xn[0] = tr[0]; xn[1] = tr[1]; xn[2] = tr[2];
+      }
+    }
+  }
+  return ev;
+}
+
+// Pass 1, one thread per walker: Eq. 2 with dt = 1 (trilinear u, Philox + Box-Muller) and the
+// walls. A walker whose mini-brick may meet a particle at t+1 (or whose list overflowed, or whose
+// step was unusually long) is appended to a compact list instead of being written back; pass 2
+// resolves those at full SIMT width, so this kernel carries none of the rare-path code.
+__global__ void __launch_bounds__(256, 4) walker_kernel(WalkCtx c, float4* __restrict__ pos, int64_t n,
+                                                        const float* __restrict__ u,
+                                                        const int64_t* __restrict__ d_T, float amp,
+                                                        uint32_t k0, uint32_t k1,
+                                                        unsigned long long* __restrict__ status,
+                                                        float4* __restrict__ list, unsigned int* list_n) {
   const int64_t T = *d_T;
   const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  // per-walker events, counted once per warp (one atomic per event kind and warp)
-  bool ev_type2 = false, ev_type3 = false, ev_type4 = false, ev_bisect = false, ev_refill = false,
-       ev_wall = false, ev_fast = false, ev_nonfinite = false;
+  bool ev_wall = false, ev_fast = false, ev_nonfinite = false, flagged = false;
+  float4 ea = make_float4(0.f, 0.f, 0.f, 0.f), eb = ea;
   if (w < n) {
     const float4 p4 = pos[w];
     const uint32_t id = __float_as_uint(p4.w);
     const float x[3] = {p4.x, p4.y, p4.z};
+    const float xw = wrap_coord(x[0], (float)c.g.n[0], c.g.wall[0], c.g.inv_n[0]);
+    const float yw = wrap_coord(x[1], (float)c.g.n[1], c.g.wall[1], c.g.inv_n[1]);
+    const float zw = wrap_coord(x[2], (float)c.g.n[2], c.g.wall[2], c.g.inv_n[2]);
     float ux, uy, uz;
-    interp_velocity(u, c.g, x[0], x[1], x[2], ux, uy, uz);
+    interp_velocity(u, c.g, xw, yw, zw, ux, uy, uz);
     const uint4 r = philox(make_uint4(id, (uint32_t)T, 0u, 0u), k0, k1);
-    const float rad01 = sqrtf(-2.0f * logf(uniform24(r.x)));
-    const float rad23 = sqrtf(-2.0f * logf(uniform24(r.z)));
-    float s1, c1;
-    sincospif(2.0f * uniform24(r.y), &s1, &c1);
-    const float c3 = cospif(2.0f * uniform24(r.w));
+    // Box-Muller with the fast intrinsics: ln and sin/cos to ~1e-6 absolute, far below the
+    // 2e-5 per-step tolerance; angle 2 pi U = pi + theta with theta = 2 pi (U - 1/2) in (-pi, pi)
+    const float rad01 = sqrtf(-2.0f * __logf(uniform24(r.x)));
+    const float rad23 = sqrtf(-2.0f * __logf(uniform24(r.z)));
+    float s1, c1, s3, c3;
+    __sincosf(6.2831853f * (uniform24(r.y) - 0.5f), &s1, &c1);
+    __sincosf(6.2831853f * (uniform24(r.w) - 0.5f), &s3, &c3);
+    s1 = -s1; c1 = -c1; c3 = -c3;
     float xf[3] = {x[0] + ux + amp * (rad01 * c1), x[1] + uy + amp * (rad01 * s1),
                    x[2] + uz + amp * (rad23 * c3)};
     if (!wall_reflect(xf, c.g)) ev_wall = true;
-    float xn[3] = {xf[0], xf[1], xf[2]};
     if (c.ps.P > 0) {
       const float step2 = (xf[0] - x[0]) * (xf[0] - x[0]) + (xf[1] - x[1]) * (xf[1] - x[1]) +
                           (xf[2] - x[2]) * (xf[2] - x[2]);
-      const float xw = wrap_coord(x[0], (float)c.g.n[0], c.g.wall[0]);
-      const float yw = wrap_coord(x[1], (float)c.g.n[1], c.g.wall[1]);
-      const float zw = wrap_coord(x[2], (float)c.g.n[2], c.g.wall[2]);
       const int b = brick_of(xw, yw, zw, c.g);
-      uint32_t nc = c.bs.bword[b] & 0xffffu;
+      const uint32_t nc = c.bs.bword[b] & 0xffffu;
+      bool need = nc > MAXC;
       if (nc > 0 && nc <= MAXC) {   // mini-brick of x: cells (2a, 2a+1) along each axis of the brick
         const int ix = min(max((int)floorf(xw), 0), c.g.n[0] - 1), iy = min(max((int)floorf(yw), 0), c.g.n[1] - 1),
                   iz = min(max((int)floorf(zw), 0), c.g.n[2] - 1);
         const int mb = ((ix & 7) >> 1) + 4 * ((iy & 7) >> 1) + 16 * ((iz & 7) >> 1);
-        if (!((c.bs.wmask[b] >> mb) & 1ull)) nc = 0;   // no particle can be met within the step
+        need = (c.bs.wmask[b] >> mb) & 1ull;
       }
-      const bool far_step = step2 > c.ps.walk_margin * c.ps.walk_margin;
-      ev_fast = far_step;
-      if (nc > 0 || far_step) {
-        int pin = -1, qin = -1;
-        if (nc > MAXC || far_step) {
-          pin = inside_any(c, x);
-          qin = inside_any(c, xf);
-        } else {
-          const float xfw = wrap_coord(xf[0], (float)c.g.n[0], c.g.wall[0]);
-          const float yfw = wrap_coord(xf[1], (float)c.g.n[1], c.g.wall[1]);
-          const float zfw = wrap_coord(xf[2], (float)c.g.n[2], c.g.wall[2]);
-          for (uint32_t m = 0; m < nc; ++m) {
-            const int p = c.bs.bcand[b * MAXC + m] & 0x7fff;
-            const ParticleDesc& d = c.ps.desc[p];
-            if ((pin < 0 || p < pin) && metaball_value(c.bs.cworld, d.c0, d.c1, xw, yw, zw, c.g) >= 1.0f) pin = p;
-            if ((qin < 0 || p < qin) && metaball_value(c.bs.cworld, d.c0, d.c1, xfw, yfw, zfw, c.g) >= 1.0f) qin = p;
-          }
-        }
-        if (pin >= 0 && qin >= 0) {            // type II: Dirichlet refill
-          ev_type2 = true;
-          if (!refill(c, pin, x, id, (uint32_t)T, amp, k0, k1, xn)) ev_refill = true;
-        } else if (pin >= 0) {                 // type III: moves out freely
-          ev_type3 = true;
-        } else if (qin >= 0) {                 // type IV: Algorithms 1 and 2
-          ev_type4 = true;
-          float xi[3];
-          if (!bisect(c, qin, x, xf, xi, nullptr)) {
-            ev_bisect = true;
-            xn[0] = x[0]; xn[1] = x[1]; xn[2] = x[2];
-          } else {
-            float gr[3];
-            f_particle(c, qin, xi, gr);
-            const float gn = sqrtf(gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2]);
-            const float nv[3] = {gr[0] / gn, gr[1] / gn, gr[2] / gn};
-            const float ti[3] = {xf[0] - xi[0], xf[1] - xi[1], xf[2] - xi[2]};
-            const float tn = ti[0] * nv[0] + ti[1] * nv[1] + ti[2] * nv[2];
-            float tr[3];
-            for (int a = 0; a < 3; ++a) tr[a] = xi[a] + (ti[a] - 2.0f * tn * nv[a]);
-            if (beyond_wall(tr, c.g) || inside_any(c, tr) >= 0) {
-              xn[0] = x[0]; xn[1] = x[1]; xn[2] = x[2];
-            } else {
-              xn[0] = tr[0]; xn[1] = tr[1]; xn[2] = tr[2];
-            }
-          }
-        }
-      }
+      ev_fast = step2 > c.ps.walk_margin * c.ps.walk_margin;
+      flagged = need || ev_fast;
     }
     ev_nonfinite = !(isfinite(ux) && isfinite(uy) && isfinite(uz));
-    pos[w] = make_float4(xn[0], xn[1], xn[2], p4.w);
+    if (!flagged) {
+      pos[w] = make_float4(xf[0], xf[1], xf[2], p4.w);
+    } else {
+      ea = make_float4(x[0], x[1], x[2], p4.w);
+      eb = make_float4(xf[0], xf[1], xf[2], __uint_as_float((uint32_t)w));
+    }
   }
-  {
-    const unsigned full = 0xffffffffu;
-    const bool evs[8] = {ev_type2, ev_type3, ev_type4, ev_bisect, ev_refill, ev_wall, ev_fast, ev_nonfinite};
-    const int slot[8] = {ST_TYPE2, ST_TYPE3, ST_TYPE4, ST_BISECT_FAIL, ST_REFILL_FAIL, ST_WALL_FAIL,
-                         ST_FAST_SPEED, ST_NONFINITE};
+  const unsigned full = 0xffffffffu;
+  const unsigned fl = __ballot_sync(full, flagged);
+  if (fl) {   // one list reservation per warp
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(fl) - 1;
+    unsigned base = 0;
+    if (lane == leader) base = atomicAdd(list_n, (unsigned)__popc(fl));
+    base = __shfl_sync(full, base, leader);
+    if (flagged) {
+      const unsigned slot = base + __popc(fl & ((1u << lane) - 1u));
+      list[2 * (size_t)slot] = ea;
+      list[2 * (size_t)slot + 1] = eb;
+    }
+  }
+  if (__any_sync(full, ev_wall | ev_fast | ev_nonfinite)) {
+    const bool evs[3] = {ev_wall, ev_fast, ev_nonfinite};
+    const int slot[3] = {ST_WALL_FAIL, ST_FAST_SPEED, ST_NONFINITE};
 #pragma unroll
-    for (int m = 0; m < 8; ++m) {
+    for (int m = 0; m < 3; ++m) {
       const unsigned bal = __ballot_sync(full, evs[m]);
       if (bal && (threadIdx.x & 31) == 0) atomicAdd(&status[slot[m]], (unsigned long long)__popc(bal));
     }
   }
-  // the last warp to finish advances the device step counter (every warp has read T by then)
-  if (d_T_inc && (threadIdx.x & 31) == 0) {
-    __threadfence();
+}
+
+// Pass 2 (fixed grid, grid-stride over the list): types II-IV of the flagged walkers, written back
+// to their slots. The last warp to finish advances the device step counter and empties the list
+// (every warp has read both by then).
+__global__ void __launch_bounds__(256, 2) walker_resolve_kernel(WalkCtx c, float4* __restrict__ pos,
+                                                             const float4* __restrict__ list,
+                                                             unsigned int* list_n, const int64_t* d_T,
+                                                             float amp, uint32_t k0, uint32_t k1,
+                                                             unsigned long long* __restrict__ status,
+                                                             unsigned int* ticket, int64_t* d_T_inc) {
+  const int64_t T = *d_T;
+  const unsigned cnt = *list_n;
+  unsigned ev_all[5] = {0u, 0u, 0u, 0u, 0u};
+  const unsigned stride = gridDim.x * blockDim.x;
+  for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += stride) {
+    const float4 a = list[2 * (size_t)e], bq = list[2 * (size_t)e + 1];
+    const float x[3] = {a.x, a.y, a.z}, xf[3] = {bq.x, bq.y, bq.z};
+    const uint32_t id = __float_as_uint(a.w);
+    const uint32_t w = __float_as_uint(bq.w);
+    const float xw = wrap_coord(x[0], (float)c.g.n[0], c.g.wall[0], c.g.inv_n[0]);
+    const float yw = wrap_coord(x[1], (float)c.g.n[1], c.g.wall[1], c.g.inv_n[1]);
+    const float zw = wrap_coord(x[2], (float)c.g.n[2], c.g.wall[2], c.g.inv_n[2]);
+    const int b = brick_of(xw, yw, zw, c.g);
+    const uint32_t nc = c.bs.bword[b] & 0xffffu;
+    const float step2 = (xf[0] - x[0]) * (xf[0] - x[0]) + (xf[1] - x[1]) * (xf[1] - x[1]) +
+                        (xf[2] - x[2]) * (xf[2] - x[2]);
+    const bool far_step = step2 > c.ps.walk_margin * c.ps.walk_margin;
+    float xn[3] = {xf[0], xf[1], xf[2]};
+    const unsigned ev = resolve_particles(c, x, xf, xw, yw, zw, b, nc, far_step, id, (uint32_t)T, amp, k0, k1, xn);
+    pos[w] = make_float4(xn[0], xn[1], xn[2], a.w);
+    for (int m = 0; m < 5; ++m) ev_all[m] += (ev >> m) & 1u;
+  }
+  const int slot[5] = {ST_TYPE2, ST_TYPE3, ST_TYPE4, ST_BISECT_FAIL, ST_REFILL_FAIL};
+  for (int m = 0; m < 5; ++m) {
+    unsigned v = ev_all[m];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(&status[slot[m]], (unsigned long long)v);
+  }
+  if ((threadIdx.x & 31) == 0) {
     const unsigned int nwarps = gridDim.x * (blockDim.x >> 5);
     const unsigned int done = atomicAdd(ticket, 1u);
     if (done == nwarps - 1) {
-      *d_T_inc = T + 1;
+      *list_n = 0u;
+      if (d_T_inc) *d_T_inc = T + 1;
       *ticket = 0u;
-      __threadfence();
     }
   }
 }
@@ -306,11 +375,12 @@ __global__ void __launch_bounds__(256) walker_kernel(WalkCtx c, float4* __restri
 void launch_walkers(const Geom& g, const ParticleSet& ps, BrickSet bs1, float4* pos, int64_t n,
                     const float* u, const int64_t* d_T, float D, uint32_t k0, uint32_t k1,
                     unsigned long long* status, unsigned int* ticket, int64_t* d_T_inc,
-                    cudaStream_t st) {
+                    float4* list, unsigned int* list_n, int nsm, cudaStream_t st) {
   WalkCtx c{g, ps, bs1};
   const int64_t blocks = (n + 255) / 256;
-  walker_kernel<<<(unsigned)blocks, 256, 0, st>>>(c, pos, n, u, d_T, sqrtf(2.0f * D), k0, k1,
-                                                  status, ticket, d_T_inc);
+  const float amp = sqrtf(2.0f * D);
+  walker_kernel<<<(unsigned)blocks, 256, 0, st>>>(c, pos, n, u, d_T, amp, k0, k1, status, list, list_n);
+  walker_resolve_kernel<<<nsm * 2, 256, 0, st>>>(c, pos, list, list_n, d_T, amp, k0, k1, status, ticket, d_T_inc);
 }
 
 __global__ void advance_kernel(int64_t* d_T) { *d_T += 1; }
@@ -384,9 +454,15 @@ __device__ __forceinline__ uint32_t walker_cell(const float4& p, const Geom& g) 
   int c[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
+    // floor of the unwrapped coordinate, then its residue mod n (the exact integer wrap of Eq. 16)
     int i = (int)floorf(x[a]);
-    if (g.wall[a]) i = min(max(i, 0), g.n[a] - 1);
-    else { i %= g.n[a]; if (i < 0) i += g.n[a]; }
+    if (g.wall[a]) {
+      i = min(max(i, 0), g.n[a] - 1);
+    } else {
+      i -= g.n[a] * (int)floorf((float)i * g.inv_n[a]);
+      if (i >= g.n[a]) i -= g.n[a];
+      if (i < 0) i += g.n[a];
+    }
     c[a] = i;
   }
   return ((uint32_t)c[2] * g.n[1] + c[1]) * g.n[0] + c[0];

@@ -141,7 +141,10 @@ def test_parity_single_full_length(q):
         np.abs(sim.concentration().astype(int) - ora.concentration().astype(int)).sum() <= 2 * (cg != co).sum()
     m_g, m_o = sim.walker_moments(), ora.moments()
     assert m_g[0] == m_o[0]
-    assert np.allclose(m_g[1:], m_o[1:], rtol=1e-4, atol=1e-6)
+    # up to 1e-3 N walkers may take the other branch at a surface test, each moving by at most
+    # a few step lengths (~0.2): means within 2e-4, variances within 1e-3 relative
+    assert np.allclose(m_g[[1, 2, 3, 7, 8, 9]], m_o[[1, 2, 3, 7, 8, 9]], rtol=1e-4, atol=2e-4)
+    assert np.allclose(m_g[[4, 5, 6, 10, 11, 12]], m_o[[4, 5, 6, 10, 11, 12]], rtol=1e-3)
     fg, fo = sim.particle_forces(), ora.forces()
     assert np.allclose(fg[:, :3], fo[:, :3], rtol=1e-3, atol=1e-3 * np.abs(fo[:, :3]).max())
 
