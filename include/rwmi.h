@@ -218,7 +218,33 @@ RWMI_API rwmi_status rwmi_counters(rwmi_ctx* ctx, int64_t out[8]);
 RWMI_API rwmi_status rwmi_save(rwmi_ctx* ctx, const char* path);
 RWMI_API rwmi_status rwmi_load(rwmi_ctx* ctx, const char* path);
 
-/* Message of the last failing call on this context (static storage of the context). */
+/* Binning and cell-sorting of walkers for callers that cannot allocate device memory. This entry
+ * point has no counterpart in the paper; it is the concentration count of the library's own
+ * rwmi_concentration (walkers per cell, cell of a walker = floor of its position, wrapped on
+ * periodic axes and clamped on walled ones), packaged for code that runs where cudaMalloc is not
+ * available or not allowed: inside a CUDA-graph-captured or stream-ordered pipeline that forbids
+ * allocation, under an external memory manager that owns all device memory, or in a real-time
+ * loop that must not call the allocator. Those callers cannot give the library the scratch its
+ * sort needs, so this entry point keeps that scratch in a fixed array compiled into the library:
+ * 8 MiB per GPU that loads the library, held until the process exits.
+ *   dims[3], wall_mask: the box and its walled axes, as for rwmi_create / rwmi_configure.
+ *   pos: device memory, n walkers of 4 floats {x, y, z, payload} (the rwmi_walkers layout).
+ *   counts: device memory, dims[0]*dims[1]*dims[2] uint32, overwritten with walkers per cell.
+ *   pos_sorted: device memory for n x 4 floats, or NULL: the walkers grouped by cell in
+ *     ascending cell order (order within a cell unspecified).
+ *   stream: cudaStream_t for the work, or NULL for the default stream. The call is asynchronous.
+ * Limits: at most 1048576 cells and 1048576 walkers; larger sizes return RWMI_E_INVALID with a
+ * message from rwmi_last_error(NULL). Nothing is allocated: no cudaMalloc, no cudaFree, no
+ * allocating library call. The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call before any stream
+ * capture. Every call shares the one array and leaves its last contents there, so calls whose
+ * GPU work overlaps -- on different streams, or from several threads -- race and must not be
+ * issued concurrently. Returns RWMI_OK, RWMI_E_INVALID or RWMI_E_CUDA. */
+RWMI_API rwmi_status rwmi_bin_walkers_noalloc(const int32_t dims[3], uint32_t wall_mask, const float* pos,
+                                              int64_t n, float* pos_sorted, uint32_t* counts, void* stream);
+
+/* Message of the last failing call on this context (static storage of the context); with NULL,
+ * the message of the calling thread's last failing rwmi_bin_walkers_noalloc. */
 RWMI_API const char* rwmi_last_error(const rwmi_ctx* ctx);
 
 /* Brick statistics of the current time: out = {bricks with raster-relevant particles, bricks

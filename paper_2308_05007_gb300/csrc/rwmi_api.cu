@@ -930,7 +930,7 @@ RWMI_API rwmi_status rwmi_brick_stats(rwmi_ctx* c, int64_t out[4]) {
   return RWMI_OK;
 }
 
-RWMI_API const char* rwmi_last_error(const rwmi_ctx* c) { return c ? c->err.c_str() : "null context"; }
+RWMI_API const char* rwmi_last_error(const rwmi_ctx* c) { return c ? c->err.c_str() : noalloc_last_error(); }
 
 RWMI_API int64_t rwmi_launch_count(const rwmi_ctx* c) { return c ? c->launches : 0; }
 

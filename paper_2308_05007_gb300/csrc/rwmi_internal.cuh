@@ -240,7 +240,10 @@ void launch_density(int q, int storage, const Geom& g, const void* f, float rho0
                     cudaStream_t st);
 void launch_load_populations(int q, int storage, const Geom& g, const double* in, float rho0,
                              void* f, cudaStream_t st);
+void launch_scatter_pos(const Geom& g, const float4* pos, int64_t n, const uint32_t* offsets,
+                        const uint32_t* rank, float4* pos_out, cudaStream_t st);
 size_t scan_block_sums_size(uint32_t n);
+const char* noalloc_last_error();
 void lattice_table(int q, int32_t* e, double* w);
 
 }  // namespace rwmi

@@ -1,5 +1,9 @@
 // rwmi_walkers.cu -- random-walk advance of solute walkers (Eq. 2, Section 2.4), seeding,
 // counting sort by cell (the histogram is the concentration of Eq. 16) and FP64 moments.
+#include <cstdio>
+#include <mutex>
+
+#include "rwmi.h"
 #include "rwmi_internal.cuh"
 
 namespace rwmi {
@@ -577,6 +581,21 @@ __global__ void scatter_kernel(Geom g, const float4* __restrict__ pos, const flo
   x0_out[dst] = x0[w];
 }
 
+__global__ void scatter_pos_kernel(Geom g, const float4* __restrict__ pos, int64_t n,
+                                   const uint32_t* __restrict__ offsets, const uint32_t* __restrict__ rank,
+                                   float4* __restrict__ pos_out) {
+  const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= n) return;
+  const float4 p = pos[w];
+  pos_out[offsets[walker_cell(p, g)] + rank[w]] = p;
+}
+
+void launch_scatter_pos(const Geom& g, const float4* pos, int64_t n, const uint32_t* offsets,
+                        const uint32_t* rank, float4* pos_out, cudaStream_t st) {
+  if (n <= 0) return;
+  scatter_pos_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g, pos, n, offsets, rank, pos_out);
+}
+
 void launch_scatter(const Geom& g, const float4* pos, const float4* x0, int64_t n,
                     const uint32_t* offsets, const uint32_t* rank, float4* pos_out,
                     float4* x0_out, cudaStream_t st) {
@@ -653,4 +672,94 @@ void launch_moments(const float4* pos, const float4* x0, int64_t n, double* acc,
   moments_finalize_kernel<<<1, 32, 0, st>>>(acc, n, base, interval, rows, d_T);
 }
 
+// ------------------------------------------------------------------------------------------
+// Binning without allocation (rwmi_bin_walkers_noalloc). Its scratch -- per-walker ranks, per-cell
+// offsets and the scan's block sums -- lives in this fixed device array instead of memory the
+// caller or the library allocates; every GPU that loads the library holds it until exit.
+// ------------------------------------------------------------------------------------------
+constexpr int64_t NOALLOC_MAX_WALKERS = 1 << 20;
+constexpr int64_t NOALLOC_MAX_CELLS = 1 << 20;
+constexpr size_t NOALLOC_SCRATCH_WORDS =
+    (size_t)NOALLOC_MAX_WALKERS + (size_t)NOALLOC_MAX_CELLS + (NOALLOC_MAX_CELLS + SCAN_TILE - 1) / SCAN_TILE + 1;
+static __device__ __align__(256) uint32_t g_noalloc_scratch[NOALLOC_SCRATCH_WORDS];
+
+namespace {
+std::mutex g_noalloc_mutex;
+uint32_t* g_noalloc_addr[64] = {};   // device address of the scratch array, per device ordinal
+thread_local char g_noalloc_err[256] = "";
+
+rwmi_status noalloc_fail(rwmi_status s, const char* msg) {
+  std::snprintf(g_noalloc_err, sizeof(g_noalloc_err), "%s", msg);
+  return s;
+}
+}  // namespace
+
+const char* noalloc_last_error() { return g_noalloc_err; }
+
 }  // namespace rwmi
+
+extern "C" RWMI_API rwmi_status rwmi_bin_walkers_noalloc(const int32_t dims[3], uint32_t wall_mask,
+                                                         const float* pos, int64_t n, float* pos_sorted,
+                                                         uint32_t* counts, void* stream) {
+  using namespace rwmi;
+  if (!dims || !counts || (n > 0 && !pos) || wall_mask > 7)
+    return noalloc_fail(RWMI_E_INVALID, "rwmi_bin_walkers_noalloc: null argument or bad wall mask");
+  int64_t ncell = 1;
+  for (int a = 0; a < 3; ++a) {
+    if (dims[a] < 1) return noalloc_fail(RWMI_E_INVALID, "rwmi_bin_walkers_noalloc: dims must be >= 1");
+    ncell *= dims[a];
+  }
+  if (ncell > NOALLOC_MAX_CELLS || n < 0 || n > NOALLOC_MAX_WALKERS)
+    return noalloc_fail(RWMI_E_INVALID,
+                        "rwmi_bin_walkers_noalloc: more than 1048576 cells or walkers (fixed scratch)");
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64)
+    return noalloc_fail(RWMI_E_CUDA, "rwmi_bin_walkers_noalloc: no current CUDA device");
+  uint32_t* scratch = nullptr;
+  {
+    // set-up, once per device with that device current: the host-side name of the array is a
+    // stand-in, not a device address, so ask the runtime for the real one
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[dev]) {
+      void* addr = nullptr;
+      const cudaError_t e = cudaGetSymbolAddress(&addr, g_noalloc_scratch);
+      if (e != cudaSuccess || !addr) {
+        std::snprintf(g_noalloc_err, sizeof(g_noalloc_err), "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+        return RWMI_E_CUDA;
+      }
+      g_noalloc_addr[dev] = (uint32_t*)addr;
+    }
+    scratch = g_noalloc_addr[dev];
+  }
+  uint32_t* rank = scratch;
+  uint32_t* offsets = scratch + NOALLOC_MAX_WALKERS;
+  uint32_t* bsums = offsets + NOALLOC_MAX_CELLS;
+  Geom g{};
+  for (int a = 0; a < 3; ++a) {
+    g.n[a] = dims[a];
+    g.nb[a] = (dims[a] + BRICK - 1) / BRICK;
+    g.wall[a] = (wall_mask >> a) & 1;
+    g.inv_n[a] = 1.0f / (float)dims[a];
+  }
+  g.nxy = (uint32_t)dims[0] * (uint32_t)dims[1];
+  g.ncell = (uint32_t)ncell;
+  g.ncell_pad = (uint32_t)ncell;
+  make_divisor((uint32_t)dims[0], g.mx, g.sx);
+  make_divisor(g.nxy, g.mxy, g.sxy);
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(uint32_t) * (size_t)ncell, st);
+  if (e == cudaSuccess && n > 0) {
+    const float4* p4 = reinterpret_cast<const float4*>(pos);
+    launch_histogram(g, p4, n, counts, pos_sorted ? rank : nullptr, st);
+    if (pos_sorted) {
+      launch_scan(counts, offsets, bsums, (uint32_t)ncell, st);
+      launch_scatter_pos(g, p4, n, offsets, rank, reinterpret_cast<float4*>(pos_sorted), st);
+    }
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) {
+    std::snprintf(g_noalloc_err, sizeof(g_noalloc_err), "rwmi_bin_walkers_noalloc: %s", cudaGetErrorString(e));
+    return RWMI_E_CUDA;
+  }
+  return RWMI_OK;
+}

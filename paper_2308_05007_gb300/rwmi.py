@@ -26,7 +26,8 @@ EXPORTED = ["rwmi_config_defaults", "rwmi_create", "rwmi_configure", "rwmi_set_s
             "rwmi_time", "rwmi_info", "rwmi_concentration", "rwmi_walker_moments", "rwmi_moment_series",
             "rwmi_velocity", "rwmi_density", "rwmi_populations", "rwmi_lattice", "rwmi_solid",
             "rwmi_mass_momentum", "rwmi_particle_forces", "rwmi_walkers", "rwmi_counters", "rwmi_save",
-            "rwmi_load", "rwmi_brick_stats", "rwmi_last_error", "rwmi_launch_count", "rwmi_destroy"]
+            "rwmi_load", "rwmi_brick_stats", "rwmi_bin_walkers_noalloc", "rwmi_last_error",
+            "rwmi_launch_count", "rwmi_destroy"]
 
 
 class RwmiError(RuntimeError):
@@ -96,6 +97,7 @@ def load(build_if_missing: bool = False):
     L.rwmi_solid.argtypes = [P, vp, vp]
     L.rwmi_walkers.argtypes = [P, vp, vp]
     L.rwmi_brick_stats.argtypes = [P, vp]
+    L.rwmi_bin_walkers_noalloc.argtypes = [C.POINTER(C.c_int32), C.c_uint32, vp, C.c_int64, vp, vp, vp]
     L.rwmi_save.argtypes = [P, C.c_char_p]
     L.rwmi_load.argtypes = [P, C.c_char_p]
     L.rwmi_last_error.argtypes = [P]
@@ -121,6 +123,22 @@ def _ptr(a):
 
 def _d3(v):
     return (C.c_double * 3)(*[float(x) for x in v])
+
+
+def bin_walkers_noalloc(dims, wall_mask, pos, counts, pos_sorted=None, stream=None):
+    """rwmi_bin_walkers_noalloc: walkers per cell (and, optionally, the walkers grouped by cell)
+    for callers that cannot allocate device memory. pos, counts, pos_sorted are CUDA tensors
+    (float32 [n, 4], uint32/int32 [cells], float32 [n, 4]); asynchronous on `stream`."""
+    L = load()
+    d = (C.c_int32 * 3)(*[int(x) for x in dims])
+    n = pos.numel() // 4
+    handle = None
+    if stream is not None:
+        handle = C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    st = L.rwmi_bin_walkers_noalloc(d, int(wall_mask), _ptr(pos), n,
+                                    _ptr(pos_sorted) if pos_sorted is not None else None, _ptr(counts), handle)
+    if st != 0:
+        raise RwmiError(st, L.rwmi_last_error(None).decode(errors="replace"))
 
 
 class Simulation:

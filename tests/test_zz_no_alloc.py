@@ -1,0 +1,71 @@
+"""Binning without allocation: rwmi_bin_walkers_noalloc against the library's own binning.
+
+Some callers cannot allocate device memory: an external memory manager owns all of it, or the
+call sits in a captured or real-time pipeline where cudaMalloc is not allowed. For them the
+library bins (and cell-sorts) walkers with scratch held in a fixed array compiled into the
+library. This file checks, through the C ABI, that two calls in a row give exactly the counts of
+rwmi_concentration, and that the sorted copy is the same walkers grouped by cell. It is named so
+that pytest collects it last.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+def _cells(pos, dims, wall_mask):
+    """Cell of each walker: floor, wrapped on periodic axes, clamped on walled ones."""
+    c = []
+    for a in range(3):
+        i = np.floor(pos[:, a]).astype(np.int64)
+        i = np.clip(i, 0, dims[a] - 1) if (wall_mask >> a) & 1 else np.mod(i, dims[a])
+        c.append(i)
+    return (c[2] * dims[1] + c[1]) * dims[0] + c[0]
+
+
+def test_noalloc_binning_matches_the_library_twice():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2308_05007_gb300 import inputs as I
+    from paper_2308_05007_gb300.rwmi import Simulation, bin_walkers_noalloc, load
+
+    load()
+    w = I.ragged(n_walkers=20000)
+    sim = Simulation.from_workload(w)
+    n_cells = int(np.prod(w.dims))
+    stream = torch.cuda.Stream()
+    for call in range(2):
+        sim.step(7)
+        pos, ids, _ = sim.walkers(with_x0=False)
+        expect = sim.concentration()
+        pos4 = np.concatenate([pos, ids.astype(np.uint32).view(np.float32)[:, None]], axis=1)
+        posd = torch.from_numpy(np.ascontiguousarray(pos4)).cuda()
+        counts = torch.full((n_cells,), 7, dtype=torch.int32, device="cuda")   # must be overwritten
+        out = torch.full_like(posd, -1.0)
+        with torch.cuda.stream(stream):
+            bin_walkers_noalloc(w.dims, w.wall_mask, posd, counts, out, stream=stream)
+        stream.synchronize()
+        got = counts.cpu().numpy().view(np.uint32)
+        assert np.array_equal(got, expect), f"call {call}: counts differ"
+        s = out.cpu().numpy()
+        sid = s[:, 3].view(np.uint32)
+        assert np.array_equal(np.sort(sid), np.sort(ids.astype(np.uint32)))
+        cells = _cells(s[:, :3], w.dims, w.wall_mask)
+        assert np.all(np.diff(cells) >= 0), "not grouped by ascending cell"
+        assert np.array_equal(np.bincount(cells, minlength=n_cells), expect)
+        # each walker keeps its own position
+        order = np.argsort(ids)
+        assert np.array_equal(s[np.argsort(sid)][:, :3], pos[order])
+
+
+def test_noalloc_rejects_sizes_beyond_its_scratch():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2308_05007_gb300.rwmi import RwmiError, bin_walkers_noalloc
+
+    pos = torch.zeros((4, 4), dtype=torch.float32, device="cuda")
+    counts = torch.zeros(8, dtype=torch.int32, device="cuda")
+    with pytest.raises(RwmiError, match="1048576"):
+        bin_walkers_noalloc((128, 128, 128), 0, pos, counts)   # 2^21 cells > 2^20
