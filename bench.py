@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--moment-interval", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
     return ap.parse_args()
 
 
@@ -205,6 +206,35 @@ def run_reference(a, rank):
     print(json.dumps(line), flush=True)
 
 
+def measure_variants(a, stream):
+    """The same workload with the other population storages (plain binary32, binary32 shifted by
+    w_i rho0, binary16 shifted) and velocity sets (D3Q15, the paper's D3Q19): per-phase GPU time
+    of 16 eager steps (CUDA events), LBM kernel HBM fraction and whole-step MLUPS."""
+    import argparse as _ap
+    from paper_2308_05007_gb300.rwmi import Simulation
+    peak = float(measured_peaks()["hbm_gbs"])
+    out = {}
+    for q in (15, 19):
+        for storage in (0, 1, 2):
+            b = _ap.Namespace(**vars(a))
+            b.q, b.storage = q, storage
+            w = workload(b)
+            sim = Simulation.from_workload(w, seed_walkers=False)
+            sim.set_stream(stream)
+            sim.seed_walkers(w.n_walkers, *w.walker_box)
+            sim.step(16)
+            ph = sim.step_timed(16)
+            sim.close()
+            s_bytes = 2 if storage == 2 else 4
+            lbm_ms = ph["lbm"] / 16
+            step_ms = sum(ph.values()) / 16
+            gbs = lbm_bytes_per_launch(w, w.n_cells, s_bytes) / (lbm_ms / 1e3) / 1e9
+            out[f"D3Q{q}_{STORE_NAMES[storage]}"] = {
+                "lbm_ms": lbm_ms, "lbm_gbs": gbs, "lbm_hbm_frac": gbs / peak,
+                "step_ms_eager": step_ms, "mlups_eager": w.n_cells / (step_ms / 1e3) / 1e6}
+    return out
+
+
 def main():
     a = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -315,15 +345,18 @@ def main():
         "phase_ms_per_step": {k: v / n_timed_phase_steps for k, v in phases.items()},
         "gpu_launches": launches,
         "bricks": sim.brick_stats(),
+        "counters": sim.counters(),
         "clocks": clk,
     }
     if e2e:
         line["e2e"] = e2e
+    sim.close()
+    if not a.no_variants:
+        line["variants"] = measure_variants(a, stream)
     if world == 1 and not a.no_cpu_baseline:
         cb = cpu_baseline(a, w)
         line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
     print(json.dumps(line), flush=True)
-    sim.close()
     if dist:
         dist.destroy_process_group()
 

@@ -208,9 +208,11 @@ RWMI_API rwmi_status rwmi_particle_forces(rwmi_ctx* ctx, double* out);
  * positions, 3 per walker, in the same order. */
 RWMI_API rwmi_status rwmi_walkers(rwmi_ctx* ctx, float* out, float* x0);
 
-/* Device counters since creation: {type I, II, III, IV walker steps (0 unless counting is
- * enabled at build time), Algorithm 1 failures, refill failures, wall failures, seed failures}. */
-RWMI_API rwmi_status rwmi_counters(rwmi_ctx* ctx, int64_t out[8]);
+/* Device counters since creation: {type I (not counted, 0), type II, III, IV walker steps,
+ * Algorithm 1 failures, refill failures, wall failures, seed failures, non-finite velocities,
+ * over-long walker steps (resolved against all particles), walkers sent to the particle-resolution
+ * pass, (cell, particle) pairs the rasteriser evaluated sub-sample by sub-sample}. */
+RWMI_API rwmi_status rwmi_counters(rwmi_ctx* ctx, int64_t out[12]);
 
 /* Checkpoint and restart: populations, walkers (positions, start positions), the step
  * counter and the particle table. A restart continues bit-identically (noise is keyed by

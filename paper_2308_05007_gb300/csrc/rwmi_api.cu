@@ -181,8 +181,9 @@ BrickSet brick_set(const rwmi_ctx* c, int par) {
 }
 
 void update_margin(rwmi_ctx* c) {
-  // longest regular walker step: |u| <= U_BOUND plus three normals of at most 5.9 each
-  c->walk_margin = U_BOUND + (float)std::sqrt(2.0 * c->D) * 5.9f * 1.7320508f + 0.01f;
+  // regular walker step: |u| <= U_BOUND plus three normals of at most 4.5 each. A longer step
+  // (|z_a| > 4.5 for some axis: ~2e-5 of steps) is flagged and resolved against all particles.
+  c->walk_margin = U_BOUND + (float)std::sqrt(2.0 * c->D) * 4.5f * 1.7320508f + 0.01f;
 }
 
 // Brick lists, poses, body force and solid fraction of the current time; zeroes its accumulators.
@@ -838,12 +839,16 @@ RWMI_API rwmi_status rwmi_walkers(rwmi_ctx* c, float* out, float* x0) {
   return RWMI_OK;
 }
 
-RWMI_API rwmi_status rwmi_counters(rwmi_ctx* c, int64_t out[8]) {
+RWMI_API rwmi_status rwmi_counters(rwmi_ctx* c, int64_t out[12]) {
   if (!c || !out) return RWMI_E_INVALID;
   CK(cudaStreamSynchronize(c->stream));
   unsigned long long st[ST_COUNT];
   CK(cudaMemcpy(st, c->status, sizeof(st), cudaMemcpyDeviceToHost));
   for (int m = 0; m < 8; ++m) out[m] = (int64_t)st[m];
+  out[8] = (int64_t)st[ST_NONFINITE];
+  out[9] = (int64_t)st[ST_FAST_SPEED];
+  out[10] = (int64_t)st[ST_RESOLVED];
+  out[11] = (int64_t)st[ST_RASTER_QUEUED];
   return RWMI_OK;
 }
 

@@ -226,18 +226,20 @@ struct CellBound { float fmax, fmin; };
 
 // Displacement x - c: with mi, the minimum image on periodic axes; without, the plain difference
 // (control points staged at the brick's nearest image, valid for every point of the brick).
-__device__ __forceinline__ float disp(float x, float c, int a, bool mi, const Geom& g) {
-  return mi ? min_image_rn(x - c, (float)g.n[a], g.wall[a]) : x - c;
+template <bool MI>
+__device__ __forceinline__ float disp(float x, float c, int a, const Geom& g) {
+  return MI ? min_image_rn(x - c, (float)g.n[a], g.wall[a]) : x - c;
 }
 
 // Bounds of Eq. 3 over a ball of radius h about (x, y, z): every control point is at least
 // r - h and at most r + h away. Fast reciprocal/sqrt: the 1e-3 decision margins dwarf their error.
-__device__ __forceinline__ CellBound bound_at(const float4* cw, int c0, int c1, float x, float y, float z,
-                                              float h, const Geom& g, bool mi = true) {
+template <bool MI>
+__device__ __forceinline__ CellBound bound_at_t(const float4* cw, int c0, int c1, float x, float y, float z,
+                                                float h, const Geom& g) {
   float fmax = 0.0f, fmin = 0.0f;
   for (int i = c0; i < c1; ++i) {
     const float4 c = cw[i];
-    const float dx = disp(x, c.x, 0, mi, g), dy = disp(y, c.y, 1, mi, g), dz = disp(z, c.z, 2, mi, g);
+    const float dx = disp<MI>(x, c.x, 0, g), dy = disp<MI>(y, c.y, 1, g), dz = disp<MI>(z, c.z, 2, g);
     const float r2 = dx * dx + dy * dy + dz * dz;
     const float r = r2 * rsqrtf(fmaxf(r2, 1e-30f));
     const float rmin = fmaxf(r - h, 1e-15f), rmax = r + h;
@@ -252,12 +254,13 @@ __device__ __forceinline__ CellBound bound_at(const float4* cw, int c0, int c1, 
 
 // Upper/lower bounds over a ball of radius h1 and the upper bound over radius h2 (one pass).
 struct Bound2 { float fmax1, fmin1, fmax2; };
-__device__ __forceinline__ Bound2 bound_two(const float4* cw, int c0, int c1, float x, float y, float z,
-                                            float h1, float h2, const Geom& g, bool mi) {
+template <bool MI>
+__device__ __forceinline__ Bound2 bound_two_t(const float4* cw, int c0, int c1, float x, float y, float z,
+                                              float h1, float h2, const Geom& g) {
   Bound2 b{0.0f, 0.0f, 0.0f};
   for (int i = c0; i < c1; ++i) {
     const float4 c = cw[i];
-    const float dx = disp(x, c.x, 0, mi, g), dy = disp(y, c.y, 1, mi, g), dz = disp(z, c.z, 2, mi, g);
+    const float dx = disp<MI>(x, c.x, 0, g), dy = disp<MI>(y, c.y, 1, g), dz = disp<MI>(z, c.z, 2, g);
     const float r2 = dx * dx + dy * dy + dz * dz;
     const float r = r2 * rsqrtf(fmaxf(r2, 1e-30f));
     const float a = fmaxf(r - h1, 1e-15f), bb = r + h1, cc = fmaxf(r - h2, 1e-15f);
@@ -270,17 +273,33 @@ __device__ __forceinline__ Bound2 bound_two(const float4* cw, int c0, int c1, fl
 
 // Sub-sample inside test: fast value from the staged control points; within 4e-5 of 1 the
 // exact binary32 sequence shared with the CPU oracle decides, on the original wrapped points.
-__device__ __forceinline__ bool subsample_inside(const float4* cw, int c0, int c1, bool mi,
-                                                 const float4* cw_exact, int e0, int e1, float x, float y,
-                                                 float z, const Geom& g) {
+template <bool MI>
+__device__ __forceinline__ bool subsample_inside_t(const float4* cw, int c0, int c1, const float4* cw_exact,
+                                                   int e0, int e1, float x, float y, float z, const Geom& g) {
   float f = 0.0f;
   for (int i = c0; i < c1; ++i) {
     const float4 c = cw[i];
-    const float dx = disp(x, c.x, 0, mi, g), dy = disp(y, c.y, 1, mi, g), dz = disp(z, c.z, 2, mi, g);
+    const float dx = disp<MI>(x, c.x, 0, g), dy = disp<MI>(y, c.y, 1, g), dz = disp<MI>(z, c.z, 2, g);
     f += __fdividef(c.w, dx * dx + dy * dy + dz * dz);
   }
   if (fabsf(f - 1.0f) > 4e-5f) return f >= 1.0f;
   return metaball_exact(cw_exact, e0, e1, x, y, z, g) >= 1.0f;
+}
+
+// Runtime dispatch on the (warp-uniform) minimum-image switch.
+__device__ __forceinline__ CellBound bound_at(const float4* cw, int c0, int c1, float x, float y, float z,
+                                              float h, const Geom& g, bool mi = true) {
+  return mi ? bound_at_t<true>(cw, c0, c1, x, y, z, h, g) : bound_at_t<false>(cw, c0, c1, x, y, z, h, g);
+}
+__device__ __forceinline__ Bound2 bound_two(const float4* cw, int c0, int c1, float x, float y, float z,
+                                            float h1, float h2, const Geom& g, bool mi) {
+  return mi ? bound_two_t<true>(cw, c0, c1, x, y, z, h1, h2, g) : bound_two_t<false>(cw, c0, c1, x, y, z, h1, h2, g);
+}
+__device__ __forceinline__ bool subsample_inside(const float4* cw, int c0, int c1, bool mi,
+                                                 const float4* cw_exact, int e0, int e1, float x, float y,
+                                                 float z, const Geom& g) {
+  return mi ? subsample_inside_t<true>(cw, c0, c1, cw_exact, e0, e1, x, y, z, g)
+            : subsample_inside_t<false>(cw, c0, c1, cw_exact, e0, e1, x, y, z, g);
 }
 
 // Sub-sample s (bit s = a + 4 b + 16 c) of cell (i, j, k) inside the particle?
@@ -300,231 +319,225 @@ __device__ uint64_t particle_mask_serial(const float4* cw, int c0, int c1, bool 
   return m;
 }
 
-constexpr int RASTER_SMEM_CENTERS = 1024;
-constexpr int RASTER_QUEUE = 1024;      // (cell, candidate) pairs whose cell straddles the surface
-constexpr int RASTER_PER_THREAD = 4;    // queued pairs one thread can remember
+constexpr int RW_WARPS = 8;        // warps (bricks in flight) per block
+constexpr int RW_CENTERS = 192;    // control points one warp stages
+constexpr int RW_CAND = 8;         // candidates one warp stages (more: the unstaged path)
 
-// One block (256 threads, 2 cells each) per brick of the raster list (grid-stride).
-//  1. the brick's raster-relevant candidates are classified once for the whole brick (outside /
-//     wholly inside / partial) and their control points staged in shared memory;
-//  2. each thread bounds Eq. 3 over its cells (half-diagonal 0.65): outside -> no sub-sample,
-//     inside -> all 64, otherwise the (cell, candidate) pair joins a shared queue;
-//  3. whole warps evaluate queued pairs, 32 sub-samples per instruction (ballot into the mask);
-//  4. each thread combines its cells' masks: count = popcount(OR), owner = most sub-samples,
-//     lowest index on ties.
-__global__ void __launch_bounds__(256, 4) raster_kernel(Geom g, ParticleSet ps, BrickSet bs,
-                                                     uint16_t* __restrict__ solid,
-                                                     unsigned long long* __restrict__ status) {
+struct RasterWarp {
+  float4 cw[RW_CENTERS];           // control points at the brick's nearest image
+  unsigned char mcls[RW_CAND][64]; // per candidate and mini-brick: class | walker bit << 2
+  int p[RW_CAND], c0[RW_CAND], c1[RW_CAND], e0[RW_CAND], cls[RW_CAND];
+};
+
+// One warp per brick of the raster list (grid-stride over warps; no block barriers):
+//  1. the brick's candidates and their control points (staged at the brick's nearest image) are
+//     gathered by the lanes in parallel, and each candidate is classified for the whole brick;
+//  2. mini-bricks (2^3 cells): raster class per candidate and the walkers' mask bit (Eq. 3 may
+//     reach 1 within sqrt(3) + the walker step margin);
+//  3. 16 rounds of 32 cells: each lane bounds Eq. 3 over its cell (outside / inside / straddling);
+//     the warp then evaluates every straddling (cell, candidate) pair together, 32 sub-samples per
+//     ballot, and the cell's lane folds the 64-bit mask in: count = popcount(OR of masks), owner =
+//     the candidate with most sub-samples, lowest index on ties.
+// All decisions use bounds with a 1e-3 margin and, within 4e-5 of f = 1, the exact binary32
+// sequence shared with the CPU oracle, so counts and owners equal the oracle's bit for bit.
+__global__ void __launch_bounds__(256, 3) raster_kernel(Geom g, ParticleSet ps, BrickSet bs,
+                                                        uint16_t* __restrict__ solid,
+                                                        unsigned long long* __restrict__ status) {
+  __shared__ RasterWarp s_rw[RW_WARPS];
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  RasterWarp& W = s_rw[wib];
   const uint32_t nbrick = (uint32_t)g.nb[0] * g.nb[1] * g.nb[2];
   const uint32_t nlist = bs.bword[nbrick];
-  __shared__ float4 s_cw[RASTER_SMEM_CENTERS];
-  __shared__ uint32_t s_q[RASTER_QUEUE];
-  __shared__ unsigned long long s_qm[RASTER_QUEUE];
-  __shared__ int s_p[MAXC], s_c0[MAXC], s_c1[MAXC], s_cls[MAXC];
-  __shared__ unsigned char s_mcls[MAXC][64];   // per candidate and mini-brick: class | walker bit << 2
-  __shared__ int s_n, s_all, s_smem, s_qn, s_mi;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  // candidate m's control points for the fast tests (staged, nearest image) and for the exact one
-#define RC_FAST(m, cw, c0, c1, mi)                                                                   \
-  const float4* cw = s_smem ? s_cw : bs.cworld;                                                      \
-  const int c0 = s_smem ? s_c0[m] : ps.desc[s_p[m]].c0, c1 = s_smem ? s_c1[m] : ps.desc[s_p[m]].c1; \
-  const bool mi = s_smem ? (s_mi != 0) : true;
-#define RC_EXACT(m, e0, e1) const int e0 = ps.desc[s_p[m]].c0, e1 = ps.desc[s_p[m]].c1;
-  for (uint32_t li = blockIdx.x; li < nlist; li += gridDim.x) {
+  unsigned long long queued = 0;
+  for (uint32_t li = blockIdx.x * RW_WARPS + wib; li < nlist; li += gridDim.x * RW_WARPS) {
     const uint32_t b = (uint32_t)bs.rlist[li];
     const int bi = b % g.nb[0], bj = (b / g.nb[0]) % g.nb[1], bk = b / (g.nb[0] * g.nb[1]);
-    if (threadIdx.x == 0) {
-      const uint32_t nc = bs.bword[b] & 0xffffu;
-      s_all = nc > MAXC;
-      int n = 0, tot = 0;
-      if (!s_all) {
-        for (uint32_t m = 0; m < nc; ++m) {
-          const uint16_t cid = bs.bcand[b * MAXC + m];
-          if (cid & 0x8000) {
-            const int p = cid & 0x7fff;
-            s_p[n] = p; s_c0[n] = tot; s_c1[n] = tot + (ps.desc[p].c1 - ps.desc[p].c0);
-            tot = s_c1[n]; ++n;
-          }
-        }
-      } else {
-        atomicAdd(&status[ST_BRICK_OVERFLOW], 1ull);
+    const uint32_t nc = bs.bword[b] & 0xffffu;
+    const bool over = nc > MAXC;
+    // 1. candidates, in parallel over lanes; offsets of their control points by a warp scan
+    int p = -1, cnt = 0, g0 = 0;
+    if (!over && lane < (int)nc) {
+      const uint16_t cid = bs.bcand[b * MAXC + lane];
+      if (cid & 0x8000) {
+        p = cid & 0x7fff;
+        g0 = ps.desc[p].c0;
+        cnt = ps.desc[p].c1 - g0;
       }
-      s_n = n;
-      s_smem = tot <= RASTER_SMEM_CENTERS;
-      s_qn = 0;
-      s_mi = 0;
     }
-    __syncthreads();
-    const int n = s_n;
-    if (!s_all) {
-      if (s_smem) {
-        // stage each control point at its image nearest the brick centre; if some point lies near
-        // the half-box distance (small boxes), the fast tests keep the per-point minimum image
-        const float bcx = (float)(bi * BRICK) + 4.0f, bcy = (float)(bj * BRICK) + 4.0f, bcz = (float)(bk * BRICK) + 4.0f;
-        const float H = 6.0f + ps.walk_margin;
-        int near_half = 0;
-        for (int m = 0; m < n; ++m) {
-          const int g0 = ps.desc[s_p[m]].c0;
-          for (int i = threadIdx.x; i < s_c1[m] - s_c0[m]; i += blockDim.x) {
-            float4 cc = bs.cworld[g0 + i];
-            float* v[3] = {&cc.x, &cc.y, &cc.z};
-            const float bc[3] = {bcx, bcy, bcz};
-            for (int a = 0; a < 3; ++a) {
-              if (g.wall[a]) continue;
-              const float na = (float)g.n[a];
-              float d = *v[a] - bc[a];
-              if (d > 0.5f * na) *v[a] -= na; else if (d < -0.5f * na) *v[a] += na;
-              d = *v[a] - bc[a];
-              if (fabsf(d) > 0.5f * na - H) near_half = 1;
-            }
-            s_cw[s_c0[m] + i] = cc;
+    const unsigned rel = __ballot_sync(full, p >= 0);
+    const int n = __popc(rel);
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(full, incl, o);
+      if (lane >= o) incl += v;
+    }
+    const int tot = __shfl_sync(full, incl, 31);
+    const bool staged = !over && n <= RW_CAND && tot <= RW_CENTERS;
+    if (staged && p >= 0) {
+      const int slot = __popc(rel & ((1u << lane) - 1u));
+      W.p[slot] = p; W.c0[slot] = incl - cnt; W.c1[slot] = incl; W.e0[slot] = g0;
+    }
+    __syncwarp();
+    bool mi = true;
+    if (staged) {
+      const float bc[3] = {(float)(bi * BRICK) + 4.0f, (float)(bj * BRICK) + 4.0f, (float)(bk * BRICK) + 4.0f};
+      const float H = 6.0f + ps.walk_margin;
+      bool near_half = false;
+      for (int m = 0; m < n; ++m) {
+        const int len = W.c1[m] - W.c0[m];
+        for (int i = lane; i < len; i += 32) {
+          float4 cc = bs.cworld[W.e0[m] + i];
+          float* v[3] = {&cc.x, &cc.y, &cc.z};
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            if (g.wall[a]) continue;
+            const float na = (float)g.n[a];
+            const float d = *v[a] - bc[a];
+            if (d > 0.5f * na) *v[a] -= na; else if (d < -0.5f * na) *v[a] += na;
+            if (fabsf(*v[a] - bc[a]) > 0.5f * na - H) near_half = true;
           }
+          W.cw[W.c0[m] + i] = cc;
         }
-        if (near_half) atomicOr(&s_mi, 1);
       }
-      __syncthreads();
-      if (threadIdx.x < n) {
-        const int m = threadIdx.x;
-        RC_FAST(m, cw, c0, c1, mi)
+      mi = __any_sync(full, near_half);
+      __syncwarp();
+      if (lane < n) {   // brick-level class (sub-samples lie within the half-diagonal of the brick)
         const float ex0 = (float)(bi * BRICK), ex1 = fminf((float)((bi + 1) * BRICK), (float)g.n[0]);
         const float ey0 = (float)(bj * BRICK), ey1 = fminf((float)((bj + 1) * BRICK), (float)g.n[1]);
         const float ez0 = (float)(bk * BRICK), ez1 = fminf((float)((bk + 1) * BRICK), (float)g.n[2]);
         const float hx = 0.5f * (ex1 - ex0) - 0.125f, hy = 0.5f * (ey1 - ey0) - 0.125f, hz = 0.5f * (ez1 - ez0) - 0.125f;
-        const CellBound bb = bound_at(cw, c0, c1, 0.5f * (ex0 + ex1), 0.5f * (ey0 + ey1), 0.5f * (ez0 + ez1),
-                                      sqrtf(hx * hx + hy * hy + hz * hz), g, mi);
-        s_cls[m] = bb.fmax < 0.999f ? 0 : (bb.fmin > 1.001f ? 1 : 2);
+        const CellBound bb = bound_at(W.cw, W.c0[lane], W.c1[lane], 0.5f * (ex0 + ex1), 0.5f * (ey0 + ey1),
+                                      0.5f * (ez0 + ez1), sqrtf(hx * hx + hy * hy + hz * hz), g, mi);
+        W.cls[lane] = bb.fmax < 0.999f ? 0 : (bb.fmin > 1.001f ? 1 : 2);
       }
-      __syncthreads();
-    }
-    // Mini-bricks (2^3 cells; sub-samples within 1.5155 of the centre): one pass per (mini-brick,
-    // candidate) classifies it for the raster (outside / inside / partial) and bounds Eq. 3 within
-    // sqrt(3) + the walker step margin, which sets the walkers' mask bit (rigorous bounds with a
-    // 1e-3 margin, as above).
-    const int ncand = s_all ? ps.P : n;
-    if (!s_all) {
-      for (int pr = threadIdx.x; pr < 64 * n; pr += blockDim.x) {
+      __syncwarp();
+      // 2. mini-bricks: raster class and walker bit per candidate
+      for (int pr = lane; pr < 64 * n; pr += 32) {
         const int mb = pr & 63, m = pr >> 6;
-        int cls = s_cls[m];
-        bool need = cls != 0;
+        const float xm = (float)(bi * BRICK + 2 * (mb & 3)) + 1.0f, ym = (float)(bj * BRICK + 2 * ((mb >> 2) & 3)) + 1.0f,
+                    zm = (float)(bk * BRICK + 2 * (mb >> 4)) + 1.0f;
+        int cls = W.cls[m];
+        bool need;
         if (cls == 2) {
-          const float xm = (float)(bi * BRICK + 2 * (mb & 3)) + 1.0f, ym = (float)(bj * BRICK + 2 * ((mb >> 2) & 3)) + 1.0f,
-                      zm = (float)(bk * BRICK + 2 * (mb >> 4)) + 1.0f;
-          RC_FAST(m, cw, c0, c1, mi)
-          const Bound2 b2 = bound_two(cw, c0, c1, xm, ym, zm, 1.5155444f, 1.7320508f + ps.walk_margin, g, mi);
+          const Bound2 b2 = bound_two(W.cw, W.c0[m], W.c1[m], xm, ym, zm, 1.5155444f, 1.7320508f + ps.walk_margin, g, mi);
           cls = b2.fmax1 < 0.999f ? 0 : (b2.fmin1 > 1.001f ? 1 : 2);
           need = b2.fmax2 >= 0.999f;
-        } else if (cls == 0) {
-          need = false;   // outside over the whole brick; the walker margin is checked below
-          const float xm = (float)(bi * BRICK + 2 * (mb & 3)) + 1.0f, ym = (float)(bj * BRICK + 2 * ((mb >> 2) & 3)) + 1.0f,
-                      zm = (float)(bk * BRICK + 2 * (mb >> 4)) + 1.0f;
-          RC_FAST(m, cw, c0, c1, mi)
-          need = bound_at(cw, c0, c1, xm, ym, zm, 1.7320508f + ps.walk_margin, g, mi).fmax >= 0.999f;
+        } else if (cls == 1) {
+          need = true;
+        } else {
+          need = bound_at(W.cw, W.c0[m], W.c1[m], xm, ym, zm, 1.7320508f + ps.walk_margin, g, mi).fmax >= 0.999f;
         }
-        s_mcls[m][mb] = (unsigned char)(cls | (need ? 4 : 0));
+        W.mcls[m][mb] = (unsigned char)(cls | (need ? 4 : 0));
+      }
+      __syncwarp();
+      bool n0 = false, n1 = false;
+      for (int m = 0; m < n; ++m) {
+        n0 |= (W.mcls[m][lane] & 4) != 0;
+        n1 |= (W.mcls[m][lane + 32] & 4) != 0;
+      }
+      const unsigned lo = __ballot_sync(full, n0), hi = __ballot_sync(full, n1);
+      if (lane == 0) bs.wmask[b] = ((unsigned long long)hi << 32) | lo;
+    } else {
+      if (lane == 0) {
+        bs.wmask[b] = ~0ull;   // every walker of this brick is tested
+        if (over) atomicAdd(&status[ST_BRICK_OVERFLOW], 1ull);
       }
     }
-    __syncthreads();
-    if (threadIdx.x < 64) {
-      bool need = s_all != 0;
-      for (int m = 0; m < n && !need; ++m) need = (s_mcls[m][threadIdx.x] & 4) != 0;
-      const unsigned bal = __ballot_sync(0xffffffffu, need);
-      if ((threadIdx.x & 31) == 0) reinterpret_cast<unsigned*>(bs.wmask + b)[threadIdx.x >> 5] = bal;
-    }
-    // 2. per-thread classification of its two cells
-    uint64_t any[2] = {0ull, 0ull};
-    int best[2] = {0, 0}, bestp[2] = {-1, -1};
-    int qidx[RASTER_PER_THREAD], qm[RASTER_PER_THREAD], qcell[RASTER_PER_THREAD];
-    int nq = 0;
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int cl = threadIdx.x + h * 256;
-      const int li_x = cl & 7, li_y = (cl >> 3) & 7, li_z = cl >> 6;
-      const int i = bi * BRICK + li_x, j = bj * BRICK + li_y, k = bk * BRICK + li_z;
-      if (i >= g.n[0] || j >= g.n[1] || k >= g.n[2]) continue;
-      const int mb = (li_x >> 1) + 4 * (li_y >> 1) + 16 * (li_z >> 1);
-      for (int m = 0; m < ncand; ++m) {
-        int p, c0, c1, e0, e1, cls = 2;
-        bool mi = true;
-        const float4* cw = bs.cworld;
-        if (s_all) {
-          p = m; c0 = e0 = ps.desc[p].c0; c1 = e1 = ps.desc[p].c1;
+    // 3. cells, 32 per round
+    for (int r = 0; r < (BRICK * BRICK * BRICK) / 32; ++r) {
+      const int cl = r * 32 + lane;
+      const int lx = cl & 7, ly = (cl >> 3) & 7, lz = cl >> 6;
+      const int i = bi * BRICK + lx, j = bj * BRICK + ly, k = bk * BRICK + lz;
+      const bool in_dom = i < g.n[0] && j < g.n[1] && k < g.n[2];
+      const int mb = (lx >> 1) + 4 * (ly >> 1) + 16 * (lz >> 1);
+      uint64_t any = 0ull;
+      int best = 0, bestp = -1;
+      unsigned pend = 0u;
+      const int ncand = staged ? n : (over ? ps.P : (int)nc);
+      for (int m = 0; in_dom && m < ncand; ++m) {
+        int pp, cls = 2, c0, c1;
+        const float4* cw;
+        bool cmi = mi;
+        if (staged) {
+          pp = W.p[m]; cls = W.mcls[m][mb] & 3; cw = W.cw; c0 = W.c0[m]; c1 = W.c1[m];
         } else {
-          p = s_p[m]; cls = s_mcls[m][mb] & 3;
-          e0 = ps.desc[p].c0; e1 = ps.desc[p].c1;
-          if (s_smem) { cw = s_cw; c0 = s_c0[m]; c1 = s_c1[m]; mi = s_mi != 0; }
-          else { c0 = e0; c1 = e1; }
+          if (over) pp = m;
+          else {
+            const uint16_t cid = bs.bcand[b * MAXC + m];
+            if (!(cid & 0x8000)) continue;
+            pp = cid & 0x7fff;
+          }
+          cw = bs.cworld; c0 = ps.desc[pp].c0; c1 = ps.desc[pp].c1; cmi = true;
         }
         if (cls == 0) continue;
-        uint64_t mk = 0ull;
+        uint64_t mk;
         if (cls == 1) {
           mk = ~0ull;
         } else {
-          const CellBound cb = bound_at(cw, c0, c1, (float)i + 0.5f, (float)j + 0.5f, (float)k + 0.5f,
-                                        0.649519053f, g, mi);
+          const CellBound cb = bound_at(cw, c0, c1, (float)i + 0.5f, (float)j + 0.5f, (float)k + 0.5f, 0.649519053f, g, cmi);
           if (cb.fmax < 0.999f) continue;
           if (cb.fmin > 1.001f) {
             mk = ~0ull;
+          } else if (staged) {
+            pend |= 1u << m;   // the whole warp evaluates it below
+            continue;
           } else {
-            int slot = -1;
-            if (!s_all && nq < RASTER_PER_THREAD) {
-              slot = atomicAdd(&s_qn, 1);
-              if (slot >= RASTER_QUEUE) slot = -1;
-            }
-            if (slot >= 0) {   // the warps evaluate it below
-              s_q[slot] = ((uint32_t)cl << 8) | (uint32_t)m;
-              qidx[nq] = slot; qm[nq] = m; qcell[nq] = h; ++nq;
-              continue;
-            }
-            mk = particle_mask_serial(cw, c0, c1, mi, bs.cworld, e0, e1, i, j, k, g);
+            mk = particle_mask_serial(cw, c0, c1, true, bs.cworld, c0, c1, i, j, k, g);
           }
         }
         const int np = __popcll(mk);
-        any[h] |= mk;
-        if (np > 0 && (np > best[h] || (np == best[h] && p < bestp[h]))) { best[h] = np; bestp[h] = p; }
+        any |= mk;
+        if (np > 0 && (np > best || (np == best && pp < bestp))) { best = np; bestp = pp; }
+      }
+      // the warp evaluates each straddling (cell, candidate) pair: 2 x 32 sub-samples
+      unsigned lanes_p = __ballot_sync(full, pend != 0u);
+      while (lanes_p) {
+        const int src = __ffs(lanes_p) - 1;
+        const unsigned pm = __shfl_sync(full, pend, src);
+        const int m = __ffs(pm) - 1;
+        const int scl = __shfl_sync(full, cl, src);
+        const int si = bi * BRICK + (scl & 7), sj = bj * BRICK + ((scl >> 3) & 7), sk = bk * BRICK + (scl >> 6);
+        const int e0 = W.e0[m], e1 = e0 + (W.c1[m] - W.c0[m]);
+        bool in_lo, in_hi;
+        const float sx = (float)si + 0.125f, sy = (float)sj + 0.125f, sz = (float)sk + 0.125f;
+        const float ax = 0.25f * (float)(lane & 3), ay = 0.25f * (float)((lane >> 2) & 3), az = 0.25f * (float)(lane >> 4);
+        if (mi) {
+          in_lo = subsample_inside_t<true>(W.cw, W.c0[m], W.c1[m], bs.cworld, e0, e1, sx + ax, sy + ay, sz + az, g);
+          in_hi = subsample_inside_t<true>(W.cw, W.c0[m], W.c1[m], bs.cworld, e0, e1, sx + ax, sy + ay, sz + az + 0.5f, g);
+        } else {
+          in_lo = subsample_inside_t<false>(W.cw, W.c0[m], W.c1[m], bs.cworld, e0, e1, sx + ax, sy + ay, sz + az, g);
+          in_hi = subsample_inside_t<false>(W.cw, W.c0[m], W.c1[m], bs.cworld, e0, e1, sx + ax, sy + ay, sz + az + 0.5f, g);
+        }
+        const unsigned blo = __ballot_sync(full, in_lo);
+        const unsigned bhi = __ballot_sync(full, in_hi);
+        if (lane == src) {
+          const uint64_t mk = ((uint64_t)bhi << 32) | blo;
+          const int np = __popcll(mk);
+          const int pp = W.p[m];
+          any |= mk;
+          if (np > 0 && (np > best || (np == best && pp < bestp))) { best = np; bestp = pp; }
+          pend &= ~(1u << m);
+        }
+        ++queued;
+        lanes_p = __ballot_sync(full, pend != 0u);
+      }
+      if (in_dom) {
+        const int count = __popcll(any);
+        const uint32_t cell = ((uint32_t)k * g.n[1] + j) * g.n[0] + i;
+        solid[cell] = count > 0 ? (uint16_t)(count | (bestp << 7)) : (uint16_t)0;
       }
     }
-    __syncthreads();
-    // 3. warps evaluate the queued (cell, candidate) pairs, two rounds of 32 sub-samples
-    const int qn = min(s_qn, RASTER_QUEUE);
-    for (int e = warp; e < qn; e += nwarps) {
-      const uint32_t ent = s_q[e];
-      const int cl = ent >> 8, m = ent & 0xff;
-      const int i = bi * BRICK + (cl & 7), j = bj * BRICK + ((cl >> 3) & 7), k = bk * BRICK + (cl >> 6);
-      RC_FAST(m, cw, c0, c1, mi)
-      RC_EXACT(m, e0, e1)
-      const unsigned lo = __ballot_sync(0xffffffffu, subsample_bit(cw, c0, c1, mi, bs.cworld, e0, e1, i, j, k, lane, g));
-      const unsigned hi = __ballot_sync(0xffffffffu, subsample_bit(cw, c0, c1, mi, bs.cworld, e0, e1, i, j, k, lane + 32, g));
-      if (lane == 0) s_qm[e] = ((unsigned long long)hi << 32) | lo;
-    }
-    __syncthreads();
-    // 4. combine and write the solid words
-    for (int t = 0; t < nq; ++t) {
-      const int h = qcell[t];
-      const uint64_t mk = s_qm[qidx[t]];
-      const int p = s_p[qm[t]];
-      const int np = __popcll(mk);
-      any[h] |= mk;
-      if (np > 0 && (np > best[h] || (np == best[h] && p < bestp[h]))) { best[h] = np; bestp[h] = p; }
-    }
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int cl = threadIdx.x + h * 256;
-      const int i = bi * BRICK + (cl & 7), j = bj * BRICK + ((cl >> 3) & 7), k = bk * BRICK + (cl >> 6);
-      if (i >= g.n[0] || j >= g.n[1] || k >= g.n[2]) continue;
-      const int count = __popcll(any[h]);
-      const uint32_t cell = ((uint32_t)k * g.n[1] + j) * g.n[0] + i;
-      solid[cell] = count > 0 ? (uint16_t)(count | (bestp[h] << 7)) : (uint16_t)0;
-    }
-    __syncthreads();
+    __syncwarp();
   }
-#undef RC_FAST
-#undef RC_EXACT
+  if (lane == 0 && queued) atomicAdd(&status[ST_RASTER_QUEUED], queued);
 }
 
 void launch_raster(const Geom& g, const ParticleSet& ps, BrickSet bs, uint16_t* solid,
                    unsigned long long* status, int nsm, cudaStream_t st) {
   if (ps.P == 0) return;
-  raster_kernel<<<nsm * 4, 256, 0, st>>>(g, ps, bs, solid, status);
+  raster_kernel<<<nsm * 3, RW_WARPS * 32, 0, st>>>(g, ps, bs, solid, status);
 }
 
 // ------------------------------------------------------------------------------------------

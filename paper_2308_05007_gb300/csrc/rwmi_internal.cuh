@@ -30,14 +30,14 @@ constexpr int BRICK = 8;            // brick edge in cells
 constexpr int MAXC = 16;            // candidate particles stored per brick
 constexpr int MAX_PARTICLES = 511;  // owner field of the solid word is 9 bits
 constexpr int MAX_CENTERS = 65535;
-constexpr float U_BOUND = 0.3f;     // lattice speed bound assumed by the walker candidate margin
+constexpr float U_BOUND = 0.1f;     // lattice speed bound assumed by the walker candidate margin
 constexpr int RED_SLOTS = 256;      // mass/momentum partial sums are striped over this many slots
 
 // Status counters (device, unsigned long long): see rwmi_counters.
 enum StatusSlot {
   ST_TYPE1 = 0, ST_TYPE2, ST_TYPE3, ST_TYPE4,
   ST_BISECT_FAIL, ST_REFILL_FAIL, ST_WALL_FAIL, ST_SEED_FAIL,
-  ST_NONFINITE, ST_BRICK_OVERFLOW, ST_FAST_SPEED, ST_COUNT
+  ST_NONFINITE, ST_BRICK_OVERFLOW, ST_FAST_SPEED, ST_RESOLVED, ST_RASTER_QUEUED, ST_COUNT
 };
 
 struct ParticleDesc {

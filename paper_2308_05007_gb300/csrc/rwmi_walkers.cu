@@ -330,7 +330,7 @@ __global__ void __launch_bounds__(256, 4) walker_kernel(WalkCtx c, float4* __res
 // Pass 2 (fixed grid, grid-stride over the list): types II-IV of the flagged walkers, written back
 // to their slots. The last warp to finish advances the device step counter and empties the list
 // (every warp has read both by then).
-__global__ void __launch_bounds__(256, 2) walker_resolve_kernel(WalkCtx c, float4* __restrict__ pos,
+__global__ void __launch_bounds__(256, 4) walker_resolve_kernel(WalkCtx c, float4* __restrict__ pos,
                                                              const float4* __restrict__ list,
                                                              unsigned int* list_n, const int64_t* d_T,
                                                              float amp, uint32_t k0, uint32_t k1,
@@ -338,6 +338,7 @@ __global__ void __launch_bounds__(256, 2) walker_resolve_kernel(WalkCtx c, float
                                                              unsigned int* ticket, int64_t* d_T_inc) {
   const int64_t T = *d_T;
   const unsigned cnt = *list_n;
+  if (blockIdx.x == 0 && threadIdx.x == 0 && cnt) atomicAdd(&status[ST_RESOLVED], (unsigned long long)cnt);
   unsigned ev_all[5] = {0u, 0u, 0u, 0u, 0u};
   const unsigned stride = gridDim.x * blockDim.x;
   for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += stride) {
@@ -354,7 +355,32 @@ __global__ void __launch_bounds__(256, 2) walker_resolve_kernel(WalkCtx c, float
                         (xf[2] - x[2]) * (xf[2] - x[2]);
     const bool far_step = step2 > c.ps.walk_margin * c.ps.walk_margin;
     float xn[3] = {xf[0], xf[1], xf[2]};
-    const unsigned ev = resolve_particles(c, x, xf, xw, yw, zw, b, nc, far_step, id, (uint32_t)T, amp, k0, k1, xn);
+    // most flagged walkers meet no particle: test x and x_f against the brick's candidates inline
+    // (one pass over each candidate's control points) and take the out-of-line path only on a hit
+    bool hit = far_step || nc > MAXC;
+    if (!hit) {
+      const float xfw = wrap_coord(xf[0], (float)c.g.n[0], c.g.wall[0], c.g.inv_n[0]);
+      const float yfw = wrap_coord(xf[1], (float)c.g.n[1], c.g.wall[1], c.g.inv_n[1]);
+      const float zfw = wrap_coord(xf[2], (float)c.g.n[2], c.g.wall[2], c.g.inv_n[2]);
+      for (uint32_t m = 0; m < nc && !hit; ++m) {
+        const ParticleDesc& d = c.ps.desc[c.bs.bcand[b * MAXC + m] & 0x7fff];
+        float fa = 0.0f, fb = 0.0f;
+        for (int i = d.c0; i < d.c1; ++i) {
+          const float4 cc = c.bs.cworld[i];
+          const float ax = min_image_rn(xw - cc.x, (float)c.g.n[0], c.g.wall[0]);
+          const float ay = min_image_rn(yw - cc.y, (float)c.g.n[1], c.g.wall[1]);
+          const float az = min_image_rn(zw - cc.z, (float)c.g.n[2], c.g.wall[2]);
+          const float bx = min_image_rn(xfw - cc.x, (float)c.g.n[0], c.g.wall[0]);
+          const float by = min_image_rn(yfw - cc.y, (float)c.g.n[1], c.g.wall[1]);
+          const float bz = min_image_rn(zfw - cc.z, (float)c.g.n[2], c.g.wall[2]);
+          fa += __fdividef(cc.w, ax * ax + ay * ay + az * az);
+          fb += __fdividef(cc.w, bx * bx + by * by + bz * bz);
+        }
+        hit = fa >= 1.0f || fb >= 1.0f;
+      }
+    }
+    unsigned ev = 0u;
+    if (hit) ev = resolve_particles(c, x, xf, xw, yw, zw, b, nc, far_step, id, (uint32_t)T, amp, k0, k1, xn);
     pos[w] = make_float4(xn[0], xn[1], xn[2], a.w);
     for (int m = 0; m < 5; ++m) ev_all[m] += (ev >> m) & 1u;
   }
@@ -384,7 +410,7 @@ void launch_walkers(const Geom& g, const ParticleSet& ps, BrickSet bs1, float4* 
   const int64_t blocks = (n + 255) / 256;
   const float amp = sqrtf(2.0f * D);
   walker_kernel<<<(unsigned)blocks, 256, 0, st>>>(c, pos, n, u, d_T, amp, k0, k1, status, list, list_n);
-  walker_resolve_kernel<<<nsm * 2, 256, 0, st>>>(c, pos, list, list_n, d_T, amp, k0, k1, status, ticket, d_T_inc);
+  walker_resolve_kernel<<<nsm * 8, 256, 0, st>>>(c, pos, list, list_n, d_T, amp, k0, k1, status, ticket, d_T_inc);
 }
 
 __global__ void advance_kernel(int64_t* d_T) { *d_T += 1; }

@@ -368,10 +368,10 @@ class Simulation:
                         (int(v) for v in out)))
 
     def counters(self) -> dict:
-        out = np.zeros(8, np.int64)
+        out = np.zeros(12, np.int64)
         self._check(self._L.rwmi_counters(self._h, _ptr(out)))
         keys = ["type_I", "type_II", "type_III", "type_IV", "bisect_fail", "refill_fail", "wall_fail",
-                "seed_fail"]
+                "seed_fail", "nonfinite", "long_steps", "resolved", "raster_queued"]
         return dict(zip(keys, (int(v) for v in out)))
 
     def save(self, path):

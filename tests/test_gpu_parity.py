@@ -342,3 +342,64 @@ def test_oscillator_full_size_sampled():
     assert np.array_equal(cg, co) and np.array_equal(og, oo)
     assert int(sim.concentration().sum()) == w.n_walkers
     assert sim.mass_momentum()[0] == pytest.approx(float(ora.n_cells), rel=1e-6)
+
+
+# ------------------------------------------------------------------------------- FP16-shift storage
+@pytest.mark.parametrize("q", [15, 19])
+def test_one_lbm_step_fp16_shifted_storage(q):
+    """Binary16 storage of f_i - w_i rho0 with binary32 arithmetic: from identical (decoded)
+    populations one step matches the oracle up to the binary16 rounding of the stored result,
+    |df| <= 2^-11 |f - w rho0| + 1e-6 max|f|."""
+    w = I.ragged(q=q, storage=2, walls=4, seed=9)
+    sim = Sim().from_workload(w, seed_walkers=False)
+    ora = Oracle.from_workload(w, seed_walkers=False)
+    perm = _perm(sim, q)
+    _, wts = lattice(q)
+    sim.step(6)
+    f_prev = sim.populations()[perm]
+    t = sim.t
+    sim.step(1)
+    f_next = sim.populations()[perm]
+    ora.set_populations(f_prev)
+    ora.set_time(t)
+    fo, uo, _ = ora.lbm_cells(np.arange(ora.n_cells))
+    dev = np.abs(fo - wts[:, None] * w.rho0)
+    assert np.all(np.abs(f_next - fo) <= 2.0 ** -11 * dev + 1e-6 * np.abs(fo).max())
+
+
+def test_precision_storages_against_the_oracle():
+    """The precision case at 96^3 (parity physics, 4 static particles, 2e4 walkers, 60 steps):
+    velocity field and dispersion-coefficient error of each storage against the FP64 oracle.
+    Bounds: shifted binary32 keeps the 1e-5 relative bound; for the others the worst-case
+    accumulation of one storage rounding per population per step, n Q eps max|stored value|
+    (binary32 unshifted: eps = 2^-24 of max|f|; binary16 shifted: eps = 2^-11 of
+    max|f - w rho0|), bounds the largest velocity error."""
+    w = I.precision(n=96, n_particles=4, n_walkers=20000, seed=2)
+    w = I.with_(w, steps=60, moment_interval=10)
+    ora = Oracle.from_workload(w)
+    mo_series = []
+    for k in range(6):
+        ora.step(10)
+        mo_series.append(ora.moments())
+    uo = ora.velocity()
+    fo = ora.populations()
+    _, wts = lattice(w.q)
+    d_ora = (mo_series[-1][4:7] - mo_series[1][4:7]) / (2 * 40)
+    errs = {}
+    for storage in (1, 0, 2):
+        sim = Sim().from_workload(I.with_(w, storage=storage))
+        sim.step(w.steps)
+        ser = sim.moment_series()
+        assert len(ser) == 6
+        d_gpu = (ser[-1, 5:8] - ser[1, 5:8]) / (2 * 40)
+        ug = sim.velocity().astype(np.float64)
+        errs[storage] = {"rel_l2_u": _rel(ug, uo), "max_abs_u": float(np.abs(ug - uo).max()),
+                         "rel_D": float(np.abs(d_gpu - d_ora).max() / np.abs(d_ora).max())}
+        sim.close()
+    print("precision errors by storage (0 fp32, 1 fp32-shift, 2 fp16-shift):", errs)
+    n, q = w.steps, w.q
+    assert errs[1]["rel_l2_u"] <= 1e-5
+    assert errs[0]["max_abs_u"] <= n * q * 2.0 ** -24 * np.abs(fo).max()
+    assert errs[2]["max_abs_u"] <= n * q * 2.0 ** -11 * np.abs(fo - wts[:, None] * w.rho0).max()
+    for st in (0, 1, 2):   # walker branch flips and the velocity error both stay small
+        assert errs[st]["rel_D"] <= 1e-2, (st, errs[st])
