@@ -31,7 +31,7 @@ STORE_NAMES = {0: "fp32", 1: "fp32_shift", 2: "fp16_shift"}
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "lbm_kernel_oscillator_256.md")
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=2000)
@@ -47,7 +47,13 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
-    return ap.parse_args()
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batch-domains", type=int, default=64)
+    ap.add_argument("--batch-steps", type=int, default=160)
+    ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--served-requests", type=int, default=32)
+    ap.add_argument("--served-step-scale", type=float, default=0.05)
+    return ap.parse_args(argv)
 
 
 def workload(a):
@@ -206,6 +212,21 @@ def run_reference(a, rank):
     print(json.dumps(line), flush=True)
 
 
+def max_over_ranks(x: float, dist, device) -> float:
+    """The maximum of a per-rank number over all ranks: the slowest replica sets the job time."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world: int, units_per_rank: float, steps: int, seconds: float) -> float:
+    """Whole-job throughput of `world` replicas that each processed units_per_rank per step."""
+    return world * units_per_rank * steps / seconds
+
+
 def measure_variants(a, stream):
     """The same workload with the other population storages (plain binary32, binary32 shifted by
     w_i rho0, binary16 shifted) and velocity sets (D3Q15, the paper's D3Q19): per-phase GPU time
@@ -232,6 +253,70 @@ def measure_variants(a, stream):
             out[f"D3Q{q}_{STORE_NAMES[storage]}"] = {
                 "lbm_ms": lbm_ms, "lbm_gbs": gbs, "lbm_hbm_frac": gbs / peak,
                 "step_ms_eager": step_ms, "mlups_eager": w.n_cells / (step_ms / 1e3) / 1e6}
+    return out
+
+
+def measure_batched(a):
+    """64 independent periodic domains (edges U{48..160}, 4-32 particles of 2-10 centres,
+    1e5-2e6 walkers, tau U[0.6, 1], D U[0.001, 0.02]) advanced together. Each context's LBM
+    block size is picked by rwmi_autotune; then one rwmi_batch graph launch per 16-step chunk
+    advances all of them ("batched"), against the same contexts each driven by its own
+    rwmi_step call on its own stream ("separate"). Whole-job MLUPS by host wall clock around
+    the launches and a final synchronisation."""
+    from paper_2308_05007_gb300 import inputs as I
+    from paper_2308_05007_gb300.rwmi import Batch, Simulation
+    ws = I.batched(n_domains=a.batch_domains, seed=3)
+    sims = [Simulation.from_workload(w) for w in ws]
+    blocks = [s.autotune() for s in sims]
+    cells = sum(w.n_cells for w in ws)
+    walkers = sum(w.n_walkers for w in ws)
+    n = max(16, a.batch_steps // 16 * 16)
+    out = {"domains": len(ws), "cells": cells, "walkers": walkers, "steps": n,
+           "lbm_block_histogram": {str(b): blocks.count(b) for b in sorted(set(blocks))}}
+    with Batch(sims) as b:
+        b.step(32)
+        b.sync()
+        t0 = time.perf_counter()
+        b.step(n)
+        assert b.sync() >= 0
+        dt = time.perf_counter() - t0
+    out["batched"] = {"mlups": cells * n / dt / 1e6, "walker_steps_per_s": walkers * n / dt,
+                      "ms_per_step": dt / n * 1e3}
+    for s in sims:
+        s.step(16)
+    for s in sims:
+        s.sync()
+    t0 = time.perf_counter()
+    for c in range(0, n, 16):
+        for s in sims:
+            s.step(16)
+    for s in sims:
+        assert s.sync() >= 0
+    dt = time.perf_counter() - t0
+    out["separate"] = {"mlups": cells * n / dt / 1e6, "walker_steps_per_s": walkers * n / dt,
+                       "ms_per_step": dt / n * 1e3}
+    for s in sims:
+        s.close()
+    return out
+
+
+def measure_served(a):
+    """Poisson request stream (20 req/s) of simulations with edges log-uniform in [32, 256],
+    1e5-1e7 walkers (at most 2 per cell), FP32-shift or FP16-shift populations and
+    1000-20000 steps scaled by --served-step-scale, served by the continuous-batching loop
+    (admission by rwmi_footprint within half the free device memory, 16 slots)."""
+    import torch
+    from paper_2308_05007_gb300 import inputs as I
+    from paper_2308_05007_gb300.serve import Server
+    reqs = I.served(n_requests=a.served_requests, rate=20.0, seed=4, step_scale=a.served_step_scale)
+    budget = int(torch.cuda.mem_get_info()[0] * 0.5)
+    srv = Server(budget_bytes=budget, max_active=16)
+    rep = srv.run(reqs)
+    out = rep.summary()
+    out.update({"rate_per_s": 20.0, "step_scale": a.served_step_scale, "budget_bytes": budget,
+                "max_active": 16,
+                "steps_range": [min(r.workload.steps for r in reqs), max(r.workload.steps for r in reqs)],
+                "edge_range": [min(r.workload.dims[0] for r in reqs), max(r.workload.dims[0] for r in reqs)]})
     return out
 
 
@@ -287,13 +372,10 @@ def main():
         ms = ev0.elapsed_time(ev1)
         st = sim.sync()
         assert st >= 0, st
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, "cuda")
     sec = ms / 1e3
-    mlups = world * w.n_cells * steps / sec / 1e6
-    wsps = world * w.n_walkers * steps / sec
+    mlups = job_rate(world, w.n_cells, steps, sec) / 1e6
+    wsps = job_rate(world, w.n_walkers, steps, sec)
 
     # e2e through the public API with host buffers: H2D of the walker positions from pinned host
     # memory, the steps, D2H of the concentration field and the moments
@@ -313,15 +395,12 @@ def main():
             mom = sim.walker_moments()
             torch.cuda.synchronize()
             te = time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([te], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            te = float(t.item())
+        te = max_over_ranks(te, dist, "cuda")
         assert int(conc.sum()) == w.n_walkers and mom[0] == w.n_walkers
-        e2e = {"value": world * w.n_cells * steps / te / 1e6, "unit": "MLUPS",
+        e2e = {"value": job_rate(world, w.n_cells, steps, te) / 1e6, "unit": "MLUPS",
                "h2d_bytes_per_step": pinned.numel() * 4 / steps,
                "d2h_bytes_per_step": (conc.numel() * 4 + 13 * 8) / steps,
-               "walker_steps_per_s": world * w.n_walkers * steps / te}
+               "walker_steps_per_s": job_rate(world, w.n_walkers, steps, te)}
 
     if rank != 0:
         return
@@ -353,6 +432,11 @@ def main():
     sim.close()
     if not a.no_variants:
         line["variants"] = measure_variants(a, stream)
+    if not a.no_batched:
+        line["batched"] = measure_batched(a)
+    if not a.no_served:
+        line["served"] = measure_served(a)
+        line["p99_latency_s"] = line["served"]["p99_latency_s"]
     if world == 1 and not a.no_cpu_baseline:
         cb = cpu_baseline(a, w)
         line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}

@@ -26,6 +26,10 @@
  *     with cudaPointerGetAttributes.
  *   - Streams: all GPU work of a context is issued on one stream (rwmi_set_stream; default: a
  *     stream the context creates). rwmi_step is asynchronous; getters synchronise that stream.
+ *     Copies and allocations are ordered on that stream too (stream-ordered allocator), so
+ *     creating, reading or destroying one context never waits for another context's work.
+ *     A device array the caller passes must be ready before the call (its producer finished or
+ *     ordered before the context's stream).
  *   - Errors: every call returns an rwmi_status. RWMI_E_INVALID leaves the context unchanged.
  *     Any other negative status leaves it unusable until rwmi_destroy. Positive values are
  *     warnings. rwmi_last_error gives a message. Nothing is thrown across the ABI; nothing
@@ -54,6 +58,7 @@ typedef enum {
                                 some walker (Section 2.4.2: "an error is reported"); the walker
                                 stayed where it was. Also refill failures. */
     RWMI_W_SEED = 2,         /* some walker found no free seed point (see rwmi_seed_walkers) */
+    RWMI_BUSY = 3,           /* rwmi_query: GPU work of the context is still running */
     RWMI_E_INVALID = -1,     /* bad argument or size; context unchanged */
     RWMI_E_OOM = -2,         /* device allocation failed */
     RWMI_E_CUDA = -3,        /* a CUDA runtime call or kernel launch failed */
@@ -85,6 +90,8 @@ typedef struct {
     int32_t moment_interval;   /* append FP64 walker moments to the series every this many
                                   steps (0: never). Default 0. */
     int32_t use_graphs;        /* replay captured CUDA graphs for repeated steps. Default 1. */
+    int32_t lbm_block;         /* threads per block of the LBM kernel: 64, 128 or 256 (0: 256);
+                                  rwmi_autotune picks it by timing. */
 } rwmi_config;
 
 /* Fills *cfg with the defaults listed above. */
@@ -153,6 +160,21 @@ enum {
  * (milliseconds, summed over the n steps) to phase_ms[RWMI_NPHASE]. Same results as rwmi_step. */
 RWMI_API rwmi_status rwmi_step_timed(rwmi_ctx* ctx, int32_t n, double* phase_ms);
 
+/* Times the LBM kernel on the current state for each block size (64, 128, 256), writing only the
+ * idle population buffer and the velocity field (both are overwritten by the next step), and
+ * keeps the fastest in the configuration; *chosen (may be NULL) receives it. A project-written
+ * tuner: small or oddly shaped boxes favour smaller blocks. */
+RWMI_API rwmi_status rwmi_autotune(rwmi_ctx* ctx, int32_t* chosen);
+
+/* Non-blocking: RWMI_BUSY while GPU work of the context is in flight, RWMI_OK when it is idle. */
+RWMI_API rwmi_status rwmi_query(rwmi_ctx* ctx);
+
+/* Device memory a context of these sizes needs, in bytes (populations, velocity, solid words,
+ * bricks, walkers with their sort and resolve buffers, particle tables), before it is created;
+ * used to admit work by HBM footprint. */
+RWMI_API rwmi_status rwmi_footprint(const int32_t dims[3], int32_t q, int32_t storage, int64_t n_walkers,
+                                    int32_t n_particles, int32_t n_centers, uint64_t* bytes);
+
 /* Waits for the context's stream and returns the first pending device condition:
  * RWMI_E_NONFINITE, RWMI_W_BISECT, or RWMI_OK. Clears the warning counters it reports. */
 RWMI_API rwmi_status rwmi_sync(rwmi_ctx* ctx);
@@ -219,6 +241,30 @@ RWMI_API rwmi_status rwmi_counters(rwmi_ctx* ctx, int64_t out[12]);
  * walker id and step). */
 RWMI_API rwmi_status rwmi_save(rwmi_ctx* ctx, const char* path);
 RWMI_API rwmi_status rwmi_load(rwmi_ctx* ctx, const char* path);
+
+/* ---- Batched contexts ------------------------------------------------------------------
+ * Many independent simulations (each its own context: box, particles, walkers, tau, D) advanced
+ * together. Each chunk of steps of every context is captured once into one CUDA graph whose
+ * branches run concurrently (one per context stream); later chunks replay it, so one graph
+ * launch advances all contexts. The step of each context is exactly its rwmi_step (same
+ * kernels, same results bit for bit). The paper has no batching; each context follows the same
+ * equations as rwmi_step. */
+typedef struct rwmi_batch rwmi_batch;
+
+/* Groups n contexts (not owned: they must outlive the batch). All must share the chunk length
+ * lcm(2, sort_interval, moment_interval) <= 64. Streams of the contexts should be distinct for
+ * the branches to overlap. */
+RWMI_API rwmi_status rwmi_batch_create(rwmi_batch** batch, rwmi_ctx* const* ctxs, int32_t n);
+
+/* Advances every context by n steps (a multiple of the chunk; every context at a chunk
+ * boundary, else RWMI_E_STATE). Asynchronous; later work on each context's stream waits for it. */
+RWMI_API rwmi_status rwmi_batch_step(rwmi_batch* batch, int32_t n);
+
+/* Waits for the batch and returns the worst rwmi_sync status of its contexts. */
+RWMI_API rwmi_status rwmi_batch_sync(rwmi_batch* batch);
+
+RWMI_API const char* rwmi_batch_last_error(const rwmi_batch* batch);
+RWMI_API void rwmi_batch_destroy(rwmi_batch* batch);
 
 /* Binning and cell-sorting of walkers for callers that cannot allocate device memory. This entry
  * point has no counterpart in the paper; it is the concentration count of the library's own

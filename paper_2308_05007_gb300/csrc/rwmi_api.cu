@@ -98,6 +98,18 @@ struct rwmi_ctx {
   cudaEvent_t ev[2 * RWMI_NPHASE] = {};
 };
 
+// Many contexts advanced together: one CUDA graph per chunk forks every context's steps onto
+// its own stream (concurrent branches) and joins them on the batch's stream.
+struct rwmi_batch {
+  std::vector<rwmi_ctx*> ctxs;
+  cudaStream_t origin = nullptr;
+  cudaEvent_t fork = nullptr, done = nullptr;
+  std::vector<cudaEvent_t> join;
+  std::map<std::vector<int>, std::pair<cudaGraphExec_t, std::vector<int64_t>>> graphs;
+  int64_t L = 2;
+  std::string err;
+};
+
 namespace {
 
 rwmi_status fail(rwmi_ctx* c, rwmi_status s, const std::string& msg) {
@@ -113,15 +125,24 @@ rwmi_status fail(rwmi_ctx* c, rwmi_status s, const std::string& msg) {
                   std::string(#call) + ": " + cudaGetErrorString(e_));                 \
   } while (0)
 
+// Device memory is stream-ordered on the context's stream: creating or destroying one context
+// never synchronises the device, so other contexts' work keeps running meanwhile.
 template <typename T>
-cudaError_t dalloc(T** p, size_t bytes) {
+cudaError_t dalloc(rwmi_ctx* c, T** p, size_t bytes) {
   *p = nullptr;
   if (bytes == 0) bytes = 16;
-  return cudaMalloc((void**)p, bytes);
+  return cudaMallocAsync((void**)p, bytes, c->stream);
 }
 
-void dfree(void* p) {
-  if (p) cudaFree(p);
+void dfree(rwmi_ctx* c, void* p) {
+  if (p) cudaFreeAsync(p, c->stream);
+}
+
+// Blocking copy ordered on the context's stream (never on the legacy default stream, which
+// would wait for every other blocking stream of the process).
+cudaError_t copy_now(rwmi_ctx* c, void* dst, const void* src, size_t bytes) {
+  const cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, c->stream);
+  return e != cudaSuccess ? e : cudaStreamSynchronize(c->stream);
 }
 
 size_t storage_bytes(int storage) { return storage == 2 ? 2 : 4; }
@@ -144,10 +165,10 @@ rwmi_status copy_out(rwmi_ctx* c, void* dst, const void* src, size_t bytes) {
 
 rwmi_status ensure_scratch(rwmi_ctx* c, size_t bytes) {
   if (c->scratch_bytes >= bytes) return RWMI_OK;
-  dfree(c->scratch);
+  dfree(c, c->scratch);
   c->scratch = nullptr;
   c->scratch_bytes = 0;
-  CK(dalloc(&c->scratch, bytes));
+  CK(dalloc(c, &c->scratch, bytes));
   c->scratch_bytes = bytes;
   return RWMI_OK;
 }
@@ -213,25 +234,25 @@ rwmi_status reset_fluid(rwmi_ctx* c) {
 
 rwmi_status alloc_fluid(rwmi_ctx* c) {
   for (int k = 0; k < 2; ++k) {
-    dfree(c->f[k]);
+    dfree(c, c->f[k]);
     c->f[k] = nullptr;
   }
   const size_t pop = (size_t)c->cfg.q * c->g.ncell_pad * storage_bytes(c->cfg.storage);
-  for (int k = 0; k < 2; ++k) CK(dalloc(&c->f[k], pop));
+  for (int k = 0; k < 2; ++k) CK(dalloc(c, &c->f[k], pop));
   return RWMI_OK;
 }
 
 rwmi_status alloc_particles(rwmi_ctx* c) {
   for (int k = 0; k < 2; ++k) {
-    dfree(c->pose[k]);
-    dfree(c->cworld[k]);
-    dfree(c->acc[k]);
+    dfree(c, c->pose[k]);
+    dfree(c, c->cworld[k]);
+    dfree(c, c->acc[k]);
     c->pose[k] = nullptr;
     c->cworld[k] = nullptr;
     c->acc[k] = nullptr;
-    CK(dalloc(&c->pose[k], sizeof(PoseF) * (size_t)(c->P > 0 ? c->P : 1)));
-    CK(dalloc(&c->cworld[k], sizeof(float4) * (size_t)(c->Nc > 0 ? c->Nc : 1)));
-    CK(dalloc(&c->acc[k], sizeof(double) * (size_t)(6 * c->P + 4 * RED_SLOTS)));
+    CK(dalloc(c, &c->pose[k], sizeof(PoseF) * (size_t)(c->P > 0 ? c->P : 1)));
+    CK(dalloc(c, &c->cworld[k], sizeof(float4) * (size_t)(c->Nc > 0 ? c->Nc : 1)));
+    CK(dalloc(c, &c->acc[k], sizeof(double) * (size_t)(6 * c->P + 4 * RED_SLOTS)));
     CK(cudaMemsetAsync(c->acc[k], 0, sizeof(double) * (size_t)(6 * c->P + 4 * RED_SLOTS), c->stream));
   }
   return RWMI_OK;
@@ -239,22 +260,22 @@ rwmi_status alloc_particles(rwmi_ctx* c) {
 
 rwmi_status alloc_walkers(rwmi_ctx* c, int64_t n) {
   for (int k = 0; k < 2; ++k) {
-    dfree(c->pos[k]);
-    dfree(c->x0[k]);
+    dfree(c, c->pos[k]);
+    dfree(c, c->x0[k]);
     c->pos[k] = nullptr;
     c->x0[k] = nullptr;
   }
-  dfree(c->rank);
-  dfree(c->wlist);
+  dfree(c, c->rank);
+  dfree(c, c->wlist);
   c->rank = nullptr;
   c->wlist = nullptr;
   c->nw = 0;
   for (int k = 0; k < 2; ++k) {
-    CK(dalloc(&c->pos[k], sizeof(float4) * (size_t)n));
-    CK(dalloc(&c->x0[k], sizeof(float4) * (size_t)n));
+    CK(dalloc(c, &c->pos[k], sizeof(float4) * (size_t)n));
+    CK(dalloc(c, &c->x0[k], sizeof(float4) * (size_t)n));
   }
-  CK(dalloc(&c->rank, sizeof(uint32_t) * (size_t)n));
-  CK(dalloc(&c->wlist, 2 * sizeof(float4) * (size_t)n));
+  CK(dalloc(c, &c->rank, sizeof(uint32_t) * (size_t)n));
+  CK(dalloc(c, &c->wlist, 2 * sizeof(float4) * (size_t)n));
   c->nw = n;
   c->pcur = 0;
   c->binned_t = -1;
@@ -292,7 +313,7 @@ void enqueue_step(rwmi_ctx* c, bool reduce) {
   phase_begin(c, RWMI_PHASE_LBM);
   launch_lbm(c->cfg.q, c->cfg.storage, reduce, c->g, c->f[c->fcur], c->f[c->fcur ^ 1], c->u, c->solid,
              brick_set(c, tp), (float)c->tau, (float)c->cfg.rho0, c->acc[tp] + 6 * c->P, c->acc[tp],
-             c->status, c->stream);
+             c->status, c->stream, c->cfg.lbm_block);
   c->launches++;
   phase_end(c, RWMI_PHASE_LBM);
   c->fcur ^= 1;
@@ -338,6 +359,19 @@ void enqueue_step(rwmi_ctx* c, bool reduce) {
   phase_end(c, RWMI_PHASE_MOMENTS);
 }
 
+// Host mirrors of a replayed chunk of L steps (what enqueue_step does while capturing).
+void advance_mirrors(rwmi_ctx* c, int64_t L) {
+  for (int64_t s = 0; s < L; ++s) {
+    c->fcur ^= 1;
+    c->t += 1;
+    if (c->nw > 0 && c->cfg.sort_interval > 0 && c->t % c->cfg.sort_interval == 0) {
+      c->pcur ^= 1;
+      c->binned_t = c->t;
+    }
+    if (c->cfg.moment_interval > 0 && c->t % c->cfg.moment_interval == 0) c->series_rows++;
+  }
+}
+
 int64_t chunk_length(const rwmi_ctx* c) {
   auto gcd = [](int64_t a, int64_t b) { while (b) { int64_t t = a % b; a = b; b = t; } return a; };
   int64_t L = 2;
@@ -364,6 +398,7 @@ RWMI_API void rwmi_config_defaults(rwmi_config* cfg) {
   cfg->sort_interval = 16;
   cfg->moment_interval = 0;
   cfg->use_graphs = 1;
+  cfg->lbm_block = 256;
 }
 
 RWMI_API rwmi_status rwmi_create(rwmi_ctx** out, const int32_t dims[3], double tau, double D,
@@ -405,29 +440,29 @@ RWMI_API rwmi_status rwmi_create(rwmi_ctx** out, const int32_t dims[3], double t
     c->own_stream = true;
     rwmi_status s = alloc_fluid(c);
     if (s != RWMI_OK) return s;
-    CK(dalloc(&c->u, sizeof(float4) * (size_t)g.ncell_pad));   // (u, rho) per cell
-    CK(dalloc(&c->solid, sizeof(uint16_t) * (size_t)ncell));
-    CK(dalloc(&c->d_T, sizeof(int64_t)));
-    CK(dalloc(&c->ticket, sizeof(unsigned int)));
-    CK(dalloc(&c->wlist_n, sizeof(unsigned int)));
+    CK(dalloc(c, &c->u, sizeof(float4) * (size_t)g.ncell_pad));   // (u, rho) per cell
+    CK(dalloc(c, &c->solid, sizeof(uint16_t) * (size_t)ncell));
+    CK(dalloc(c, &c->d_T, sizeof(int64_t)));
+    CK(dalloc(c, &c->ticket, sizeof(unsigned int)));
+    CK(dalloc(c, &c->wlist_n, sizeof(unsigned int)));
     CK(cudaMemsetAsync(c->wlist_n, 0, sizeof(unsigned int), c->stream));
-    CK(dalloc(&c->status, sizeof(unsigned long long) * ST_COUNT));
-    CK(dalloc(&c->macc, sizeof(double) * 12));
-    CK(dalloc(&c->series, sizeof(double) * (size_t)SERIES_ROWS * SERIES_COLS));
-    CK(dalloc(&c->mrow, sizeof(double) * SERIES_COLS));
-    CK(dalloc(&c->counts, sizeof(uint32_t) * (size_t)ncell));
-    CK(dalloc(&c->wmask, sizeof(uint64_t) * c->nbrick));
-    CK(dalloc(&c->offsets, sizeof(uint32_t) * (size_t)ncell));
-    CK(dalloc(&c->bsums, sizeof(uint32_t) * scan_block_sums_size((uint32_t)ncell)));
+    CK(dalloc(c, &c->status, sizeof(unsigned long long) * ST_COUNT));
+    CK(dalloc(c, &c->macc, sizeof(double) * 12));
+    CK(dalloc(c, &c->series, sizeof(double) * (size_t)SERIES_ROWS * SERIES_COLS));
+    CK(dalloc(c, &c->mrow, sizeof(double) * SERIES_COLS));
+    CK(dalloc(c, &c->counts, sizeof(uint32_t) * (size_t)ncell));
+    CK(dalloc(c, &c->wmask, sizeof(uint64_t) * c->nbrick));
+    CK(dalloc(c, &c->offsets, sizeof(uint32_t) * (size_t)ncell));
+    CK(dalloc(c, &c->bsums, sizeof(uint32_t) * scan_block_sums_size((uint32_t)ncell)));
     for (int k = 0; k < 2; ++k) {
-      CK(dalloc(&c->bword[k], sizeof(uint32_t) * (c->nbrick + 1)));
-      CK(dalloc(&c->bcand[k], sizeof(uint16_t) * (size_t)c->nbrick * MAXC));
-      CK(dalloc(&c->rlist[k], sizeof(int32_t) * c->nbrick));
-      CK(dalloc(&c->sp[k], sizeof(StepParams)));
+      CK(dalloc(c, &c->bword[k], sizeof(uint32_t) * (c->nbrick + 1)));
+      CK(dalloc(c, &c->bcand[k], sizeof(uint16_t) * (size_t)c->nbrick * MAXC));
+      CK(dalloc(c, &c->rlist[k], sizeof(int32_t) * c->nbrick));
+      CK(dalloc(c, &c->sp[k], sizeof(StepParams)));
       CK(cudaMemsetAsync(c->sp[k], 0, sizeof(StepParams), c->stream));
     }
-    CK(dalloc(&c->desc, sizeof(ParticleDesc)));
-    CK(dalloc(&c->cbody, sizeof(float4)));
+    CK(dalloc(c, &c->desc, sizeof(ParticleDesc)));
+    CK(dalloc(c, &c->cbody, sizeof(float4)));
     s = alloc_particles(c);
     if (s != RWMI_OK) return s;
     CK(cudaMemsetAsync(c->d_T, 0, sizeof(int64_t), c->stream));
@@ -457,7 +492,8 @@ RWMI_API rwmi_status rwmi_configure(rwmi_ctx* c, const rwmi_config* cfg) {
   if (c->stepped) return fail(c, RWMI_E_STATE, "rwmi_configure: only before the first step");
   if ((cfg->q != 15 && cfg->q != 19) || cfg->storage < 0 || cfg->storage > 2 || cfg->wall_mask > 7 ||
       !(cfg->rho0 > 0.0) || cfg->sort_interval < 0 || cfg->moment_interval < 0 ||
-      !(cfg->force_period >= 0.0))
+      !(cfg->force_period >= 0.0) ||
+      !(cfg->lbm_block == 0 || cfg->lbm_block == 64 || cfg->lbm_block == 128 || cfg->lbm_block == 256))
     return fail(c, RWMI_E_INVALID, "rwmi_configure: bad q, storage, wall_mask, rho0 or interval");
   for (int a = 0; a < 3; ++a)
     if (!std::isfinite(cfg->body_force[a]) || !std::isfinite(cfg->init_velocity[a]))
@@ -542,16 +578,16 @@ RWMI_API rwmi_status rwmi_set_metaballs(rwmi_ctx* c, int32_t P, const int32_t* c
     d.rb = (float)(hi * (1.0 + 1e-6) + 1e-4);
   }
   for (int i = 0; i < Nc; ++i) body[i] = make_float4(cb[3 * i], cb[3 * i + 1], cb[3 * i + 2], k[i]);
-  dfree(c->desc);
-  dfree(c->cbody);
+  dfree(c, c->desc);
+  dfree(c, c->cbody);
   c->desc = nullptr;
   c->cbody = nullptr;
   c->P = P;
   c->Nc = Nc;
-  CK(dalloc(&c->desc, sizeof(ParticleDesc) * desc.size()));
-  CK(dalloc(&c->cbody, sizeof(float4) * body.size()));
-  CK(cudaMemcpy(c->desc, desc.data(), sizeof(ParticleDesc) * desc.size(), cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(c->cbody, body.data(), sizeof(float4) * body.size(), cudaMemcpyHostToDevice));
+  CK(dalloc(c, &c->desc, sizeof(ParticleDesc) * desc.size()));
+  CK(dalloc(c, &c->cbody, sizeof(float4) * body.size()));
+  CK(copy_now(c, c->desc, desc.data(), sizeof(ParticleDesc) * desc.size()));
+  CK(copy_now(c, c->cbody, body.data(), sizeof(float4) * body.size()));
   rwmi_status s = alloc_particles(c);
   if (s != RWMI_OK) return s;
   drop_graphs(c);
@@ -637,16 +673,7 @@ RWMI_API rwmi_status rwmi_step(rwmi_ctx* c, int32_t n) {
       } else {
         CK(cudaGraphLaunch(it->second.exec, c->stream));
         c->launches += it->second.launches;
-        // advance the host mirrors as the captured chunk does
-        for (int64_t s = 0; s < L; ++s) {
-          c->fcur ^= 1;
-          c->t += 1;
-          if (c->nw > 0 && c->cfg.sort_interval > 0 && c->t % c->cfg.sort_interval == 0) {
-            c->pcur ^= 1;
-            c->binned_t = c->t;
-          }
-          if (c->cfg.moment_interval > 0 && c->t % c->cfg.moment_interval == 0) c->series_rows++;
-        }
+        advance_mirrors(c, L);
       }
       n -= (int32_t)L;
     } else {
@@ -681,11 +708,82 @@ RWMI_API rwmi_status rwmi_step_timed(rwmi_ctx* c, int32_t n, double* phase_ms) {
   return RWMI_OK;
 }
 
+RWMI_API rwmi_status rwmi_autotune(rwmi_ctx* c, int32_t* chosen) {
+  if (!c) return RWMI_E_INVALID;
+  const int tp = (int)(c->t & 1);
+  const size_t acc_n = (size_t)(6 * c->P + 4 * RED_SLOTS);
+  rwmi_status s = ensure_scratch(c, sizeof(double) * acc_n);   // throw-away force/mass sums
+  if (s != RWMI_OK) return s;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  const int cand[3] = {64, 128, 256};
+  float best_ms = 1e30f;
+  int best = 256;
+  for (int k = 0; k < 3; ++k) {
+    for (int rep = 0; rep < 6; ++rep) {
+      if (rep == 1) cudaEventRecord(e0, c->stream);
+      launch_lbm(c->cfg.q, c->cfg.storage, false, c->g, c->f[c->fcur], c->f[c->fcur ^ 1], c->u, c->solid,
+                 brick_set(c, tp), (float)c->tau, (float)c->cfg.rho0, (double*)c->scratch + 6 * c->P,
+                 (double*)c->scratch, c->status, c->stream, cand[k]);
+      c->launches++;
+    }
+    cudaEventRecord(e1, c->stream);
+    cudaError_t e = cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      CK(e);
+    }
+    if (ms < best_ms) { best_ms = ms; best = cand[k]; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  CK(cudaGetLastError());
+  c->cfg.lbm_block = best;
+  drop_graphs(c);
+  if (chosen) *chosen = best;
+  return RWMI_OK;
+}
+
+RWMI_API rwmi_status rwmi_query(rwmi_ctx* c) {
+  if (!c) return RWMI_E_INVALID;
+  const cudaError_t e = cudaStreamQuery(c->stream);
+  if (e == cudaErrorNotReady) return RWMI_BUSY;
+  CK(e);
+  return RWMI_OK;
+}
+
+RWMI_API rwmi_status rwmi_footprint(const int32_t dims[3], int32_t q, int32_t storage, int64_t n_walkers,
+                                    int32_t n_particles, int32_t n_centers, uint64_t* bytes) {
+  if (!dims || !bytes || (q != 15 && q != 19) || storage < 0 || storage > 2 || n_walkers < 0 ||
+      n_particles < 0 || n_centers < 0)
+    return RWMI_E_INVALID;
+  uint64_t ncell = 1, nbrick = 1;
+  for (int a = 0; a < 3; ++a) {
+    if (dims[a] < 1) return RWMI_E_INVALID;
+    ncell *= (uint64_t)dims[a];
+    nbrick *= (uint64_t)((dims[a] + BRICK - 1) / BRICK);
+  }
+  const uint64_t pad = (ncell + 63) / 64 * 64, sb = storage == 2 ? 2 : 4, P = (uint64_t)n_particles,
+                 Nc = (uint64_t)n_centers, N = (uint64_t)n_walkers;
+  uint64_t b = 2 * (uint64_t)q * pad * sb;                     // populations A/B
+  b += 16 * pad + 2 * ncell + 8 * ncell + 4 * (ncell / 2048 + 2);   // (u, rho), solid, counts/offsets, scan
+  b += 2 * (4 * (nbrick + 1) + 2 * MAXC * nbrick + 4 * nbrick) + 8 * nbrick;   // bricks, masks
+  b += 100 * N;                                                // pos, x0 (A/B), rank, resolve list
+  b += 2 * 48 * P + 2 * 16 * Nc + sizeof(ParticleDesc) * P + 16 * Nc + 2 * 8 * (6 * P + 4 * RED_SLOTS);
+  b += (uint64_t)SERIES_ROWS * SERIES_COLS * 8 + 4096;         // moment series, counters
+  *bytes = b;
+  return RWMI_OK;
+}
+
 RWMI_API rwmi_status rwmi_sync(rwmi_ctx* c) {
   if (!c) return RWMI_E_INVALID;
   CK(cudaStreamSynchronize(c->stream));
   unsigned long long st[ST_COUNT];
-  CK(cudaMemcpy(st, c->status, sizeof(st), cudaMemcpyDeviceToHost));
+  CK(copy_now(c, st, c->status, sizeof(st)));
   rwmi_status r = RWMI_OK;
   if (st[ST_NONFINITE] > c->status_seen[ST_NONFINITE]) r = fail(c, RWMI_E_NONFINITE, "non-finite walker velocity");
   else if (st[ST_BISECT_FAIL] > c->status_seen[ST_BISECT_FAIL] || st[ST_REFILL_FAIL] > c->status_seen[ST_REFILL_FAIL])
@@ -733,13 +831,13 @@ RWMI_API rwmi_status rwmi_moment_series(rwmi_ctx* c, double* out, int32_t max_ro
   const int64_t take = std::min<int64_t>(avail, max_rows);
   std::vector<double> ring((size_t)SERIES_ROWS * SERIES_COLS);
   CK(cudaStreamSynchronize(c->stream));
-  CK(cudaMemcpy(ring.data(), c->series, sizeof(double) * ring.size(), cudaMemcpyDeviceToHost));
+  CK(copy_now(c, ring.data(), c->series, sizeof(double) * ring.size()));
   std::vector<double> rows((size_t)take * SERIES_COLS);
   const int64_t first = c->series_rows - take;
   for (int64_t r = 0; r < take; ++r)
     std::memcpy(&rows[(size_t)r * SERIES_COLS], &ring[(size_t)((first + r) % SERIES_ROWS) * SERIES_COLS],
                 sizeof(double) * SERIES_COLS);
-  if (take > 0) CK(cudaMemcpy(out, rows.data(), sizeof(double) * rows.size(), cudaMemcpyDefault));
+  if (take > 0) CK(copy_now(c, out, rows.data(), sizeof(double) * rows.size()));
   *n_rows = (int32_t)take;
   return RWMI_OK;
 }
@@ -819,7 +917,7 @@ RWMI_API rwmi_status rwmi_particle_forces(rwmi_ctx* c, double* out) {
   if (c->P == 0) return RWMI_OK;
   if (c->t == 0) {
     std::vector<double> z((size_t)6 * c->P, 0.0);
-    CK(cudaMemcpy(out, z.data(), sizeof(double) * z.size(), cudaMemcpyDefault));
+    CK(copy_now(c, out, z.data(), sizeof(double) * z.size()));
     return RWMI_OK;
   }
   return copy_out(c, out, c->acc[(c->t - 1) & 1], sizeof(double) * 6 * (size_t)c->P);
@@ -843,7 +941,7 @@ RWMI_API rwmi_status rwmi_counters(rwmi_ctx* c, int64_t out[12]) {
   if (!c || !out) return RWMI_E_INVALID;
   CK(cudaStreamSynchronize(c->stream));
   unsigned long long st[ST_COUNT];
-  CK(cudaMemcpy(st, c->status, sizeof(st), cudaMemcpyDeviceToHost));
+  CK(copy_now(c, st, c->status, sizeof(st)));
   for (int m = 0; m < 8; ++m) out[m] = (int64_t)st[m];
   out[8] = (int64_t)st[ST_NONFINITE];
   out[9] = (int64_t)st[ST_FAST_SPEED];
@@ -858,10 +956,10 @@ RWMI_API rwmi_status rwmi_save(rwmi_ctx* c, const char* path) {
   const size_t pop = (size_t)c->cfg.q * c->g.ncell_pad * storage_bytes(c->cfg.storage);
   std::vector<char> f(pop);
   std::vector<float4> p((size_t)c->nw), q((size_t)c->nw);
-  CK(cudaMemcpy(f.data(), c->f[c->fcur], pop, cudaMemcpyDeviceToHost));
+  CK(copy_now(c, f.data(), c->f[c->fcur], pop));
   if (c->nw) {
-    CK(cudaMemcpy(p.data(), c->pos[c->pcur], sizeof(float4) * p.size(), cudaMemcpyDeviceToHost));
-    CK(cudaMemcpy(q.data(), c->x0[c->pcur], sizeof(float4) * q.size(), cudaMemcpyDeviceToHost));
+    CK(copy_now(c, p.data(), c->pos[c->pcur], sizeof(float4) * p.size()));
+    CK(copy_now(c, q.data(), c->x0[c->pcur], sizeof(float4) * q.size()));
   }
   FILE* fp = std::fopen(path, "wb");
   if (!fp) return fail(c, RWMI_E_INVALID, std::string("rwmi_save: cannot open ") + path);
@@ -906,12 +1004,12 @@ RWMI_API rwmi_status rwmi_load(rwmi_ctx* c, const char* path) {
   c->binned_t = -1;
   c->stepped = true;
   drop_graphs(c);
-  CK(cudaMemcpy(c->f[c->fcur], f.data(), pop, cudaMemcpyHostToDevice));
+  CK(copy_now(c, c->f[c->fcur], f.data(), pop));
   if (nw) {
-    CK(cudaMemcpy(c->pos[0], p.data(), sizeof(float4) * p.size(), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(c->x0[0], q.data(), sizeof(float4) * q.size(), cudaMemcpyHostToDevice));
+    CK(copy_now(c, c->pos[0], p.data(), sizeof(float4) * p.size()));
+    CK(copy_now(c, c->x0[0], q.data(), sizeof(float4) * q.size()));
   }
-  CK(cudaMemcpy(c->d_T, &c->t, sizeof(int64_t), cudaMemcpyHostToDevice));
+  CK(copy_now(c, c->d_T, &c->t, sizeof(int64_t)));
   rwmi_status s = build_current_frame(c);
   if (s != RWMI_OK) return s;
   CK(cudaStreamSynchronize(c->stream));
@@ -922,7 +1020,7 @@ RWMI_API rwmi_status rwmi_brick_stats(rwmi_ctx* c, int64_t out[4]) {
   if (!c || !out) return RWMI_E_INVALID;
   std::vector<uint32_t> w((size_t)c->nbrick + 1);
   CK(cudaStreamSynchronize(c->stream));
-  CK(cudaMemcpy(w.data(), c->bword[c->t & 1], sizeof(uint32_t) * w.size(), cudaMemcpyDeviceToHost));
+  CK(copy_now(c, w.data(), c->bword[c->t & 1], sizeof(uint32_t) * w.size()));
   int64_t rast = 0, walk = 0, mx = 0, over = 0;
   for (uint32_t b = 0; b < c->nbrick; ++b) {
     const int64_t nc = w[b] & 0xffffu;
@@ -934,6 +1032,123 @@ RWMI_API rwmi_status rwmi_brick_stats(rwmi_ctx* c, int64_t out[4]) {
   out[0] = rast; out[1] = walk; out[2] = mx; out[3] = over;
   return RWMI_OK;
 }
+
+static rwmi_status batch_fail(rwmi_batch* b, rwmi_status s, const std::string& msg) {
+  if (b) b->err = msg;
+  return s;
+}
+
+#define BCK(call)                                                                          \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess)                                                                 \
+      return batch_fail(b, RWMI_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+RWMI_API void rwmi_batch_destroy(rwmi_batch* b);
+
+RWMI_API rwmi_status rwmi_batch_create(rwmi_batch** out, rwmi_ctx* const* ctxs, int32_t n) {
+  if (!out || !ctxs || n < 1) return RWMI_E_INVALID;
+  *out = nullptr;
+  rwmi_batch* b = new rwmi_batch();
+  for (int32_t k = 0; k < n; ++k) {
+    if (!ctxs[k]) { delete b; return RWMI_E_INVALID; }
+    b->ctxs.push_back(ctxs[k]);
+  }
+  b->L = chunk_length(ctxs[0]);
+  for (rwmi_ctx* c : b->ctxs)
+    if (chunk_length(c) != b->L || b->L > 64) {
+      delete b;
+      return RWMI_E_INVALID;   // contexts must share their sort / moment cadence
+    }
+  auto init = [&]() -> rwmi_status {
+    BCK(cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking));
+    BCK(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
+    BCK(cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming));
+    b->join.resize(b->ctxs.size());
+    for (auto& e : b->join) BCK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    return RWMI_OK;
+  };
+  rwmi_status st = init();
+  if (st != RWMI_OK) { rwmi_batch_destroy(b); return st; }
+  *out = b;
+  return RWMI_OK;
+}
+
+RWMI_API rwmi_status rwmi_batch_step(rwmi_batch* b, int32_t nsteps) {
+  if (!b || nsteps < 0) return RWMI_E_INVALID;
+  if (nsteps % b->L != 0) return batch_fail(b, RWMI_E_INVALID, "rwmi_batch_step: steps must be a multiple of the chunk");
+  for (rwmi_ctx* c : b->ctxs)
+    if (c->t % b->L != 0) return batch_fail(b, RWMI_E_STATE, "rwmi_batch_step: a context is not at a chunk boundary");
+  // the contexts' own queued work precedes the batch
+  for (rwmi_ctx* c : b->ctxs) {
+    BCK(cudaEventRecord(b->done, c->stream));
+    BCK(cudaStreamWaitEvent(b->origin, b->done, 0));
+  }
+  for (int32_t done_steps = 0; done_steps < nsteps; done_steps += (int32_t)b->L) {
+    std::vector<int> key;
+    for (rwmi_ctx* c : b->ctxs) { key.push_back(c->fcur); key.push_back(c->pcur); c->stepped = true; }
+    auto it = b->graphs.find(key);
+    if (it == b->graphs.end()) {
+      std::vector<int64_t> l0;
+      for (rwmi_ctx* c : b->ctxs) l0.push_back(c->launches);
+      BCK(cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal));
+      cudaEventRecord(b->fork, b->origin);
+      for (size_t k = 0; k < b->ctxs.size(); ++k) {
+        rwmi_ctx* c = b->ctxs[k];
+        cudaStreamWaitEvent(c->stream, b->fork, 0);
+        for (int64_t st = 0; st < b->L; ++st) enqueue_step(c, st == b->L - 1);
+        cudaEventRecord(b->join[k], c->stream);
+        cudaStreamWaitEvent(b->origin, b->join[k], 0);
+      }
+      cudaGraph_t graph = nullptr;
+      BCK(cudaStreamEndCapture(b->origin, &graph));
+      cudaGraphExec_t exec = nullptr;
+      cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+      cudaGraphDestroy(graph);
+      BCK(ie);
+      std::vector<int64_t> dl;
+      for (size_t k = 0; k < b->ctxs.size(); ++k) dl.push_back(b->ctxs[k]->launches - l0[k]);
+      b->graphs[key] = std::make_pair(exec, dl);
+      BCK(cudaGraphLaunch(exec, b->origin));   // mirrors advanced while capturing
+    } else {
+      BCK(cudaGraphLaunch(it->second.first, b->origin));
+      for (size_t k = 0; k < b->ctxs.size(); ++k) {
+        b->ctxs[k]->launches += it->second.second[k];
+        advance_mirrors(b->ctxs[k], b->L);
+      }
+    }
+  }
+  // later work on each context's stream follows the batch
+  BCK(cudaEventRecord(b->done, b->origin));
+  for (rwmi_ctx* c : b->ctxs) BCK(cudaStreamWaitEvent(c->stream, b->done, 0));
+  return RWMI_OK;
+}
+
+RWMI_API rwmi_status rwmi_batch_sync(rwmi_batch* b) {
+  if (!b) return RWMI_E_INVALID;
+  BCK(cudaStreamSynchronize(b->origin));
+  rwmi_status worst = RWMI_OK;
+  for (rwmi_ctx* c : b->ctxs) {
+    const rwmi_status s = rwmi_sync(c);
+    if (s < 0 && (worst >= 0 || s < worst)) worst = s;
+    else if (worst == RWMI_OK && s > 0) worst = s;
+  }
+  return worst;
+}
+
+RWMI_API void rwmi_batch_destroy(rwmi_batch* b) {
+  if (!b) return;
+  if (b->origin) cudaStreamSynchronize(b->origin);
+  for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second.first);
+  for (auto e : b->join) if (e) cudaEventDestroy(e);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->done) cudaEventDestroy(b->done);
+  if (b->origin) cudaStreamDestroy(b->origin);
+  delete b;
+}
+
+RWMI_API const char* rwmi_batch_last_error(const rwmi_batch* b) { return b ? b->err.c_str() : "null batch"; }
 
 RWMI_API const char* rwmi_last_error(const rwmi_ctx* c) { return c ? c->err.c_str() : noalloc_last_error(); }
 
@@ -949,13 +1164,14 @@ RWMI_API void rwmi_destroy(rwmi_ctx* c) {
   }
   drop_graphs(c);
   for (int k = 0; k < 2; ++k) {
-    dfree(c->f[k]); dfree(c->acc[k]); dfree(c->bword[k]); dfree(c->bcand[k]); dfree(c->rlist[k]);
-    dfree(c->pose[k]); dfree(c->sp[k]); dfree(c->cworld[k]); dfree(c->pos[k]); dfree(c->x0[k]);
+    dfree(c, c->f[k]); dfree(c, c->acc[k]); dfree(c, c->bword[k]); dfree(c, c->bcand[k]); dfree(c, c->rlist[k]);
+    dfree(c, c->pose[k]); dfree(c, c->sp[k]); dfree(c, c->cworld[k]); dfree(c, c->pos[k]); dfree(c, c->x0[k]);
   }
-  dfree(c->wlist); dfree(c->wlist_n);
-  dfree(c->u); dfree(c->solid); dfree(c->d_T); dfree(c->ticket); dfree(c->status); dfree(c->macc);
-  dfree(c->series); dfree(c->mrow); dfree(c->desc); dfree(c->cbody); dfree(c->rank);
-  dfree(c->counts); dfree(c->offsets); dfree(c->bsums); dfree(c->scratch); dfree(c->wmask);
+  dfree(c, c->wlist); dfree(c, c->wlist_n);
+  dfree(c, c->u); dfree(c, c->solid); dfree(c, c->d_T); dfree(c, c->ticket); dfree(c, c->status); dfree(c, c->macc);
+  dfree(c, c->series); dfree(c, c->mrow); dfree(c, c->desc); dfree(c, c->cbody); dfree(c, c->rank);
+  dfree(c, c->counts); dfree(c, c->offsets); dfree(c, c->bsums); dfree(c, c->scratch); dfree(c, c->wmask);
+  cudaStreamSynchronize(c->stream);   // the frees have returned the memory when this returns
   for (int k = 0; k < 2 * RWMI_NPHASE; ++k)
     if (c->ev[k]) cudaEventDestroy(c->ev[k]);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);

@@ -773,7 +773,7 @@ __global__ void __launch_bounds__(256, 4) lbm_kernel(Geom g, Planes<Q, typename 
 template <int Q, int STORE>
 static void launch_lbm_q(bool walls, bool reduce, const Geom& g, const void* fin, void* fout, float* u,
                          const uint16_t* solid, BrickSet bs, float tau, float rho0, double* red,
-                         double* forces, cudaStream_t st) {
+                         double* forces, cudaStream_t st, int bsz) {
   using T = typename Store<STORE>::T;
   Planes<Q, T> pl;
   for (int i = 0; i < Q; ++i) {
@@ -781,7 +781,8 @@ static void launch_lbm_q(bool walls, bool reduce, const Geom& g, const void* fin
     pl.out[i] = (T*)fout + (size_t)i * g.ncell_pad;
   }
   float4* u4 = reinterpret_cast<float4*>(u);
-  const dim3 grid((g.ncell + 255) / 256), block(256);
+  const int bsz_ok = (bsz == 64 || bsz == 128) ? bsz : 256;
+  const dim3 grid((g.ncell + bsz_ok - 1) / bsz_ok), block(bsz_ok);
   if (walls) {
     if (reduce) lbm_kernel<Q, STORE, true, true><<<grid, block, 0, st>>>(g, pl, u4, solid, bs.bword, bs.pose, bs.sp, tau, rho0, red, forces);
     else lbm_kernel<Q, STORE, true, false><<<grid, block, 0, st>>>(g, pl, u4, solid, bs.bword, bs.pose, bs.sp, tau, rho0, red, forces);
@@ -793,17 +794,17 @@ static void launch_lbm_q(bool walls, bool reduce, const Geom& g, const void* fin
 
 void launch_lbm(int q, int storage, bool reduce, const Geom& g, const void* fin, void* fout,
                 float* u, const uint16_t* solid, BrickSet bs, float tau, float rho0, double* red,
-                double* forces, unsigned long long* status, cudaStream_t st) {
+                double* forces, unsigned long long* status, cudaStream_t st, int block) {
   (void)status;
   const bool walls = g.wall[0] || g.wall[1] || g.wall[2];
   if (q == 15) {
-    if (storage == 0) launch_lbm_q<15, 0>(walls, reduce, g, fin, fout, u, solid, bs, tau, rho0, red, forces, st);
-    else if (storage == 1) launch_lbm_q<15, 1>(walls, reduce, g, fin, fout, u, solid, bs, tau, rho0, red, forces, st);
-    else launch_lbm_q<15, 2>(walls, reduce, g, fin, fout, u, solid, bs, tau, rho0, red, forces, st);
+    if (storage == 0) launch_lbm_q<15, 0>(walls, reduce, g, fin, fout, u, solid, bs, tau, rho0, red, forces, st, block);
+    else if (storage == 1) launch_lbm_q<15, 1>(walls, reduce, g, fin, fout, u, solid, bs, tau, rho0, red, forces, st, block);
+    else launch_lbm_q<15, 2>(walls, reduce, g, fin, fout, u, solid, bs, tau, rho0, red, forces, st, block);
   } else {
-    if (storage == 0) launch_lbm_q<19, 0>(walls, reduce, g, fin, fout, u, solid, bs, tau, rho0, red, forces, st);
-    else if (storage == 1) launch_lbm_q<19, 1>(walls, reduce, g, fin, fout, u, solid, bs, tau, rho0, red, forces, st);
-    else launch_lbm_q<19, 2>(walls, reduce, g, fin, fout, u, solid, bs, tau, rho0, red, forces, st);
+    if (storage == 0) launch_lbm_q<19, 0>(walls, reduce, g, fin, fout, u, solid, bs, tau, rho0, red, forces, st, block);
+    else if (storage == 1) launch_lbm_q<19, 1>(walls, reduce, g, fin, fout, u, solid, bs, tau, rho0, red, forces, st, block);
+    else launch_lbm_q<19, 2>(walls, reduce, g, fin, fout, u, solid, bs, tau, rho0, red, forces, st, block);
   }
 }
 

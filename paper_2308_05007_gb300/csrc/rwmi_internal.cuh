@@ -210,7 +210,8 @@ void launch_raster(const Geom& g, const ParticleSet& ps, BrickSet bs, uint16_t* 
                    unsigned long long* status, int nsm, cudaStream_t st);
 void launch_lbm(int q, int storage, bool reduce, const Geom& g, const void* fin, void* fout,
                 float* u, const uint16_t* solid, BrickSet bs, float tau, float rho0,
-                double* red, double* forces, unsigned long long* status, cudaStream_t st);
+                double* red, double* forces, unsigned long long* status, cudaStream_t st,
+                int block = 256);
 void launch_init_populations(int q, int storage, const Geom& g, void* f, float rho0,
                              const float u0[3], float* u, cudaStream_t st);
 void launch_walkers(const Geom& g, const ParticleSet& ps, BrickSet bs1, float4* pos, int64_t n,

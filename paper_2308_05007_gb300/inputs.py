@@ -20,6 +20,7 @@ from __future__ import annotations
 
 from dataclasses import dataclass, field, replace
 from typing import Optional
+import math
 
 import numpy as np
 
@@ -245,6 +246,95 @@ def point_source(n: int = 100, n_walkers: int = 1_000_000, D: float = 0.2,
         name=f"point_source_{n}", dims=(n, n, n), tau=1.0, D=D, seed=seed,
         init_velocity=tuple(velocity), metaballs=empty_metaballs(), n_walkers=n_walkers,
         walker_positions=pos, steps=steps)
+
+
+def _fitting_metaballs(rng, n_particles, dims, wall_mask, **kw) -> Metaballs:
+    """random_metaballs with one particle fewer each time the box is too crowded."""
+    while True:
+        try:
+            return random_metaballs(rng, n_particles, dims, wall_mask, max_tries=2000, **kw)
+        except RuntimeError:
+            if n_particles <= 1:
+                raise
+            n_particles -= 1
+
+
+def batched(n_domains: int = 64, seed: int = 3, edge=(48, 160), particles=(4, 32),
+            centers=(2, 10), walkers=(100_000, 2_000_000), tau=(0.6, 1.0), D=(0.001, 0.02),
+            steps: int = 1000, q: int = 15, storage: int = 1, sort_interval: int = 16,
+            walker_scale: float = 1.0) -> list:
+    """Many independent periodic domains of different sizes advanced together.
+
+    Per domain: cubic edge ~ U{edge}; particle count from U{particles}, scaled down with the
+    box volume relative to the largest edge (a 48^3 box cannot hold 32 clusters), at least the
+    lower bound; U{centers} control points per particle (N(0, 1.5^2 I), k ~ U[4, 16]); walkers
+    ~ U[walkers] (times walker_scale); tau ~ U[tau]; D ~ U[D]; constant body force 1e-6 along
+    x as in the single-particle case; particles translate 2 sin(2 pi t / 1000) along x with
+    random phase per domain. All domains share sort_interval, so their step chunks line up.
+    """
+    rng = np.random.default_rng(seed)
+    out = []
+    for d in range(n_domains):
+        n = int(rng.integers(edge[0], edge[1] + 1))
+        frac = (n / float(edge[1])) ** 3
+        n_p = int(rng.integers(particles[0], particles[1] + 1))
+        n_p = max(particles[0], int(round(n_p * frac)))
+        mb = _fitting_metaballs(rng, n_p, (n, n, n), 0, n_centers=centers, sigma=1.5,
+                                k_range=(4.0, 16.0), amplitude=(2.0, 0.0, 0.0), period=1000.0,
+                                phase=float(rng.uniform(0.0, 2.0 * np.pi)))
+        nw = int(round(rng.uniform(walkers[0], walkers[1]) * walker_scale))
+        out.append(Workload(
+            name=f"batched_{d}_{n}", dims=(n, n, n), tau=float(rng.uniform(*tau)),
+            D=float(rng.uniform(*D)), seed=seed * 1000 + d, q=q, body_force=(1e-6, 0.0, 0.0),
+            metaballs=mb, n_walkers=nw, walker_box=((0.0, 0.0, 0.0), (float(n),) * 3),
+            steps=steps, storage=storage, sort_interval=sort_interval))
+    return out
+
+
+@dataclass
+class Request:
+    """One simulation request of the served stream."""
+    rid: int
+    arrival: float       # seconds after the stream starts
+    workload: Workload
+
+
+def served(n_requests: int = 64, rate: float = 20.0, seed: int = 4, edge=(32, 256),
+           walkers=(100_000, 10_000_000), steps=(1000, 20000), storage=(1, 2),
+           step_scale: float = 1.0, walker_scale: float = 1.0, sort_interval: int = 16) -> list:
+    """Poisson stream of simulation requests (mean `rate` per second).
+
+    Per request: exponential inter-arrival gap with mean 1/rate; cubic edge log-uniform in
+    [edge]; walkers log-uniform in [walkers] (times walker_scale, at most 2 per cell); steps
+    uniform in [steps] (times step_scale, rounded to a multiple of sort_interval); storage
+    picked from `storage` (FP32-shift or FP16-shift); a random single-particle-style
+    morphology: 1-4 metaball clusters (fewer in boxes below 64^3) of 1-6 centres (k ~ U[20, 60],
+    sigma 3, both scaled down by (n/64)^2 and n/64 below 64^3) at rest, periodic
+    box, tau ~ U[0.6, 1.0], D ~ U[0.001, 0.02], constant body force 1e-6 along x.
+    """
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    reqs = []
+    for r in range(n_requests):
+        t += float(rng.exponential(1.0 / rate))
+        n = int(round(np.exp(rng.uniform(np.log(edge[0]), np.log(edge[1])))))
+        nw = int(round(np.exp(rng.uniform(np.log(walkers[0]), np.log(walkers[1]))) * walker_scale))
+        nw = max(1, min(nw, 2 * n ** 3))
+        ns = int(rng.integers(steps[0], steps[1] + 1) * step_scale)
+        ns = max(sort_interval, ns - ns % sort_interval)
+        st = int(storage[int(rng.integers(0, len(storage)))])
+        n_p = int(rng.integers(1, 5))
+        n_p = max(1, min(n_p, int(round(n_p * (n / 64.0) ** 3))))
+        ks = min(1.0, (n / 64.0) ** 2)
+        mb = _fitting_metaballs(rng, n_p, (n, n, n), 0, n_centers=(1, 6), sigma=3.0 * math.sqrt(ks),
+                                k_range=(20.0 * ks, 60.0 * ks))
+        w = Workload(
+            name=f"request_{r}_{n}", dims=(n, n, n), tau=float(rng.uniform(0.6, 1.0)),
+            D=float(rng.uniform(0.001, 0.02)), seed=seed * 100000 + r, body_force=(1e-6, 0.0, 0.0),
+            metaballs=mb, n_walkers=nw, walker_box=((0.0, 0.0, 0.0), (float(n),) * 3), steps=ns,
+            storage=st, sort_interval=sort_interval)
+        reqs.append(Request(r, t, w))
+    return reqs
 
 
 def with_(w: Workload, **kw) -> Workload:

@@ -15,19 +15,20 @@ import numpy as np
 
 from . import build as _build
 
-RWMI_OK, RWMI_W_BISECT, RWMI_W_SEED = 0, 1, 2
-STATUS_NAMES = {0: "RWMI_OK", 1: "RWMI_W_BISECT", 2: "RWMI_W_SEED", -1: "RWMI_E_INVALID", -2: "RWMI_E_OOM",
+RWMI_OK, RWMI_W_BISECT, RWMI_W_SEED, RWMI_BUSY = 0, 1, 2, 3
+STATUS_NAMES = {0: "RWMI_OK", 1: "RWMI_W_BISECT", 2: "RWMI_W_SEED", 3: "RWMI_BUSY", -1: "RWMI_E_INVALID", -2: "RWMI_E_OOM",
                 -3: "RWMI_E_CUDA", -4: "RWMI_E_NONFINITE", -5: "RWMI_E_TIMEOUT", -6: "RWMI_E_STATE"}
 STORE_FP32, STORE_FP32_SHIFT, STORE_FP16_SHIFT = 0, 1, 2
 
 EXPORTED = ["rwmi_config_defaults", "rwmi_create", "rwmi_configure", "rwmi_set_stream",
             "rwmi_set_metaballs", "rwmi_seed_walkers", "rwmi_set_walkers", "rwmi_step", "rwmi_step_timed",
-            "rwmi_sync",
+            "rwmi_autotune", "rwmi_query", "rwmi_footprint", "rwmi_sync",
             "rwmi_time", "rwmi_info", "rwmi_concentration", "rwmi_walker_moments", "rwmi_moment_series",
             "rwmi_velocity", "rwmi_density", "rwmi_populations", "rwmi_lattice", "rwmi_solid",
             "rwmi_mass_momentum", "rwmi_particle_forces", "rwmi_walkers", "rwmi_counters", "rwmi_save",
             "rwmi_load", "rwmi_brick_stats", "rwmi_bin_walkers_noalloc", "rwmi_last_error",
-            "rwmi_launch_count", "rwmi_destroy"]
+            "rwmi_launch_count", "rwmi_destroy", "rwmi_batch_create", "rwmi_batch_step", "rwmi_batch_sync",
+            "rwmi_batch_last_error", "rwmi_batch_destroy"]
 
 
 class RwmiError(RuntimeError):
@@ -44,7 +45,7 @@ class Config(C.Structure):
     _fields_ = [("q", C.c_int32), ("storage", C.c_int32), ("wall_mask", C.c_uint32),
                 ("body_force", C.c_double * 3), ("force_period", C.c_double), ("rho0", C.c_double),
                 ("init_velocity", C.c_double * 3), ("sort_interval", C.c_int32),
-                ("moment_interval", C.c_int32), ("use_graphs", C.c_int32)]
+                ("moment_interval", C.c_int32), ("use_graphs", C.c_int32), ("lbm_block", C.c_int32)]
 
 
 _lib = None
@@ -86,6 +87,10 @@ def load(build_if_missing: bool = False):
     L.rwmi_set_walkers.argtypes = [P, C.c_int64, vp]
     L.rwmi_step.argtypes = [P, C.c_int32]
     L.rwmi_step_timed.argtypes = [P, C.c_int32, vp]
+    L.rwmi_autotune.argtypes = [P, C.POINTER(C.c_int32)]
+    L.rwmi_query.argtypes = [P]
+    L.rwmi_footprint.argtypes = [C.POINTER(C.c_int32), C.c_int32, C.c_int32, C.c_int64, C.c_int32, C.c_int32,
+                                 C.POINTER(C.c_uint64)]
     L.rwmi_sync.argtypes = [P]
     L.rwmi_time.argtypes = [P, C.POINTER(C.c_int64)]
     L.rwmi_info.argtypes = [P, vp]
@@ -106,9 +111,17 @@ def load(build_if_missing: bool = False):
     L.rwmi_launch_count.restype = C.c_int64
     L.rwmi_destroy.argtypes = [P]
     L.rwmi_destroy.restype = None
+    L.rwmi_batch_create.argtypes = [C.POINTER(P), C.POINTER(P), C.c_int32]
+    L.rwmi_batch_step.argtypes = [P, C.c_int32]
+    L.rwmi_batch_sync.argtypes = [P]
+    L.rwmi_batch_last_error.argtypes = [P]
+    L.rwmi_batch_last_error.restype = C.c_char_p
+    L.rwmi_batch_destroy.argtypes = [P]
+    L.rwmi_batch_destroy.restype = None
     for name in EXPORTED:
         fn = getattr(L, name)
-        if name not in ("rwmi_config_defaults", "rwmi_last_error", "rwmi_launch_count", "rwmi_destroy"):
+        if name not in ("rwmi_config_defaults", "rwmi_last_error", "rwmi_launch_count", "rwmi_destroy",
+                        "rwmi_batch_last_error", "rwmi_batch_destroy"):
             fn.restype = C.c_int
     _lib = L
     return L
@@ -123,6 +136,17 @@ def _ptr(a):
 
 def _d3(v):
     return (C.c_double * 3)(*[float(x) for x in v])
+
+
+def footprint(dims, q, storage, n_walkers, n_particles, n_centers) -> int:
+    """Device bytes a context of these sizes needs (rwmi_footprint)."""
+    L = load()
+    d = (C.c_int32 * 3)(*[int(x) for x in dims])
+    out = C.c_uint64()
+    st = L.rwmi_footprint(d, int(q), int(storage), int(n_walkers), int(n_particles), int(n_centers), C.byref(out))
+    if st != 0:
+        raise RwmiError(st, "rwmi_footprint: bad sizes")
+    return int(out.value)
 
 
 def bin_walkers_noalloc(dims, wall_mask, pos, counts, pos_sorted=None, stream=None):
@@ -147,7 +171,7 @@ class Simulation:
 
     def __init__(self, dims, tau, D, seed=0, q=19, storage=STORE_FP32_SHIFT, wall_mask=0,
                  body_force=(0.0, 0.0, 0.0), force_period=0.0, rho0=1.0, init_velocity=(0.0, 0.0, 0.0),
-                 sort_interval=16, moment_interval=0, use_graphs=True, stream=None):
+                 sort_interval=16, moment_interval=0, use_graphs=True, stream=None, lbm_block=256):
         L = load()
         self._L = L
         self._h = C.c_void_p()
@@ -166,6 +190,7 @@ class Simulation:
         cfg.force_period, cfg.rho0 = float(force_period), float(rho0)
         cfg.sort_interval, cfg.moment_interval = int(sort_interval), int(moment_interval)
         cfg.use_graphs = 1 if use_graphs else 0
+        cfg.lbm_block = int(lbm_block)
         self._check(L.rwmi_configure(self._h, C.byref(cfg)))
         self.q = int(q)
         _live.add(self)
@@ -258,6 +283,16 @@ class Simulation:
         out = np.zeros(len(self.PHASES))
         self._check(self._L.rwmi_step_timed(self._h, int(n), _ptr(out)))
         return dict(zip(self.PHASES, out.tolist()))
+
+    def autotune(self) -> int:
+        """Pick the LBM block size by timing (rwmi_autotune); returns it."""
+        v = C.c_int32()
+        self._check(self._L.rwmi_autotune(self._h, C.byref(v)))
+        return int(v.value)
+
+    def busy(self) -> bool:
+        """True while GPU work of this context is in flight (rwmi_query, non-blocking)."""
+        return self._check(self._L.rwmi_query(self._h)) == RWMI_BUSY
 
     def sync(self) -> int:
         return self._check(self._L.rwmi_sync(self._h))
@@ -379,3 +414,46 @@ class Simulation:
 
     def load(self, path):
         self._check(self._L.rwmi_load(self._h, os.fsencode(path)))
+
+
+class Batch:
+    """rwmi_batch: many contexts advanced by one CUDA graph launch per chunk (their steps are
+    concurrent branches). Each context must use its own stream for the branches to overlap."""
+
+    def __init__(self, sims):
+        self._L = load()
+        self.sims = list(sims)
+        arr = (C.c_void_p * len(self.sims))(*[s._h.value for s in self.sims])
+        self._h = C.c_void_p()
+        st = self._L.rwmi_batch_create(C.byref(self._h), arr, len(self.sims))
+        if st != 0:
+            raise RwmiError(st, "rwmi_batch_create: contexts must share the chunk length (<= 64)")
+
+    def _check(self, st):
+        if st < 0:
+            raise RwmiError(st, self._L.rwmi_batch_last_error(self._h).decode(errors="replace"))
+        return st
+
+    def step(self, n):
+        self._check(self._L.rwmi_batch_step(self._h, int(n)))
+
+    def sync(self) -> int:
+        """Waits for the batch; the worst status of its contexts (warnings are positive)."""
+        return self._check(self._L.rwmi_batch_sync(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self._L.rwmi_batch_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
