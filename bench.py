@@ -47,6 +47,7 @@ def parse(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--overlap", type=int, default=1, choices=[0, 1])
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batch-domains", type=int, default=64)
     ap.add_argument("--batch-steps", type=int, default=160)
@@ -85,6 +86,8 @@ def config_dict(a, w):
         "moment_interval": w.moment_interval,
         "l2": "inputs larger than L2 (populations 2 x %.2f GB), no flush" % (w.n_cells * w.q * (2 if w.storage == 2 else 4) / 1e9),
         "graphs": "CUDA graph per %d steps" % max(w.sort_interval, w.moment_interval, 2),
+        "schedule": ("raster of t+1 on a second stream beside the LBM of t" if getattr(a, "overlap", 1)
+                     else "serial"),
     }
 
 
@@ -141,6 +144,15 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "fallback": True}
 
 
+def lbm_source_digest() -> str:
+    """First 16 hex digits of the SHA-256 of the LBM kernel's sources (kernel + lattice header)."""
+    import hashlib
+    h = hashlib.sha256()
+    for name in ("rwmi_lbm.cu", "rwmi_lattice.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2308_05007_gb300", "csrc", name), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def profiled_traffic(a):
     """Per-launch DRAM bytes of the LBM kernel from the committed ncu summary, if that summary
     was taken on this workload and on the current kernel source (else None)."""
@@ -149,8 +161,7 @@ def profiled_traffic(a):
         text = open(PROFILE_SUMMARY).read()
     except OSError:
         return None
-    src = open(os.path.join(ROOT, "paper_2308_05007_gb300", "csrc", "rwmi_fluid.cu"), "rb").read()
-    digest = hashlib.sha256(src).hexdigest()[:16]
+    digest = lbm_source_digest()
     vals = {}
     for line in text.splitlines():
         if ":" in line and line.strip().startswith("- "):
@@ -340,7 +351,7 @@ def main():
     w = workload(a)
     s_bytes = 2 if w.storage == 2 else 4
     stream = torch.cuda.Stream()
-    sim = Simulation.from_workload(w, seed_walkers=False)
+    sim = Simulation.from_workload(w, seed_walkers=False, overlap=bool(a.overlap))
     sim.set_stream(stream)
     sim.seed_walkers(w.n_walkers, *w.walker_box)
     L = 16

@@ -11,7 +11,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "librwmi.so")
-SOURCES = ["rwmi_fluid.cu", "rwmi_walkers.cu", "rwmi_api.cu"]
+SOURCES = ["rwmi_fluid.cu", "rwmi_lbm.cu", "rwmi_walkers.cu", "rwmi_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "-I" + os.path.join(ROOT, "include"), "-I" + CSRC]

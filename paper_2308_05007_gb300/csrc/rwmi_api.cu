@@ -43,13 +43,15 @@ struct rwmi_ctx {
   int device = 0, nsm = 152;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
+  cudaStream_t side = nullptr;                     // raster of t+1 beside the LBM of t
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   bool stepped = false;
   std::string err;
 
   // device state
   void* f[2] = {nullptr, nullptr};
   float* u = nullptr;
-  uint16_t* solid = nullptr;
+  uint16_t* solid[2] = {nullptr, nullptr};   // per time parity: raster of t+1 beside the LBM of t
   int64_t* d_T = nullptr;
   unsigned int* ticket = nullptr;
   unsigned long long* status = nullptr;
@@ -215,7 +217,7 @@ rwmi_status build_current_frame(rwmi_ctx* c) {
                   c->cfg.force_period, 1, c->acc[par], c->stream);
   c->launches++;
   if (c->P > 0) {
-    launch_raster(c->g, particle_set(c), brick_set(c, par), c->solid, c->status, c->nsm, c->stream);
+    launch_raster(c->g, particle_set(c), brick_set(c, par), c->solid[par], c->status, c->nsm, c->stream);
     c->launches++;
   }
   CK(cudaGetLastError());
@@ -302,35 +304,53 @@ void phase_end(rwmi_ctx* c, int ph) {
 }
 
 // One timestep t -> t+1 (host mirrors advance as the launches are queued). The solid fraction of
-// time t was rasterised at the end of the previous step (or at set-up); this step rasterises t+1
-// before the walkers, whose mini-brick masks come from that raster. `reduce`: also form the FP64
+// time t was rasterised during the previous step (or at set-up) into solid[t & 1]; this step
+// rasterises t+1 into solid[(t+1) & 1] before the walkers, whose mini-brick masks come from that
+// raster. With cfg.overlap the raster runs on the side stream, forked after the poses of t+1 and
+// joined before the walkers, so it overlaps the LBM of t (HBM-bound vs ALU-bound); step_timed
+// keeps the serial order so that each phase is timed alone. `reduce`: also form the FP64
 // mass/momentum sums of this step.
 void enqueue_step(rwmi_ctx* c, bool reduce) {
   const int tp = (int)(c->t & 1), tn = tp ^ 1;
   const ParticleSet ps = particle_set(c);
   const uint32_t k0 = (uint32_t)c->seed, k1 = (uint32_t)(c->seed >> 32);
-  // LBM at t
-  phase_begin(c, RWMI_PHASE_LBM);
-  launch_lbm(c->cfg.q, c->cfg.storage, reduce, c->g, c->f[c->fcur], c->f[c->fcur ^ 1], c->u, c->solid,
-             brick_set(c, tp), (float)c->tau, (float)c->cfg.rho0, c->acc[tp] + 6 * c->P, c->acc[tp],
-             c->status, c->stream, c->cfg.lbm_block);
-  c->launches++;
-  phase_end(c, RWMI_PHASE_LBM);
-  c->fcur ^= 1;
-  // particles, bricks and body force of t+1
-  phase_begin(c, RWMI_PHASE_POSE);
-  cudaMemsetAsync(c->bword[tn], 0, sizeof(uint32_t) * (c->nbrick + 1), c->stream);
-  launch_pose_bin(c->g, ps, brick_set(c, tn), c->d_T, 1, c->cfg.body_force, c->cfg.force_period, 1,
-                  c->acc[tn], c->stream);
-  c->launches++;
-  phase_end(c, RWMI_PHASE_POSE);
-  // solid fraction of t+1 (used by the LBM of the next step) and the walkers' masks
-  phase_begin(c, RWMI_PHASE_RASTER);
-  if (c->P > 0) {
-    launch_raster(c->g, ps, brick_set(c, tn), c->solid, c->status, c->nsm, c->stream);
+  const bool overlap = c->cfg.overlap && !c->timing && c->P > 0;
+  auto pose = [&]() {   // particles, bricks and body force of t+1
+    phase_begin(c, RWMI_PHASE_POSE);
+    cudaMemsetAsync(c->bword[tn], 0, sizeof(uint32_t) * (c->nbrick + 1), c->stream);
+    launch_pose_bin(c->g, ps, brick_set(c, tn), c->d_T, 1, c->cfg.body_force, c->cfg.force_period, 1,
+                    c->acc[tn], c->stream);
     c->launches++;
+    phase_end(c, RWMI_PHASE_POSE);
+  };
+  auto lbm = [&]() {    // LBM at t
+    phase_begin(c, RWMI_PHASE_LBM);
+    launch_lbm(c->cfg.q, c->cfg.storage, reduce, c->g, c->f[c->fcur], c->f[c->fcur ^ 1], c->u, c->solid[tp],
+               brick_set(c, tp), (float)c->tau, (float)c->cfg.rho0, c->acc[tp] + 6 * c->P, c->acc[tp],
+               c->status, c->stream, c->cfg.lbm_block);
+    c->launches++;
+    phase_end(c, RWMI_PHASE_LBM);
+    c->fcur ^= 1;
+  };
+  if (overlap) {
+    pose();
+    cudaEventRecord(c->fork_ev, c->stream);
+    cudaStreamWaitEvent(c->side, c->fork_ev, 0);
+    launch_raster(c->g, ps, brick_set(c, tn), c->solid[tn], c->status, c->nsm, c->side);
+    c->launches++;
+    cudaEventRecord(c->join_ev, c->side);
+    lbm();
+    cudaStreamWaitEvent(c->stream, c->join_ev, 0);
+  } else {
+    lbm();
+    pose();
+    phase_begin(c, RWMI_PHASE_RASTER);
+    if (c->P > 0) {
+      launch_raster(c->g, ps, brick_set(c, tn), c->solid[tn], c->status, c->nsm, c->stream);
+      c->launches++;
+    }
+    phase_end(c, RWMI_PHASE_RASTER);
   }
-  phase_end(c, RWMI_PHASE_RASTER);
   // walkers t -> t+1; the walker kernel's last warp advances the device step counter
   phase_begin(c, RWMI_PHASE_WALKERS);
   if (c->nw > 0) {
@@ -399,6 +419,7 @@ RWMI_API void rwmi_config_defaults(rwmi_config* cfg) {
   cfg->moment_interval = 0;
   cfg->use_graphs = 1;
   cfg->lbm_block = 256;
+  cfg->overlap = 1;
 }
 
 RWMI_API rwmi_status rwmi_create(rwmi_ctx** out, const int32_t dims[3], double tau, double D,
@@ -441,7 +462,10 @@ RWMI_API rwmi_status rwmi_create(rwmi_ctx** out, const int32_t dims[3], double t
     rwmi_status s = alloc_fluid(c);
     if (s != RWMI_OK) return s;
     CK(dalloc(c, &c->u, sizeof(float4) * (size_t)g.ncell_pad));   // (u, rho) per cell
-    CK(dalloc(c, &c->solid, sizeof(uint16_t) * (size_t)ncell));
+    for (int k = 0; k < 2; ++k) CK(dalloc(c, &c->solid[k], sizeof(uint16_t) * (size_t)ncell));
+    CK(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&c->join_ev, cudaEventDisableTiming));
     CK(dalloc(c, &c->d_T, sizeof(int64_t)));
     CK(dalloc(c, &c->ticket, sizeof(unsigned int)));
     CK(dalloc(c, &c->wlist_n, sizeof(unsigned int)));
@@ -469,7 +493,7 @@ RWMI_API rwmi_status rwmi_create(rwmi_ctx** out, const int32_t dims[3], double t
     CK(cudaMemsetAsync(c->ticket, 0, sizeof(unsigned int), c->stream));
     CK(cudaMemsetAsync(c->status, 0, sizeof(unsigned long long) * ST_COUNT, c->stream));
     CK(cudaMemsetAsync(c->macc, 0, sizeof(double) * 12, c->stream));
-    CK(cudaMemsetAsync(c->solid, 0, sizeof(uint16_t) * (size_t)ncell, c->stream));
+    for (int k = 0; k < 2; ++k) CK(cudaMemsetAsync(c->solid[k], 0, sizeof(uint16_t) * (size_t)ncell, c->stream));
     s = reset_fluid(c);
     if (s != RWMI_OK) return s;
     s = build_current_frame(c);
@@ -723,7 +747,7 @@ RWMI_API rwmi_status rwmi_autotune(rwmi_ctx* c, int32_t* chosen) {
   for (int k = 0; k < 3; ++k) {
     for (int rep = 0; rep < 6; ++rep) {
       if (rep == 1) cudaEventRecord(e0, c->stream);
-      launch_lbm(c->cfg.q, c->cfg.storage, false, c->g, c->f[c->fcur], c->f[c->fcur ^ 1], c->u, c->solid,
+      launch_lbm(c->cfg.q, c->cfg.storage, false, c->g, c->f[c->fcur], c->f[c->fcur ^ 1], c->u, c->solid[c->t & 1],
                  brick_set(c, tp), (float)c->tau, (float)c->cfg.rho0, (double*)c->scratch + 6 * c->P,
                  (double*)c->scratch, c->status, c->stream, cand[k]);
       c->launches++;
@@ -888,7 +912,7 @@ RWMI_API rwmi_status rwmi_solid(rwmi_ctx* c, int32_t* count, int32_t* owner) {
   rwmi_status s = ensure_scratch(c, bytes);
   if (s != RWMI_OK) return s;
   int32_t* tmp = (int32_t*)c->scratch;   // the current time was rasterised by the last step / set-up
-  launch_unpack_solid(c->g, c->solid, c->bword[par], tmp, tmp + c->ncell, c->stream);
+  launch_unpack_solid(c->g, c->solid[par], c->bword[par], tmp, tmp + c->ncell, c->stream);
   c->launches++;
   CK(cudaGetLastError());
   s = copy_out(c, count, tmp, sizeof(int32_t) * (size_t)c->ncell);
@@ -1168,12 +1192,15 @@ RWMI_API void rwmi_destroy(rwmi_ctx* c) {
     dfree(c, c->pose[k]); dfree(c, c->sp[k]); dfree(c, c->cworld[k]); dfree(c, c->pos[k]); dfree(c, c->x0[k]);
   }
   dfree(c, c->wlist); dfree(c, c->wlist_n);
-  dfree(c, c->u); dfree(c, c->solid); dfree(c, c->d_T); dfree(c, c->ticket); dfree(c, c->status); dfree(c, c->macc);
+  dfree(c, c->u); dfree(c, c->solid[0]); dfree(c, c->solid[1]); dfree(c, c->d_T); dfree(c, c->ticket); dfree(c, c->status); dfree(c, c->macc);
   dfree(c, c->series); dfree(c, c->mrow); dfree(c, c->desc); dfree(c, c->cbody); dfree(c, c->rank);
   dfree(c, c->counts); dfree(c, c->offsets); dfree(c, c->bsums); dfree(c, c->scratch); dfree(c, c->wmask);
   cudaStreamSynchronize(c->stream);   // the frees have returned the memory when this returns
   for (int k = 0; k < 2 * RWMI_NPHASE; ++k)
     if (c->ev[k]) cudaEventDestroy(c->ev[k]);
+  if (c->fork_ev) cudaEventDestroy(c->fork_ev);
+  if (c->join_ev) cudaEventDestroy(c->join_ev);
+  if (c->side) cudaStreamDestroy(c->side);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
 }

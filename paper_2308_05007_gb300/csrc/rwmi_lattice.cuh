@@ -1,0 +1,66 @@
+// rwmi_lattice.cuh -- velocity sets and population storage policies shared by the LBM kernel
+// and the initialisation / read-back kernels.
+#pragma once
+#include <cuda_fp16.h>
+
+#include "rwmi_internal.cuh"
+
+namespace rwmi {
+
+// ------------------------------------------------------------------------------------------
+// Velocity sets. Directions 1..H form one half of the set; direction i + H is the opposite of i.
+//   D3Q15 half: (1,0,0) (0,1,0) (0,0,1) (1,1,1) (1,1,-1) (1,-1,1) (1,-1,-1)
+//   D3Q19 half: (1,0,0) (0,1,0) (0,0,1) (1,1,0) (1,-1,0) (1,0,1) (1,0,-1) (0,1,1) (0,1,-1)
+// Weights: D3Q15 2/9, 1/9, 1/72; D3Q19 1/3, 1/18, 1/36 (c_s^2 = 1/3).
+// ------------------------------------------------------------------------------------------
+__host__ __device__ constexpr int half15(int i, int a) {
+  return a == 0 ? (i == 2 || i == 3 ? 0 : 1)
+       : a == 1 ? (i == 1 || i == 3 ? 0 : (i == 2 || i == 4 || i == 5) ? 1 : -1)
+                : (i == 1 || i == 2 ? 0 : (i == 3 || i == 4 || i == 6) ? 1 : -1);
+}
+__host__ __device__ constexpr int half19(int i, int a) {
+  return a == 0 ? ((i == 1 || (i >= 4 && i <= 7)) ? 1 : 0)
+       : a == 1 ? ((i == 2 || i == 4 || i == 8 || i == 9) ? 1 : (i == 5 ? -1 : 0))
+                : ((i == 3 || i == 6 || i == 8) ? 1 : ((i == 7 || i == 9) ? -1 : 0));
+}
+template <int Q> struct Lat {
+  static constexpr int H = (Q - 1) / 2;
+  __host__ __device__ static constexpr int e(int i, int a) {
+    return i == 0 ? 0
+         : i <= H ? (Q == 15 ? half15(i, a) : half19(i, a))
+                  : -(Q == 15 ? half15(i - H, a) : half19(i - H, a));
+  }
+  __host__ __device__ static constexpr int e2(int i) {
+    return e(i, 0) * e(i, 0) + e(i, 1) * e(i, 1) + e(i, 2) * e(i, 2);
+  }
+  __host__ __device__ static constexpr float w(int i) {
+    return Q == 15 ? (e2(i) == 0 ? 2.0f / 9.0f : e2(i) == 1 ? 1.0f / 9.0f : 1.0f / 72.0f)
+                   : (e2(i) == 0 ? 1.0f / 3.0f : e2(i) == 1 ? 1.0f / 18.0f : 1.0f / 36.0f);
+  }
+  __host__ __device__ static constexpr int opp(int i) { return i == 0 ? 0 : (i <= H ? i + H : i - H); }
+};
+
+
+// Population storage: binary32 f_i, binary32 f_i - w_i rho0 ("shifted") or binary16 shifted;
+// arithmetic is binary32 in every case.
+template <int STORE> struct Store;
+template <> struct Store<0> {
+  using T = float;
+  static constexpr bool shifted = false;
+  __device__ static float ld(const T* p) { return *p; }
+  __device__ static void st(T* p, float v) { *p = v; }
+};
+template <> struct Store<1> {
+  using T = float;
+  static constexpr bool shifted = true;
+  __device__ static float ld(const T* p) { return *p; }
+  __device__ static void st(T* p, float v) { *p = v; }
+};
+template <> struct Store<2> {
+  using T = __half;
+  static constexpr bool shifted = true;
+  __device__ static float ld(const T* p) { return __half2float(*p); }
+  __device__ static void st(T* p, float v) { *p = __float2half_rn(v); }
+};
+
+}  // namespace rwmi

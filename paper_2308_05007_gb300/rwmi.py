@@ -45,7 +45,8 @@ class Config(C.Structure):
     _fields_ = [("q", C.c_int32), ("storage", C.c_int32), ("wall_mask", C.c_uint32),
                 ("body_force", C.c_double * 3), ("force_period", C.c_double), ("rho0", C.c_double),
                 ("init_velocity", C.c_double * 3), ("sort_interval", C.c_int32),
-                ("moment_interval", C.c_int32), ("use_graphs", C.c_int32), ("lbm_block", C.c_int32)]
+                ("moment_interval", C.c_int32), ("use_graphs", C.c_int32), ("lbm_block", C.c_int32),
+                ("overlap", C.c_int32)]
 
 
 _lib = None
@@ -171,7 +172,8 @@ class Simulation:
 
     def __init__(self, dims, tau, D, seed=0, q=19, storage=STORE_FP32_SHIFT, wall_mask=0,
                  body_force=(0.0, 0.0, 0.0), force_period=0.0, rho0=1.0, init_velocity=(0.0, 0.0, 0.0),
-                 sort_interval=16, moment_interval=0, use_graphs=True, stream=None, lbm_block=256):
+                 sort_interval=16, moment_interval=0, use_graphs=True, stream=None, lbm_block=256,
+                 overlap=True):
         L = load()
         self._L = L
         self._h = C.c_void_p()
@@ -191,6 +193,7 @@ class Simulation:
         cfg.sort_interval, cfg.moment_interval = int(sort_interval), int(moment_interval)
         cfg.use_graphs = 1 if use_graphs else 0
         cfg.lbm_block = int(lbm_block)
+        cfg.overlap = 1 if overlap else 0
         self._check(L.rwmi_configure(self._h, C.byref(cfg)))
         self.q = int(q)
         _live.add(self)

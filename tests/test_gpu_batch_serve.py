@@ -110,6 +110,31 @@ def test_autotuned_block_size_changes_no_result():
         _same(ref, _state(s), "autotuned", regrouped=True)
 
 
+def test_overlapped_raster_changes_no_result():
+    """The raster of t+1 on a second stream beside the LBM of t gives the serial schedule's
+    results bit for bit (eager and graph-replayed)."""
+    _need_gpu()
+    from paper_2308_05007_gb300 import inputs as I
+    from paper_2308_05007_gb300.rwmi import Simulation
+    w = I.with_(I.ragged(n_walkers=4000), sort_interval=4)
+    out = {}
+    for overlap in (False, True):
+        for graphs in (False, True):
+            with Simulation.from_workload(w, overlap=overlap, use_graphs=graphs) as s:
+                s.step(13)
+                st = _state(s)
+                st["solid"] = s.solid()
+                st["forces"] = s.particle_forces()
+            out[(overlap, graphs)] = st
+    ref = out[(False, False)]
+    for key, st in out.items():
+        _same(ref, st, f"overlap={key[0]} graphs={key[1]}")
+        for a, b in zip(ref["solid"], st["solid"]):
+            assert np.array_equal(a, b)
+        np.testing.assert_allclose(ref["forces"], st["forces"], rtol=1e-12,
+                                   atol=1e-12 * np.max(np.abs(ref["forces"])))
+
+
 def test_query_and_footprint():
     torch = _need_gpu()
     from paper_2308_05007_gb300 import inputs as I
