@@ -47,7 +47,7 @@ def parse(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
-    ap.add_argument("--overlap", type=int, default=1, choices=[0, 1])
+    ap.add_argument("--overlap", type=int, default=2, choices=[0, 1, 2])
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batch-domains", type=int, default=64)
     ap.add_argument("--batch-steps", type=int, default=160)
@@ -86,8 +86,9 @@ def config_dict(a, w):
         "moment_interval": w.moment_interval,
         "l2": "inputs larger than L2 (populations 2 x %.2f GB), no flush" % (w.n_cells * w.q * (2 if w.storage == 2 else 4) / 1e9),
         "graphs": "CUDA graph per %d steps" % max(w.sort_interval, w.moment_interval, 2),
-        "schedule": ("raster of t+1 on a second stream beside the LBM of t" if getattr(a, "overlap", 1)
-                     else "serial"),
+        "schedule": {0: "serial", 1: "raster of t+1 on a second stream beside the LBM of t",
+                     2: "raster of t+1 beside the LBM of t; walkers of t on a third stream beside "
+                        "the fluid of t+1"}[getattr(a, "overlap", 2)],
     }
 
 
@@ -351,7 +352,7 @@ def main():
     w = workload(a)
     s_bytes = 2 if w.storage == 2 else 4
     stream = torch.cuda.Stream()
-    sim = Simulation.from_workload(w, seed_walkers=False, overlap=bool(a.overlap))
+    sim = Simulation.from_workload(w, seed_walkers=False, overlap=a.overlap)
     sim.set_stream(stream)
     sim.seed_walkers(w.n_walkers, *w.walker_box)
     L = 16

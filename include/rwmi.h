@@ -92,9 +92,12 @@ typedef struct {
     int32_t use_graphs;        /* replay captured CUDA graphs for repeated steps. Default 1. */
     int32_t lbm_block;         /* threads per block of the LBM kernel: 64, 128 or 256 (0: 256);
                                   rwmi_autotune picks it by timing. */
-    int32_t overlap;           /* 1: rasterise the solid fraction of t+1 on a second stream while
-                                  the LBM of t runs (they use different units: ALU vs HBM);
-                                  0: one after the other. Same results either way. Default 1. */
+    int32_t overlap;           /* step schedule, same results bit for bit in every case:
+                                  0: one stream, phases one after the other;
+                                  1: the raster of t+1 on a second stream while the LBM of t runs
+                                     (ALU-bound beside HBM-bound);
+                                  2: as 1, and the walkers of t (with sort and moments) on a third
+                                     stream beside the fluid of t+1. Default 2. */
 } rwmi_config;
 
 /* Fills *cfg with the defaults listed above. */

@@ -43,14 +43,15 @@ struct rwmi_ctx {
   int device = 0, nsm = 152;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
-  cudaStream_t side = nullptr;                     // raster of t+1 beside the LBM of t
-  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
+  cudaStream_t side = nullptr;    // raster of t+1 beside the LBM of t
+  cudaStream_t wst = nullptr;     // walkers of t beside the fluid of t+1
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr, fluid_ev = nullptr, walk_ev[2] = {nullptr, nullptr};
   bool stepped = false;
   std::string err;
 
   // device state
   void* f[2] = {nullptr, nullptr};
-  float* u = nullptr;
+  float* u[2] = {nullptr, nullptr};   // (u, rho) per time parity: the LBM of t writes u[t & 1]
   uint16_t* solid[2] = {nullptr, nullptr};   // per time parity: raster of t+1 beside the LBM of t
   int64_t* d_T = nullptr;
   unsigned int* ticket = nullptr;
@@ -60,7 +61,7 @@ struct rwmi_ctx {
   double* series = nullptr;              // [SERIES_ROWS][SERIES_COLS]
   double* mrow = nullptr;                // on-demand moments row [SERIES_COLS]
   // bricks per time parity (the walker masks are rewritten by every raster)
-  uint64_t* wmask = nullptr;
+  uint64_t* wmask[2] = {nullptr, nullptr};
   uint32_t* bword[2] = {nullptr, nullptr};
   uint16_t* bcand[2] = {nullptr, nullptr};
   int32_t* rlist[2] = {nullptr, nullptr};
@@ -89,6 +90,8 @@ struct rwmi_ctx {
 
   // host mirrors
   int64_t t = 0;
+  int64_t t_base = 0;   // value of the device counter d_T: t at the start of the current run
+  bool walk_rec[2] = {false, false};   // walk_ev[p] recorded in the current run
   int fcur = 0, pcur = 0;
   int64_t binned_t = -1;
   int64_t series_rows = 0;
@@ -193,7 +196,7 @@ ParticleSet particle_set(const rwmi_ctx* c) {
 
 BrickSet brick_set(const rwmi_ctx* c, int par) {
   BrickSet b;
-  b.wmask = c->wmask;
+  b.wmask = c->wmask[par];
   b.bword = c->bword[par];
   b.bcand = c->bcand[par];
   b.rlist = c->rlist[par];
@@ -228,7 +231,7 @@ rwmi_status reset_fluid(rwmi_ctx* c) {
   const float u0[3] = {(float)c->cfg.init_velocity[0], (float)c->cfg.init_velocity[1],
                        (float)c->cfg.init_velocity[2]};
   launch_init_populations(c->cfg.q, c->cfg.storage, c->g, c->f[c->fcur], (float)c->cfg.rho0, u0,
-                          c->u, c->stream);
+                          c->u[(c->t + 1) & 1], c->stream);
   c->launches++;
   CK(cudaGetLastError());
   return RWMI_OK;
@@ -286,12 +289,12 @@ rwmi_status alloc_walkers(rwmi_ctx* c, int64_t n) {
 }
 
 // Counting sort of the walkers by cell; the histogram is the concentration of Eq. 16.
-void enqueue_sort(rwmi_ctx* c) {
-  cudaMemsetAsync(c->counts, 0, sizeof(uint32_t) * (size_t)c->ncell, c->stream);
-  launch_histogram(c->g, c->pos[c->pcur], c->nw, c->counts, c->rank, c->stream);
-  launch_scan(c->counts, c->offsets, c->bsums, (uint32_t)c->ncell, c->stream);
+void enqueue_sort(rwmi_ctx* c, cudaStream_t st) {
+  cudaMemsetAsync(c->counts, 0, sizeof(uint32_t) * (size_t)c->ncell, st);
+  launch_histogram(c->g, c->pos[c->pcur], c->nw, c->counts, c->rank, st);
+  launch_scan(c->counts, c->offsets, c->bsums, (uint32_t)c->ncell, st);
   launch_scatter(c->g, c->pos[c->pcur], c->x0[c->pcur], c->nw, c->offsets, c->rank,
-                 c->pos[c->pcur ^ 1], c->x0[c->pcur ^ 1], c->stream);
+                 c->pos[c->pcur ^ 1], c->x0[c->pcur ^ 1], st);
   c->launches += 5;
   c->pcur ^= 1;
 }
@@ -303,36 +306,47 @@ void phase_end(rwmi_ctx* c, int ph) {
   if (c->timing) cudaEventRecord(c->ev[2 * ph + 1], c->stream);
 }
 
-// One timestep t -> t+1 (host mirrors advance as the launches are queued). The solid fraction of
-// time t was rasterised during the previous step (or at set-up) into solid[t & 1]; this step
-// rasterises t+1 into solid[(t+1) & 1] before the walkers, whose mini-brick masks come from that
-// raster. With cfg.overlap the raster runs on the side stream, forked after the poses of t+1 and
-// joined before the walkers, so it overlaps the LBM of t (HBM-bound vs ALU-bound); step_timed
-// keeps the serial order so that each phase is timed alone. `reduce`: also form the FP64
-// mass/momentum sums of this step.
+// One timestep t -> t+1 of a run of steps (host mirrors advance as the launches are queued).
+// Buffers are per time parity where two steps' kernels may overlap: the solid fraction of t is
+// solid[t & 1] (rasterised during step t-1, or at set-up), the LBM of t writes u[t & 1], the
+// raster of t+1 writes solid/wmask[(t+1) & 1], and bricks of t+1 are bricks[(t+1) & 1].
+// Schedules (cfg.overlap; rwmi_step_timed always takes 0 so that each phase is timed alone):
+//   0  one stream: LBM(t), poses(t+1), raster(t+1), walkers(t), sort/moments.
+//   1  poses(t+1) first; raster(t+1) on the side stream while LBM(t) runs on the main one (the
+//      raster is ALU-bound, the LBM HBM-bound); join; walkers on the main stream.
+//   2  as 1, and the walkers (with sort and moments) run on their own stream, one step behind
+//      the fluid: walkers(t) overlap LBM(t+1) and raster(t+2). Step t+2's fluid work waits for
+//      walkers(t), the last reader of the parity it overwrites.
+// Kernels take their time as d_T + offset (d_T = t at the start of the run), so concurrent
+// steps never race on a counter; segment_end advances d_T once per run. `reduce`: also form the
+// FP64 mass/momentum sums of this step.
 void enqueue_step(rwmi_ctx* c, bool reduce) {
   const int tp = (int)(c->t & 1), tn = tp ^ 1;
+  const int toff = (int)(c->t - c->t_base);
   const ParticleSet ps = particle_set(c);
   const uint32_t k0 = (uint32_t)c->seed, k1 = (uint32_t)(c->seed >> 32);
-  const bool overlap = c->cfg.overlap && !c->timing && c->P > 0;
+  const int level = c->timing ? 0 : c->cfg.overlap;
+  const bool fork_raster = level >= 1 && c->P > 0;
+  cudaStream_t ws = level >= 2 ? c->wst : c->stream;
+  if (ws != c->stream && c->walk_rec[tp]) cudaStreamWaitEvent(c->stream, c->walk_ev[tp], 0);
   auto pose = [&]() {   // particles, bricks and body force of t+1
     phase_begin(c, RWMI_PHASE_POSE);
     cudaMemsetAsync(c->bword[tn], 0, sizeof(uint32_t) * (c->nbrick + 1), c->stream);
-    launch_pose_bin(c->g, ps, brick_set(c, tn), c->d_T, 1, c->cfg.body_force, c->cfg.force_period, 1,
+    launch_pose_bin(c->g, ps, brick_set(c, tn), c->d_T, toff + 1, c->cfg.body_force, c->cfg.force_period, 1,
                     c->acc[tn], c->stream);
     c->launches++;
     phase_end(c, RWMI_PHASE_POSE);
   };
   auto lbm = [&]() {    // LBM at t
     phase_begin(c, RWMI_PHASE_LBM);
-    launch_lbm(c->cfg.q, c->cfg.storage, reduce, c->g, c->f[c->fcur], c->f[c->fcur ^ 1], c->u, c->solid[tp],
+    launch_lbm(c->cfg.q, c->cfg.storage, reduce, c->g, c->f[c->fcur], c->f[c->fcur ^ 1], c->u[tp], c->solid[tp],
                brick_set(c, tp), (float)c->tau, (float)c->cfg.rho0, c->acc[tp] + 6 * c->P, c->acc[tp],
                c->status, c->stream, c->cfg.lbm_block);
     c->launches++;
     phase_end(c, RWMI_PHASE_LBM);
     c->fcur ^= 1;
   };
-  if (overlap) {
+  if (fork_raster) {
     pose();
     cudaEventRecord(c->fork_ev, c->stream);
     cudaStreamWaitEvent(c->side, c->fork_ev, 0);
@@ -351,32 +365,51 @@ void enqueue_step(rwmi_ctx* c, bool reduce) {
     }
     phase_end(c, RWMI_PHASE_RASTER);
   }
-  // walkers t -> t+1; the walker kernel's last warp advances the device step counter
+  // walkers t -> t+1: u of t, particles of t+1
+  if (ws != c->stream) {
+    cudaEventRecord(c->fluid_ev, c->stream);
+    cudaStreamWaitEvent(ws, c->fluid_ev, 0);
+  }
   phase_begin(c, RWMI_PHASE_WALKERS);
   if (c->nw > 0) {
-    launch_walkers(c->g, ps, brick_set(c, tn), c->pos[c->pcur], c->nw, c->u, c->d_T, (float)c->D, k0,
-                   k1, c->status, c->ticket, c->d_T, c->wlist, c->wlist_n, c->nsm, c->stream);
+    launch_walkers(c->g, ps, brick_set(c, tn), c->pos[c->pcur], c->nw, c->u[tp], c->d_T, toff, (float)c->D,
+                   k0, k1, c->status, c->ticket, c->wlist, c->wlist_n, c->nsm, ws);
     c->launches += 2;
-  } else {
-    launch_advance(c->d_T, c->stream);
-    c->launches++;
   }
   phase_end(c, RWMI_PHASE_WALKERS);
   c->t += 1;
   phase_begin(c, RWMI_PHASE_SORT);
   if (c->nw > 0 && c->cfg.sort_interval > 0 && c->t % c->cfg.sort_interval == 0) {
-    enqueue_sort(c);
+    enqueue_sort(c, ws);
     c->binned_t = c->t;
   }
   phase_end(c, RWMI_PHASE_SORT);
   phase_begin(c, RWMI_PHASE_MOMENTS);
   if (c->cfg.moment_interval > 0 && c->t % c->cfg.moment_interval == 0) {
     launch_moments(c->pos[c->pcur], c->x0[c->pcur], c->nw, c->macc, c->series, c->cfg.moment_interval,
-                   SERIES_ROWS, c->d_T, c->stream);
+                   SERIES_ROWS, c->d_T, toff + 1, ws);
     c->launches += c->nw > 0 ? 2 : 1;
     c->series_rows++;
   }
   phase_end(c, RWMI_PHASE_MOMENTS);
+  if (ws != c->stream) {
+    cudaEventRecord(c->walk_ev[tp], ws);
+    c->walk_rec[tp] = true;
+  }
+}
+
+// Closes a run of steps: the main stream joins the walker stream, and one launch advances the
+// device counter d_T by the run's length (no kernel of the run is still reading it).
+void segment_end(rwmi_ctx* c) {
+  if (c->walk_rec[0] || c->walk_rec[1]) {
+    cudaStreamWaitEvent(c->stream, c->walk_ev[(c->t - 1) & 1], 0);
+    c->walk_rec[0] = c->walk_rec[1] = false;
+  }
+  if (c->t > c->t_base) {
+    launch_advance(c->d_T, c->t - c->t_base, c->stream);
+    c->launches++;
+    c->t_base = c->t;
+  }
 }
 
 // Host mirrors of a replayed chunk of L steps (what enqueue_step does while capturing).
@@ -390,6 +423,7 @@ void advance_mirrors(rwmi_ctx* c, int64_t L) {
     }
     if (c->cfg.moment_interval > 0 && c->t % c->cfg.moment_interval == 0) c->series_rows++;
   }
+  c->t_base = c->t;
 }
 
 int64_t chunk_length(const rwmi_ctx* c) {
@@ -419,7 +453,7 @@ RWMI_API void rwmi_config_defaults(rwmi_config* cfg) {
   cfg->moment_interval = 0;
   cfg->use_graphs = 1;
   cfg->lbm_block = 256;
-  cfg->overlap = 1;
+  cfg->overlap = 2;
 }
 
 RWMI_API rwmi_status rwmi_create(rwmi_ctx** out, const int32_t dims[3], double tau, double D,
@@ -461,11 +495,12 @@ RWMI_API rwmi_status rwmi_create(rwmi_ctx** out, const int32_t dims[3], double t
     c->own_stream = true;
     rwmi_status s = alloc_fluid(c);
     if (s != RWMI_OK) return s;
-    CK(dalloc(c, &c->u, sizeof(float4) * (size_t)g.ncell_pad));   // (u, rho) per cell
+    for (int k = 0; k < 2; ++k) CK(dalloc(c, &c->u[k], sizeof(float4) * (size_t)g.ncell_pad));
     for (int k = 0; k < 2; ++k) CK(dalloc(c, &c->solid[k], sizeof(uint16_t) * (size_t)ncell));
     CK(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
-    CK(cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming));
-    CK(cudaEventCreateWithFlags(&c->join_ev, cudaEventDisableTiming));
+    CK(cudaStreamCreateWithFlags(&c->wst, cudaStreamNonBlocking));
+    for (cudaEvent_t* e : {&c->fork_ev, &c->join_ev, &c->fluid_ev, &c->walk_ev[0], &c->walk_ev[1]})
+      CK(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
     CK(dalloc(c, &c->d_T, sizeof(int64_t)));
     CK(dalloc(c, &c->ticket, sizeof(unsigned int)));
     CK(dalloc(c, &c->wlist_n, sizeof(unsigned int)));
@@ -475,7 +510,7 @@ RWMI_API rwmi_status rwmi_create(rwmi_ctx** out, const int32_t dims[3], double t
     CK(dalloc(c, &c->series, sizeof(double) * (size_t)SERIES_ROWS * SERIES_COLS));
     CK(dalloc(c, &c->mrow, sizeof(double) * SERIES_COLS));
     CK(dalloc(c, &c->counts, sizeof(uint32_t) * (size_t)ncell));
-    CK(dalloc(c, &c->wmask, sizeof(uint64_t) * c->nbrick));
+    for (int k = 0; k < 2; ++k) CK(dalloc(c, &c->wmask[k], sizeof(uint64_t) * c->nbrick));
     CK(dalloc(c, &c->offsets, sizeof(uint32_t) * (size_t)ncell));
     CK(dalloc(c, &c->bsums, sizeof(uint32_t) * scan_block_sums_size((uint32_t)ncell)));
     for (int k = 0; k < 2; ++k) {
@@ -517,7 +552,8 @@ RWMI_API rwmi_status rwmi_configure(rwmi_ctx* c, const rwmi_config* cfg) {
   if ((cfg->q != 15 && cfg->q != 19) || cfg->storage < 0 || cfg->storage > 2 || cfg->wall_mask > 7 ||
       !(cfg->rho0 > 0.0) || cfg->sort_interval < 0 || cfg->moment_interval < 0 ||
       !(cfg->force_period >= 0.0) ||
-      !(cfg->lbm_block == 0 || cfg->lbm_block == 64 || cfg->lbm_block == 128 || cfg->lbm_block == 256))
+      !(cfg->lbm_block == 0 || cfg->lbm_block == 64 || cfg->lbm_block == 128 || cfg->lbm_block == 256) ||
+      cfg->overlap < 0 || cfg->overlap > 2)
     return fail(c, RWMI_E_INVALID, "rwmi_configure: bad q, storage, wall_mask, rho0 or interval");
   for (int a = 0; a < 3; ++a)
     if (!std::isfinite(cfg->body_force[a]) || !std::isfinite(cfg->init_velocity[a]))
@@ -685,6 +721,7 @@ RWMI_API rwmi_status rwmi_step(rwmi_ctx* c, int32_t n) {
         const int64_t l0 = c->launches;
         CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
         for (int64_t s = 0; s < L; ++s) enqueue_step(c, s == L - 1);   // sums on the chunk's last step
+        segment_end(c);
         cudaGraph_t graph = nullptr;
         CK(cudaStreamEndCapture(c->stream, &graph));
         GraphEntry e;
@@ -700,9 +737,11 @@ RWMI_API rwmi_status rwmi_step(rwmi_ctx* c, int32_t n) {
         advance_mirrors(c, L);
       }
       n -= (int32_t)L;
-    } else {
-      enqueue_step(c, true);
-      n -= 1;
+    } else {   // eager run up to the next chunk boundary (or all n without graphs)
+      int64_t k = graphs ? std::min<int64_t>(n, L - c->t % L) : n;
+      n -= (int32_t)k;
+      while (k-- > 0) enqueue_step(c, true);
+      segment_end(c);
     }
   }
   CK(cudaGetLastError());
@@ -717,6 +756,7 @@ RWMI_API rwmi_status rwmi_step_timed(rwmi_ctx* c, int32_t n, double* phase_ms) {
   c->timing = true;
   for (int32_t s = 0; s < n; ++s) {
     enqueue_step(c, s == n - 1);   // as in a replayed chunk: the sums on the last step only
+    segment_end(c);
     cudaError_t e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
       c->timing = false;
@@ -747,7 +787,7 @@ RWMI_API rwmi_status rwmi_autotune(rwmi_ctx* c, int32_t* chosen) {
   for (int k = 0; k < 3; ++k) {
     for (int rep = 0; rep < 6; ++rep) {
       if (rep == 1) cudaEventRecord(e0, c->stream);
-      launch_lbm(c->cfg.q, c->cfg.storage, false, c->g, c->f[c->fcur], c->f[c->fcur ^ 1], c->u, c->solid[c->t & 1],
+      launch_lbm(c->cfg.q, c->cfg.storage, false, c->g, c->f[c->fcur], c->f[c->fcur ^ 1], c->u[c->t & 1], c->solid[c->t & 1],
                  brick_set(c, tp), (float)c->tau, (float)c->cfg.rho0, (double*)c->scratch + 6 * c->P,
                  (double*)c->scratch, c->status, c->stream, cand[k]);
       c->launches++;
@@ -794,8 +834,8 @@ RWMI_API rwmi_status rwmi_footprint(const int32_t dims[3], int32_t q, int32_t st
   const uint64_t pad = (ncell + 63) / 64 * 64, sb = storage == 2 ? 2 : 4, P = (uint64_t)n_particles,
                  Nc = (uint64_t)n_centers, N = (uint64_t)n_walkers;
   uint64_t b = 2 * (uint64_t)q * pad * sb;                     // populations A/B
-  b += 16 * pad + 2 * ncell + 8 * ncell + 4 * (ncell / 2048 + 2);   // (u, rho), solid, counts/offsets, scan
-  b += 2 * (4 * (nbrick + 1) + 2 * MAXC * nbrick + 4 * nbrick) + 8 * nbrick;   // bricks, masks
+  b += 2 * 16 * pad + 2 * 2 * ncell + 8 * ncell + 4 * (ncell / 2048 + 2);   // (u, rho), solid, counts/offsets, scan
+  b += 2 * (4 * (nbrick + 1) + 2 * MAXC * nbrick + 4 * nbrick) + 2 * 8 * nbrick;   // bricks, masks
   b += 100 * N;                                                // pos, x0 (A/B), rank, resolve list
   b += 2 * 48 * P + 2 * 16 * Nc + sizeof(ParticleDesc) * P + 16 * Nc + 2 * 8 * (6 * P + 4 * RED_SLOTS);
   b += (uint64_t)SERIES_ROWS * SERIES_COLS * 8 + 4096;         // moment series, counters
@@ -843,7 +883,7 @@ RWMI_API rwmi_status rwmi_concentration(rwmi_ctx* c, uint32_t* out) {
 
 RWMI_API rwmi_status rwmi_walker_moments(rwmi_ctx* c, double out[13]) {
   if (!c || !out) return RWMI_E_INVALID;
-  launch_moments(c->pos[c->pcur], c->x0[c->pcur], c->nw, c->macc, c->mrow, 0, 1, c->d_T, c->stream);
+  launch_moments(c->pos[c->pcur], c->x0[c->pcur], c->nw, c->macc, c->mrow, 0, 1, c->d_T, 0, c->stream);
   c->launches += c->nw > 0 ? 2 : 1;
   CK(cudaGetLastError());
   return copy_out(c, out, c->mrow + 1, sizeof(double) * 13);
@@ -870,7 +910,7 @@ RWMI_API rwmi_status rwmi_velocity(rwmi_ctx* c, float* out) {
   if (!c || !out) return RWMI_E_INVALID;
   rwmi_status s = ensure_scratch(c, sizeof(float) * 3 * (size_t)c->ncell);
   if (s != RWMI_OK) return s;
-  launch_velocity_aos(c->g, c->u, (float*)c->scratch, c->stream);
+  launch_velocity_aos(c->g, c->u[(c->t + 1) & 1], (float*)c->scratch, c->stream);
   c->launches++;
   CK(cudaGetLastError());
   return copy_out(c, out, c->scratch, sizeof(float) * 3 * (size_t)c->ncell);
@@ -1034,6 +1074,7 @@ RWMI_API rwmi_status rwmi_load(rwmi_ctx* c, const char* path) {
     CK(copy_now(c, c->x0[0], q.data(), sizeof(float4) * q.size()));
   }
   CK(copy_now(c, c->d_T, &c->t, sizeof(int64_t)));
+  c->t_base = c->t;
   rwmi_status s = build_current_frame(c);
   if (s != RWMI_OK) return s;
   CK(cudaStreamSynchronize(c->stream));
@@ -1122,6 +1163,7 @@ RWMI_API rwmi_status rwmi_batch_step(rwmi_batch* b, int32_t nsteps) {
         rwmi_ctx* c = b->ctxs[k];
         cudaStreamWaitEvent(c->stream, b->fork, 0);
         for (int64_t st = 0; st < b->L; ++st) enqueue_step(c, st == b->L - 1);
+        segment_end(c);
         cudaEventRecord(b->join[k], c->stream);
         cudaStreamWaitEvent(b->origin, b->join[k], 0);
       }
@@ -1192,15 +1234,16 @@ RWMI_API void rwmi_destroy(rwmi_ctx* c) {
     dfree(c, c->pose[k]); dfree(c, c->sp[k]); dfree(c, c->cworld[k]); dfree(c, c->pos[k]); dfree(c, c->x0[k]);
   }
   dfree(c, c->wlist); dfree(c, c->wlist_n);
-  dfree(c, c->u); dfree(c, c->solid[0]); dfree(c, c->solid[1]); dfree(c, c->d_T); dfree(c, c->ticket); dfree(c, c->status); dfree(c, c->macc);
+  dfree(c, c->u[0]); dfree(c, c->u[1]); dfree(c, c->solid[0]); dfree(c, c->solid[1]); dfree(c, c->d_T); dfree(c, c->ticket); dfree(c, c->status); dfree(c, c->macc);
   dfree(c, c->series); dfree(c, c->mrow); dfree(c, c->desc); dfree(c, c->cbody); dfree(c, c->rank);
-  dfree(c, c->counts); dfree(c, c->offsets); dfree(c, c->bsums); dfree(c, c->scratch); dfree(c, c->wmask);
+  dfree(c, c->counts); dfree(c, c->offsets); dfree(c, c->bsums); dfree(c, c->scratch); dfree(c, c->wmask[0]); dfree(c, c->wmask[1]);
   cudaStreamSynchronize(c->stream);   // the frees have returned the memory when this returns
   for (int k = 0; k < 2 * RWMI_NPHASE; ++k)
     if (c->ev[k]) cudaEventDestroy(c->ev[k]);
-  if (c->fork_ev) cudaEventDestroy(c->fork_ev);
-  if (c->join_ev) cudaEventDestroy(c->join_ev);
+  for (cudaEvent_t e : {c->fork_ev, c->join_ev, c->fluid_ev, c->walk_ev[0], c->walk_ev[1]})
+    if (e) cudaEventDestroy(e);
   if (c->side) cudaStreamDestroy(c->side);
+  if (c->wst) cudaStreamDestroy(c->wst);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
 }

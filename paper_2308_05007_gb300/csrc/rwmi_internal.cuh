@@ -214,11 +214,14 @@ void launch_lbm(int q, int storage, bool reduce, const Geom& g, const void* fin,
                 int block = 256);
 void launch_init_populations(int q, int storage, const Geom& g, void* f, float rho0,
                              const float u0[3], float* u, cudaStream_t st);
+// Time of a launch: *d_T (the step counter at the start of the current run of steps, advanced
+// only between runs) plus toff, fixed when the launch is queued or captured. Kernels of several
+// steps may then run concurrently without racing on the counter.
 void launch_walkers(const Geom& g, const ParticleSet& ps, BrickSet bs1, float4* pos, int64_t n,
-                    const float* u, const int64_t* d_T, float D, uint32_t k0, uint32_t k1,
-                    unsigned long long* status, unsigned int* ticket, int64_t* d_T_inc,
-                    float4* list, unsigned int* list_n, int nsm, cudaStream_t st);
-void launch_advance(int64_t* d_T, cudaStream_t st);
+                    const float* u, const int64_t* d_T, int toff, float D, uint32_t k0, uint32_t k1,
+                    unsigned long long* status, unsigned int* ticket, float4* list,
+                    unsigned int* list_n, int nsm, cudaStream_t st);
+void launch_advance(int64_t* d_T, int64_t k, cudaStream_t st);
 void launch_seed(const Geom& g, const ParticleSet& ps, BrickSet bs, float4* pos, float4* x0,
                  int64_t n, const double lo[3], const double hi[3], uint32_t k0, uint32_t k1,
                  unsigned long long* status, cudaStream_t st);
@@ -231,7 +234,7 @@ void launch_scatter(const Geom& g, const float4* pos, const float4* x0, int64_t 
                     const uint32_t* offsets, const uint32_t* rank, float4* pos_out,
                     float4* x0_out, cudaStream_t st);
 void launch_moments(const float4* pos, const float4* x0, int64_t n, double* acc, double* base,
-                    int interval, int rows, const int64_t* d_T, cudaStream_t st);
+                    int interval, int rows, const int64_t* d_T, int toff, cudaStream_t st);
 void launch_unpack_solid(const Geom& g, const uint16_t* solid, const uint32_t* bword,
                          int32_t* count, int32_t* owner, cudaStream_t st);
 void launch_populations_f64(int q, int storage, const Geom& g, const void* f, float rho0,

@@ -250,11 +250,11 @@ __device__ __noinline__ unsigned resolve_particles(const WalkCtx& c, const float
 // resolves those at full SIMT width, so this kernel carries none of the rare-path code.
 __global__ void __launch_bounds__(256, 4) walker_kernel(WalkCtx c, float4* __restrict__ pos, int64_t n,
                                                         const float* __restrict__ u,
-                                                        const int64_t* __restrict__ d_T, float amp,
-                                                        uint32_t k0, uint32_t k1,
+                                                        const int64_t* __restrict__ d_T, int toff,
+                                                        float amp, uint32_t k0, uint32_t k1,
                                                         unsigned long long* __restrict__ status,
                                                         float4* __restrict__ list, unsigned int* list_n) {
-  const int64_t T = *d_T;
+  const int64_t T = *d_T + toff;
   const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   bool ev_wall = false, ev_fast = false, ev_nonfinite = false, flagged = false;
   float4 ea = make_float4(0.f, 0.f, 0.f, 0.f), eb = ea;
@@ -328,15 +328,15 @@ __global__ void __launch_bounds__(256, 4) walker_kernel(WalkCtx c, float4* __res
 }
 
 // Pass 2 (fixed grid, grid-stride over the list): types II-IV of the flagged walkers, written back
-// to their slots. The last warp to finish advances the device step counter and empties the list
-// (every warp has read both by then).
+// to their slots. The last warp to finish empties the list (every warp has read its length by
+// then).
 __global__ void __launch_bounds__(256, 4) walker_resolve_kernel(WalkCtx c, float4* __restrict__ pos,
                                                              const float4* __restrict__ list,
                                                              unsigned int* list_n, const int64_t* d_T,
-                                                             float amp, uint32_t k0, uint32_t k1,
+                                                             int toff, float amp, uint32_t k0, uint32_t k1,
                                                              unsigned long long* __restrict__ status,
-                                                             unsigned int* ticket, int64_t* d_T_inc) {
-  const int64_t T = *d_T;
+                                                             unsigned int* ticket) {
+  const int64_t T = *d_T + toff;
   const unsigned cnt = *list_n;
   if (blockIdx.x == 0 && threadIdx.x == 0 && cnt) atomicAdd(&status[ST_RESOLVED], (unsigned long long)cnt);
   unsigned ev_all[5] = {0u, 0u, 0u, 0u, 0u};
@@ -396,25 +396,24 @@ __global__ void __launch_bounds__(256, 4) walker_resolve_kernel(WalkCtx c, float
     const unsigned int done = atomicAdd(ticket, 1u);
     if (done == nwarps - 1) {
       *list_n = 0u;
-      if (d_T_inc) *d_T_inc = T + 1;
       *ticket = 0u;
     }
   }
 }
 
 void launch_walkers(const Geom& g, const ParticleSet& ps, BrickSet bs1, float4* pos, int64_t n,
-                    const float* u, const int64_t* d_T, float D, uint32_t k0, uint32_t k1,
-                    unsigned long long* status, unsigned int* ticket, int64_t* d_T_inc,
-                    float4* list, unsigned int* list_n, int nsm, cudaStream_t st) {
+                    const float* u, const int64_t* d_T, int toff, float D, uint32_t k0, uint32_t k1,
+                    unsigned long long* status, unsigned int* ticket, float4* list,
+                    unsigned int* list_n, int nsm, cudaStream_t st) {
   WalkCtx c{g, ps, bs1};
   const int64_t blocks = (n + 255) / 256;
   const float amp = sqrtf(2.0f * D);
-  walker_kernel<<<(unsigned)blocks, 256, 0, st>>>(c, pos, n, u, d_T, amp, k0, k1, status, list, list_n);
-  walker_resolve_kernel<<<nsm * 8, 256, 0, st>>>(c, pos, list, list_n, d_T, amp, k0, k1, status, ticket, d_T_inc);
+  walker_kernel<<<(unsigned)blocks, 256, 0, st>>>(c, pos, n, u, d_T, toff, amp, k0, k1, status, list, list_n);
+  walker_resolve_kernel<<<nsm * 8, 256, 0, st>>>(c, pos, list, list_n, d_T, toff, amp, k0, k1, status, ticket);
 }
 
-__global__ void advance_kernel(int64_t* d_T) { *d_T += 1; }
-void launch_advance(int64_t* d_T, cudaStream_t st) { advance_kernel<<<1, 1, 0, st>>>(d_T); }
+__global__ void advance_kernel(int64_t* d_T, int64_t k) { *d_T += k; }
+void launch_advance(int64_t* d_T, int64_t k, cudaStream_t st) { advance_kernel<<<1, 1, 0, st>>>(d_T, k); }
 
 // ------------------------------------------------------------------------------------------
 // Seeding: walker w tries Philox counters (w, a, 2, 0); point lo + U (hi - lo) in explicitly
@@ -670,10 +669,10 @@ __global__ void moments_kernel(const float4* __restrict__ pos, const float4* __r
 // interval > 0 the row is slot (t / interval - 1) mod rows of the series at base (so a replayed
 // graph writes the row of the step it runs), otherwise base itself.
 __global__ void moments_finalize_kernel(double* acc, int64_t n, double* base, int interval, int rows,
-                                        const int64_t* d_T) {
+                                        const int64_t* d_T, int toff) {
   if (threadIdx.x != 0) return;
   const double N = (double)n;
-  const int64_t t = *d_T;
+  const int64_t t = *d_T + toff;
   double* out_row = base;
   if (interval > 0) out_row = base + (size_t)(((t / interval) - 1) % rows) * 14;
   out_row[0] = (double)t;
@@ -689,13 +688,13 @@ __global__ void moments_finalize_kernel(double* acc, int64_t n, double* base, in
 }
 
 void launch_moments(const float4* pos, const float4* x0, int64_t n, double* acc, double* base,
-                    int interval, int rows, const int64_t* d_T, cudaStream_t st) {
+                    int interval, int rows, const int64_t* d_T, int toff, cudaStream_t st) {
   if (n > 0) {
     int64_t blocks = (n + 255) / 256;
     if (blocks > 152 * 8) blocks = 152 * 8;
     moments_kernel<<<(unsigned)blocks, 256, 0, st>>>(pos, x0, n, acc);
   }
-  moments_finalize_kernel<<<1, 32, 0, st>>>(acc, n, base, interval, rows, d_T);
+  moments_finalize_kernel<<<1, 32, 0, st>>>(acc, n, base, interval, rows, d_T, toff);
 }
 
 // ------------------------------------------------------------------------------------------

@@ -173,7 +173,7 @@ class Simulation:
     def __init__(self, dims, tau, D, seed=0, q=19, storage=STORE_FP32_SHIFT, wall_mask=0,
                  body_force=(0.0, 0.0, 0.0), force_period=0.0, rho0=1.0, init_velocity=(0.0, 0.0, 0.0),
                  sort_interval=16, moment_interval=0, use_graphs=True, stream=None, lbm_block=256,
-                 overlap=True):
+                 overlap=2):
         L = load()
         self._L = L
         self._h = C.c_void_p()
@@ -193,7 +193,7 @@ class Simulation:
         cfg.sort_interval, cfg.moment_interval = int(sort_interval), int(moment_interval)
         cfg.use_graphs = 1 if use_graphs else 0
         cfg.lbm_block = int(lbm_block)
-        cfg.overlap = 1 if overlap else 0
+        cfg.overlap = int(overlap)
         self._check(L.rwmi_configure(self._h, C.byref(cfg)))
         self.q = int(q)
         _live.add(self)

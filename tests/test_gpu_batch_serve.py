@@ -111,28 +111,32 @@ def test_autotuned_block_size_changes_no_result():
 
 
 def test_overlapped_raster_changes_no_result():
-    """The raster of t+1 on a second stream beside the LBM of t gives the serial schedule's
-    results bit for bit (eager and graph-replayed)."""
+    """The overlapped schedules (raster of t+1 beside the LBM of t; walkers of t beside the
+    fluid of t+1) give the serial schedule's results bit for bit, eager and graph-replayed."""
     _need_gpu()
     from paper_2308_05007_gb300 import inputs as I
     from paper_2308_05007_gb300.rwmi import Simulation
-    w = I.with_(I.ragged(n_walkers=4000), sort_interval=4)
+    w = I.with_(I.ragged(n_walkers=4000), sort_interval=4, moment_interval=2)
     out = {}
-    for overlap in (False, True):
+    for overlap in (0, 1, 2):
         for graphs in (False, True):
             with Simulation.from_workload(w, overlap=overlap, use_graphs=graphs) as s:
                 s.step(13)
                 st = _state(s)
                 st["solid"] = s.solid()
                 st["forces"] = s.particle_forces()
+                st["series"] = s.moment_series()
             out[(overlap, graphs)] = st
-    ref = out[(False, False)]
+    ref = out[(0, False)]
     for key, st in out.items():
         _same(ref, st, f"overlap={key[0]} graphs={key[1]}")
         for a, b in zip(ref["solid"], st["solid"]):
             assert np.array_equal(a, b)
         np.testing.assert_allclose(ref["forces"], st["forces"], rtol=1e-12,
                                    atol=1e-12 * np.max(np.abs(ref["forces"])))
+        assert ref["series"].shape == st["series"].shape == (6, 14)
+        assert np.array_equal(ref["series"][:, 0], np.arange(2, 14, 2))   # the row of each step
+        np.testing.assert_allclose(ref["series"], st["series"], rtol=1e-12, atol=1e-12)
 
 
 def test_query_and_footprint():
