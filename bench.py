@@ -27,7 +27,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "LBM MLUPS + walker-steps/s and %HBM roofline, FP32/FP16-shift vs plain; p99 latency"
-STORE_NAMES = {0: "fp32", 1: "fp32_shift", 2: "fp16_shift"}
+STORE_NAMES = {0: "fp32", 1: "fp32_shift", 2: "fp16_shift", 3: "fp64_shift"}
+STORE_BYTES = {0: 4, 1: 4, 2: 2, 3: 8}
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "lbm_kernel_oscillator_256.md")
 
 
@@ -84,7 +85,7 @@ def config_dict(a, w):
         "cells": w.n_cells, "walkers": w.n_walkers, "particles": a.particles, "q": w.q,
         "storage": STORE_NAMES[w.storage], "sort_interval": w.sort_interval,
         "moment_interval": w.moment_interval,
-        "l2": "inputs larger than L2 (populations 2 x %.2f GB), no flush" % (w.n_cells * w.q * (2 if w.storage == 2 else 4) / 1e9),
+        "l2": "inputs larger than L2 (populations 2 x %.2f GB), no flush" % (w.n_cells * w.q * STORE_BYTES[w.storage] / 1e9),
         "graphs": "CUDA graph per %d steps" % max(w.sort_interval, w.moment_interval, 2),
         "schedule": {0: "serial", 1: "raster of t+1 on a second stream beside the LBM of t",
                      2: "raster of t+1 beside the LBM of t; walkers of t on a third stream beside "
@@ -241,14 +242,15 @@ def job_rate(world: int, units_per_rank: float, steps: int, seconds: float) -> f
 
 def measure_variants(a, stream):
     """The same workload with the other population storages (plain binary32, binary32 shifted by
-    w_i rho0, binary16 shifted) and velocity sets (D3Q15, the paper's D3Q19): per-phase GPU time
-    of 16 eager steps (CUDA events), LBM kernel HBM fraction and whole-step MLUPS."""
+    w_i rho0, binary16 shifted, binary64 shifted with binary64 arithmetic) and velocity sets
+    (D3Q15, the paper's D3Q19): per-phase GPU time of 16 eager steps (CUDA events), LBM kernel
+    HBM fraction and whole-step MLUPS. The binary64 run is bound by GB300's FP64 rate, not HBM."""
     import argparse as _ap
     from paper_2308_05007_gb300.rwmi import Simulation
     peak = float(measured_peaks()["hbm_gbs"])
     out = {}
     for q in (15, 19):
-        for storage in (0, 1, 2):
+        for storage in (0, 1, 2, 3):
             b = _ap.Namespace(**vars(a))
             b.q, b.storage = q, storage
             w = workload(b)
@@ -258,7 +260,7 @@ def measure_variants(a, stream):
             sim.step(16)
             ph = sim.step_timed(16)
             sim.close()
-            s_bytes = 2 if storage == 2 else 4
+            s_bytes = STORE_BYTES[storage]
             lbm_ms = ph["lbm"] / 16
             step_ms = sum(ph.values()) / 16
             gbs = lbm_bytes_per_launch(w, w.n_cells, s_bytes) / (lbm_ms / 1e3) / 1e9
@@ -350,7 +352,7 @@ def main():
     from paper_2308_05007_gb300.rwmi import Simulation
 
     w = workload(a)
-    s_bytes = 2 if w.storage == 2 else 4
+    s_bytes = STORE_BYTES[w.storage]
     stream = torch.cuda.Stream()
     sim = Simulation.from_workload(w, seed_walkers=False, overlap=a.overlap)
     sim.set_stream(stream)
@@ -425,7 +427,8 @@ def main():
     line = {
         "metric": METRIC, "value": mlups, "unit": "MLUPS", "n_gpus": world, "steps": steps,
         "warmup": warm, "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config_dict(a, w),
+        "vs_baseline": None, "dtype": "f64" if w.storage == 3 else "f32", "data": "synthetic",
+        "config": config_dict(a, w),
         "walker_steps_per_s": wsps,
         "step_hbm_frac": step_bytes / (ms / steps / 1e3) / 1e9 / peak,
         "step_algorithmic_bytes": step_bytes,

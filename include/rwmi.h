@@ -67,12 +67,15 @@ typedef enum {
     RWMI_E_STATE = -6        /* call out of order (e.g. stepping before configuration ends) */
 } rwmi_status;
 
-/* Storage of the populations in HBM; arithmetic is FP32 in every case. */
+/* Storage of the populations in HBM and the arithmetic of the LBM update. The walkers, the
+ * rasteriser and the velocity field handed to the walkers are binary32 in every case. */
 enum {
-    RWMI_STORE_FP32 = 0,          /* f_i as binary32 */
-    RWMI_STORE_FP32_SHIFT = 1,    /* f_i - w_i rho0 as binary32 (default; keeps u ~ 1e-4 exact
-                                     to ~1e-7 relative) */
-    RWMI_STORE_FP16_SHIFT = 2     /* f_i - w_i rho0 as binary16 */
+    RWMI_STORE_FP32 = 0,          /* f_i as binary32, binary32 arithmetic */
+    RWMI_STORE_FP32_SHIFT = 1,    /* f_i - w_i rho0 as binary32, binary32 arithmetic (default;
+                                     keeps u ~ 1e-4 exact to ~1e-7 relative) */
+    RWMI_STORE_FP16_SHIFT = 2,    /* f_i - w_i rho0 as binary16, binary32 arithmetic */
+    RWMI_STORE_FP64_SHIFT = 3     /* f_i - w_i rho0 as binary64, binary64 arithmetic: the
+                                     FP64-on-GPU reference run (GB300's FP64 rate is low) */
 };
 
 typedef struct {

@@ -54,7 +54,6 @@ struct rwmi_ctx {
   float* u[2] = {nullptr, nullptr};   // (u, rho) per time parity: the LBM of t writes u[t & 1]
   uint16_t* solid[2] = {nullptr, nullptr};   // per time parity: raster of t+1 beside the LBM of t
   int64_t* d_T = nullptr;
-  unsigned int* ticket = nullptr;
   unsigned long long* status = nullptr;
   double* acc[2] = {nullptr, nullptr};   // per time parity: forces [6P] + mass/momentum [4]
   double* macc = nullptr;                // moment accumulators [12]
@@ -150,7 +149,7 @@ cudaError_t copy_now(rwmi_ctx* c, void* dst, const void* src, size_t bytes) {
   return e != cudaSuccess ? e : cudaStreamSynchronize(c->stream);
 }
 
-size_t storage_bytes(int storage) { return storage == 2 ? 2 : 4; }
+size_t storage_bytes(int storage) { return storage == 2 ? 2 : storage == 3 ? 8 : 4; }
 
 bool is_device_ptr(const void* p) {
   cudaPointerAttributes a;
@@ -201,6 +200,7 @@ BrickSet brick_set(const rwmi_ctx* c, int par) {
   b.bcand = c->bcand[par];
   b.rlist = c->rlist[par];
   b.pose = c->pose[par];
+  b.posed = reinterpret_cast<PoseD*>(c->pose[par] + (c->P > 0 ? c->P : 1));   // 48 P bytes: aligned
   b.cworld = c->cworld[par];
   b.sp = c->sp[par];
   return b;
@@ -228,9 +228,8 @@ rwmi_status build_current_frame(rwmi_ctx* c) {
 }
 
 rwmi_status reset_fluid(rwmi_ctx* c) {
-  const float u0[3] = {(float)c->cfg.init_velocity[0], (float)c->cfg.init_velocity[1],
-                       (float)c->cfg.init_velocity[2]};
-  launch_init_populations(c->cfg.q, c->cfg.storage, c->g, c->f[c->fcur], (float)c->cfg.rho0, u0,
+  const double u0[3] = {c->cfg.init_velocity[0], c->cfg.init_velocity[1], c->cfg.init_velocity[2]};
+  launch_init_populations(c->cfg.q, c->cfg.storage, c->g, c->f[c->fcur], c->cfg.rho0, u0,
                           c->u[(c->t + 1) & 1], c->stream);
   c->launches++;
   CK(cudaGetLastError());
@@ -255,7 +254,7 @@ rwmi_status alloc_particles(rwmi_ctx* c) {
     c->pose[k] = nullptr;
     c->cworld[k] = nullptr;
     c->acc[k] = nullptr;
-    CK(dalloc(c, &c->pose[k], sizeof(PoseF) * (size_t)(c->P > 0 ? c->P : 1)));
+    CK(dalloc(c, &c->pose[k], (sizeof(PoseF) + sizeof(PoseD)) * (size_t)(c->P > 0 ? c->P : 1)));
     CK(dalloc(c, &c->cworld[k], sizeof(float4) * (size_t)(c->Nc > 0 ? c->Nc : 1)));
     CK(dalloc(c, &c->acc[k], sizeof(double) * (size_t)(6 * c->P + 4 * RED_SLOTS)));
     CK(cudaMemsetAsync(c->acc[k], 0, sizeof(double) * (size_t)(6 * c->P + 4 * RED_SLOTS), c->stream));
@@ -280,11 +279,13 @@ rwmi_status alloc_walkers(rwmi_ctx* c, int64_t n) {
     CK(dalloc(c, &c->x0[k], sizeof(float4) * (size_t)n));
   }
   CK(dalloc(c, &c->rank, sizeof(uint32_t) * (size_t)n));
-  CK(dalloc(c, &c->wlist, 2 * sizeof(float4) * (size_t)n));
+  CK(dalloc(c, &c->wlist, 2 * sizeof(float4) * (size_t)(WLIST_STRIPES * wlist_stripe_cap(n))));
   c->nw = n;
   c->pcur = 0;
   c->binned_t = -1;
   drop_graphs(c);
+  // the flagged-walker list counters of both parities start at zero for new walkers
+  CK(cudaMemsetAsync(c->wlist_n, 0, sizeof(unsigned int) * 2 * WLIST_STRIPES, c->stream));
   return RWMI_OK;
 }
 
@@ -340,7 +341,7 @@ void enqueue_step(rwmi_ctx* c, bool reduce) {
   auto lbm = [&]() {    // LBM at t
     phase_begin(c, RWMI_PHASE_LBM);
     launch_lbm(c->cfg.q, c->cfg.storage, reduce, c->g, c->f[c->fcur], c->f[c->fcur ^ 1], c->u[tp], c->solid[tp],
-               brick_set(c, tp), (float)c->tau, (float)c->cfg.rho0, c->acc[tp] + 6 * c->P, c->acc[tp],
+               brick_set(c, tp), c->tau, c->cfg.rho0, c->acc[tp] + 6 * c->P, c->acc[tp],
                c->status, c->stream, c->cfg.lbm_block);
     c->launches++;
     phase_end(c, RWMI_PHASE_LBM);
@@ -372,8 +373,8 @@ void enqueue_step(rwmi_ctx* c, bool reduce) {
   }
   phase_begin(c, RWMI_PHASE_WALKERS);
   if (c->nw > 0) {
-    launch_walkers(c->g, ps, brick_set(c, tn), c->pos[c->pcur], c->nw, c->u[tp], c->d_T, toff, (float)c->D,
-                   k0, k1, c->status, c->ticket, c->wlist, c->wlist_n, c->nsm, ws);
+    launch_walkers(c->g, ps, brick_set(c, tn), c->pos[c->pcur], c->nw, c->u[tp], c->d_T, toff, tp, (float)c->D,
+                   k0, k1, c->status, c->wlist, c->wlist_n, c->nsm, ws);
     c->launches += 2;
   }
   phase_end(c, RWMI_PHASE_WALKERS);
@@ -502,9 +503,8 @@ RWMI_API rwmi_status rwmi_create(rwmi_ctx** out, const int32_t dims[3], double t
     for (cudaEvent_t* e : {&c->fork_ev, &c->join_ev, &c->fluid_ev, &c->walk_ev[0], &c->walk_ev[1]})
       CK(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
     CK(dalloc(c, &c->d_T, sizeof(int64_t)));
-    CK(dalloc(c, &c->ticket, sizeof(unsigned int)));
-    CK(dalloc(c, &c->wlist_n, sizeof(unsigned int)));
-    CK(cudaMemsetAsync(c->wlist_n, 0, sizeof(unsigned int), c->stream));
+    CK(dalloc(c, &c->wlist_n, sizeof(unsigned int) * 2 * WLIST_STRIPES));
+    CK(cudaMemsetAsync(c->wlist_n, 0, sizeof(unsigned int) * 2 * WLIST_STRIPES, c->stream));
     CK(dalloc(c, &c->status, sizeof(unsigned long long) * ST_COUNT));
     CK(dalloc(c, &c->macc, sizeof(double) * 12));
     CK(dalloc(c, &c->series, sizeof(double) * (size_t)SERIES_ROWS * SERIES_COLS));
@@ -525,7 +525,6 @@ RWMI_API rwmi_status rwmi_create(rwmi_ctx** out, const int32_t dims[3], double t
     s = alloc_particles(c);
     if (s != RWMI_OK) return s;
     CK(cudaMemsetAsync(c->d_T, 0, sizeof(int64_t), c->stream));
-    CK(cudaMemsetAsync(c->ticket, 0, sizeof(unsigned int), c->stream));
     CK(cudaMemsetAsync(c->status, 0, sizeof(unsigned long long) * ST_COUNT, c->stream));
     CK(cudaMemsetAsync(c->macc, 0, sizeof(double) * 12, c->stream));
     for (int k = 0; k < 2; ++k) CK(cudaMemsetAsync(c->solid[k], 0, sizeof(uint16_t) * (size_t)ncell, c->stream));
@@ -549,7 +548,7 @@ RWMI_API rwmi_status rwmi_create(rwmi_ctx** out, const int32_t dims[3], double t
 RWMI_API rwmi_status rwmi_configure(rwmi_ctx* c, const rwmi_config* cfg) {
   if (!c || !cfg) return RWMI_E_INVALID;
   if (c->stepped) return fail(c, RWMI_E_STATE, "rwmi_configure: only before the first step");
-  if ((cfg->q != 15 && cfg->q != 19) || cfg->storage < 0 || cfg->storage > 2 || cfg->wall_mask > 7 ||
+  if ((cfg->q != 15 && cfg->q != 19) || cfg->storage < 0 || cfg->storage > 3 || cfg->wall_mask > 7 ||
       !(cfg->rho0 > 0.0) || cfg->sort_interval < 0 || cfg->moment_interval < 0 ||
       !(cfg->force_period >= 0.0) ||
       !(cfg->lbm_block == 0 || cfg->lbm_block == 64 || cfg->lbm_block == 128 || cfg->lbm_block == 256) ||
@@ -788,7 +787,7 @@ RWMI_API rwmi_status rwmi_autotune(rwmi_ctx* c, int32_t* chosen) {
     for (int rep = 0; rep < 6; ++rep) {
       if (rep == 1) cudaEventRecord(e0, c->stream);
       launch_lbm(c->cfg.q, c->cfg.storage, false, c->g, c->f[c->fcur], c->f[c->fcur ^ 1], c->u[c->t & 1], c->solid[c->t & 1],
-                 brick_set(c, tp), (float)c->tau, (float)c->cfg.rho0, (double*)c->scratch + 6 * c->P,
+                 brick_set(c, tp), c->tau, c->cfg.rho0, (double*)c->scratch + 6 * c->P,
                  (double*)c->scratch, c->status, c->stream, cand[k]);
       c->launches++;
     }
@@ -822,7 +821,7 @@ RWMI_API rwmi_status rwmi_query(rwmi_ctx* c) {
 
 RWMI_API rwmi_status rwmi_footprint(const int32_t dims[3], int32_t q, int32_t storage, int64_t n_walkers,
                                     int32_t n_particles, int32_t n_centers, uint64_t* bytes) {
-  if (!dims || !bytes || (q != 15 && q != 19) || storage < 0 || storage > 2 || n_walkers < 0 ||
+  if (!dims || !bytes || (q != 15 && q != 19) || storage < 0 || storage > 3 || n_walkers < 0 ||
       n_particles < 0 || n_centers < 0)
     return RWMI_E_INVALID;
   uint64_t ncell = 1, nbrick = 1;
@@ -831,13 +830,13 @@ RWMI_API rwmi_status rwmi_footprint(const int32_t dims[3], int32_t q, int32_t st
     ncell *= (uint64_t)dims[a];
     nbrick *= (uint64_t)((dims[a] + BRICK - 1) / BRICK);
   }
-  const uint64_t pad = (ncell + 63) / 64 * 64, sb = storage == 2 ? 2 : 4, P = (uint64_t)n_particles,
+  const uint64_t pad = (ncell + 63) / 64 * 64, sb = storage_bytes(storage), P = (uint64_t)n_particles,
                  Nc = (uint64_t)n_centers, N = (uint64_t)n_walkers;
   uint64_t b = 2 * (uint64_t)q * pad * sb;                     // populations A/B
   b += 2 * 16 * pad + 2 * 2 * ncell + 8 * ncell + 4 * (ncell / 2048 + 2);   // (u, rho), solid, counts/offsets, scan
   b += 2 * (4 * (nbrick + 1) + 2 * MAXC * nbrick + 4 * nbrick) + 2 * 8 * nbrick;   // bricks, masks
   b += 100 * N;                                                // pos, x0 (A/B), rank, resolve list
-  b += 2 * 48 * P + 2 * 16 * Nc + sizeof(ParticleDesc) * P + 16 * Nc + 2 * 8 * (6 * P + 4 * RED_SLOTS);
+  b += 2 * (48 + 80) * P + 2 * 16 * Nc + sizeof(ParticleDesc) * P + 16 * Nc + 2 * 8 * (6 * P + 4 * RED_SLOTS);
   b += (uint64_t)SERIES_ROWS * SERIES_COLS * 8 + 4096;         // moment series, counters
   *bytes = b;
   return RWMI_OK;
@@ -920,7 +919,7 @@ RWMI_API rwmi_status rwmi_density(rwmi_ctx* c, float* out) {
   if (!c || !out) return RWMI_E_INVALID;
   rwmi_status s = ensure_scratch(c, sizeof(float) * (size_t)c->ncell);
   if (s != RWMI_OK) return s;
-  launch_density(c->cfg.q, c->cfg.storage, c->g, c->f[c->fcur], (float)c->cfg.rho0, (float*)c->scratch, c->stream);
+  launch_density(c->cfg.q, c->cfg.storage, c->g, c->f[c->fcur], c->cfg.rho0, (float*)c->scratch, c->stream);
   c->launches++;
   CK(cudaGetLastError());
   return copy_out(c, out, c->scratch, sizeof(float) * (size_t)c->ncell);
@@ -931,7 +930,7 @@ RWMI_API rwmi_status rwmi_populations(rwmi_ctx* c, double* out) {
   const size_t bytes = sizeof(double) * (size_t)c->cfg.q * (size_t)c->ncell;
   rwmi_status s = ensure_scratch(c, bytes);
   if (s != RWMI_OK) return s;
-  launch_populations_f64(c->cfg.q, c->cfg.storage, c->g, c->f[c->fcur], (float)c->cfg.rho0,
+  launch_populations_f64(c->cfg.q, c->cfg.storage, c->g, c->f[c->fcur], c->cfg.rho0,
                          (double*)c->scratch, c->stream);
   c->launches++;
   CK(cudaGetLastError());
@@ -1075,6 +1074,7 @@ RWMI_API rwmi_status rwmi_load(rwmi_ctx* c, const char* path) {
   }
   CK(copy_now(c, c->d_T, &c->t, sizeof(int64_t)));
   c->t_base = c->t;
+  CK(cudaMemsetAsync(c->wlist_n, 0, sizeof(unsigned int) * 2 * WLIST_STRIPES, c->stream));
   rwmi_status s = build_current_frame(c);
   if (s != RWMI_OK) return s;
   CK(cudaStreamSynchronize(c->stream));
@@ -1234,7 +1234,7 @@ RWMI_API void rwmi_destroy(rwmi_ctx* c) {
     dfree(c, c->pose[k]); dfree(c, c->sp[k]); dfree(c, c->cworld[k]); dfree(c, c->pos[k]); dfree(c, c->x0[k]);
   }
   dfree(c, c->wlist); dfree(c, c->wlist_n);
-  dfree(c, c->u[0]); dfree(c, c->u[1]); dfree(c, c->solid[0]); dfree(c, c->solid[1]); dfree(c, c->d_T); dfree(c, c->ticket); dfree(c, c->status); dfree(c, c->macc);
+  dfree(c, c->u[0]); dfree(c, c->u[1]); dfree(c, c->solid[0]); dfree(c, c->solid[1]); dfree(c, c->d_T); dfree(c, c->status); dfree(c, c->macc);
   dfree(c, c->series); dfree(c, c->mrow); dfree(c, c->desc); dfree(c, c->cbody); dfree(c, c->rank);
   dfree(c, c->counts); dfree(c, c->offsets); dfree(c, c->bsums); dfree(c, c->scratch); dfree(c, c->wmask[0]); dfree(c, c->wmask[1]);
   cudaStreamSynchronize(c->stream);   // the frees have returned the memory when this returns

@@ -34,6 +34,9 @@ __global__ void pose_bin_kernel(Geom g, ParticleSet ps, BrickSet bs, const int64
   const int64_t t = *d_T + t_offset;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     const double s = fper > 0.0 ? sin(2.0 * 3.141592653589793 * (double)t / fper) : 1.0;
+    bs.sp->Fd[0] = F0x * s;
+    bs.sp->Fd[1] = F0y * s;
+    bs.sp->Fd[2] = F0z * s;
     bs.sp->F[0] = (float)(F0x * s);
     bs.sp->F[1] = (float)(F0y * s);
     bs.sp->F[2] = (float)(F0z * s);
@@ -84,6 +87,14 @@ __global__ void pose_bin_kernel(Geom g, ParticleSet ps, BrickSet bs, const int64
       pf.pad[a] = 0.0f;
     }
     bs.pose[p] = pf;
+    PoseD pd;
+    for (int a = 0; a < 3; ++a) {
+      pd.o[a] = wrap_d(org[a], (double)g.n[a], g.wall[a]);
+      pd.v[a] = vel[a];
+      pd.w[a] = d.omega[a];
+    }
+    pd.pad = 0.0;
+    bs.posed[p] = pd;
   }
   __syncthreads();
   for (int i = d.c0 + threadIdx.x; i < d.c1; i += blockDim.x) {
@@ -507,25 +518,29 @@ void launch_raster(const Geom& g, const ParticleSet& ps, BrickSet bs, uint16_t* 
 // Initial state, checkpoint load and read-back helpers
 // ------------------------------------------------------------------------------------------
 template <int Q, int STORE>
-__global__ void init_pop_kernel(Geom g, void* f_, float rho0, float ux, float uy, float uz, float* u) {
+__global__ void init_pop_kernel(Geom g, void* f_, double rho0_d, double ux_d, double uy_d, double uz_d,
+                                float* u) {
   using L = Lat<Q>;
   using S = Store<STORE>;
+  using R = typename S::R;
   typename S::T* f = (typename S::T*)f_;
   const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= g.ncell) return;
-  const float uu = ux * ux + uy * uy + uz * uz;
+  const R rho0 = (R)rho0_d, ux = (R)ux_d, uy = (R)uy_d, uz = (R)uz_d;
+  const R uu = ux * ux + uy * uy + uz * uz;
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
-    const float eu = L::e(i, 0) * ux + L::e(i, 1) * uy + L::e(i, 2) * uz;
-    const float dev = 3.0f * eu + 4.5f * eu * eu - 1.5f * uu;
-    const float v = S::shifted ? L::w(i) * rho0 * dev : L::w(i) * rho0 * (1.0f + dev);
+    const R eu = L::e(i, 0) * ux + L::e(i, 1) * uy + L::e(i, 2) * uz;
+    const R dev = R(3) * eu + R(4.5) * eu * eu - R(1.5) * uu;
+    const R w = L::template wt<R>(i);
+    const R v = S::shifted ? w * rho0 * dev : w * rho0 * (R(1) + dev);
     S::st(f + (size_t)i * g.ncell_pad + c, v);
   }
-  reinterpret_cast<float4*>(u)[c] = make_float4(ux, uy, uz, rho0);
+  reinterpret_cast<float4*>(u)[c] = make_float4((float)ux, (float)uy, (float)uz, (float)rho0);
 }
 
 template <int Q, int STORE>
-__global__ void pop_f64_kernel(Geom g, const void* f_, float rho0, double* out) {
+__global__ void pop_f64_kernel(Geom g, const void* f_, double rho0, double* out) {
   using L = Lat<Q>;
   using S = Store<STORE>;
   const typename S::T* f = (const typename S::T*)f_;
@@ -534,35 +549,36 @@ __global__ void pop_f64_kernel(Geom g, const void* f_, float rho0, double* out) 
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     const double v = (double)S::ld(f + (size_t)i * g.ncell_pad + c);
-    out[(size_t)i * g.ncell + c] = S::shifted ? v + (double)L::w(i) * (double)rho0 : v;
+    out[(size_t)i * g.ncell + c] = S::shifted ? v + L::template wt<double>(i) * rho0 : v;
   }
 }
 
 template <int Q, int STORE>
-__global__ void load_pop_kernel(Geom g, const double* in, float rho0, void* f_) {
+__global__ void load_pop_kernel(Geom g, const double* in, double rho0, void* f_) {
   using L = Lat<Q>;
   using S = Store<STORE>;
+  using R = typename S::R;
   typename S::T* f = (typename S::T*)f_;
   const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= g.ncell) return;
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     const double v = in[(size_t)i * g.ncell + c];
-    S::st(f + (size_t)i * g.ncell_pad + c,
-          (float)(S::shifted ? v - (double)L::w(i) * (double)rho0 : v));
+    S::st(f + (size_t)i * g.ncell_pad + c, (R)(S::shifted ? v - L::template wt<double>(i) * rho0 : v));
   }
 }
 
 template <int Q, int STORE>
-__global__ void density_kernel(Geom g, const void* f_, float rho0, float* out) {
+__global__ void density_kernel(Geom g, const void* f_, double rho0, float* out) {
   using S = Store<STORE>;
+  using R = typename S::R;
   const typename S::T* f = (const typename S::T*)f_;
   const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= g.ncell) return;
-  float s = 0.0f;
+  R s = R(0);
 #pragma unroll
   for (int i = 0; i < Q; ++i) s += S::ld(f + (size_t)i * g.ncell_pad + c);
-  out[c] = S::shifted ? rho0 + s : s;
+  out[c] = (float)(S::shifted ? (R)rho0 + s : s);
 }
 
 #define RWMI_DISPATCH(q, storage, KERNEL, ...)                                   \
@@ -571,27 +587,29 @@ __global__ void density_kernel(Geom g, const void* f_, float rho0, float* out) {
     if ((q) == 15) {                                                             \
       if ((storage) == 0) KERNEL<15, 0><<<grid_, 256, 0, st>>>(__VA_ARGS__);     \
       else if ((storage) == 1) KERNEL<15, 1><<<grid_, 256, 0, st>>>(__VA_ARGS__);\
-      else KERNEL<15, 2><<<grid_, 256, 0, st>>>(__VA_ARGS__);                    \
+      else if ((storage) == 2) KERNEL<15, 2><<<grid_, 256, 0, st>>>(__VA_ARGS__);\
+      else KERNEL<15, 3><<<grid_, 256, 0, st>>>(__VA_ARGS__);                    \
     } else {                                                                     \
       if ((storage) == 0) KERNEL<19, 0><<<grid_, 256, 0, st>>>(__VA_ARGS__);     \
       else if ((storage) == 1) KERNEL<19, 1><<<grid_, 256, 0, st>>>(__VA_ARGS__);\
-      else KERNEL<19, 2><<<grid_, 256, 0, st>>>(__VA_ARGS__);                    \
+      else if ((storage) == 2) KERNEL<19, 2><<<grid_, 256, 0, st>>>(__VA_ARGS__);\
+      else KERNEL<19, 3><<<grid_, 256, 0, st>>>(__VA_ARGS__);                    \
     }                                                                            \
   } while (0)
 
-void launch_init_populations(int q, int storage, const Geom& g, void* f, float rho0,
-                             const float u0[3], float* u, cudaStream_t st) {
+void launch_init_populations(int q, int storage, const Geom& g, void* f, double rho0,
+                             const double u0[3], float* u, cudaStream_t st) {
   RWMI_DISPATCH(q, storage, init_pop_kernel, g, f, rho0, u0[0], u0[1], u0[2], u);
 }
-void launch_populations_f64(int q, int storage, const Geom& g, const void* f, float rho0,
+void launch_populations_f64(int q, int storage, const Geom& g, const void* f, double rho0,
                             double* out, cudaStream_t st) {
   RWMI_DISPATCH(q, storage, pop_f64_kernel, g, f, rho0, out);
 }
-void launch_load_populations(int q, int storage, const Geom& g, const double* in, float rho0,
+void launch_load_populations(int q, int storage, const Geom& g, const double* in, double rho0,
                              void* f, cudaStream_t st) {
   RWMI_DISPATCH(q, storage, load_pop_kernel, g, in, rho0, f);
 }
-void launch_density(int q, int storage, const Geom& g, const void* f, float rho0, float* out,
+void launch_density(int q, int storage, const Geom& g, const void* f, double rho0, float* out,
                     cudaStream_t st) {
   RWMI_DISPATCH(q, storage, density_kernel, g, f, rho0, out);
 }

@@ -51,10 +51,16 @@ struct PoseF {     // particle state at one time: wrapped origin, velocity, spin
   float o[3], v[3], w[3];
   float pad[3];
 };
+struct PoseD {     // the same in binary64 (read by the binary64 LBM)
+  double o[3], v[3], w[3];
+  double pad;
+};
 
 struct StepParams {  // per time parity
-  float F[3];      // body force density at that time
+  float F[3];      // body force density at that time (binary32)
   float pad;
+  double Fd[3];    // the same in binary64 (for the binary64 LBM)
+  double padd;
 };
 
 // Geometry shared by all kernels (passed by value).
@@ -192,6 +198,7 @@ struct BrickSet {
   uint16_t* bcand;    // [nbrick * MAXC]
   int32_t* rlist;     // [nbrick]
   PoseF* pose;        // [P]
+  PoseD* posed;       // [P], stored after pose
   float4* cworld;     // [Nc]
   StepParams* sp;     // [1]
 };
@@ -209,17 +216,27 @@ void launch_pose_bin(const Geom& g, const ParticleSet& ps, BrickSet bs, const in
 void launch_raster(const Geom& g, const ParticleSet& ps, BrickSet bs, uint16_t* solid,
                    unsigned long long* status, int nsm, cudaStream_t st);
 void launch_lbm(int q, int storage, bool reduce, const Geom& g, const void* fin, void* fout,
-                float* u, const uint16_t* solid, BrickSet bs, float tau, float rho0,
+                float* u, const uint16_t* solid, BrickSet bs, double tau, double rho0,
                 double* red, double* forces, unsigned long long* status, cudaStream_t st,
                 int block = 256);
-void launch_init_populations(int q, int storage, const Geom& g, void* f, float rho0,
-                             const float u0[3], float* u, cudaStream_t st);
+void launch_init_populations(int q, int storage, const Geom& g, void* f, double rho0,
+                             const double u0[3], float* u, cudaStream_t st);
 // Time of a launch: *d_T (the step counter at the start of the current run of steps, advanced
 // only between runs) plus toff, fixed when the launch is queued or captured. Kernels of several
 // steps may then run concurrently without racing on the counter.
+// The flagged-walker list of the two-pass walker step is split into WLIST_STRIPES parts, each
+// with its own append counter (block b appends to part b mod WLIST_STRIPES), so the appends do
+// not serialise on one address. Capacity per part: wlist_stripe_cap(n) walkers.
+constexpr int WLIST_STRIPES = 32;
+inline int64_t wlist_stripe_cap(int64_t n) {
+  const int64_t blocks = (n + 255) / 256;
+  return (blocks + WLIST_STRIPES - 1) / WLIST_STRIPES * 256;
+}
+// list_n: 2 * WLIST_STRIPES counters, one set per time parity (toff_parity = t mod 2); both
+// sets must be zero before the first step.
 void launch_walkers(const Geom& g, const ParticleSet& ps, BrickSet bs1, float4* pos, int64_t n,
-                    const float* u, const int64_t* d_T, int toff, float D, uint32_t k0, uint32_t k1,
-                    unsigned long long* status, unsigned int* ticket, float4* list,
+                    const float* u, const int64_t* d_T, int toff, int toff_parity, float D,
+                    uint32_t k0, uint32_t k1, unsigned long long* status, float4* list,
                     unsigned int* list_n, int nsm, cudaStream_t st);
 void launch_advance(int64_t* d_T, int64_t k, cudaStream_t st);
 void launch_seed(const Geom& g, const ParticleSet& ps, BrickSet bs, float4* pos, float4* x0,
@@ -237,12 +254,12 @@ void launch_moments(const float4* pos, const float4* x0, int64_t n, double* acc,
                     int interval, int rows, const int64_t* d_T, int toff, cudaStream_t st);
 void launch_unpack_solid(const Geom& g, const uint16_t* solid, const uint32_t* bword,
                          int32_t* count, int32_t* owner, cudaStream_t st);
-void launch_populations_f64(int q, int storage, const Geom& g, const void* f, float rho0,
+void launch_populations_f64(int q, int storage, const Geom& g, const void* f, double rho0,
                             double* out, cudaStream_t st);
 void launch_velocity_aos(const Geom& g, const float* u, float* out, cudaStream_t st);
-void launch_density(int q, int storage, const Geom& g, const void* f, float rho0, float* out,
+void launch_density(int q, int storage, const Geom& g, const void* f, double rho0, float* out,
                     cudaStream_t st);
-void launch_load_populations(int q, int storage, const Geom& g, const double* in, float rho0,
+void launch_load_populations(int q, int storage, const Geom& g, const double* in, double rho0,
                              void* f, cudaStream_t st);
 void launch_scatter_pos(const Geom& g, const float4* pos, int64_t n, const uint32_t* offsets,
                         const uint32_t* rank, float4* pos_out, cudaStream_t st);

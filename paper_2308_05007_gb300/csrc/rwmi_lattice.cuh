@@ -33,34 +33,45 @@ template <int Q> struct Lat {
   __host__ __device__ static constexpr int e2(int i) {
     return e(i, 0) * e(i, 0) + e(i, 1) * e(i, 1) + e(i, 2) * e(i, 2);
   }
-  __host__ __device__ static constexpr float w(int i) {
-    return Q == 15 ? (e2(i) == 0 ? 2.0f / 9.0f : e2(i) == 1 ? 1.0f / 9.0f : 1.0f / 72.0f)
-                   : (e2(i) == 0 ? 1.0f / 3.0f : e2(i) == 1 ? 1.0f / 18.0f : 1.0f / 36.0f);
-  }
   __host__ __device__ static constexpr int opp(int i) { return i == 0 ? 0 : (i <= H ? i + H : i - H); }
+  // weight in the arithmetic type R (each a correctly rounded constant)
+  template <typename R> __host__ __device__ static constexpr R wt(int i) {
+    return Q == 15 ? (e2(i) == 0 ? R(2) / R(9) : e2(i) == 1 ? R(1) / R(9) : R(1) / R(72))
+                   : (e2(i) == 0 ? R(1) / R(3) : e2(i) == 1 ? R(1) / R(18) : R(1) / R(36));
+  }
 };
 
 
-// Population storage: binary32 f_i, binary32 f_i - w_i rho0 ("shifted") or binary16 shifted;
-// arithmetic is binary32 in every case.
+// Population storage: binary32 f_i, binary32 f_i - w_i rho0 ("shifted"), binary16 shifted (all
+// with binary32 arithmetic), or binary64 shifted with binary64 arithmetic.
 template <int STORE> struct Store;
-template <> struct Store<0> {
+template <> struct Store<0> {   // binary32 f_i
   using T = float;
+  using R = float;              // arithmetic type of the LBM update
   static constexpr bool shifted = false;
-  __device__ static float ld(const T* p) { return *p; }
-  __device__ static void st(T* p, float v) { *p = v; }
+  __device__ static R ld(const T* p) { return *p; }
+  __device__ static void st(T* p, R v) { *p = v; }
 };
-template <> struct Store<1> {
+template <> struct Store<1> {   // binary32 f_i - w_i rho0
   using T = float;
+  using R = float;
   static constexpr bool shifted = true;
-  __device__ static float ld(const T* p) { return *p; }
-  __device__ static void st(T* p, float v) { *p = v; }
+  __device__ static R ld(const T* p) { return *p; }
+  __device__ static void st(T* p, R v) { *p = v; }
 };
-template <> struct Store<2> {
+template <> struct Store<2> {   // binary16 f_i - w_i rho0, binary32 arithmetic
   using T = __half;
+  using R = float;
   static constexpr bool shifted = true;
-  __device__ static float ld(const T* p) { return __half2float(*p); }
-  __device__ static void st(T* p, float v) { *p = __float2half_rn(v); }
+  __device__ static R ld(const T* p) { return __half2float(*p); }
+  __device__ static void st(T* p, R v) { *p = __float2half_rn(v); }
+};
+template <> struct Store<3> {   // binary64 f_i - w_i rho0, binary64 arithmetic (reference run)
+  using T = double;
+  using R = double;
+  static constexpr bool shifted = true;
+  __device__ static R ld(const T* p) { return *p; }
+  __device__ static void st(T* p, R v) { *p = v; }
 };
 
 }  // namespace rwmi

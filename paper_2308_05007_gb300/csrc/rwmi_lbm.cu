@@ -18,17 +18,33 @@ template <int Q, typename T> struct Planes {
   T* out[Q];
 };
 
+// Pose of particle p in the arithmetic type: the binary64 copy for the binary64 update.
+template <typename R>
+__device__ __forceinline__ void load_pose(const PoseF* pose, const PoseD* posed, int p, R* o, R* v, R* w) {
+  if (sizeof(R) == 8) {
+    const PoseD& q = posed[p];
+    for (int a = 0; a < 3; ++a) { o[a] = (R)q.o[a]; v[a] = (R)q.v[a]; w[a] = (R)q.w[a]; }
+  } else {
+    const PoseF q = pose[p];
+    for (int a = 0; a < 3; ++a) { o[a] = (R)q.o[a]; v[a] = (R)q.v[a]; w[a] = (R)q.w[a]; }
+  }
+}
+
 template <int Q, int STORE, bool WALLS, bool REDUCE>
-__global__ void __launch_bounds__(256, 4) lbm_kernel(Geom g, Planes<Q, typename Store<STORE>::T> pl,
+__global__ void __launch_bounds__(256, sizeof(typename Store<STORE>::R) == 8 ? 2 : 4)
+lbm_kernel(Geom g, Planes<Q, typename Store<STORE>::T> pl,
                                                   float4* __restrict__ u4,
                                                   const uint16_t* __restrict__ solid,
                                                   const uint32_t* __restrict__ bword,
                                                   const PoseF* __restrict__ pose,
-                                                  const StepParams* __restrict__ sp, float tau,
-                                                  float rho0, double* __restrict__ red,
+                                                  const PoseD* __restrict__ posed,
+                                                  const StepParams* __restrict__ sp, double tau_d,
+                                                  double rho0_d, double* __restrict__ red,
                                                   double* __restrict__ forces) {
   using L = Lat<Q>;
   using S = Store<STORE>;
+  using R = typename S::R;   // arithmetic type: binary32, or binary64 for the binary64 storage
+  const R tau = (R)tau_d, rho0 = (R)rho0_d;
   const uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x;
   const bool valid = idx < g.ncell;
   const int c = (int)(valid ? idx : g.ncell - 1);   // tail lanes recompute the last cell, store nothing
@@ -42,7 +58,7 @@ __global__ void __launch_bounds__(256, 4) lbm_kernel(Geom g, Planes<Q, typename 
   const int ox_p = x == 0 ? nx - 1 : -1, ox_m = (int)x == nx - 1 ? -(nx - 1) : 1;
   const int oy_p = y == 0 ? (ny - 1) * sy : -sy, oy_m = (int)y == ny - 1 ? -(ny - 1) * sy : sy;
   const int oz_p = z == 0 ? (nz - 1) * sz : -sz, oz_m = (int)z == nz - 1 ? -(nz - 1) * sz : sz;
-  float f[Q];
+  R f[Q];
   bool wall_cell = false;
   if (WALLS)
     wall_cell = (g.wall[0] && (x == 0 || (int)x == nx - 1)) || (g.wall[1] && (y == 0 || (int)y == ny - 1)) ||
@@ -70,7 +86,7 @@ __global__ void __launch_bounds__(256, 4) lbm_kernel(Geom g, Planes<Q, typename 
     }
   }
   // moments (Eqs. 14-15); with shifted storage f holds f_i - w_i rho0
-  float drho = 0.0f, jx = 0.0f, jy = 0.0f, jz = 0.0f;
+  R drho = R(0.0), jx = R(0.0), jy = R(0.0), jz = R(0.0);
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     drho += f[i];
@@ -78,14 +94,16 @@ __global__ void __launch_bounds__(256, 4) lbm_kernel(Geom g, Planes<Q, typename 
     if (L::e(i, 1)) jy += L::e(i, 1) * f[i];
     if (L::e(i, 2)) jz += L::e(i, 2) * f[i];
   }
-  const float rho = S::shifted ? rho0 + drho : drho;
-  const float Fx = sp->F[0], Fy = sp->F[1], Fz = sp->F[2];
-  const float inv_rho = 1.0f / rho;
-  const float ux = (jx + 0.5f * Fx) * inv_rho, uy = (jy + 0.5f * Fy) * inv_rho,
-              uz = (jz + 0.5f * Fz) * inv_rho;
-  const float uu = ux * ux + uy * uy + uz * uz;
+  const R rho = S::shifted ? rho0 + drho : drho;
+  const R Fx = sizeof(R) == 8 ? (R)sp->Fd[0] : (R)sp->F[0];
+  const R Fy = sizeof(R) == 8 ? (R)sp->Fd[1] : (R)sp->F[1];
+  const R Fz = sizeof(R) == 8 ? (R)sp->Fd[2] : (R)sp->F[2];
+  const R inv_rho = R(1.0) / rho;
+  const R ux = (jx + R(0.5) * Fx) * inv_rho, uy = (jy + R(0.5) * Fy) * inv_rho,
+              uz = (jz + R(0.5) * Fz) * inv_rho;
+  const R uu = ux * ux + uy * uy + uz * uz;
   // partially saturated cell: solid word valid only in bricks flagged for this time
-  float B = 0.0f, usx = 0.0f, usy = 0.0f, usz = 0.0f;
+  R B = R(0.0), usx = R(0.0), usy = R(0.0), usz = R(0.0);
   int owner = -1;
   {
     const uint32_t b = ((z >> 3) * (uint32_t)g.nb[1] + (y >> 3)) * (uint32_t)g.nb[0] + (x >> 3);
@@ -94,81 +112,83 @@ __global__ void __launch_bounds__(256, 4) lbm_kernel(Geom g, Planes<Q, typename 
       const int cnt = sw & 0x7f;
       if (cnt && valid) {
         owner = sw >> 7;
-        const float eps = (float)cnt * (1.0f / 64.0f);
-        B = eps * (tau - 0.5f) / ((1.0f - eps) + (tau - 0.5f));
-        const PoseF ps_ = pose[owner];
-        float r[3] = {(float)x + 0.5f - ps_.o[0], (float)y + 0.5f - ps_.o[1], (float)z + 0.5f - ps_.o[2]};
+        const R eps = (R)cnt * (R(1.0) / R(64.0));
+        B = eps * (tau - R(0.5)) / ((R(1.0) - eps) + (tau - R(0.5)));
+        R po[3], pv[3], pw[3];
+        load_pose<R>(pose, posed, owner, po, pv, pw);
+        R r[3] = {(R)x + R(0.5) - po[0], (R)y + R(0.5) - po[1], (R)z + R(0.5) - po[2]};
         for (int a = 0; a < 3; ++a)
           if (!g.wall[a]) {
-            const float na = (float)g.n[a];
-            if (r[a] > 0.5f * na) r[a] -= na; else if (r[a] < -0.5f * na) r[a] += na;
+            const R na = (R)g.n[a];
+            if (r[a] > R(0.5) * na) r[a] -= na; else if (r[a] < -R(0.5) * na) r[a] += na;
           }
-        usx = ps_.v[0] + ps_.w[1] * r[2] - ps_.w[2] * r[1];
-        usy = ps_.v[1] + ps_.w[2] * r[0] - ps_.w[0] * r[2];
-        usz = ps_.v[2] + ps_.w[0] * r[1] - ps_.w[1] * r[0];
+        usx = pv[0] + pw[1] * r[2] - pw[2] * r[1];
+        usy = pv[1] + pw[2] * r[0] - pw[0] * r[2];
+        usz = pv[2] + pw[0] * r[1] - pw[1] * r[0];
       }
     }
   }
-  const float omB = 1.0f - B;
-  const float rtau = omB / tau;              // (1 - B) / tau
-  const float guo = omB * (1.0f - 0.5f / tau);
-  const float uF = ux * Fx + uy * Fy + uz * Fz;
-  const float usus = usx * usx + usy * usy + usz * usz;
-  float dpx = 0.0f, dpy = 0.0f, dpz = 0.0f;
-  float out[Q];
+  const R omB = R(1.0) - B;
+  const R rtau = omB / tau;              // (1 - B) / tau
+  const R guo = omB * (R(1.0) - R(0.5) / tau);
+  const R uF = ux * Fx + uy * Fy + uz * Fz;
+  const R usus = usx * usx + usy * usy + usz * usz;
+  R dpx = R(0.0), dpy = R(0.0), dpz = R(0.0);
+  R out[Q];
   {  // rest direction; its own opposite: Omega_0 = feq_0(rho, u_s) - feq_0(rho, u)
-    const float w = L::w(0);
-    const float dev = -1.5f * uu;
-    const float feq_s = S::shifted ? w * (drho + rho * dev) : w * rho * (1.0f + dev);
-    const float om0 = B > 0.0f ? 1.5f * w * rho * (uu - usus) : 0.0f;
-    out[0] = f[0] - rtau * (f[0] - feq_s) + guo * w * (-3.0f * uF) + B * om0;
+    const R w = L::template wt<R>(0);
+    const R dev = -R(1.5) * uu;
+    const R feq_s = S::shifted ? w * (drho + rho * dev) : w * rho * (R(1.0) + dev);
+    const R om0 = B > R(0.0) ? R(1.5) * w * rho * (uu - usus) : R(0.0);
+    out[0] = f[0] - rtau * (f[0] - feq_s) + guo * w * (-R(3.0) * uF) + B * om0;
   }
   // opposite pairs (i, i + H) share e.u
 #pragma unroll
   for (int i = 1; i <= L::H; ++i) {
     const int io = i + L::H;
     const int ex = L::e(i, 0), ey = L::e(i, 1), ez = L::e(i, 2);
-    const float w = L::w(i);
-    const float eu = ex * ux + ey * uy + ez * uz;
-    const float eF = ex * Fx + ey * Fy + ez * Fz;
-    const float sym = 4.5f * eu * eu - 1.5f * uu;        // even part of feq / (w rho)
-    const float base = S::shifted ? w * drho : w * rho;  // w rho (minus w rho0 when shifted)
-    const float wr = w * rho;
-    const float feq_p = base + wr * (3.0f * eu + sym);
-    const float feq_m = base + wr * (-3.0f * eu + sym);
-    const float gw = guo * w;
-    out[i] = f[i] - rtau * (f[i] - feq_p) + gw * (3.0f * (eF - uF) + 9.0f * eu * eF);
-    out[io] = f[io] - rtau * (f[io] - feq_m) + gw * (3.0f * (-eF - uF) + 9.0f * eu * eF);
-    if (B > 0.0f) {
-      const float eus = ex * usx + ey * usy + ez * usz;
-      const float common = wr * (4.5f * (eus * eus - eu * eu) - 1.5f * (usus - uu));
-      const float odd = wr * 3.0f * (eu + eus);
-      const float om_p = (f[io] - f[i]) + odd + common;   // Omega_i
-      const float om_m = (f[i] - f[io]) - odd + common;   // Omega_opp(i)
+    const R w = L::template wt<R>(i);
+    const R eu = ex * ux + ey * uy + ez * uz;
+    const R eF = ex * Fx + ey * Fy + ez * Fz;
+    const R sym = R(4.5) * eu * eu - R(1.5) * uu;        // even part of feq / (w rho)
+    const R base = S::shifted ? w * drho : w * rho;  // w rho (minus w rho0 when shifted)
+    const R wr = w * rho;
+    const R feq_p = base + wr * (R(3.0) * eu + sym);
+    const R feq_m = base + wr * (-R(3.0) * eu + sym);
+    const R gw = guo * w;
+    out[i] = f[i] - rtau * (f[i] - feq_p) + gw * (R(3.0) * (eF - uF) + R(9.0) * eu * eF);
+    out[io] = f[io] - rtau * (f[io] - feq_m) + gw * (R(3.0) * (-eF - uF) + R(9.0) * eu * eF);
+    if (B > R(0.0)) {
+      const R eus = ex * usx + ey * usy + ez * usz;
+      const R common = wr * (R(4.5) * (eus * eus - eu * eu) - R(1.5) * (usus - uu));
+      const R odd = wr * R(3.0) * (eu + eus);
+      const R om_p = (f[io] - f[i]) + odd + common;   // Omega_i
+      const R om_m = (f[i] - f[io]) - odd + common;   // Omega_opp(i)
       out[i] += B * om_p;
       out[io] += B * om_m;
-      const float dm = B * (om_p - om_m);                 // B (Omega_i e_i + Omega_opp e_opp) / e_i
+      const R dm = B * (om_p - om_m);                 // B (Omega_i e_i + Omega_opp e_opp) / e_i
       dpx += dm * ex; dpy += dm * ey; dpz += dm * ez;
     }
   }
   if (valid) {
 #pragma unroll
     for (int i = 0; i < Q; ++i) S::st(pl.out[i] + c, out[i]);
-    u4[c] = make_float4(ux, uy, uz, rho);
+    u4[c] = make_float4((float)ux, (float)uy, (float)uz, (float)rho);
   }
   // hydrodynamic force on the owner particle: -B sum_i Omega_i e_i; torque about its origin
   const unsigned full = 0xffffffffu;
   const bool hasF = owner >= 0;
   if (__any_sync(full, hasF)) {
-    float Fc[3] = {-dpx, -dpy, -dpz};
-    float Tc[3] = {0.0f, 0.0f, 0.0f};
+    R Fc[3] = {-dpx, -dpy, -dpz};
+    R Tc[3] = {R(0.0), R(0.0), R(0.0)};
     if (hasF) {
-      const PoseF ps_ = pose[owner];
-      float r[3] = {(float)x + 0.5f - ps_.o[0], (float)y + 0.5f - ps_.o[1], (float)z + 0.5f - ps_.o[2]};
+      R po[3], pv[3], pw[3];
+      load_pose<R>(pose, posed, owner, po, pv, pw);
+      R r[3] = {(R)x + R(0.5) - po[0], (R)y + R(0.5) - po[1], (R)z + R(0.5) - po[2]};
       for (int a = 0; a < 3; ++a)
         if (!g.wall[a]) {
-          const float na = (float)g.n[a];
-          if (r[a] > 0.5f * na) r[a] -= na; else if (r[a] < -0.5f * na) r[a] += na;
+          const R na = (R)g.n[a];
+          if (r[a] > R(0.5) * na) r[a] -= na; else if (r[a] < -R(0.5) * na) r[a] += na;
         }
       Tc[0] = r[1] * Fc[2] - r[2] * Fc[1];
       Tc[1] = r[2] * Fc[0] - r[0] * Fc[2];
@@ -178,10 +198,10 @@ __global__ void __launch_bounds__(256, 4) lbm_kernel(Geom g, Planes<Q, typename 
     const int first = __shfl_sync(full, key, __ffs(__ballot_sync(full, hasF)) - 1);
     const bool uniform = __all_sync(full, !hasF || key == first);
     if (uniform) {
-      float v[6] = {Fc[0], Fc[1], Fc[2], Tc[0], Tc[1], Tc[2]};
+      R v[6] = {Fc[0], Fc[1], Fc[2], Tc[0], Tc[1], Tc[2]};
 #pragma unroll
       for (int m = 0; m < 6; ++m) {
-        if (!hasF) v[m] = 0.0f;
+        if (!hasF) v[m] = R(0.0);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v[m] += __shfl_xor_sync(full, v[m], o);
       }
@@ -194,21 +214,22 @@ __global__ void __launch_bounds__(256, 4) lbm_kernel(Geom g, Planes<Q, typename 
       }
     }
   }
-  if (REDUCE) {   // sums of (rho - rho0) and sum_i f_i e_i (pre-collision): binary32 within the
-                  // block (256 small deviations), FP64 across blocks (GB300's FP64 pipe is narrow)
-    float v[4] = {valid ? (S::shifted ? drho : rho - rho0) : 0.0f, valid ? jx : 0.0f,
-                  valid ? jy : 0.0f, valid ? jz : 0.0f};
+  if (REDUCE) {   // sums of (rho - rho0) and sum_i f_i e_i (pre-collision): the arithmetic type
+                  // within the block (256 small deviations), FP64 across blocks (GB300's FP64
+                  // pipe is narrow)
+    R v[4] = {valid ? (S::shifted ? drho : rho - rho0) : R(0.0), valid ? jx : R(0.0),
+                  valid ? jy : R(0.0), valid ? jz : R(0.0)};
 #pragma unroll
     for (int m = 0; m < 4; ++m)
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) v[m] += __shfl_xor_sync(full, v[m], o);
-    __shared__ float s_red[8][4];
+    __shared__ R s_red[8][4];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (lane == 0)
       for (int m = 0; m < 4; ++m) s_red[wid][m] = v[m];
     __syncthreads();
     if (threadIdx.x < 4) {   // striped slots keep the FP64 atomics of 65536 blocks uncontended
-      float s = 0.0f;
+      R s = R(0.0);
       for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += s_red[w][threadIdx.x];
       atomicAdd(&red[4 * (blockIdx.x % RED_SLOTS) + threadIdx.x], (double)s);
     }
@@ -217,7 +238,7 @@ __global__ void __launch_bounds__(256, 4) lbm_kernel(Geom g, Planes<Q, typename 
 
 template <int Q, int STORE>
 static void launch_lbm_q(bool walls, bool reduce, const Geom& g, const void* fin, void* fout, float* u,
-                         const uint16_t* solid, BrickSet bs, float tau, float rho0, double* red,
+                         const uint16_t* solid, BrickSet bs, double tau, double rho0, double* red,
                          double* forces, cudaStream_t st, int bsz) {
   using T = typename Store<STORE>::T;
   Planes<Q, T> pl;
@@ -229,27 +250,29 @@ static void launch_lbm_q(bool walls, bool reduce, const Geom& g, const void* fin
   const int bsz_ok = (bsz == 64 || bsz == 128) ? bsz : 256;
   const dim3 grid((g.ncell + bsz_ok - 1) / bsz_ok), block(bsz_ok);
   if (walls) {
-    if (reduce) lbm_kernel<Q, STORE, true, true><<<grid, block, 0, st>>>(g, pl, u4, solid, bs.bword, bs.pose, bs.sp, tau, rho0, red, forces);
-    else lbm_kernel<Q, STORE, true, false><<<grid, block, 0, st>>>(g, pl, u4, solid, bs.bword, bs.pose, bs.sp, tau, rho0, red, forces);
+    if (reduce) lbm_kernel<Q, STORE, true, true><<<grid, block, 0, st>>>(g, pl, u4, solid, bs.bword, bs.pose, bs.posed, bs.sp, tau, rho0, red, forces);
+    else lbm_kernel<Q, STORE, true, false><<<grid, block, 0, st>>>(g, pl, u4, solid, bs.bword, bs.pose, bs.posed, bs.sp, tau, rho0, red, forces);
   } else {
-    if (reduce) lbm_kernel<Q, STORE, false, true><<<grid, block, 0, st>>>(g, pl, u4, solid, bs.bword, bs.pose, bs.sp, tau, rho0, red, forces);
-    else lbm_kernel<Q, STORE, false, false><<<grid, block, 0, st>>>(g, pl, u4, solid, bs.bword, bs.pose, bs.sp, tau, rho0, red, forces);
+    if (reduce) lbm_kernel<Q, STORE, false, true><<<grid, block, 0, st>>>(g, pl, u4, solid, bs.bword, bs.pose, bs.posed, bs.sp, tau, rho0, red, forces);
+    else lbm_kernel<Q, STORE, false, false><<<grid, block, 0, st>>>(g, pl, u4, solid, bs.bword, bs.pose, bs.posed, bs.sp, tau, rho0, red, forces);
   }
 }
 
 void launch_lbm(int q, int storage, bool reduce, const Geom& g, const void* fin, void* fout,
-                float* u, const uint16_t* solid, BrickSet bs, float tau, float rho0, double* red,
+                float* u, const uint16_t* solid, BrickSet bs, double tau, double rho0, double* red,
                 double* forces, unsigned long long* status, cudaStream_t st, int block) {
   (void)status;
   const bool walls = g.wall[0] || g.wall[1] || g.wall[2];
   if (q == 15) {
     if (storage == 0) launch_lbm_q<15, 0>(walls, reduce, g, fin, fout, u, solid, bs, tau, rho0, red, forces, st, block);
     else if (storage == 1) launch_lbm_q<15, 1>(walls, reduce, g, fin, fout, u, solid, bs, tau, rho0, red, forces, st, block);
-    else launch_lbm_q<15, 2>(walls, reduce, g, fin, fout, u, solid, bs, tau, rho0, red, forces, st, block);
+    else if (storage == 2) launch_lbm_q<15, 2>(walls, reduce, g, fin, fout, u, solid, bs, tau, rho0, red, forces, st, block);
+    else launch_lbm_q<15, 3>(walls, reduce, g, fin, fout, u, solid, bs, tau, rho0, red, forces, st, block);
   } else {
     if (storage == 0) launch_lbm_q<19, 0>(walls, reduce, g, fin, fout, u, solid, bs, tau, rho0, red, forces, st, block);
     else if (storage == 1) launch_lbm_q<19, 1>(walls, reduce, g, fin, fout, u, solid, bs, tau, rho0, red, forces, st, block);
-    else launch_lbm_q<19, 2>(walls, reduce, g, fin, fout, u, solid, bs, tau, rho0, red, forces, st, block);
+    else if (storage == 2) launch_lbm_q<19, 2>(walls, reduce, g, fin, fout, u, solid, bs, tau, rho0, red, forces, st, block);
+    else launch_lbm_q<19, 3>(walls, reduce, g, fin, fout, u, solid, bs, tau, rho0, red, forces, st, block);
   }
 }
 

@@ -253,7 +253,8 @@ __global__ void __launch_bounds__(256, 4) walker_kernel(WalkCtx c, float4* __res
                                                         const int64_t* __restrict__ d_T, int toff,
                                                         float amp, uint32_t k0, uint32_t k1,
                                                         unsigned long long* __restrict__ status,
-                                                        float4* __restrict__ list, unsigned int* list_n) {
+                                                        float4* __restrict__ list, unsigned int* list_n,
+                                                        int64_t cap) {
   const int64_t T = *d_T + toff;
   const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   bool ev_wall = false, ev_fast = false, ev_nonfinite = false, flagged = false;
@@ -304,16 +305,17 @@ __global__ void __launch_bounds__(256, 4) walker_kernel(WalkCtx c, float4* __res
   }
   const unsigned full = 0xffffffffu;
   const unsigned fl = __ballot_sync(full, flagged);
-  if (fl) {   // one list reservation per warp
+  if (fl) {   // one list reservation per warp, on this block's stripe of the list
     const int lane = threadIdx.x & 31;
     const int leader = __ffs(fl) - 1;
+    const int stripe = (int)(blockIdx.x % WLIST_STRIPES);
     unsigned base = 0;
-    if (lane == leader) base = atomicAdd(list_n, (unsigned)__popc(fl));
+    if (lane == leader) base = atomicAdd(&list_n[stripe], (unsigned)__popc(fl));
     base = __shfl_sync(full, base, leader);
     if (flagged) {
-      const unsigned slot = base + __popc(fl & ((1u << lane) - 1u));
-      list[2 * (size_t)slot] = ea;
-      list[2 * (size_t)slot + 1] = eb;
+      const size_t slot = (size_t)stripe * (size_t)cap + base + __popc(fl & ((1u << lane) - 1u));
+      list[2 * slot] = ea;
+      list[2 * slot + 1] = eb;
     }
   }
   if (__any_sync(full, ev_wall | ev_fast | ev_nonfinite)) {
@@ -327,22 +329,44 @@ __global__ void __launch_bounds__(256, 4) walker_kernel(WalkCtx c, float4* __res
   }
 }
 
-// Pass 2 (fixed grid, grid-stride over the list): types II-IV of the flagged walkers, written back
-// to their slots. The last warp to finish empties the list (every warp has read its length by
-// then).
+// Pass 2 (fixed grid, grid-stride over the list stripes taken as one sequence): types II-IV of
+// the flagged walkers, written back to their slots. Block 0 clears the other parity's counters,
+// which the next step's pass 1 appends to.
 __global__ void __launch_bounds__(256, 4) walker_resolve_kernel(WalkCtx c, float4* __restrict__ pos,
                                                              const float4* __restrict__ list,
-                                                             unsigned int* list_n, const int64_t* d_T,
+                                                             const unsigned int* list_n,
+                                                             unsigned int* list_n_next, const int64_t* d_T,
                                                              int toff, float amp, uint32_t k0, uint32_t k1,
                                                              unsigned long long* __restrict__ status,
-                                                             unsigned int* ticket) {
+                                                             int64_t cap) {
   const int64_t T = *d_T + toff;
-  const unsigned cnt = *list_n;
-  if (blockIdx.x == 0 && threadIdx.x == 0 && cnt) atomicAdd(&status[ST_RESOLVED], (unsigned long long)cnt);
+  // the stripes as one sequence: s_pre[k] = entries in stripes before k (first warp's scan)
+  __shared__ unsigned s_pre[WLIST_STRIPES + 1];
+  static_assert(WLIST_STRIPES == 32, "one lane per stripe");
+  if (threadIdx.x < 32) {
+    const unsigned v = list_n[threadIdx.x];
+    unsigned incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+      if ((int)threadIdx.x >= o) incl += y;
+    }
+    s_pre[threadIdx.x + 1] = incl;
+    if (threadIdx.x == 0) s_pre[0] = 0u;
+    if (blockIdx.x == 0) {
+      if (v) atomicAdd(&status[ST_RESOLVED], (unsigned long long)v);
+      list_n_next[threadIdx.x] = 0u;   // the next step's counters (nobody reads them now)
+    }
+  }
+  __syncthreads();
+  const unsigned total = s_pre[WLIST_STRIPES];
   unsigned ev_all[5] = {0u, 0u, 0u, 0u, 0u};
   const unsigned stride = gridDim.x * blockDim.x;
-  for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += stride) {
-    const float4 a = list[2 * (size_t)e], bq = list[2 * (size_t)e + 1];
+  for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += stride) {
+    int k = 0;
+    while (s_pre[k + 1] <= e) ++k;   // stripe of entry e (k < WLIST_STRIPES since e < total)
+    const size_t slot = (size_t)k * (size_t)cap + (e - s_pre[k]);
+    const float4 a = list[2 * slot], bq = list[2 * slot + 1];
     const float x[3] = {a.x, a.y, a.z}, xf[3] = {bq.x, bq.y, bq.z};
     const uint32_t id = __float_as_uint(a.w);
     const uint32_t w = __float_as_uint(bq.w);
@@ -391,25 +415,22 @@ __global__ void __launch_bounds__(256, 4) walker_resolve_kernel(WalkCtx c, float
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     if ((threadIdx.x & 31) == 0 && v) atomicAdd(&status[slot[m]], (unsigned long long)v);
   }
-  if ((threadIdx.x & 31) == 0) {
-    const unsigned int nwarps = gridDim.x * (blockDim.x >> 5);
-    const unsigned int done = atomicAdd(ticket, 1u);
-    if (done == nwarps - 1) {
-      *list_n = 0u;
-      *ticket = 0u;
-    }
-  }
 }
 
 void launch_walkers(const Geom& g, const ParticleSet& ps, BrickSet bs1, float4* pos, int64_t n,
-                    const float* u, const int64_t* d_T, int toff, float D, uint32_t k0, uint32_t k1,
-                    unsigned long long* status, unsigned int* ticket, float4* list,
+                    const float* u, const int64_t* d_T, int toff, int toff_parity, float D,
+                    uint32_t k0, uint32_t k1, unsigned long long* status, float4* list,
                     unsigned int* list_n, int nsm, cudaStream_t st) {
   WalkCtx c{g, ps, bs1};
   const int64_t blocks = (n + 255) / 256;
   const float amp = sqrtf(2.0f * D);
-  walker_kernel<<<(unsigned)blocks, 256, 0, st>>>(c, pos, n, u, d_T, toff, amp, k0, k1, status, list, list_n);
-  walker_resolve_kernel<<<nsm * 8, 256, 0, st>>>(c, pos, list, list_n, d_T, toff, amp, k0, k1, status, ticket);
+  const int64_t cap = wlist_stripe_cap(n);
+  // counters per time parity: this step appends to list_n[par], the resolve pass clears the other
+  // set for the next step (no memset launch, no completion ticket)
+  unsigned int* cur = list_n + WLIST_STRIPES * (toff_parity & 1);
+  unsigned int* nxt = list_n + WLIST_STRIPES * ((toff_parity + 1) & 1);
+  walker_kernel<<<(unsigned)blocks, 256, 0, st>>>(c, pos, n, u, d_T, toff, amp, k0, k1, status, list, cur, cap);
+  walker_resolve_kernel<<<nsm * 8, 256, 0, st>>>(c, pos, list, cur, nxt, d_T, toff, amp, k0, k1, status, cap);
 }
 
 __global__ void advance_kernel(int64_t* d_T, int64_t k) { *d_T += k; }

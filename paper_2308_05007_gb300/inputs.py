@@ -70,7 +70,7 @@ class Workload:
     walker_box: Optional[tuple] = None   # ((lo3), (hi3)) for uniform seeding in the fluid
     walker_positions: Optional[np.ndarray] = None  # explicit float32 [N, 3] start positions
     steps: int = 1
-    storage: int = 1                     # 0 FP32, 1 FP32 shifted by w_i rho0, 2 FP16 shifted
+    storage: int = 1                     # 0 FP32, 1 FP32 shifted by w_i rho0, 2 FP16 shifted, 3 FP64 shifted
     sort_interval: int = 0
     moment_interval: int = 0
     notes: str = ""

@@ -18,7 +18,7 @@ from . import build as _build
 RWMI_OK, RWMI_W_BISECT, RWMI_W_SEED, RWMI_BUSY = 0, 1, 2, 3
 STATUS_NAMES = {0: "RWMI_OK", 1: "RWMI_W_BISECT", 2: "RWMI_W_SEED", 3: "RWMI_BUSY", -1: "RWMI_E_INVALID", -2: "RWMI_E_OOM",
                 -3: "RWMI_E_CUDA", -4: "RWMI_E_NONFINITE", -5: "RWMI_E_TIMEOUT", -6: "RWMI_E_STATE"}
-STORE_FP32, STORE_FP32_SHIFT, STORE_FP16_SHIFT = 0, 1, 2
+STORE_FP32, STORE_FP32_SHIFT, STORE_FP16_SHIFT, STORE_FP64_SHIFT = 0, 1, 2, 3
 
 EXPORTED = ["rwmi_config_defaults", "rwmi_create", "rwmi_configure", "rwmi_set_stream",
             "rwmi_set_metaballs", "rwmi_seed_walkers", "rwmi_set_walkers", "rwmi_step", "rwmi_step_timed",

@@ -367,9 +367,34 @@ def test_one_lbm_step_fp16_shifted_storage(q):
     assert np.all(np.abs(f_next - fo) <= 2.0 ** -11 * dev + 1e-6 * np.abs(fo).max())
 
 
+@pytest.mark.parametrize("q", [15, 19])
+def test_one_lbm_step_fp64_storage(q):
+    """Binary64 storage and arithmetic (the FP64-on-GPU run), with moving, spinning particles
+    and walls: from identical populations one step matches the FP64 oracle to the rounding of a
+    few dozen binary64 operations per population, |df| <= 1e-13 max|f|."""
+    w = I.ragged(q=q, storage=3, walls=4, seed=9)
+    sim = Sim().from_workload(w, seed_walkers=False)
+    ora = Oracle.from_workload(w, seed_walkers=False)
+    perm = _perm(sim, q)
+    sim.step(6)
+    f_prev = sim.populations()[perm]
+    t = sim.t
+    sim.step(1)
+    f_next = sim.populations()[perm]
+    ora.set_populations(f_prev)
+    ora.set_time(t)
+    fo, uo, _ = ora.lbm_cells(np.arange(ora.n_cells))
+    err = np.abs(f_next - fo)
+    if err.max() > 1e-13 * np.abs(fo).max():
+        d, cell = np.unravel_index(np.argmax(err), err.shape)
+        pytest.fail(f"binary64 step differs from the oracle by {err.max():.3e} "
+                    f"(direction {d}, cell {cell}; median {np.median(err):.3e})")
+
+
 def test_precision_storages_against_the_oracle():
     """The precision case at 96^3 (parity physics, 4 static particles, 2e4 walkers, 60 steps):
-    velocity field and dispersion-coefficient error of each storage against the FP64 oracle.
+    velocity field, population and dispersion-coefficient error of each storage (binary32,
+    binary32 shifted, binary16 shifted, binary64 shifted) against the FP64 oracle.
     Bounds: shifted binary32 keeps the 1e-5 relative bound; for the others the worst-case
     accumulation of one storage rounding per population per step, n Q eps max|stored value|
     (binary32 unshifted: eps = 2^-24 of max|f|; binary16 shifted: eps = 2^-11 of
@@ -386,20 +411,26 @@ def test_precision_storages_against_the_oracle():
     _, wts = lattice(w.q)
     d_ora = (mo_series[-1][4:7] - mo_series[1][4:7]) / (2 * 40)
     errs = {}
-    for storage in (1, 0, 2):
+    for storage in (1, 0, 2, 3):
         sim = Sim().from_workload(I.with_(w, storage=storage))
         sim.step(w.steps)
         ser = sim.moment_series()
         assert len(ser) == 6
         d_gpu = (ser[-1, 5:8] - ser[1, 5:8]) / (2 * 40)
         ug = sim.velocity().astype(np.float64)
+        fg = sim.populations()[_perm(sim, w.q)]
         errs[storage] = {"rel_l2_u": _rel(ug, uo), "max_abs_u": float(np.abs(ug - uo).max()),
+                         "rel_l2_f": _rel(fg, fo),
                          "rel_D": float(np.abs(d_gpu - d_ora).max() / np.abs(d_ora).max())}
         sim.close()
-    print("precision errors by storage (0 fp32, 1 fp32-shift, 2 fp16-shift):", errs)
+    print("precision errors by storage (0 fp32, 1 fp32-shift, 2 fp16-shift, 3 fp64-shift):", errs)
     n, q = w.steps, w.q
     assert errs[1]["rel_l2_u"] <= 1e-5
     assert errs[0]["max_abs_u"] <= n * q * 2.0 ** -24 * np.abs(fo).max()
     assert errs[2]["max_abs_u"] <= n * q * 2.0 ** -11 * np.abs(fo - wts[:, None] * w.rho0).max()
-    for st in (0, 1, 2):   # walker branch flips and the velocity error both stay small
+    # binary64: populations to accumulated binary64 rounding; the velocity handed out (and to the
+    # walkers) is binary32, so u carries one binary32 rounding per component
+    assert errs[3]["rel_l2_f"] <= 1e-12
+    assert errs[3]["rel_l2_u"] <= 2.0 ** -23
+    for st in (0, 1, 2, 3):   # walker branch flips and the velocity error both stay small
         assert errs[st]["rel_D"] <= 1e-2, (st, errs[st])
