@@ -291,12 +291,12 @@ rwmi_status alloc_walkers(rwmi_ctx* c, int64_t n) {
 
 // Counting sort of the walkers by cell; the histogram is the concentration of Eq. 16.
 void enqueue_sort(rwmi_ctx* c, cudaStream_t st) {
-  cudaMemsetAsync(c->counts, 0, sizeof(uint32_t) * (size_t)c->ncell, st);
+  launch_clear_u32(c->counts, (uint32_t)c->ncell, st);
   launch_histogram(c->g, c->pos[c->pcur], c->nw, c->counts, c->rank, st);
   launch_scan(c->counts, c->offsets, c->bsums, (uint32_t)c->ncell, st);
   launch_scatter(c->g, c->pos[c->pcur], c->x0[c->pcur], c->nw, c->offsets, c->rank,
                  c->pos[c->pcur ^ 1], c->x0[c->pcur ^ 1], st);
-  c->launches += 5;
+  c->launches += 6;
   c->pcur ^= 1;
 }
 
@@ -332,7 +332,8 @@ void enqueue_step(rwmi_ctx* c, bool reduce) {
   if (ws != c->stream && c->walk_rec[tp]) cudaStreamWaitEvent(c->stream, c->walk_ev[tp], 0);
   auto pose = [&]() {   // particles, bricks and body force of t+1
     phase_begin(c, RWMI_PHASE_POSE);
-    cudaMemsetAsync(c->bword[tn], 0, sizeof(uint32_t) * (c->nbrick + 1), c->stream);
+    launch_clear_u32(c->bword[tn], c->nbrick + 1, c->stream);
+    c->launches++;
     launch_pose_bin(c->g, ps, brick_set(c, tn), c->d_T, toff + 1, c->cfg.body_force, c->cfg.force_period, 1,
                     c->acc[tn], c->stream);
     c->launches++;

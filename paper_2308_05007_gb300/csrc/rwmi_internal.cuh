@@ -210,6 +210,7 @@ struct ParticleSet {
   float walk_margin;          // candidate margin for walkers, cells
 };
 
+void launch_clear_u32(uint32_t* p, uint32_t n, cudaStream_t st);
 void launch_pose_bin(const Geom& g, const ParticleSet& ps, BrickSet bs, const int64_t* d_T,
                      int t_offset, const double F0[3], double force_period, int zero_forces,
                      double* forces, cudaStream_t st);
