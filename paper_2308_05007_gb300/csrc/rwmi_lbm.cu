@@ -175,10 +175,12 @@ lbm_kernel(Geom g, Planes<Q, typename Store<STORE>::T> pl,
     for (int i = 0; i < Q; ++i) S::st(pl.out[i] + c, out[i]);
     u4[c] = make_float4((float)ux, (float)uy, (float)uz, (float)rho);
   }
-  // hydrodynamic force on the owner particle: -B sum_i Omega_i e_i; torque about its origin
+  // hydrodynamic force on the owner particle: -B sum_i Omega_i e_i; torque about its origin.
+  // Formed, like the mass/momentum sums, only on the step whose sums are read (REDUCE); the
+  // accumulators of every other step are cleared again before anyone reads them.
   const unsigned full = 0xffffffffu;
   const bool hasF = owner >= 0;
-  if (__any_sync(full, hasF)) {
+  if (REDUCE && __any_sync(full, hasF)) {
     R Fc[3] = {-dpx, -dpy, -dpz};
     R Tc[3] = {R(0.0), R(0.0), R(0.0)};
     if (hasF) {
