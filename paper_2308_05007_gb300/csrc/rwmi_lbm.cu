@@ -38,13 +38,15 @@ lbm_kernel(Geom g, Planes<Q, typename Store<STORE>::T> pl,
                                                   const uint32_t* __restrict__ bword,
                                                   const PoseF* __restrict__ pose,
                                                   const PoseD* __restrict__ posed,
-                                                  const StepParams* __restrict__ sp, double tau_d,
-                                                  double rho0_d, double* __restrict__ red,
+                                                  const StepParams* __restrict__ sp,
+                                                  typename Store<STORE>::R tau,
+                                                  typename Store<STORE>::R rho0, double* __restrict__ red,
                                                   double* __restrict__ forces) {
   using L = Lat<Q>;
   using S = Store<STORE>;
   using R = typename S::R;   // arithmetic type: binary32, or binary64 for the binary64 storage
-  const R tau = (R)tau_d, rho0 = (R)rho0_d;
+  // tau and rho0 arrive in R (converted on the host: a per-thread binary64 -> binary32
+  // conversion would occupy GB300's narrow FP64 pipe)
   const uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x;
   const bool valid = idx < g.ncell;
   const int c = (int)(valid ? idx : g.ncell - 1);   // tail lanes recompute the last cell, store nothing
@@ -243,6 +245,7 @@ static void launch_lbm_q(bool walls, bool reduce, const Geom& g, const void* fin
                          const uint16_t* solid, BrickSet bs, double tau, double rho0, double* red,
                          double* forces, cudaStream_t st, int bsz) {
   using T = typename Store<STORE>::T;
+  using R = typename Store<STORE>::R;
   Planes<Q, T> pl;
   for (int i = 0; i < Q; ++i) {
     pl.in[i] = (const T*)fin + (size_t)i * g.ncell_pad;
@@ -252,11 +255,11 @@ static void launch_lbm_q(bool walls, bool reduce, const Geom& g, const void* fin
   const int bsz_ok = (bsz == 64 || bsz == 128) ? bsz : 256;
   const dim3 grid((g.ncell + bsz_ok - 1) / bsz_ok), block(bsz_ok);
   if (walls) {
-    if (reduce) lbm_kernel<Q, STORE, true, true><<<grid, block, 0, st>>>(g, pl, u4, solid, bs.bword, bs.pose, bs.posed, bs.sp, tau, rho0, red, forces);
-    else lbm_kernel<Q, STORE, true, false><<<grid, block, 0, st>>>(g, pl, u4, solid, bs.bword, bs.pose, bs.posed, bs.sp, tau, rho0, red, forces);
+    if (reduce) lbm_kernel<Q, STORE, true, true><<<grid, block, 0, st>>>(g, pl, u4, solid, bs.bword, bs.pose, bs.posed, bs.sp, (R)tau, (R)rho0, red, forces);
+    else lbm_kernel<Q, STORE, true, false><<<grid, block, 0, st>>>(g, pl, u4, solid, bs.bword, bs.pose, bs.posed, bs.sp, (R)tau, (R)rho0, red, forces);
   } else {
-    if (reduce) lbm_kernel<Q, STORE, false, true><<<grid, block, 0, st>>>(g, pl, u4, solid, bs.bword, bs.pose, bs.posed, bs.sp, tau, rho0, red, forces);
-    else lbm_kernel<Q, STORE, false, false><<<grid, block, 0, st>>>(g, pl, u4, solid, bs.bword, bs.pose, bs.posed, bs.sp, tau, rho0, red, forces);
+    if (reduce) lbm_kernel<Q, STORE, false, true><<<grid, block, 0, st>>>(g, pl, u4, solid, bs.bword, bs.pose, bs.posed, bs.sp, (R)tau, (R)rho0, red, forces);
+    else lbm_kernel<Q, STORE, false, false><<<grid, block, 0, st>>>(g, pl, u4, solid, bs.bword, bs.pose, bs.posed, bs.sp, (R)tau, (R)rho0, red, forces);
   }
 }
 

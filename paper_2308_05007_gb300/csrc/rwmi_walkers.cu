@@ -126,6 +126,33 @@ __device__ int inside_any(const WalkCtx& c, const float* x) {
   return -1;
 }
 
+// inside_any through the candidate list of x's own brick: a particle holding x lies within its
+// bound radius of x, so it is on that list (built at the same time with a larger radius). Same
+// answer (lowest index), a handful of particles instead of all; all of them when the list
+// overflowed.
+__device__ int inside_cand(const WalkCtx& c, const float* x) {
+  const float xw = wrap_coord(x[0], (float)c.g.n[0], c.g.wall[0], c.g.inv_n[0]);
+  const float yw = wrap_coord(x[1], (float)c.g.n[1], c.g.wall[1], c.g.inv_n[1]);
+  const float zw = wrap_coord(x[2], (float)c.g.n[2], c.g.wall[2], c.g.inv_n[2]);
+  const int b = brick_of(xw, yw, zw, c.g);
+  const uint32_t nc = c.bs.bword[b] & 0xffffu;
+  if (nc > MAXC) return inside_any(c, x);
+  int best = -1;
+  for (uint32_t m = 0; m < nc; ++m) {
+    const int p = c.bs.bcand[b * MAXC + m] & 0x7fff;
+    if (best >= 0 && p > best) continue;
+    const PoseF& pp = c.bs.pose[p];
+    const float dx = min_image_rn(xw - pp.o[0], (float)c.g.n[0], c.g.wall[0]);
+    const float dy = min_image_rn(yw - pp.o[1], (float)c.g.n[1], c.g.wall[1]);
+    const float dz = min_image_rn(zw - pp.o[2], (float)c.g.n[2], c.g.wall[2]);
+    const float rb = c.ps.desc[p].rb + 1e-3f;
+    if (dx * dx + dy * dy + dz * dz > rb * rb) continue;
+    const ParticleDesc& d = c.ps.desc[p];
+    if (metaball_value(c.bs.cworld, d.c0, d.c1, xw, yw, zw, c.g) >= 1.0f) best = p;
+  }
+  return best;
+}
+
 // Algorithm 1: bisection from outside point a (f < 1) to inside point b (f >= 1) of particle p;
 // |f(mid) - 1| < 1e-3 converges; at most 200 iterations. aout: final outside end.
 __device__ bool bisect(const WalkCtx& c, int p, const float* a_in, const float* b_in, float* xi, float* aout) {
@@ -177,13 +204,13 @@ __device__ bool refill(const WalkCtx& c, int p, const float* x, uint32_t id, uin
   const float rad = amp * cbrtf(uniform24(r.z));
   float xr[3] = {xs[0] + rad * st * cp, xs[1] + rad * st * sp, xs[2] + rad * ct};
   wall_reflect(xr, c.g);
-  if (inside_any(c, xr) >= 0) {
+  if (inside_cand(c, xr) >= 0) {
     const float dn = (xr[0] - xs[0]) * no[0] + (xr[1] - xs[1]) * no[1] + (xr[2] - xs[2]) * no[2];
     if (dn < 0.0f) for (int a = 0; a < 3; ++a) xr[a] -= 2.0f * dn * no[a];
     wall_reflect(xr, c.g);
-    if (inside_any(c, xr) >= 0) {
+    if (inside_cand(c, xr) >= 0) {
       xr[0] = aend[0]; xr[1] = aend[1]; xr[2] = aend[2];
-      if (inside_any(c, xr) >= 0) { xnew[0] = xr[0]; xnew[1] = xr[1]; xnew[2] = xr[2]; return false; }
+      if (inside_cand(c, xr) >= 0) { xnew[0] = xr[0]; xnew[1] = xr[1]; xnew[2] = xr[2]; return false; }
     }
   }
   xnew[0] = xr[0]; xnew[1] = xr[1]; xnew[2] = xr[2];
@@ -201,8 +228,8 @@ __device__ __noinline__ unsigned resolve_particles(const WalkCtx& c, const float
   unsigned ev = 0u;
   int pin = -1, qin = -1;
   if (nc > MAXC || far_step) {
-    pin = inside_any(c, x);
-    qin = inside_any(c, xf);
+    pin = inside_cand(c, x);
+    qin = inside_cand(c, xf);
   } else {
     const float xfw = wrap_coord(xf[0], (float)c.g.n[0], c.g.wall[0], c.g.inv_n[0]);
     const float yfw = wrap_coord(xf[1], (float)c.g.n[1], c.g.wall[1], c.g.inv_n[1]);
@@ -234,7 +261,7 @@ __device__ __noinline__ unsigned resolve_particles(const WalkCtx& c, const float
       const float tn = ti[0] * nv[0] + ti[1] * nv[1] + ti[2] * nv[2];
       float tr[3];
       for (int a = 0; a < 3; ++a) tr[a] = xi[a] + (ti[a] - 2.0f * tn * nv[a]);
-      if (beyond_wall(tr, c.g) || inside_any(c, tr) >= 0) {
+      if (beyond_wall(tr, c.g) || inside_cand(c, tr) >= 0) {
         xn[0] = x[0]; xn[1] = x[1]; xn[2] = x[2];
       } else {
         xn[0] = tr[0]; xn[1] = tr[1]; xn[2] = tr[2];
