@@ -50,6 +50,7 @@ def parse(argv=None):
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--overlap", type=int, default=2, choices=[0, 1, 2])
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-precision", action="store_true")
     ap.add_argument("--batch-domains", type=int, default=64)
     ap.add_argument("--batch-steps", type=int, default=160)
     ap.add_argument("--no-served", action="store_true")
@@ -270,6 +271,45 @@ def measure_variants(a, stream):
     return out
 
 
+def measure_precision_case(a):
+    """The precision workload at full size: 384^3 periodic box (parity physics: tau 0.8, constant
+    body force 1e-6 along x), 128 static particles, 3e7 walkers, for each population storage.
+    Whole-step throughput over graph-replayed steps (CUDA events on the context's stream after a
+    warm-up), and the step's algorithmic bytes against the measured HBM peak."""
+    import torch
+    from paper_2308_05007_gb300 import inputs as I
+    from paper_2308_05007_gb300.rwmi import Simulation
+    peak = float(measured_peaks()["hbm_gbs"])
+    out = {}
+    base = I.precision(n=384, n_particles=128, n_walkers=30_000_000, seed=2)
+    base = I.with_(base, sort_interval=16, moment_interval=16)
+    stream = torch.cuda.Stream()
+    for storage in (1, 0, 2, 3):
+        w = I.with_(base, storage=storage)
+        sim = Simulation.from_workload(w, seed_walkers=False)
+        sim.set_stream(stream)
+        sim.seed_walkers(w.n_walkers, *w.walker_box)
+        n = 16 if storage == 3 else 48
+        with torch.cuda.stream(stream):
+            sim.step(16)
+            assert sim.sync() >= 0
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sim.step(n)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / n
+            assert sim.sync() >= 0
+        sim.close()
+        sb = STORE_BYTES[storage]
+        step_bytes = bytes_per_step(w, w.n_cells, sb)
+        out[STORE_NAMES[storage]] = {"ms_per_step": ms, "mlups": w.n_cells / (ms / 1e3) / 1e6,
+                                     "walker_steps_per_s": w.n_walkers / (ms / 1e3),
+                                     "step_hbm_frac": step_bytes / (ms / 1e3) / 1e9 / peak, "steps": n}
+    return {"workload": "384^3 periodic, tau 0.8, F=1e-6 x, 128 static metaball particles, 3e7 walkers, "
+                        "D=0.01, D3Q15", "cells": base.n_cells, "walkers": base.n_walkers, "storages": out}
+
+
 def measure_batched(a):
     """64 independent periodic domains (edges U{48..160}, 4-32 particles of 2-10 centres,
     1e5-2e6 walkers, tau U[0.6, 1], D U[0.001, 0.02]) advanced together. Each context's LBM
@@ -447,6 +487,8 @@ def main():
     sim.close()
     if not a.no_variants:
         line["variants"] = measure_variants(a, stream)
+    if not a.no_precision:
+        line["precision_384"] = measure_precision_case(a)
     if not a.no_batched:
         line["batched"] = measure_batched(a)
     if not a.no_served:
