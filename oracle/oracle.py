@@ -82,6 +82,12 @@ def lib():
             L.orc_trilinear.argtypes = [P, C.c_void_p, C.c_void_p]
             L.orc_pose.argtypes = [P, C.c_longlong, C.c_int, C.c_void_p, C.c_void_p]
             L.orc_lattice.argtypes = [C.c_int, C.c_void_p, C.c_void_p]
+            L.orc_set_coupling.argtypes = [P, C.c_int]
+            L.orc_nodes.argtypes = [P, C.c_longlong, C.c_void_p]
+            L.orc_ibb_q.restype = C.c_double
+            L.orc_ibb_q.argtypes = [P, C.c_longlong, C.c_int, C.c_longlong, C.c_longlong, C.c_longlong, C.c_void_p]
+            L.orc_ibb_link.restype = C.c_double
+            L.orc_ibb_link.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, dp, dp, dp, C.c_double]
             _lib = L
     return _lib
 
@@ -136,6 +142,8 @@ class Oracle:
         o = cls(w.dims, q=w.q, tau=w.tau, D=w.D, seed=w.seed, wall_mask=w.wall_mask,
                 body_force=w.body_force, force_period=w.force_period, rho0=w.rho0,
                 init_velocity=w.init_velocity)
+        if getattr(w, "coupling", 0):
+            o.set_coupling(w.coupling)
         if w.metaballs is not None and w.metaballs.n_particles > 0:
             o.set_metaballs(w.metaballs)
         if seed_walkers and w.n_walkers:
@@ -196,6 +204,21 @@ class Oracle:
 
     def set_time(self, t):
         lib().orc_set_time(self.h, int(t))
+
+    def set_coupling(self, mode):
+        """0: partially saturated cells; 1: IBB, momentum exchange and refilling (Section 2.4.3)."""
+        lib().orc_set_coupling(self.h, int(mode))
+
+    def nodes(self, t=None):
+        """IBB node classes at time t: 1 + owning particle for solid nodes, 0 for fluid."""
+        out = np.zeros(self.n_cells, np.int32)
+        lib().orc_nodes(self.h, int(self.t if t is None else t), _ptr(out))
+        return out
+
+    def ibb_q(self, t, p, ijk, e):
+        """q of Eq. 25 on the link from node ijk along lattice vector e, particle p, time t."""
+        ev = np.ascontiguousarray(e, np.int32)
+        return float(lib().orc_ibb_q(self.h, int(t), int(p), int(ijk[0]), int(ijk[1]), int(ijk[2]), _ptr(ev)))
 
     # ---- outputs ----
     def velocity(self) -> np.ndarray:
@@ -340,3 +363,8 @@ class Oracle:
         v = np.zeros(3)
         lib().orc_pose(self.h, int(t), int(p), _ptr(o), _ptr(v))
         return o, v
+
+
+def ibb_link(q, i, qf, rho_f, uf, uff, uw, Gp):
+    """Eqs. 23-25 for one link: G_i(x_f, t + 1) with i the direction away from the wall."""
+    return float(lib().orc_ibb_link(int(q), int(i), float(qf), float(rho_f), _d3(uf), _d3(uff), _d3(uw), float(Gp)))

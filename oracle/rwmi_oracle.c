@@ -132,6 +132,8 @@ typedef struct {
 
     long long t;
     long long cnt_type[4], bisect_fail, refill_fail, wall_fail, seed_fail;
+
+    int coupling;            /* 0: partially saturated cells; 1: IBB + momentum exchange + refilling */
 } orc_t;
 
 static long long cell_index(const orc_t* o, long long i, long long j, long long k)
@@ -490,8 +492,11 @@ static void pull_cell(const orc_t* o, long long i, long long j, long long k, dou
     }
 }
 
+static void ibb_step(orc_t* o, long long t);
+
 static void lbm_step(orc_t* o, long long t)
 {
+    if (o->coupling == 1) { ibb_step(o, t); return; }
     if (o->solid_time != t) rasterize(o, t);
     frame_t fr;
     frame_alloc(o, &fr);
@@ -533,6 +538,208 @@ static void lbm_step(orc_t* o, long long t)
     o->f = o->fn;
     o->fn = tmp;
     frame_free(&fr);
+}
+
+/* ------------------------------------------------------------------------------------------
+ * The paper's own particle-fluid coupling, Section 2.4.3, used instead of partially saturated
+ * cells when coupling = 1: interpolated bounce-back on the moving particle surface (Eqs. 23-25),
+ * Galilean-invariant momentum exchange for the force, local refilling (Eqs. 26-27).
+ * Readings (the paper leaves these open):
+ *  - A node (cell centre) is solid at time t when Eq. 3 of some particle reaches c0 = 1 there,
+ *    decided in binary32 with the fixed operation order of metaball32; it belongs to the lowest
+ *    such particle index.
+ *  - q of Eq. 25: the fraction of the link from the fluid node x_f to the solid node at which
+ *    Eq. 3 of the solid node's particle crosses 1: 24 bisection steps in binary32 (midpoint
+ *    0.5 (lo + hi), link point x_f + mid e), q = the middle of the last bracket.
+ *  - u_f, u_ff and rho_f are the velocity and density of the previous LBM update (rho_f as the
+ *    sum of x_f's own post-collision populations, which carry the same mass); x_ff = x_f + e_i,
+ *    one node further from the wall, and u_ff = u_f when x_ff is solid or beyond a wall.
+ *  - The non-equilibrium part G^neq_i'(x_d) of Eq. 24 is taken at x_f:
+ *    G+_i'(x_f, t) - G^eq_i'(rho_f, u_f).
+ *  - Force on the particle per link (Galilean-invariant momentum exchange, Wen et al. 2014):
+ *    (e_i' - u_w) G+_i'(x_f) - (e_i - u_w) G_i(x_f, t + 1); torque (x_w - o_p) x that force,
+ *    with x_w = x_f + q e_i' the wall point and u_w the particle's rigid velocity there.
+ *  - Refilling: a node solid at t - 1 and fluid at t has no populations of its own, so Eq. 26's
+ *    G_i' does not exist and Eq. 27 applies: G^eq(rho0, u_new), u_new the covering
+ *    particle's rigid velocity at the node at time t.
+ *  - Solid nodes hold G^eq(rho0, u_s) at their particle's rigid velocity u_s and report u_s
+ *    (the walkers interpolate it); the mass and momentum sums count fluid nodes only.
+ * ------------------------------------------------------------------------------------------ */
+
+/* Rigid velocity of particle p at x: v_p + omega_p x (x - o_p), minimum image */
+static void rigid_velocity(const orc_t* o, const frame_t* fr, int p, const double x[3], double u[3])
+{
+    double r[3];
+    for (int a = 0; a < 3; ++a) r[a] = min_image(o, a, x[a] - fr->o[3 * p + a]);
+    const double* v = fr->v + 3 * p;
+    const double* w = fr->w + 3 * p;
+    u[0] = v[0] + w[1] * r[2] - w[2] * r[1];
+    u[1] = v[1] + w[2] * r[0] - w[0] * r[2];
+    u[2] = v[2] + w[0] * r[1] - w[1] * r[0];
+}
+
+/* Node classes at time t: node[c] = 1 + the lowest particle whose Eq. 3 reaches 1 at the cell
+ * centre (binary32 decision), 0 for a fluid node. */
+static void classify_nodes(const orc_t* o, long long t, int* node)
+{
+    frame_t fr;
+    frame_alloc(o, &fr);
+    frame_at(o, t, &fr);
+    for (long long k = 0; k < o->n[2]; ++k)
+        for (long long j = 0; j < o->n[1]; ++j)
+            for (long long i = 0; i < o->n[0]; ++i) {
+                long long c = cell_index(o, i, j, k);
+                double xc[3] = {i + 0.5, j + 0.5, k + 0.5};
+                float xs[3] = {(float)i + 0.5f, (float)j + 0.5f, (float)k + 0.5f};
+                node[c] = 0;
+                for (int p = 0; p < o->P; ++p)
+                    if (origin_distance(o, &fr, p, xc) <= o->Rb[p] + 1.0 && metaball32(o, &fr, p, xs) >= 1.0f) {
+                        node[c] = p + 1;
+                        break;
+                    }
+            }
+    frame_free(&fr);
+}
+
+/* q of Eq. 25 on the link from node (i, j, k) along e (towards particle p's solid node) */
+static float ibb_q(const orc_t* o, const frame_t* fr, int p, long long i, long long j, long long k, const int* e)
+{
+    const float x0[3] = {(float)i + 0.5f, (float)j + 0.5f, (float)k + 0.5f};
+    float lo = 0.0f, hi = 1.0f;
+    for (int it = 0; it < 24; ++it) {
+        float mid = 0.5f * (lo + hi);
+        float xm[3];
+        for (int a = 0; a < 3; ++a) {
+            float step = mid * (float)e[a];
+            xm[a] = x0[a] + step;
+        }
+        if (metaball32(o, fr, p, xm) >= 1.0f) hi = mid;
+        else lo = mid;
+    }
+    return 0.5f * (lo + hi);
+}
+
+/* Eqs. 23-25 for one link: the population G_i(x_f, t + 1) entering x_f from the wall, i the
+ * direction away from the wall and ip = opposite(i) the direction into it. */
+static double ibb_link(int q, int i, int ip, double qf, double rho_f, const double uf[3], const double uff[3],
+                       const double uw[3], double Gp)
+{
+    double us[3], uss[3], ud[3];
+    for (int a = 0; a < 3; ++a) {
+        if (qf <= 0.5) us[a] = 2.0 * qf * uf[a] + (1.0 - 2.0 * qf) * uff[a];
+        else us[a] = (1.0 - qf) / qf * uf[a] + (2.0 * qf - 1.0) / qf * uw[a];
+        uss[a] = (1.0 - qf) / (1.0 + qf) * uff[a] + 2.0 * qf / (1.0 + qf) * uw[a];
+        ud[a] = us[a] / 3.0 + 2.0 * uss[a] / 3.0;
+    }
+    const int* e = lattice_e(q, i);
+    double eu = e[0] * uw[0] + e[1] * uw[1] + e[2] * uw[2];
+    double gneq = Gp - feq(q, ip, rho_f, uf);
+    return feq(q, ip, rho_f, ud) + gneq + 6.0 * lattice_weight(q, ip) * rho_f * eu;
+}
+
+static void ibb_step(orc_t* o, long long t)
+{
+    const int q = o->q;
+    const long long n = o->ncell;
+    int* nprev = (int*)malloc(sizeof(int) * (size_t)n);
+    int* ncur = (int*)malloc(sizeof(int) * (size_t)n);
+    double* uprev = (double*)malloc(sizeof(double) * 3 * (size_t)n);
+    memcpy(uprev, o->u, sizeof(double) * 3 * (size_t)n);
+    classify_nodes(o, t - 1, nprev);
+    classify_nodes(o, t, ncur);
+    frame_t fr;
+    frame_alloc(o, &fr);
+    frame_at(o, t, &fr);
+    double F[3];
+    body_force(o, t, F);
+    /* refilling of nodes uncovered since t - 1, Eq. 27 */
+    for (long long k = 0; k < o->n[2]; ++k)
+        for (long long j = 0; j < o->n[1]; ++j)
+            for (long long i = 0; i < o->n[0]; ++i) {
+                long long c = cell_index(o, i, j, k);
+                if (nprev[c] == 0 || ncur[c] != 0) continue;
+                double xc[3] = {i + 0.5, j + 0.5, k + 0.5}, un[3];
+                rigid_velocity(o, &fr, nprev[c] - 1, xc, un);
+                for (int m = 0; m < q; ++m) o->f[(size_t)m * n + c] = feq(q, m, o->rho0, un);
+            }
+    o->mass = 0.0;
+    o->mom[0] = o->mom[1] = o->mom[2] = 0.0;
+    for (int m = 0; m < 3 * o->P; ++m) { o->Fp[m] = 0.0; o->Tp[m] = 0.0; }
+    for (long long k = 0; k < o->n[2]; ++k)
+        for (long long j = 0; j < o->n[1]; ++j)
+            for (long long i = 0; i < o->n[0]; ++i) {
+                long long c = cell_index(o, i, j, k);
+                double xc[3] = {i + 0.5, j + 0.5, k + 0.5};
+                if (ncur[c] != 0) {   /* solid node */
+                    double us[3];
+                    rigid_velocity(o, &fr, ncur[c] - 1, xc, us);
+                    for (int m = 0; m < q; ++m) o->fn[(size_t)m * n + c] = feq(q, m, o->rho0, us);
+                    for (int a = 0; a < 3; ++a) o->u[3 * c + a] = us[a];
+                    o->rho[c] = o->rho0;
+                    continue;
+                }
+                double fi[19], fo[19], u[3], rho, dp[3];
+                pull_cell(o, i, j, k, fi);
+                double rho_f = 0.0;
+                for (int m = 0; m < q; ++m) rho_f += o->f[(size_t)m * n + c];
+                const double* uf = uprev + 3 * c;
+                long long ijk[3] = {i, j, k};
+                for (int m = 0; m < q; ++m) {
+                    const int* e = lattice_e(q, m);
+                    long long s[3], ff[3];
+                    int blocked = 0, ff_out = 0;
+                    for (int a = 0; a < 3; ++a) {
+                        s[a] = ijk[a] - e[a];
+                        ff[a] = ijk[a] + e[a];
+                        if (o->wall[a]) {
+                            if (s[a] < 0 || s[a] >= o->n[a]) blocked = 1;
+                            if (ff[a] < 0 || ff[a] >= o->n[a]) ff_out = 1;
+                        } else {
+                            s[a] = wrapll(s[a], o->n[a]);
+                            ff[a] = wrapll(ff[a], o->n[a]);
+                        }
+                    }
+                    if (blocked) continue;                       /* plane wall: bounce-back above */
+                    long long cs = cell_index(o, s[0], s[1], s[2]);
+                    if (ncur[cs] == 0) continue;                 /* fluid source: plain pull */
+                    const int p = ncur[cs] - 1, ip = opposite(m);
+                    const int* eip = lattice_e(q, ip);
+                    const double qf = (double)ibb_q(o, &fr, p, i, j, k, eip);
+                    double xw[3], uw[3];
+                    for (int a = 0; a < 3; ++a) xw[a] = xc[a] + qf * eip[a];
+                    rigid_velocity(o, &fr, p, xw, uw);
+                    const double* uff = uf;
+                    if (!ff_out) {
+                        long long cf = cell_index(o, ff[0], ff[1], ff[2]);
+                        if (ncur[cf] == 0) uff = uprev + 3 * cf;
+                    }
+                    const double Gp = o->f[(size_t)ip * n + c];
+                    fi[m] = ibb_link(q, m, ip, qf, rho_f, uf, uff, uw, Gp);
+                    double Fl[3], r[3];
+                    for (int a = 0; a < 3; ++a) Fl[a] = (eip[a] - uw[a]) * Gp - (e[a] - uw[a]) * fi[m];
+                    for (int a = 0; a < 3; ++a) r[a] = min_image(o, a, xw[a] - fr.o[3 * p + a]);
+                    for (int a = 0; a < 3; ++a) o->Fp[3 * p + a] += Fl[a];
+                    o->Tp[3 * p + 0] += r[1] * Fl[2] - r[2] * Fl[1];
+                    o->Tp[3 * p + 1] += r[2] * Fl[0] - r[0] * Fl[2];
+                    o->Tp[3 * p + 2] += r[0] * Fl[1] - r[1] * Fl[0];
+                }
+                collide_cell(o, &fr, t, i, j, k, 0, -1, fi, F, fo, u, &rho, dp);
+                for (int m = 0; m < q; ++m) o->fn[(size_t)m * n + c] = fo[m];
+                for (int a = 0; a < 3; ++a) o->u[3 * c + a] = u[a];
+                o->rho[c] = rho;
+                o->mass += rho;
+                for (int m = 0; m < q; ++m) {
+                    const int* e = lattice_e(q, m);
+                    for (int a = 0; a < 3; ++a) o->mom[a] += fi[m] * e[a];
+                }
+            }
+    double* tmp = o->f;
+    o->f = o->fn;
+    o->fn = tmp;
+    frame_free(&fr);
+    free(nprev);
+    free(ncur);
+    free(uprev);
 }
 
 /* ------------------------------------------------------------------------------------------
@@ -949,7 +1156,7 @@ ORC_API void orc_step(void* h, long long nsteps)
 {
     orc_t* o = (orc_t*)h;
     for (long long s = 0; s < nsteps; ++s) {
-        rasterize(o, o->t);
+        if (!o->coupling) rasterize(o, o->t);
         lbm_step(o, o->t);
         walkers_step(o, o->t);
         o->t++;
@@ -961,7 +1168,7 @@ ORC_API void orc_step_fluid(void* h, long long nsteps)
 {
     orc_t* o = (orc_t*)h;
     for (long long s = 0; s < nsteps; ++s) {
-        rasterize(o, o->t);
+        if (!o->coupling) rasterize(o, o->t);
         lbm_step(o, o->t);
         o->t++;
     }
@@ -1122,6 +1329,28 @@ ORC_API void orc_walkers_advance(void* h, long long n, const double* x, const ui
     frame_at(o, o->t + 1, &fr1);
     for (long long w = 0; w < n; ++w) walker_advance(o, &fr1, o->u, ids[w], (uint32_t)o->t, x + 3 * w, xout + 3 * w);
     frame_free(&fr1);
+}
+
+/* Particle-fluid coupling: 0 partially saturated cells (default), 1 IBB (Section 2.4.3) */
+ORC_API void orc_set_coupling(void* h, int mode) { ((orc_t*)h)->coupling = mode; }
+
+ORC_API void orc_nodes(void* h, long long t, int* node) { classify_nodes((orc_t*)h, t, node); }
+
+ORC_API double orc_ibb_q(void* h, long long t, int p, long long i, long long j, long long k, const int e[3])
+{
+    orc_t* o = (orc_t*)h;
+    frame_t fr;
+    frame_alloc(o, &fr);
+    frame_at(o, t, &fr);
+    double qv = (double)ibb_q(o, &fr, p, i, j, k, e);
+    frame_free(&fr);
+    return qv;
+}
+
+ORC_API double orc_ibb_link(int q, int i, double qf, double rho_f, const double uf[3], const double uff[3],
+                            const double uw[3], double Gp)
+{
+    return ibb_link(q, i, opposite(i), qf, rho_f, uf, uff, uw, Gp);
 }
 
 /* ---- single-function entry points for the CPU pins ---- */

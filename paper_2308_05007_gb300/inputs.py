@@ -73,6 +73,7 @@ class Workload:
     storage: int = 1                     # 0 FP32, 1 FP32 shifted by w_i rho0, 2 FP16 shifted, 3 FP64 shifted
     sort_interval: int = 0
     moment_interval: int = 0
+    coupling: int = 0                    # 0 partially saturated cells, 1 IBB (Section 2.4.3)
     notes: str = ""
 
     @property

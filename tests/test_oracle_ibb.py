@@ -1,0 +1,132 @@
+"""Pins for the oracle's IBB coupling (Section 2.4.3: interpolated bounce-back, Eqs. 23-25;
+Galilean-invariant momentum exchange; refilling, Eqs. 26-27), independent of the oracle itself:
+closed-form ray-sphere intersections for q, the link formula's special cases, an exact momentum
+balance for a resting particle, the rest state, and Galilean invariance of the force."""
+import numpy as np
+import pytest
+
+from oracle.oracle import Oracle, ibb_link, lattice
+from paper_2308_05007_gb300 import inputs as I
+
+
+def _sphere_workload(n=24, center=(12.3, 11.7, 12.1), k=36.0, F=(0.0, 0.0, 0.0), tau=0.8,
+                     velocity=(0.0, 0.0, 0.0), particle_velocity=None):
+    mb = I.single_sphere(center, k=k)
+    if particle_velocity is not None:
+        # a sinusoid whose velocity is particle_velocity at t = 0 and stays within 1e-6 of it
+        # over the first steps: period 1e6, amplitude v T / (2 pi)
+        T = 1e6
+        mb.period[:] = T
+        mb.phase[:] = 0.0
+        mb.amplitude[0] = np.asarray(particle_velocity) * T / (2 * np.pi)
+    return I.Workload(name="ibb_sphere", dims=(n, n, n), tau=tau, D=0.0, seed=0, q=15,
+                      body_force=F, init_velocity=velocity, metaballs=mb, coupling=1, steps=1)
+
+
+def test_q_is_the_ray_sphere_intersection():
+    """For one centre f = k/r^2, the surface f = 1 is the sphere r = sqrt(k); q along every link
+    from a fluid node into a solid node is the smaller root of |x + s e - c|^2 = k."""
+    w = _sphere_workload()
+    o = Oracle.from_workload(w, seed_walkers=False)
+    e, _ = lattice(w.q)
+    node = o.nodes(0)
+    n = w.dims[0]
+    c = np.array(w.metaballs.origin[0])
+    R2 = w.metaballs.k[0]
+    checked = 0
+    for cell in np.where(node == 0)[0]:
+        ijk = np.array([cell % n, (cell // n) % n, cell // (n * n)])
+        x = ijk + 0.5
+        for m in range(1, w.q):
+            s = (ijk + e[m]) % n
+            if node[(s[2] * n + s[1]) * n + s[0]] == 0:
+                continue
+            d = x - c
+            a, b, cc = e[m] @ e[m], 2 * d @ e[m], d @ d - R2
+            s_exact = (-b - np.sqrt(b * b - 4 * a * cc)) / (2 * a)
+            assert 0.0 < s_exact <= 1.0
+            assert abs(o.ibb_q(0, 0, ijk, e[m]) - s_exact) <= 1e-5, (ijk, e[m])
+            checked += 1
+    assert checked > 500
+
+
+def test_link_formula_special_cases():
+    q = 15
+    e, w = lattice(q)
+    i = int(np.where((e == [1, 0, 0]).all(1))[0][0])
+    ip = int(np.where((e == [-1, 0, 0]).all(1))[0][0])
+    rho = 1.02
+    u = np.array([0.03, -0.01, 0.02])
+    Gp = 0.13
+
+    def feq(m, r, v):
+        eu = e[m] @ v
+        return w[m] * r * (1 + 3 * eu + 4.5 * eu * eu - 1.5 * v @ v)
+
+    # q = 1/2 with one velocity everywhere: the moving-wall bounce-back G+_i' + 6 w rho e_i.u_w
+    assert ibb_link(q, i, 0.5, rho, u, u, u, Gp) == pytest.approx(Gp + 6 * w[ip] * rho * (e[i] @ u), abs=1e-15)
+    # q = 1: u_d* = u_d** = u_w, so the equilibrium part is taken at the wall velocity
+    uf, uff, uw = np.array([0.01, 0.0, 0.0]), np.array([0.02, 0.01, 0.0]), np.array([0.0, 0.0, 0.04])
+    want = feq(ip, rho, uw) + Gp - feq(ip, rho, uf) + 6 * w[ip] * rho * (e[i] @ uw)
+    assert ibb_link(q, i, 1.0, rho, uf, uff, uw, Gp) == pytest.approx(want, abs=1e-15)
+    # the two branches of u_d* meet at q = 1/2
+    lo = ibb_link(q, i, 0.5, rho, uf, uff, uw, Gp)
+    hi = ibb_link(q, i, 0.5 + 1e-12, rho, uf, uff, uw, Gp)
+    assert abs(lo - hi) < 1e-11
+    # q -> 0: u_d* = u_ff, u_d** = u_ff, so the equilibrium part is taken at u_ff
+    want0 = feq(ip, rho, uff) + Gp - feq(ip, rho, uf) + 6 * w[ip] * rho * (e[i] @ uw)
+    assert ibb_link(q, i, 1e-14, rho, uf, uff, uw, Gp) == pytest.approx(want0, abs=1e-12)
+
+
+def _fluid_momentum(o, q):
+    e, _ = lattice(q)
+    f = o.populations()
+    fluid = o.nodes() == 0
+    return (e.T.astype(float) @ f[:, fluid]).sum(1), int(fluid.sum())
+
+
+def test_resting_particle_momentum_balance_is_exact():
+    """A particle at rest: the fluid's momentum changes by the body force on its nodes minus the
+    momentum exchanged with the particle, P(t+1) - P(t) = N_f F - F_p, to rounding."""
+    F = np.array([2e-5, -1e-5, 5e-6])
+    w = _sphere_workload(F=tuple(F))
+    o = Oracle.from_workload(w, seed_walkers=False)
+    o.step_fluid(3)
+    for _ in range(3):
+        P0, nf = _fluid_momentum(o, w.q)
+        o.step_fluid(1)
+        P1, nf1 = _fluid_momentum(o, w.q)
+        Fp = o.forces()[0, :3]
+        assert nf == nf1
+        # rounding of the two sums over nf nodes x Q populations of size < 1
+        np.testing.assert_allclose(P1 - P0, nf * F - Fp, rtol=0, atol=2 * nf * w.q * 2.0 ** -52)
+    assert np.linalg.norm(Fp) > 1e-3 * nf * np.linalg.norm(F)   # the particle does take force
+
+
+def test_rest_state_is_kept():
+    w = _sphere_workload()
+    o = Oracle.from_workload(w, seed_walkers=False)
+    o.step_fluid(4)
+    assert np.abs(o.velocity()).max() < 1e-15
+    assert np.abs(o.forces()).max() < 1e-14
+
+
+def test_force_is_galilean_invariant():
+    """Fluid and particle translating together at U: the momentum exchange (Galilean-invariant
+    form) sees no force beyond rounding, IBB keeps the stream uniform, and refilled nodes start
+    at the stream's velocity; the same particle held at rest in the same stream feels the drag."""
+    U = (0.04, 0.0, 0.0)
+    moving = Oracle.from_workload(_sphere_workload(velocity=U, particle_velocity=U), seed_walkers=False)
+    held = Oracle.from_workload(_sphere_workload(velocity=U), seed_walkers=False)
+    nodes0 = moving.nodes(0)
+    moving.step_fluid(4)
+    held.step_fluid(4)
+    assert (moving.nodes(4) != nodes0).sum() > 10   # nodes were covered and uncovered (refilled)
+    f_moving = np.linalg.norm(moving.forces()[0, :3])
+    f_held = np.linalg.norm(held.forces()[0, :3])
+    assert f_held > 1.0
+    assert f_moving < 1e-6 * f_held, (f_moving, f_held)
+    # the stream around the co-moving particle stays uniform (to the particle's 1e-6 drift from
+    # constant velocity over these steps, and rounding)
+    u = moving.velocity().reshape(-1, 3)
+    assert np.abs(u - np.array(U)).max() < 1e-9
