@@ -101,6 +101,12 @@ typedef struct {
                                      (ALU-bound beside HBM-bound);
                                   2: as 1, and the walkers of t (with sort and moments) on a third
                                      stream beside the fluid of t+1. Default 2. */
+    int32_t coupling;          /* particle-fluid coupling of the LBM: 0 partially saturated cells
+                                  (Noble-Torczynski; default); 1 the paper's own (Section 2.4.3):
+                                  interpolated bounce-back on the moving metaball surface
+                                  (Eqs. 23-25), Galilean-invariant momentum exchange for the
+                                  force, refilling of uncovered nodes (Eq. 27). IBB requires
+                                  storage FP32_SHIFT or FP64_SHIFT (else RWMI_E_INVALID). */
 } rwmi_config;
 
 /* Fills *cfg with the defaults listed above. */
@@ -225,6 +231,11 @@ RWMI_API rwmi_status rwmi_lattice(rwmi_ctx* ctx, int32_t* e, double* w, int32_t*
  * count[c] (0..64 sub-samples inside a particle, epsilon = count / 64) and owner[c] (particle
  * index, -1 if none). */
 RWMI_API rwmi_status rwmi_solid(rwmi_ctx* ctx, int32_t* count, int32_t* owner);
+
+/* IBB node classes of the current time (Section 2.4.3, the coupling = 1 reading): out[c] = 0 for a
+ * fluid node, 1 + p when the cell centre lies inside particle p (Eq. 3 >= 1 in binary32, lowest
+ * index). Computed on demand with any coupling. out: int32[ncell], host or device. */
+RWMI_API rwmi_status rwmi_nodes(rwmi_ctx* ctx, int32_t* out);
 
 /* {sum rho, sum_i f_i e_i (3 components)} over all cells at the last LBM step (FP64 sums;
  * formed on the last step of every rwmi_step call). */

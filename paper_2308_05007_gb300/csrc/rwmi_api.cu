@@ -53,6 +53,7 @@ struct rwmi_ctx {
   void* f[2] = {nullptr, nullptr};
   float* u[2] = {nullptr, nullptr};   // (u, rho) per time parity: the LBM of t writes u[t & 1]
   uint16_t* solid[2] = {nullptr, nullptr};   // per time parity: raster of t+1 beside the LBM of t
+  uint16_t* node[2] = {nullptr, nullptr};    // IBB node classes per time parity (0 fluid, 1 + particle)
   int64_t* d_T = nullptr;
   unsigned long long* status = nullptr;
   double* acc[2] = {nullptr, nullptr};   // per time parity: forces [6P] + mass/momentum [4]
@@ -210,11 +211,23 @@ void update_margin(rwmi_ctx* c) {
   // regular walker step: |u| <= U_BOUND plus three normals of at most 4.5 each. A longer step
   // (|z_a| > 4.5 for some axis: ~2e-5 of steps) is flagged and resolved against all particles.
   c->walk_margin = U_BOUND + (float)std::sqrt(2.0 * c->D) * 4.5f * 1.7320508f + 0.01f;
+  // IBB: a cell whose lattice neighbour (up to sqrt(3) away) is solid must lie in a flagged brick,
+  // so that cells of other bricks skip the neighbour checks
+  if (c->cfg.coupling == 1 && c->walk_margin < 1.75f) c->walk_margin = 1.75f;
 }
 
 // Brick lists, poses, body force and solid fraction of the current time; zeroes its accumulators.
 rwmi_status build_current_frame(rwmi_ctx* c) {
   const int par = (int)(c->t & 1);
+  if (c->cfg.coupling == 1 && c->P > 0) {   // IBB: node classes of t - 1 (the first step refills from them)
+    const int pp = par ^ 1;
+    launch_clear_u32(c->bword[pp], c->nbrick + 1, c->stream);
+    launch_pose_bin(c->g, particle_set(c), brick_set(c, pp), c->d_T, -1, c->cfg.body_force,
+                    c->cfg.force_period, 1, c->acc[pp], c->stream);
+    launch_nodes(c->cfg.q, c->cfg.storage, c->g, particle_set(c), brick_set(c, pp), c->node[pp], c->node[pp],
+                 c->f[c->fcur], c->cfg.rho0, false, c->stream);
+    c->launches += 3;
+  }
   CK(cudaMemsetAsync(c->bword[par], 0, sizeof(uint32_t) * (c->nbrick + 1), c->stream));
   launch_pose_bin(c->g, particle_set(c), brick_set(c, par), c->d_T, 0, c->cfg.body_force,
                   c->cfg.force_period, 1, c->acc[par], c->stream);
@@ -339,11 +352,21 @@ void enqueue_step(rwmi_ctx* c, bool reduce) {
     c->launches++;
     phase_end(c, RWMI_PHASE_POSE);
   };
+  const bool ibb = c->cfg.coupling == 1 && c->P > 0;
   auto lbm = [&]() {    // LBM at t
     phase_begin(c, RWMI_PHASE_LBM);
+    IbbArgs ia;
+    if (ibb) {   // node classes of t, refilling of nodes uncovered since t - 1
+      launch_nodes(c->cfg.q, c->cfg.storage, c->g, ps, brick_set(c, tp), c->node[tn], c->node[tp],
+                   c->f[c->fcur], c->cfg.rho0, true, c->stream);
+      c->launches++;
+      ia.nodes = c->node[tp];
+      ia.uprev = reinterpret_cast<const float4*>(c->u[tn]);
+      ia.desc = c->desc;
+    }
     launch_lbm(c->cfg.q, c->cfg.storage, reduce, c->g, c->f[c->fcur], c->f[c->fcur ^ 1], c->u[tp], c->solid[tp],
                brick_set(c, tp), c->tau, c->cfg.rho0, c->acc[tp] + 6 * c->P, c->acc[tp],
-               c->status, c->stream, c->cfg.lbm_block);
+               c->status, c->stream, c->cfg.lbm_block, ibb ? &ia : nullptr);
     c->launches++;
     phase_end(c, RWMI_PHASE_LBM);
     c->fcur ^= 1;
@@ -499,6 +522,7 @@ RWMI_API rwmi_status rwmi_create(rwmi_ctx** out, const int32_t dims[3], double t
     if (s != RWMI_OK) return s;
     for (int k = 0; k < 2; ++k) CK(dalloc(c, &c->u[k], sizeof(float4) * (size_t)g.ncell_pad));
     for (int k = 0; k < 2; ++k) CK(dalloc(c, &c->solid[k], sizeof(uint16_t) * (size_t)ncell));
+    for (int k = 0; k < 2; ++k) CK(dalloc(c, &c->node[k], sizeof(uint16_t) * (size_t)ncell));
     CK(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
     CK(cudaStreamCreateWithFlags(&c->wst, cudaStreamNonBlocking));
     for (cudaEvent_t* e : {&c->fork_ev, &c->join_ev, &c->fluid_ev, &c->walk_ev[0], &c->walk_ev[1]})
@@ -529,6 +553,7 @@ RWMI_API rwmi_status rwmi_create(rwmi_ctx** out, const int32_t dims[3], double t
     CK(cudaMemsetAsync(c->status, 0, sizeof(unsigned long long) * ST_COUNT, c->stream));
     CK(cudaMemsetAsync(c->macc, 0, sizeof(double) * 12, c->stream));
     for (int k = 0; k < 2; ++k) CK(cudaMemsetAsync(c->solid[k], 0, sizeof(uint16_t) * (size_t)ncell, c->stream));
+    for (int k = 0; k < 2; ++k) CK(cudaMemsetAsync(c->node[k], 0, sizeof(uint16_t) * (size_t)ncell, c->stream));
     s = reset_fluid(c);
     if (s != RWMI_OK) return s;
     s = build_current_frame(c);
@@ -553,13 +578,15 @@ RWMI_API rwmi_status rwmi_configure(rwmi_ctx* c, const rwmi_config* cfg) {
       !(cfg->rho0 > 0.0) || cfg->sort_interval < 0 || cfg->moment_interval < 0 ||
       !(cfg->force_period >= 0.0) ||
       !(cfg->lbm_block == 0 || cfg->lbm_block == 64 || cfg->lbm_block == 128 || cfg->lbm_block == 256) ||
-      cfg->overlap < 0 || cfg->overlap > 2)
+      cfg->overlap < 0 || cfg->overlap > 2 || cfg->coupling < 0 || cfg->coupling > 1 ||
+      (cfg->coupling == 1 && cfg->storage != RWMI_STORE_FP32_SHIFT && cfg->storage != RWMI_STORE_FP64_SHIFT))
     return fail(c, RWMI_E_INVALID, "rwmi_configure: bad q, storage, wall_mask, rho0 or interval");
   for (int a = 0; a < 3; ++a)
     if (!std::isfinite(cfg->body_force[a]) || !std::isfinite(cfg->init_velocity[a]))
       return fail(c, RWMI_E_INVALID, "rwmi_configure: non-finite force or velocity");
   const bool realloc_f = cfg->q != c->cfg.q || cfg->storage != c->cfg.storage;
   c->cfg = *cfg;
+  update_margin(c);
   for (int a = 0; a < 3; ++a) c->g.wall[a] = (cfg->wall_mask >> a) & 1;
   drop_graphs(c);
   if (realloc_f) {
@@ -784,12 +811,22 @@ RWMI_API rwmi_status rwmi_autotune(rwmi_ctx* c, int32_t* chosen) {
   const int cand[3] = {64, 128, 256};
   float best_ms = 1e30f;
   int best = 256;
+  IbbArgs ia;
+  const bool ibb = c->cfg.coupling == 1 && c->P > 0;
+  if (ibb) {   // node classes of this time (no refilling: the step itself redoes them)
+    launch_nodes(c->cfg.q, c->cfg.storage, c->g, particle_set(c), brick_set(c, tp), c->node[tp ^ 1], c->node[tp],
+                 c->f[c->fcur], c->cfg.rho0, false, c->stream);
+    c->launches++;
+    ia.nodes = c->node[tp];
+    ia.uprev = reinterpret_cast<const float4*>(c->u[tp ^ 1]);
+    ia.desc = c->desc;
+  }
   for (int k = 0; k < 3; ++k) {
     for (int rep = 0; rep < 6; ++rep) {
       if (rep == 1) cudaEventRecord(e0, c->stream);
       launch_lbm(c->cfg.q, c->cfg.storage, false, c->g, c->f[c->fcur], c->f[c->fcur ^ 1], c->u[c->t & 1], c->solid[c->t & 1],
                  brick_set(c, tp), c->tau, c->cfg.rho0, (double*)c->scratch + 6 * c->P,
-                 (double*)c->scratch, c->status, c->stream, cand[k]);
+                 (double*)c->scratch, c->status, c->stream, cand[k], ibb ? &ia : nullptr);
       c->launches++;
     }
     cudaEventRecord(e1, c->stream);
@@ -834,7 +871,7 @@ RWMI_API rwmi_status rwmi_footprint(const int32_t dims[3], int32_t q, int32_t st
   const uint64_t pad = (ncell + 63) / 64 * 64, sb = storage_bytes(storage), P = (uint64_t)n_particles,
                  Nc = (uint64_t)n_centers, N = (uint64_t)n_walkers;
   uint64_t b = 2 * (uint64_t)q * pad * sb;                     // populations A/B
-  b += 2 * 16 * pad + 2 * 2 * ncell + 8 * ncell + 4 * (ncell / 2048 + 2);   // (u, rho), solid, counts/offsets, scan
+  b += 2 * 16 * pad + 2 * 2 * ncell + 2 * 2 * ncell + 8 * ncell + 4 * (ncell / 2048 + 2);   // (u, rho), solid, nodes, counts/offsets, scan
   b += 2 * (4 * (nbrick + 1) + 2 * MAXC * nbrick + 4 * nbrick) + 2 * 8 * nbrick;   // bricks, masks
   b += 100 * N;                                                // pos, x0 (A/B), rank, resolve list
   b += 2 * (48 + 80) * P + 2 * 16 * Nc + sizeof(ParticleDesc) * P + 16 * Nc + 2 * 8 * (6 * P + 4 * RED_SLOTS);
@@ -958,6 +995,28 @@ RWMI_API rwmi_status rwmi_solid(rwmi_ctx* c, int32_t* count, int32_t* owner) {
   s = copy_out(c, count, tmp, sizeof(int32_t) * (size_t)c->ncell);
   if (s != RWMI_OK) return s;
   return copy_out(c, owner, tmp + c->ncell, sizeof(int32_t) * (size_t)c->ncell);
+}
+
+RWMI_API rwmi_status rwmi_nodes(rwmi_ctx* c, int32_t* node) {
+  if (!c || !node) return RWMI_E_INVALID;
+  const int par = (int)(c->t & 1);
+  const size_t n = (size_t)c->ncell;
+  rwmi_status s = ensure_scratch(c, (sizeof(uint16_t) + sizeof(int32_t)) * n + 256);
+  if (s != RWMI_OK) return s;
+  uint16_t* tmp = (uint16_t*)c->scratch;
+  if (c->P > 0) {
+    launch_nodes(c->cfg.q, c->cfg.storage, c->g, particle_set(c), brick_set(c, par), tmp, tmp, c->f[c->fcur],
+                 c->cfg.rho0, false, c->stream);
+    c->launches++;
+  } else {
+    CK(cudaMemsetAsync(tmp, 0, sizeof(uint16_t) * n, c->stream));
+  }
+  std::vector<uint16_t> h(n);
+  CK(copy_now(c, h.data(), tmp, sizeof(uint16_t) * n));
+  std::vector<int32_t> o(n);
+  for (size_t k = 0; k < n; ++k) o[k] = h[k];
+  CK(copy_now(c, node, o.data(), sizeof(int32_t) * n));
+  return RWMI_OK;
 }
 
 RWMI_API rwmi_status rwmi_mass_momentum(rwmi_ctx* c, double out[4]) {
@@ -1235,7 +1294,7 @@ RWMI_API void rwmi_destroy(rwmi_ctx* c) {
     dfree(c, c->pose[k]); dfree(c, c->sp[k]); dfree(c, c->cworld[k]); dfree(c, c->pos[k]); dfree(c, c->x0[k]);
   }
   dfree(c, c->wlist); dfree(c, c->wlist_n);
-  dfree(c, c->u[0]); dfree(c, c->u[1]); dfree(c, c->solid[0]); dfree(c, c->solid[1]); dfree(c, c->d_T); dfree(c, c->status); dfree(c, c->macc);
+  dfree(c, c->u[0]); dfree(c, c->u[1]); dfree(c, c->solid[0]); dfree(c, c->solid[1]); dfree(c, c->node[0]); dfree(c, c->node[1]); dfree(c, c->d_T); dfree(c, c->status); dfree(c, c->macc);
   dfree(c, c->series); dfree(c, c->mrow); dfree(c, c->desc); dfree(c, c->cbody); dfree(c, c->rank);
   dfree(c, c->counts); dfree(c, c->offsets); dfree(c, c->bsums); dfree(c, c->scratch); dfree(c, c->wmask[0]); dfree(c, c->wmask[1]);
   cudaStreamSynchronize(c->stream);   // the frees have returned the memory when this returns

@@ -626,6 +626,60 @@ void launch_density(int q, int storage, const Geom& g, const void* f, double rho
   RWMI_DISPATCH(q, storage, density_kernel, g, f, rho0, out);
 }
 
+// IBB node classes (Section 2.4.3): a cell centre is solid when Eq. 3 of some particle reaches 1
+// there (binary32, the CPU oracle's operation order), owned by the lowest such particle index.
+// Only cells of flagged bricks can be solid. With refill, a node solid in prev and fluid now gets
+// G^eq(rho0, u_new) with u_new its former particle's rigid velocity (Eq. 27).
+template <int Q, int STORE>
+__global__ void node_kernel(Geom g, ParticleSet ps, BrickSet bs, const uint16_t* __restrict__ prev,
+                            uint16_t* __restrict__ cur, void* f_, double rho0_d, int refill) {
+  using L = Lat<Q>;
+  using S = Store<STORE>;
+  using R = typename S::R;
+  const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.ncell) return;
+  const uint32_t z = fast_div(c, g.mxy, g.sxy), rem = c - z * g.nxy;
+  const uint32_t y = fast_div(rem, g.mx, g.sx), x = rem - y * g.n[0];
+  const uint32_t b = ((z >> 3) * (uint32_t)g.nb[1] + (y >> 3)) * (uint32_t)g.nb[0] + (x >> 3);
+  const uint32_t w = bs.bword[b];
+  int node = 0;
+  if (w >> 16) {
+    const float xs = (float)x + 0.5f, ys = (float)y + 0.5f, zs = (float)z + 0.5f;
+    const uint32_t nc = w & 0xffffu;
+    if (nc > MAXC) {
+      for (int p = 0; p < ps.P && node == 0; ++p)
+        if (metaball_exact(bs.cworld, ps.desc[p].c0, ps.desc[p].c1, xs, ys, zs, g) >= 1.0f) node = p + 1;
+    } else {
+      int best = 0x7fffffff;
+      for (uint32_t m = 0; m < nc; ++m) {
+        const int p = bs.bcand[b * MAXC + m] & 0x7fff;
+        if (p < best && metaball_exact(bs.cworld, ps.desc[p].c0, ps.desc[p].c1, xs, ys, zs, g) >= 1.0f) best = p;
+      }
+      if (best != 0x7fffffff) node = best + 1;
+    }
+  }
+  cur[c] = (uint16_t)node;
+  if (refill && node == 0 && prev[c] != 0) {
+    R un[3];
+    rigid_velocity<R>(g, bs.pose, bs.posed, (int)prev[c] - 1, (R)x + R(0.5), (R)y + R(0.5), (R)z + R(0.5), un);
+    const R rho0 = (R)rho0_d, uu = un[0] * un[0] + un[1] * un[1] + un[2] * un[2];
+    typename S::T* f = (typename S::T*)f_;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const R eu = (R)L::e(i, 0) * un[0] + (R)L::e(i, 1) * un[1] + (R)L::e(i, 2) * un[2];
+      const R dev = R(3) * eu + R(4.5) * eu * eu - R(1.5) * uu;
+      const R wi = L::template wt<R>(i);
+      S::st(f + (size_t)i * g.ncell_pad + c, S::shifted ? wi * rho0 * dev : wi * rho0 * (R(1) + dev));
+    }
+  }
+}
+
+void launch_nodes(int q, int storage, const Geom& g, const ParticleSet& ps, BrickSet bs,
+                  const uint16_t* prev, uint16_t* cur, void* f, double rho0, bool refill,
+                  cudaStream_t st) {
+  RWMI_DISPATCH(q, storage, node_kernel, g, ps, bs, prev, cur, f, rho0, refill ? 1 : 0);
+}
+
 __global__ void unpack_solid_kernel(Geom g, const uint16_t* solid, const uint32_t* bword,
                                     int32_t* count, int32_t* owner) {
   const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;

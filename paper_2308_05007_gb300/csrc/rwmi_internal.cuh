@@ -216,10 +216,22 @@ void launch_pose_bin(const Geom& g, const ParticleSet& ps, BrickSet bs, const in
                      double* forces, cudaStream_t st);
 void launch_raster(const Geom& g, const ParticleSet& ps, BrickSet bs, uint16_t* solid,
                    unsigned long long* status, int nsm, cudaStream_t st);
+// Extra inputs of the IBB coupling: node classes of this time, (u, rho) of the previous update,
+// particle descriptors (control point ranges). nullptr selects the partially saturated cells.
+struct IbbArgs {
+  const uint16_t* nodes = nullptr;
+  const float4* uprev = nullptr;
+  const ParticleDesc* desc = nullptr;
+};
 void launch_lbm(int q, int storage, bool reduce, const Geom& g, const void* fin, void* fout,
                 float* u, const uint16_t* solid, BrickSet bs, double tau, double rho0,
                 double* red, double* forces, unsigned long long* status, cudaStream_t st,
-                int block = 256);
+                int block = 256, const IbbArgs* ibb = nullptr);
+// IBB node classes at time t (bricks bs of that time) into cur; with refill, nodes solid in prev
+// and fluid now get the equilibrium at their former particle's rigid velocity (Eq. 27).
+void launch_nodes(int q, int storage, const Geom& g, const ParticleSet& ps, BrickSet bs,
+                  const uint16_t* prev, uint16_t* cur, void* f, double rho0, bool refill,
+                  cudaStream_t st);
 void launch_init_populations(int q, int storage, const Geom& g, void* f, double rho0,
                              const double u0[3], float* u, cudaStream_t st);
 // Time of a launch: *d_T (the step counter at the start of the current run of steps, advanced

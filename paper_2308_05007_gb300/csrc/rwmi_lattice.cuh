@@ -74,4 +74,33 @@ template <> struct Store<3> {   // binary64 f_i - w_i rho0, binary64 arithmetic 
   __device__ static void st(T* p, R v) { *p = v; }
 };
 
+// Pose of particle p in the arithmetic type: the binary64 copy for the binary64 update.
+template <typename R>
+__device__ __forceinline__ void load_pose(const PoseF* pose, const PoseD* posed, int p, R* o, R* v, R* w) {
+  if (sizeof(R) == 8) {
+    const PoseD& q = posed[p];
+    for (int a = 0; a < 3; ++a) { o[a] = (R)q.o[a]; v[a] = (R)q.v[a]; w[a] = (R)q.w[a]; }
+  } else {
+    const PoseF q = pose[p];
+    for (int a = 0; a < 3; ++a) { o[a] = (R)q.o[a]; v[a] = (R)q.v[a]; w[a] = (R)q.w[a]; }
+  }
+}
+
+// Rigid velocity v_p + omega_p x (x - o_p) of particle p at the point (x, y, z), minimum image.
+template <typename R>
+__device__ __forceinline__ void rigid_velocity(const Geom& g, const PoseF* pose, const PoseD* posed, int p,
+                                               R x, R y, R z, R* u) {
+  R po[3], pv[3], pw[3];
+  load_pose<R>(pose, posed, p, po, pv, pw);
+  R r[3] = {x - po[0], y - po[1], z - po[2]};
+  for (int a = 0; a < 3; ++a)
+    if (!g.wall[a]) {
+      const R na = (R)g.n[a];
+      if (r[a] > R(0.5) * na) r[a] -= na; else if (r[a] < -R(0.5) * na) r[a] += na;
+    }
+  u[0] = pv[0] + pw[1] * r[2] - pw[2] * r[1];
+  u[1] = pv[1] + pw[2] * r[0] - pw[0] * r[2];
+  u[2] = pv[2] + pw[0] * r[1] - pw[1] * r[0];
+}
+
 }  // namespace rwmi

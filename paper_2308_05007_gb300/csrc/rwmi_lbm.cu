@@ -18,20 +18,29 @@ template <int Q, typename T> struct Planes {
   T* out[Q];
 };
 
-// Pose of particle p in the arithmetic type: the binary64 copy for the binary64 update.
-template <typename R>
-__device__ __forceinline__ void load_pose(const PoseF* pose, const PoseD* posed, int p, R* o, R* v, R* w) {
-  if (sizeof(R) == 8) {
-    const PoseD& q = posed[p];
-    for (int a = 0; a < 3; ++a) { o[a] = (R)q.o[a]; v[a] = (R)q.v[a]; w[a] = (R)q.w[a]; }
-  } else {
-    const PoseF q = pose[p];
-    for (int a = 0; a < 3; ++a) { o[a] = (R)q.o[a]; v[a] = (R)q.v[a]; w[a] = (R)q.w[a]; }
+// q of Eq. 25: 24 binary32 bisection steps on Eq. 3 of one particle along x_f + s e, s in [0, 1]
+// (the CPU oracle's sequence: midpoint 0.5 (lo + hi), point x_f + mid e), q = the bracket's
+// middle. Out of line: every unrolled link of the LBM kernel calls it.
+__device__ __noinline__ float ibb_link_q(const float4* __restrict__ cw, int c0, int c1, float x0, float y0,
+                                         float z0, int ex, int ey, int ez, const Geom& g) {
+  float lo = 0.0f, hi = 1.0f;
+  for (int it = 0; it < 24; ++it) {
+    const float mid = __fmul_rn(0.5f, __fadd_rn(lo, hi));
+    const float xm = __fadd_rn(x0, __fmul_rn(mid, (float)ex));
+    const float ym = __fadd_rn(y0, __fmul_rn(mid, (float)ey));
+    const float zm = __fadd_rn(z0, __fmul_rn(mid, (float)ez));
+    if (metaball_exact(cw, c0, c1, xm, ym, zm, g) >= 1.0f) hi = mid; else lo = mid;
   }
+  return __fmul_rn(0.5f, __fadd_rn(lo, hi));
 }
 
-template <int Q, int STORE, bool WALLS, bool REDUCE>
-__global__ void __launch_bounds__(256, sizeof(typename Store<STORE>::R) == 8 ? 2 : 4)
+// IBB: the paper's coupling (Section 2.4.3) instead of partially saturated cells. A cell of a
+// flagged brick reads its node class; a solid node holds the equilibrium at its particle's rigid
+// velocity; a fluid node replaces the population pulled from each solid neighbour by Eqs. 23-25
+// (q by the same binary32 bisection as the CPU oracle) and, on reduction steps, adds the
+// Galilean-invariant momentum exchange of the link to its particle's force and torque.
+template <int Q, int STORE, bool WALLS, bool REDUCE, bool IBB>
+__global__ void __launch_bounds__(256, (sizeof(typename Store<STORE>::R) == 8 || IBB) ? 2 : 4)
 lbm_kernel(Geom g, Planes<Q, typename Store<STORE>::T> pl,
                                                   float4* __restrict__ u4,
                                                   const uint16_t* __restrict__ solid,
@@ -41,7 +50,11 @@ lbm_kernel(Geom g, Planes<Q, typename Store<STORE>::T> pl,
                                                   const StepParams* __restrict__ sp,
                                                   typename Store<STORE>::R tau,
                                                   typename Store<STORE>::R rho0, double* __restrict__ red,
-                                                  double* __restrict__ forces) {
+                                                  double* __restrict__ forces,
+                                                  const uint16_t* __restrict__ nodes,
+                                                  const float4* __restrict__ uprev,
+                                                  const ParticleDesc* __restrict__ desc,
+                                                  const float4* __restrict__ cworld) {
   using L = Lat<Q>;
   using S = Store<STORE>;
   using R = typename S::R;   // arithmetic type: binary32, or binary64 for the binary64 storage
@@ -87,6 +100,105 @@ lbm_kernel(Geom g, Planes<Q, typename Store<STORE>::T> pl,
       f[i] = blk ? S::ld(pl.in[L::opp(i)] + c) : S::ld(pl.in[i] + (c + off));
     }
   }
+  // ---- the paper's coupling: IBB links of a fluid node next to solid nodes (Eqs. 23-25) ----
+  bool solid_self = false;
+  R Fib[3] = {R(0), R(0), R(0)}, Tib[3] = {R(0), R(0), R(0)};
+  int ib_owner = -1;
+  if constexpr (IBB) {
+    const uint32_t bq = ((z >> 3) * (uint32_t)g.nb[1] + (y >> 3)) * (uint32_t)g.nb[0] + (x >> 3);
+    if (bword[bq] >> 16) {   // cells of other bricks have no solid neighbour (brick radius >= rb + sqrt 3)
+      if (nodes[c] != 0) {
+        solid_self = true;
+      } else {
+        const bool wx_p = WALLS && g.wall[0] && x == 0, wx_m = WALLS && g.wall[0] && (int)x == nx - 1;
+        const bool wy_p = WALLS && g.wall[1] && y == 0, wy_m = WALLS && g.wall[1] && (int)y == ny - 1;
+        const bool wz_p = WALLS && g.wall[2] && z == 0, wz_m = WALLS && g.wall[2] && (int)z == nz - 1;
+        auto off_of = [&](int i) {
+          const int ex = L::e(i, 0), ey = L::e(i, 1), ez = L::e(i, 2);
+          return (ex > 0 ? ox_p : ex < 0 ? ox_m : 0) + (ey > 0 ? oy_p : ey < 0 ? oy_m : 0) +
+                 (ez > 0 ? oz_p : ez < 0 ? oz_m : 0);
+        };
+        auto blocked = [&](int i) {   // x - e_i beyond a plane wall
+          const int ex = L::e(i, 0), ey = L::e(i, 1), ez = L::e(i, 2);
+          return (ex > 0 && wx_p) || (ex < 0 && wx_m) || (ey > 0 && wy_p) || (ey < 0 && wy_m) ||
+                 (ez > 0 && wz_p) || (ez < 0 && wz_m);
+        };
+        bool have = false;
+        R rho_f = R(0), uf[3] = {R(0), R(0), R(0)};
+        const float x0 = (float)x + 0.5f, y0 = (float)y + 0.5f, z0 = (float)z + 0.5f;
+#pragma unroll   // f[i] must stay in registers: a run-time index would put f in local memory
+        for (int i = 1; i < Q; ++i) {
+          if (blocked(i)) continue;
+          const int ns = (int)nodes[c + off_of(i)];
+          if (ns == 0) continue;
+          if (!have) {   // rho_f: x_f's own post-collision populations; u_f: the previous update
+            R sum = R(0);
+            for (int j = 0; j < Q; ++j) sum += S::ld(pl.in[j] + c);
+            rho_f = S::shifted ? rho0 + sum : sum;
+            const float4 v = uprev[c];
+            uf[0] = (R)v.x; uf[1] = (R)v.y; uf[2] = (R)v.z;
+            have = true;
+          }
+          const int p = ns - 1, ip = L::opp(i);
+          const int ex = L::e(ip, 0), ey = L::e(ip, 1), ez = L::e(ip, 2);   // into the wall
+          const R qf = (R)ibb_link_q(cworld, desc[p].c0, desc[p].c1, x0, y0, z0, ex, ey, ez, g);
+          const R xw[3] = {(R)x + R(0.5) + qf * (R)ex, (R)y + R(0.5) + qf * (R)ey, (R)z + R(0.5) + qf * (R)ez};
+          R uw[3];
+          rigid_velocity<R>(g, pose, posed, p, xw[0], xw[1], xw[2], uw);
+          R uff[3] = {uf[0], uf[1], uf[2]};
+          if (!blocked(ip)) {   // x_ff = x_f + e_i, unless solid or beyond a wall
+            const int cf = c + off_of(ip);
+            if (nodes[cf] == 0) {
+              const float4 v = uprev[cf];
+              uff[0] = (R)v.x; uff[1] = (R)v.y; uff[2] = (R)v.z;
+            }
+          }
+          R ud[3];
+          for (int a = 0; a < 3; ++a) {
+            const R us1 = qf <= R(0.5) ? R(2) * qf * uf[a] + (R(1) - R(2) * qf) * uff[a]
+                                       : (R(1) - qf) / qf * uf[a] + (R(2) * qf - R(1)) / qf * uw[a];
+            const R us2 = (R(1) - qf) / (R(1) + qf) * uff[a] + R(2) * qf / (R(1) + qf) * uw[a];
+            ud[a] = us1 / R(3) + R(2) * us2 / R(3);
+          }
+          const R w = L::template wt<R>(ip);
+          const R eud = (R)ex * ud[0] + (R)ey * ud[1] + (R)ez * ud[2];
+          const R euf = (R)ex * uf[0] + (R)ey * uf[1] + (R)ez * uf[2];
+          const R uud = ud[0] * ud[0] + ud[1] * ud[1] + ud[2] * ud[2];
+          const R uuf = uf[0] * uf[0] + uf[1] * uf[1] + uf[2] * uf[2];
+          const R euw = -((R)ex * uw[0] + (R)ey * uw[1] + (R)ez * uw[2]);   // e_i . u_w, e_i = -e_ip
+          const R Gp = S::ld(pl.in[ip] + c);
+          // G^eq_ip(rho_f, u_d) + G^neq_ip(x_f) + 6 w rho_f e_i.u_w; the storage shift cancels
+          const R G = Gp + w * rho_f * (R(3) * (eud - euf) + R(4.5) * (eud * eud - euf * euf) - R(1.5) * (uud - uuf)) +
+                      R(6) * w * rho_f * euw;
+          f[i] = G;
+          if (REDUCE && valid) {   // (e_ip - u_w) G+_ip - (e_i - u_w) G_i on particle p; torque about its origin
+            const R sh = S::shifted ? w * rho0 : R(0);
+            const R gp = Gp + sh, gi = G + sh;
+            const R Fl[3] = {((R)ex - uw[0]) * gp - (-(R)ex - uw[0]) * gi, ((R)ey - uw[1]) * gp - (-(R)ey - uw[1]) * gi,
+                             ((R)ez - uw[2]) * gp - (-(R)ez - uw[2]) * gi};
+            R po[3], pv[3], pw[3];
+            load_pose<R>(pose, posed, p, po, pv, pw);
+            R r[3] = {xw[0] - po[0], xw[1] - po[1], xw[2] - po[2]};
+            for (int a = 0; a < 3; ++a)
+              if (!g.wall[a]) {
+                const R na = (R)g.n[a];
+                if (r[a] > R(0.5) * na) r[a] -= na; else if (r[a] < -R(0.5) * na) r[a] += na;
+              }
+            const R Tl[3] = {r[1] * Fl[2] - r[2] * Fl[1], r[2] * Fl[0] - r[0] * Fl[2], r[0] * Fl[1] - r[1] * Fl[0]};
+            if (ib_owner < 0 || ib_owner == p) {
+              ib_owner = p;
+              for (int a = 0; a < 3; ++a) { Fib[a] += Fl[a]; Tib[a] += Tl[a]; }
+            } else {   // a second particle at one node: rare, direct atomics
+              for (int a = 0; a < 3; ++a) {
+                atomicAdd(&forces[6 * p + a], (double)Fl[a]);
+                atomicAdd(&forces[6 * p + 3 + a], (double)Tl[a]);
+              }
+            }
+          }
+        }
+      }
+    }
+  }
   // moments (Eqs. 14-15); with shifted storage f holds f_i - w_i rho0
   R drho = R(0.0), jx = R(0.0), jy = R(0.0), jz = R(0.0);
 #pragma unroll
@@ -107,7 +219,7 @@ lbm_kernel(Geom g, Planes<Q, typename Store<STORE>::T> pl,
   // partially saturated cell: solid word valid only in bricks flagged for this time
   R B = R(0.0), usx = R(0.0), usy = R(0.0), usz = R(0.0);
   int owner = -1;
-  {
+  if constexpr (!IBB) {
     const uint32_t b = ((z >> 3) * (uint32_t)g.nb[1] + (y >> 3)) * (uint32_t)g.nb[0] + (x >> 3);
     if (bword[b] >> 16) {
       const uint16_t sw = solid[c];
@@ -172,20 +284,37 @@ lbm_kernel(Geom g, Planes<Q, typename Store<STORE>::T> pl,
       dpx += dm * ex; dpy += dm * ey; dpz += dm * ez;
     }
   }
+  if (IBB && solid_self) {   // solid node: equilibrium at the particle's rigid velocity, rho0
+    R us[3];
+    rigid_velocity<R>(g, pose, posed, (int)nodes[c] - 1, (R)x + R(0.5), (R)y + R(0.5), (R)z + R(0.5), us);
+    const R uus = us[0] * us[0] + us[1] * us[1] + us[2] * us[2];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const R eu = (R)L::e(i, 0) * us[0] + (R)L::e(i, 1) * us[1] + (R)L::e(i, 2) * us[2];
+      const R dev = R(3) * eu + R(4.5) * eu * eu - R(1.5) * uus;
+      const R wi = L::template wt<R>(i);
+      out[i] = S::shifted ? wi * rho0 * dev : wi * rho0 * (R(1) + dev);
+    }
+    if (valid) u4[c] = make_float4((float)us[0], (float)us[1], (float)us[2], (float)rho0);
+  } else if (valid) {
+    u4[c] = make_float4((float)ux, (float)uy, (float)uz, (float)rho);
+  }
   if (valid) {
 #pragma unroll
     for (int i = 0; i < Q; ++i) S::st(pl.out[i] + c, out[i]);
-    u4[c] = make_float4((float)ux, (float)uy, (float)uz, (float)rho);
   }
   // hydrodynamic force on the owner particle: -B sum_i Omega_i e_i; torque about its origin.
   // Formed, like the mass/momentum sums, only on the step whose sums are read (REDUCE); the
   // accumulators of every other step are cleared again before anyone reads them.
   const unsigned full = 0xffffffffu;
-  const bool hasF = owner >= 0;
+  const bool hasF = IBB ? (ib_owner >= 0) : (owner >= 0);
+  if (IBB) owner = ib_owner;
   if (REDUCE && __any_sync(full, hasF)) {
     R Fc[3] = {-dpx, -dpy, -dpz};
     R Tc[3] = {R(0.0), R(0.0), R(0.0)};
-    if (hasF) {
+    if (IBB) {   // link forces and torques summed above
+      for (int a = 0; a < 3; ++a) { Fc[a] = Fib[a]; Tc[a] = Tib[a]; }
+    } else if (hasF) {
       R po[3], pv[3], pw[3];
       load_pose<R>(pose, posed, owner, po, pv, pw);
       R r[3] = {(R)x + R(0.5) - po[0], (R)y + R(0.5) - po[1], (R)z + R(0.5) - po[2]};
@@ -221,8 +350,9 @@ lbm_kernel(Geom g, Planes<Q, typename Store<STORE>::T> pl,
   if (REDUCE) {   // sums of (rho - rho0) and sum_i f_i e_i (pre-collision): the arithmetic type
                   // within the block (256 small deviations), FP64 across blocks (GB300's FP64
                   // pipe is narrow)
-    R v[4] = {valid ? (S::shifted ? drho : rho - rho0) : R(0.0), valid ? jx : R(0.0),
-                  valid ? jy : R(0.0), valid ? jz : R(0.0)};
+    const bool fl = valid && !solid_self;   // fluid nodes only (solid nodes: IBB)
+    R v[4] = {fl ? (S::shifted ? drho : rho - rho0) : R(0.0), fl ? jx : R(0.0),
+                  fl ? jy : R(0.0), fl ? jz : R(0.0)};
 #pragma unroll
     for (int m = 0; m < 4; ++m)
 #pragma unroll
@@ -240,10 +370,10 @@ lbm_kernel(Geom g, Planes<Q, typename Store<STORE>::T> pl,
   }
 }
 
-template <int Q, int STORE>
+template <int Q, int STORE, bool IBB>
 static void launch_lbm_q(bool walls, bool reduce, const Geom& g, const void* fin, void* fout, float* u,
                          const uint16_t* solid, BrickSet bs, double tau, double rho0, double* red,
-                         double* forces, cudaStream_t st, int bsz) {
+                         double* forces, cudaStream_t st, int bsz, const IbbArgs& ib) {
   using T = typename Store<STORE>::T;
   using R = typename Store<STORE>::R;
   Planes<Q, T> pl;
@@ -255,30 +385,41 @@ static void launch_lbm_q(bool walls, bool reduce, const Geom& g, const void* fin
   const int bsz_ok = (bsz == 64 || bsz == 128) ? bsz : 256;
   const dim3 grid((g.ncell + bsz_ok - 1) / bsz_ok), block(bsz_ok);
   if (walls) {
-    if (reduce) lbm_kernel<Q, STORE, true, true><<<grid, block, 0, st>>>(g, pl, u4, solid, bs.bword, bs.pose, bs.posed, bs.sp, (R)tau, (R)rho0, red, forces);
-    else lbm_kernel<Q, STORE, true, false><<<grid, block, 0, st>>>(g, pl, u4, solid, bs.bword, bs.pose, bs.posed, bs.sp, (R)tau, (R)rho0, red, forces);
+    if (reduce) lbm_kernel<Q, STORE, true, true, IBB><<<grid, block, 0, st>>>(g, pl, u4, solid, bs.bword, bs.pose, bs.posed, bs.sp, (R)tau, (R)rho0, red, forces, ib.nodes, ib.uprev, ib.desc, bs.cworld);
+    else lbm_kernel<Q, STORE, true, false, IBB><<<grid, block, 0, st>>>(g, pl, u4, solid, bs.bword, bs.pose, bs.posed, bs.sp, (R)tau, (R)rho0, red, forces, ib.nodes, ib.uprev, ib.desc, bs.cworld);
   } else {
-    if (reduce) lbm_kernel<Q, STORE, false, true><<<grid, block, 0, st>>>(g, pl, u4, solid, bs.bword, bs.pose, bs.posed, bs.sp, (R)tau, (R)rho0, red, forces);
-    else lbm_kernel<Q, STORE, false, false><<<grid, block, 0, st>>>(g, pl, u4, solid, bs.bword, bs.pose, bs.posed, bs.sp, (R)tau, (R)rho0, red, forces);
+    if (reduce) lbm_kernel<Q, STORE, false, true, IBB><<<grid, block, 0, st>>>(g, pl, u4, solid, bs.bword, bs.pose, bs.posed, bs.sp, (R)tau, (R)rho0, red, forces, ib.nodes, ib.uprev, ib.desc, bs.cworld);
+    else lbm_kernel<Q, STORE, false, false, IBB><<<grid, block, 0, st>>>(g, pl, u4, solid, bs.bword, bs.pose, bs.posed, bs.sp, (R)tau, (R)rho0, red, forces, ib.nodes, ib.uprev, ib.desc, bs.cworld);
   }
 }
 
 void launch_lbm(int q, int storage, bool reduce, const Geom& g, const void* fin, void* fout,
                 float* u, const uint16_t* solid, BrickSet bs, double tau, double rho0, double* red,
-                double* forces, unsigned long long* status, cudaStream_t st, int block) {
+                double* forces, unsigned long long* status, cudaStream_t st, int block, const IbbArgs* ibb) {
   (void)status;
   const bool walls = g.wall[0] || g.wall[1] || g.wall[2];
+  const IbbArgs none{};
+  const IbbArgs& ib = ibb ? *ibb : none;
+  // IBB is built for binary32-shifted and binary64 storage (the configuration check refuses the
+  // others); the other storages run the partially saturated cells only
+#define RWMI_LBM_PSM(QQ, SS) \
+  launch_lbm_q<QQ, SS, false>(walls, reduce, g, fin, fout, u, solid, bs, tau, rho0, red, forces, st, block, ib)
+#define RWMI_LBM_CASE(QQ, SS)                                                                           \
+  if (ibb) launch_lbm_q<QQ, SS, true>(walls, reduce, g, fin, fout, u, solid, bs, tau, rho0, red, forces, st, block, ib); \
+  else RWMI_LBM_PSM(QQ, SS)
   if (q == 15) {
-    if (storage == 0) launch_lbm_q<15, 0>(walls, reduce, g, fin, fout, u, solid, bs, tau, rho0, red, forces, st, block);
-    else if (storage == 1) launch_lbm_q<15, 1>(walls, reduce, g, fin, fout, u, solid, bs, tau, rho0, red, forces, st, block);
-    else if (storage == 2) launch_lbm_q<15, 2>(walls, reduce, g, fin, fout, u, solid, bs, tau, rho0, red, forces, st, block);
-    else launch_lbm_q<15, 3>(walls, reduce, g, fin, fout, u, solid, bs, tau, rho0, red, forces, st, block);
+    if (storage == 0) { RWMI_LBM_PSM(15, 0); }
+    else if (storage == 1) { RWMI_LBM_CASE(15, 1); }
+    else if (storage == 2) { RWMI_LBM_PSM(15, 2); }
+    else { RWMI_LBM_CASE(15, 3); }
   } else {
-    if (storage == 0) launch_lbm_q<19, 0>(walls, reduce, g, fin, fout, u, solid, bs, tau, rho0, red, forces, st, block);
-    else if (storage == 1) launch_lbm_q<19, 1>(walls, reduce, g, fin, fout, u, solid, bs, tau, rho0, red, forces, st, block);
-    else if (storage == 2) launch_lbm_q<19, 2>(walls, reduce, g, fin, fout, u, solid, bs, tau, rho0, red, forces, st, block);
-    else launch_lbm_q<19, 3>(walls, reduce, g, fin, fout, u, solid, bs, tau, rho0, red, forces, st, block);
+    if (storage == 0) { RWMI_LBM_PSM(19, 0); }
+    else if (storage == 1) { RWMI_LBM_CASE(19, 1); }
+    else if (storage == 2) { RWMI_LBM_PSM(19, 2); }
+    else { RWMI_LBM_CASE(19, 3); }
   }
+#undef RWMI_LBM_CASE
+#undef RWMI_LBM_PSM
 }
 
 }  // namespace rwmi

@@ -24,7 +24,7 @@ EXPORTED = ["rwmi_config_defaults", "rwmi_create", "rwmi_configure", "rwmi_set_s
             "rwmi_set_metaballs", "rwmi_seed_walkers", "rwmi_set_walkers", "rwmi_step", "rwmi_step_timed",
             "rwmi_autotune", "rwmi_query", "rwmi_footprint", "rwmi_sync",
             "rwmi_time", "rwmi_info", "rwmi_concentration", "rwmi_walker_moments", "rwmi_moment_series",
-            "rwmi_velocity", "rwmi_density", "rwmi_populations", "rwmi_lattice", "rwmi_solid",
+            "rwmi_velocity", "rwmi_density", "rwmi_populations", "rwmi_lattice", "rwmi_solid", "rwmi_nodes",
             "rwmi_mass_momentum", "rwmi_particle_forces", "rwmi_walkers", "rwmi_counters", "rwmi_save",
             "rwmi_load", "rwmi_brick_stats", "rwmi_bin_walkers_noalloc", "rwmi_last_error",
             "rwmi_launch_count", "rwmi_destroy", "rwmi_batch_create", "rwmi_batch_step", "rwmi_batch_sync",
@@ -46,7 +46,7 @@ class Config(C.Structure):
                 ("body_force", C.c_double * 3), ("force_period", C.c_double), ("rho0", C.c_double),
                 ("init_velocity", C.c_double * 3), ("sort_interval", C.c_int32),
                 ("moment_interval", C.c_int32), ("use_graphs", C.c_int32), ("lbm_block", C.c_int32),
-                ("overlap", C.c_int32)]
+                ("overlap", C.c_int32), ("coupling", C.c_int32)]
 
 
 _lib = None
@@ -101,6 +101,7 @@ def load(build_if_missing: bool = False):
     L.rwmi_moment_series.argtypes = [P, vp, C.c_int32, C.POINTER(C.c_int32)]
     L.rwmi_lattice.argtypes = [P, vp, vp, C.POINTER(C.c_int32)]
     L.rwmi_solid.argtypes = [P, vp, vp]
+    L.rwmi_nodes.argtypes = [P, vp]
     L.rwmi_walkers.argtypes = [P, vp, vp]
     L.rwmi_brick_stats.argtypes = [P, vp]
     L.rwmi_bin_walkers_noalloc.argtypes = [C.POINTER(C.c_int32), C.c_uint32, vp, C.c_int64, vp, vp, vp]
@@ -173,7 +174,7 @@ class Simulation:
     def __init__(self, dims, tau, D, seed=0, q=19, storage=STORE_FP32_SHIFT, wall_mask=0,
                  body_force=(0.0, 0.0, 0.0), force_period=0.0, rho0=1.0, init_velocity=(0.0, 0.0, 0.0),
                  sort_interval=16, moment_interval=0, use_graphs=True, stream=None, lbm_block=256,
-                 overlap=2):
+                 overlap=2, coupling=0):
         L = load()
         self._L = L
         self._h = C.c_void_p()
@@ -194,6 +195,7 @@ class Simulation:
         cfg.use_graphs = 1 if use_graphs else 0
         cfg.lbm_block = int(lbm_block)
         cfg.overlap = int(overlap)
+        cfg.coupling = int(coupling)
         self._check(L.rwmi_configure(self._h, C.byref(cfg)))
         self.q = int(q)
         _live.add(self)
@@ -204,7 +206,8 @@ class Simulation:
     def from_workload(cls, w, seed_walkers=True, **overrides):
         kw = dict(q=w.q, storage=w.storage, wall_mask=w.wall_mask, body_force=w.body_force,
                   force_period=w.force_period, rho0=w.rho0, init_velocity=w.init_velocity,
-                  sort_interval=w.sort_interval, moment_interval=w.moment_interval)
+                  sort_interval=w.sort_interval, moment_interval=w.moment_interval,
+                  coupling=getattr(w, "coupling", 0))
         kw.update(overrides)
         s = cls(w.dims, w.tau, w.D, w.seed, **kw)
         if w.metaballs is not None and w.metaballs.n_particles > 0:
@@ -373,6 +376,12 @@ class Simulation:
         own = np.zeros(self.n_cells, np.int32)
         self._check(self._L.rwmi_solid(self._h, _ptr(cnt), _ptr(own)))
         return cnt, own
+
+    def nodes(self):
+        """IBB node classes of the current time: 0 fluid, 1 + particle index for solid nodes."""
+        out = np.zeros(self.n_cells, np.int32)
+        self._check(self._L.rwmi_nodes(self._h, _ptr(out)))
+        return out
 
     def mass_momentum(self):
         out = np.zeros(4)

@@ -1,0 +1,107 @@
+"""The paper's own coupling on the GPU (Section 2.4.3: IBB, Eqs. 23-25; Galilean-invariant
+momentum exchange; refilling, Eq. 27) against the FP64 CPU oracle.
+
+- Node classes (cell centre inside a particle, binary32 decision) are bit-exact, over a
+  trajectory of moving, spinning particles between walls.
+- One step from identical populations and velocities: q comes out of the same binary32 bisection
+  on both sides, so the populations differ only by the update's arithmetic. Binary64 storage
+  matches to 1e-12 of max|f|. Binary32-shifted storage matches to a few binary32 roundings of
+  the update (2e-6 of max|f| and of max|f - w rho0| ~ 1e-3 of the link terms).
+- Forces and torques from the momentum exchange agree to the same precision.
+- The three step schedules and graph replay give identical results.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+def _need_gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _ibb_workload(storage=1, q=15, walls=4, seed=9):
+    from paper_2308_05007_gb300 import inputs as I
+    return I.with_(I.ragged(q=q, storage=storage, walls=walls, seed=seed), coupling=1)
+
+
+def test_ibb_nodes_bit_exact_along_a_trajectory():
+    _need_gpu()
+    from oracle.oracle import Oracle
+    from paper_2308_05007_gb300.rwmi import Simulation
+    w = _ibb_workload()
+    ora = Oracle.from_workload(w, seed_walkers=False)
+    with Simulation.from_workload(w, seed_walkers=False) as sim:
+        for t in (0, 5, 17, 40):
+            sim.step(t - sim.t)
+            assert np.array_equal(sim.nodes(), ora.nodes(t)), f"t={t}"
+        assert (sim.nodes() > 0).sum() > 50
+
+
+@pytest.mark.parametrize("storage,q", [(1, 15), (1, 19), (3, 15), (3, 19)])
+def test_ibb_one_step_from_identical_state(storage, q):
+    _need_gpu()
+    from oracle.oracle import Oracle, lattice
+    from paper_2308_05007_gb300.rwmi import Simulation
+    w = _ibb_workload(storage=storage, q=q)
+    with Simulation.from_workload(w, seed_walkers=False) as sim:
+        eg, _ = sim.lattice()
+        eo, wts = lattice(q)
+        perm = np.array([int(np.where((eg == eo[i]).all(1))[0][0]) for i in range(q)])
+        sim.step(11)
+        t = sim.t
+        f_prev = sim.populations()[perm]
+        u_prev = sim.velocity().astype(np.float64)   # the previous update's velocity (u_f, u_ff)
+        sim.step(1)
+        f_gpu = sim.populations()[perm]
+        F_gpu = sim.particle_forces()
+        nodes_t = sim.nodes()   # classes of t + 1; the step used those of t
+    ora = Oracle.from_workload(w, seed_walkers=False)
+    ora.set_populations(f_prev)
+    ora.set_velocity(u_prev)
+    ora.set_time(t)
+    fluid_t = ora.nodes(t) == 0
+    ora.step_fluid(1)
+    f_ora = ora.populations()
+    F_ora = ora.forces()
+    assert fluid_t.sum() < ora.n_cells and (ora.nodes(t) != ora.nodes(t - 1)).any()
+    err = np.abs(f_gpu - f_ora)
+    if storage == 3:
+        tol = 1e-12 * np.abs(f_ora).max()
+        ftol = 1e-9
+    else:
+        tol = 2e-6 * np.abs(f_ora).max()
+        ftol = 2e-4
+    assert err.max() <= tol, (err.max(), tol)
+    scale = np.abs(F_ora).max()
+    assert np.abs(F_gpu - F_ora).max() <= ftol * scale, (F_gpu, F_ora)
+    del nodes_t
+
+
+def test_ibb_schedules_and_graphs_agree():
+    _need_gpu()
+    from paper_2308_05007_gb300.rwmi import Simulation
+    w = _ibb_workload()
+    ref = None
+    for overlap in (0, 1, 2):
+        for graphs in (False, True):
+            with Simulation.from_workload(w, seed_walkers=True, overlap=overlap, use_graphs=graphs) as s:
+                s.step(13)
+                pos, _ = s.walkers_by_id()
+                st = (s.populations(), s.velocity(), pos, s.particle_forces())
+            if ref is None:
+                ref = st
+            else:
+                for a, b in zip(ref[:3], st[:3]):
+                    assert np.array_equal(a, b), (overlap, graphs)
+                np.testing.assert_allclose(ref[3], st[3], rtol=1e-12, atol=1e-12 * np.abs(ref[3]).max())
+
+
+def test_ibb_rejects_other_storages():
+    _need_gpu()
+    from paper_2308_05007_gb300.rwmi import RwmiError, Simulation
+    w = _ibb_workload(storage=2)
+    with pytest.raises(RwmiError):
+        Simulation.from_workload(w, seed_walkers=False)
