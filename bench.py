@@ -49,6 +49,7 @@ def parse(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--overlap", type=int, default=2, choices=[0, 1, 2])
+    ap.add_argument("--coupling", type=int, default=0, choices=[0, 1])
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-precision", action="store_true")
     ap.add_argument("--batch-domains", type=int, default=64)
@@ -62,6 +63,7 @@ def parse(argv=None):
 def workload(a):
     from paper_2308_05007_gb300 import inputs as I
     w = I.oscillator(n=a.n, n_particles=a.particles, n_walkers=a.walkers, q=a.q, storage=a.storage)
+    w = I.with_(w, coupling=getattr(a, "coupling", 0))
     return I.with_(w, sort_interval=a.sort_interval, moment_interval=a.moment_interval)
 
 
@@ -245,8 +247,13 @@ def measure_variants(a, stream):
     """The same workload with the other population storages (plain binary32, binary32 shifted by
     w_i rho0, binary16 shifted, binary64 shifted with binary64 arithmetic) and velocity sets
     (D3Q15, the paper's D3Q19): per-phase GPU time of 16 eager steps (CUDA events), LBM kernel
-    HBM fraction and whole-step MLUPS. The binary64 run is bound by GB300's FP64 rate, not HBM."""
+    HBM fraction and whole-step MLUPS. The binary64 run is bound by GB300's FP64 rate, not HBM.
+    Last, the paper's IBB coupling in place of partially saturated cells (graph-replayed step
+    time as well)."""
     import argparse as _ap
+
+    import torch
+    from paper_2308_05007_gb300 import inputs as I
     from paper_2308_05007_gb300.rwmi import Simulation
     peak = float(measured_peaks()["hbm_gbs"])
     out = {}
@@ -268,6 +275,31 @@ def measure_variants(a, stream):
             out[f"D3Q{q}_{STORE_NAMES[storage]}"] = {
                 "lbm_ms": lbm_ms, "lbm_gbs": gbs, "lbm_hbm_frac": gbs / peak,
                 "step_ms_eager": step_ms, "mlups_eager": w.n_cells / (step_ms / 1e3) / 1e6}
+    # the paper's own coupling (IBB + momentum exchange + refilling) instead of partially
+    # saturated cells, binary32 shifted storage; its LBM phase includes the node classification
+    for q in (15, 19):
+        b = _ap.Namespace(**vars(a))
+        b.q, b.storage = q, 1
+        w = I.with_(workload(b), coupling=1)
+        sim = Simulation.from_workload(w, seed_walkers=False)
+        sim.set_stream(stream)
+        sim.seed_walkers(w.n_walkers, *w.walker_box)
+        sim.step(16)
+        ph = sim.step_timed(16)
+        sim.step(32)
+        with torch.cuda.stream(stream):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sim.step(64)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        step_ms = e0.elapsed_time(e1) / 64
+        sim.close()
+        lbm_ms = ph["lbm"] / 16
+        gbs = lbm_bytes_per_launch(w, w.n_cells, 4) / (lbm_ms / 1e3) / 1e9
+        out[f"D3Q{q}_fp32_shift_ibb"] = {
+            "lbm_ms": lbm_ms, "lbm_gbs": gbs, "lbm_hbm_frac": gbs / peak,
+            "step_ms": step_ms, "mlups": w.n_cells / (step_ms / 1e3) / 1e6}
     return out
 
 

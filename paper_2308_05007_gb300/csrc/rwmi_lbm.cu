@@ -20,8 +20,8 @@ template <int Q, typename T> struct Planes {
 
 // q of Eq. 25: 24 binary32 bisection steps on Eq. 3 of one particle along x_f + s e, s in [0, 1]
 // (the CPU oracle's sequence: midpoint 0.5 (lo + hi), point x_f + mid e), q = the bracket's
-// middle. Out of line: every unrolled link of the LBM kernel calls it.
-__device__ __noinline__ float ibb_link_q(const float4* __restrict__ cw, int c0, int c1, float x0, float y0,
+// middle. The LBM kernel calls it from one (not unrolled) loop over the warp's link table.
+__device__ __forceinline__ float ibb_link_q(const float4* __restrict__ cw, int c0, int c1, float x0, float y0,
                                          float z0, int ex, int ey, int ez, const Geom& g) {
   float lo = 0.0f, hi = 1.0f;
   for (int it = 0; it < 24; ++it) {
@@ -105,94 +105,128 @@ lbm_kernel(Geom g, Planes<Q, typename Store<STORE>::T> pl,
   R Fib[3] = {R(0), R(0), R(0)}, Tib[3] = {R(0), R(0), R(0)};
   int ib_owner = -1;
   if constexpr (IBB) {
+    // link table of the warp: q of every (cell, direction) link, computed one link per lane
+    __shared__ float s_q[8][32 * (Q - 1)];
+    __shared__ int s_link[8][32 * (Q - 1)];   // lane | direction << 5 | particle << 10
+    const unsigned fullm = 0xffffffffu;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const bool wx_p = WALLS && g.wall[0] && x == 0, wx_m = WALLS && g.wall[0] && (int)x == nx - 1;
+    const bool wy_p = WALLS && g.wall[1] && y == 0, wy_m = WALLS && g.wall[1] && (int)y == ny - 1;
+    const bool wz_p = WALLS && g.wall[2] && z == 0, wz_m = WALLS && g.wall[2] && (int)z == nz - 1;
+    auto off_of = [&](int i) {
+      const int ex = L::e(i, 0), ey = L::e(i, 1), ez = L::e(i, 2);
+      return (ex > 0 ? ox_p : ex < 0 ? ox_m : 0) + (ey > 0 ? oy_p : ey < 0 ? oy_m : 0) +
+             (ez > 0 ? oz_p : ez < 0 ? oz_m : 0);
+    };
+    auto blocked = [&](int i) {   // x - e_i beyond a plane wall
+      const int ex = L::e(i, 0), ey = L::e(i, 1), ez = L::e(i, 2);
+      return (ex > 0 && wx_p) || (ex < 0 && wx_m) || (ey > 0 && wy_p) || (ey < 0 && wy_m) ||
+             (ez > 0 && wz_p) || (ez < 0 && wz_m);
+    };
+    unsigned lmask = 0u;   // directions i whose source x - e_i is a solid node
     const uint32_t bq = ((z >> 3) * (uint32_t)g.nb[1] + (y >> 3)) * (uint32_t)g.nb[0] + (x >> 3);
-    if (bword[bq] >> 16) {   // cells of other bricks have no solid neighbour (brick radius >= rb + sqrt 3)
+    if (valid && (bword[bq] >> 16)) {   // cells of other bricks have no solid neighbour (radius >= rb + sqrt 3)
       if (nodes[c] != 0) {
         solid_self = true;
       } else {
-        const bool wx_p = WALLS && g.wall[0] && x == 0, wx_m = WALLS && g.wall[0] && (int)x == nx - 1;
-        const bool wy_p = WALLS && g.wall[1] && y == 0, wy_m = WALLS && g.wall[1] && (int)y == ny - 1;
-        const bool wz_p = WALLS && g.wall[2] && z == 0, wz_m = WALLS && g.wall[2] && (int)z == nz - 1;
-        auto off_of = [&](int i) {
-          const int ex = L::e(i, 0), ey = L::e(i, 1), ez = L::e(i, 2);
-          return (ex > 0 ? ox_p : ex < 0 ? ox_m : 0) + (ey > 0 ? oy_p : ey < 0 ? oy_m : 0) +
-                 (ez > 0 ? oz_p : ez < 0 ? oz_m : 0);
-        };
-        auto blocked = [&](int i) {   // x - e_i beyond a plane wall
-          const int ex = L::e(i, 0), ey = L::e(i, 1), ez = L::e(i, 2);
-          return (ex > 0 && wx_p) || (ex < 0 && wx_m) || (ey > 0 && wy_p) || (ey < 0 && wy_m) ||
-                 (ez > 0 && wz_p) || (ez < 0 && wz_m);
-        };
-        bool have = false;
-        R rho_f = R(0), uf[3] = {R(0), R(0), R(0)};
-        const float x0 = (float)x + 0.5f, y0 = (float)y + 0.5f, z0 = (float)z + 0.5f;
+#pragma unroll
+        for (int i = 1; i < Q; ++i)
+          if (!blocked(i) && nodes[c + off_of(i)] != 0) lmask |= 1u << i;
+      }
+    }
+    const int nl = __popc(lmask);
+    int incl = nl;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(fullm, incl, o);
+      if (lane >= o) incl += v;
+    }
+    const int first = incl - nl, total = __shfl_sync(fullm, incl, 31);
+    if (total > 0) {   // warp-uniform
+      int k = first;
+      for (unsigned m = lmask; m; m &= m - 1u) {
+        const int i = __ffs(m) - 1;
+        s_link[wid][k++] = lane | (i << 5) | (((int)nodes[c + off_of(i)] - 1) << 10);
+      }
+      __syncwarp();
+      for (int jl = lane; jl < total; jl += 32) {
+        const int lk = s_link[wid][jl];
+        const uint32_t cc = blockIdx.x * blockDim.x + (uint32_t)(wid * 32 + (lk & 31));   // a valid cell
+        const uint32_t cz = fast_div(cc, g.mxy, g.sxy), cr = cc - cz * g.nxy;
+        const uint32_t cy = fast_div(cr, g.mx, g.sx), cx = cr - cy * g.n[0];
+        const int ip = L::opp((lk >> 5) & 31), p = lk >> 10;
+        s_q[wid][jl] = ibb_link_q(cworld, desc[p].c0, desc[p].c1, (float)cx + 0.5f, (float)cy + 0.5f,
+                                  (float)cz + 0.5f, L::e(ip, 0), L::e(ip, 1), L::e(ip, 2), g);
+      }
+      __syncwarp();
+    }
+    if (lmask) {
+      R rho_f, uf[3];
+      {   // rho_f: x_f's own post-collision populations; u_f: the previous update
+        R sum = R(0);
+#pragma unroll
+        for (int j = 0; j < Q; ++j) sum += S::ld(pl.in[j] + c);
+        rho_f = S::shifted ? rho0 + sum : sum;
+        const float4 v = uprev[c];
+        uf[0] = (R)v.x; uf[1] = (R)v.y; uf[2] = (R)v.z;
+      }
+      int k = first;
 #pragma unroll   // f[i] must stay in registers: a run-time index would put f in local memory
-        for (int i = 1; i < Q; ++i) {
-          if (blocked(i)) continue;
-          const int ns = (int)nodes[c + off_of(i)];
-          if (ns == 0) continue;
-          if (!have) {   // rho_f: x_f's own post-collision populations; u_f: the previous update
-            R sum = R(0);
-            for (int j = 0; j < Q; ++j) sum += S::ld(pl.in[j] + c);
-            rho_f = S::shifted ? rho0 + sum : sum;
-            const float4 v = uprev[c];
-            uf[0] = (R)v.x; uf[1] = (R)v.y; uf[2] = (R)v.z;
-            have = true;
+      for (int i = 1; i < Q; ++i) {
+        if (!((lmask >> i) & 1u)) continue;
+        const int ip = L::opp(i), p = (int)nodes[c + off_of(i)] - 1;
+        const int ex = L::e(ip, 0), ey = L::e(ip, 1), ez = L::e(ip, 2);   // into the wall
+        const R qf = (R)s_q[wid][k++];
+        const R xw[3] = {(R)x + R(0.5) + qf * (R)ex, (R)y + R(0.5) + qf * (R)ey, (R)z + R(0.5) + qf * (R)ez};
+        R uw[3];
+        rigid_velocity<R>(g, pose, posed, p, xw[0], xw[1], xw[2], uw);
+        R uff[3] = {uf[0], uf[1], uf[2]};
+        if (!blocked(ip)) {   // x_ff = x_f + e_i, unless solid or beyond a wall
+          const int cf = c + off_of(ip);
+          if (nodes[cf] == 0) {
+            const float4 v = uprev[cf];
+            uff[0] = (R)v.x; uff[1] = (R)v.y; uff[2] = (R)v.z;
           }
-          const int p = ns - 1, ip = L::opp(i);
-          const int ex = L::e(ip, 0), ey = L::e(ip, 1), ez = L::e(ip, 2);   // into the wall
-          const R qf = (R)ibb_link_q(cworld, desc[p].c0, desc[p].c1, x0, y0, z0, ex, ey, ez, g);
-          const R xw[3] = {(R)x + R(0.5) + qf * (R)ex, (R)y + R(0.5) + qf * (R)ey, (R)z + R(0.5) + qf * (R)ez};
-          R uw[3];
-          rigid_velocity<R>(g, pose, posed, p, xw[0], xw[1], xw[2], uw);
-          R uff[3] = {uf[0], uf[1], uf[2]};
-          if (!blocked(ip)) {   // x_ff = x_f + e_i, unless solid or beyond a wall
-            const int cf = c + off_of(ip);
-            if (nodes[cf] == 0) {
-              const float4 v = uprev[cf];
-              uff[0] = (R)v.x; uff[1] = (R)v.y; uff[2] = (R)v.z;
+        }
+        R ud[3];
+        for (int a = 0; a < 3; ++a) {
+          const R us1 = qf <= R(0.5) ? R(2) * qf * uf[a] + (R(1) - R(2) * qf) * uff[a]
+                                     : (R(1) - qf) / qf * uf[a] + (R(2) * qf - R(1)) / qf * uw[a];
+          const R us2 = (R(1) - qf) / (R(1) + qf) * uff[a] + R(2) * qf / (R(1) + qf) * uw[a];
+          ud[a] = us1 / R(3) + R(2) * us2 / R(3);
+        }
+        const R w = L::template wt<R>(ip);
+        const R eud = (R)ex * ud[0] + (R)ey * ud[1] + (R)ez * ud[2];
+        const R euf = (R)ex * uf[0] + (R)ey * uf[1] + (R)ez * uf[2];
+        const R uud = ud[0] * ud[0] + ud[1] * ud[1] + ud[2] * ud[2];
+        const R uuf = uf[0] * uf[0] + uf[1] * uf[1] + uf[2] * uf[2];
+        const R euw = -((R)ex * uw[0] + (R)ey * uw[1] + (R)ez * uw[2]);   // e_i . u_w, e_i = -e_ip
+        const R Gp = S::ld(pl.in[ip] + c);
+        // G^eq_ip(rho_f, u_d) + G^neq_ip(x_f) + 6 w rho_f e_i.u_w; the storage shift cancels
+        const R G = Gp + w * rho_f * (R(3) * (eud - euf) + R(4.5) * (eud * eud - euf * euf) - R(1.5) * (uud - uuf)) +
+                    R(6) * w * rho_f * euw;
+        f[i] = G;
+        if (REDUCE) {   // (e_ip - u_w) G+_ip - (e_i - u_w) G_i on particle p; torque about its origin
+          const R sh = S::shifted ? w * rho0 : R(0);
+          const R gp = Gp + sh, gi = G + sh;
+          const R Fl[3] = {((R)ex - uw[0]) * gp - (-(R)ex - uw[0]) * gi, ((R)ey - uw[1]) * gp - (-(R)ey - uw[1]) * gi,
+                           ((R)ez - uw[2]) * gp - (-(R)ez - uw[2]) * gi};
+          R po[3], pv[3], pw[3];
+          load_pose<R>(pose, posed, p, po, pv, pw);
+          R r[3] = {xw[0] - po[0], xw[1] - po[1], xw[2] - po[2]};
+          for (int a = 0; a < 3; ++a)
+            if (!g.wall[a]) {
+              const R na = (R)g.n[a];
+              if (r[a] > R(0.5) * na) r[a] -= na; else if (r[a] < -R(0.5) * na) r[a] += na;
             }
-          }
-          R ud[3];
-          for (int a = 0; a < 3; ++a) {
-            const R us1 = qf <= R(0.5) ? R(2) * qf * uf[a] + (R(1) - R(2) * qf) * uff[a]
-                                       : (R(1) - qf) / qf * uf[a] + (R(2) * qf - R(1)) / qf * uw[a];
-            const R us2 = (R(1) - qf) / (R(1) + qf) * uff[a] + R(2) * qf / (R(1) + qf) * uw[a];
-            ud[a] = us1 / R(3) + R(2) * us2 / R(3);
-          }
-          const R w = L::template wt<R>(ip);
-          const R eud = (R)ex * ud[0] + (R)ey * ud[1] + (R)ez * ud[2];
-          const R euf = (R)ex * uf[0] + (R)ey * uf[1] + (R)ez * uf[2];
-          const R uud = ud[0] * ud[0] + ud[1] * ud[1] + ud[2] * ud[2];
-          const R uuf = uf[0] * uf[0] + uf[1] * uf[1] + uf[2] * uf[2];
-          const R euw = -((R)ex * uw[0] + (R)ey * uw[1] + (R)ez * uw[2]);   // e_i . u_w, e_i = -e_ip
-          const R Gp = S::ld(pl.in[ip] + c);
-          // G^eq_ip(rho_f, u_d) + G^neq_ip(x_f) + 6 w rho_f e_i.u_w; the storage shift cancels
-          const R G = Gp + w * rho_f * (R(3) * (eud - euf) + R(4.5) * (eud * eud - euf * euf) - R(1.5) * (uud - uuf)) +
-                      R(6) * w * rho_f * euw;
-          f[i] = G;
-          if (REDUCE && valid) {   // (e_ip - u_w) G+_ip - (e_i - u_w) G_i on particle p; torque about its origin
-            const R sh = S::shifted ? w * rho0 : R(0);
-            const R gp = Gp + sh, gi = G + sh;
-            const R Fl[3] = {((R)ex - uw[0]) * gp - (-(R)ex - uw[0]) * gi, ((R)ey - uw[1]) * gp - (-(R)ey - uw[1]) * gi,
-                             ((R)ez - uw[2]) * gp - (-(R)ez - uw[2]) * gi};
-            R po[3], pv[3], pw[3];
-            load_pose<R>(pose, posed, p, po, pv, pw);
-            R r[3] = {xw[0] - po[0], xw[1] - po[1], xw[2] - po[2]};
-            for (int a = 0; a < 3; ++a)
-              if (!g.wall[a]) {
-                const R na = (R)g.n[a];
-                if (r[a] > R(0.5) * na) r[a] -= na; else if (r[a] < -R(0.5) * na) r[a] += na;
-              }
-            const R Tl[3] = {r[1] * Fl[2] - r[2] * Fl[1], r[2] * Fl[0] - r[0] * Fl[2], r[0] * Fl[1] - r[1] * Fl[0]};
-            if (ib_owner < 0 || ib_owner == p) {
-              ib_owner = p;
-              for (int a = 0; a < 3; ++a) { Fib[a] += Fl[a]; Tib[a] += Tl[a]; }
-            } else {   // a second particle at one node: rare, direct atomics
-              for (int a = 0; a < 3; ++a) {
-                atomicAdd(&forces[6 * p + a], (double)Fl[a]);
-                atomicAdd(&forces[6 * p + 3 + a], (double)Tl[a]);
-              }
+          const R Tl[3] = {r[1] * Fl[2] - r[2] * Fl[1], r[2] * Fl[0] - r[0] * Fl[2], r[0] * Fl[1] - r[1] * Fl[0]};
+          if (ib_owner < 0 || ib_owner == p) {
+            ib_owner = p;
+            for (int a = 0; a < 3; ++a) { Fib[a] += Fl[a]; Tib[a] += Tl[a]; }
+          } else {   // a second particle at one node: rare, direct atomics
+            for (int a = 0; a < 3; ++a) {
+              atomicAdd(&forces[6 * p + a], (double)Fl[a]);
+              atomicAdd(&forces[6 * p + 3 + a], (double)Tl[a]);
             }
           }
         }
