@@ -223,7 +223,7 @@ def run_reference(a, rank):
         "walker_steps_per_s": cb["walker_steps_per_s"],
         "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
         "e2e": {"value": cb["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-        "note": "FP64 CPU oracle (the reference arm of this build); --steps/--warmup are replaced by the bounded sample",
+        "note": "FP64 CPU oracle as the reference arm; --steps/--warmup are replaced by the bounded sample",
     }
     print(json.dumps(line), flush=True)
 
