@@ -326,7 +326,7 @@ struct RasterWarp {
 //     the candidate with most sub-samples, lowest index on ties.
 // All decisions use bounds with a 1e-3 margin and, within 4e-5 of f = 1, the exact binary32
 // sequence shared with the CPU oracle, so counts and owners equal the oracle's bit for bit.
-__global__ void __launch_bounds__(256, 3) raster_kernel(Geom g, ParticleSet ps, BrickSet bs,
+__global__ void __launch_bounds__(256, 4) raster_kernel(Geom g, ParticleSet ps, BrickSet bs,
                                                         uint16_t* __restrict__ solid,
                                                         unsigned long long* __restrict__ status) {
   __shared__ RasterWarp s_rw[RW_WARPS];
@@ -523,7 +523,7 @@ __global__ void __launch_bounds__(256, 3) raster_kernel(Geom g, ParticleSet ps, 
 void launch_raster(const Geom& g, const ParticleSet& ps, BrickSet bs, uint16_t* solid,
                    unsigned long long* status, int nsm, cudaStream_t st) {
   if (ps.P == 0) return;
-  raster_kernel<<<nsm * 3, RW_WARPS * 32, 0, st>>>(g, ps, bs, solid, status);
+  raster_kernel<<<nsm * 4, RW_WARPS * 32, 0, st>>>(g, ps, bs, solid, status);
 }
 
 // ------------------------------------------------------------------------------------------
