@@ -275,7 +275,7 @@ __device__ __noinline__ unsigned resolve_particles(const WalkCtx& c, const float
 // walls. A walker whose mini-brick may meet a particle at t+1 (or whose list overflowed, or whose
 // step was unusually long) is appended to a compact list instead of being written back; pass 2
 // resolves those at full SIMT width, so this kernel carries none of the rare-path code.
-__global__ void __launch_bounds__(256, 4) walker_kernel(WalkCtx c, float4* __restrict__ pos, int64_t n,
+__global__ void __launch_bounds__(256, 6) walker_kernel(WalkCtx c, float4* __restrict__ pos, int64_t n,
                                                         const float* __restrict__ u,
                                                         const int64_t* __restrict__ d_T, int toff,
                                                         float amp, uint32_t k0, uint32_t k1,
