@@ -40,7 +40,7 @@ __device__ __forceinline__ float ibb_link_q(const float4* __restrict__ cw, int c
 // (q by the same binary32 bisection as the CPU oracle) and, on reduction steps, adds the
 // Galilean-invariant momentum exchange of the link to its particle's force and torque.
 template <int Q, int STORE, bool WALLS, bool REDUCE, bool IBB>
-__global__ void __launch_bounds__(256, (sizeof(typename Store<STORE>::R) == 8 || IBB) ? 2 : 6)
+__global__ void __launch_bounds__(256, (sizeof(typename Store<STORE>::R) == 8 || IBB) ? 2 : (Q == 19 ? 5 : 6))
 lbm_kernel(Geom g, Planes<Q, typename Store<STORE>::T> pl,
                                                   float4* __restrict__ u4,
                                                   const uint16_t* __restrict__ solid,
