@@ -367,7 +367,7 @@ void enqueue_step(rwmi_ctx* c, bool reduce) {
     launch_lbm(c->cfg.q, c->cfg.storage, reduce, c->g, c->f[c->fcur], c->f[c->fcur ^ 1], c->u[tp], c->solid[tp],
                brick_set(c, tp), c->tau, c->cfg.rho0, c->acc[tp] + 6 * c->P, c->acc[tp],
                c->status, c->stream, c->cfg.lbm_block, ibb ? &ia : nullptr);
-    c->launches++;
+    c->launches += reduce ? 2 : 1;   // the reduce-only pass on reduction steps
     phase_end(c, RWMI_PHASE_LBM);
     c->fcur ^= 1;
   };

@@ -39,6 +39,10 @@ __device__ __forceinline__ float ibb_link_q(const float4* __restrict__ cw, int c
 // velocity; a fluid node replaces the population pulled from each solid neighbour by Eqs. 23-25
 // (q by the same binary32 bisection as the CPU oracle) and, on reduction steps, adds the
 // Galilean-invariant momentum exchange of the link to its particle's force and torque.
+// REDUCE: a reduce-only pass. It runs after the regular (non-reducing) update on the steps whose
+// sums are read, re-pulls the same input populations and forms the FP64 sums and particle forces,
+// and stores nothing. Stored populations therefore always come from one compiled update, and the
+// reducing and non-reducing steps agree bit for bit.
 template <int Q, int STORE, bool WALLS, bool REDUCE, bool IBB>
 __global__ void __launch_bounds__(256, (sizeof(typename Store<STORE>::R) == 8 || IBB) ? 2 : (Q == 19 ? 5 : 6))
 lbm_kernel(Geom g, Planes<Q, typename Store<STORE>::T> pl,
@@ -318,6 +322,7 @@ lbm_kernel(Geom g, Planes<Q, typename Store<STORE>::T> pl,
       dpx += dm * ex; dpy += dm * ey; dpz += dm * ez;
     }
   }
+  if (!REDUCE) {   // the reduce-only pass stores nothing
   if (IBB && solid_self) {   // solid node: equilibrium at the particle's rigid velocity, rho0
     R us[3];
     rigid_velocity<R>(g, pose, posed, (int)nodes[c] - 1, (R)x + R(0.5), (R)y + R(0.5), (R)z + R(0.5), us);
@@ -336,6 +341,7 @@ lbm_kernel(Geom g, Planes<Q, typename Store<STORE>::T> pl,
   if (valid) {
 #pragma unroll
     for (int i = 0; i < Q; ++i) S::st(pl.out[i] + c, out[i]);
+  }
   }
   // hydrodynamic force on the owner particle: -B sum_i Omega_i e_i; torque about its origin.
   // Formed, like the mass/momentum sums, only on the step whose sums are read (REDUCE); the
@@ -418,13 +424,15 @@ static void launch_lbm_q(bool walls, bool reduce, const Geom& g, const void* fin
   float4* u4 = reinterpret_cast<float4*>(u);
   const int bsz_ok = (bsz == 64 || bsz == 128) ? bsz : 256;
   const dim3 grid((g.ncell + bsz_ok - 1) / bsz_ok), block(bsz_ok);
+#define RWMI_LBM_ARGS g, pl, u4, solid, bs.bword, bs.pose, bs.posed, bs.sp, (R)tau, (R)rho0, red, forces, ib.nodes, ib.uprev, ib.desc, bs.cworld
   if (walls) {
-    if (reduce) lbm_kernel<Q, STORE, true, true, IBB><<<grid, block, 0, st>>>(g, pl, u4, solid, bs.bword, bs.pose, bs.posed, bs.sp, (R)tau, (R)rho0, red, forces, ib.nodes, ib.uprev, ib.desc, bs.cworld);
-    else lbm_kernel<Q, STORE, true, false, IBB><<<grid, block, 0, st>>>(g, pl, u4, solid, bs.bword, bs.pose, bs.posed, bs.sp, (R)tau, (R)rho0, red, forces, ib.nodes, ib.uprev, ib.desc, bs.cworld);
+    lbm_kernel<Q, STORE, true, false, IBB><<<grid, block, 0, st>>>(RWMI_LBM_ARGS);
+    if (reduce) lbm_kernel<Q, STORE, true, true, IBB><<<grid, block, 0, st>>>(RWMI_LBM_ARGS);
   } else {
-    if (reduce) lbm_kernel<Q, STORE, false, true, IBB><<<grid, block, 0, st>>>(g, pl, u4, solid, bs.bword, bs.pose, bs.posed, bs.sp, (R)tau, (R)rho0, red, forces, ib.nodes, ib.uprev, ib.desc, bs.cworld);
-    else lbm_kernel<Q, STORE, false, false, IBB><<<grid, block, 0, st>>>(g, pl, u4, solid, bs.bword, bs.pose, bs.posed, bs.sp, (R)tau, (R)rho0, red, forces, ib.nodes, ib.uprev, ib.desc, bs.cworld);
+    lbm_kernel<Q, STORE, false, false, IBB><<<grid, block, 0, st>>>(RWMI_LBM_ARGS);
+    if (reduce) lbm_kernel<Q, STORE, false, true, IBB><<<grid, block, 0, st>>>(RWMI_LBM_ARGS);
   }
+#undef RWMI_LBM_ARGS
 }
 
 void launch_lbm(int q, int storage, bool reduce, const Geom& g, const void* fin, void* fout,
