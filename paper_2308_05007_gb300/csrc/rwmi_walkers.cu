@@ -680,27 +680,52 @@ void launch_scatter(const Geom& g, const float4* pos, const float4* x0, int64_t 
 // FP64 walker moments: sums of d = x - x0, d^2, x, x^2 per axis (exact FP64 differences of the
 // binary32 positions), then {N, mean d, var d, mean x, var x}.
 // ------------------------------------------------------------------------------------------
+// Float-float (double-binary32) accumulation: a value hi + lo carried exactly by error-free
+// transformations (Knuth's TwoSum, FMA TwoProduct), about 48 significant bits. It replaces the
+// per-walker binary64 arithmetic, which GB300's narrow FP64 pipe made the cost of the moments.
+struct FF { float hi, lo; };
+__device__ __forceinline__ FF ff_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+// acc += (th + tl), then renormalised
+__device__ __forceinline__ void ff_acc(FF& acc, float th, float tl) {
+  const FF s = ff_two_sum(acc.hi, th);
+  const float e = __fadd_rn(s.lo, __fadd_rn(acc.lo, tl));
+  const float hi = __fadd_rn(s.hi, e);
+  acc.lo = __fsub_rn(e, __fsub_rn(hi, s.hi));
+  acc.hi = hi;
+}
+
 __global__ void moments_kernel(const float4* __restrict__ pos, const float4* __restrict__ x0, int64_t n,
                                double* __restrict__ acc) {
-  double v[12];
+  FF a[12];
 #pragma unroll
-  for (int m = 0; m < 12; ++m) v[m] = 0.0;
+  for (int m = 0; m < 12; ++m) a[m] = {0.0f, 0.0f};
   for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < n; w += (int64_t)gridDim.x * blockDim.x) {
     const float4 p = pos[w], q = x0[w];
-    const double xs[3] = {p.x, p.y, p.z}, x0s[3] = {q.x, q.y, q.z};
+    const float xs[3] = {p.x, p.y, p.z}, x0s[3] = {q.x, q.y, q.z};
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const double d = xs[a] - x0s[a];
-      v[a] += d;
-      v[3 + a] += d * d;
-      v[6 + a] += xs[a];
-      v[9 + a] += xs[a] * xs[a];
+    for (int k = 0; k < 3; ++k) {
+      const FF d = ff_two_sum(xs[k], -x0s[k]);                 // x - x0, exact
+      ff_acc(a[k], d.hi, d.lo);
+      const float p2 = __fmul_rn(d.hi, d.hi);                    // d^2 = hi^2 + 2 hi lo (+ lo^2 < 2^-48 d^2)
+      const float e2 = __fadd_rn(__fmaf_rn(d.hi, d.hi, -p2), __fmul_rn(2.0f, __fmul_rn(d.hi, d.lo)));
+      ff_acc(a[3 + k], p2, e2);
+      ff_acc(a[6 + k], xs[k], 0.0f);
+      const float x2 = __fmul_rn(xs[k], xs[k]);                  // x^2 exactly as x2 + fma residue
+      ff_acc(a[9 + k], x2, __fmaf_rn(xs[k], xs[k], -x2));
     }
   }
+  double v[12];
 #pragma unroll
-  for (int m = 0; m < 12; ++m)
+  for (int m = 0; m < 12; ++m) {
+    v[m] = (double)a[m].hi + (double)a[m].lo;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v[m] += __shfl_xor_sync(0xffffffffu, v[m], o);
+  }
   __shared__ double s[8][12];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (lane == 0)

@@ -191,6 +191,32 @@ def test_one_walker_step_from_identical_inputs(wl):
 
 
 # ------------------------------------------------------------------------------- invariants
+def _check_moments(m, x, x0):
+    """The walker moments against their definition in FP64 over the GPU's own binary32 positions:
+    {N, mean d, var d, mean x, var x}, d = x - x0. The GPU sums in float-float per thread (about
+    48 bits) and FP64 across threads (at most ~800 chained additions, 1e-13 relative). The
+    reference sums each component as a contiguous row, where numpy sums pairwise (error ~
+    log2(N) eps); numpy's axis-0 mean of an (N, 3) array adds sequentially and is itself off by
+    ~1e-13."""
+    x, x0 = np.ascontiguousarray(x.T, np.float64), np.ascontiguousarray(x0.T, np.float64)
+    d = x - x0
+    n = x.shape[1]
+    assert m[0] == n
+    md, mx = d.sum(1) / n, x.sum(1) / n
+    d2, x2 = (d * d).sum(1) / n, (x * x).sum(1) / n
+    want = np.concatenate([md, d2 - md * md, mx, x2 - mx * mx])
+    s2 = np.concatenate([d2, d2, x2, x2])
+    assert np.all(np.abs(m[1:] - want) <= 1e-12 * s2), (m[1:] - want, s2)
+
+
+def test_moments_match_their_definition():
+    w = I.ragged(n_walkers=200_000)
+    sim = Sim().from_workload(w)
+    sim.step(7)
+    x, x0 = sim.walkers_by_id()
+    _check_moments(sim.walker_moments(), x, x0)
+
+
 def test_binning_is_exact_for_identical_positions():
     w = I.ragged(n_walkers=20000)
     sim = Sim().from_workload(w)
@@ -320,7 +346,8 @@ def test_oscillator_full_size_sampled():
     assert sim.sync() >= 0
     f_next = sim.populations()
     u = sim.velocity()
-    x_next, _ = sim.walkers_by_id()
+    x_next, x0_next = sim.walkers_by_id()
+    _check_moments(sim.walker_moments(), x_next, x0_next)
     ora = Oracle.from_workload(w, seed_walkers=False)
     cg, og = sim.solid()   # solid of time t + 1 on the GPU
     ora.set_populations(f_prev)
