@@ -221,14 +221,14 @@ rwmi_status build_current_frame(rwmi_ctx* c) {
   const int par = (int)(c->t & 1);
   if (c->cfg.coupling == 1 && c->P > 0) {   // IBB: node classes of t - 1 (the first step refills from them)
     const int pp = par ^ 1;
-    launch_clear_u32(c->bword[pp], c->nbrick + 1, c->stream);
+    launch_clear_u32(c->bword[pp], c->nbrick + BWORD_EXTRA, c->stream);
     launch_pose_bin(c->g, particle_set(c), brick_set(c, pp), c->d_T, -1, c->cfg.body_force,
                     c->cfg.force_period, 1, c->acc[pp], c->stream);
     launch_nodes(c->cfg.q, c->cfg.storage, c->g, particle_set(c), brick_set(c, pp), c->node[pp], c->node[pp],
                  c->f[c->fcur], c->cfg.rho0, false, c->stream);
     c->launches += 3;
   }
-  CK(cudaMemsetAsync(c->bword[par], 0, sizeof(uint32_t) * (c->nbrick + 1), c->stream));
+  CK(cudaMemsetAsync(c->bword[par], 0, sizeof(uint32_t) * (c->nbrick + BWORD_EXTRA), c->stream));
   launch_pose_bin(c->g, particle_set(c), brick_set(c, par), c->d_T, 0, c->cfg.body_force,
                   c->cfg.force_period, 1, c->acc[par], c->stream);
   c->launches++;
@@ -345,7 +345,7 @@ void enqueue_step(rwmi_ctx* c, bool reduce) {
   if (ws != c->stream && c->walk_rec[tp]) cudaStreamWaitEvent(c->stream, c->walk_ev[tp], 0);
   auto pose = [&]() {   // particles, bricks and body force of t+1
     phase_begin(c, RWMI_PHASE_POSE);
-    launch_clear_u32(c->bword[tn], c->nbrick + 1, c->stream);
+    launch_clear_u32(c->bword[tn], c->nbrick + BWORD_EXTRA, c->stream);
     c->launches++;
     launch_pose_bin(c->g, ps, brick_set(c, tn), c->d_T, toff + 1, c->cfg.body_force, c->cfg.force_period, 1,
                     c->acc[tn], c->stream);
@@ -539,7 +539,7 @@ RWMI_API rwmi_status rwmi_create(rwmi_ctx** out, const int32_t dims[3], double t
     CK(dalloc(c, &c->offsets, sizeof(uint32_t) * (size_t)ncell));
     CK(dalloc(c, &c->bsums, sizeof(uint32_t) * scan_block_sums_size((uint32_t)ncell)));
     for (int k = 0; k < 2; ++k) {
-      CK(dalloc(c, &c->bword[k], sizeof(uint32_t) * (c->nbrick + 1)));
+      CK(dalloc(c, &c->bword[k], sizeof(uint32_t) * (c->nbrick + BWORD_EXTRA)));
       CK(dalloc(c, &c->bcand[k], sizeof(uint16_t) * (size_t)c->nbrick * MAXC));
       CK(dalloc(c, &c->rlist[k], sizeof(int32_t) * c->nbrick));
       CK(dalloc(c, &c->sp[k], sizeof(StepParams)));
@@ -872,7 +872,7 @@ RWMI_API rwmi_status rwmi_footprint(const int32_t dims[3], int32_t q, int32_t st
                  Nc = (uint64_t)n_centers, N = (uint64_t)n_walkers;
   uint64_t b = 2 * (uint64_t)q * pad * sb;                     // populations A/B
   b += 2 * 16 * pad + 2 * 2 * ncell + 2 * 2 * ncell + 8 * ncell + 4 * (ncell / 2048 + 2);   // (u, rho), solid, nodes, counts/offsets, scan
-  b += 2 * (4 * (nbrick + 1) + 2 * MAXC * nbrick + 4 * nbrick) + 2 * 8 * nbrick;   // bricks, masks
+  b += 2 * (4 * (nbrick + BWORD_EXTRA) + 2 * MAXC * nbrick + 4 * nbrick) + 2 * 8 * nbrick;   // bricks, masks
   b += 100 * N;                                                // pos, x0 (A/B), rank, resolve list
   b += 2 * (48 + 80) * P + 2 * 16 * Nc + sizeof(ParticleDesc) * P + 16 * Nc + 2 * 8 * (6 * P + 4 * RED_SLOTS);
   b += (uint64_t)SERIES_ROWS * SERIES_COLS * 8 + 4096;         // moment series, counters

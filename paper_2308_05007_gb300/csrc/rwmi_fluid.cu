@@ -336,7 +336,13 @@ __global__ void __launch_bounds__(256, 4) raster_kernel(Geom g, ParticleSet ps, 
   const uint32_t nbrick = (uint32_t)g.nb[0] * g.nb[1] * g.nb[2];
   const uint32_t nlist = bs.bword[nbrick];
   unsigned long long queued = 0;
-  for (uint32_t li = blockIdx.x * RW_WARPS + wib; li < nlist; li += gridDim.x * RW_WARPS) {
+  // bricks are taken from a shared counter (bword[nbrick + 1], zero after the brick pass), one
+  // per warp at a time: their cost ranges from a few bound tests to ~100 straddling cells, and a
+  // fixed assignment left a long tail
+  uint32_t li = 0;
+  if (lane == 0) li = atomicAdd(&bs.bword[nbrick + 1], 1u);
+  li = __shfl_sync(full, li, 0);
+  for (; li < nlist; ) {
     const uint32_t b = (uint32_t)bs.rlist[li];
     const int bi = b % g.nb[0], bj = (b / g.nb[0]) % g.nb[1], bk = b / (g.nb[0] * g.nb[1]);
     const uint32_t nc = bs.bword[b] & 0xffffu;
@@ -516,6 +522,8 @@ __global__ void __launch_bounds__(256, 4) raster_kernel(Geom g, ParticleSet ps, 
       }
     }
     __syncwarp();
+    if (lane == 0) li = atomicAdd(&bs.bword[nbrick + 1], 1u);
+    li = __shfl_sync(full, li, 0);
   }
   if (lane == 0 && queued) atomicAdd(&status[ST_RASTER_QUEUED], queued);
 }
@@ -523,7 +531,10 @@ __global__ void __launch_bounds__(256, 4) raster_kernel(Geom g, ParticleSet ps, 
 void launch_raster(const Geom& g, const ParticleSet& ps, BrickSet bs, uint16_t* solid,
                    unsigned long long* status, int nsm, cudaStream_t st) {
   if (ps.P == 0) return;
-  raster_kernel<<<nsm * 4, RW_WARPS * 32, 0, st>>>(g, ps, bs, solid, status);
+  // two blocks per SM: the raster runs beside the LBM, which takes the rest of each SM (four
+  // blocks per SM held every register file and left the LBM to start only as they finished;
+  // one block per SM made the raster itself the longer branch)
+  raster_kernel<<<nsm * 2, RW_WARPS * 32, 0, st>>>(g, ps, bs, solid, status);
 }
 
 // ------------------------------------------------------------------------------------------

@@ -8,9 +8,9 @@
 //                                         with one 16-byte store, gathered by walkers (8 loads)
 //   solid         solid[ncell]            uint16: sub-sample count (bits 0-6) | owner (bits 7-15),
 //                                         valid only in bricks flagged for the current time
-//   bricks        8x8x8-cell bricks, per time parity: bword[nbrick+1] (walker-candidate count in
-//                 bits 0-15, raster-relevant count in bits 16-31; the extra last word counts
-//                 rlist), bcand[nbrick][MAXC] (uint16 particle ids, bit 15 = raster-relevant),
+//   bricks        8x8x8-cell bricks, per time parity: bword[nbrick+2] (walker-candidate count in
+//                 bits 0-15, raster-relevant count in bits 16-31; word nbrick counts rlist, word
+//                 nbrick+1 is the raster's work counter), bcand[nbrick][MAXC] (uint16 particle ids, bit 15 = raster-relevant),
 //                 rlist[nbrick] (bricks holding raster-relevant particles); wmask[nbrick] 64-bit
 //                 masks of 2^3-cell mini-bricks where walkers must test particles
 //   particles     desc[P] (trajectory), cbody[Nc] float4 (body-frame x, y, z, k),
@@ -28,6 +28,7 @@ namespace rwmi {
 
 constexpr int BRICK = 8;            // brick edge in cells
 constexpr int MAXC = 16;            // candidate particles stored per brick
+constexpr uint32_t BWORD_EXTRA = 2; // words after the per-brick words of bword
 constexpr int MAX_PARTICLES = 511;  // owner field of the solid word is 9 bits
 constexpr int MAX_CENTERS = 65535;
 constexpr float U_BOUND = 0.1f;     // lattice speed bound assumed by the walker candidate margin
@@ -238,8 +239,9 @@ void launch_init_populations(int q, int storage, const Geom& g, void* f, double 
 // only between runs) plus toff, fixed when the launch is queued or captured. Kernels of several
 // steps may then run concurrently without racing on the counter.
 // The flagged-walker list of the two-pass walker step is split into WLIST_STRIPES parts, each
-// with its own append counter (block b appends to part b mod WLIST_STRIPES), so the appends do
-// not serialise on one address. Capacity per part: wlist_stripe_cap(n) walkers.
+// with its own append counter (the walkers of chunk k = w / 256 append to part k mod
+// WLIST_STRIPES), so the appends do not serialise on one address. A part receives at most
+// ceil(chunks / WLIST_STRIPES) chunks: capacity wlist_stripe_cap(n) walkers.
 constexpr int WLIST_STRIPES = 32;
 inline int64_t wlist_stripe_cap(int64_t n) {
   const int64_t blocks = (n + 255) / 256;

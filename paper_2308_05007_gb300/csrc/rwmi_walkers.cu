@@ -271,11 +271,16 @@ __device__ __noinline__ unsigned resolve_particles(const WalkCtx& c, const float
   return ev;
 }
 
+// pass-1 grid: every block resident at once (5 blocks of 256 threads at 48 registers per SM),
+// looping over the walkers -- measured faster than one block per 256 walkers, and than grids
+// that leave SM room for the kernels beside it
+constexpr int WALKER_BLOCKS_PER_SM = 5;
+
 // Pass 1, one thread per walker: Eq. 2 with dt = 1 (trilinear u, Philox + Box-Muller) and the
 // walls. A walker whose mini-brick may meet a particle at t+1 (or whose list overflowed, or whose
 // step was unusually long) is appended to a compact list instead of being written back; pass 2
 // resolves those at full SIMT width, so this kernel carries none of the rare-path code.
-__global__ void __launch_bounds__(256, 6) walker_kernel(WalkCtx c, float4* __restrict__ pos, int64_t n,
+__global__ void __launch_bounds__(256, 5) walker_kernel(WalkCtx c, float4* __restrict__ pos, int64_t n,
                                                         const float* __restrict__ u,
                                                         const int64_t* __restrict__ d_T, int toff,
                                                         float amp, uint32_t k0, uint32_t k1,
@@ -283,75 +288,79 @@ __global__ void __launch_bounds__(256, 6) walker_kernel(WalkCtx c, float4* __res
                                                         float4* __restrict__ list, unsigned int* list_n,
                                                         int64_t cap) {
   const int64_t T = *d_T + toff;
-  const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  bool ev_wall = false, ev_fast = false, ev_nonfinite = false, flagged = false;
-  float4 ea = make_float4(0.f, 0.f, 0.f, 0.f), eb = ea;
-  if (w < n) {
-    const float4 p4 = pos[w];
-    const uint32_t id = __float_as_uint(p4.w);
-    const float x[3] = {p4.x, p4.y, p4.z};
-    const float xw = wrap_coord(x[0], (float)c.g.n[0], c.g.wall[0], c.g.inv_n[0]);
-    const float yw = wrap_coord(x[1], (float)c.g.n[1], c.g.wall[1], c.g.inv_n[1]);
-    const float zw = wrap_coord(x[2], (float)c.g.n[2], c.g.wall[2], c.g.inv_n[2]);
-    float ux, uy, uz;
-    interp_velocity(u, c.g, xw, yw, zw, ux, uy, uz);
-    const uint4 r = philox(make_uint4(id, (uint32_t)T, 0u, 0u), k0, k1);
-    // Box-Muller with the fast intrinsics: ln and sin/cos to ~1e-6 absolute, far below the
-    // 2e-5 per-step tolerance; angle 2 pi U = pi + theta with theta = 2 pi (U - 1/2) in (-pi, pi)
-    const float rad01 = sqrtf(-2.0f * __logf(uniform24(r.x)));
-    const float rad23 = sqrtf(-2.0f * __logf(uniform24(r.z)));
-    float s1, c1, s3, c3;
-    __sincosf(6.2831853f * (uniform24(r.y) - 0.5f), &s1, &c1);
-    __sincosf(6.2831853f * (uniform24(r.w) - 0.5f), &s3, &c3);
-    s1 = -s1; c1 = -c1; c3 = -c3;
-    float xf[3] = {x[0] + ux + amp * (rad01 * c1), x[1] + uy + amp * (rad01 * s1),
-                   x[2] + uz + amp * (rad23 * c3)};
-    if (!wall_reflect(xf, c.g)) ev_wall = true;
-    if (c.ps.P > 0) {
-      const float step2 = (xf[0] - x[0]) * (xf[0] - x[0]) + (xf[1] - x[1]) * (xf[1] - x[1]) +
-                          (xf[2] - x[2]) * (xf[2] - x[2]);
-      const int b = brick_of(xw, yw, zw, c.g);
-      const uint32_t nc = c.bs.bword[b] & 0xffffu;
-      bool need = nc > MAXC;
-      if (nc > 0 && nc <= MAXC) {   // mini-brick of x: cells (2a, 2a+1) along each axis of the brick
-        const int ix = min(max((int)floorf(xw), 0), c.g.n[0] - 1), iy = min(max((int)floorf(yw), 0), c.g.n[1] - 1),
-                  iz = min(max((int)floorf(zw), 0), c.g.n[2] - 1);
-        const int mb = ((ix & 7) >> 1) + 4 * ((iy & 7) >> 1) + 16 * ((iz & 7) >> 1);
-        need = (c.bs.wmask[b] >> mb) & 1ull;
+  // grid-stride over chunks of 256 walkers (block-uniform), so that a fixed grid leaves room on
+  // every SM for the kernels that run beside this one
+  for (int64_t chunk = blockIdx.x; chunk * 256 < n; chunk += gridDim.x) {
+    const int64_t w = chunk * 256 + threadIdx.x;
+    bool ev_wall = false, ev_fast = false, ev_nonfinite = false, flagged = false;
+    float4 ea = make_float4(0.f, 0.f, 0.f, 0.f), eb = ea;
+    if (w < n) {
+      const float4 p4 = pos[w];
+      const uint32_t id = __float_as_uint(p4.w);
+      const float x[3] = {p4.x, p4.y, p4.z};
+      const float xw = wrap_coord(x[0], (float)c.g.n[0], c.g.wall[0], c.g.inv_n[0]);
+      const float yw = wrap_coord(x[1], (float)c.g.n[1], c.g.wall[1], c.g.inv_n[1]);
+      const float zw = wrap_coord(x[2], (float)c.g.n[2], c.g.wall[2], c.g.inv_n[2]);
+      float ux, uy, uz;
+      interp_velocity(u, c.g, xw, yw, zw, ux, uy, uz);
+      const uint4 r = philox(make_uint4(id, (uint32_t)T, 0u, 0u), k0, k1);
+      // Box-Muller with the fast intrinsics: ln and sin/cos to ~1e-6 absolute, far below the
+      // 2e-5 per-step tolerance; angle 2 pi U = pi + theta with theta = 2 pi (U - 1/2) in (-pi, pi)
+      const float rad01 = sqrtf(-2.0f * __logf(uniform24(r.x)));
+      const float rad23 = sqrtf(-2.0f * __logf(uniform24(r.z)));
+      float s1, c1, s3, c3;
+      __sincosf(6.2831853f * (uniform24(r.y) - 0.5f), &s1, &c1);
+      __sincosf(6.2831853f * (uniform24(r.w) - 0.5f), &s3, &c3);
+      s1 = -s1; c1 = -c1; c3 = -c3;
+      float xf[3] = {x[0] + ux + amp * (rad01 * c1), x[1] + uy + amp * (rad01 * s1),
+                     x[2] + uz + amp * (rad23 * c3)};
+      if (!wall_reflect(xf, c.g)) ev_wall = true;
+      if (c.ps.P > 0) {
+        const float step2 = (xf[0] - x[0]) * (xf[0] - x[0]) + (xf[1] - x[1]) * (xf[1] - x[1]) +
+                            (xf[2] - x[2]) * (xf[2] - x[2]);
+        const int b = brick_of(xw, yw, zw, c.g);
+        const uint32_t nc = c.bs.bword[b] & 0xffffu;
+        bool need = nc > MAXC;
+        if (nc > 0 && nc <= MAXC) {   // mini-brick of x: cells (2a, 2a+1) along each axis of the brick
+          const int ix = min(max((int)floorf(xw), 0), c.g.n[0] - 1), iy = min(max((int)floorf(yw), 0), c.g.n[1] - 1),
+                    iz = min(max((int)floorf(zw), 0), c.g.n[2] - 1);
+          const int mb = ((ix & 7) >> 1) + 4 * ((iy & 7) >> 1) + 16 * ((iz & 7) >> 1);
+          need = (c.bs.wmask[b] >> mb) & 1ull;
+        }
+        ev_fast = step2 > c.ps.walk_margin * c.ps.walk_margin;
+        flagged = need || ev_fast;
       }
-      ev_fast = step2 > c.ps.walk_margin * c.ps.walk_margin;
-      flagged = need || ev_fast;
+      ev_nonfinite = !(isfinite(ux) && isfinite(uy) && isfinite(uz));
+      if (!flagged) {
+        pos[w] = make_float4(xf[0], xf[1], xf[2], p4.w);
+      } else {
+        ea = make_float4(x[0], x[1], x[2], p4.w);
+        eb = make_float4(xf[0], xf[1], xf[2], __uint_as_float((uint32_t)w));
+      }
     }
-    ev_nonfinite = !(isfinite(ux) && isfinite(uy) && isfinite(uz));
-    if (!flagged) {
-      pos[w] = make_float4(xf[0], xf[1], xf[2], p4.w);
-    } else {
-      ea = make_float4(x[0], x[1], x[2], p4.w);
-      eb = make_float4(xf[0], xf[1], xf[2], __uint_as_float((uint32_t)w));
+    const unsigned full = 0xffffffffu;
+    const unsigned fl = __ballot_sync(full, flagged);
+    if (fl) {   // one list reservation per warp, on this chunk's stripe of the list
+      const int lane = threadIdx.x & 31;
+      const int leader = __ffs(fl) - 1;
+      const int stripe = (int)(chunk % WLIST_STRIPES);
+      unsigned base = 0;
+      if (lane == leader) base = atomicAdd(&list_n[stripe], (unsigned)__popc(fl));
+      base = __shfl_sync(full, base, leader);
+      if (flagged) {
+        const size_t slot = (size_t)stripe * (size_t)cap + base + __popc(fl & ((1u << lane) - 1u));
+        list[2 * slot] = ea;
+        list[2 * slot + 1] = eb;
+      }
     }
-  }
-  const unsigned full = 0xffffffffu;
-  const unsigned fl = __ballot_sync(full, flagged);
-  if (fl) {   // one list reservation per warp, on this block's stripe of the list
-    const int lane = threadIdx.x & 31;
-    const int leader = __ffs(fl) - 1;
-    const int stripe = (int)(blockIdx.x % WLIST_STRIPES);
-    unsigned base = 0;
-    if (lane == leader) base = atomicAdd(&list_n[stripe], (unsigned)__popc(fl));
-    base = __shfl_sync(full, base, leader);
-    if (flagged) {
-      const size_t slot = (size_t)stripe * (size_t)cap + base + __popc(fl & ((1u << lane) - 1u));
-      list[2 * slot] = ea;
-      list[2 * slot + 1] = eb;
-    }
-  }
-  if (__any_sync(full, ev_wall | ev_fast | ev_nonfinite)) {
-    const bool evs[3] = {ev_wall, ev_fast, ev_nonfinite};
-    const int slot[3] = {ST_WALL_FAIL, ST_FAST_SPEED, ST_NONFINITE};
-#pragma unroll
-    for (int m = 0; m < 3; ++m) {
-      const unsigned bal = __ballot_sync(full, evs[m]);
-      if (bal && (threadIdx.x & 31) == 0) atomicAdd(&status[slot[m]], (unsigned long long)__popc(bal));
+    if (__any_sync(full, ev_wall | ev_fast | ev_nonfinite)) {
+      const bool evs[3] = {ev_wall, ev_fast, ev_nonfinite};
+      const int slot[3] = {ST_WALL_FAIL, ST_FAST_SPEED, ST_NONFINITE};
+  #pragma unroll
+      for (int m = 0; m < 3; ++m) {
+        const unsigned bal = __ballot_sync(full, evs[m]);
+        if (bal && (threadIdx.x & 31) == 0) atomicAdd(&status[slot[m]], (unsigned long long)__popc(bal));
+      }
     }
   }
 }
@@ -456,7 +465,8 @@ void launch_walkers(const Geom& g, const ParticleSet& ps, BrickSet bs1, float4* 
   // set for the next step (no memset launch, no completion ticket)
   unsigned int* cur = list_n + WLIST_STRIPES * (toff_parity & 1);
   unsigned int* nxt = list_n + WLIST_STRIPES * ((toff_parity + 1) & 1);
-  walker_kernel<<<(unsigned)blocks, 256, 0, st>>>(c, pos, n, u, d_T, toff, amp, k0, k1, status, list, cur, cap);
+  const int64_t grid = blocks < (int64_t)nsm * WALKER_BLOCKS_PER_SM ? blocks : (int64_t)nsm * WALKER_BLOCKS_PER_SM;
+  walker_kernel<<<(unsigned)grid, 256, 0, st>>>(c, pos, n, u, d_T, toff, amp, k0, k1, status, list, cur, cap);
   walker_resolve_kernel<<<nsm * 8, 256, 0, st>>>(c, pos, list, cur, nxt, d_T, toff, amp, k0, k1, status, cap);
 }
 
@@ -719,17 +729,23 @@ __global__ void moments_kernel(const float4* __restrict__ pos, const float4* __r
       ff_acc(a[9 + k], x2, __fmaf_rn(xs[k], xs[k], -x2));
     }
   }
-  double v[12];
+  // warp sums in float-float too; binary64 from the warp level on
 #pragma unroll
-  for (int m = 0; m < 12; ++m) {
-    v[m] = (double)a[m].hi + (double)a[m].lo;
+  for (int m = 0; m < 12; ++m)
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v[m] += __shfl_xor_sync(0xffffffffu, v[m], o);
-  }
+    for (int o = 16; o > 0; o >>= 1) {
+      const float oh = __shfl_xor_sync(0xffffffffu, a[m].hi, o), ol = __shfl_xor_sync(0xffffffffu, a[m].lo, o);
+      ff_acc(a[m], oh, ol);
+    }
   __shared__ double s[8][12];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (lane == 0)
-    for (int m = 0; m < 12; ++m) s[wid][m] = v[m];
+  if (lane < 12) {
+    float hi = a[0].hi, lo = a[0].lo;
+#pragma unroll
+    for (int m = 1; m < 12; ++m)
+      if (lane == m) { hi = a[m].hi; lo = a[m].lo; }
+    s[wid][lane] = (double)hi + (double)lo;
+  }
   __syncthreads();
   if (threadIdx.x < 12) {
     double t = 0.0;
@@ -764,7 +780,7 @@ void launch_moments(const float4* pos, const float4* x0, int64_t n, double* acc,
                     int interval, int rows, const int64_t* d_T, int toff, cudaStream_t st) {
   if (n > 0) {
     int64_t blocks = (n + 255) / 256;
-    if (blocks > 152 * 8) blocks = 152 * 8;
+    if (blocks > 152 * 4) blocks = 152 * 4;
     moments_kernel<<<(unsigned)blocks, 256, 0, st>>>(pos, x0, n, acc);
   }
   moments_finalize_kernel<<<1, 32, 0, st>>>(acc, n, base, interval, rows, d_T, toff);
