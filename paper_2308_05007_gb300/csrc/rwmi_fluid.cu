@@ -272,6 +272,27 @@ __device__ __forceinline__ bool subsample_inside_t(const float4* cw, int c0, int
   return metaball_exact(cw_exact, e0, e1, x, y, z, g) >= 1.0f;
 }
 
+// Two sub-samples of one lane that differ only in z (z and z + 1/2), in one pass over the
+// staged control points: the point load, the x/y displacements and dx^2 + dy^2 are shared.
+// Same fast-value tolerance and exact fallback as subsample_inside_t.
+template <bool MI>
+__device__ __forceinline__ void subsample_pair_t(const float4* cw, int c0, int c1, const float4* cw_exact, int e0,
+                                                 int e1, float x, float y, float z, const Geom& g, bool& in_lo,
+                                                 bool& in_hi) {
+  const float zh = z + 0.5f;
+  float flo = 0.0f, fhi = 0.0f;
+  for (int i = c0; i < c1; ++i) {
+    const float4 c = cw[i];
+    const float dx = disp<MI>(x, c.x, 0, g), dy = disp<MI>(y, c.y, 1, g);
+    const float dzl = disp<MI>(z, c.z, 2, g), dzh = disp<MI>(zh, c.z, 2, g);
+    const float rxy = dx * dx + dy * dy;
+    flo += __fdividef(c.w, rxy + dzl * dzl);
+    fhi += __fdividef(c.w, rxy + dzh * dzh);
+  }
+  in_lo = fabsf(flo - 1.0f) > 4e-5f ? flo >= 1.0f : metaball_exact(cw_exact, e0, e1, x, y, z, g) >= 1.0f;
+  in_hi = fabsf(fhi - 1.0f) > 4e-5f ? fhi >= 1.0f : metaball_exact(cw_exact, e0, e1, x, y, zh, g) >= 1.0f;
+}
+
 // Runtime dispatch on the (warp-uniform) minimum-image switch.
 __device__ __forceinline__ CellBound bound_at(const float4* cw, int c0, int c1, float x, float y, float z,
                                               float h, const Geom& g, bool mi = true) {
@@ -495,13 +516,10 @@ __global__ void __launch_bounds__(256, 4) raster_kernel(Geom g, ParticleSet ps, 
         bool in_lo, in_hi;
         const float sx = (float)si + 0.125f, sy = (float)sj + 0.125f, sz = (float)sk + 0.125f;
         const float ax = 0.25f * (float)(lane & 3), ay = 0.25f * (float)((lane >> 2) & 3), az = 0.25f * (float)(lane >> 4);
-        if (mi) {
-          in_lo = subsample_inside_t<true>(W.cw, W.c0[m], W.c1[m], bs.cworld, e0, e1, sx + ax, sy + ay, sz + az, g);
-          in_hi = subsample_inside_t<true>(W.cw, W.c0[m], W.c1[m], bs.cworld, e0, e1, sx + ax, sy + ay, sz + az + 0.5f, g);
-        } else {
-          in_lo = subsample_inside_t<false>(W.cw, W.c0[m], W.c1[m], bs.cworld, e0, e1, sx + ax, sy + ay, sz + az, g);
-          in_hi = subsample_inside_t<false>(W.cw, W.c0[m], W.c1[m], bs.cworld, e0, e1, sx + ax, sy + ay, sz + az + 0.5f, g);
-        }
+        if (mi)
+          subsample_pair_t<true>(W.cw, W.c0[m], W.c1[m], bs.cworld, e0, e1, sx + ax, sy + ay, sz + az, g, in_lo, in_hi);
+        else
+          subsample_pair_t<false>(W.cw, W.c0[m], W.c1[m], bs.cworld, e0, e1, sx + ax, sy + ay, sz + az, g, in_lo, in_hi);
         const unsigned blo = __ballot_sync(full, in_lo);
         const unsigned bhi = __ballot_sync(full, in_hi);
         if (lane == src) {
