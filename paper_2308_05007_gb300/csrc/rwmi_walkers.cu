@@ -290,17 +290,31 @@ __global__ void __launch_bounds__(256, 5) walker_kernel(WalkCtx c, float4* __res
   const int64_t T = *d_T + toff;
   // grid-stride over chunks of 256 walkers (block-uniform), so that a fixed grid leaves room on
   // every SM for the kernels that run beside this one
+  // the next chunk's positions are loaded while this chunk's gathers are in flight
+  float4 p4_next = make_float4(0.f, 0.f, 0.f, 0.f);
+  if ((int64_t)blockIdx.x * 256 + threadIdx.x < n) p4_next = pos[(int64_t)blockIdx.x * 256 + threadIdx.x];
   for (int64_t chunk = blockIdx.x; chunk * 256 < n; chunk += gridDim.x) {
     const int64_t w = chunk * 256 + threadIdx.x;
+    const float4 p4 = p4_next;
+    if (w + (int64_t)gridDim.x * 256 < n) p4_next = pos[w + (int64_t)gridDim.x * 256];
     bool ev_wall = false, ev_fast = false, ev_nonfinite = false, flagged = false;
     float4 ea = make_float4(0.f, 0.f, 0.f, 0.f), eb = ea;
     if (w < n) {
-      const float4 p4 = pos[w];
       const uint32_t id = __float_as_uint(p4.w);
       const float x[3] = {p4.x, p4.y, p4.z};
       const float xw = wrap_coord(x[0], (float)c.g.n[0], c.g.wall[0], c.g.inv_n[0]);
       const float yw = wrap_coord(x[1], (float)c.g.n[1], c.g.wall[1], c.g.inv_n[1]);
       const float zw = wrap_coord(x[2], (float)c.g.n[2], c.g.wall[2], c.g.inv_n[2]);
+      // brick word and mini-brick mask of x, loaded together with the velocity gathers (the mask
+      // is used only when 0 < candidates <= MAXC, where the raster wrote it)
+      int b = 0;
+      uint32_t nc = 0u;
+      unsigned long long wm = 0ull;
+      if (c.ps.P > 0) {
+        b = brick_of(xw, yw, zw, c.g);
+        nc = c.bs.bword[b] & 0xffffu;
+        wm = c.bs.wmask[b];
+      }
       float ux, uy, uz;
       interp_velocity(u, c.g, xw, yw, zw, ux, uy, uz);
       const uint4 r = philox(make_uint4(id, (uint32_t)T, 0u, 0u), k0, k1);
@@ -318,14 +332,12 @@ __global__ void __launch_bounds__(256, 5) walker_kernel(WalkCtx c, float4* __res
       if (c.ps.P > 0) {
         const float step2 = (xf[0] - x[0]) * (xf[0] - x[0]) + (xf[1] - x[1]) * (xf[1] - x[1]) +
                             (xf[2] - x[2]) * (xf[2] - x[2]);
-        const int b = brick_of(xw, yw, zw, c.g);
-        const uint32_t nc = c.bs.bword[b] & 0xffffu;
         bool need = nc > MAXC;
         if (nc > 0 && nc <= MAXC) {   // mini-brick of x: cells (2a, 2a+1) along each axis of the brick
           const int ix = min(max((int)floorf(xw), 0), c.g.n[0] - 1), iy = min(max((int)floorf(yw), 0), c.g.n[1] - 1),
                     iz = min(max((int)floorf(zw), 0), c.g.n[2] - 1);
           const int mb = ((ix & 7) >> 1) + 4 * ((iy & 7) >> 1) + 16 * ((iz & 7) >> 1);
-          need = (c.bs.wmask[b] >> mb) & 1ull;
+          need = (wm >> mb) & 1ull;
         }
         ev_fast = step2 > c.ps.walk_margin * c.ps.walk_margin;
         flagged = need || ev_fast;
