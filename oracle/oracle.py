@@ -86,6 +86,15 @@ def lib():
             L.orc_nodes.argtypes = [P, C.c_longlong, C.c_void_p]
             L.orc_ibb_q.restype = C.c_double
             L.orc_ibb_q.argtypes = [P, C.c_longlong, C.c_int, C.c_longlong, C.c_longlong, C.c_longlong, C.c_void_p]
+            L.orc_set_dem.restype = C.c_int
+            L.orc_set_dem.argtypes = [P, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double, dp,
+                                      C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                      C.c_void_p]
+            for name in ("orc_particle_state", "orc_set_particle_state"):
+                getattr(L, name).argtypes = [P, C.c_void_p]
+            L.orc_dem_pair_geom.argtypes = [P, C.c_int, C.c_int, C.c_void_p]
+            L.orc_dem_wall_geom.argtypes = [P, C.c_int, C.c_int, C.c_void_p]
+            L.orc_dem_advance.argtypes = [P, C.c_longlong]
             L.orc_ibb_link.restype = C.c_double
             L.orc_ibb_link.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, dp, dp, dp, C.c_double]
             _lib = L
@@ -146,6 +155,8 @@ class Oracle:
             o.set_coupling(w.coupling)
         if w.metaballs is not None and w.metaballs.n_particles > 0:
             o.set_metaballs(w.metaballs)
+            if getattr(w, "dem", None) is not None:
+                o.set_dem(w.dem)
         if seed_walkers and w.n_walkers:
             if w.walker_positions is not None:
                 o.set_walkers(np.asarray(w.walker_positions, np.float64))
@@ -177,6 +188,50 @@ class Oracle:
         self.n_particles = int(len(m["coff"]) - 1)
         lib().orc_set_metaballs(self.h, self.n_particles, _ptr(m["coff"]), _ptr(m["cb"]), _ptr(m["k"]),
                                 _ptr(m["org"]), _ptr(m["amp"]), _ptr(m["per"]), _ptr(m["pha"]), _ptr(m["omg"]))
+
+    def set_dem(self, dem):
+        """Free DEM (Eqs. 4-11) instead of the prescribed trajectories, from the current time."""
+        P = self.n_particles
+        self._dem = dict(
+            m=np.ascontiguousarray(dem.mass, np.float64).reshape(P),
+            I=np.ascontiguousarray(dem.inertia, np.float64).reshape(P * 6),
+            Rs=np.ascontiguousarray(dem.sphere_radius, np.float64).reshape(P),
+            v=None if dem.velocity is None else np.ascontiguousarray(dem.velocity, np.float64).reshape(P * 3),
+            w=None if dem.spin is None else np.ascontiguousarray(dem.spin, np.float64).reshape(P * 3))
+        d = self._dem
+        rc = lib().orc_set_dem(self.h, float(dem.kn), float(dem.eta_n), float(dem.kt), float(dem.eta_t),
+                               float(dem.mu_s), _d3(dem.gravity), int(dem.substeps), int(dem.hydro),
+                               _ptr(d["m"]), _ptr(d["I"]), _ptr(d["Rs"]),
+                               None if d["v"] is None else _ptr(d["v"]),
+                               None if d["w"] is None else _ptr(d["w"]))
+        if rc != 0:
+            raise ValueError("oracle: invalid DEM set-up")
+
+    def particle_state(self) -> np.ndarray:
+        """[P, 13]: origin (unwrapped), quaternion (w, x, y, z), velocity, spin."""
+        out = np.zeros((max(self.n_particles, 1), 13))
+        lib().orc_particle_state(self.h, _ptr(out))
+        return out[: self.n_particles]
+
+    def set_particle_state(self, st):
+        st = np.ascontiguousarray(st, np.float64).reshape(self.n_particles, 13)
+        lib().orc_set_particle_state(self.h, _ptr(st))
+
+    def dem_pair_geom(self, i, j) -> dict:
+        """Eqs. 7-9 for particles i, j in the current state, as a new contact."""
+        out = np.zeros(16)
+        lib().orc_dem_pair_geom(self.h, int(i), int(j), _ptr(out))
+        return dict(xm=out[0:3], xc0=out[3:6], xc1=out[6:9], n=out[9:12], delta=float(out[12]), xcp=out[13:16])
+
+    def dem_wall_geom(self, p, face) -> dict:
+        """Eqs. 10-11 for particle p and wall face 2 axis + side, as a new contact."""
+        out = np.zeros(13)
+        lib().orc_dem_wall_geom(self.h, int(p), int(face), _ptr(out))
+        return dict(xcm=out[0:3], xcw=out[3:6], n=out[6:9], delta=float(out[9]), xcp=out[10:13])
+
+    def dem_advance(self, n=1):
+        """n LBM steps' worth of DEM steps, fluid and walkers frozen."""
+        lib().orc_dem_advance(self.h, int(n))
 
     def seed_walkers(self, n, lo, hi, max_attempts=1000) -> int:
         self.n_walkers = int(n)

@@ -134,6 +134,16 @@ typedef struct {
     long long cnt_type[4], bisect_fail, refill_fail, wall_fail, seed_fail;
 
     int coupling;            /* 0: partially saturated cells; 1: IBB + momentum exchange + refilling */
+
+    /* free DEM (Eqs. 4-11), active once orc_set_dem is called */
+    int dem, dem_nsub, dem_hydro;
+    double dem_kn, dem_etan, dem_kt, dem_etat, dem_mus, dem_g[3];
+    double* dst;             /* [13 P] origin (unwrapped), quaternion (w, x, y, z), velocity, spin */
+    double *dmass, *dIb, *dRs, *dzoom;   /* [P], [6 P] body inertia (xx yy zz xy xz yz), [P], [P] */
+    double *dxi, *dxm;       /* pairs (i < j) at i P + j: tangential spring, Newton point [3 each] */
+    unsigned char* dact;     /* pair in contact at the last substep */
+    double *dxiw, *dxmw;     /* walls: particle p, face f (2 axis + side) at 6 p + f */
+    unsigned char* dactw;
 } orc_t;
 
 static long long cell_index(const orc_t* o, long long i, long long j, long long k)
@@ -203,11 +213,16 @@ static void frame_alloc(const orc_t* o, frame_t* fr)
 }
 static void frame_free(frame_t* fr) { free(fr->c); free(fr->c32); free(fr->o); free(fr->v); free(fr->w); }
 
+static void dem_pose(const orc_t* o, int p, double org[3], double vel[3], double R[3][3]);
+
+/* With the free DEM only the current state exists: every t reads it (the stepping order below
+ * asks for the frame of the state's own time). */
 static void frame_at(const orc_t* o, long long t, frame_t* fr)
 {
     for (int p = 0; p < o->P; ++p) {
         double org[3], vel[3], R[3][3];
-        particle_pose(o, t, p, org, vel, R);
+        if (o->dem) dem_pose(o, p, org, vel, R);
+        else particle_pose(o, t, p, org, vel, R);
         for (int i = o->coff[p]; i < o->coff[p + 1]; ++i) {
             double cw[3];
             for (int a = 0; a < 3; ++a)
@@ -220,7 +235,7 @@ static void frame_at(const orc_t* o, long long t, frame_t* fr)
         for (int a = 0; a < 3; ++a) {
             fr->o[3 * p + a] = org[a];
             fr->v[3 * p + a] = vel[a];
-            fr->w[3 * p + a] = o->omg[3 * p + a];
+            fr->w[3 * p + a] = o->dem ? o->dst[13 * p + 10 + a] : o->omg[3 * p + a];
         }
     }
 }
@@ -1013,6 +1028,476 @@ static long long walker_cell(const orc_t* o, const double x[3])
 }
 
 /* ------------------------------------------------------------------------------------------
+ * Free DEM (Section 2.2, Eqs. 4-11), used instead of the prescribed trajectories once
+ * orc_set_dem has been called. Units are lattice units; one LBM step holds `substeps` DEM
+ * steps of dt = 1 / substeps. Readings (the paper leaves these open or defers them to its
+ * references):
+ *  - Sphero-metaball (Eq. 6 context): particle p's contact shape is its metaball scaled about the
+ *    body origin by s_p = 1 - R_s,p / R_b,p (control points times s_p, weights times s_p^2) and
+ *    dilated by the sphere radius R_s,p. R_b,p is the bound radius (f_p < 1 beyond it), so a
+ *    single centre at the origin is reproduced exactly.
+ *  - Pair contact (Eqs. 6-9): Newton-Raphson on grad(f0 + f1) = 0 (Eq. 7) for the internal
+ *    metaballs, DEM_NEWTON_NEW iterations from the deterministic start below, or
+ *    DEM_NEWTON_CONT from the previous substep's point while the contact lasts; a step longer
+ *    than one lattice unit is scaled to one, and a singular Hessian ends the iteration.
+ *    Eq. 8: q0 is chosen so that f0(x_m + q0 grad f0(x_m)) = 1 holds, as the text imposes:
+ *    the crossing nearest to x_m, from the printed first-order Taylor value by a bracketed
+ *    Newton iteration in q0 (surface_along). The single first-order step misplaces the surface
+ *    point by about a lattice unit when x_m lies far from it, which happens when R_s is
+ *    comparable to the gap between the internal shapes. Eq. 9 with
+ *    n = (x_c1 - x_c0) / |x_c1 - x_c0| from particle 0 towards particle 1 and
+ *    x_cp = x_c0 + (R_s0 - delta/2) n, the middle of the overlap (the printed orientation of n
+ *    would put the contact point inside particle 0).
+ *    Start: the internal control points a of particle 0 and b of particle 1 with the smallest
+ *    |c_a - c_b| - r_a - r_b (r = sqrt of the internal weight; first pair on ties), and
+ *    x = c_a + r_a / (r_a + r_b) (c_b - c_a).
+ *  - Wall contact (Eqs. 10-11) on both faces of every walled axis: Newton-Raphson on
+ *    (d_b f, d_c f, f - 1) = 0 (b, c the two axes along the face) gives the point x_cm of the
+ *    internal surface closest to the face; x_cw is its projection on the face, n the face's
+ *    normal into the box, delta = R_s - (x_cm - x_cw).n, x_cp = x_cw + delta/2 n as printed.
+ *    Start: the control point reaching farthest towards the face, moved by its internal radius.
+ *  - Normal force (linear spring-dashpot): F_n = max(0, k_n delta + eta_n (v_i - v_j).n_ij),
+ *    with n_ij from particle i towards the other body and velocities taken at the contact point;
+ *    it acts on i along -n_ij (no attraction).
+ *  - Tangential force (Eq. 5): the spring xi, projected on the current tangent plane, grows by
+ *    v_t dt (v_t: tangential part of the other body's contact-point velocity relative to i's);
+ *    F_t0 = k_t xi + eta_t v_t on i; when |F_t0| > mu_s F_n the force is mu_s F_n F_t0/|F_t0|
+ *    and the spring is reset to (F_t - eta_t v_t) / k_t. The spring is cleared when the contact
+ *    ends.
+ *  - Eq. 4, per DEM step: F = m g + sum F^c + F^e, T = sum T^c + T^e (torques about the
+ *    origin); v += dt F / m, o += dt v (symplectic Euler); w += dt I_w^-1 (T - w x I_w w) with
+ *    I_w = R I_b R^T; q += dt/2 (0, w) q, then normalised. F^e and T^e are the hydrodynamic
+ *    force and torque of the LBM update of the same step, held over its DEM steps (or zero
+ *    with the hydrodynamic coupling off). Pair forces are summed per particle in pair order,
+ *    then the wall forces.
+ *  - Periodic axes: a pair is evaluated at the minimum image of the second origin relative to
+ *    the first; origins stay unwrapped.
+ * ------------------------------------------------------------------------------------------ */
+#define DEM_NEWTON_NEW 24
+#define DEM_NEWTON_CONT 6
+#define DEM_SURFACE_ITERS 24
+#define DEM_SURFACE_HALVINGS 16
+
+/* Rotation matrix of the unit quaternion (w, x, y, z) */
+static void quat_matrix(const double* q, double R[3][3])
+{
+    double w = q[0], x = q[1], y = q[2], z = q[3];
+    R[0][0] = 1.0 - 2.0 * (y * y + z * z);
+    R[0][1] = 2.0 * (x * y - w * z);
+    R[0][2] = 2.0 * (x * z + w * y);
+    R[1][0] = 2.0 * (x * y + w * z);
+    R[1][1] = 1.0 - 2.0 * (x * x + z * z);
+    R[1][2] = 2.0 * (y * z - w * x);
+    R[2][0] = 2.0 * (x * z - w * y);
+    R[2][1] = 2.0 * (y * z + w * x);
+    R[2][2] = 1.0 - 2.0 * (x * x + y * y);
+}
+
+static void dem_pose(const orc_t* o, int p, double org[3], double vel[3], double R[3][3])
+{
+    const double* st = o->dst + 13 * (size_t)p;
+    for (int a = 0; a < 3; ++a) { org[a] = st[a]; vel[a] = st[7 + a]; }
+    quat_matrix(st + 3, R);
+}
+
+/* Internal (zoomed) control points of particle p in world coordinates about origin org, and
+ * their weights; returns their count */
+static int dem_internal(const orc_t* o, int p, const double org[3], double* cw, double* kw)
+{
+    double R[3][3], dummy[3], od[3];
+    dem_pose(o, p, od, dummy, R);
+    double s = o->dzoom[p];
+    int n = 0;
+    for (int i = o->coff[p]; i < o->coff[p + 1]; ++i, ++n) {
+        double b[3] = {s * o->cbody[3 * i], s * o->cbody[3 * i + 1], s * o->cbody[3 * i + 2]};
+        for (int a = 0; a < 3; ++a) cw[3 * n + a] = org[a] + R[a][0] * b[0] + R[a][1] * b[1] + R[a][2] * b[2];
+        kw[n] = s * s * o->kc[i];
+    }
+    return n;
+}
+
+/* Eq. 3 with its gradient and Hessian (xx yy zz xy xz yz) at x, no wrapping */
+static double mb_eval(const double* cw, const double* kw, int n, const double x[3], double g[3], double H[6])
+{
+    double f = 0.0;
+    for (int a = 0; a < 3; ++a) g[a] = 0.0;
+    for (int m = 0; m < 6; ++m) H[m] = 0.0;
+    for (int i = 0; i < n; ++i) {
+        double r[3] = {x[0] - cw[3 * i], x[1] - cw[3 * i + 1], x[2] - cw[3 * i + 2]};
+        double r2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+        double inv2 = 1.0 / r2, k = kw[i];
+        double fi = k * inv2;
+        f += fi;
+        double c1 = -2.0 * fi * inv2;          /* d/dx k/r^2 = -2 k r / r^4 */
+        double c2 = 8.0 * fi * inv2 * inv2;    /* second derivative: -2k/r^4 I + 8k r r^T / r^6 */
+        for (int a = 0; a < 3; ++a) g[a] += c1 * r[a];
+        H[0] += c1 + c2 * r[0] * r[0];
+        H[1] += c1 + c2 * r[1] * r[1];
+        H[2] += c1 + c2 * r[2] * r[2];
+        H[3] += c2 * r[0] * r[1];
+        H[4] += c2 * r[0] * r[2];
+        H[5] += c2 * r[1] * r[2];
+    }
+    return f;
+}
+
+/* Solves the 3x3 system A d = b by Cramer's rule; returns 0 when |det| is tiny */
+static int solve3(double A[3][3], const double b[3], double d[3])
+{
+    double det = A[0][0] * (A[1][1] * A[2][2] - A[1][2] * A[2][1])
+               - A[0][1] * (A[1][0] * A[2][2] - A[1][2] * A[2][0])
+               + A[0][2] * (A[1][0] * A[2][1] - A[1][1] * A[2][0]);
+    if (!(fabs(det) > 1e-300)) return 0;
+    d[0] = (b[0] * (A[1][1] * A[2][2] - A[1][2] * A[2][1]) - A[0][1] * (b[1] * A[2][2] - A[1][2] * b[2])
+            + A[0][2] * (b[1] * A[2][1] - A[1][1] * b[2])) / det;
+    d[1] = (A[0][0] * (b[1] * A[2][2] - A[1][2] * b[2]) - b[0] * (A[1][0] * A[2][2] - A[1][2] * A[2][0])
+            + A[0][2] * (A[1][0] * b[2] - b[1] * A[2][0])) / det;
+    d[2] = (A[0][0] * (A[1][1] * b[2] - b[1] * A[2][1]) - A[0][1] * (A[1][0] * b[2] - b[1] * A[2][0])
+            + b[0] * (A[1][0] * A[2][1] - A[1][1] * A[2][0])) / det;
+    return 1;
+}
+
+/* Newton step with its length limited to one lattice unit; returns 0 when singular */
+static int newton_update(double A[3][3], const double G[3], double x[3])
+{
+    double b[3] = {-G[0], -G[1], -G[2]}, d[3];
+    if (!solve3(A, b, d)) return 0;
+    double len = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    double sc = len > 1.0 ? 1.0 / len : 1.0;
+    for (int a = 0; a < 3; ++a) x[a] += sc * d[a];
+    return 1;
+}
+
+/* Eq. 8: x_c = x_m + q grad f(x_m) with f(x_c) = 1, the crossing nearest to x_m. q starts from
+ * the printed first-order Taylor value q1 = (1 - f(x_m)) / |grad f(x_m)|^2; the bracket is
+ * [0, q_in] with q_in the first of q1, q1/2, q1/4, ... (at most DEM_SURFACE_HALVINGS halvings)
+ * where f >= 1; then DEM_SURFACE_ITERS Newton steps in q (each the same Taylor step from the
+ * current point), a step that leaves the bracket replaced by bisection. Without an inside point
+ * q stays q1. */
+static void surface_along(const double* c, const double* k, int n, const double xm[3], double xc[3])
+{
+    double g[3], gx[3], H[6], x[3];
+    double f = mb_eval(c, k, n, xm, g, H);
+    double q1 = (1.0 - f) / (g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+    double lo = 0.0, hi = q1, q = q1;
+    int inside = 0;
+    for (int h = 0; h <= DEM_SURFACE_HALVINGS; ++h) {
+        for (int a = 0; a < 3; ++a) x[a] = xm[a] + hi * g[a];
+        if (mb_eval(c, k, n, x, gx, H) >= 1.0) { inside = 1; break; }
+        hi = 0.5 * hi;
+    }
+    if (inside) {
+        q = hi;
+        for (int it = 0; it < DEM_SURFACE_ITERS; ++it) {
+            for (int a = 0; a < 3; ++a) x[a] = xm[a] + q * g[a];
+            double fx = mb_eval(c, k, n, x, gx, H);
+            if (fx == 1.0) break;
+            if (fx > 1.0) hi = q; else lo = q;
+            double dq = gx[0] * g[0] + gx[1] * g[1] + gx[2] * g[2];
+            double qn = fabs(dq) > 1e-300 ? q - (fx - 1.0) / dq : 0.5 * (lo + hi);
+            if (!(qn > lo && qn < hi)) qn = 0.5 * (lo + hi);
+            q = qn;
+        }
+    }
+    for (int a = 0; a < 3; ++a) xc[a] = xm[a] + q * g[a];
+}
+
+/* Contact geometry of one pair (Eqs. 7-9). xm: in = start (when cont), out = Newton point.
+ * Returns delta; writes x_c0, x_c1, n (0 towards 1) and x_cp. */
+static double dem_pair_geom(const double* c0, const double* k0, int n0, const double* c1, const double* k1,
+                            int n1, double Rs0, double Rs1, int cont, double xm[3], double xc0[3],
+                            double xc1[3], double nrm[3], double xcp[3])
+{
+    if (!cont) {
+        int ba = 0, bb = 0;
+        double best = INFINITY;
+        for (int a = 0; a < n0; ++a)
+            for (int b = 0; b < n1; ++b) {
+                double d[3] = {c1[3 * b] - c0[3 * a], c1[3 * b + 1] - c0[3 * a + 1], c1[3 * b + 2] - c0[3 * a + 2]};
+                double gap = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]) - sqrt(k0[a]) - sqrt(k1[b]);
+                if (gap < best) { best = gap; ba = a; bb = b; }
+            }
+        double ra = sqrt(k0[ba]), rb = sqrt(k1[bb]), w = ra / (ra + rb);
+        for (int a = 0; a < 3; ++a) xm[a] = c0[3 * ba + a] + w * (c1[3 * bb + a] - c0[3 * ba + a]);
+    }
+    int iters = cont ? DEM_NEWTON_CONT : DEM_NEWTON_NEW;
+    for (int it = 0; it < iters; ++it) {
+        double g0[3], g1[3], H0[6], H1[6];
+        mb_eval(c0, k0, n0, xm, g0, H0);
+        mb_eval(c1, k1, n1, xm, g1, H1);
+        double G[3] = {g0[0] + g1[0], g0[1] + g1[1], g0[2] + g1[2]};
+        double A[3][3] = {{H0[0] + H1[0], H0[3] + H1[3], H0[4] + H1[4]},
+                          {H0[3] + H1[3], H0[1] + H1[1], H0[5] + H1[5]},
+                          {H0[4] + H1[4], H0[5] + H1[5], H0[2] + H1[2]}};
+        if (!newton_update(A, G, xm)) break;
+    }
+    surface_along(c0, k0, n0, xm, xc0);
+    surface_along(c1, k1, n1, xm, xc1);
+    double d[3] = {xc1[0] - xc0[0], xc1[1] - xc0[1], xc1[2] - xc0[2]};
+    double dist = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    double delta = Rs0 + Rs1 - dist;
+    for (int a = 0; a < 3; ++a) nrm[a] = dist > 0.0 ? d[a] / dist : 0.0;
+    for (int a = 0; a < 3; ++a) xcp[a] = xc0[a] + (Rs0 - 0.5 * delta) * nrm[a];
+    return delta;
+}
+
+/* Contact geometry of a particle and the face `side` (0: plane x_a = 0, 1: plane x_a = L) of
+ * walled axis a (Eqs. 10-11). Returns delta; writes x_cm, x_cw, n (into the box), x_cp. */
+static double dem_wall_geom(const double* c, const double* k, int n, int a, int side, double L, double Rs,
+                            int cont, double xm[3], double xcw[3], double nrm[3], double xcp[3])
+{
+    double sg = side ? -1.0 : 1.0;   /* inward normal along axis a */
+    if (!cont) {
+        int bi = 0;
+        double best = INFINITY;
+        for (int i = 0; i < n; ++i) {
+            double reach = side ? -(c[3 * i + a] + sqrt(k[i])) : c[3 * i + a] - sqrt(k[i]);
+            if (reach < best) { best = reach; bi = i; }
+        }
+        for (int b = 0; b < 3; ++b) xm[b] = c[3 * bi + b];
+        xm[a] -= sg * sqrt(k[bi]);
+    }
+    int b = (a + 1) % 3, cc = (a + 2) % 3;
+    if (b > cc) { int t = b; b = cc; cc = t; }
+    int iters = cont ? DEM_NEWTON_CONT : DEM_NEWTON_NEW;
+    for (int it = 0; it < iters; ++it) {
+        double g[3], H6[6];
+        double f = mb_eval(c, k, n, xm, g, H6);
+        double H[3][3] = {{H6[0], H6[3], H6[4]}, {H6[3], H6[1], H6[5]}, {H6[4], H6[5], H6[2]}};
+        double G[3] = {g[b], g[cc], f - 1.0};
+        double A[3][3] = {{H[b][0], H[b][1], H[b][2]}, {H[cc][0], H[cc][1], H[cc][2]}, {g[0], g[1], g[2]}};
+        if (!newton_update(A, G, xm)) break;
+    }
+    for (int d = 0; d < 3; ++d) { xcw[d] = xm[d]; nrm[d] = 0.0; }
+    xcw[a] = side ? L : 0.0;
+    nrm[a] = sg;
+    double dist = (xm[a] - xcw[a]) * sg;
+    double delta = Rs - dist;
+    for (int d = 0; d < 3; ++d) xcp[d] = xcw[d] + 0.5 * delta * nrm[d];
+    return delta;
+}
+
+/* Velocity of body p's material point at x (origin org): v + w x (x - org) */
+static void dem_point_velocity(const orc_t* o, int p, const double org[3], const double x[3], double v[3])
+{
+    const double* st = o->dst + 13 * (size_t)p;
+    double r[3] = {x[0] - org[0], x[1] - org[1], x[2] - org[2]};
+    const double* w = st + 10;
+    v[0] = st[7] + (w[1] * r[2] - w[2] * r[1]);
+    v[1] = st[8] + (w[2] * r[0] - w[0] * r[2]);
+    v[2] = st[9] + (w[0] * r[1] - w[1] * r[0]);
+}
+
+/* Contact force on body i (normal spring-dashpot and Eq. 5). n: from i towards the other body;
+ * vi, vj: contact-point velocities; xi: the contact's tangential spring, updated. */
+static void dem_contact_force(const orc_t* o, double delta, const double n[3], const double vi[3],
+                              const double vj[3], double dt, double xi[3], double F[3])
+{
+    double vr[3] = {vj[0] - vi[0], vj[1] - vi[1], vj[2] - vi[2]};
+    double vn = vr[0] * n[0] + vr[1] * n[1] + vr[2] * n[2];   /* -(v_i - v_j).n */
+    double Fn = o->dem_kn * delta - o->dem_etan * vn;
+    if (Fn < 0.0) Fn = 0.0;
+    double vt[3] = {vr[0] - vn * n[0], vr[1] - vn * n[1], vr[2] - vn * n[2]};
+    double xn = xi[0] * n[0] + xi[1] * n[1] + xi[2] * n[2];
+    for (int a = 0; a < 3; ++a) xi[a] = (xi[a] - xn * n[a]) + vt[a] * dt;
+    double Ft[3];
+    for (int a = 0; a < 3; ++a) Ft[a] = o->dem_kt * xi[a] + o->dem_etat * vt[a];
+    double mag = sqrt(Ft[0] * Ft[0] + Ft[1] * Ft[1] + Ft[2] * Ft[2]);
+    double lim = o->dem_mus * Fn;
+    if (mag > lim) {
+        double sc = lim / mag;
+        for (int a = 0; a < 3; ++a) {
+            Ft[a] = Ft[a] * sc;
+            xi[a] = o->dem_kt > 0.0 ? (Ft[a] - o->dem_etat * vt[a]) / o->dem_kt : 0.0;
+        }
+    }
+    for (int a = 0; a < 3; ++a) F[a] = Ft[a] - Fn * n[a];
+}
+
+static void cross3(const double a[3], const double b[3], double c[3])
+{
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+/* Minimum-image origin of particle j seen from particle i's origin (origins unwrapped) */
+static void dem_image(const orc_t* o, const double oi[3], const double oj[3], double out[3])
+{
+    for (int a = 0; a < 3; ++a) {
+        double d = oj[a] - oi[a];
+        if (!o->wall[a]) d -= (double)o->n[a] * floor(d / (double)o->n[a] + 0.5);
+        out[a] = oi[a] + d;
+    }
+}
+
+/* Pair (i < j) force and torques of one DEM step, from the state at its start; updates the
+ * pair's spring, Newton point and contact flag. Writes the force on i and both torques. */
+static void dem_pair(orc_t* o, int i, int j, double dt, double Fi[3], double Ti[3], double Tj[3],
+                     double* cbuf, double* kbuf)
+{
+    size_t pr = (size_t)i * o->P + j;
+    for (int a = 0; a < 3; ++a) Fi[a] = Ti[a] = Tj[a] = 0.0;
+    const double* si = o->dst + 13 * (size_t)i;
+    const double* sj = o->dst + 13 * (size_t)j;
+    double oj[3];
+    dem_image(o, si, sj, oj);
+    double d[3] = {oj[0] - si[0], oj[1] - si[1], oj[2] - si[2]};
+    double reach = o->Rb[i] + o->Rb[j];
+    if (d[0] * d[0] + d[1] * d[1] + d[2] * d[2] >= reach * reach) {   /* bound spheres apart */
+        o->dact[pr] = 0;
+        for (int a = 0; a < 3; ++a) o->dxi[3 * pr + a] = 0.0;
+        return;
+    }
+    double* c0 = cbuf; double* k0 = kbuf;
+    int n0 = dem_internal(o, i, si, c0, k0);
+    double* c1 = cbuf + 3 * n0; double* k1 = kbuf + n0;
+    int n1 = dem_internal(o, j, oj, c1, k1);
+    double xc0[3], xc1[3], nrm[3], xcp[3];
+    double* xm = o->dxm + 3 * pr;
+    double delta = dem_pair_geom(c0, k0, n0, c1, k1, n1, o->dRs[i], o->dRs[j], o->dact[pr], xm, xc0, xc1,
+                                 nrm, xcp);
+    double* xi = o->dxi + 3 * pr;
+    if (!(delta > 0.0)) {
+        o->dact[pr] = 0;
+        for (int a = 0; a < 3; ++a) xi[a] = 0.0;
+        return;
+    }
+    o->dact[pr] = 1;
+    double vi[3], vj[3];
+    dem_point_velocity(o, i, si, xcp, vi);
+    dem_point_velocity(o, j, oj, xcp, vj);
+    dem_contact_force(o, delta, nrm, vi, vj, dt, xi, Fi);
+    double ri[3] = {xcp[0] - si[0], xcp[1] - si[1], xcp[2] - si[2]};
+    double rj[3] = {xcp[0] - oj[0], xcp[1] - oj[1], xcp[2] - oj[2]};
+    double Fj[3] = {-Fi[0], -Fi[1], -Fi[2]};
+    cross3(ri, Fi, Ti);
+    cross3(rj, Fj, Tj);
+}
+
+/* Wall face f = 2 a + side of particle p: force and torque of one DEM step */
+static void dem_wall(orc_t* o, int p, int f, double dt, double Fw[3], double Tw[3], double* cbuf, double* kbuf)
+{
+    size_t wi = 6 * (size_t)p + f;
+    int a = f >> 1, side = f & 1;
+    for (int b = 0; b < 3; ++b) Fw[b] = Tw[b] = 0.0;
+    const double* sp = o->dst + 13 * (size_t)p;
+    double L = (double)o->n[a];
+    double gap = side ? L - sp[a] : sp[a];
+    if (!o->wall[a] || gap >= o->Rb[p]) {
+        o->dactw[wi] = 0;
+        for (int b = 0; b < 3; ++b) o->dxiw[3 * wi + b] = 0.0;
+        return;
+    }
+    int n = dem_internal(o, p, sp, cbuf, kbuf);
+    double xcw[3], nrm[3], xcp[3];
+    double* xm = o->dxmw + 3 * wi;
+    double delta = dem_wall_geom(cbuf, kbuf, n, a, side, L, o->dRs[p], o->dactw[wi], xm, xcw, nrm, xcp);
+    double* xi = o->dxiw + 3 * wi;
+    if (!(delta > 0.0)) {
+        o->dactw[wi] = 0;
+        for (int b = 0; b < 3; ++b) xi[b] = 0.0;
+        return;
+    }
+    o->dactw[wi] = 1;
+    double vi[3], vw[3] = {0.0, 0.0, 0.0};
+    dem_point_velocity(o, p, sp, xcp, vi);
+    double nw[3] = {-nrm[0], -nrm[1], -nrm[2]};   /* from the particle towards the wall */
+    dem_contact_force(o, delta, nw, vi, vw, dt, xi, Fw);
+    double r[3] = {xcp[0] - sp[0], xcp[1] - sp[1], xcp[2] - sp[2]};
+    cross3(r, Fw, Tw);
+}
+
+/* One DEM step of length dt (Eq. 4) with hydrodynamic force Fe, torque Te (may be NULL) */
+static void dem_substep(orc_t* o, double dt, const double* Fe, const double* Te)
+{
+    int P = o->P;
+    size_t PP = (size_t)P * P;
+    double* pF = (double*)calloc(3 * PP + 3, sizeof(double));
+    double* pTi = (double*)calloc(3 * PP + 3, sizeof(double));
+    double* pTj = (double*)calloc(3 * PP + 3, sizeof(double));
+    double* wF = (double*)calloc(18 * (size_t)P + 3, sizeof(double));
+    double* wT = (double*)calloc(18 * (size_t)P + 3, sizeof(double));
+    double* cbuf = (double*)malloc(sizeof(double) * (6 * (size_t)o->Nc + 6));
+    double* kbuf = (double*)malloc(sizeof(double) * (2 * (size_t)o->Nc + 2));
+    for (int i = 0; i < P; ++i)
+        for (int j = i + 1; j < P; ++j) {
+            size_t pr = (size_t)i * P + j;
+            dem_pair(o, i, j, dt, pF + 3 * pr, pTi + 3 * pr, pTj + 3 * pr, cbuf, kbuf);
+        }
+    for (int p = 0; p < P; ++p)
+        for (int f = 0; f < 6; ++f) dem_wall(o, p, f, dt, wF + 3 * (6 * (size_t)p + f), wT + 3 * (6 * (size_t)p + f), cbuf, kbuf);
+    for (int p = 0; p < P; ++p) {
+        double F[3] = {0.0, 0.0, 0.0}, T[3] = {0.0, 0.0, 0.0};
+        for (int j = 0; j < P; ++j) {
+            if (j < p) {
+                size_t pr = (size_t)j * P + p;
+                for (int a = 0; a < 3; ++a) { F[a] = F[a] - pF[3 * pr + a]; T[a] = T[a] + pTj[3 * pr + a]; }
+            } else if (j > p) {
+                size_t pr = (size_t)p * P + j;
+                for (int a = 0; a < 3; ++a) { F[a] = F[a] + pF[3 * pr + a]; T[a] = T[a] + pTi[3 * pr + a]; }
+            }
+        }
+        for (int f = 0; f < 6; ++f)
+            for (int a = 0; a < 3; ++a) {
+                F[a] = F[a] + wF[3 * (6 * (size_t)p + f) + a];
+                T[a] = T[a] + wT[3 * (6 * (size_t)p + f) + a];
+            }
+        double m = o->dmass[p];
+        for (int a = 0; a < 3; ++a) {
+            if (Fe) { F[a] = F[a] + Fe[3 * p + a]; T[a] = T[a] + Te[3 * p + a]; }
+            F[a] = F[a] + m * o->dem_g[a];
+        }
+        double* st = o->dst + 13 * (size_t)p;
+        /* translation: symplectic Euler */
+        for (int a = 0; a < 3; ++a) {
+            st[7 + a] = st[7 + a] + dt * (F[a] / m);
+            st[a] = st[a] + dt * st[7 + a];
+        }
+        /* rotation: I_w = R I_b R^T, w += dt I_w^-1 (T - w x I_w w) */
+        double R[3][3];
+        quat_matrix(st + 3, R);
+        const double* Ib6 = o->dIb + 6 * (size_t)p;
+        double Ib[3][3] = {{Ib6[0], Ib6[3], Ib6[4]}, {Ib6[3], Ib6[1], Ib6[5]}, {Ib6[4], Ib6[5], Ib6[2]}};
+        double RI[3][3], Iw[3][3];
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) RI[a][b] = R[a][0] * Ib[0][b] + R[a][1] * Ib[1][b] + R[a][2] * Ib[2][b];
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) Iw[a][b] = RI[a][0] * R[b][0] + RI[a][1] * R[b][1] + RI[a][2] * R[b][2];
+        double* w = st + 10;
+        double Lw[3] = {Iw[0][0] * w[0] + Iw[0][1] * w[1] + Iw[0][2] * w[2],
+                        Iw[1][0] * w[0] + Iw[1][1] * w[1] + Iw[1][2] * w[2],
+                        Iw[2][0] * w[0] + Iw[2][1] * w[1] + Iw[2][2] * w[2]};
+        double gyro[3];
+        cross3(w, Lw, gyro);
+        double rhs[3] = {T[0] - gyro[0], T[1] - gyro[1], T[2] - gyro[2]}, dw[3];
+        if (solve3(Iw, rhs, dw))
+            for (int a = 0; a < 3; ++a) w[a] = w[a] + dt * dw[a];
+        /* orientation: q += dt/2 (0, w) q, normalised */
+        double* q = st + 3;
+        double qw = q[0], qv[3] = {q[1], q[2], q[3]}, wxq[3];
+        cross3(w, qv, wxq);
+        double h = 0.5 * dt;
+        double nq[4] = {qw - h * (w[0] * qv[0] + w[1] * qv[1] + w[2] * qv[2]),
+                        qv[0] + h * (qw * w[0] + wxq[0]),
+                        qv[1] + h * (qw * w[1] + wxq[1]),
+                        qv[2] + h * (qw * w[2] + wxq[2])};
+        double nn = sqrt(nq[0] * nq[0] + nq[1] * nq[1] + nq[2] * nq[2] + nq[3] * nq[3]);
+        for (int a = 0; a < 4; ++a) q[a] = nq[a] / nn;
+    }
+    free(pF); free(pTi); free(pTj); free(wF); free(wT); free(cbuf); free(kbuf);
+}
+
+/* The DEM part of one LBM step: `substeps` DEM steps with the hydrodynamic force and torque of
+ * the LBM update just made (Fp, Tp), when the coupling is on */
+static void dem_advance(orc_t* o)
+{
+    double dt = 1.0 / (double)o->dem_nsub;
+    for (int s = 0; s < o->dem_nsub; ++s)
+        dem_substep(o, dt, o->dem_hydro ? o->Fp : NULL, o->dem_hydro ? o->Tp : NULL);
+}
+
+/* ------------------------------------------------------------------------------------------
  * Exported API (ctypes). All arrays are host arrays owned by the caller.
  * ------------------------------------------------------------------------------------------ */
 ORC_API void* orc_create(const int dims[3], int q, double tau, double D, uint64_t seed,
@@ -1060,6 +1545,8 @@ ORC_API void orc_destroy(void* h)
     free(o->coff); free(o->cbody); free(o->kc); free(o->kc32);
     free(o->org); free(o->amp); free(o->per); free(o->pha); free(o->omg); free(o->Rb);
     free(o->Fp); free(o->Tp); free(o->x); free(o->x0);
+    free(o->dst); free(o->dmass); free(o->dIb); free(o->dRs); free(o->dzoom);
+    free(o->dxi); free(o->dxm); free(o->dact); free(o->dxiw); free(o->dxmw); free(o->dactw);
     free(o);
 }
 
@@ -1158,6 +1645,7 @@ ORC_API void orc_step(void* h, long long nsteps)
     for (long long s = 0; s < nsteps; ++s) {
         if (!o->coupling) rasterize(o, o->t);
         lbm_step(o, o->t);
+        if (o->dem) dem_advance(o);   /* particles t -> t+1 with the force of this update */
         walkers_step(o, o->t);
         o->t++;
     }
@@ -1170,6 +1658,7 @@ ORC_API void orc_step_fluid(void* h, long long nsteps)
     for (long long s = 0; s < nsteps; ++s) {
         if (!o->coupling) rasterize(o, o->t);
         lbm_step(o, o->t);
+        if (o->dem) dem_advance(o);
         o->t++;
     }
 }
@@ -1449,4 +1938,110 @@ ORC_API void orc_lattice(int q, int* e, double* w)
         for (int a = 0; a < 3; ++a) e[3 * i + a] = lattice_e(q, i)[a];
         w[i] = lattice_weight(q, i);
     }
+}
+
+/* Free DEM set-up: contact law, gravity, DEM steps per LBM step, hydrodynamic coupling on/off,
+ * and per particle the mass, body-frame inertia (xx yy zz xy xz yz), sphere radius R_s, initial
+ * velocity and spin (NULL: those of the prescribed motion at the current time). The state starts
+ * at the prescribed origin of the current time with the body frame as given (identity
+ * orientation). Returns 0, or -1 for an invalid set-up. */
+ORC_API int orc_set_dem(void* h, double kn, double etan, double kt, double etat, double mus,
+                        const double g[3], int nsub, int hydro, const double* mass, const double* inertia,
+                        const double* Rs, const double* v0, const double* w0)
+{
+    orc_t* o = (orc_t*)h;
+    int P = o->P;
+    if (o->coupling != 0 || nsub < 1 || P < 1 || kn < 0.0 || etan < 0.0 || kt < 0.0 || etat < 0.0 || mus < 0.0)
+        return -1;
+    for (int p = 0; p < P; ++p)
+        if (!(mass[p] > 0.0) || !(Rs[p] > 0.0) || !(Rs[p] < o->Rb[p])) return -1;
+    free(o->dst); free(o->dmass); free(o->dIb); free(o->dRs); free(o->dzoom);
+    free(o->dxi); free(o->dxm); free(o->dact); free(o->dxiw); free(o->dxmw); free(o->dactw);
+    size_t PP = (size_t)P * P;
+    o->dst = (double*)calloc(13 * (size_t)P, sizeof(double));
+    o->dmass = (double*)malloc(sizeof(double) * (size_t)P);
+    o->dIb = (double*)malloc(sizeof(double) * 6 * (size_t)P);
+    o->dRs = (double*)malloc(sizeof(double) * (size_t)P);
+    o->dzoom = (double*)malloc(sizeof(double) * (size_t)P);
+    o->dxi = (double*)calloc(3 * PP, sizeof(double));
+    o->dxm = (double*)calloc(3 * PP, sizeof(double));
+    o->dact = (unsigned char*)calloc(PP, 1);
+    o->dxiw = (double*)calloc(18 * (size_t)P, sizeof(double));
+    o->dxmw = (double*)calloc(18 * (size_t)P, sizeof(double));
+    o->dactw = (unsigned char*)calloc(6 * (size_t)P, 1);
+    o->dem_kn = kn; o->dem_etan = etan; o->dem_kt = kt; o->dem_etat = etat; o->dem_mus = mus;
+    for (int a = 0; a < 3; ++a) o->dem_g[a] = g[a];
+    o->dem_nsub = nsub;
+    o->dem_hydro = hydro ? 1 : 0;
+    for (int p = 0; p < P; ++p) {
+        double org[3], vel[3], R[3][3];
+        particle_pose(o, o->t, p, org, vel, R);
+        double* st = o->dst + 13 * (size_t)p;
+        for (int a = 0; a < 3; ++a) {
+            st[a] = org[a];
+            st[7 + a] = v0 ? v0[3 * p + a] : vel[a];
+            st[10 + a] = w0 ? w0[3 * p + a] : o->omg[3 * p + a];
+        }
+        st[3] = 1.0; st[4] = st[5] = st[6] = 0.0;
+        o->dmass[p] = mass[p];
+        for (int m = 0; m < 6; ++m) o->dIb[6 * p + m] = inertia[6 * p + m];
+        o->dRs[p] = Rs[p];
+        o->dzoom[p] = 1.0 - Rs[p] / o->Rb[p];
+    }
+    o->dem = 1;
+    o->solid_time = -1;
+    return 0;
+}
+
+ORC_API void orc_particle_state(void* h, double* out)
+{
+    orc_t* o = (orc_t*)h;
+    if (o->dem) memcpy(out, o->dst, sizeof(double) * 13 * (size_t)o->P);
+}
+
+ORC_API void orc_set_particle_state(void* h, const double* st)
+{
+    orc_t* o = (orc_t*)h;
+    if (o->dem) memcpy(o->dst, st, sizeof(double) * 13 * (size_t)o->P);
+    o->solid_time = -1;
+}
+
+/* Contact geometry of pair (i, j) in the current state, as a new contact (Eqs. 7-9):
+ * out = x_m[3], x_c0[3], x_c1[3], n[3], delta, x_cp[3] */
+ORC_API void orc_dem_pair_geom(void* h, int i, int j, double* out)
+{
+    orc_t* o = (orc_t*)h;
+    double* cbuf = (double*)malloc(sizeof(double) * (6 * (size_t)o->Nc + 6));
+    double* kbuf = (double*)malloc(sizeof(double) * (2 * (size_t)o->Nc + 2));
+    const double* si = o->dst + 13 * (size_t)i;
+    double oj[3];
+    dem_image(o, si, o->dst + 13 * (size_t)j, oj);
+    int n0 = dem_internal(o, i, si, cbuf, kbuf);
+    int n1 = dem_internal(o, j, oj, cbuf + 3 * n0, kbuf + n0);
+    double xm[3];
+    out[12] = dem_pair_geom(cbuf, kbuf, n0, cbuf + 3 * n0, kbuf + n0, n1, o->dRs[i], o->dRs[j], 0, xm,
+                            out + 3, out + 6, out + 9, out + 13);
+    for (int a = 0; a < 3; ++a) out[a] = xm[a];
+    free(cbuf); free(kbuf);
+}
+
+/* Contact geometry of particle p and wall face f = 2 axis + side, as a new contact (Eqs. 10-11):
+ * out = x_cm[3], x_cw[3], n[3], delta, x_cp[3] */
+ORC_API void orc_dem_wall_geom(void* h, int p, int f, double* out)
+{
+    orc_t* o = (orc_t*)h;
+    double* cbuf = (double*)malloc(sizeof(double) * (3 * (size_t)o->Nc + 3));
+    double* kbuf = (double*)malloc(sizeof(double) * ((size_t)o->Nc + 1));
+    int n = dem_internal(o, p, o->dst + 13 * (size_t)p, cbuf, kbuf);
+    out[9] = dem_wall_geom(cbuf, kbuf, n, f >> 1, f & 1, (double)o->n[f >> 1], o->dRs[p], 0, out, out + 3,
+                           out + 6, out + 10);
+    free(cbuf); free(kbuf);
+}
+
+/* DEM steps alone (no fluid, no walkers): the hydrodynamic force and torque are those of the
+ * last LBM update when the coupling is on */
+ORC_API void orc_dem_advance(void* h, long long nsteps)
+{
+    orc_t* o = (orc_t*)h;
+    for (long long s = 0; s < nsteps; ++s) dem_advance(o);
 }

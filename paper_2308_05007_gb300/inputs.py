@@ -53,6 +53,32 @@ class Metaballs:
 
 
 @dataclass
+class Dem:
+    """Free DEM set-up (Eqs. 4-11), lattice units. The particles then move under gravity, contact
+    forces and (with hydro = 1) the fluid's force and torque, instead of following prescribed
+    trajectories; the prescribed motion only gives the start (origin, and velocity and spin when
+    these are None).
+
+    Per particle: mass, body-frame inertia about the origin (xx, yy, zz, xy, xz, yz), and the
+    sphero-metaball sphere radius R_s. Contact law: normal stiffness kn and damping eta_n,
+    tangential stiffness kt and damping eta_t, static friction mu_s. `substeps` DEM steps make
+    one LBM step."""
+    mass: np.ndarray                     # float64 [P]
+    inertia: np.ndarray                  # float64 [P, 6]
+    sphere_radius: np.ndarray            # float64 [P]
+    velocity: Optional[np.ndarray] = None  # float64 [P, 3]
+    spin: Optional[np.ndarray] = None      # float64 [P, 3]
+    kn: float = 200.0
+    eta_n: float = 0.0
+    kt: float = 0.0
+    eta_t: float = 0.0
+    mu_s: float = 0.0
+    gravity: tuple = (0.0, 0.0, 0.0)
+    substeps: int = 10
+    hydro: int = 1
+
+
+@dataclass
 class Workload:
     name: str
     dims: tuple                          # (nx, ny, nz)
@@ -74,6 +100,7 @@ class Workload:
     sort_interval: int = 0
     moment_interval: int = 0
     coupling: int = 0                    # 0 partially saturated cells, 1 IBB (Section 2.4.3)
+    dem: Optional[Dem] = None            # free DEM instead of prescribed trajectories
     notes: str = ""
 
     @property
@@ -340,3 +367,82 @@ def served(n_requests: int = 64, rate: float = 20.0, seed: int = 4, edge=(32, 25
 
 def with_(w: Workload, **kw) -> Workload:
     return replace(w, **kw)
+
+
+# ------------------------------------------------------------------------------------------
+# Free-DEM inputs
+# ------------------------------------------------------------------------------------------
+def cluster_mass_properties(mb: Metaballs, density: float):
+    """Mass properties of each particle, approximated by the spheres of radius sqrt(k_i) about
+    its control points (overlaps counted twice) at the given density. The body frame is moved
+    to that approximate centre of mass (control points and origin shifted together, so the
+    world positions stay the same). Returns (recentred Metaballs, mass [P], inertia [P, 6]
+    about the new origin: xx, yy, zz, xy, xz, yz)."""
+    P = mb.n_particles
+    cb = mb.centers_body.astype(np.float64).copy()
+    origin = mb.origin.astype(np.float64).copy()
+    mass = np.zeros(P)
+    inertia = np.zeros((P, 6))
+    for p in range(P):
+        sl = slice(int(mb.center_offsets[p]), int(mb.center_offsets[p + 1]))
+        r = np.sqrt(mb.k[sl].astype(np.float64))
+        mi = density * (4.0 / 3.0) * math.pi * r ** 3
+        com = (mi[:, None] * cb[sl]).sum(0) / mi.sum()
+        cb[sl] -= com
+        origin[p] += com
+        c = cb[sl]
+        sph = 0.4 * mi * r ** 2
+        cc = (c * c).sum(1)
+        I = np.zeros((3, 3))
+        for m_, s_, v, v2 in zip(mi, sph, c, cc):
+            I += s_ * np.eye(3) + m_ * (v2 * np.eye(3) - np.outer(v, v))
+        mass[p] = mi.sum()
+        inertia[p] = [I[0, 0], I[1, 1], I[2, 2], I[0, 1], I[0, 2], I[1, 2]]
+    mb2 = replace(mb, centers_body=cb.astype(np.float32), origin=origin)
+    return mb2, mass, inertia
+
+
+def sphere_radii(mb: Metaballs, fraction: float = 0.5) -> np.ndarray:
+    """R_s of each particle: a fraction of its smallest control-point radius sqrt(k_i). Every
+    such sphere lies inside the particle, so R_s stays below the bound radius."""
+    out = np.zeros(mb.n_particles)
+    for p in range(mb.n_particles):
+        sl = slice(int(mb.center_offsets[p]), int(mb.center_offsets[p + 1]))
+        out[p] = fraction * float(np.sqrt(mb.k[sl].astype(np.float64)).min())
+    return out
+
+
+def dem_box(dims=(40, 36, 44), n_particles: int = 4, seed: int = 11, density: float = 2.5,
+            speed: float = 0.05, gravity=(0.0, 0.0, -5e-4), kn: float = 50.0, eta_n: float = 2.0,
+            kt: float = 20.0, eta_t: float = 1.0, mu_s: float = 0.4, substeps: int = 10,
+            hydro: int = 1, n_walkers: int = 3000, storage: int = 1, q: int = 15) -> Workload:
+    """Small walled box (z-walls) of free multi-centre particles: random start velocities of the
+    given speed, gravity along -z, damped frictional contacts; several contacts within a few
+    tens of steps. Parity and invariant tests use it."""
+    rng = np.random.default_rng(seed)
+    mb = random_metaballs(rng, n_particles, dims, wall_mask=4, n_centers=(2, 3), sigma=1.2,
+                          k_range=(4.0, 9.0))
+    mb, mass, inertia = cluster_mass_properties(mb, density)
+    v = rng.normal(size=(n_particles, 3))
+    v *= speed / np.linalg.norm(v, axis=1, keepdims=True)
+    w = rng.normal(scale=0.01, size=(n_particles, 3))
+    dem = Dem(mass=mass, inertia=inertia, sphere_radius=sphere_radii(mb), velocity=v, spin=w, kn=kn,
+              eta_n=eta_n, kt=kt, eta_t=eta_t, mu_s=mu_s, gravity=tuple(gravity), substeps=substeps,
+              hydro=hydro)
+    return Workload(
+        name=f"dem_box_{dims[0]}x{dims[1]}x{dims[2]}", dims=tuple(dims), tau=0.8, D=0.02, seed=seed, q=q,
+        wall_mask=4, metaballs=mb, dem=dem, n_walkers=n_walkers,
+        walker_box=((0.0, 0.0, 0.0), tuple(float(d) for d in dims)), steps=40, storage=storage)
+
+
+def oscillator_dem(n: int = 256, n_particles: int = 64, n_walkers: int = 10_000_000, density: float = 2.0,
+                   gravity=(0.0, 0.0, -2e-5), kn: float = 1000.0, eta_n: float = 20.0, kt: float = 400.0,
+                   eta_t: float = 10.0, mu_s: float = 0.5, substeps: int = 10, **kw) -> Workload:
+    """The oscillator workload with free particles: they start on their prescribed motion
+    (x-velocity 5 (2 pi / 2000)) and then move under the oscillating flow, gravity and
+    contacts."""
+    w = oscillator(n=n, n_particles=n_particles, n_walkers=n_walkers, **kw)
+    mb, mass, inertia = cluster_mass_properties(w.metaballs, density)
+    dem = Dem(mass=mass, inertia=inertia, sphere_radius=sphere_radii(mb), kn=kn, eta_n=eta_n, kt=kt,
+              eta_t=eta_t, mu_s=mu_s, gravity=tuple(gravity), substeps=substeps, hydro=1)
+    return replace(w, name=f"oscillator_dem_{n}", metaballs=mb, dem=dem)

@@ -1,0 +1,251 @@
+"""Pins for the oracle's free DEM (Section 2.2, Eqs. 4-11), independent of the oracle itself:
+closed forms for sphere contacts (single-centre metaballs are spheres, and the sphero-metaball
+of a sphere is that sphere), conservation laws, a separately integrated contact ODE for the
+coefficient of restitution, the static overlap under gravity, the 5/7 rolling law, the exact
+free-fall sequence of symplectic Euler, and torque-free spin."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle.oracle import Oracle
+from paper_2308_05007_gb300 import inputs as I
+
+
+def _spheres(centers, ks, dims=(48, 48, 48), walls=0, Rs=None, velocity=None, spin=None, kn=200.0,
+             eta_n=0.0, kt=0.0, eta_t=0.0, mu_s=0.0, gravity=(0.0, 0.0, 0.0), substeps=20, density=2.0):
+    P = len(ks)
+    mb = I.Metaballs(
+        center_offsets=np.arange(P + 1, dtype=np.int32),
+        centers_body=np.zeros((P, 3), np.float32),
+        k=np.asarray(ks, np.float32),
+        origin=np.asarray(centers, np.float64).reshape(P, 3),
+        amplitude=np.zeros((P, 3)), period=np.zeros(P), phase=np.zeros(P), omega=np.zeros((P, 3)))
+    mb, mass, inertia = I.cluster_mass_properties(mb, density)
+    dem = I.Dem(mass=mass, inertia=inertia,
+                sphere_radius=np.asarray(Rs if Rs is not None else [0.25 * math.sqrt(k) for k in ks], float),
+                velocity=None if velocity is None else np.asarray(velocity, float),
+                spin=None if spin is None else np.asarray(spin, float),
+                kn=kn, eta_n=eta_n, kt=kt, eta_t=eta_t, mu_s=mu_s, gravity=gravity, substeps=substeps,
+                hydro=0)
+    w = I.Workload(name="dem_spheres", dims=dims, tau=0.8, D=0.0, seed=0, wall_mask=walls, metaballs=mb,
+                   dem=dem)
+    return Oracle.from_workload(w, seed_walkers=False), mass, inertia
+
+
+def test_pair_geometry_of_two_spheres_is_exact():
+    """Two single-centre particles (radii 6 and 4) overlapping by 0.1 along an oblique line:
+    Eqs. 7-9 give the overlap exactly, the normal along the line of centres (from 0 towards 1)
+    and the contact point in the middle of the overlap, for any sphere radius R_s."""
+    u = np.array([1.0, 2.0, 2.0]) / 3.0
+    o0 = np.array([20.0, 17.0, 15.0])
+    o1 = o0 + 9.9 * u
+    for Rs in ([1.5, 1.0], [3.0, 0.5], [0.2, 2.5]):
+        o, _, _ = _spheres([o0, o1], [36.0, 16.0], Rs=Rs)
+        g = o.dem_pair_geom(0, 1)
+        assert g["delta"] == pytest.approx(0.1, abs=1e-9)
+        np.testing.assert_allclose(g["n"], u, atol=1e-10)
+        np.testing.assert_allclose(g["xcp"], o0 + (6.0 - 0.05) * u, atol=1e-9)
+        np.testing.assert_allclose(g["xc0"], o0 + (6.0 - Rs[0]) * u, atol=1e-9)
+        np.testing.assert_allclose(g["xc1"], o1 - (4.0 - Rs[1]) * u, atol=1e-9)
+        # the stationary point of f0 + f1 lies on the line of centres
+        r = g["xm"] - o0
+        assert np.linalg.norm(r - (r @ u) * u) < 1e-9
+
+
+def test_pair_geometry_across_a_periodic_face():
+    """The same pair split by the periodic x face: the minimum image gives the same contact."""
+    u = np.array([1.0, 0.0, 0.0])
+    o0 = np.array([45.0, 20.0, 20.0])
+    o1 = o0 + 9.9 * u - np.array([48.0, 0.0, 0.0])
+    o, _, _ = _spheres([o0, o1], [36.0, 16.0], Rs=[1.5, 1.0])
+    g = o.dem_pair_geom(0, 1)
+    assert g["delta"] == pytest.approx(0.1, abs=1e-9)
+    np.testing.assert_allclose(g["n"], u, atol=1e-10)
+
+
+def test_wall_geometry_of_a_sphere_is_exact():
+    """A sphere of radius 5 at height 4.7 over the z = 0 face overlaps it by 0.3; one at 4.8 below
+    the z = 48 face by 0.2. Normal into the box, contact point delta/2 inside it (Eq. 11)."""
+    o, _, _ = _spheres([[20.0, 21.0, 4.7], [30.0, 25.0, 43.2]], [25.0, 25.0], walls=4, Rs=[1.0, 2.0])
+    lo = o.dem_wall_geom(0, 4)
+    assert lo["delta"] == pytest.approx(0.3, abs=1e-9)
+    np.testing.assert_allclose(lo["n"], [0, 0, 1], atol=0)
+    np.testing.assert_allclose(lo["xcw"], [20.0, 21.0, 0.0], atol=1e-9)
+    np.testing.assert_allclose(lo["xcp"], [20.0, 21.0, 0.15], atol=1e-9)
+    np.testing.assert_allclose(lo["xcm"], [20.0, 21.0, 4.7 - 4.0], atol=1e-9)
+    hi = o.dem_wall_geom(1, 5)
+    assert hi["delta"] == pytest.approx(0.2, abs=1e-9)
+    np.testing.assert_allclose(hi["n"], [0, 0, -1], atol=0)
+
+
+def test_pair_geometry_is_symmetric_for_clusters():
+    """Multi-centre particles: exchanging the two gives the same overlap and the opposite normal."""
+    w = I.dem_box(n_particles=2, seed=5)
+    mb = w.metaballs
+    # move particle 1 next to particle 0
+    d = np.array([1.0, 0.4, -0.3]) / np.linalg.norm([1.0, 0.4, -0.3])
+    o = Oracle.from_workload(w, seed_walkers=False)
+    st = o.particle_state()
+    for gap in (3.0, 4.0, 5.0):
+        st[1, :3] = st[0, :3] + gap * d
+        o.set_particle_state(st)
+        a, b = o.dem_pair_geom(0, 1), o.dem_pair_geom(1, 0)
+        assert a["delta"] == pytest.approx(b["delta"], abs=1e-9)
+        np.testing.assert_allclose(a["n"], -b["n"], atol=1e-9)
+        assert abs(np.linalg.norm(a["n"]) - 1.0) < 1e-12
+    del mb
+
+
+def test_free_fall_is_the_symplectic_euler_sequence():
+    """No contact: after k DEM steps v = k dt g and z = z0 + dt^2 g k (k + 1) / 2 exactly (to
+    rounding), and the spin-free orientation stays the identity."""
+    g = -3e-4
+    o, _, _ = _spheres([[24.0, 24.0, 30.0]], [9.0], gravity=(0.0, 0.0, g), substeps=8)
+    o.dem_advance(5)
+    st = o.particle_state()[0]
+    k, dt = 40, 1.0 / 8
+    assert st[9] == pytest.approx(k * dt * g, rel=1e-13)
+    assert st[2] == pytest.approx(30.0 + dt * dt * g * k * (k + 1) / 2, abs=1e-12)
+    np.testing.assert_array_equal(st[3:7], [1.0, 0.0, 0.0, 0.0])
+
+
+def _head_on(m_ratio_k=(36.0, 16.0), v=(0.03, -0.02), eta_n=0.0, kn=200.0, substeps=40, steps=400):
+    u = np.array([0.0, 0.6, 0.8])
+    o0 = np.array([24.0, 14.0, 14.0])
+    o1 = o0 + 10.4 * u
+    o, mass, _ = _spheres([o0, o1], list(m_ratio_k), Rs=[1.0, 1.0], velocity=[v[0] * u, v[1] * u],
+                          kn=kn, eta_n=eta_n, substeps=substeps)
+    p_hist, e_hist, contact = [], [], False
+    for _ in range(steps):
+        o.dem_advance(1)
+        st = o.particle_state()
+        p_hist.append(mass[0] * st[0, 7:10] + mass[1] * st[1, 7:10])
+        e_hist.append(0.5 * mass[0] * st[0, 7:10] @ st[0, 7:10] + 0.5 * mass[1] * st[1, 7:10] @ st[1, 7:10])
+        gap = np.linalg.norm(st[1, :3] - st[0, :3]) - 10.0
+        contact |= gap < 0
+    st = o.particle_state()
+    return o, mass, u, np.array(p_hist), np.array(e_hist), st, contact
+
+
+def test_elastic_collision_conserves_momentum_and_energy():
+    """Head-on elastic collision of unequal spheres: momentum is conserved to rounding at every
+    step (equal and opposite pair forces), and the final velocities are the elastic ones to the
+    integrator's O(dt) error."""
+    o, mass, u, P, E, st, contact = _head_on()
+    assert contact
+    p0 = mass[0] * 0.03 * u + mass[1] * (-0.02) * u
+    assert np.abs(P - p0).max() <= 1e-13 * np.abs(p0).max() * 10
+    v0, v1 = 0.03, -0.02
+    m0, m1 = mass
+    v0f = ((m0 - m1) * v0 + 2 * m1 * v1) / (m0 + m1)
+    v1f = ((m1 - m0) * v1 + 2 * m0 * v0) / (m0 + m1)
+    assert st[0, 7:10] @ u == pytest.approx(v0f, rel=2e-3)
+    assert st[1, 7:10] @ u == pytest.approx(v1f, rel=2e-3)
+    assert E[-1] == pytest.approx(E[0], rel=2e-3)
+
+
+def _restitution_ode(m_eff, kn, eta, v_in, dt=1e-4):
+    """Brute-force RK4 of the 1D contact: overlap x, m_eff x'' = -max(0, kn x + eta x')."""
+    def acc(x, v):
+        return -max(0.0, kn * x + eta * v) / m_eff
+    x, v = 0.0, v_in
+    while True:
+        k1x, k1v = v, acc(x, v)
+        k2x, k2v = v + 0.5 * dt * k1v, acc(x + 0.5 * dt * k1x, v + 0.5 * dt * k1v)
+        k3x, k3v = v + 0.5 * dt * k2v, acc(x + 0.5 * dt * k2x, v + 0.5 * dt * k2v)
+        k4x, k4v = v + dt * k3v, acc(x + dt * k3x, v + dt * k3v)
+        x += dt / 6 * (k1x + 2 * k2x + 2 * k3x + k4x)
+        v += dt / 6 * (k1v + 2 * k2v + 2 * k3v + k4v)
+        if x < 0.0 and v < 0.0:
+            return -v / v_in
+
+
+def test_damped_collision_restitution_matches_the_contact_ode():
+    eta = 15.0
+    o, mass, u, P, E, st, contact = _head_on(eta_n=eta, substeps=200, steps=300)
+    m_eff = mass[0] * mass[1] / (mass[0] + mass[1])
+    e_ode = _restitution_ode(m_eff, 200.0, eta, 0.05)
+    rel_out = (st[0, 7:10] - st[1, 7:10]) @ u
+    e_dem = -rel_out / 0.05
+    assert 0.2 < e_ode < 0.95
+    assert e_dem == pytest.approx(e_ode, abs=2e-3)
+
+
+def test_resting_overlap_on_the_floor_is_mg_over_kn():
+    g, kn = -4e-4, 200.0
+    o, mass, _ = _spheres([[24.0, 24.0, 4.95]], [25.0], walls=4, gravity=(0.0, 0.0, g), kn=kn, eta_n=60.0,
+                          substeps=20)
+    o.dem_advance(1200)   # the start overlap of 0.05 bounces it for ~500 steps
+    st = o.particle_state()[0]
+    delta = 5.0 - st[2]
+    assert delta == pytest.approx(-mass[0] * g / kn, rel=1e-6)
+    assert abs(st[9]) < 1e-9
+
+
+def test_sliding_sphere_ends_rolling_at_five_sevenths():
+    """A solid sphere launched without spin along a floor with Coulomb friction slides, then
+    rolls without slipping at 5/7 of its launch speed (I = 2/5 m r^2)."""
+    g, kn, v0 = -1e-3, 400.0, 0.04
+    rest = 4.0 - 0.5 * (0.0)  # centre height; the overlap settles at m g / kn
+    o, mass, inertia = _spheres([[10.0, 24.0, rest]], [16.0], walls=4, gravity=(0.0, 0.0, g), kn=kn,
+                                eta_n=40.0, kt=200.0, eta_t=10.0, mu_s=0.3, velocity=[[v0, 0.0, 0.0]],
+                                substeps=20)
+    assert inertia[0, 0] == pytest.approx(0.4 * mass[0] * 16.0, rel=1e-12)
+    o.dem_advance(800)
+    st = o.particle_state()[0]
+    vx, wy = st[7], st[11]
+    assert vx == pytest.approx(5.0 / 7.0 * v0, rel=1.5e-2)
+    r = 4.0 - 0.5 * (-mass[0] * g / kn)   # lever arm: centre to the contact point
+    assert vx - wy * r == pytest.approx(0.0, abs=2e-4 * v0 * 10)
+
+
+def test_torque_free_isotropic_spin():
+    """An isotropic body spins at constant angular velocity (the gyroscopic term vanishes
+    exactly) and its orientation turns by |w| t about w, to the first-order integrator's error."""
+    w = np.array([0.004, -0.006, 0.012])
+    o, _, _ = _spheres([[24.0, 24.0, 24.0]], [9.0], spin=[w], substeps=10)
+    o.dem_advance(100)
+    st = o.particle_state()[0]
+    np.testing.assert_array_equal(st[10:13], w)
+    ang = np.linalg.norm(w) * 100
+    ax = w / np.linalg.norm(w)
+    want = np.concatenate([[math.cos(ang / 2)], math.sin(ang / 2) * ax])
+    np.testing.assert_allclose(st[3:7], want, atol=5e-4)
+    assert abs(np.linalg.norm(st[3:7]) - 1.0) < 1e-14
+
+
+def test_periodic_many_body_momentum_is_conserved():
+    """Frictional, damped collisions among several clusters in a periodic box, no gravity, no
+    walls, fluid force off: total momentum is conserved to rounding."""
+    w = I.dem_box(dims=(30, 28, 26), n_particles=5, seed=3, speed=0.08, gravity=(0.0, 0.0, 0.0), hydro=0)
+    w = I.with_(w, wall_mask=0)
+    o = Oracle.from_workload(w, seed_walkers=False)
+    m = w.dem.mass
+    p0 = (m[:, None] * o.particle_state()[:, 7:10]).sum(0)
+    touched = False
+    for _ in range(400):
+        o.dem_advance(1)
+        st = o.particle_state()
+        v = st[:, 7:10]
+        touched |= bool(np.abs(v - w.dem.velocity).max() > 1e-6)
+        p = (m[:, None] * v).sum(0)
+        assert np.abs(p - p0).max() <= 1e-12 * np.abs(m[:, None] * w.dem.velocity).sum()
+    assert touched
+
+
+def test_fluid_drags_free_particles():
+    """Coupled step (Eq. 4 with F^e, T^e from the partially saturated cells): particles at rest
+    in a fluid driven along x by a body force pick up +x velocity; fluid mass is conserved."""
+    w = I.dem_box(dims=(24, 22, 30), n_particles=2, seed=2, speed=0.0, gravity=(0.0, 0.0, 0.0), hydro=1,
+                  n_walkers=200)
+    w = I.with_(w, body_force=(2e-5, 0.0, 0.0))
+    w.dem.velocity[:] = 0.0
+    w.dem.spin[:] = 0.0
+    o = Oracle.from_workload(w)
+    o.step(30)
+    st = o.particle_state()
+    assert (st[:, 7] > 1e-6).all(), st[:, 7:10]
+    assert np.abs(st[:, 8:10]).max() < 0.5 * st[:, 7].min()
+    mass = o.density().sum()
+    assert mass == pytest.approx(o.n_cells * 1.0, rel=1e-12)
