@@ -141,6 +141,52 @@ RWMI_API rwmi_status rwmi_set_metaballs(rwmi_ctx* ctx, int32_t n_particles,
                                         const double* amplitude, const double* period,
                                         const double* phase, const double* omega);
 
+/* ---- Free DEM (Section 2.2, Eqs. 4-11) ------------------------------------------------------
+ * Instead of their prescribed trajectories the particles can move freely: Eq. 4 (Newton's and
+ * Euler's equations) under gravity, contact forces and the fluid's force and torque. Contacts
+ * use the sphero-metaball of Eqs. 6-11: the metaball scaled about its body origin by
+ * s = 1 - R_s / R_c (R_c = max_i |c_i| + sqrt(k_i)) and dilated by the sphere radius R_s; pair
+ * geometry by Newton-Raphson on grad(f_0 + f_1) = 0 (Eq. 7) and Eq. 8 solved for f = 1 along the
+ * gradient; wall geometry (faces of walled axes) by Newton-Raphson for the point of the scaled
+ * surface closest to the face. Normal force: linear spring-dashpot, k_n delta plus eta_n times
+ * the approach speed, never attractive. Tangential force: Eq. 5, a spring k_t xi plus damping
+ * eta_t, limited to mu_s times the normal force. Integration per DEM step dt = 1 / substeps:
+ * symplectic Euler for the origin, explicit Euler for the spin (world frame, gyroscopic term
+ * included) and a normalised first-order quaternion update for the orientation. The fluid force
+ * and torque of step t's LBM update act over its DEM steps (hydro = 1). The arithmetic is
+ * binary64 without contraction, so with hydro = 0 trajectories equal the CPU oracle's. */
+typedef struct {
+  double kn, eta_n;       /* normal stiffness and damping (lattice units) */
+  double kt, eta_t;       /* tangential stiffness and damping (Eq. 5) */
+  double mu_s;            /* static friction coefficient (Eq. 5) */
+  double gravity[3];      /* g of Eq. 4 */
+  int32_t substeps;       /* DEM steps per LBM step, >= 1 */
+  int32_t hydro;          /* 1: F^e, T^e of Eq. 4 are the fluid's force and torque; 0: none */
+} rwmi_dem_config;
+
+/* kn 200, eta_n 0, kt 0, eta_t 0, mu_s 0, gravity 0, substeps 10, hydro 1 */
+RWMI_API void rwmi_dem_defaults(rwmi_dem_config* cfg);
+
+/* Switches the current particles to the free DEM from the current time. Per particle (host
+ * arrays): mass [P] > 0, body-frame inertia tensor about the origin [6 P] (xx, yy, zz, xy, xz,
+ * yz), sphere radius R_s [P] with 0 < R_s < R_c, initial velocity and spin [3 P] (NULL: those of
+ * the prescribed motion at the current time). The state starts at the prescribed origin of the
+ * current time with the body frame as given. Requires partially saturated cells (coupling 0),
+ * binary32-shifted or binary64 storage, and at most 16 control points per particle; every step
+ * then forms the fluid force in the LBM update itself (one fused pass). RWMI_E_INVALID otherwise.
+ * Before the first step, or after a restart. */
+RWMI_API rwmi_status rwmi_set_dem(rwmi_ctx* ctx, const rwmi_dem_config* cfg, const double* mass,
+                                  const double* inertia, const double* sphere_radius,
+                                  const double* velocity, const double* spin);
+
+/* Free-DEM state, out[13 p .. 13 p + 12] = origin (unwrapped) x y z, orientation quaternion
+ * w x y z, velocity, spin (world frame), binary64; RWMI_E_STATE without rwmi_set_dem. */
+RWMI_API rwmi_status rwmi_particle_state(rwmi_ctx* ctx, double* out);
+
+/* Overwrites the free-DEM state (same layout, host array) and rebuilds the particle frame of
+ * the current time; contact memory (springs) is kept. */
+RWMI_API rwmi_status rwmi_set_particle_state(rwmi_ctx* ctx, const double* state);
+
 /* Seeds n walkers uniformly in the fluid part of the box [box_lo, box_hi] (inside the domain)
  * at the current time. Walker w draws Philox counters (w, a, 2, 0), a = 0, 1, ..., < 1000,
  * takes the point box_lo + U (box_hi - box_lo) and keeps the first one outside every particle
@@ -257,8 +303,9 @@ RWMI_API rwmi_status rwmi_walkers(rwmi_ctx* ctx, float* out, float* x0);
 RWMI_API rwmi_status rwmi_counters(rwmi_ctx* ctx, int64_t out[12]);
 
 /* Checkpoint and restart: populations, walkers (positions, start positions), the step
- * counter and the particle table. A restart continues bit-identically (noise is keyed by
- * walker id and step). */
+ * counter, the particle table and, in free-DEM runs, the particle state and contact memory. A
+ * restart continues bit-identically (noise is keyed by walker id and step). A free-DEM
+ * checkpoint loads into a context set up with rwmi_set_dem for the same particles. */
 RWMI_API rwmi_status rwmi_save(rwmi_ctx* ctx, const char* path);
 RWMI_API rwmi_status rwmi_load(rwmi_ctx* ctx, const char* path);
 

@@ -1033,9 +1033,10 @@ static long long walker_cell(const orc_t* o, const double x[3])
  * steps of dt = 1 / substeps. Readings (the paper leaves these open or defers them to its
  * references):
  *  - Sphero-metaball (Eq. 6 context): particle p's contact shape is its metaball scaled about the
- *    body origin by s_p = 1 - R_s,p / R_b,p (control points times s_p, weights times s_p^2) and
- *    dilated by the sphere radius R_s,p. R_b,p is the bound radius (f_p < 1 beyond it), so a
- *    single centre at the origin is reproduced exactly.
+ *    body origin by s_p = 1 - R_s,p / R_c,p (control points times s_p, weights times s_p^2) and
+ *    dilated by the sphere radius R_s,p, with R_c,p = max_i (|c_i| + sqrt(k_i)) over the
+ *    body-frame control points, so a single centre at the origin is reproduced exactly. The
+ *    bound radius R_b,p (f_p < 1 beyond it) only skips pairs and faces out of reach.
  *  - Pair contact (Eqs. 6-9): Newton-Raphson on grad(f0 + f1) = 0 (Eq. 7) for the internal
  *    metaballs, DEM_NEWTON_NEW iterations from the deterministic start below, or
  *    DEM_NEWTON_CONT from the previous substep's point while the contact lasts; a step longer
@@ -1940,6 +1941,19 @@ ORC_API void orc_lattice(int q, int* e, double* w)
     }
 }
 
+/* R_c = max_i (|c_i| + sqrt(k_i)) over particle p's body-frame control points */
+static double dem_reach(const orc_t* o, int p)
+{
+    double r = 0.0;
+    for (int i = o->coff[p]; i < o->coff[p + 1]; ++i) {
+        double c = sqrt(o->cbody[3 * i] * o->cbody[3 * i] + o->cbody[3 * i + 1] * o->cbody[3 * i + 1]
+                        + o->cbody[3 * i + 2] * o->cbody[3 * i + 2]);
+        double e = c + sqrt(o->kc[i]);
+        if (e > r) r = e;
+    }
+    return r;
+}
+
 /* Free DEM set-up: contact law, gravity, DEM steps per LBM step, hydrodynamic coupling on/off,
  * and per particle the mass, body-frame inertia (xx yy zz xy xz yz), sphere radius R_s, initial
  * velocity and spin (NULL: those of the prescribed motion at the current time). The state starts
@@ -1954,7 +1968,7 @@ ORC_API int orc_set_dem(void* h, double kn, double etan, double kt, double etat,
     if (o->coupling != 0 || nsub < 1 || P < 1 || kn < 0.0 || etan < 0.0 || kt < 0.0 || etat < 0.0 || mus < 0.0)
         return -1;
     for (int p = 0; p < P; ++p)
-        if (!(mass[p] > 0.0) || !(Rs[p] > 0.0) || !(Rs[p] < o->Rb[p])) return -1;
+        if (!(mass[p] > 0.0) || !(Rs[p] > 0.0) || !(Rs[p] < dem_reach(o, p))) return -1;
     free(o->dst); free(o->dmass); free(o->dIb); free(o->dRs); free(o->dzoom);
     free(o->dxi); free(o->dxm); free(o->dact); free(o->dxiw); free(o->dxmw); free(o->dactw);
     size_t PP = (size_t)P * P;
@@ -1986,7 +2000,7 @@ ORC_API int orc_set_dem(void* h, double kn, double etan, double kt, double etat,
         o->dmass[p] = mass[p];
         for (int m = 0; m < 6; ++m) o->dIb[6 * p + m] = inertia[6 * p + m];
         o->dRs[p] = Rs[p];
-        o->dzoom[p] = 1.0 - Rs[p] / o->Rb[p];
+        o->dzoom[p] = 1.0 - Rs[p] / dem_reach(o, p);
     }
     o->dem = 1;
     o->solid_time = -1;

@@ -11,7 +11,9 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "librwmi.so")
-SOURCES = ["rwmi_fluid.cu", "rwmi_lbm.cu", "rwmi_walkers.cu", "rwmi_api.cu"]
+SOURCES = ["rwmi_fluid.cu", "rwmi_lbm.cu", "rwmi_walkers.cu", "rwmi_dem.cu", "rwmi_api.cu"]
+# the DEM rounds every binary64 operation as written (no fused multiply-add contraction)
+SOURCE_FLAGS = {"rwmi_dem.cu": ["-fmad=false"]}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "-I" + os.path.join(ROOT, "include"), "-I" + CSRC]
@@ -34,7 +36,7 @@ def _stale() -> bool:
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile the three translation units in parallel and link the shared library."""
+    """Compile the translation units in parallel and link the shared library."""
     if not force and not _stale():
         return LIB
     os.makedirs(BUILD, exist_ok=True)
@@ -42,7 +44,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     def compile_one(src):
         obj = os.path.join(BUILD, src.replace(".cu", ".o"))
-        cmd = [nvcc, *ARCH, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [nvcc, *ARCH, *FLAGS, *SOURCE_FLAGS.get(src, []), "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stderr}")

@@ -2,6 +2,7 @@
 // memory, the per-step launch sequence (replayed from captured CUDA graphs), read-back and
 // checkpointing. Every step of the method runs in the kernels of rwmi_fluid.cu and
 // rwmi_walkers.cu; this file only sequences them.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -19,6 +20,7 @@ namespace {
 constexpr int SERIES_ROWS = 65536;
 constexpr int SERIES_COLS = 14;
 constexpr uint64_t CKPT_MAGIC = 0x31494d5752ULL;  // "RWMI1"
+constexpr uint64_t CKPT_DEM_MAGIC = 0x314d4544ULL;  // "DEM1": the free-DEM section
 
 struct GraphKey {
   int fcur, pcur;
@@ -74,6 +76,14 @@ struct rwmi_ctx {
   ParticleDesc* desc = nullptr;
   float4* cbody = nullptr;
   float walk_margin = 1.0f;
+  std::vector<float4> hbody;             // host copy of the body-frame control points
+  std::vector<int> hcoff;                // [P + 1]
+  // free DEM (rwmi_set_dem): one binary64 allocation for the state, parameters, contact memory
+  // and slot forces (dem_layout), one byte allocation for the contact flags
+  bool dem = false;
+  rwmi_dem_config demcfg{};
+  double* dem_d = nullptr;
+  unsigned char* dem_b = nullptr;
   // walkers
   int64_t nw = 0;
   float4* pos[2] = {nullptr, nullptr};
@@ -191,7 +201,44 @@ ParticleSet particle_set(const rwmi_ctx* c) {
   ps.desc = c->desc;
   ps.cbody = c->cbody;
   ps.walk_margin = c->walk_margin;
+  ps.dem = c->dem ? c->dem_d : nullptr;   // the state sits first in dem_d
   return ps;
+}
+
+// Free-DEM buffers of P particles: binary64 words, then contact-flag bytes
+size_t dem_doubles(size_t P) { return 94 * P + 15 * P * P; }
+size_t dem_bytes(size_t P) { return P * P + 6 * P; }
+
+// Views of a context's DEM buffers; the fluid force is that of time parity tp (step t's update)
+DemArgs dem_args(const rwmi_ctx* c, int tp) {
+  DemArgs a;
+  const size_t P = (size_t)c->P, PP = P * P;
+  a.P = c->P;
+  for (int e = 0; e < 3; ++e) { a.n[e] = c->n[e]; a.wall[e] = c->g.wall[e]; a.g[e] = c->demcfg.gravity[e]; }
+  a.desc = c->desc;
+  a.cbody = c->cbody;
+  double* b = c->dem_d;
+  a.st = b; b += 13 * P;
+  a.mass = b; b += P;
+  a.Ib = b; b += 6 * P;
+  a.Rs = b; b += P;
+  a.zoom = b; b += P;
+  a.xi = b; b += 3 * PP;
+  a.xm = b; b += 3 * PP;
+  a.xiw = b; b += 18 * P;
+  a.xmw = b; b += 18 * P;
+  a.pF = b; b += 3 * PP;
+  a.pTi = b; b += 3 * PP;
+  a.pTj = b; b += 3 * PP;
+  a.wF = b; b += 18 * P;
+  a.wT = b;
+  a.act = c->dem_b;
+  a.actw = c->dem_b + PP;
+  a.Fe = c->demcfg.hydro ? c->acc[tp] : nullptr;
+  a.kn = c->demcfg.kn; a.etan = c->demcfg.eta_n; a.kt = c->demcfg.kt; a.etat = c->demcfg.eta_t;
+  a.mus = c->demcfg.mu_s;
+  a.dt = 1.0 / (double)c->demcfg.substeps;
+  return a;
 }
 
 BrickSet brick_set(const rwmi_ctx* c, int par) {
@@ -343,8 +390,13 @@ void enqueue_step(rwmi_ctx* c, bool reduce) {
   const bool fork_raster = level >= 1 && c->P > 0;
   cudaStream_t ws = level >= 2 ? c->wst : c->stream;
   if (ws != c->stream && c->walk_rec[tp]) cudaStreamWaitEvent(c->stream, c->walk_ev[tp], 0);
+  const bool dem = c->dem && c->P > 0;
   auto pose = [&]() {   // particles, bricks and body force of t+1
     phase_begin(c, RWMI_PHASE_POSE);
+    if (dem) {   // free DEM from t to t+1 with the fluid force of the LBM update of t
+      launch_dem(dem_args(c, tp), c->demcfg.substeps, c->stream);
+      c->launches += 2 * c->demcfg.substeps;
+    }
     launch_clear_u32(c->bword[tn], c->nbrick + BWORD_EXTRA, c->stream);
     c->launches++;
     launch_pose_bin(c->g, ps, brick_set(c, tn), c->d_T, toff + 1, c->cfg.body_force, c->cfg.force_period, 1,
@@ -366,12 +418,19 @@ void enqueue_step(rwmi_ctx* c, bool reduce) {
     }
     launch_lbm(c->cfg.q, c->cfg.storage, reduce, c->g, c->f[c->fcur], c->f[c->fcur ^ 1], c->u[tp], c->solid[tp],
                brick_set(c, tp), c->tau, c->cfg.rho0, c->acc[tp] + 6 * c->P, c->acc[tp],
-               c->status, c->stream, c->cfg.lbm_block, ibb ? &ia : nullptr);
-    c->launches += reduce ? 2 : 1;   // the reduce-only pass on reduction steps
+               c->status, c->stream, c->cfg.lbm_block, ibb ? &ia : nullptr, dem);
+    c->launches += dem ? 1 : reduce ? 2 : 1;   // fused with DEM; else the reduce-only pass on reduction steps
     phase_end(c, RWMI_PHASE_LBM);
     c->fcur ^= 1;
   };
-  if (fork_raster) {
+  if (dem) {   // the particles of t+1 follow from the fluid force of t: raster after the LBM
+    lbm();
+    pose();
+    phase_begin(c, RWMI_PHASE_RASTER);
+    launch_raster(c->g, ps, brick_set(c, tn), c->solid[tn], c->status, c->nsm, c->stream);
+    c->launches++;
+    phase_end(c, RWMI_PHASE_RASTER);
+  } else if (fork_raster) {
     pose();
     cudaEventRecord(c->fork_ev, c->stream);
     cudaStreamWaitEvent(c->side, c->fork_ev, 0);
@@ -584,6 +643,8 @@ RWMI_API rwmi_status rwmi_configure(rwmi_ctx* c, const rwmi_config* cfg) {
   for (int a = 0; a < 3; ++a)
     if (!std::isfinite(cfg->body_force[a]) || !std::isfinite(cfg->init_velocity[a]))
       return fail(c, RWMI_E_INVALID, "rwmi_configure: non-finite force or velocity");
+  if (c->dem && (cfg->coupling != 0 || (cfg->storage != RWMI_STORE_FP32_SHIFT && cfg->storage != RWMI_STORE_FP64_SHIFT)))
+    return fail(c, RWMI_E_INVALID, "rwmi_configure: the free DEM needs coupling 0 and storage 1 or 3");
   const bool realloc_f = cfg->q != c->cfg.q || cfg->storage != c->cfg.storage;
   c->cfg = *cfg;
   update_margin(c);
@@ -669,8 +730,15 @@ RWMI_API rwmi_status rwmi_set_metaballs(rwmi_ctx* c, int32_t P, const int32_t* c
   dfree(c, c->cbody);
   c->desc = nullptr;
   c->cbody = nullptr;
+  dfree(c, c->dem_d);
+  dfree(c, c->dem_b);
+  c->dem_d = nullptr;
+  c->dem_b = nullptr;
+  c->dem = false;   // new particles follow their prescribed trajectories until rwmi_set_dem
   c->P = P;
   c->Nc = Nc;
+  c->hbody.assign(body.begin(), body.begin() + Nc);
+  c->hcoff.assign(coff, coff + (P > 0 ? P + 1 : 0));
   CK(dalloc(c, &c->desc, sizeof(ParticleDesc) * desc.size()));
   CK(dalloc(c, &c->cbody, sizeof(float4) * body.size()));
   CK(copy_now(c, c->desc, desc.data(), sizeof(ParticleDesc) * desc.size()));
@@ -680,6 +748,105 @@ RWMI_API rwmi_status rwmi_set_metaballs(rwmi_ctx* c, int32_t P, const int32_t* c
   drop_graphs(c);
   s = build_current_frame(c);
   if (s != RWMI_OK) return s;
+  CK(cudaStreamSynchronize(c->stream));
+  return RWMI_OK;
+}
+
+RWMI_API void rwmi_dem_defaults(rwmi_dem_config* cfg) {
+  if (!cfg) return;
+  *cfg = rwmi_dem_config{};
+  cfg->kn = 200.0;
+  cfg->substeps = 10;
+  cfg->hydro = 1;
+}
+
+RWMI_API rwmi_status rwmi_set_dem(rwmi_ctx* c, const rwmi_dem_config* cfg, const double* mass,
+                                  const double* inertia, const double* Rs, const double* vel,
+                                  const double* spin) {
+  if (!c || !cfg) return RWMI_E_INVALID;
+  if (c->P < 1 || !mass || !inertia || !Rs) return fail(c, RWMI_E_INVALID, "rwmi_set_dem: no particles or null array");
+  if (c->cfg.coupling != 0 || (c->cfg.storage != RWMI_STORE_FP32_SHIFT && c->cfg.storage != RWMI_STORE_FP64_SHIFT))
+    return fail(c, RWMI_E_INVALID, "rwmi_set_dem: needs coupling 0 and storage 1 or 3");
+  if (!(cfg->kn >= 0.0) || !(cfg->eta_n >= 0.0) || !(cfg->kt >= 0.0) || !(cfg->eta_t >= 0.0) || !(cfg->mu_s >= 0.0) ||
+      !std::isfinite(cfg->kn + cfg->eta_n + cfg->kt + cfg->eta_t + cfg->mu_s) || cfg->substeps < 1 ||
+      cfg->substeps > 100000 || (cfg->hydro != 0 && cfg->hydro != 1))
+    return fail(c, RWMI_E_INVALID, "rwmi_set_dem: bad contact law or substeps");
+  for (int a = 0; a < 3; ++a)
+    if (!std::isfinite(cfg->gravity[a])) return fail(c, RWMI_E_INVALID, "rwmi_set_dem: non-finite gravity");
+  const int P = c->P;
+  std::vector<ParticleDesc> desc((size_t)P);
+  CK(copy_now(c, desc.data(), c->desc, sizeof(ParticleDesc) * desc.size()));
+  std::vector<double> st((size_t)13 * P, 0.0);
+  for (int p = 0; p < P; ++p) {
+    const ParticleDesc& d = desc[p];
+    if (d.c1 - d.c0 > DEM_MAX_CP) return fail(c, RWMI_E_INVALID, "rwmi_set_dem: more than 16 control points");
+    double reach = 0.0;   // validation only (the kernel forms the zoom)
+    for (int i = d.c0; i < d.c1; ++i) {
+      const float4 b = c->hbody[i];
+      reach = std::max(reach, std::sqrt((double)b.x * b.x + (double)b.y * b.y + (double)b.z * b.z) +
+                                  std::sqrt((double)b.w));
+    }
+    if (!(mass[p] > 0.0) || !std::isfinite(mass[p]) || !(Rs[p] > 0.0) || !(Rs[p] < reach))
+      return fail(c, RWMI_E_INVALID, "rwmi_set_dem: need mass > 0 and 0 < R_s < max |c_i| + sqrt(k_i)");
+    for (int m = 0; m < 6; ++m)
+      if (!std::isfinite(inertia[6 * p + m])) return fail(c, RWMI_E_INVALID, "rwmi_set_dem: non-finite inertia");
+    // the prescribed motion at the current time gives the start
+    double s = 0.0, cdt = 0.0;
+    if (d.period > 0.0) {
+      const double th = 2.0 * 3.141592653589793 * (double)c->t / d.period + d.phase;
+      s = std::sin(th);
+      cdt = std::cos(th) * 2.0 * 3.141592653589793 / d.period;
+    }
+    double* q = st.data() + 13 * (size_t)p;
+    for (int a = 0; a < 3; ++a) {
+      q[a] = d.period > 0.0 ? d.org[a] + d.amp[a] * s : d.org[a];
+      q[7 + a] = vel ? vel[3 * p + a] : d.amp[a] * cdt;
+      q[10 + a] = spin ? spin[3 * p + a] : d.omega[a];
+      if (!std::isfinite(q[7 + a]) || !std::isfinite(q[10 + a]))
+        return fail(c, RWMI_E_INVALID, "rwmi_set_dem: non-finite velocity or spin");
+    }
+    q[3] = 1.0;
+  }
+  dfree(c, c->dem_d);
+  dfree(c, c->dem_b);
+  c->dem_d = nullptr;
+  c->dem_b = nullptr;
+  c->dem = false;
+  CK(dalloc(c, &c->dem_d, sizeof(double) * dem_doubles((size_t)P)));
+  CK(dalloc(c, &c->dem_b, dem_bytes((size_t)P)));
+  CK(cudaMemsetAsync(c->dem_d, 0, sizeof(double) * dem_doubles((size_t)P), c->stream));
+  CK(cudaMemsetAsync(c->dem_b, 0, dem_bytes((size_t)P), c->stream));
+  c->demcfg = *cfg;
+  c->dem = true;
+  DemArgs a = dem_args(c, (int)(c->t & 1));
+  CK(copy_now(c, a.st, st.data(), sizeof(double) * st.size()));
+  CK(copy_now(c, const_cast<double*>(a.mass), mass, sizeof(double) * (size_t)P));
+  CK(copy_now(c, const_cast<double*>(a.Ib), inertia, sizeof(double) * 6 * (size_t)P));
+  CK(copy_now(c, const_cast<double*>(a.Rs), Rs, sizeof(double) * (size_t)P));
+  launch_dem_init(a, c->stream);
+  drop_graphs(c);
+  rwmi_status r = build_current_frame(c);
+  if (r != RWMI_OK) return r;
+  CK(cudaStreamSynchronize(c->stream));
+  CK(cudaGetLastError());
+  return RWMI_OK;
+}
+
+RWMI_API rwmi_status rwmi_particle_state(rwmi_ctx* c, double* out) {
+  if (!c || !out) return RWMI_E_INVALID;
+  if (!c->dem) return fail(c, RWMI_E_STATE, "rwmi_particle_state: no free DEM (rwmi_set_dem)");
+  CK(copy_now(c, out, c->dem_d, sizeof(double) * 13 * (size_t)c->P));
+  return RWMI_OK;
+}
+
+RWMI_API rwmi_status rwmi_set_particle_state(rwmi_ctx* c, const double* state) {
+  if (!c || !state) return RWMI_E_INVALID;
+  if (!c->dem) return fail(c, RWMI_E_STATE, "rwmi_set_particle_state: no free DEM (rwmi_set_dem)");
+  for (size_t m = 0; m < (size_t)13 * c->P; ++m)
+    if (!std::isfinite(state[m])) return fail(c, RWMI_E_INVALID, "rwmi_set_particle_state: non-finite value");
+  CK(copy_now(c, c->dem_d, state, sizeof(double) * 13 * (size_t)c->P));
+  rwmi_status r = build_current_frame(c);
+  if (r != RWMI_OK) return r;
   CK(cudaStreamSynchronize(c->stream));
   return RWMI_OK;
 }
@@ -1091,6 +1258,19 @@ RWMI_API rwmi_status rwmi_save(rwmi_ctx* c, const char* path) {
   bool ok = std::fwrite(hdr, sizeof(hdr), 1, fp) == 1 && std::fwrite(f.data(), 1, pop, fp) == pop;
   if (c->nw) ok = ok && std::fwrite(p.data(), sizeof(float4), p.size(), fp) == p.size() &&
                   std::fwrite(q.data(), sizeof(float4), q.size(), fp) == q.size();
+  if (c->dem && ok) {   // free DEM: state, parameters, contact memory and flags
+    std::vector<double> dd(dem_doubles((size_t)c->P));
+    std::vector<unsigned char> db(dem_bytes((size_t)c->P));
+    if (copy_now(c, dd.data(), c->dem_d, sizeof(double) * dd.size()) != cudaSuccess ||
+        copy_now(c, db.data(), c->dem_b, db.size()) != cudaSuccess) {
+      std::fclose(fp);
+      return fail(c, RWMI_E_CUDA, "rwmi_save: reading the DEM state failed");
+    }
+    const int64_t dh[2] = {(int64_t)CKPT_DEM_MAGIC, c->P};
+    ok = std::fwrite(dh, sizeof(dh), 1, fp) == 1 && std::fwrite(&c->demcfg, sizeof(c->demcfg), 1, fp) == 1 &&
+         std::fwrite(dd.data(), sizeof(double), dd.size(), fp) == dd.size() &&
+         std::fwrite(db.data(), 1, db.size(), fp) == db.size();
+  }
   ok = (std::fclose(fp) == 0) && ok;
   if (!ok) return fail(c, RWMI_E_INVALID, "rwmi_save: write failed");
   return RWMI_OK;
@@ -1114,8 +1294,22 @@ RWMI_API rwmi_status rwmi_load(rwmi_ctx* c, const char* path) {
   bool ok = std::fread(f.data(), 1, pop, fp) == pop;
   if (nw) ok = ok && std::fread(p.data(), sizeof(float4), p.size(), fp) == p.size() &&
                std::fread(q.data(), sizeof(float4), q.size(), fp) == q.size();
+  std::vector<double> dd;
+  std::vector<unsigned char> db;
+  rwmi_dem_config dcfg{};
+  int64_t dh[2] = {0, 0};
+  const bool has_dem = ok && std::fread(dh, sizeof(dh), 1, fp) == 1 && dh[0] == (int64_t)CKPT_DEM_MAGIC;
+  if (has_dem) {
+    dd.resize(dem_doubles((size_t)c->P));
+    db.resize(dem_bytes((size_t)c->P));
+    ok = dh[1] == c->P && std::fread(&dcfg, sizeof(dcfg), 1, fp) == 1 &&
+         std::fread(dd.data(), sizeof(double), dd.size(), fp) == dd.size() &&
+         std::fread(db.data(), 1, db.size(), fp) == db.size();
+  }
   std::fclose(fp);
   if (!ok) return fail(c, RWMI_E_INVALID, "rwmi_load: truncated checkpoint");
+  if (has_dem != c->dem)
+    return fail(c, RWMI_E_INVALID, "rwmi_load: free-DEM checkpoints load into free-DEM contexts only");
   CK(cudaStreamSynchronize(c->stream));
   if (nw != c->nw) {
     rwmi_status s = alloc_walkers(c, nw);
@@ -1131,6 +1325,11 @@ RWMI_API rwmi_status rwmi_load(rwmi_ctx* c, const char* path) {
   if (nw) {
     CK(copy_now(c, c->pos[0], p.data(), sizeof(float4) * p.size()));
     CK(copy_now(c, c->x0[0], q.data(), sizeof(float4) * q.size()));
+  }
+  if (has_dem) {
+    c->demcfg = dcfg;
+    CK(copy_now(c, c->dem_d, dd.data(), sizeof(double) * dd.size()));
+    CK(copy_now(c, c->dem_b, db.data(), db.size()));
   }
   CK(copy_now(c, c->d_T, &c->t, sizeof(int64_t)));
   c->t_base = c->t;
@@ -1297,6 +1496,7 @@ RWMI_API void rwmi_destroy(rwmi_ctx* c) {
   dfree(c, c->u[0]); dfree(c, c->u[1]); dfree(c, c->solid[0]); dfree(c, c->solid[1]); dfree(c, c->node[0]); dfree(c, c->node[1]); dfree(c, c->d_T); dfree(c, c->status); dfree(c, c->macc);
   dfree(c, c->series); dfree(c, c->mrow); dfree(c, c->desc); dfree(c, c->cbody); dfree(c, c->rank);
   dfree(c, c->counts); dfree(c, c->offsets); dfree(c, c->bsums); dfree(c, c->scratch); dfree(c, c->wmask[0]); dfree(c, c->wmask[1]);
+  dfree(c, c->dem_d); dfree(c, c->dem_b);
   cudaStreamSynchronize(c->stream);   // the frees have returned the memory when this returns
   for (int k = 0; k < 2 * RWMI_NPHASE; ++k)
     if (c->ev[k]) cudaEventDestroy(c->ev[k]);

@@ -53,22 +53,38 @@ __global__ void pose_bin_kernel(Geom g, ParticleSet ps, BrickSet bs, const int64
   // round identically on both sides, so no fused multiply-add here.
   if (threadIdx.x == 0) {
     const double two_pi = 6.283185307179586;
-    double s = 0.0, cdt = 0.0;
-    if (d.period > 0.0) {
-      const double th = __dadd_rn(__ddiv_rn(__dmul_rn(two_pi, (double)t), d.period), d.phase);
-      s = sin(th);
-      cdt = cos(th) * two_pi / d.period;
-    }
-    double org[3], vel[3];
-    for (int a = 0; a < 3; ++a) {
-      org[a] = __dadd_rn(d.org[a], __dmul_rn(d.amp[a], s));
-      vel[a] = d.amp[a] * cdt;
-    }
-    // constant spin: body frame turned by |omega| t about omega / |omega| (Rodrigues)
-    const double wn = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(d.omega[0], d.omega[0]),
-                                                     __dmul_rn(d.omega[1], d.omega[1])),
-                                           __dmul_rn(d.omega[2], d.omega[2])));
+    double org[3], vel[3], spin[3];
+    double wn = 0.0;
     for (int m = 0; m < 9; ++m) sR[m] = (m % 4 == 0) ? 1.0 : 0.0;
+    if (ps.dem) {   // free DEM: the state's origin, velocity, spin and orientation quaternion
+      const double* st = ps.dem + 13 * p;
+      for (int a = 0; a < 3; ++a) { org[a] = st[a]; vel[a] = st[7 + a]; spin[a] = st[10 + a]; }
+      const double w = st[3], x = st[4], y = st[5], z = st[6];
+      sR[0] = __dsub_rn(1.0, __dmul_rn(2.0, __dadd_rn(__dmul_rn(y, y), __dmul_rn(z, z))));
+      sR[1] = __dmul_rn(2.0, __dsub_rn(__dmul_rn(x, y), __dmul_rn(w, z)));
+      sR[2] = __dmul_rn(2.0, __dadd_rn(__dmul_rn(x, z), __dmul_rn(w, y)));
+      sR[3] = __dmul_rn(2.0, __dadd_rn(__dmul_rn(x, y), __dmul_rn(w, z)));
+      sR[4] = __dsub_rn(1.0, __dmul_rn(2.0, __dadd_rn(__dmul_rn(x, x), __dmul_rn(z, z))));
+      sR[5] = __dmul_rn(2.0, __dsub_rn(__dmul_rn(y, z), __dmul_rn(w, x)));
+      sR[6] = __dmul_rn(2.0, __dsub_rn(__dmul_rn(x, z), __dmul_rn(w, y)));
+      sR[7] = __dmul_rn(2.0, __dadd_rn(__dmul_rn(y, z), __dmul_rn(w, x)));
+      sR[8] = __dsub_rn(1.0, __dmul_rn(2.0, __dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y))));
+    } else {
+      double s = 0.0, cdt = 0.0;
+      if (d.period > 0.0) {
+        const double th = __dadd_rn(__ddiv_rn(__dmul_rn(two_pi, (double)t), d.period), d.phase);
+        s = sin(th);
+        cdt = cos(th) * two_pi / d.period;
+      }
+      for (int a = 0; a < 3; ++a) {
+        org[a] = __dadd_rn(d.org[a], __dmul_rn(d.amp[a], s));
+        vel[a] = d.amp[a] * cdt;
+        spin[a] = d.omega[a];
+      }
+      // constant spin: body frame turned by |omega| t about omega / |omega| (Rodrigues)
+      wn = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(d.omega[0], d.omega[0]), __dmul_rn(d.omega[1], d.omega[1])),
+                                __dmul_rn(d.omega[2], d.omega[2])));
+    }
     if (wn > 0.0) {
       const double ax[3] = {__ddiv_rn(d.omega[0], wn), __ddiv_rn(d.omega[1], wn), __ddiv_rn(d.omega[2], wn)};
       const double ang = __dmul_rn(wn, (double)t), ca = cos(ang), sa = sin(ang);
@@ -83,7 +99,7 @@ __global__ void pose_bin_kernel(Geom g, ParticleSet ps, BrickSet bs, const int64
     for (int a = 0; a < 3; ++a) {
       pf.o[a] = (float)wrap_d(org[a], (double)g.n[a], g.wall[a]);
       pf.v[a] = (float)vel[a];
-      pf.w[a] = (float)d.omega[a];
+      pf.w[a] = (float)spin[a];
       pf.pad[a] = 0.0f;
     }
     bs.pose[p] = pf;
@@ -91,7 +107,7 @@ __global__ void pose_bin_kernel(Geom g, ParticleSet ps, BrickSet bs, const int64
     for (int a = 0; a < 3; ++a) {
       pd.o[a] = wrap_d(org[a], (double)g.n[a], g.wall[a]);
       pd.v[a] = vel[a];
-      pd.w[a] = d.omega[a];
+      pd.w[a] = spin[a];
     }
     pd.pad = 0.0;
     bs.posed[p] = pd;

@@ -209,6 +209,8 @@ struct ParticleSet {
   const ParticleDesc* desc;   // [P]
   const float4* cbody;        // [Nc]
   float walk_margin;          // candidate margin for walkers, cells
+  const double* dem = nullptr;   // free-DEM state [13 P] (origin, quaternion, velocity, spin), or
+                                 // nullptr for the prescribed trajectories
 };
 
 void launch_clear_u32(uint32_t* p, uint32_t n, cudaStream_t st);
@@ -224,10 +226,38 @@ struct IbbArgs {
   const float4* uprev = nullptr;
   const ParticleDesc* desc = nullptr;
 };
+// fused: the update and the reduction in one pass (free-DEM runs, which read the forces every
+// step; binary32-shifted and binary64 storage, partially saturated cells)
 void launch_lbm(int q, int storage, bool reduce, const Geom& g, const void* fin, void* fout,
                 float* u, const uint16_t* solid, BrickSet bs, double tau, double rho0,
                 double* red, double* forces, unsigned long long* status, cudaStream_t st,
-                int block = 256, const IbbArgs* ibb = nullptr);
+                int block = 256, const IbbArgs* ibb = nullptr, bool fused = false);
+
+// Free DEM (Section 2.2, Eqs. 4-11) of a context: contact law, state and per-pair memory. Pair
+// slots (i < j) sit at i P + j, wall slots (particle p, face 2 axis + side) at 6 p + face.
+constexpr int DEM_MAX_CP = 16;   // control points per particle the DEM takes
+struct DemArgs {
+  int P;
+  int n[3], wall[3];
+  const ParticleDesc* desc;
+  const float4* cbody;
+  double* st;                                  // [13 P]
+  const double *mass, *Ib, *Rs;                // [P], [6 P], [P]
+  double* zoom;                                // [P] internal-metaball scale
+  double *xi, *xm;                             // pairs [3 P P]
+  unsigned char* act;                          // pairs [P P]
+  double *xiw, *xmw;                           // walls [18 P]
+  unsigned char* actw;                         // walls [6 P]
+  double *pF, *pTi, *pTj;                      // pair force on i, torques on i and j [3 P P]
+  double *wF, *wT;                             // wall force and torque [18 P]
+  const double* Fe;                            // fluid force and torque [6 P], or nullptr
+  double kn, etan, kt, etat, mus, g[3];
+  double dt;                                   // 1 / substeps
+};
+// substeps DEM steps: two launches each (contacts, then integration)
+void launch_dem(const DemArgs& a, int substeps, cudaStream_t st);
+// the zoom factors from the sphere radii (rwmi_set_dem)
+void launch_dem_init(const DemArgs& a, cudaStream_t st);
 // IBB node classes at time t (bricks bs of that time) into cur; with refill, nodes solid in prev
 // and fluid now get the equilibrium at their former particle's rigid velocity (Eq. 27).
 void launch_nodes(int q, int storage, const Geom& g, const ParticleSet& ps, BrickSet bs,

@@ -39,11 +39,12 @@ __device__ __forceinline__ float ibb_link_q(const float4* __restrict__ cw, int c
 // velocity; a fluid node replaces the population pulled from each solid neighbour by Eqs. 23-25
 // (q by the same binary32 bisection as the CPU oracle) and, on reduction steps, adds the
 // Galilean-invariant momentum exchange of the link to its particle's force and torque.
-// REDUCE: a reduce-only pass. It runs after the regular (non-reducing) update on the steps whose
+// MODE 0: the update. MODE 1: a reduce-only pass. It runs after the update on the steps whose
 // sums are read, re-pulls the same input populations and forms the FP64 sums and particle forces,
 // and stores nothing. Stored populations therefore always come from one compiled update, and the
-// reducing and non-reducing steps agree bit for bit.
-template <int Q, int STORE, bool WALLS, bool REDUCE, bool IBB>
+// reducing and non-reducing steps agree bit for bit. MODE 2: update and reduction in one pass,
+// for free-DEM runs, which read the forces on every step (so every step runs this one mode).
+template <int Q, int STORE, bool WALLS, int MODE, bool IBB>
 __global__ void __launch_bounds__(256, (sizeof(typename Store<STORE>::R) == 8 || IBB) ? 2 : (Q == 19 ? 5 : 6))
 lbm_kernel(Geom g, Planes<Q, typename Store<STORE>::T> pl,
                                                   float4* __restrict__ u4,
@@ -62,6 +63,7 @@ lbm_kernel(Geom g, Planes<Q, typename Store<STORE>::T> pl,
   using L = Lat<Q>;
   using S = Store<STORE>;
   using R = typename S::R;   // arithmetic type: binary32, or binary64 for the binary64 storage
+  constexpr bool REDUCE = MODE != 0, STORES = MODE != 1;
   // tau and rho0 arrive in R (converted on the host: a per-thread binary64 -> binary32
   // conversion would occupy GB300's narrow FP64 pipe)
   const uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x;
@@ -322,7 +324,7 @@ lbm_kernel(Geom g, Planes<Q, typename Store<STORE>::T> pl,
       dpx += dm * ex; dpy += dm * ey; dpz += dm * ez;
     }
   }
-  if (!REDUCE) {   // the reduce-only pass stores nothing
+  if (STORES) {   // the reduce-only pass stores nothing
   if (IBB && solid_self) {   // solid node: equilibrium at the particle's rigid velocity, rho0
     R us[3];
     rigid_velocity<R>(g, pose, posed, (int)nodes[c] - 1, (R)x + R(0.5), (R)y + R(0.5), (R)z + R(0.5), us);
@@ -413,7 +415,7 @@ lbm_kernel(Geom g, Planes<Q, typename Store<STORE>::T> pl,
 template <int Q, int STORE, bool IBB>
 static void launch_lbm_q(bool walls, bool reduce, const Geom& g, const void* fin, void* fout, float* u,
                          const uint16_t* solid, BrickSet bs, double tau, double rho0, double* red,
-                         double* forces, cudaStream_t st, int bsz, const IbbArgs& ib) {
+                         double* forces, cudaStream_t st, int bsz, const IbbArgs& ib, bool fused) {
   using T = typename Store<STORE>::T;
   using R = typename Store<STORE>::R;
   Planes<Q, T> pl;
@@ -425,19 +427,27 @@ static void launch_lbm_q(bool walls, bool reduce, const Geom& g, const void* fin
   const int bsz_ok = (bsz == 64 || bsz == 128) ? bsz : 256;
   const dim3 grid((g.ncell + bsz_ok - 1) / bsz_ok), block(bsz_ok);
 #define RWMI_LBM_ARGS g, pl, u4, solid, bs.bword, bs.pose, bs.posed, bs.sp, (R)tau, (R)rho0, red, forces, ib.nodes, ib.uprev, ib.desc, bs.cworld
+  if constexpr ((STORE == 1 || STORE == 3) && !IBB) {   // the fused mode of free-DEM runs
+    if (fused) {
+      if (walls) lbm_kernel<Q, STORE, true, 2, IBB><<<grid, block, 0, st>>>(RWMI_LBM_ARGS);
+      else lbm_kernel<Q, STORE, false, 2, IBB><<<grid, block, 0, st>>>(RWMI_LBM_ARGS);
+      return;
+    }
+  }
   if (walls) {
-    lbm_kernel<Q, STORE, true, false, IBB><<<grid, block, 0, st>>>(RWMI_LBM_ARGS);
-    if (reduce) lbm_kernel<Q, STORE, true, true, IBB><<<grid, block, 0, st>>>(RWMI_LBM_ARGS);
+    lbm_kernel<Q, STORE, true, 0, IBB><<<grid, block, 0, st>>>(RWMI_LBM_ARGS);
+    if (reduce) lbm_kernel<Q, STORE, true, 1, IBB><<<grid, block, 0, st>>>(RWMI_LBM_ARGS);
   } else {
-    lbm_kernel<Q, STORE, false, false, IBB><<<grid, block, 0, st>>>(RWMI_LBM_ARGS);
-    if (reduce) lbm_kernel<Q, STORE, false, true, IBB><<<grid, block, 0, st>>>(RWMI_LBM_ARGS);
+    lbm_kernel<Q, STORE, false, 0, IBB><<<grid, block, 0, st>>>(RWMI_LBM_ARGS);
+    if (reduce) lbm_kernel<Q, STORE, false, 1, IBB><<<grid, block, 0, st>>>(RWMI_LBM_ARGS);
   }
 #undef RWMI_LBM_ARGS
 }
 
 void launch_lbm(int q, int storage, bool reduce, const Geom& g, const void* fin, void* fout,
                 float* u, const uint16_t* solid, BrickSet bs, double tau, double rho0, double* red,
-                double* forces, unsigned long long* status, cudaStream_t st, int block, const IbbArgs* ibb) {
+                double* forces, unsigned long long* status, cudaStream_t st, int block, const IbbArgs* ibb,
+                bool fused) {
   (void)status;
   const bool walls = g.wall[0] || g.wall[1] || g.wall[2];
   const IbbArgs none{};
@@ -445,9 +455,9 @@ void launch_lbm(int q, int storage, bool reduce, const Geom& g, const void* fin,
   // IBB is built for binary32-shifted and binary64 storage (the configuration check refuses the
   // others); the other storages run the partially saturated cells only
 #define RWMI_LBM_PSM(QQ, SS) \
-  launch_lbm_q<QQ, SS, false>(walls, reduce, g, fin, fout, u, solid, bs, tau, rho0, red, forces, st, block, ib)
+  launch_lbm_q<QQ, SS, false>(walls, reduce, g, fin, fout, u, solid, bs, tau, rho0, red, forces, st, block, ib, fused)
 #define RWMI_LBM_CASE(QQ, SS)                                                                           \
-  if (ibb) launch_lbm_q<QQ, SS, true>(walls, reduce, g, fin, fout, u, solid, bs, tau, rho0, red, forces, st, block, ib); \
+  if (ibb) launch_lbm_q<QQ, SS, true>(walls, reduce, g, fin, fout, u, solid, bs, tau, rho0, red, forces, st, block, ib, false); \
   else RWMI_LBM_PSM(QQ, SS)
   if (q == 15) {
     if (storage == 0) { RWMI_LBM_PSM(15, 0); }

@@ -28,7 +28,8 @@ EXPORTED = ["rwmi_config_defaults", "rwmi_create", "rwmi_configure", "rwmi_set_s
             "rwmi_mass_momentum", "rwmi_particle_forces", "rwmi_walkers", "rwmi_counters", "rwmi_save",
             "rwmi_load", "rwmi_brick_stats", "rwmi_bin_walkers_noalloc", "rwmi_last_error",
             "rwmi_launch_count", "rwmi_destroy", "rwmi_batch_create", "rwmi_batch_step", "rwmi_batch_sync",
-            "rwmi_batch_last_error", "rwmi_batch_destroy"]
+            "rwmi_batch_last_error", "rwmi_batch_destroy", "rwmi_dem_defaults", "rwmi_set_dem",
+            "rwmi_particle_state", "rwmi_set_particle_state"]
 
 
 class RwmiError(RuntimeError):
@@ -47,6 +48,12 @@ class Config(C.Structure):
                 ("init_velocity", C.c_double * 3), ("sort_interval", C.c_int32),
                 ("moment_interval", C.c_int32), ("use_graphs", C.c_int32), ("lbm_block", C.c_int32),
                 ("overlap", C.c_int32), ("coupling", C.c_int32)]
+
+
+class DemConfig(C.Structure):
+    _fields_ = [("kn", C.c_double), ("eta_n", C.c_double), ("kt", C.c_double), ("eta_t", C.c_double),
+                ("mu_s", C.c_double), ("gravity", C.c_double * 3), ("substeps", C.c_int32),
+                ("hydro", C.c_int32)]
 
 
 _lib = None
@@ -120,10 +127,15 @@ def load(build_if_missing: bool = False):
     L.rwmi_batch_last_error.restype = C.c_char_p
     L.rwmi_batch_destroy.argtypes = [P]
     L.rwmi_batch_destroy.restype = None
+    L.rwmi_dem_defaults.argtypes = [C.POINTER(DemConfig)]
+    L.rwmi_dem_defaults.restype = None
+    L.rwmi_set_dem.argtypes = [P, C.POINTER(DemConfig), vp, vp, vp, vp, vp]
+    L.rwmi_particle_state.argtypes = [P, vp]
+    L.rwmi_set_particle_state.argtypes = [P, vp]
     for name in EXPORTED:
         fn = getattr(L, name)
         if name not in ("rwmi_config_defaults", "rwmi_last_error", "rwmi_launch_count", "rwmi_destroy",
-                        "rwmi_batch_last_error", "rwmi_batch_destroy"):
+                        "rwmi_batch_last_error", "rwmi_batch_destroy", "rwmi_dem_defaults"):
             fn.restype = C.c_int
     _lib = L
     return L
@@ -212,6 +224,8 @@ class Simulation:
         s = cls(w.dims, w.tau, w.D, w.seed, **kw)
         if w.metaballs is not None and w.metaballs.n_particles > 0:
             s.set_metaballs(w.metaballs)
+            if getattr(w, "dem", None) is not None:
+                s.set_dem(w.dem)
         if seed_walkers and w.n_walkers:
             if w.walker_positions is not None:
                 s.set_walkers(w.walker_positions)
@@ -261,6 +275,35 @@ class Simulation:
         self._check(self._L.rwmi_set_metaballs(self._h, P, _ptr(keep["coff"]), _ptr(keep["cb"]), _ptr(keep["k"]),
                                                _ptr(keep["org"]), _ptr(keep["amp"]), _ptr(keep["per"]),
                                                _ptr(keep["pha"]), _ptr(keep["omg"])))
+
+    def set_dem(self, dem):
+        """Free DEM (Eqs. 4-11) from the current time; `dem` has the fields of inputs.Dem."""
+        cfg = DemConfig()
+        self._L.rwmi_dem_defaults(C.byref(cfg))
+        cfg.kn, cfg.eta_n, cfg.kt, cfg.eta_t, cfg.mu_s = (float(dem.kn), float(dem.eta_n), float(dem.kt),
+                                                          float(dem.eta_t), float(dem.mu_s))
+        for a in range(3):
+            cfg.gravity[a] = float(dem.gravity[a])
+        cfg.substeps, cfg.hydro = int(dem.substeps), int(dem.hydro)
+        P = self.n_particles
+        keep = dict(m=np.ascontiguousarray(dem.mass, np.float64).reshape(P),
+                    I=np.ascontiguousarray(dem.inertia, np.float64).reshape(6 * P),
+                    Rs=np.ascontiguousarray(dem.sphere_radius, np.float64).reshape(P),
+                    v=None if dem.velocity is None else np.ascontiguousarray(dem.velocity, np.float64).reshape(3 * P),
+                    w=None if dem.spin is None else np.ascontiguousarray(dem.spin, np.float64).reshape(3 * P))
+        self._check(self._L.rwmi_set_dem(self._h, C.byref(cfg), _ptr(keep["m"]), _ptr(keep["I"]), _ptr(keep["Rs"]),
+                                         None if keep["v"] is None else _ptr(keep["v"]),
+                                         None if keep["w"] is None else _ptr(keep["w"])))
+
+    def particle_state(self, out=None):
+        """Free-DEM state [P, 13]: origin (unwrapped), quaternion (w, x, y, z), velocity, spin."""
+        out = self._out(out, (self.n_particles, 13), np.float64)
+        self._check(self._L.rwmi_particle_state(self._h, _ptr(out)))
+        return out
+
+    def set_particle_state(self, st):
+        st = np.ascontiguousarray(st, np.float64).reshape(self.n_particles, 13)
+        self._check(self._L.rwmi_set_particle_state(self._h, _ptr(st)))
 
     def seed_walkers(self, n, lo, hi):
         st = self._check(self._L.rwmi_seed_walkers(self._h, int(n), _d3(lo), _d3(hi)))

@@ -1,0 +1,151 @@
+"""Free DEM on the GPU (Section 2.2, Eqs. 4-11) against the FP64 CPU oracle.
+
+- Fluid force off (hydro = 0): the particle trajectories do not depend on the fluid, and the
+  DEM kernels round every binary64 operation as the oracle does (no contraction, IEEE division
+  and square root, the same operation order), so the states agree bit for bit through contacts
+  between particles and with the walls.
+- Fluid force on: one step from the GPU's own state (populations, velocity, particles) against
+  the oracle. The particles' new velocities differ only through the hydrodynamic force, which
+  the GPU forms in binary32 (relative 1e-4 of the force, times dt / m).
+- The three schedules, graph replay and a checkpoint restart give identical results.
+- Set-ups the library cannot run (IBB coupling, binary16 storage) are refused.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from oracle.oracle import Oracle
+from paper_2308_05007_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2308_05007_gb300 import rwmi
+    rwmi.load()
+    yield
+
+
+def _converging(hydro=0, seed=11, n_particles=4, speed=0.1):
+    """dem_box with every particle aimed at the common centre, so that contacts follow."""
+    w = I.dem_box(n_particles=n_particles, seed=seed, hydro=hydro)
+    o = w.metaballs.origin
+    aim = o.mean(0) - o
+    w.dem.velocity[:] = speed * aim / np.linalg.norm(aim, axis=1, keepdims=True)
+    return w
+
+
+def test_trajectories_bit_exact_without_fluid_force():
+    from paper_2308_05007_gb300.rwmi import Simulation
+    w = _converging(hydro=0)
+    ora = Oracle.from_workload(w, seed_walkers=False)
+    with Simulation.from_workload(w, seed_walkers=False) as sim:
+        g0 = sim.particle_state()
+        np.testing.assert_array_equal(g0, ora.particle_state())
+        touched = False
+        for chunk in range(8):
+            sim.step(20)
+            ora.dem_advance(20)
+            st = sim.particle_state()
+            np.testing.assert_array_equal(st, ora.particle_state(), err_msg=f"after {20 * (chunk + 1)} steps")
+            free = g0[:, 7:10] + (20 * (chunk + 1)) * np.asarray(w.dem.gravity)
+            touched |= bool(np.abs(st[:, 7:10] - free).max() > 1e-6)
+    assert touched, "no contact happened"
+
+
+def test_solid_fraction_follows_the_dem_state():
+    """The raster of a free-DEM run uses the particle state: bit-exact against the oracle's
+    rasteriser fed the same state."""
+    from paper_2308_05007_gb300.rwmi import Simulation
+    w = _converging(hydro=0)
+    ora = Oracle.from_workload(w, seed_walkers=False)
+    with Simulation.from_workload(w, seed_walkers=False) as sim:
+        sim.step(37)
+        st = sim.particle_state()
+        cg, og = sim.solid()
+    ora.set_particle_state(st)
+    co, oo = ora.solid(ora.t)
+    assert np.array_equal(cg, co) and np.array_equal(og, oo)
+    assert (cg > 0).sum() > 100
+
+
+def test_coupled_step_from_identical_state():
+    from paper_2308_05007_gb300.rwmi import Simulation
+    from oracle.oracle import lattice
+    w = I.dem_box(n_particles=3, seed=4, speed=0.0, gravity=(0.0, 0.0, -2e-4), hydro=1, n_walkers=0)
+    w = I.with_(w, body_force=(3e-5, 0.0, 0.0))
+    w.dem.velocity[:] = 0.0
+    w.dem.spin[:] = 0.0
+    with Simulation.from_workload(w, seed_walkers=False) as sim:
+        eg, _ = sim.lattice()
+        eo, _ = lattice(w.q)
+        perm = np.array([int(np.where((eg == eo[i]).all(1))[0][0]) for i in range(w.q)])
+        sim.step(12)
+        t = sim.t
+        f0 = sim.populations()[perm]
+        st0 = sim.particle_state()
+        sim.step(1)
+        st1 = sim.particle_state()
+        Fg = sim.particle_forces()
+    ora = Oracle.from_workload(w, seed_walkers=False)
+    ora.set_populations(f0)
+    ora.set_time(t)
+    ora.set_particle_state(st0)
+    ora.step_fluid(1)
+    Fo = ora.forces()
+    so = ora.particle_state()
+    assert np.abs(Fo[:, :3]).max() > 1e-4   # the fluid does push
+    tolF = 2e-4 * np.abs(Fo[:, :3]).max()
+    tolT = 2e-4 * np.abs(Fo[:, 3:]).max()
+    np.testing.assert_allclose(Fg[:, :3], Fo[:, :3], rtol=0, atol=tolF)
+    np.testing.assert_allclose(Fg[:, 3:], Fo[:, 3:], rtol=0, atol=tolT)
+    # one LBM step = the DEM steps of dt = 1 / substeps: velocity error <= force error / m, origin
+    # error <= that (times sum of dt k dt <= 1), spin error <= torque error / smallest inertia
+    dv = tolF / w.dem.mass.min()
+    dw = tolT / w.dem.inertia[:, :3].min()
+    assert np.abs(st1[:, 7:10] - so[:, 7:10]).max() <= dv + 1e-15
+    assert np.abs(st1[:, :3] - so[:, :3]).max() <= dv + 1e-12
+    assert np.abs(st1[:, 10:13] - so[:, 10:13]).max() <= dw + 1e-15
+    assert np.abs(st1[:, 7:10] - st0[:, 7:10]).max() > 100 * dv   # the step moved them
+
+
+def test_schedules_graphs_and_restart_agree(tmp_path):
+    from paper_2308_05007_gb300.rwmi import Simulation
+    w = _converging(hydro=1)
+    ref = None
+    for overlap in (0, 1, 2):
+        for graphs in (False, True):
+            with Simulation.from_workload(w, overlap=overlap, use_graphs=graphs, sort_interval=4) as s:
+                s.step(30)
+                pos, _ = s.walkers_by_id()
+                res = (s.particle_state(), s.populations(), pos)
+            if ref is None:
+                ref = res
+            else:
+                for a, b in zip(ref, res):
+                    assert np.array_equal(a, b), (overlap, graphs)
+    path = os.fspath(tmp_path / "dem.ckpt")
+    with Simulation.from_workload(w, sort_interval=4) as s:
+        s.step(14)
+        s.save(path)
+        s.step(16)
+        want = (s.particle_state(), s.populations())
+    with Simulation.from_workload(w, sort_interval=4) as s:
+        s.load(path)
+        s.step(16)
+        got = (s.particle_state(), s.populations())
+    for a, b in zip(want, got):
+        assert np.array_equal(a, b)
+
+
+def test_refused_setups():
+    from paper_2308_05007_gb300.rwmi import RwmiError, Simulation
+    for kw in (dict(coupling=1), dict(storage=2)):
+        w = I.with_(_converging(), **kw)
+        with pytest.raises(RwmiError):
+            Simulation.from_workload(w, seed_walkers=False)
