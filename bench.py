@@ -248,10 +248,11 @@ def measure_variants(a, stream):
     w_i rho0, binary16 shifted, binary64 shifted with binary64 arithmetic) and velocity sets
     (D3Q15, the paper's D3Q19): per-phase GPU time of 16 eager steps (CUDA events), LBM kernel
     HBM fraction and whole-step MLUPS. The binary64 run is bound by GB300's FP64 rate, not HBM.
-    Last, the paper's IBB coupling in place of partially saturated cells (graph-replayed step
-    time as well)."""
+    Then the paper's IBB coupling in place of partially saturated cells, and free particles (the
+    DEM of Eqs. 4-11) in place of the prescribed motion (graph-replayed step time as well)."""
     import argparse as _ap
 
+    import numpy as np
     import torch
     from paper_2308_05007_gb300 import inputs as I
     from paper_2308_05007_gb300.rwmi import Simulation
@@ -300,6 +301,33 @@ def measure_variants(a, stream):
         out[f"D3Q{q}_fp32_shift_ibb"] = {
             "lbm_ms": lbm_ms, "lbm_gbs": gbs, "lbm_hbm_frac": gbs / peak,
             "step_ms": step_ms, "mlups": w.n_cells / (step_ms / 1e3) / 1e6}
+    # free particles (Eqs. 4-11) in place of the prescribed motion: the same box and particles,
+    # density 2, gravity, damped frictional contacts, 10 DEM steps per LBM step; the LBM forms the
+    # force in its update on every step, and the raster of t+1 follows the DEM
+    w = I.oscillator_dem(n=a.n, n_particles=a.particles, n_walkers=a.walkers, q=15, storage=1)
+    w = I.with_(w, sort_interval=a.sort_interval, moment_interval=a.moment_interval)
+    sim = Simulation.from_workload(w, seed_walkers=False)
+    sim.set_stream(stream)
+    sim.seed_walkers(w.n_walkers, *w.walker_box)
+    sim.step(16)
+    ph = sim.step_timed(16)
+    sim.step(32)
+    with torch.cuda.stream(stream):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.step(64)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    step_ms = e0.elapsed_time(e1) / 64
+    st = sim.particle_state()
+    sim.close()
+    lbm_ms = ph["lbm"] / 16
+    gbs = lbm_bytes_per_launch(w, w.n_cells, 4) / (lbm_ms / 1e3) / 1e9
+    out["D3Q15_fp32_shift_dem"] = {
+        "lbm_ms": lbm_ms, "lbm_gbs": gbs, "lbm_hbm_frac": gbs / peak,
+        "dem_and_poses_ms": ph["pose_bricks"] / 16, "substeps": w.dem.substeps,
+        "step_ms": step_ms, "mlups": w.n_cells / (step_ms / 1e3) / 1e6,
+        "max_particle_speed": float(np.linalg.norm(st[:, 7:10], axis=1).max())}
     return out
 
 

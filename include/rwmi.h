@@ -168,16 +168,24 @@ typedef struct {
 RWMI_API void rwmi_dem_defaults(rwmi_dem_config* cfg);
 
 /* Switches the current particles to the free DEM from the current time. Per particle (host
- * arrays): mass [P] > 0, body-frame inertia tensor about the origin [6 P] (xx, yy, zz, xy, xz,
- * yz), sphere radius R_s [P] with 0 < R_s < R_c, initial velocity and spin [3 P] (NULL: those of
- * the prescribed motion at the current time). The state starts at the prescribed origin of the
- * current time with the body frame as given. Requires partially saturated cells (coupling 0),
- * binary32-shifted or binary64 storage, and at most 16 control points per particle; every step
- * then forms the fluid force in the LBM update itself (one fused pass). RWMI_E_INVALID otherwise.
- * Before the first step, or after a restart. */
-RWMI_API rwmi_status rwmi_set_dem(rwmi_ctx* ctx, const rwmi_dem_config* cfg, const double* mass,
-                                  const double* inertia, const double* sphere_radius,
-                                  const double* velocity, const double* spin);
+ * arrays): density [P] > 0, sphere radius R_s [P], initial velocity and spin [3 P] (NULL: those
+ * of the prescribed motion at the current time). Mass, centre of mass and inertia tensor come
+ * from the metaball itself: body-frame sample points (i + 1/2) h, h = 1/4, inside when the
+ * binary32 sum of Eq. 3 reaches 1, summed exactly as integers (rwmi_particle_mass). The body
+ * frame is then moved to the centre of mass (control points c_i - c_m in binary32), so the
+ * state's origin is the centre of mass. The state starts at the prescribed origin of the
+ * current time (plus c_m) with the body frame as given. Requires 0 < R_s < max |c_i - c_m| +
+ * sqrt(k_i), partially saturated cells (coupling 0), binary32-shifted or binary64 storage, and
+ * at most 16 control points per particle; every step then forms the fluid force in the LBM
+ * update itself (one fused pass). RWMI_E_INVALID otherwise (context unchanged), RWMI_E_STATE if
+ * the particles are free already. Before the first step. */
+RWMI_API rwmi_status rwmi_set_dem(rwmi_ctx* ctx, const rwmi_dem_config* cfg, const double* density,
+                                  const double* sphere_radius, const double* velocity,
+                                  const double* spin);
+
+/* Mass properties of the free particles, out[10 p .. 10 p + 9] = mass, centre of mass in the body
+ * frame given to rwmi_set_metaballs (3), inertia tensor about it (xx, yy, zz, xy, xz, yz). */
+RWMI_API rwmi_status rwmi_particle_mass(rwmi_ctx* ctx, double* out);
 
 /* Free-DEM state, out[13 p .. 13 p + 12] = origin (unwrapped) x y z, orientation quaternion
  * w x y z, velocity, spin (world frame), binary64; RWMI_E_STATE without rwmi_set_dem. */

@@ -88,9 +88,8 @@ def lib():
             L.orc_ibb_q.argtypes = [P, C.c_longlong, C.c_int, C.c_longlong, C.c_longlong, C.c_longlong, C.c_void_p]
             L.orc_set_dem.restype = C.c_int
             L.orc_set_dem.argtypes = [P, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double, dp,
-                                      C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
-                                      C.c_void_p]
-            for name in ("orc_particle_state", "orc_set_particle_state"):
+                                      C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+            for name in ("orc_particle_state", "orc_set_particle_state", "orc_dem_mass"):
                 getattr(L, name).argtypes = [P, C.c_void_p]
             L.orc_dem_pair_geom.argtypes = [P, C.c_int, C.c_int, C.c_void_p]
             L.orc_dem_wall_geom.argtypes = [P, C.c_int, C.c_int, C.c_void_p]
@@ -193,19 +192,24 @@ class Oracle:
         """Free DEM (Eqs. 4-11) instead of the prescribed trajectories, from the current time."""
         P = self.n_particles
         self._dem = dict(
-            m=np.ascontiguousarray(dem.mass, np.float64).reshape(P),
-            I=np.ascontiguousarray(dem.inertia, np.float64).reshape(P * 6),
+            rho=np.ascontiguousarray(np.broadcast_to(dem.density, (P,)), np.float64),
             Rs=np.ascontiguousarray(dem.sphere_radius, np.float64).reshape(P),
             v=None if dem.velocity is None else np.ascontiguousarray(dem.velocity, np.float64).reshape(P * 3),
             w=None if dem.spin is None else np.ascontiguousarray(dem.spin, np.float64).reshape(P * 3))
         d = self._dem
         rc = lib().orc_set_dem(self.h, float(dem.kn), float(dem.eta_n), float(dem.kt), float(dem.eta_t),
                                float(dem.mu_s), _d3(dem.gravity), int(dem.substeps), int(dem.hydro),
-                               _ptr(d["m"]), _ptr(d["I"]), _ptr(d["Rs"]),
+                               _ptr(d["rho"]), _ptr(d["Rs"]),
                                None if d["v"] is None else _ptr(d["v"]),
                                None if d["w"] is None else _ptr(d["w"]))
         if rc != 0:
             raise ValueError("oracle: invalid DEM set-up")
+
+    def dem_mass(self) -> np.ndarray:
+        """[P, 10]: mass, centre of mass (given body frame), inertia about it (xx yy zz xy xz yz)."""
+        out = np.zeros((max(self.n_particles, 1), 10))
+        lib().orc_dem_mass(self.h, _ptr(out))
+        return out[: self.n_particles]
 
     def particle_state(self) -> np.ndarray:
         """[P, 13]: origin (unwrapped), quaternion (w, x, y, z), velocity, spin."""

@@ -140,6 +140,7 @@ typedef struct {
     double dem_kn, dem_etan, dem_kt, dem_etat, dem_mus, dem_g[3];
     double* dst;             /* [13 P] origin (unwrapped), quaternion (w, x, y, z), velocity, spin */
     double *dmass, *dIb, *dRs, *dzoom;   /* [P], [6 P] body inertia (xx yy zz xy xz yz), [P], [P] */
+    double* dcm;             /* [10 P] mass properties (orc_dem_mass) */
     double *dxi, *dxm;       /* pairs (i < j) at i P + j: tangential spring, Newton point [3 each] */
     unsigned char* dact;     /* pair in contact at the last substep */
     double *dxiw, *dxmw;     /* walls: particle p, face f (2 axis + side) at 6 p + f */
@@ -1546,7 +1547,7 @@ ORC_API void orc_destroy(void* h)
     free(o->coff); free(o->cbody); free(o->kc); free(o->kc32);
     free(o->org); free(o->amp); free(o->per); free(o->pha); free(o->omg); free(o->Rb);
     free(o->Fp); free(o->Tp); free(o->x); free(o->x0);
-    free(o->dst); free(o->dmass); free(o->dIb); free(o->dRs); free(o->dzoom);
+    free(o->dst); free(o->dmass); free(o->dIb); free(o->dRs); free(o->dzoom); free(o->dcm);
     free(o->dxi); free(o->dxm); free(o->dact); free(o->dxiw); free(o->dxmw); free(o->dactw);
     free(o);
 }
@@ -1954,13 +1955,65 @@ static double dem_reach(const orc_t* o, int p)
     return r;
 }
 
+/* Mass properties of particle p from its metaball (Eq. 3) at density rho: the body-frame sample
+ * points (i + 1/2) h, h = 1/4, out to the bound radius, inside when the binary32 sum (the
+ * operation order of metaball32, no wrapping) reaches 1. The sums of the inside points' counts,
+ * coordinates and coordinate products are integers (in units of h/2), so they are exact; then
+ * m = rho n h^3, the centre of mass, and the inertia tensor about it (xx yy zz xy xz yz). */
+#define DEM_MASS_H 0.25
+static void dem_mass(const orc_t* o, int p, double rho, double out[10])
+{
+    int N = (int)ceil(o->Rb[p] / DEM_MASS_H) + 1;
+    long long n = 0, S1[3] = {0, 0, 0}, S2[6] = {0, 0, 0, 0, 0, 0};
+    for (int k = -N; k < N; ++k)
+        for (int j = -N; j < N; ++j)
+            for (int i = -N; i < N; ++i) {
+                int a = 2 * i + 1, b = 2 * j + 1, c = 2 * k + 1;
+                float x[3] = {(float)a * 0.125f, (float)b * 0.125f, (float)c * 0.125f};
+                float f = 0.0f;
+                for (int m = o->coff[p]; m < o->coff[p + 1]; ++m) {
+                    float dx = x[0] - (float)o->cbody[3 * m];
+                    float dy = x[1] - (float)o->cbody[3 * m + 1];
+                    float dz = x[2] - (float)o->cbody[3 * m + 2];
+                    float xx = dx * dx;
+                    float yy = dy * dy;
+                    float zz = dz * dz;
+                    float r2 = xx + yy;
+                    r2 = r2 + zz;
+                    f = f + o->kc32[m] / r2;
+                }
+                if (f >= 1.0f) {
+                    n++;
+                    S1[0] += a; S1[1] += b; S1[2] += c;
+                    S2[0] += (long long)a * a; S2[1] += (long long)b * b; S2[2] += (long long)c * c;
+                    S2[3] += (long long)a * b; S2[4] += (long long)a * c; S2[5] += (long long)b * c;
+                }
+            }
+    double dn = (double)n;
+    out[0] = rho * (dn * 0.015625);
+    double cm[3];
+    for (int e = 0; e < 3; ++e) { cm[e] = ((double)S1[e] * 0.125) / dn; out[1 + e] = cm[e]; }
+    static const int ia[6] = {0, 1, 2, 0, 0, 1}, ib[6] = {0, 1, 2, 1, 2, 2};
+    double J[6], w = rho * 0.015625;
+    for (int m = 0; m < 6; ++m) J[m] = ((double)S2[m] * 0.015625 - (dn * cm[ia[m]]) * cm[ib[m]]) * w;
+    out[4] = J[1] + J[2];
+    out[5] = J[0] + J[2];
+    out[6] = J[0] + J[1];
+    out[7] = -J[3];
+    out[8] = -J[4];
+    out[9] = -J[5];
+}
+
 /* Free DEM set-up: contact law, gravity, DEM steps per LBM step, hydrodynamic coupling on/off,
- * and per particle the mass, body-frame inertia (xx yy zz xy xz yz), sphere radius R_s, initial
- * velocity and spin (NULL: those of the prescribed motion at the current time). The state starts
- * at the prescribed origin of the current time with the body frame as given (identity
- * orientation). Returns 0, or -1 for an invalid set-up. */
+ * and per particle the density, sphere radius R_s, initial velocity and spin (NULL: those of the
+ * prescribed motion at the current time). Mass, centre of mass and inertia follow from the
+ * metaball (dem_mass); the body frame is then moved to the centre of mass (control points
+ * c_i - c_m rounded to binary32, origin + c_m), so that the state's origin is the centre of
+ * mass and the fluid's torque is taken about it. The state starts at the prescribed origin of
+ * the current time with the body frame as given (identity orientation). Returns 0, or -1 for
+ * an invalid set-up. */
 ORC_API int orc_set_dem(void* h, double kn, double etan, double kt, double etat, double mus,
-                        const double g[3], int nsub, int hydro, const double* mass, const double* inertia,
+                        const double g[3], int nsub, int hydro, const double* density,
                         const double* Rs, const double* v0, const double* w0)
 {
     orc_t* o = (orc_t*)h;
@@ -1968,8 +2021,21 @@ ORC_API int orc_set_dem(void* h, double kn, double etan, double kt, double etat,
     if (o->coupling != 0 || nsub < 1 || P < 1 || kn < 0.0 || etan < 0.0 || kt < 0.0 || etat < 0.0 || mus < 0.0)
         return -1;
     for (int p = 0; p < P; ++p)
-        if (!(mass[p] > 0.0) || !(Rs[p] > 0.0) || !(Rs[p] < dem_reach(o, p))) return -1;
-    free(o->dst); free(o->dmass); free(o->dIb); free(o->dRs); free(o->dzoom);
+        if (!(density[p] > 0.0) || !(Rs[p] > 0.0)) return -1;
+    double* mp = (double*)malloc(sizeof(double) * 10 * (size_t)P);
+    for (int p = 0; p < P; ++p) {
+        dem_mass(o, p, density[p], mp + 10 * p);
+        if (!(mp[10 * p] > 0.0)) { free(mp); return -1; }
+    }
+    /* recentre the body frames on the centres of mass */
+    for (int p = 0; p < P; ++p) {
+        const double* cm = mp + 10 * p + 1;
+        for (int i = o->coff[p]; i < o->coff[p + 1]; ++i)
+            for (int a = 0; a < 3; ++a) o->cbody[3 * i + a] = (double)(float)(o->cbody[3 * i + a] - cm[a]);
+        o->Rb[p] = bound_radius(o, p);
+        if (!(Rs[p] < dem_reach(o, p))) { free(mp); return -1; }
+    }
+    free(o->dst); free(o->dmass); free(o->dIb); free(o->dRs); free(o->dzoom); free(o->dcm);
     free(o->dxi); free(o->dxm); free(o->dact); free(o->dxiw); free(o->dxmw); free(o->dactw);
     size_t PP = (size_t)P * P;
     o->dst = (double*)calloc(13 * (size_t)P, sizeof(double));
@@ -1977,6 +2043,7 @@ ORC_API int orc_set_dem(void* h, double kn, double etan, double kt, double etat,
     o->dIb = (double*)malloc(sizeof(double) * 6 * (size_t)P);
     o->dRs = (double*)malloc(sizeof(double) * (size_t)P);
     o->dzoom = (double*)malloc(sizeof(double) * (size_t)P);
+    o->dcm = mp;
     o->dxi = (double*)calloc(3 * PP, sizeof(double));
     o->dxm = (double*)calloc(3 * PP, sizeof(double));
     o->dact = (unsigned char*)calloc(PP, 1);
@@ -1992,19 +2059,27 @@ ORC_API int orc_set_dem(void* h, double kn, double etan, double kt, double etat,
         particle_pose(o, o->t, p, org, vel, R);
         double* st = o->dst + 13 * (size_t)p;
         for (int a = 0; a < 3; ++a) {
-            st[a] = org[a];
+            st[a] = org[a] + mp[10 * p + 1 + a];
             st[7 + a] = v0 ? v0[3 * p + a] : vel[a];
             st[10 + a] = w0 ? w0[3 * p + a] : o->omg[3 * p + a];
         }
         st[3] = 1.0; st[4] = st[5] = st[6] = 0.0;
-        o->dmass[p] = mass[p];
-        for (int m = 0; m < 6; ++m) o->dIb[6 * p + m] = inertia[6 * p + m];
+        o->dmass[p] = mp[10 * p];
+        for (int m = 0; m < 6; ++m) o->dIb[6 * p + m] = mp[10 * p + 4 + m];
         o->dRs[p] = Rs[p];
         o->dzoom[p] = 1.0 - Rs[p] / dem_reach(o, p);
     }
     o->dem = 1;
     o->solid_time = -1;
     return 0;
+}
+
+/* Mass properties of the free-DEM particles: out[10 p ..] = mass, centre of mass in the original
+ * body frame (3), inertia about it (xx yy zz xy xz yz) */
+ORC_API void orc_dem_mass(void* h, double* out)
+{
+    orc_t* o = (orc_t*)h;
+    if (o->dem) memcpy(out, o->dcm, sizeof(double) * 10 * (size_t)o->P);
 }
 
 ORC_API void orc_particle_state(void* h, double* out)

@@ -205,8 +205,33 @@ ParticleSet particle_set(const rwmi_ctx* c) {
   return ps;
 }
 
-// Free-DEM buffers of P particles: binary64 words, then contact-flag bytes
-size_t dem_doubles(size_t P) { return 94 * P + 15 * P * P; }
+// Bound radius of a particle about its body origin: with r = |x - o|, |x - x_i| >= r - |c_i|, so
+// f <= sum k_i / (r - |c_i|)^2 once r > max |c_i|; beyond the unit crossing of that falling bound
+// f stays below 1. Inflated a little, since it only has to be conservative.
+float bound_radius(const float4* body, int c0, int c1) {
+  double cmax = 0.0, ksum = 0.0;
+  std::vector<double> cn;
+  for (int i = c0; i < c1; ++i) {
+    const double r = std::sqrt((double)body[i].x * body[i].x + (double)body[i].y * body[i].y +
+                               (double)body[i].z * body[i].z);
+    cn.push_back(r);
+    cmax = std::max(cmax, r);
+    ksum += body[i].w;
+  }
+  double lo = cmax, hi = cmax + std::sqrt(ksum) + 1e-9;
+  for (int it = 0; it < 200; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    double s = 0.0;
+    for (size_t m = 0; m < cn.size(); ++m) s += (double)body[c0 + m].w / ((mid - cn[m]) * (mid - cn[m]));
+    if (s > 1.0) lo = mid; else hi = mid;
+  }
+  return (float)(hi * (1.0 + 1e-6) + 1e-4);
+}
+
+// Free-DEM buffers of P particles: binary64 words (dem_args' views, then the mass properties
+// [10 P]), then contact-flag bytes
+size_t dem_doubles(size_t P) { return 104 * P + 15 * P * P; }
+double* dem_props(const rwmi_ctx* c) { return c->dem_d + 94 * (size_t)c->P + 15 * (size_t)c->P * c->P; }
 size_t dem_bytes(size_t P) { return P * P + 6 * P; }
 
 // Views of a context's DEM buffers; the fluid force is that of time parity tp (step t's update)
@@ -703,29 +728,13 @@ RWMI_API rwmi_status rwmi_set_metaballs(rwmi_ctx* c, int32_t P, const int32_t* c
       return fail(c, RWMI_E_INVALID, "rwmi_set_metaballs: bad period or phase");
     d.c0 = coff[p];
     d.c1 = coff[p + 1];
-    // Bound radius: with r = |x - o|, |x - x_i| >= r - |c_i|, so f <= sum k_i / (r - |c_i|)^2
-    // once r > max |c_i|; beyond the unit crossing of that falling bound f stays below 1.
-    double cmax = 0.0, ksum = 0.0;
-    std::vector<double> cn;
     for (int i = d.c0; i < d.c1; ++i) {
       if (!(k[i] > 0.0f) || !std::isfinite(cb[3 * i]) || !std::isfinite(cb[3 * i + 1]) || !std::isfinite(cb[3 * i + 2]))
         return fail(c, RWMI_E_INVALID, "rwmi_set_metaballs: bad control point");
-      const double r = std::sqrt((double)cb[3 * i] * cb[3 * i] + (double)cb[3 * i + 1] * cb[3 * i + 1] +
-                                 (double)cb[3 * i + 2] * cb[3 * i + 2]);
-      cn.push_back(r);
-      cmax = std::max(cmax, r);
-      ksum += k[i];
+      body[i] = make_float4(cb[3 * i], cb[3 * i + 1], cb[3 * i + 2], k[i]);
     }
-    double lo = cmax, hi = cmax + std::sqrt(ksum) + 1e-9;
-    for (int it = 0; it < 200; ++it) {
-      const double mid = 0.5 * (lo + hi);
-      double s = 0.0;
-      for (size_t m = 0; m < cn.size(); ++m) s += (double)k[d.c0 + m] / ((mid - cn[m]) * (mid - cn[m]));
-      if (s > 1.0) lo = mid; else hi = mid;
-    }
-    d.rb = (float)(hi * (1.0 + 1e-6) + 1e-4);
+    d.rb = bound_radius(body.data(), d.c0, d.c1);
   }
-  for (int i = 0; i < Nc; ++i) body[i] = make_float4(cb[3 * i], cb[3 * i + 1], cb[3 * i + 2], k[i]);
   dfree(c, c->desc);
   dfree(c, c->cbody);
   c->desc = nullptr;
@@ -760,11 +769,11 @@ RWMI_API void rwmi_dem_defaults(rwmi_dem_config* cfg) {
   cfg->hydro = 1;
 }
 
-RWMI_API rwmi_status rwmi_set_dem(rwmi_ctx* c, const rwmi_dem_config* cfg, const double* mass,
-                                  const double* inertia, const double* Rs, const double* vel,
-                                  const double* spin) {
+RWMI_API rwmi_status rwmi_set_dem(rwmi_ctx* c, const rwmi_dem_config* cfg, const double* density,
+                                  const double* Rs, const double* vel, const double* spin) {
   if (!c || !cfg) return RWMI_E_INVALID;
-  if (c->P < 1 || !mass || !inertia || !Rs) return fail(c, RWMI_E_INVALID, "rwmi_set_dem: no particles or null array");
+  if (c->P < 1 || !density || !Rs) return fail(c, RWMI_E_INVALID, "rwmi_set_dem: no particles or null array");
+  if (c->dem) return fail(c, RWMI_E_STATE, "rwmi_set_dem: the particles are free already");
   if (c->cfg.coupling != 0 || (c->cfg.storage != RWMI_STORE_FP32_SHIFT && c->cfg.storage != RWMI_STORE_FP64_SHIFT))
     return fail(c, RWMI_E_INVALID, "rwmi_set_dem: needs coupling 0 and storage 1 or 3");
   if (!(cfg->kn >= 0.0) || !(cfg->eta_n >= 0.0) || !(cfg->kt >= 0.0) || !(cfg->eta_t >= 0.0) || !(cfg->mu_s >= 0.0) ||
@@ -780,16 +789,8 @@ RWMI_API rwmi_status rwmi_set_dem(rwmi_ctx* c, const rwmi_dem_config* cfg, const
   for (int p = 0; p < P; ++p) {
     const ParticleDesc& d = desc[p];
     if (d.c1 - d.c0 > DEM_MAX_CP) return fail(c, RWMI_E_INVALID, "rwmi_set_dem: more than 16 control points");
-    double reach = 0.0;   // validation only (the kernel forms the zoom)
-    for (int i = d.c0; i < d.c1; ++i) {
-      const float4 b = c->hbody[i];
-      reach = std::max(reach, std::sqrt((double)b.x * b.x + (double)b.y * b.y + (double)b.z * b.z) +
-                                  std::sqrt((double)b.w));
-    }
-    if (!(mass[p] > 0.0) || !std::isfinite(mass[p]) || !(Rs[p] > 0.0) || !(Rs[p] < reach))
-      return fail(c, RWMI_E_INVALID, "rwmi_set_dem: need mass > 0 and 0 < R_s < max |c_i| + sqrt(k_i)");
-    for (int m = 0; m < 6; ++m)
-      if (!std::isfinite(inertia[6 * p + m])) return fail(c, RWMI_E_INVALID, "rwmi_set_dem: non-finite inertia");
+    if (!(density[p] > 0.0) || !std::isfinite(density[p]) || !(Rs[p] > 0.0) || !std::isfinite(Rs[p]))
+      return fail(c, RWMI_E_INVALID, "rwmi_set_dem: need density > 0 and R_s > 0");
     // the prescribed motion at the current time gives the start
     double s = 0.0, cdt = 0.0;
     if (d.period > 0.0) {
@@ -807,28 +808,66 @@ RWMI_API rwmi_status rwmi_set_dem(rwmi_ctx* c, const rwmi_dem_config* cfg, const
     }
     q[3] = 1.0;
   }
-  dfree(c, c->dem_d);
-  dfree(c, c->dem_b);
-  c->dem_d = nullptr;
-  c->dem_b = nullptr;
-  c->dem = false;
   CK(dalloc(c, &c->dem_d, sizeof(double) * dem_doubles((size_t)P)));
   CK(dalloc(c, &c->dem_b, dem_bytes((size_t)P)));
   CK(cudaMemsetAsync(c->dem_d, 0, sizeof(double) * dem_doubles((size_t)P), c->stream));
   CK(cudaMemsetAsync(c->dem_b, 0, dem_bytes((size_t)P), c->stream));
   c->demcfg = *cfg;
-  c->dem = true;
   DemArgs a = dem_args(c, (int)(c->t & 1));
+  double* dens = nullptr;
+  unsigned long long* sums = nullptr;
+  CK(dalloc(c, &dens, sizeof(double) * (size_t)P));
+  CK(dalloc(c, &sums, sizeof(unsigned long long) * 10 * (size_t)P));
+  CK(cudaMemsetAsync(sums, 0, sizeof(unsigned long long) * 10 * (size_t)P, c->stream));
   CK(copy_now(c, a.st, st.data(), sizeof(double) * st.size()));
-  CK(copy_now(c, const_cast<double*>(a.mass), mass, sizeof(double) * (size_t)P));
-  CK(copy_now(c, const_cast<double*>(a.Ib), inertia, sizeof(double) * 6 * (size_t)P));
+  CK(copy_now(c, dens, density, sizeof(double) * (size_t)P));
   CK(copy_now(c, const_cast<double*>(a.Rs), Rs, sizeof(double) * (size_t)P));
+  const std::vector<float4> old_body = c->hbody;
+  launch_dem_mass(a, sums, dens, const_cast<double*>(a.mass), const_cast<double*>(a.Ib), dem_props(c), c->cbody,
+                  c->stream);
+  dfree(c, dens);
+  dfree(c, sums);
+  // the recentred body frames: host copy and bound radii
+  CK(copy_now(c, c->hbody.data(), c->cbody, sizeof(float4) * c->hbody.size()));
+  bool ok = true;
+  std::vector<double> props((size_t)10 * P);
+  CK(copy_now(c, props.data(), dem_props(c), sizeof(double) * props.size()));
+  for (int p = 0; p < P; ++p) {
+    ParticleDesc& d = desc[p];
+    d.rb = bound_radius(c->hbody.data(), d.c0, d.c1);
+    double reach = 0.0;   // validation only (the kernel forms the zoom)
+    for (int i = d.c0; i < d.c1; ++i) {
+      const float4 b = c->hbody[i];
+      reach = std::max(reach, std::sqrt((double)b.x * b.x + (double)b.y * b.y + (double)b.z * b.z) +
+                                  std::sqrt((double)b.w));
+    }
+    ok = ok && Rs[p] < reach && props[10 * p] > 0.0;
+  }
+  if (!ok) {   // restore the body frames: the context stays as it was
+    c->hbody = old_body;
+    CK(copy_now(c, c->cbody, old_body.data(), sizeof(float4) * old_body.size()));
+    dfree(c, c->dem_d);
+    dfree(c, c->dem_b);
+    c->dem_d = nullptr;
+    c->dem_b = nullptr;
+    return fail(c, RWMI_E_INVALID, "rwmi_set_dem: need 0 < R_s < max |c_i - c_m| + sqrt(k_i) and a non-empty shape");
+  }
+  CK(copy_now(c, c->desc, desc.data(), sizeof(ParticleDesc) * desc.size()));
+  a = dem_args(c, (int)(c->t & 1));
   launch_dem_init(a, c->stream);
+  c->dem = true;
   drop_graphs(c);
   rwmi_status r = build_current_frame(c);
   if (r != RWMI_OK) return r;
   CK(cudaStreamSynchronize(c->stream));
   CK(cudaGetLastError());
+  return RWMI_OK;
+}
+
+RWMI_API rwmi_status rwmi_particle_mass(rwmi_ctx* c, double* out) {
+  if (!c || !out) return RWMI_E_INVALID;
+  if (!c->dem) return fail(c, RWMI_E_STATE, "rwmi_particle_mass: no free DEM (rwmi_set_dem)");
+  CK(copy_now(c, out, dem_props(c), sizeof(double) * 10 * (size_t)c->P));
   return RWMI_OK;
 }
 

@@ -416,7 +416,88 @@ __global__ void dem_init_kernel(DemArgs a) {
   a.zoom[p] = 1.0 - a.Rs[p] / r;
 }
 
+// Mass properties from the metaball: body-frame sample points (i + 1/2) h, h = 1/4, out to the
+// bound radius (N points per half-axis), inside when the binary32 sum reaches 1; integer sums in
+// units of h/2 per particle: count, coordinates (3), products (xx yy zz xy xz yz). One block per
+// particle; the sums are exact, so their order does not matter.
+__global__ void dem_mass_sums_kernel(DemArgs a, unsigned long long* sums) {
+  const int p = blockIdx.x;
+  const ParticleDesc& d = a.desc[p];
+  const int N = (int)ceil((double)d.rb / 0.25) + 1;
+  const int side = 2 * N;
+  const long long total = (long long)side * side * side;
+  long long v[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  for (long long m = threadIdx.x; m < total; m += blockDim.x) {
+    const int i = (int)(m % side) - N, j = (int)((m / side) % side) - N, k = (int)(m / ((long long)side * side)) - N;
+    const int ca = 2 * i + 1, cb = 2 * j + 1, cc = 2 * k + 1;
+    const float x = (float)ca * 0.125f, y = (float)cb * 0.125f, z = (float)cc * 0.125f;
+    float f = 0.0f;
+    for (int q = d.c0; q < d.c1; ++q) {
+      const float4 c = a.cbody[q];
+      const float dx = x - c.x, dy = y - c.y, dz = z - c.z;
+      const float xx = dx * dx, yy = dy * dy, zz = dz * dz;
+      float r2 = xx + yy;
+      r2 = r2 + zz;
+      f = f + c.w / r2;
+    }
+    if (f >= 1.0f) {
+      v[0] += 1; v[1] += ca; v[2] += cb; v[3] += cc;
+      v[4] += (long long)ca * ca; v[5] += (long long)cb * cb; v[6] += (long long)cc * cc;
+      v[7] += (long long)ca * cb; v[8] += (long long)ca * cc; v[9] += (long long)cb * cc;
+    }
+  }
+  for (int e = 0; e < 10; ++e) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[e] += __shfl_xor_sync(0xffffffffu, v[e], o);
+    if ((threadIdx.x & 31) == 0 && v[e]) atomicAdd(&sums[10 * p + e], (unsigned long long)v[e]);
+  }
+}
+
+// Per particle: mass, centre of mass and inertia about it (the oracle's formulas and order);
+// moves the body frame to the centre of mass (control points c_i - c_m in binary32, state
+// origin + c_m)
+__global__ void dem_mass_finish_kernel(DemArgs a, const unsigned long long* sums, const double* density,
+                                       double* mass, double* Ib, double* props, float4* cbody) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= a.P) return;
+  long long S[10];
+  for (int e = 0; e < 10; ++e) S[e] = (long long)sums[10 * p + e];
+  const double dn = (double)S[0];
+  const double rho = density[p];
+  double* out = props + 10 * p;
+  out[0] = rho * (dn * 0.015625);
+  double cm[3];
+  for (int e = 0; e < 3; ++e) { cm[e] = ((double)S[1 + e] * 0.125) / dn; out[1 + e] = cm[e]; }
+  const int ia[6] = {0, 1, 2, 0, 0, 1}, ib[6] = {0, 1, 2, 1, 2, 2};
+  double J[6];
+  const double w = rho * 0.015625;
+  for (int m = 0; m < 6; ++m) J[m] = ((double)S[4 + m] * 0.015625 - (dn * cm[ia[m]]) * cm[ib[m]]) * w;
+  out[4] = J[1] + J[2];
+  out[5] = J[0] + J[2];
+  out[6] = J[0] + J[1];
+  out[7] = -J[3];
+  out[8] = -J[4];
+  out[9] = -J[5];
+  mass[p] = out[0];
+  for (int m = 0; m < 6; ++m) Ib[6 * p + m] = out[4 + m];
+  for (int q = a.desc[p].c0; q < a.desc[p].c1; ++q) {
+    float4 c = cbody[q];
+    c.x = (float)((double)c.x - cm[0]);
+    c.y = (float)((double)c.y - cm[1]);
+    c.z = (float)((double)c.z - cm[2]);
+    cbody[q] = c;
+  }
+  for (int e = 0; e < 3; ++e) a.st[13 * p + e] = a.st[13 * p + e] + cm[e];
+}
+
 }  // namespace
+
+void launch_dem_mass(const DemArgs& a, unsigned long long* sums, const double* density, double* mass, double* Ib,
+                     double* props, float4* cbody, cudaStream_t st) {
+  if (a.P <= 0) return;
+  dem_mass_sums_kernel<<<(unsigned)a.P, 256, 0, st>>>(a, sums);
+  dem_mass_finish_kernel<<<(unsigned)((a.P + 127) / 128), 128, 0, st>>>(a, sums, density, mass, Ib, props, cbody);
+}
 
 void launch_dem_init(const DemArgs& a, cudaStream_t st) {
   if (a.P > 0) dem_init_kernel<<<(unsigned)((a.P + 127) / 128), 128, 0, st>>>(a);

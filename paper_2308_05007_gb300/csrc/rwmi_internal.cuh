@@ -258,6 +258,11 @@ struct DemArgs {
 void launch_dem(const DemArgs& a, int substeps, cudaStream_t st);
 // the zoom factors from the sphere radii (rwmi_set_dem)
 void launch_dem_init(const DemArgs& a, cudaStream_t st);
+// mass properties from the metaballs at the given densities: integer sample sums (zeroed by the
+// caller, [10 P]), then mass, inertia, props [10 P] (mass, centre of mass, inertia); moves the
+// body frames (cbody) and the state origins to the centres of mass
+void launch_dem_mass(const DemArgs& a, unsigned long long* sums, const double* density, double* mass, double* Ib,
+                     double* props, float4* cbody, cudaStream_t st);
 // IBB node classes at time t (bricks bs of that time) into cur; with refill, nodes solid in prev
 // and fluid now get the equilibrium at their former particle's rigid velocity (Eq. 27).
 void launch_nodes(int q, int storage, const Geom& g, const ParticleSet& ps, BrickSet bs,

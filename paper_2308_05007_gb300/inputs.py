@@ -57,14 +57,12 @@ class Dem:
     """Free DEM set-up (Eqs. 4-11), lattice units. The particles then move under gravity, contact
     forces and (with hydro = 1) the fluid's force and torque, instead of following prescribed
     trajectories; the prescribed motion only gives the start (origin, and velocity and spin when
-    these are None).
+    these are None). Mass and inertia follow from each metaball and its density.
 
-    Per particle: mass, body-frame inertia about the origin (xx, yy, zz, xy, xz, yz), and the
-    sphero-metaball sphere radius R_s. Contact law: normal stiffness kn and damping eta_n,
-    tangential stiffness kt and damping eta_t, static friction mu_s. `substeps` DEM steps make
-    one LBM step."""
-    mass: np.ndarray                     # float64 [P]
-    inertia: np.ndarray                  # float64 [P, 6]
+    Contact law: normal stiffness kn and damping eta_n, tangential stiffness kt and damping
+    eta_t, static friction mu_s; sphere_radius is the sphero-metaball's R_s per particle.
+    `substeps` DEM steps make one LBM step."""
+    density: object                      # float or float64 [P], relative to the fluid's rho0
     sphere_radius: np.ndarray            # float64 [P]
     velocity: Optional[np.ndarray] = None  # float64 [P, 3]
     spin: Optional[np.ndarray] = None      # float64 [P, 3]
@@ -372,36 +370,6 @@ def with_(w: Workload, **kw) -> Workload:
 # ------------------------------------------------------------------------------------------
 # Free-DEM inputs
 # ------------------------------------------------------------------------------------------
-def cluster_mass_properties(mb: Metaballs, density: float):
-    """Mass properties of each particle, approximated by the spheres of radius sqrt(k_i) about
-    its control points (overlaps counted twice) at the given density. The body frame is moved
-    to that approximate centre of mass (control points and origin shifted together, so the
-    world positions stay the same). Returns (recentred Metaballs, mass [P], inertia [P, 6]
-    about the new origin: xx, yy, zz, xy, xz, yz)."""
-    P = mb.n_particles
-    cb = mb.centers_body.astype(np.float64).copy()
-    origin = mb.origin.astype(np.float64).copy()
-    mass = np.zeros(P)
-    inertia = np.zeros((P, 6))
-    for p in range(P):
-        sl = slice(int(mb.center_offsets[p]), int(mb.center_offsets[p + 1]))
-        r = np.sqrt(mb.k[sl].astype(np.float64))
-        mi = density * (4.0 / 3.0) * math.pi * r ** 3
-        com = (mi[:, None] * cb[sl]).sum(0) / mi.sum()
-        cb[sl] -= com
-        origin[p] += com
-        c = cb[sl]
-        sph = 0.4 * mi * r ** 2
-        cc = (c * c).sum(1)
-        I = np.zeros((3, 3))
-        for m_, s_, v, v2 in zip(mi, sph, c, cc):
-            I += s_ * np.eye(3) + m_ * (v2 * np.eye(3) - np.outer(v, v))
-        mass[p] = mi.sum()
-        inertia[p] = [I[0, 0], I[1, 1], I[2, 2], I[0, 1], I[0, 2], I[1, 2]]
-    mb2 = replace(mb, centers_body=cb.astype(np.float32), origin=origin)
-    return mb2, mass, inertia
-
-
 def sphere_radii(mb: Metaballs, fraction: float = 0.5) -> np.ndarray:
     """R_s of each particle: a fraction of its smallest control-point radius sqrt(k_i). Every
     such sphere lies inside the particle, so R_s stays below the bound radius."""
@@ -422,11 +390,10 @@ def dem_box(dims=(40, 36, 44), n_particles: int = 4, seed: int = 11, density: fl
     rng = np.random.default_rng(seed)
     mb = random_metaballs(rng, n_particles, dims, wall_mask=4, n_centers=(2, 3), sigma=1.2,
                           k_range=(4.0, 9.0))
-    mb, mass, inertia = cluster_mass_properties(mb, density)
     v = rng.normal(size=(n_particles, 3))
     v *= speed / np.linalg.norm(v, axis=1, keepdims=True)
     w = rng.normal(scale=0.01, size=(n_particles, 3))
-    dem = Dem(mass=mass, inertia=inertia, sphere_radius=sphere_radii(mb), velocity=v, spin=w, kn=kn,
+    dem = Dem(density=density, sphere_radius=sphere_radii(mb), velocity=v, spin=w, kn=kn,
               eta_n=eta_n, kt=kt, eta_t=eta_t, mu_s=mu_s, gravity=tuple(gravity), substeps=substeps,
               hydro=hydro)
     return Workload(
@@ -442,7 +409,6 @@ def oscillator_dem(n: int = 256, n_particles: int = 64, n_walkers: int = 10_000_
     (x-velocity 5 (2 pi / 2000)) and then move under the oscillating flow, gravity and
     contacts."""
     w = oscillator(n=n, n_particles=n_particles, n_walkers=n_walkers, **kw)
-    mb, mass, inertia = cluster_mass_properties(w.metaballs, density)
-    dem = Dem(mass=mass, inertia=inertia, sphere_radius=sphere_radii(mb), kn=kn, eta_n=eta_n, kt=kt,
+    dem = Dem(density=density, sphere_radius=sphere_radii(w.metaballs), kn=kn, eta_n=eta_n, kt=kt,
               eta_t=eta_t, mu_s=mu_s, gravity=tuple(gravity), substeps=substeps, hydro=1)
-    return replace(w, name=f"oscillator_dem_{n}", metaballs=mb, dem=dem)
+    return replace(w, name=f"oscillator_dem_{n}", dem=dem)

@@ -29,7 +29,7 @@ EXPORTED = ["rwmi_config_defaults", "rwmi_create", "rwmi_configure", "rwmi_set_s
             "rwmi_load", "rwmi_brick_stats", "rwmi_bin_walkers_noalloc", "rwmi_last_error",
             "rwmi_launch_count", "rwmi_destroy", "rwmi_batch_create", "rwmi_batch_step", "rwmi_batch_sync",
             "rwmi_batch_last_error", "rwmi_batch_destroy", "rwmi_dem_defaults", "rwmi_set_dem",
-            "rwmi_particle_state", "rwmi_set_particle_state"]
+            "rwmi_particle_state", "rwmi_set_particle_state", "rwmi_particle_mass"]
 
 
 class RwmiError(RuntimeError):
@@ -129,8 +129,9 @@ def load(build_if_missing: bool = False):
     L.rwmi_batch_destroy.restype = None
     L.rwmi_dem_defaults.argtypes = [C.POINTER(DemConfig)]
     L.rwmi_dem_defaults.restype = None
-    L.rwmi_set_dem.argtypes = [P, C.POINTER(DemConfig), vp, vp, vp, vp, vp]
+    L.rwmi_set_dem.argtypes = [P, C.POINTER(DemConfig), vp, vp, vp, vp]
     L.rwmi_particle_state.argtypes = [P, vp]
+    L.rwmi_particle_mass.argtypes = [P, vp]
     L.rwmi_set_particle_state.argtypes = [P, vp]
     for name in EXPORTED:
         fn = getattr(L, name)
@@ -286,14 +287,19 @@ class Simulation:
             cfg.gravity[a] = float(dem.gravity[a])
         cfg.substeps, cfg.hydro = int(dem.substeps), int(dem.hydro)
         P = self.n_particles
-        keep = dict(m=np.ascontiguousarray(dem.mass, np.float64).reshape(P),
-                    I=np.ascontiguousarray(dem.inertia, np.float64).reshape(6 * P),
+        keep = dict(rho=np.ascontiguousarray(np.broadcast_to(dem.density, (P,)), np.float64),
                     Rs=np.ascontiguousarray(dem.sphere_radius, np.float64).reshape(P),
                     v=None if dem.velocity is None else np.ascontiguousarray(dem.velocity, np.float64).reshape(3 * P),
                     w=None if dem.spin is None else np.ascontiguousarray(dem.spin, np.float64).reshape(3 * P))
-        self._check(self._L.rwmi_set_dem(self._h, C.byref(cfg), _ptr(keep["m"]), _ptr(keep["I"]), _ptr(keep["Rs"]),
+        self._check(self._L.rwmi_set_dem(self._h, C.byref(cfg), _ptr(keep["rho"]), _ptr(keep["Rs"]),
                                          None if keep["v"] is None else _ptr(keep["v"]),
                                          None if keep["w"] is None else _ptr(keep["w"])))
+
+    def particle_mass(self):
+        """[P, 10]: mass, centre of mass (given body frame), inertia about it (xx yy zz xy xz yz)."""
+        out = np.zeros((self.n_particles, 10))
+        self._check(self._L.rwmi_particle_mass(self._h, _ptr(out)))
+        return out
 
     def particle_state(self, out=None):
         """Free-DEM state [P, 13]: origin (unwrapped), quaternion (w, x, y, z), velocity, spin."""
