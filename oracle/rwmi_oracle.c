@@ -142,7 +142,7 @@ typedef struct {
     double *dmass, *dIb, *dRs, *dzoom;   /* [P], [6 P] body inertia (xx yy zz xy xz yz), [P], [P] */
     double* dcm;             /* [10 P] mass properties (orc_dem_mass) */
     double *dxi, *dxm;       /* pairs (i < j) at i P + j: tangential spring, Newton point [3 each] */
-    unsigned char* dact;     /* pair in contact at the last substep */
+    unsigned char* dact;     /* pair in contact at the last DEM step */
     double *dxiw, *dxmw;     /* walls: particle p, face f (2 axis + side) at 6 p + f */
     unsigned char* dactw;
 } orc_t;
@@ -1039,9 +1039,11 @@ static long long walker_cell(const orc_t* o, const double x[3])
  *    body-frame control points, so a single centre at the origin is reproduced exactly. The
  *    bound radius R_b,p (f_p < 1 beyond it) only skips pairs and faces out of reach.
  *  - Pair contact (Eqs. 6-9): Newton-Raphson on grad(f0 + f1) = 0 (Eq. 7) for the internal
- *    metaballs, DEM_NEWTON_NEW iterations from the deterministic start below, or
- *    DEM_NEWTON_CONT from the previous substep's point while the contact lasts; a step longer
- *    than one lattice unit is scaled to one, and a singular Hessian ends the iteration.
+ *    metaballs, at most DEM_NEWTON_NEW iterations from the deterministic start below, or
+ *    DEM_NEWTON_CONT from the previous DEM step's point while the contact lasts; a step longer
+ *    than one lattice unit is scaled to one, and a singular Hessian or a step below 1e-12 ends
+ *    the iteration. Pairs and faces out of reach (bound spheres apart) are skipped: they cannot
+ *    touch, so skipping changes no result.
  *    Eq. 8: q0 is chosen so that f0(x_m + q0 grad f0(x_m)) = 1 holds, as the text imposes:
  *    the crossing nearest to x_m, from the printed first-order Taylor value by a bracketed
  *    Newton iteration in q0 (surface_along). The single first-order step misplaces the surface
@@ -1159,7 +1161,8 @@ static int solve3(double A[3][3], const double b[3], double d[3])
     return 1;
 }
 
-/* Newton step with its length limited to one lattice unit; returns 0 when singular */
+/* Newton step with its length limited to one lattice unit; returns 0 when singular or when the
+ * step was below 1e-12 (converged) */
 static int newton_update(double A[3][3], const double G[3], double x[3])
 {
     double b[3] = {-G[0], -G[1], -G[2]}, d[3];
@@ -1167,7 +1170,7 @@ static int newton_update(double A[3][3], const double G[3], double x[3])
     double len = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
     double sc = len > 1.0 ? 1.0 / len : 1.0;
     for (int a = 0; a < 3; ++a) x[a] += sc * d[a];
-    return 1;
+    return len > 1e-12;
 }
 
 /* Eq. 8: x_c = x_m + q grad f(x_m) with f(x_c) = 1, the crossing nearest to x_m. q starts from
@@ -1198,6 +1201,7 @@ static void surface_along(const double* c, const double* k, int n, const double 
             double dq = gx[0] * g[0] + gx[1] * g[1] + gx[2] * g[2];
             double qn = fabs(dq) > 1e-300 ? q - (fx - 1.0) / dq : 0.5 * (lo + hi);
             if (!(qn > lo && qn < hi)) qn = 0.5 * (lo + hi);
+            if (qn == q) break;
             q = qn;
         }
     }
@@ -1357,7 +1361,7 @@ static void dem_pair(orc_t* o, int i, int j, double dt, double Fi[3], double Ti[
     int n1 = dem_internal(o, j, oj, c1, k1);
     double xc0[3], xc1[3], nrm[3], xcp[3];
     double* xm = o->dxm + 3 * pr;
-    double delta = dem_pair_geom(c0, k0, n0, c1, k1, n1, o->dRs[i], o->dRs[j], o->dact[pr], xm, xc0, xc1,
+    double delta = dem_pair_geom(c0, k0, n0, c1, k1, n1, o->dRs[i], o->dRs[j], o->dact[pr] != 0, xm, xc0, xc1,
                                  nrm, xcp);
     double* xi = o->dxi + 3 * pr;
     if (!(delta > 0.0)) {
@@ -1394,7 +1398,7 @@ static void dem_wall(orc_t* o, int p, int f, double dt, double Fw[3], double Tw[
     int n = dem_internal(o, p, sp, cbuf, kbuf);
     double xcw[3], nrm[3], xcp[3];
     double* xm = o->dxmw + 3 * wi;
-    double delta = dem_wall_geom(cbuf, kbuf, n, a, side, L, o->dRs[p], o->dactw[wi], xm, xcw, nrm, xcp);
+    double delta = dem_wall_geom(cbuf, kbuf, n, a, side, L, o->dRs[p], o->dactw[wi] != 0, xm, xcw, nrm, xcp);
     double* xi = o->dxiw + 3 * wi;
     if (!(delta > 0.0)) {
         o->dactw[wi] = 0;

@@ -228,9 +228,11 @@ float bound_radius(const float4* body, int c0, int c1) {
   return (float)(hi * (1.0 + 1e-6) + 1e-4);
 }
 
-// Free-DEM buffers of P particles: binary64 words (dem_args' views, then the mass properties
-// [10 P]), then contact-flag bytes
-size_t dem_doubles(size_t P) { return 104 * P + 15 * P * P; }
+// Free-DEM buffers of P particles: binary64 words (dem_args' views, the mass properties [10 P],
+// then the binary32 reach cache, [P] float4 at an even word offset so that it is 16-byte
+// aligned), then contact-flag bytes
+size_t dem_posf_offset(size_t P) { return (104 * P + 15 * P * P + 1) & ~(size_t)1; }
+size_t dem_doubles(size_t P) { return dem_posf_offset(P) + 2 * P; }
 double* dem_props(const rwmi_ctx* c) { return c->dem_d + 94 * (size_t)c->P + 15 * (size_t)c->P * c->P; }
 size_t dem_bytes(size_t P) { return P * P + 6 * P; }
 
@@ -257,6 +259,7 @@ DemArgs dem_args(const rwmi_ctx* c, int tp) {
   a.pTj = b; b += 3 * PP;
   a.wF = b; b += 18 * P;
   a.wT = b;
+  a.posf = reinterpret_cast<float4*>(c->dem_d + dem_posf_offset(P));   // after the mass properties
   a.act = c->dem_b;
   a.actw = c->dem_b + PP;
   a.Fe = c->demcfg.hydro ? c->acc[tp] : nullptr;
@@ -419,8 +422,7 @@ void enqueue_step(rwmi_ctx* c, bool reduce) {
   auto pose = [&]() {   // particles, bricks and body force of t+1
     phase_begin(c, RWMI_PHASE_POSE);
     if (dem) {   // free DEM from t to t+1 with the fluid force of the LBM update of t
-      launch_dem(dem_args(c, tp), c->demcfg.substeps, c->stream);
-      c->launches += 2 * c->demcfg.substeps;
+      c->launches += launch_dem(dem_args(c, tp), c->demcfg.substeps, c->stream);
     }
     launch_clear_u32(c->bword[tn], c->nbrick + BWORD_EXTRA, c->stream);
     c->launches++;
@@ -884,6 +886,7 @@ RWMI_API rwmi_status rwmi_set_particle_state(rwmi_ctx* c, const double* state) {
   for (size_t m = 0; m < (size_t)13 * c->P; ++m)
     if (!std::isfinite(state[m])) return fail(c, RWMI_E_INVALID, "rwmi_set_particle_state: non-finite value");
   CK(copy_now(c, c->dem_d, state, sizeof(double) * 13 * (size_t)c->P));
+  launch_dem_init(dem_args(c, (int)(c->t & 1)), c->stream);   // zoom (unchanged) and reach cache
   rwmi_status r = build_current_frame(c);
   if (r != RWMI_OK) return r;
   CK(cudaStreamSynchronize(c->stream));

@@ -7,7 +7,8 @@
 // switched off the trajectories then follow the CPU oracle's bit for bit, which the GPU tests
 // check; the formulas and their readings are the oracle's.
 //
-// One DEM step is two launches:
+// One DEM step is two launches (or, for up to 128 particles, every DEM step of an LBM step is one
+// single-block launch, dem_fused_kernel, with block barriers between the two phases):
 //   dem_contacts_kernel   one thread per pair slot (i < j) and per wall slot (particle, face):
 //                         reach test, Newton-Raphson geometry, force law; writes the slot's
 //                         force and torques (zero when apart) and its spring and Newton point;
@@ -20,8 +21,8 @@
 namespace rwmi {
 namespace {
 
-constexpr int NEWTON_NEW = 24;        // Newton iterations of a new contact
-constexpr int NEWTON_CONT = 6;        // ... of a contact kept from the previous DEM step
+constexpr int NEWTON_NEW = 24;        // Newton iterations (at most) from the deterministic start
+constexpr int NEWTON_CONT = 6;        // ... from the previous DEM step's point (pair within reach then)
 constexpr int SURFACE_ITERS = 24;     // bracketed Newton iterations for Eq. 8's q
 constexpr int SURFACE_HALVINGS = 16;  // halvings of the first-order q looking for an inside point
 
@@ -92,7 +93,7 @@ __device__ bool solve3(const double A[3][3], const double b[3], double d[3]) {
   return true;
 }
 
-// Newton step, at most one lattice unit long; false when singular
+// Newton step, at most one lattice unit long; false when singular or converged (step < 1e-12)
 __device__ bool newton_update(const double A[3][3], const double G[3], double x[3]) {
   const double b[3] = {-G[0], -G[1], -G[2]};
   double d[3];
@@ -100,7 +101,7 @@ __device__ bool newton_update(const double A[3][3], const double G[3], double x[
   const double len = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
   const double sc = len > 1.0 ? 1.0 / len : 1.0;
   for (int e = 0; e < 3; ++e) x[e] += sc * d[e];
-  return true;
+  return len > 1e-12;
 }
 
 // Eq. 8: x_c = x_m + q grad f(x_m) with f(x_c) = 1, the crossing nearest to x_m (first-order
@@ -126,6 +127,7 @@ __device__ void surface_along(const double* c, const double* k, int n, const dou
       const double dq = gx[0] * g[0] + gx[1] * g[1] + gx[2] * g[2];
       double qn = fabs(dq) > 1e-300 ? q - (fx - 1.0) / dq : 0.5 * (lo + hi);
       if (!(qn > lo && qn < hi)) qn = 0.5 * (lo + hi);
+      if (qn == q) break;
       q = qn;
     }
   }
@@ -252,6 +254,21 @@ __device__ void pair_slot(const DemArgs& a, int i, int j) {
   double* Ti = a.pTi + 3 * pr;
   double* Tj = a.pTj + 3 * pr;
   double* xi = a.xi + 3 * pr;
+  {   // binary32 reach prefilter: bound spheres apart by more than a margin cannot touch
+    const float4 pi = a.posf[i], pj = a.posf[j];
+    const float dv[3] = {pj.x - pi.x, pj.y - pi.y, pj.z - pi.z};
+    float d2 = 0.0f;
+    for (int e = 0; e < 3; ++e) {
+      float dd = dv[e];
+      if (!a.wall[e]) dd -= (float)a.n[e] * rintf(dd / (float)a.n[e]);
+      d2 += dd * dd;
+    }
+    const float reach = pi.w + pj.w + 0.01f;
+    if (d2 > reach * reach) {   // the slot's forces are read only while in contact
+      if (a.act[pr]) { a.act[pr] = 0; clear3(xi); }
+      return;
+    }
+  }
   clear3(F); clear3(Ti); clear3(Tj);
   const double* si = a.st + 13 * i;
   const double* sj = a.st + 13 * j;
@@ -299,6 +316,15 @@ __device__ void wall_slot(const DemArgs& a, int p, int f) {
   double* F = a.wF + 3 * wi;
   double* T = a.wT + 3 * wi;
   double* xi = a.xiw + 3 * wi;
+  {   // binary32 reach prefilter
+    const float4 pf = a.posf[p];
+    const float c = ax == 0 ? pf.x : ax == 1 ? pf.y : pf.z;
+    const float gapf = side ? (float)a.n[ax] - c : c;
+    if (!a.wall[ax] || gapf > pf.w + 0.01f) {
+      if (a.actw[wi]) { a.actw[wi] = 0; clear3(xi); }
+      return;
+    }
+  }
   clear3(F); clear3(T);
   const double* sp = a.st + 13 * p;
   const double L = (double)a.n[ax];
@@ -341,25 +367,57 @@ __global__ void __launch_bounds__(64) dem_contacts_kernel(DemArgs a, int npairs)
   }
 }
 
+__device__ void integrate_particle(const DemArgs& a, int p);
+
 __global__ void dem_integrate_kernel(DemArgs a) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= a.P) return;
+  if (p < a.P) integrate_particle(a, p);
+}
+
+// Every DEM step of one LBM step in one block: contact slots, a block barrier, integration, a
+// block barrier. For small particle counts, where launch latency would dominate.
+constexpr int DEM_FUSED_THREADS = 512;
+constexpr int DEM_FUSED_MAX_P = 128;
+__global__ void __launch_bounds__(DEM_FUSED_THREADS, 1) dem_fused_kernel(DemArgs a, int npairs, int substeps) {
+  const int slots = npairs + 6 * a.P;
+  for (int s = 0; s < substeps; ++s) {
+    for (int k = threadIdx.x; k < slots; k += blockDim.x) {
+      if (k < npairs) {
+        int i = 0, rem = k;
+        while (rem >= a.P - 1 - i) { rem -= a.P - 1 - i; ++i; }
+        pair_slot(a, i, i + 1 + rem);
+      } else {
+        const int w = k - npairs;
+        wall_slot(a, w / 6, w % 6);
+      }
+    }
+    __syncthreads();
+    for (int p = threadIdx.x; p < a.P; p += blockDim.x) integrate_particle(a, p);
+    __syncthreads();
+  }
+}
+
+__device__ void integrate_particle(const DemArgs& a, int p) {
   const int P = a.P;
   double F[3] = {0.0, 0.0, 0.0}, T[3] = {0.0, 0.0, 0.0};
+  // slots not in contact hold no force: adding their zeros would change no bit, so they are skipped
   for (int j = 0; j < P; ++j) {
     if (j < p) {
       const size_t pr = (size_t)j * P + p;
-      for (int e = 0; e < 3; ++e) { F[e] = F[e] - a.pF[3 * pr + e]; T[e] = T[e] + a.pTj[3 * pr + e]; }
+      if (a.act[pr])
+        for (int e = 0; e < 3; ++e) { F[e] = F[e] - a.pF[3 * pr + e]; T[e] = T[e] + a.pTj[3 * pr + e]; }
     } else if (j > p) {
       const size_t pr = (size_t)p * P + j;
-      for (int e = 0; e < 3; ++e) { F[e] = F[e] + a.pF[3 * pr + e]; T[e] = T[e] + a.pTi[3 * pr + e]; }
+      if (a.act[pr])
+        for (int e = 0; e < 3; ++e) { F[e] = F[e] + a.pF[3 * pr + e]; T[e] = T[e] + a.pTi[3 * pr + e]; }
     }
   }
   for (int f = 0; f < 6; ++f)
-    for (int e = 0; e < 3; ++e) {
-      F[e] = F[e] + a.wF[3 * (6 * (size_t)p + f) + e];
-      T[e] = T[e] + a.wT[3 * (6 * (size_t)p + f) + e];
-    }
+    if (a.actw[6 * (size_t)p + f])
+      for (int e = 0; e < 3; ++e) {
+        F[e] = F[e] + a.wF[3 * (6 * (size_t)p + f) + e];
+        T[e] = T[e] + a.wT[3 * (6 * (size_t)p + f) + e];
+      }
   const double m = a.mass[p];
   for (int e = 0; e < 3; ++e) {
     if (a.Fe) { F[e] = F[e] + a.Fe[6 * p + e]; T[e] = T[e] + a.Fe[6 * p + 3 + e]; }
@@ -400,6 +458,7 @@ __global__ void dem_integrate_kernel(DemArgs a) {
                         qv[2] + h * (qw * w[2] + wxq[2])};
   const double nn = sqrt(nq[0] * nq[0] + nq[1] * nq[1] + nq[2] * nq[2] + nq[3] * nq[3]);
   for (int e = 0; e < 4; ++e) q[e] = nq[e] / nn;
+  a.posf[p] = make_float4((float)st[0], (float)st[1], (float)st[2], a.desc[p].rb);
 }
 
 // zoom s_p = 1 - R_s,p / R_c,p with R_c,p = max_i (|c_i| + sqrt(k_i)) over the body frame
@@ -414,6 +473,8 @@ __global__ void dem_init_kernel(DemArgs a) {
     if (e > r) r = e;
   }
   a.zoom[p] = 1.0 - a.Rs[p] / r;
+  const double* st = a.st + 13 * p;
+  a.posf[p] = make_float4((float)st[0], (float)st[1], (float)st[2], a.desc[p].rb);
 }
 
 // Mass properties from the metaball: body-frame sample points (i + 1/2) h, h = 1/4, out to the
@@ -503,15 +564,20 @@ void launch_dem_init(const DemArgs& a, cudaStream_t st) {
   if (a.P > 0) dem_init_kernel<<<(unsigned)((a.P + 127) / 128), 128, 0, st>>>(a);
 }
 
-void launch_dem(const DemArgs& a, int substeps, cudaStream_t st) {
-  if (a.P <= 0) return;
+int launch_dem(const DemArgs& a, int substeps, cudaStream_t st) {
+  if (a.P <= 0) return 0;
   const int npairs = a.P * (a.P - 1) / 2;
+  if (a.P <= DEM_FUSED_MAX_P) {   // one block takes every step
+    dem_fused_kernel<<<1, DEM_FUSED_THREADS, 0, st>>>(a, npairs, substeps);
+    return 1;
+  }
   const int slots = npairs + 6 * a.P;
   const unsigned cblocks = (unsigned)((slots + 63) / 64), iblocks = (unsigned)((a.P + 127) / 128);
   for (int s = 0; s < substeps; ++s) {
     dem_contacts_kernel<<<cblocks, 64, 0, st>>>(a, npairs);
     dem_integrate_kernel<<<iblocks, 128, 0, st>>>(a);
   }
+  return 2 * substeps;
 }
 
 }  // namespace rwmi

@@ -245,17 +245,20 @@ struct DemArgs {
   const double *mass, *Ib, *Rs;                // [P], [6 P], [P]
   double* zoom;                                // [P] internal-metaball scale
   double *xi, *xm;                             // pairs [3 P P]
-  unsigned char* act;                          // pairs [P P]
+  unsigned char* act;                          // pairs [P P]: in contact at the last DEM step
   double *xiw, *xmw;                           // walls [18 P]
   unsigned char* actw;                         // walls [6 P]
   double *pF, *pTi, *pTj;                      // pair force on i, torques on i and j [3 P P]
   double *wF, *wT;                             // wall force and torque [18 P]
+  float4* posf;                                // [P] origin in binary32 and bound radius: reach
+                                               // prefilter (conservative, with a margin)
   const double* Fe;                            // fluid force and torque [6 P], or nullptr
   double kn, etan, kt, etat, mus, g[3];
   double dt;                                   // 1 / substeps
 };
-// substeps DEM steps: two launches each (contacts, then integration)
-void launch_dem(const DemArgs& a, int substeps, cudaStream_t st);
+// substeps DEM steps: one single-block launch for up to 128 particles, else two launches per DEM
+// step (contacts, then integration); returns the number of launches
+int launch_dem(const DemArgs& a, int substeps, cudaStream_t st);
 // the zoom factors from the sphere radii (rwmi_set_dem)
 void launch_dem_init(const DemArgs& a, cudaStream_t st);
 // mass properties from the metaballs at the given densities: integer sample sums (zeroed by the
