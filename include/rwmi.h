@@ -175,8 +175,9 @@ RWMI_API void rwmi_dem_defaults(rwmi_dem_config* cfg);
  * frame is then moved to the centre of mass (control points c_i - c_m in binary32), so the
  * state's origin is the centre of mass. The state starts at the prescribed origin of the
  * current time (plus c_m) with the body frame as given. Requires 0 < R_s < max |c_i - c_m| +
- * sqrt(k_i), partially saturated cells (coupling 0), binary32-shifted or binary64 storage, and
- * at most 16 control points per particle; every step then forms the fluid force in the LBM
+ * sqrt(k_i), binary32-shifted or binary64 storage, and at most 16 control points per particle;
+ * either coupling (with IBB the node classes of t - 1 are those of the previous step, and at the
+ * first step of the free run those of t). Every step then forms the fluid force in the LBM
  * update itself (one fused pass). RWMI_E_INVALID otherwise (context unchanged), RWMI_E_STATE if
  * the particles are free already. Before the first step. */
 RWMI_API rwmi_status rwmi_set_dem(rwmi_ctx* ctx, const rwmi_dem_config* cfg, const double* density,

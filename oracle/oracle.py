@@ -94,6 +94,7 @@ def lib():
             L.orc_dem_pair_geom.argtypes = [P, C.c_int, C.c_int, C.c_void_p]
             L.orc_dem_wall_geom.argtypes = [P, C.c_int, C.c_int, C.c_void_p]
             L.orc_dem_advance.argtypes = [P, C.c_longlong]
+            L.orc_set_prev_nodes.argtypes = [P, C.c_longlong, C.c_void_p]
             L.orc_ibb_link.restype = C.c_double
             L.orc_ibb_link.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, dp, dp, dp, C.c_double]
             _lib = L
@@ -232,6 +233,11 @@ class Oracle:
         out = np.zeros(13)
         lib().orc_dem_wall_geom(self.h, int(p), int(face), _ptr(out))
         return dict(xcm=out[0:3], xcw=out[3:6], n=out[6:9], delta=float(out[9]), xcp=out[10:13])
+
+    def set_prev_nodes(self, t_prev, nodes):
+        """IBB with the free DEM: node classes of t_prev, refilled from at the step t_prev + 1."""
+        nodes = np.ascontiguousarray(nodes, np.int32).reshape(self.n_cells)
+        lib().orc_set_prev_nodes(self.h, int(t_prev), _ptr(nodes))
 
     def dem_advance(self, n=1):
         """n LBM steps' worth of DEM steps, fluid and walkers frozen."""

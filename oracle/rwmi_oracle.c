@@ -141,6 +141,8 @@ typedef struct {
     double* dst;             /* [13 P] origin (unwrapped), quaternion (w, x, y, z), velocity, spin */
     double *dmass, *dIb, *dRs, *dzoom;   /* [P], [6 P] body inertia (xx yy zz xy xz yz), [P], [P] */
     double* dcm;             /* [10 P] mass properties (orc_dem_mass) */
+    int* dem_nodes;          /* IBB node classes of the last LBM step (free DEM) */
+    long long dem_nodes_t;
     double *dxi, *dxm;       /* pairs (i < j) at i P + j: tangential spring, Newton point [3 each] */
     unsigned char* dact;     /* pair in contact at the last DEM step */
     double *dxiw, *dxmw;     /* walls: particle p, face f (2 axis + side) at 6 p + f */
@@ -661,8 +663,13 @@ static void ibb_step(orc_t* o, long long t)
     int* ncur = (int*)malloc(sizeof(int) * (size_t)n);
     double* uprev = (double*)malloc(sizeof(double) * 3 * (size_t)n);
     memcpy(uprev, o->u, sizeof(double) * 3 * (size_t)n);
-    classify_nodes(o, t - 1, nprev);
     classify_nodes(o, t, ncur);
+    /* With the free DEM only the current particle state exists: the classes of t - 1 are those
+     * this step stored at the previous time, and at the first step of a run the classes of t
+     * (nothing is refilled then). */
+    if (!o->dem) classify_nodes(o, t - 1, nprev);
+    else if (o->dem_nodes_t == t - 1) memcpy(nprev, o->dem_nodes, sizeof(int) * (size_t)n);
+    else memcpy(nprev, ncur, sizeof(int) * (size_t)n);
     frame_t fr;
     frame_alloc(o, &fr);
     frame_at(o, t, &fr);
@@ -754,6 +761,11 @@ static void ibb_step(orc_t* o, long long t)
     o->fn = tmp;
     frame_free(&fr);
     free(nprev);
+    if (o->dem) {   /* the classes of t, for the next step */
+        if (!o->dem_nodes) o->dem_nodes = (int*)malloc(sizeof(int) * (size_t)n);
+        memcpy(o->dem_nodes, ncur, sizeof(int) * (size_t)n);
+        o->dem_nodes_t = t;
+    }
     free(ncur);
     free(uprev);
 }
@@ -1551,7 +1563,7 @@ ORC_API void orc_destroy(void* h)
     free(o->coff); free(o->cbody); free(o->kc); free(o->kc32);
     free(o->org); free(o->amp); free(o->per); free(o->pha); free(o->omg); free(o->Rb);
     free(o->Fp); free(o->Tp); free(o->x); free(o->x0);
-    free(o->dst); free(o->dmass); free(o->dIb); free(o->dRs); free(o->dzoom); free(o->dcm);
+    free(o->dst); free(o->dmass); free(o->dIb); free(o->dRs); free(o->dzoom); free(o->dcm); free(o->dem_nodes);
     free(o->dxi); free(o->dxm); free(o->dact); free(o->dxiw); free(o->dxmw); free(o->dactw);
     free(o);
 }
@@ -2022,7 +2034,7 @@ ORC_API int orc_set_dem(void* h, double kn, double etan, double kt, double etat,
 {
     orc_t* o = (orc_t*)h;
     int P = o->P;
-    if (o->coupling != 0 || nsub < 1 || P < 1 || kn < 0.0 || etan < 0.0 || kt < 0.0 || etat < 0.0 || mus < 0.0)
+    if (nsub < 1 || P < 1 || kn < 0.0 || etan < 0.0 || kt < 0.0 || etat < 0.0 || mus < 0.0)
         return -1;
     for (int p = 0; p < P; ++p)
         if (!(density[p] > 0.0) || !(Rs[p] > 0.0)) return -1;
@@ -2074,6 +2086,7 @@ ORC_API int orc_set_dem(void* h, double kn, double etan, double kt, double etat,
         o->dzoom[p] = 1.0 - Rs[p] / dem_reach(o, p);
     }
     o->dem = 1;
+    o->dem_nodes_t = -2;
     o->solid_time = -1;
     return 0;
 }
@@ -2137,4 +2150,14 @@ ORC_API void orc_dem_advance(void* h, long long nsteps)
 {
     orc_t* o = (orc_t*)h;
     for (long long s = 0; s < nsteps; ++s) dem_advance(o);
+}
+
+/* IBB with the free DEM: the node classes of time t_prev (0 fluid, 1 + particle), which the
+ * step at t_prev + 1 refills from */
+ORC_API void orc_set_prev_nodes(void* h, long long t_prev, const int* nodes)
+{
+    orc_t* o = (orc_t*)h;
+    if (!o->dem_nodes) o->dem_nodes = (int*)malloc(sizeof(int) * (size_t)o->ncell);
+    memcpy(o->dem_nodes, nodes, sizeof(int) * (size_t)o->ncell);
+    o->dem_nodes_t = t_prev;
 }

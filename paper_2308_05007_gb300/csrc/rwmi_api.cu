@@ -670,8 +670,8 @@ RWMI_API rwmi_status rwmi_configure(rwmi_ctx* c, const rwmi_config* cfg) {
   for (int a = 0; a < 3; ++a)
     if (!std::isfinite(cfg->body_force[a]) || !std::isfinite(cfg->init_velocity[a]))
       return fail(c, RWMI_E_INVALID, "rwmi_configure: non-finite force or velocity");
-  if (c->dem && (cfg->coupling != 0 || (cfg->storage != RWMI_STORE_FP32_SHIFT && cfg->storage != RWMI_STORE_FP64_SHIFT)))
-    return fail(c, RWMI_E_INVALID, "rwmi_configure: the free DEM needs coupling 0 and storage 1 or 3");
+  if (c->dem && cfg->storage != RWMI_STORE_FP32_SHIFT && cfg->storage != RWMI_STORE_FP64_SHIFT)
+    return fail(c, RWMI_E_INVALID, "rwmi_configure: the free DEM needs storage 1 or 3");
   const bool realloc_f = cfg->q != c->cfg.q || cfg->storage != c->cfg.storage;
   c->cfg = *cfg;
   update_margin(c);
@@ -776,8 +776,8 @@ RWMI_API rwmi_status rwmi_set_dem(rwmi_ctx* c, const rwmi_dem_config* cfg, const
   if (!c || !cfg) return RWMI_E_INVALID;
   if (c->P < 1 || !density || !Rs) return fail(c, RWMI_E_INVALID, "rwmi_set_dem: no particles or null array");
   if (c->dem) return fail(c, RWMI_E_STATE, "rwmi_set_dem: the particles are free already");
-  if (c->cfg.coupling != 0 || (c->cfg.storage != RWMI_STORE_FP32_SHIFT && c->cfg.storage != RWMI_STORE_FP64_SHIFT))
-    return fail(c, RWMI_E_INVALID, "rwmi_set_dem: needs coupling 0 and storage 1 or 3");
+  if (c->cfg.storage != RWMI_STORE_FP32_SHIFT && c->cfg.storage != RWMI_STORE_FP64_SHIFT)
+    return fail(c, RWMI_E_INVALID, "rwmi_set_dem: needs storage 1 or 3");
   if (!(cfg->kn >= 0.0) || !(cfg->eta_n >= 0.0) || !(cfg->kt >= 0.0) || !(cfg->eta_t >= 0.0) || !(cfg->mu_s >= 0.0) ||
       !std::isfinite(cfg->kn + cfg->eta_n + cfg->kt + cfg->eta_t + cfg->mu_s) || cfg->substeps < 1 ||
       cfg->substeps > 100000 || (cfg->hydro != 0 && cfg->hydro != 1))

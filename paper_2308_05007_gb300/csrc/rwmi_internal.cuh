@@ -227,7 +227,7 @@ struct IbbArgs {
   const ParticleDesc* desc = nullptr;
 };
 // fused: the update and the reduction in one pass (free-DEM runs, which read the forces every
-// step; binary32-shifted and binary64 storage, partially saturated cells)
+// step; binary32-shifted and binary64 storage)
 void launch_lbm(int q, int storage, bool reduce, const Geom& g, const void* fin, void* fout,
                 float* u, const uint16_t* solid, BrickSet bs, double tau, double rho0,
                 double* red, double* forces, unsigned long long* status, cudaStream_t st,

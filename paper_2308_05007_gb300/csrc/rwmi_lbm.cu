@@ -427,7 +427,7 @@ static void launch_lbm_q(bool walls, bool reduce, const Geom& g, const void* fin
   const int bsz_ok = (bsz == 64 || bsz == 128) ? bsz : 256;
   const dim3 grid((g.ncell + bsz_ok - 1) / bsz_ok), block(bsz_ok);
 #define RWMI_LBM_ARGS g, pl, u4, solid, bs.bword, bs.pose, bs.posed, bs.sp, (R)tau, (R)rho0, red, forces, ib.nodes, ib.uprev, ib.desc, bs.cworld
-  if constexpr ((STORE == 1 || STORE == 3) && !IBB) {   // the fused mode of free-DEM runs
+  if constexpr (STORE == 1 || STORE == 3) {   // the fused mode of free-DEM runs
     if (fused) {
       if (walls) lbm_kernel<Q, STORE, true, 2, IBB><<<grid, block, 0, st>>>(RWMI_LBM_ARGS);
       else lbm_kernel<Q, STORE, false, 2, IBB><<<grid, block, 0, st>>>(RWMI_LBM_ARGS);
@@ -457,7 +457,7 @@ void launch_lbm(int q, int storage, bool reduce, const Geom& g, const void* fin,
 #define RWMI_LBM_PSM(QQ, SS) \
   launch_lbm_q<QQ, SS, false>(walls, reduce, g, fin, fout, u, solid, bs, tau, rho0, red, forces, st, block, ib, fused)
 #define RWMI_LBM_CASE(QQ, SS)                                                                           \
-  if (ibb) launch_lbm_q<QQ, SS, true>(walls, reduce, g, fin, fout, u, solid, bs, tau, rho0, red, forces, st, block, ib, false); \
+  if (ibb) launch_lbm_q<QQ, SS, true>(walls, reduce, g, fin, fout, u, solid, bs, tau, rho0, red, forces, st, block, ib, fused); \
   else RWMI_LBM_PSM(QQ, SS)
   if (q == 15) {
     if (storage == 0) { RWMI_LBM_PSM(15, 0); }

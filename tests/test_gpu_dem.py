@@ -8,7 +8,9 @@
   the oracle. The particles' new velocities differ only through the hydrodynamic force, which
   the GPU forms in binary32 (relative 1e-4 of the force, times dt / m).
 - The three schedules, graph replay and a checkpoint restart give identical results.
-- Set-ups the library cannot run (IBB coupling, binary16 storage) are refused.
+- With the paper's IBB coupling: one coupled step against the oracle (given the previous step's
+  node classes), and identical schedules and graphs.
+- Set-ups the library cannot run (binary16 or unshifted binary32 storage) are refused.
 """
 import os
 
@@ -164,7 +166,75 @@ def test_schedules_graphs_and_restart_agree(tmp_path):
 
 def test_refused_setups():
     from paper_2308_05007_gb300.rwmi import RwmiError, Simulation
-    for kw in (dict(coupling=1), dict(storage=2)):
+    for kw in (dict(storage=2), dict(storage=0)):
         w = I.with_(_converging(), **kw)
         with pytest.raises(RwmiError):
             Simulation.from_workload(w, seed_walkers=False)
+
+
+@pytest.mark.parametrize("storage", [1, 3])
+def test_ibb_coupled_step_from_identical_state(storage):
+    """The paper's own pairing: free particles with interpolated bounce-back, momentum exchange
+    and refilling (Section 2.4.3). One step from the GPU's state against the oracle, which is
+    given the same populations, velocity (u_f, u_ff of Eq. 24), particle state and node classes
+    of the previous step; the forces and the new particle state agree within the LBM update's
+    precision (binary64 storage: 1e-9 of the force)."""
+    from paper_2308_05007_gb300.rwmi import Simulation
+    from oracle.oracle import lattice
+    w = I.dem_box(n_particles=3, seed=4, speed=0.0, gravity=(0.0, 0.0, -2e-4), hydro=1, n_walkers=0,
+                  storage=storage)
+    w = I.with_(w, body_force=(3e-5, 0.0, 0.0), coupling=1)
+    w.dem.velocity[:] = 0.0
+    w.dem.spin[:] = 0.0
+    with Simulation.from_workload(w, seed_walkers=False) as sim:
+        eg, _ = sim.lattice()
+        eo, _ = lattice(w.q)
+        perm = np.array([int(np.where((eg == eo[i]).all(1))[0][0]) for i in range(w.q)])
+        sim.step(11)
+        nodes_prev = sim.nodes()
+        sim.step(1)
+        t = sim.t
+        f0 = sim.populations()[perm]
+        u0 = sim.velocity().astype(np.float64)
+        st0 = sim.particle_state()
+        sim.step(1)
+        st1 = sim.particle_state()
+        Fg = sim.particle_forces()
+        mp = sim.particle_mass()
+    ora = Oracle.from_workload(w, seed_walkers=False)
+    ora.set_populations(f0)
+    ora.set_velocity(u0)
+    ora.set_time(t)
+    ora.set_particle_state(st0)
+    ora.set_prev_nodes(t - 1, nodes_prev)
+    ora.step_fluid(1)
+    Fo = ora.forces()
+    so = ora.particle_state()
+    assert np.abs(Fo[:, :3]).max() > 1e-4
+    rel = 1e-9 if storage == 3 else 2e-4
+    tolF = rel * np.abs(Fo[:, :3]).max()
+    radius = (3.0 * mp[:, 0].max() / (4.0 * np.pi * w.dem.density)) ** (1.0 / 3.0) + 2.0
+    tolT = tolF * radius
+    np.testing.assert_allclose(Fg[:, :3], Fo[:, :3], rtol=0, atol=tolF)
+    np.testing.assert_allclose(Fg[:, 3:], Fo[:, 3:], rtol=0, atol=tolT)
+    dv = tolF / mp[:, 0].min()
+    dw = tolT / mp[:, 4:7].min()
+    assert np.abs(st1[:, 7:10] - so[:, 7:10]).max() <= dv + 1e-15
+    assert np.abs(st1[:, :3] - so[:, :3]).max() <= dv + 1e-12
+    assert np.abs(st1[:, 10:13] - so[:, 10:13]).max() <= dw + 1e-15
+
+
+def test_ibb_schedules_and_graphs_agree():
+    from paper_2308_05007_gb300.rwmi import Simulation
+    w = I.with_(_converging(hydro=1), coupling=1)
+    ref = None
+    for overlap in (0, 2):
+        for graphs in (False, True):
+            with Simulation.from_workload(w, overlap=overlap, use_graphs=graphs, sort_interval=4) as s:
+                s.step(20)
+                res = (s.particle_state(), s.populations())
+            if ref is None:
+                ref = res
+            else:
+                for a, b in zip(ref, res):
+                    assert np.array_equal(a, b), (overlap, graphs)
