@@ -328,6 +328,25 @@ def measure_variants(a, stream):
         "dem_and_poses_ms": ph["pose_bricks"] / 16, "substeps": w.dem.substeps,
         "step_ms": step_ms, "mlups": w.n_cells / (step_ms / 1e3) / 1e6,
         "max_particle_speed": float(np.linalg.norm(st[:, 7:10], axis=1).max())}
+    # the paper's own pairing: free particles with IBB, momentum exchange and refilling
+    wi = I.with_(w, coupling=1)
+    sim = Simulation.from_workload(wi, seed_walkers=False)
+    sim.set_stream(stream)
+    sim.seed_walkers(wi.n_walkers, *wi.walker_box)
+    sim.step(16)
+    ph = sim.step_timed(8)
+    sim.step(8)
+    with torch.cuda.stream(stream):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.step(32)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    step_ms = e0.elapsed_time(e1) / 32
+    sim.close()
+    out["D3Q15_fp32_shift_ibb_dem"] = {
+        "lbm_ms": ph["lbm"] / 8, "dem_and_poses_ms": ph["pose_bricks"] / 8, "step_ms": step_ms,
+        "mlups": wi.n_cells / (step_ms / 1e3) / 1e6}
     return out
 
 

@@ -162,6 +162,11 @@ def test_schedules_graphs_and_restart_agree(tmp_path):
         got = (s.particle_state(), s.populations())
     for a, b in zip(want, got):
         assert np.array_equal(a, b)
+    # a free-DEM checkpoint does not load into a context with prescribed motion
+    from paper_2308_05007_gb300.rwmi import RwmiError
+    with Simulation.from_workload(I.with_(w, dem=None), sort_interval=4) as s:
+        with pytest.raises(RwmiError):
+            s.load(path)
 
 
 def test_refused_setups():
