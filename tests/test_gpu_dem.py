@@ -75,6 +75,26 @@ def test_trajectories_bit_exact_without_fluid_force():
     assert touched, "no contact happened"
 
 
+def test_many_particles_take_the_two_launch_path_bit_exactly():
+    """More than 128 particles: two launches per DEM step instead of one block; the same slot and
+    integration code, so still bit-identical to the oracle (fluid force off), contacts included."""
+    from paper_2308_05007_gb300.rwmi import Simulation
+    w = I.dem_box(dims=(96, 96, 96), n_particles=130, seed=21, hydro=0, n_walkers=0, speed=0.12)
+    o = w.metaballs.origin
+    aim = o.mean(0) - o
+    w.dem.velocity[:] = 0.12 * aim / np.linalg.norm(aim, axis=1, keepdims=True)
+    ora = Oracle.from_workload(w, seed_walkers=False)
+    with Simulation.from_workload(w, seed_walkers=False) as sim:
+        g0 = sim.particle_state()
+        np.testing.assert_array_equal(g0, ora.particle_state())
+        sim.step(140)
+        ora.dem_advance(140)
+        st = sim.particle_state()
+    np.testing.assert_array_equal(st, ora.particle_state())
+    free = g0[:, 7:10] + 140 * np.asarray(w.dem.gravity)
+    assert (np.abs(st[:, 7:10] - free).max(1) > 1e-6).sum() > 10, "too few contacts"
+
+
 def test_solid_fraction_follows_the_dem_state():
     """The raster of a free-DEM run uses the particle state: bit-exact against the oracle's
     rasteriser fed the same state."""
