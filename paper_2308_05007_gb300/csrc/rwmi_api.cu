@@ -56,6 +56,7 @@ struct rwmi_ctx {
   float* u[2] = {nullptr, nullptr};   // (u, rho) per time parity: the LBM of t writes u[t & 1]
   uint16_t* solid[2] = {nullptr, nullptr};   // per time parity: raster of t+1 beside the LBM of t
   uint16_t* node[2] = {nullptr, nullptr};    // IBB node classes per time parity (0 fluid, 1 + particle)
+  IbbLinks ibl;                              // IBB link list (allocated with coupling 1)
   int64_t* d_T = nullptr;
   unsigned long long* status = nullptr;
   double* acc[2] = {nullptr, nullptr};   // per time parity: forces [6P] + mass/momentum [4]
@@ -442,6 +443,12 @@ void enqueue_step(rwmi_ctx* c, bool reduce) {
       ia.nodes = c->node[tp];
       ia.uprev = reinterpret_cast<const float4*>(c->u[tn]);
       ia.desc = c->desc;
+      launch_ibb_links(c->cfg.q, c->g, brick_set(c, tp), c->node[tp], c->ibl, tp, c->desc, c->status, c->nsm,
+                       c->stream);
+      c->launches += 2;
+      ia.base = c->ibl.base;
+      ia.q = c->ibl.q;
+      ia.cap = c->ibl.cap;
     }
     launch_lbm(c->cfg.q, c->cfg.storage, reduce, c->g, c->f[c->fcur], c->f[c->fcur ^ 1], c->u[tp], c->solid[tp],
                brick_set(c, tp), c->tau, c->cfg.rho0, c->acc[tp] + 6 * c->P, c->acc[tp],
@@ -682,6 +689,15 @@ RWMI_API rwmi_status rwmi_configure(rwmi_ctx* c, const rwmi_config* cfg) {
     if (s != RWMI_OK) return s;
   }
   c->fcur = 0;
+  if (cfg->coupling == 1 && !c->ibl.base) {   // IBB link list: half a link per cell (2^20 at least)
+    c->ibl.cap = (int)std::min<int64_t>(std::max<int64_t>(c->ncell / 2, 1 << 20), 0x7fffffff);
+    CK(dalloc(c, &c->ibl.base, sizeof(int32_t) * (size_t)c->ncell));
+    CK(dalloc(c, &c->ibl.cell, sizeof(uint32_t) * (size_t)c->ibl.cap));
+    CK(dalloc(c, &c->ibl.meta, sizeof(uint32_t) * (size_t)c->ibl.cap));
+    CK(dalloc(c, &c->ibl.q, sizeof(float) * (size_t)c->ibl.cap));
+    CK(dalloc(c, &c->ibl.count, sizeof(unsigned int) * 2));
+  }
+  if (c->ibl.count) CK(cudaMemsetAsync(c->ibl.count, 0, sizeof(unsigned int) * 2, c->stream));
   rwmi_status s = reset_fluid(c);
   if (s != RWMI_OK) return s;
   s = build_current_frame(c);
@@ -1029,6 +1045,12 @@ RWMI_API rwmi_status rwmi_autotune(rwmi_ctx* c, int32_t* chosen) {
     ia.nodes = c->node[tp];
     ia.uprev = reinterpret_cast<const float4*>(c->u[tp ^ 1]);
     ia.desc = c->desc;
+    launch_ibb_links(c->cfg.q, c->g, brick_set(c, tp), c->node[tp], c->ibl, tp, c->desc, c->status, c->nsm,
+                     c->stream);
+    c->launches += 2;
+    ia.base = c->ibl.base;
+    ia.q = c->ibl.q;
+    ia.cap = c->ibl.cap;
   }
   for (int k = 0; k < 3; ++k) {
     for (int rep = 0; rep < 6; ++rep) {
@@ -1051,6 +1073,7 @@ RWMI_API rwmi_status rwmi_autotune(rwmi_ctx* c, int32_t* chosen) {
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  if (ibb) CK(cudaMemsetAsync(c->ibl.count, 0, sizeof(unsigned int) * 2, c->stream));   // the step appends anew
   CK(cudaGetLastError());
   c->cfg.lbm_block = best;
   drop_graphs(c);
@@ -1376,6 +1399,7 @@ RWMI_API rwmi_status rwmi_load(rwmi_ctx* c, const char* path) {
   CK(copy_now(c, c->d_T, &c->t, sizeof(int64_t)));
   c->t_base = c->t;
   CK(cudaMemsetAsync(c->wlist_n, 0, sizeof(unsigned int) * 2 * WLIST_STRIPES, c->stream));
+  if (c->ibl.count) CK(cudaMemsetAsync(c->ibl.count, 0, sizeof(unsigned int) * 2, c->stream));
   rwmi_status s = build_current_frame(c);
   if (s != RWMI_OK) return s;
   CK(cudaStreamSynchronize(c->stream));
@@ -1539,6 +1563,7 @@ RWMI_API void rwmi_destroy(rwmi_ctx* c) {
   dfree(c, c->series); dfree(c, c->mrow); dfree(c, c->desc); dfree(c, c->cbody); dfree(c, c->rank);
   dfree(c, c->counts); dfree(c, c->offsets); dfree(c, c->bsums); dfree(c, c->scratch); dfree(c, c->wmask[0]); dfree(c, c->wmask[1]);
   dfree(c, c->dem_d); dfree(c, c->dem_b);
+  dfree(c, c->ibl.base); dfree(c, c->ibl.cell); dfree(c, c->ibl.meta); dfree(c, c->ibl.q); dfree(c, c->ibl.count);
   cudaStreamSynchronize(c->stream);   // the frees have returned the memory when this returns
   for (int k = 0; k < 2 * RWMI_NPHASE; ++k)
     if (c->ev[k]) cudaEventDestroy(c->ev[k]);

@@ -38,7 +38,7 @@ constexpr int RED_SLOTS = 256;      // mass/momentum partial sums are striped ov
 enum StatusSlot {
   ST_TYPE1 = 0, ST_TYPE2, ST_TYPE3, ST_TYPE4,
   ST_BISECT_FAIL, ST_REFILL_FAIL, ST_WALL_FAIL, ST_SEED_FAIL,
-  ST_NONFINITE, ST_BRICK_OVERFLOW, ST_FAST_SPEED, ST_RESOLVED, ST_RASTER_QUEUED, ST_COUNT
+  ST_NONFINITE, ST_BRICK_OVERFLOW, ST_FAST_SPEED, ST_RESOLVED, ST_RASTER_QUEUED, ST_IBB_OVERFLOW, ST_COUNT
 };
 
 struct ParticleDesc {
@@ -225,7 +225,22 @@ struct IbbArgs {
   const uint16_t* nodes = nullptr;
   const float4* uprev = nullptr;
   const ParticleDesc* desc = nullptr;
+  const int32_t* base = nullptr;   // per cell: index of its first link in q (ibb links)
+  const float* q = nullptr;        // q of every link (Eq. 25)
+  int cap = 0;                     // capacity of the link list
 };
+// The IBB link list of a context: per cell the index of its first link, per link the cell, the
+// direction | particle << 8, and q; two append counters (time parities).
+struct IbbLinks {
+  int32_t* base = nullptr;
+  uint32_t *cell = nullptr, *meta = nullptr;
+  float* q = nullptr;
+  unsigned int* count = nullptr;
+  int cap = 0;
+};
+// Links of time t (node classes nodes, bricks bs) and their q, before the LBM update of t
+void launch_ibb_links(int q, const Geom& g, BrickSet bs, const uint16_t* nodes, const IbbLinks& lk, int par,
+                      const ParticleDesc* desc, unsigned long long* status, int nsm, cudaStream_t st);
 // fused: the update and the reduction in one pass (free-DEM runs, which read the forces every
 // step; binary32-shifted and binary64 storage)
 void launch_lbm(int q, int storage, bool reduce, const Geom& g, const void* fin, void* fout,

@@ -45,7 +45,7 @@ __device__ __forceinline__ float ibb_link_q(const float4* __restrict__ cw, int c
 // reducing and non-reducing steps agree bit for bit. MODE 2: update and reduction in one pass,
 // for free-DEM runs, which read the forces on every step (so every step runs this one mode).
 template <int Q, int STORE, bool WALLS, int MODE, bool IBB>
-__global__ void __launch_bounds__(256, (sizeof(typename Store<STORE>::R) == 8 || IBB) ? 2 : (Q == 19 ? 5 : 6))
+__global__ void __launch_bounds__(256, sizeof(typename Store<STORE>::R) == 8 ? 2 : IBB ? 4 : (Q == 19 ? 5 : 6))
 lbm_kernel(Geom g, Planes<Q, typename Store<STORE>::T> pl,
                                                   float4* __restrict__ u4,
                                                   const uint16_t* __restrict__ solid,
@@ -59,7 +59,9 @@ lbm_kernel(Geom g, Planes<Q, typename Store<STORE>::T> pl,
                                                   const uint16_t* __restrict__ nodes,
                                                   const float4* __restrict__ uprev,
                                                   const ParticleDesc* __restrict__ desc,
-                                                  const float4* __restrict__ cworld) {
+                                                  const float4* __restrict__ cworld,
+                                                  const int32_t* __restrict__ ib_base,
+                                                  const float* __restrict__ ib_q, int ib_cap) {
   using L = Lat<Q>;
   using S = Store<STORE>;
   using R = typename S::R;   // arithmetic type: binary32, or binary64 for the binary64 storage
@@ -111,11 +113,8 @@ lbm_kernel(Geom g, Planes<Q, typename Store<STORE>::T> pl,
   R Fib[3] = {R(0), R(0), R(0)}, Tib[3] = {R(0), R(0), R(0)};
   int ib_owner = -1;
   if constexpr (IBB) {
-    // link table of the warp: q of every (cell, direction) link, computed one link per lane
-    __shared__ float s_q[8][32 * (Q - 1)];
-    __shared__ int s_link[8][32 * (Q - 1)];   // lane | direction << 5 | particle << 10
-    const unsigned fullm = 0xffffffffu;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    // q of every link (Eq. 25) comes from ibb_q_kernel, which ran before at full occupancy: the
+    // cell's links sit at ib_base[c] in direction order (ibb_links_kernel, same rule as lmask)
     const bool wx_p = WALLS && g.wall[0] && x == 0, wx_m = WALLS && g.wall[0] && (int)x == nx - 1;
     const bool wy_p = WALLS && g.wall[1] && y == 0, wy_m = WALLS && g.wall[1] && (int)y == ny - 1;
     const bool wz_p = WALLS && g.wall[2] && z == 0, wz_m = WALLS && g.wall[2] && (int)z == nz - 1;
@@ -140,32 +139,6 @@ lbm_kernel(Geom g, Planes<Q, typename Store<STORE>::T> pl,
           if (!blocked(i) && nodes[c + off_of(i)] != 0) lmask |= 1u << i;
       }
     }
-    const int nl = __popc(lmask);
-    int incl = nl;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int v = __shfl_up_sync(fullm, incl, o);
-      if (lane >= o) incl += v;
-    }
-    const int first = incl - nl, total = __shfl_sync(fullm, incl, 31);
-    if (total > 0) {   // warp-uniform
-      int k = first;
-      for (unsigned m = lmask; m; m &= m - 1u) {
-        const int i = __ffs(m) - 1;
-        s_link[wid][k++] = lane | (i << 5) | (((int)nodes[c + off_of(i)] - 1) << 10);
-      }
-      __syncwarp();
-      for (int jl = lane; jl < total; jl += 32) {
-        const int lk = s_link[wid][jl];
-        const uint32_t cc = blockIdx.x * blockDim.x + (uint32_t)(wid * 32 + (lk & 31));   // a valid cell
-        const uint32_t cz = fast_div(cc, g.mxy, g.sxy), cr = cc - cz * g.nxy;
-        const uint32_t cy = fast_div(cr, g.mx, g.sx), cx = cr - cy * g.n[0];
-        const int ip = L::opp((lk >> 5) & 31), p = lk >> 10;
-        s_q[wid][jl] = ibb_link_q(cworld, desc[p].c0, desc[p].c1, (float)cx + 0.5f, (float)cy + 0.5f,
-                                  (float)cz + 0.5f, L::e(ip, 0), L::e(ip, 1), L::e(ip, 2), g);
-      }
-      __syncwarp();
-    }
     if (lmask) {
       R rho_f, uf[3];
       {   // rho_f: x_f's own post-collision populations; u_f: the previous update
@@ -176,13 +149,16 @@ lbm_kernel(Geom g, Planes<Q, typename Store<STORE>::T> pl,
         const float4 v = uprev[c];
         uf[0] = (R)v.x; uf[1] = (R)v.y; uf[2] = (R)v.z;
       }
-      int k = first;
+      int k = ib_base[c];
 #pragma unroll   // f[i] must stay in registers: a run-time index would put f in local memory
       for (int i = 1; i < Q; ++i) {
         if (!((lmask >> i) & 1u)) continue;
         const int ip = L::opp(i), p = (int)nodes[c + off_of(i)] - 1;
         const int ex = L::e(ip, 0), ey = L::e(ip, 1), ez = L::e(ip, 2);   // into the wall
-        const R qf = (R)s_q[wid][k++];
+        // beyond the list's capacity (counted in the status) the same bisection runs here
+        const R qf = (R)(k < ib_cap ? ib_q[k] : ibb_link_q(cworld, desc[p].c0, desc[p].c1, (float)x + 0.5f,
+                                                         (float)y + 0.5f, (float)z + 0.5f, ex, ey, ez, g));
+        ++k;
         const R xw[3] = {(R)x + R(0.5) + qf * (R)ex, (R)y + R(0.5) + qf * (R)ey, (R)z + R(0.5) + qf * (R)ez};
         R uw[3];
         rigid_velocity<R>(g, pose, posed, p, xw[0], xw[1], xw[2], uw);
@@ -412,6 +388,113 @@ lbm_kernel(Geom g, Planes<Q, typename Store<STORE>::T> pl,
   }
 }
 
+// ---- IBB links (Eq. 25) ahead of the LBM update ------------------------------------------
+// Every fluid node of a flagged brick whose lattice neighbour x - e_i is a solid node owns the
+// link (x, i). ibb_links_kernel appends a node's links in direction order (warp-aggregated) and
+// keeps the index of its first one; ibb_q_kernel then runs the 24-step binary32 bisection of
+// every link at full occupancy, instead of inside the occupancy-bound LBM kernel.
+template <int Q, bool WALLS>
+__global__ void __launch_bounds__(256) ibb_links_kernel(Geom g, const uint32_t* __restrict__ bword,
+                                                        const uint16_t* __restrict__ nodes,
+                                                        int32_t* __restrict__ base, uint32_t* __restrict__ lcell,
+                                                        uint32_t* __restrict__ lmeta, unsigned int* count, int cap,
+                                                        unsigned long long* __restrict__ status) {
+  using L = Lat<Q>;
+  const uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool valid = idx < g.ncell;
+  const int c = (int)(valid ? idx : g.ncell - 1);
+  const uint32_t z = fast_div((uint32_t)c, g.mxy, g.sxy);
+  const uint32_t rem = (uint32_t)c - z * g.nxy;
+  const uint32_t y = fast_div(rem, g.mx, g.sx);
+  const uint32_t x = rem - y * g.n[0];
+  const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+  const int sy = nx, sz = (int)g.nxy;
+  const int ox_p = x == 0 ? nx - 1 : -1, ox_m = (int)x == nx - 1 ? -(nx - 1) : 1;
+  const int oy_p = y == 0 ? (ny - 1) * sy : -sy, oy_m = (int)y == ny - 1 ? -(ny - 1) * sy : sy;
+  const int oz_p = z == 0 ? (nz - 1) * sz : -sz, oz_m = (int)z == nz - 1 ? -(nz - 1) * sz : sz;
+  const bool wx_p = WALLS && g.wall[0] && x == 0, wx_m = WALLS && g.wall[0] && (int)x == nx - 1;
+  const bool wy_p = WALLS && g.wall[1] && y == 0, wy_m = WALLS && g.wall[1] && (int)y == ny - 1;
+  const bool wz_p = WALLS && g.wall[2] && z == 0, wz_m = WALLS && g.wall[2] && (int)z == nz - 1;
+  auto off_of = [&](int i) {
+    const int ex = L::e(i, 0), ey = L::e(i, 1), ez = L::e(i, 2);
+    return (ex > 0 ? ox_p : ex < 0 ? ox_m : 0) + (ey > 0 ? oy_p : ey < 0 ? oy_m : 0) +
+           (ez > 0 ? oz_p : ez < 0 ? oz_m : 0);
+  };
+  auto blocked = [&](int i) {
+    const int ex = L::e(i, 0), ey = L::e(i, 1), ez = L::e(i, 2);
+    return (ex > 0 && wx_p) || (ex < 0 && wx_m) || (ey > 0 && wy_p) || (ey < 0 && wy_m) ||
+           (ez > 0 && wz_p) || (ez < 0 && wz_m);
+  };
+  unsigned lmask = 0u;
+  const uint32_t bq = ((z >> 3) * (uint32_t)g.nb[1] + (y >> 3)) * (uint32_t)g.nb[0] + (x >> 3);
+  if (valid && (bword[bq] >> 16) && nodes[c] == 0) {
+#pragma unroll
+    for (int i = 1; i < Q; ++i)
+      if (!blocked(i) && nodes[c + off_of(i)] != 0) lmask |= 1u << i;
+  }
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int nl = __popc(lmask);
+  int incl = nl;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(full, incl, o);
+    if (lane >= o) incl += v;
+  }
+  const int total = __shfl_sync(full, incl, 31);
+  if (total == 0) return;   // warp-uniform
+  unsigned first = 0;
+  if (lane == 31) first = atomicAdd(count, (unsigned)total);
+  first = __shfl_sync(full, first, 31) + (unsigned)(incl - nl);
+  if (!nl) return;
+  base[c] = (int32_t)first;
+  unsigned k = first;
+  for (unsigned m = lmask; m; m &= m - 1u, ++k) {
+    const int i = __ffs(m) - 1;
+    if (k < (unsigned)cap) {
+      lcell[k] = (uint32_t)c;
+      lmeta[k] = (uint32_t)i | ((uint32_t)(nodes[c + off_of(i)] - 1) << 8);
+    }
+  }
+  if (first + (unsigned)nl > (unsigned)cap) atomicAdd(&status[ST_IBB_OVERFLOW], 1ull);
+}
+
+template <int Q>
+__global__ void __launch_bounds__(256) ibb_q_kernel(Geom g, const float4* __restrict__ cworld,
+                                                    const ParticleDesc* __restrict__ desc,
+                                                    const uint32_t* __restrict__ lcell,
+                                                    const uint32_t* __restrict__ lmeta, const unsigned int* count,
+                                                    unsigned int* count_next, int cap, float* __restrict__ q) {
+  using L = Lat<Q>;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *count_next = 0u;   // the next step appends there
+  const unsigned n = min(*count, (unsigned)cap);
+  for (unsigned j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    const uint32_t c = lcell[j], meta = lmeta[j];
+    const uint32_t z = fast_div(c, g.mxy, g.sxy), r = c - z * g.nxy;
+    const uint32_t y = fast_div(r, g.mx, g.sx), x = r - y * g.n[0];
+    const int i = (int)(meta & 31u), p = (int)(meta >> 8), ip = L::opp(i);
+    q[j] = ibb_link_q(cworld, desc[p].c0, desc[p].c1, (float)x + 0.5f, (float)y + 0.5f, (float)z + 0.5f,
+                      L::e(ip, 0), L::e(ip, 1), L::e(ip, 2), g);
+  }
+}
+
+void launch_ibb_links(int q, const Geom& g, BrickSet bs, const uint16_t* nodes, const IbbLinks& lk, int par,
+                      const ParticleDesc* desc, unsigned long long* status, int nsm, cudaStream_t st) {
+  const bool walls = g.wall[0] || g.wall[1] || g.wall[2];
+  const unsigned blocks = (unsigned)((g.ncell + 255) / 256);
+  unsigned int* cnt = lk.count + (par & 1);
+  unsigned int* nxt = lk.count + ((par + 1) & 1);
+  if (q == 15) {
+    if (walls) ibb_links_kernel<15, true><<<blocks, 256, 0, st>>>(g, bs.bword, nodes, lk.base, lk.cell, lk.meta, cnt, lk.cap, status);
+    else ibb_links_kernel<15, false><<<blocks, 256, 0, st>>>(g, bs.bword, nodes, lk.base, lk.cell, lk.meta, cnt, lk.cap, status);
+    ibb_q_kernel<15><<<nsm * 8, 256, 0, st>>>(g, bs.cworld, desc, lk.cell, lk.meta, cnt, nxt, lk.cap, lk.q);
+  } else {
+    if (walls) ibb_links_kernel<19, true><<<blocks, 256, 0, st>>>(g, bs.bword, nodes, lk.base, lk.cell, lk.meta, cnt, lk.cap, status);
+    else ibb_links_kernel<19, false><<<blocks, 256, 0, st>>>(g, bs.bword, nodes, lk.base, lk.cell, lk.meta, cnt, lk.cap, status);
+    ibb_q_kernel<19><<<nsm * 8, 256, 0, st>>>(g, bs.cworld, desc, lk.cell, lk.meta, cnt, nxt, lk.cap, lk.q);
+  }
+}
+
 template <int Q, int STORE, bool IBB>
 static void launch_lbm_q(bool walls, bool reduce, const Geom& g, const void* fin, void* fout, float* u,
                          const uint16_t* solid, BrickSet bs, double tau, double rho0, double* red,
@@ -426,7 +509,7 @@ static void launch_lbm_q(bool walls, bool reduce, const Geom& g, const void* fin
   float4* u4 = reinterpret_cast<float4*>(u);
   const int bsz_ok = (bsz == 64 || bsz == 128) ? bsz : 256;
   const dim3 grid((g.ncell + bsz_ok - 1) / bsz_ok), block(bsz_ok);
-#define RWMI_LBM_ARGS g, pl, u4, solid, bs.bword, bs.pose, bs.posed, bs.sp, (R)tau, (R)rho0, red, forces, ib.nodes, ib.uprev, ib.desc, bs.cworld
+#define RWMI_LBM_ARGS g, pl, u4, solid, bs.bword, bs.pose, bs.posed, bs.sp, (R)tau, (R)rho0, red, forces, ib.nodes, ib.uprev, ib.desc, bs.cworld, ib.base, ib.q, ib.cap
   if constexpr (STORE == 1 || STORE == 3) {   // the fused mode of free-DEM runs
     if (fused) {
       if (walls) lbm_kernel<Q, STORE, true, 2, IBB><<<grid, block, 0, st>>>(RWMI_LBM_ARGS);
