@@ -60,6 +60,8 @@ def lib():
                          "orc_mass_momentum", "orc_forces", "orc_counters"):
                 getattr(L, name).argtypes = [P, C.c_void_p]
             L.orc_solid.argtypes = [P, C.c_longlong, C.c_void_p, C.c_void_p]
+            L.orc_solid_cells.argtypes = [P, C.c_longlong, C.c_longlong, C.c_void_p, C.c_void_p,
+                                          C.c_void_p]
             L.orc_walkers.argtypes = [P, C.c_void_p, C.c_void_p]
             L.orc_bin_positions.argtypes = [P, C.c_longlong, C.c_void_p, C.c_void_p]
             L.orc_lbm_cells.argtypes = [P, C.c_longlong, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
@@ -314,6 +316,15 @@ class Oracle:
         cnt = np.zeros(self.n_cells, np.int32)
         own = np.zeros(self.n_cells, np.int32)
         lib().orc_solid(self.h, t, _ptr(cnt), _ptr(own))
+        return cnt, own
+
+    def solid_cells(self, cells, t=None):
+        """Solid sub-sample count and owner of the listed cells at step t (default: now)."""
+        cells = np.ascontiguousarray(cells, np.int64)
+        cnt = np.zeros(len(cells), np.int32)
+        own = np.zeros(len(cells), np.int32)
+        lib().orc_solid_cells(self.h, int(self.t if t is None else t), len(cells), _ptr(cells),
+                              _ptr(cnt), _ptr(own))
         return cnt, own
 
     def walkers(self):

@@ -372,6 +372,36 @@ static int inside_any32(const orc_t* o, const frame_t* fr, const float x[3])
  * Every sub-sample of every cell is tested; a particle is skipped for a cell only when the
  * cell lies wholly beyond its bound radius, where Eq. 3 stays below 1.
  * ------------------------------------------------------------------------------------------ */
+/* Solid fraction of one cell (Reading R3): sub-sample count and owner of cell (i, j, k) against
+ * the poses in fr. cand and npart are scratch arrays of P + 1 ints. */
+static void raster_cell(const orc_t* o, const frame_t* fr, long long i, long long j, long long k,
+                        int* cand, int* npart, int* cnt_out, int* own_out)
+{
+    double xc[3] = {i + 0.5, j + 0.5, k + 0.5};
+    int nc = 0;
+    for (int p = 0; p < o->P; ++p)
+        if (origin_distance(o, fr, p, xc) <= o->Rb[p] + 1.0) { cand[nc++] = p; npart[p] = 0; }
+    int count = 0;
+    if (nc > 0) {
+        for (int cz = 0; cz < 4; ++cz)
+            for (int cy = 0; cy < 4; ++cy)
+                for (int cx = 0; cx < 4; ++cx) {
+                    float xs[3] = {(float)i + (0.125f + 0.25f * (float)cx),
+                                   (float)j + (0.125f + 0.25f * (float)cy),
+                                   (float)k + (0.125f + 0.25f * (float)cz)};
+                    int solid = 0;
+                    for (int m = 0; m < nc; ++m)
+                        if (metaball32(o, fr, cand[m], xs) >= 1.0f) { npart[cand[m]]++; solid = 1; }
+                    count += solid;
+                }
+    }
+    int owner = -1, best = 0;
+    for (int m = 0; m < nc; ++m)
+        if (npart[cand[m]] > best) { best = npart[cand[m]]; owner = cand[m]; }
+    *cnt_out = count;
+    *own_out = count > 0 ? owner : -1;
+}
+
 static void rasterize(orc_t* o, long long t)
 {
     frame_t fr;
@@ -383,29 +413,7 @@ static void rasterize(orc_t* o, long long t)
         for (long long j = 0; j < o->n[1]; ++j)
             for (long long i = 0; i < o->n[0]; ++i) {
                 long long c = cell_index(o, i, j, k);
-                double xc[3] = {i + 0.5, j + 0.5, k + 0.5};
-                int nc = 0;
-                for (int p = 0; p < o->P; ++p)
-                    if (origin_distance(o, &fr, p, xc) <= o->Rb[p] + 1.0) { cand[nc++] = p; npart[p] = 0; }
-                int count = 0;
-                if (nc > 0) {
-                    for (int cz = 0; cz < 4; ++cz)
-                        for (int cy = 0; cy < 4; ++cy)
-                            for (int cx = 0; cx < 4; ++cx) {
-                                float xs[3] = {(float)i + (0.125f + 0.25f * (float)cx),
-                                               (float)j + (0.125f + 0.25f * (float)cy),
-                                               (float)k + (0.125f + 0.25f * (float)cz)};
-                                int solid = 0;
-                                for (int m = 0; m < nc; ++m)
-                                    if (metaball32(o, &fr, cand[m], xs) >= 1.0f) { npart[cand[m]]++; solid = 1; }
-                                count += solid;
-                            }
-                }
-                int owner = -1, best = 0;
-                for (int m = 0; m < nc; ++m)
-                    if (npart[cand[m]] > best) { best = npart[cand[m]]; owner = cand[m]; }
-                o->cnt[c] = count;
-                o->own[c] = count > 0 ? owner : -1;
+                raster_cell(o, &fr, i, j, k, cand, npart, &o->cnt[c], &o->own[c]);
             }
     free(cand);
     free(npart);
@@ -1716,6 +1724,26 @@ ORC_API void orc_solid(void* h, long long t, int* count, int* owner)
     if (o->solid_time != t) rasterize(o, t);
     memcpy(count, o->cnt, sizeof(int) * (size_t)o->ncell);
     memcpy(owner, o->own, sizeof(int) * (size_t)o->ncell);
+}
+/* Solid fraction at step t of the n listed cells only (the rule of orc_solid, cell by cell); the
+ * context's own solid arrays are left as they are. */
+ORC_API void orc_solid_cells(void* h, long long t, long long n, const int64_t* cells, int* count,
+                             int* owner)
+{
+    orc_t* o = (orc_t*)h;
+    frame_t fr;
+    frame_alloc(o, &fr);
+    frame_at(o, t, &fr);
+    int* cand = (int*)malloc(sizeof(int) * (size_t)(o->P + 1));
+    int* npart = (int*)calloc((size_t)o->P + 1, sizeof(int));
+    for (long long m = 0; m < n; ++m) {
+        long long c = cells[m];
+        long long i = c % o->n[0], j = (c / o->n[0]) % o->n[1], k = c / ((long long)o->n[0] * o->n[1]);
+        raster_cell(o, &fr, i, j, k, cand, npart, &count[m], &owner[m]);
+    }
+    free(cand);
+    free(npart);
+    frame_free(&fr);
 }
 ORC_API void orc_walkers(void* h, double* x, double* x0)
 {

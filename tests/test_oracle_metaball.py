@@ -186,6 +186,22 @@ def test_solid_fraction_equals_brute_force(t):
     assert cnt.max() == 64 and (cnt > 0).sum() > 50
 
 
+@pytest.mark.parametrize("t", [0, 9])
+def test_sampled_solid_fraction_equals_brute_force(t):
+    """The cell-list entry (used to time bounded samples) gives the brute-force counts and
+    owners of exactly the listed cells, in list order, repeats included."""
+    dims, walls = (16, 14, 13), 4
+    mb = _two_ball()
+    mb.origin[:, 2] = [6.5, 6.0]
+    cnt_b, own_b, o = _brute_solid(dims, walls, mb, t)
+    cells = np.random.default_rng(5).integers(0, cnt_b.size, 700)
+    cells[:3] = [0, cnt_b.size - 1, 0]
+    cnt, own = o.solid_cells(cells, t)
+    assert np.array_equal(cnt, cnt_b[cells])
+    assert np.array_equal(own, own_b[cells])
+    assert (cnt > 0).any() and (cnt == 0).any()
+
+
 def test_solid_fraction_sphere_volume():
     """Sum of epsilon over cells converges to the sphere volume (4/3) pi r^3."""
     for r, c in ((6.0, (16.0, 16.0, 16.0)), (4.5, (10.3, 11.7, 9.1))):
