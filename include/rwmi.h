@@ -30,10 +30,14 @@
  *     creating, reading or destroying one context never waits for another context's work.
  *     A device array the caller passes must be ready before the call (its producer finished or
  *     ordered before the context's stream).
- *   - Errors: every call returns an rwmi_status. RWMI_E_INVALID leaves the context unchanged.
- *     Any other negative status leaves it unusable until rwmi_destroy. Positive values are
- *     warnings. rwmi_last_error gives a message. Nothing is thrown across the ABI; nothing
- *     exits. Calls on one context are not thread-safe.
+ *   - Errors: every call returns an rwmi_status. RWMI_E_INVALID and RWMI_E_STATE (a call made
+ *     in the wrong state) leave the context unchanged. RWMI_E_NONFINITE reports non-finite
+ *     values in the state; the context still answers, so the state can be read out.
+ *     RWMI_E_OOM and RWMI_E_CUDA fence the context: its device state may be half built, so
+ *     every later call on it except rwmi_last_error, rwmi_launch_count and rwmi_destroy
+ *     returns RWMI_E_STATE, and rwmi_last_error keeps the message of the failure that fenced
+ *     it. Positive values are warnings. Nothing is thrown across the ABI; nothing exits.
+ *     Calls on one context are not thread-safe.
  */
 #ifndef RWMI_H
 #define RWMI_H
@@ -378,7 +382,20 @@ RWMI_API rwmi_status rwmi_brick_stats(rwmi_ctx* ctx, int64_t out[4]);
 /* Number of kernel launches the context has issued (for launch accounting). */
 RWMI_API int64_t rwmi_launch_count(const rwmi_ctx* ctx);
 
-/* Frees every resource of the context; NULL is allowed. */
+/* Host-side fault injection for tests of the failure paths. Device allocations are numbered
+ * process-wide from 0 in the order the library makes them (rwmi_alloc_count gives how many have
+ * been made). After this call, the first `after` allocations succeed and the next one reports
+ * RWMI_E_OOM without reaching the CUDA allocator; that disarms the injection. after < 0
+ * disarms it at once. No GPU memory is filled and nothing faults. Returns the allocation count
+ * at the time of the call. Not thread-safe against allocations made meanwhile by other
+ * threads. */
+RWMI_API int64_t rwmi_inject_alloc_failure(int64_t after);
+
+/* Number of device allocations the library has made (or refused by injection) in this process. */
+RWMI_API int64_t rwmi_alloc_count(void);
+
+/* Frees every resource of the context; NULL is allowed. A context fenced by RWMI_E_OOM or
+ * RWMI_E_CUDA is freed as far as it was built. */
 RWMI_API void rwmi_destroy(rwmi_ctx* ctx);
 
 #ifdef __cplusplus

@@ -3,6 +3,7 @@
 // checkpointing. Every step of the method runs in the kernels of rwmi_fluid.cu and
 // rwmi_walkers.cu; this file only sequences them.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -111,6 +112,9 @@ struct rwmi_ctx {
   std::map<GraphKey, GraphEntry> graphs;
   // phase timing (rwmi_step_timed): events[phase] start/stop pairs when enabled
   bool timing = false;
+  // Set by an allocation or CUDA failure: the device state may be half built, so every later
+  // call but rwmi_last_error and rwmi_destroy is refused with RWMI_E_STATE.
+  bool broken = false;
   cudaEvent_t ev[2 * RWMI_NPHASE] = {};
 };
 
@@ -129,9 +133,18 @@ struct rwmi_batch {
 namespace {
 
 rwmi_status fail(rwmi_ctx* c, rwmi_status s, const std::string& msg) {
-  if (c) c->err = msg;
+  if (c) {
+    c->err = msg;
+    if (s == RWMI_E_OOM || s == RWMI_E_CUDA) c->broken = true;
+  }
   return s;
 }
+
+// A context fenced by an earlier failure refuses the call; its message stays the first failure's.
+#define GUARD(c)                                \
+  do {                                          \
+    if ((c)->broken) return RWMI_E_STATE;       \
+  } while (0)
 
 #define CK(call)                                                                       \
   do {                                                                                 \
@@ -143,16 +156,35 @@ rwmi_status fail(rwmi_ctx* c, rwmi_status s, const std::string& msg) {
 
 // Device memory is stream-ordered on the context's stream: creating or destroying one context
 // never synchronises the device, so other contexts' work keeps running meanwhile.
+// Host-side fault injection (rwmi_inject_alloc_failure): the allocation whose process-wide
+// index equals g_fail_at reports cudaErrorMemoryAllocation without reaching the allocator.
+std::atomic<int64_t> g_alloc_count{0};
+std::atomic<int64_t> g_fail_at{-1};
+
 template <typename T>
 cudaError_t dalloc(rwmi_ctx* c, T** p, size_t bytes) {
   *p = nullptr;
   if (bytes == 0) bytes = 16;
+  const int64_t k = g_alloc_count.fetch_add(1);
+  int64_t at = k;
+  if (g_fail_at.compare_exchange_strong(at, -1)) return cudaErrorMemoryAllocation;
   return cudaMallocAsync((void**)p, bytes, c->stream);
 }
 
 void dfree(rwmi_ctx* c, void* p) {
   if (p) cudaFreeAsync(p, c->stream);
 }
+
+// Device scratch owned by one API call: freed, stream-ordered, on every return path.
+template <typename T>
+struct CallScratch {
+  rwmi_ctx* c;
+  T* p = nullptr;
+  explicit CallScratch(rwmi_ctx* cc) : c(cc) {}
+  CallScratch(const CallScratch&) = delete;
+  CallScratch& operator=(const CallScratch&) = delete;
+  ~CallScratch() { dfree(c, p); }
+};
 
 // Blocking copy ordered on the context's stream (never on the legacy default stream, which
 // would wait for every other blocking stream of the process).
@@ -666,6 +698,7 @@ RWMI_API rwmi_status rwmi_create(rwmi_ctx** out, const int32_t dims[3], double t
 
 RWMI_API rwmi_status rwmi_configure(rwmi_ctx* c, const rwmi_config* cfg) {
   if (!c || !cfg) return RWMI_E_INVALID;
+  GUARD(c);
   if (c->stepped) return fail(c, RWMI_E_STATE, "rwmi_configure: only before the first step");
   if ((cfg->q != 15 && cfg->q != 19) || cfg->storage < 0 || cfg->storage > 3 || cfg->wall_mask > 7 ||
       !(cfg->rho0 > 0.0) || cfg->sort_interval < 0 || cfg->moment_interval < 0 ||
@@ -708,6 +741,7 @@ RWMI_API rwmi_status rwmi_configure(rwmi_ctx* c, const rwmi_config* cfg) {
 
 RWMI_API rwmi_status rwmi_set_stream(rwmi_ctx* c, void* stream) {
   if (!c) return RWMI_E_INVALID;
+  GUARD(c);
   CK(cudaStreamSynchronize(c->stream));
   if (stream == nullptr) return RWMI_OK;   // keep the context's own (blocking) stream
   if (c->own_stream) cudaStreamDestroy(c->stream);
@@ -721,6 +755,7 @@ RWMI_API rwmi_status rwmi_set_metaballs(rwmi_ctx* c, int32_t P, const int32_t* c
                                         const float* k, const double* origin, const double* amplitude,
                                         const double* period, const double* phase, const double* omega) {
   if (!c) return RWMI_E_INVALID;
+  GUARD(c);
   if (c->stepped) return fail(c, RWMI_E_STATE, "rwmi_set_metaballs: only before the first step");
   if (P < 0 || P > MAX_PARTICLES) return fail(c, RWMI_E_INVALID, "rwmi_set_metaballs: 0 <= P <= 511");
   if (P > 0 && (!coff || !cb || !k || !origin || !amplitude || !period || !phase))
@@ -790,6 +825,7 @@ RWMI_API void rwmi_dem_defaults(rwmi_dem_config* cfg) {
 RWMI_API rwmi_status rwmi_set_dem(rwmi_ctx* c, const rwmi_dem_config* cfg, const double* density,
                                   const double* Rs, const double* vel, const double* spin) {
   if (!c || !cfg) return RWMI_E_INVALID;
+  GUARD(c);
   if (c->P < 1 || !density || !Rs) return fail(c, RWMI_E_INVALID, "rwmi_set_dem: no particles or null array");
   if (c->dem) return fail(c, RWMI_E_STATE, "rwmi_set_dem: the particles are free already");
   if (c->cfg.storage != RWMI_STORE_FP32_SHIFT && c->cfg.storage != RWMI_STORE_FP64_SHIFT)
@@ -832,19 +868,19 @@ RWMI_API rwmi_status rwmi_set_dem(rwmi_ctx* c, const rwmi_dem_config* cfg, const
   CK(cudaMemsetAsync(c->dem_b, 0, dem_bytes((size_t)P), c->stream));
   c->demcfg = *cfg;
   DemArgs a = dem_args(c, (int)(c->t & 1));
-  double* dens = nullptr;
-  unsigned long long* sums = nullptr;
-  CK(dalloc(c, &dens, sizeof(double) * (size_t)P));
-  CK(dalloc(c, &sums, sizeof(unsigned long long) * 10 * (size_t)P));
-  CK(cudaMemsetAsync(sums, 0, sizeof(unsigned long long) * 10 * (size_t)P, c->stream));
-  CK(copy_now(c, a.st, st.data(), sizeof(double) * st.size()));
-  CK(copy_now(c, dens, density, sizeof(double) * (size_t)P));
-  CK(copy_now(c, const_cast<double*>(a.Rs), Rs, sizeof(double) * (size_t)P));
+  {
+    CallScratch<double> dens(c);
+    CallScratch<unsigned long long> sums(c);
+    CK(dalloc(c, &dens.p, sizeof(double) * (size_t)P));
+    CK(dalloc(c, &sums.p, sizeof(unsigned long long) * 10 * (size_t)P));
+    CK(cudaMemsetAsync(sums.p, 0, sizeof(unsigned long long) * 10 * (size_t)P, c->stream));
+    CK(copy_now(c, a.st, st.data(), sizeof(double) * st.size()));
+    CK(copy_now(c, dens.p, density, sizeof(double) * (size_t)P));
+    CK(copy_now(c, const_cast<double*>(a.Rs), Rs, sizeof(double) * (size_t)P));
+    launch_dem_mass(a, sums.p, dens.p, const_cast<double*>(a.mass), const_cast<double*>(a.Ib), dem_props(c),
+                    c->cbody, c->stream);
+  }
   const std::vector<float4> old_body = c->hbody;
-  launch_dem_mass(a, sums, dens, const_cast<double*>(a.mass), const_cast<double*>(a.Ib), dem_props(c), c->cbody,
-                  c->stream);
-  dfree(c, dens);
-  dfree(c, sums);
   // the recentred body frames: host copy and bound radii
   CK(copy_now(c, c->hbody.data(), c->cbody, sizeof(float4) * c->hbody.size()));
   bool ok = true;
@@ -884,6 +920,7 @@ RWMI_API rwmi_status rwmi_set_dem(rwmi_ctx* c, const rwmi_dem_config* cfg, const
 
 RWMI_API rwmi_status rwmi_particle_mass(rwmi_ctx* c, double* out) {
   if (!c || !out) return RWMI_E_INVALID;
+  GUARD(c);
   if (!c->dem) return fail(c, RWMI_E_STATE, "rwmi_particle_mass: no free DEM (rwmi_set_dem)");
   CK(copy_now(c, out, dem_props(c), sizeof(double) * 10 * (size_t)c->P));
   return RWMI_OK;
@@ -891,6 +928,7 @@ RWMI_API rwmi_status rwmi_particle_mass(rwmi_ctx* c, double* out) {
 
 RWMI_API rwmi_status rwmi_particle_state(rwmi_ctx* c, double* out) {
   if (!c || !out) return RWMI_E_INVALID;
+  GUARD(c);
   if (!c->dem) return fail(c, RWMI_E_STATE, "rwmi_particle_state: no free DEM (rwmi_set_dem)");
   CK(copy_now(c, out, c->dem_d, sizeof(double) * 13 * (size_t)c->P));
   return RWMI_OK;
@@ -898,6 +936,7 @@ RWMI_API rwmi_status rwmi_particle_state(rwmi_ctx* c, double* out) {
 
 RWMI_API rwmi_status rwmi_set_particle_state(rwmi_ctx* c, const double* state) {
   if (!c || !state) return RWMI_E_INVALID;
+  GUARD(c);
   if (!c->dem) return fail(c, RWMI_E_STATE, "rwmi_set_particle_state: no free DEM (rwmi_set_dem)");
   for (size_t m = 0; m < (size_t)13 * c->P; ++m)
     if (!std::isfinite(state[m])) return fail(c, RWMI_E_INVALID, "rwmi_set_particle_state: non-finite value");
@@ -911,6 +950,7 @@ RWMI_API rwmi_status rwmi_set_particle_state(rwmi_ctx* c, const double* state) {
 
 RWMI_API rwmi_status rwmi_seed_walkers(rwmi_ctx* c, int64_t n, const double lo[3], const double hi[3]) {
   if (!c || !lo || !hi) return RWMI_E_INVALID;
+  GUARD(c);
   if (n < 0 || n > 0x7fffffffLL) return fail(c, RWMI_E_INVALID, "rwmi_seed_walkers: 0 <= n < 2^31");
   for (int a = 0; a < 3; ++a)
     if (!(lo[a] >= 0.0) || !(hi[a] <= (double)c->n[a]) || !(lo[a] <= hi[a]))
@@ -936,6 +976,7 @@ RWMI_API rwmi_status rwmi_seed_walkers(rwmi_ctx* c, int64_t n, const double lo[3
 
 RWMI_API rwmi_status rwmi_set_walkers(rwmi_ctx* c, int64_t n, const float* pos) {
   if (!c || (n > 0 && !pos)) return RWMI_E_INVALID;
+  GUARD(c);
   if (n < 0 || n > 0x7fffffffLL) return fail(c, RWMI_E_INVALID, "rwmi_set_walkers: 0 <= n < 2^31");
   std::vector<float> host;
   const float* src = pos;
@@ -962,6 +1003,7 @@ RWMI_API rwmi_status rwmi_set_walkers(rwmi_ctx* c, int64_t n, const float* pos) 
 
 RWMI_API rwmi_status rwmi_step(rwmi_ctx* c, int32_t n) {
   if (!c || n < 0) return RWMI_E_INVALID;
+  GUARD(c);
   c->stepped = true;
   const int64_t L = chunk_length(c);
   const bool graphs = c->cfg.use_graphs && L <= 64;
@@ -1002,6 +1044,7 @@ RWMI_API rwmi_status rwmi_step(rwmi_ctx* c, int32_t n) {
 
 RWMI_API rwmi_status rwmi_step_timed(rwmi_ctx* c, int32_t n, double* phase_ms) {
   if (!c || n < 0 || !phase_ms) return RWMI_E_INVALID;
+  GUARD(c);
   c->stepped = true;
   for (int k = 0; k < 2 * RWMI_NPHASE; ++k)
     if (!c->ev[k]) CK(cudaEventCreate(&c->ev[k]));
@@ -1026,6 +1069,7 @@ RWMI_API rwmi_status rwmi_step_timed(rwmi_ctx* c, int32_t n, double* phase_ms) {
 
 RWMI_API rwmi_status rwmi_autotune(rwmi_ctx* c, int32_t* chosen) {
   if (!c) return RWMI_E_INVALID;
+  GUARD(c);
   const int tp = (int)(c->t & 1);
   const size_t acc_n = (size_t)(6 * c->P + 4 * RED_SLOTS);
   rwmi_status s = ensure_scratch(c, sizeof(double) * acc_n);   // throw-away force/mass sums
@@ -1083,6 +1127,7 @@ RWMI_API rwmi_status rwmi_autotune(rwmi_ctx* c, int32_t* chosen) {
 
 RWMI_API rwmi_status rwmi_query(rwmi_ctx* c) {
   if (!c) return RWMI_E_INVALID;
+  GUARD(c);
   const cudaError_t e = cudaStreamQuery(c->stream);
   if (e == cudaErrorNotReady) return RWMI_BUSY;
   CK(e);
@@ -1114,6 +1159,7 @@ RWMI_API rwmi_status rwmi_footprint(const int32_t dims[3], int32_t q, int32_t st
 
 RWMI_API rwmi_status rwmi_sync(rwmi_ctx* c) {
   if (!c) return RWMI_E_INVALID;
+  GUARD(c);
   CK(cudaStreamSynchronize(c->stream));
   unsigned long long st[ST_COUNT];
   CK(copy_now(c, st, c->status, sizeof(st)));
@@ -1127,12 +1173,14 @@ RWMI_API rwmi_status rwmi_sync(rwmi_ctx* c) {
 
 RWMI_API rwmi_status rwmi_time(rwmi_ctx* c, int64_t* t) {
   if (!c || !t) return RWMI_E_INVALID;
+  GUARD(c);
   *t = c->t;
   return RWMI_OK;
 }
 
 RWMI_API rwmi_status rwmi_info(rwmi_ctx* c, int64_t out[8]) {
   if (!c || !out) return RWMI_E_INVALID;
+  GUARD(c);
   const int64_t v[8] = {c->n[0], c->n[1], c->n[2], c->cfg.q, c->cfg.storage, c->nw, c->P, c->t};
   std::memcpy(out, v, sizeof(v));
   return RWMI_OK;
@@ -1140,6 +1188,7 @@ RWMI_API rwmi_status rwmi_info(rwmi_ctx* c, int64_t out[8]) {
 
 RWMI_API rwmi_status rwmi_concentration(rwmi_ctx* c, uint32_t* out) {
   if (!c || !out) return RWMI_E_INVALID;
+  GUARD(c);
   if (c->binned_t != c->t) {
     CK(cudaMemsetAsync(c->counts, 0, sizeof(uint32_t) * (size_t)c->ncell, c->stream));
     launch_histogram(c->g, c->pos[c->pcur], c->nw, c->counts, nullptr, c->stream);
@@ -1152,6 +1201,7 @@ RWMI_API rwmi_status rwmi_concentration(rwmi_ctx* c, uint32_t* out) {
 
 RWMI_API rwmi_status rwmi_walker_moments(rwmi_ctx* c, double out[13]) {
   if (!c || !out) return RWMI_E_INVALID;
+  GUARD(c);
   launch_moments(c->pos[c->pcur], c->x0[c->pcur], c->nw, c->macc, c->mrow, 0, 1, c->d_T, 0, c->stream);
   c->launches += c->nw > 0 ? 2 : 1;
   CK(cudaGetLastError());
@@ -1160,6 +1210,7 @@ RWMI_API rwmi_status rwmi_walker_moments(rwmi_ctx* c, double out[13]) {
 
 RWMI_API rwmi_status rwmi_moment_series(rwmi_ctx* c, double* out, int32_t max_rows, int32_t* n_rows) {
   if (!c || !out || !n_rows || max_rows < 0) return RWMI_E_INVALID;
+  GUARD(c);
   const int64_t avail = std::min<int64_t>(c->series_rows, SERIES_ROWS);
   const int64_t take = std::min<int64_t>(avail, max_rows);
   std::vector<double> ring((size_t)SERIES_ROWS * SERIES_COLS);
@@ -1177,6 +1228,7 @@ RWMI_API rwmi_status rwmi_moment_series(rwmi_ctx* c, double* out, int32_t max_ro
 
 RWMI_API rwmi_status rwmi_velocity(rwmi_ctx* c, float* out) {
   if (!c || !out) return RWMI_E_INVALID;
+  GUARD(c);
   rwmi_status s = ensure_scratch(c, sizeof(float) * 3 * (size_t)c->ncell);
   if (s != RWMI_OK) return s;
   launch_velocity_aos(c->g, c->u[(c->t + 1) & 1], (float*)c->scratch, c->stream);
@@ -1187,6 +1239,7 @@ RWMI_API rwmi_status rwmi_velocity(rwmi_ctx* c, float* out) {
 
 RWMI_API rwmi_status rwmi_density(rwmi_ctx* c, float* out) {
   if (!c || !out) return RWMI_E_INVALID;
+  GUARD(c);
   rwmi_status s = ensure_scratch(c, sizeof(float) * (size_t)c->ncell);
   if (s != RWMI_OK) return s;
   launch_density(c->cfg.q, c->cfg.storage, c->g, c->f[c->fcur], c->cfg.rho0, (float*)c->scratch, c->stream);
@@ -1197,6 +1250,7 @@ RWMI_API rwmi_status rwmi_density(rwmi_ctx* c, float* out) {
 
 RWMI_API rwmi_status rwmi_populations(rwmi_ctx* c, double* out) {
   if (!c || !out) return RWMI_E_INVALID;
+  GUARD(c);
   const size_t bytes = sizeof(double) * (size_t)c->cfg.q * (size_t)c->ncell;
   rwmi_status s = ensure_scratch(c, bytes);
   if (s != RWMI_OK) return s;
@@ -1209,6 +1263,7 @@ RWMI_API rwmi_status rwmi_populations(rwmi_ctx* c, double* out) {
 
 RWMI_API rwmi_status rwmi_lattice(rwmi_ctx* c, int32_t* e, double* w, int32_t* q) {
   if (!c) return RWMI_E_INVALID;
+  GUARD(c);
   if (q) *q = c->cfg.q;
   if (e && w) lattice_table(c->cfg.q, e, w);
   return RWMI_OK;
@@ -1216,6 +1271,7 @@ RWMI_API rwmi_status rwmi_lattice(rwmi_ctx* c, int32_t* e, double* w, int32_t* q
 
 RWMI_API rwmi_status rwmi_solid(rwmi_ctx* c, int32_t* count, int32_t* owner) {
   if (!c || !count || !owner) return RWMI_E_INVALID;
+  GUARD(c);
   const int par = (int)(c->t & 1);
   const size_t bytes = sizeof(int32_t) * 2 * (size_t)c->ncell;
   rwmi_status s = ensure_scratch(c, bytes);
@@ -1231,6 +1287,7 @@ RWMI_API rwmi_status rwmi_solid(rwmi_ctx* c, int32_t* count, int32_t* owner) {
 
 RWMI_API rwmi_status rwmi_nodes(rwmi_ctx* c, int32_t* node) {
   if (!c || !node) return RWMI_E_INVALID;
+  GUARD(c);
   const int par = (int)(c->t & 1);
   const size_t n = (size_t)c->ncell;
   rwmi_status s = ensure_scratch(c, (sizeof(uint16_t) + sizeof(int32_t)) * n + 256);
@@ -1253,6 +1310,7 @@ RWMI_API rwmi_status rwmi_nodes(rwmi_ctx* c, int32_t* node) {
 
 RWMI_API rwmi_status rwmi_mass_momentum(rwmi_ctx* c, double out[4]) {
   if (!c || !out) return RWMI_E_INVALID;
+  GUARD(c);
   double v[4] = {0.0, 0.0, 0.0, 0.0};
   if (c->t > 0) {
     std::vector<double> slots((size_t)4 * RED_SLOTS);
@@ -1269,6 +1327,7 @@ RWMI_API rwmi_status rwmi_mass_momentum(rwmi_ctx* c, double out[4]) {
 
 RWMI_API rwmi_status rwmi_particle_forces(rwmi_ctx* c, double* out) {
   if (!c || (!out && c->P > 0)) return RWMI_E_INVALID;
+  GUARD(c);
   if (c->P == 0) return RWMI_OK;
   if (c->t == 0) {
     std::vector<double> z((size_t)6 * c->P, 0.0);
@@ -1280,6 +1339,7 @@ RWMI_API rwmi_status rwmi_particle_forces(rwmi_ctx* c, double* out) {
 
 RWMI_API rwmi_status rwmi_walkers(rwmi_ctx* c, float* out, float* x0) {
   if (!c || (!out && c->nw > 0)) return RWMI_E_INVALID;
+  GUARD(c);
   if (c->nw == 0) return RWMI_OK;
   rwmi_status s = copy_out(c, out, c->pos[c->pcur], sizeof(float4) * (size_t)c->nw);
   if (s != RWMI_OK) return s;
@@ -1294,6 +1354,7 @@ RWMI_API rwmi_status rwmi_walkers(rwmi_ctx* c, float* out, float* x0) {
 
 RWMI_API rwmi_status rwmi_counters(rwmi_ctx* c, int64_t out[12]) {
   if (!c || !out) return RWMI_E_INVALID;
+  GUARD(c);
   CK(cudaStreamSynchronize(c->stream));
   unsigned long long st[ST_COUNT];
   CK(copy_now(c, st, c->status, sizeof(st)));
@@ -1307,6 +1368,7 @@ RWMI_API rwmi_status rwmi_counters(rwmi_ctx* c, int64_t out[12]) {
 
 RWMI_API rwmi_status rwmi_save(rwmi_ctx* c, const char* path) {
   if (!c || !path) return RWMI_E_INVALID;
+  GUARD(c);
   CK(cudaStreamSynchronize(c->stream));
   const size_t pop = (size_t)c->cfg.q * c->g.ncell_pad * storage_bytes(c->cfg.storage);
   std::vector<char> f(pop);
@@ -1343,6 +1405,7 @@ RWMI_API rwmi_status rwmi_save(rwmi_ctx* c, const char* path) {
 
 RWMI_API rwmi_status rwmi_load(rwmi_ctx* c, const char* path) {
   if (!c || !path) return RWMI_E_INVALID;
+  GUARD(c);
   FILE* fp = std::fopen(path, "rb");
   if (!fp) return fail(c, RWMI_E_INVALID, std::string("rwmi_load: cannot open ") + path);
   int64_t hdr[10];
@@ -1408,6 +1471,7 @@ RWMI_API rwmi_status rwmi_load(rwmi_ctx* c, const char* path) {
 
 RWMI_API rwmi_status rwmi_brick_stats(rwmi_ctx* c, int64_t out[4]) {
   if (!c || !out) return RWMI_E_INVALID;
+  GUARD(c);
   std::vector<uint32_t> w((size_t)c->nbrick + 1);
   CK(cudaStreamSynchronize(c->stream));
   CK(copy_now(c, w.data(), c->bword[c->t & 1], sizeof(uint32_t) * w.size()));
@@ -1443,6 +1507,7 @@ RWMI_API rwmi_status rwmi_batch_create(rwmi_batch** out, rwmi_ctx* const* ctxs, 
   rwmi_batch* b = new rwmi_batch();
   for (int32_t k = 0; k < n; ++k) {
     if (!ctxs[k]) { delete b; return RWMI_E_INVALID; }
+    if (ctxs[k]->broken) { delete b; return RWMI_E_STATE; }
     b->ctxs.push_back(ctxs[k]);
   }
   b->L = chunk_length(ctxs[0]);
@@ -1468,8 +1533,10 @@ RWMI_API rwmi_status rwmi_batch_create(rwmi_batch** out, rwmi_ctx* const* ctxs, 
 RWMI_API rwmi_status rwmi_batch_step(rwmi_batch* b, int32_t nsteps) {
   if (!b || nsteps < 0) return RWMI_E_INVALID;
   if (nsteps % b->L != 0) return batch_fail(b, RWMI_E_INVALID, "rwmi_batch_step: steps must be a multiple of the chunk");
-  for (rwmi_ctx* c : b->ctxs)
+  for (rwmi_ctx* c : b->ctxs) {
+    if (c->broken) return batch_fail(b, RWMI_E_STATE, "rwmi_batch_step: a context failed earlier: " + c->err);
     if (c->t % b->L != 0) return batch_fail(b, RWMI_E_STATE, "rwmi_batch_step: a context is not at a chunk boundary");
+  }
   // the contexts' own queued work precedes the batch
   for (rwmi_ctx* c : b->ctxs) {
     BCK(cudaEventRecord(b->done, c->stream));
@@ -1544,6 +1611,14 @@ RWMI_API const char* rwmi_batch_last_error(const rwmi_batch* b) { return b ? b->
 RWMI_API const char* rwmi_last_error(const rwmi_ctx* c) { return c ? c->err.c_str() : noalloc_last_error(); }
 
 RWMI_API int64_t rwmi_launch_count(const rwmi_ctx* c) { return c ? c->launches : 0; }
+
+RWMI_API int64_t rwmi_inject_alloc_failure(int64_t after) {
+  const int64_t now = g_alloc_count.load();
+  g_fail_at.store(after < 0 ? -1 : now + after);
+  return now;
+}
+
+RWMI_API int64_t rwmi_alloc_count(void) { return g_alloc_count.load(); }
 
 RWMI_API void rwmi_destroy(rwmi_ctx* c) {
   if (!c) return;

@@ -29,7 +29,8 @@ EXPORTED = ["rwmi_config_defaults", "rwmi_create", "rwmi_configure", "rwmi_set_s
             "rwmi_load", "rwmi_brick_stats", "rwmi_bin_walkers_noalloc", "rwmi_last_error",
             "rwmi_launch_count", "rwmi_destroy", "rwmi_batch_create", "rwmi_batch_step", "rwmi_batch_sync",
             "rwmi_batch_last_error", "rwmi_batch_destroy", "rwmi_dem_defaults", "rwmi_set_dem",
-            "rwmi_particle_state", "rwmi_set_particle_state", "rwmi_particle_mass"]
+            "rwmi_particle_state", "rwmi_set_particle_state", "rwmi_particle_mass",
+            "rwmi_inject_alloc_failure", "rwmi_alloc_count"]
 
 
 class RwmiError(RuntimeError):
@@ -133,10 +134,15 @@ def load(build_if_missing: bool = False):
     L.rwmi_particle_state.argtypes = [P, vp]
     L.rwmi_particle_mass.argtypes = [P, vp]
     L.rwmi_set_particle_state.argtypes = [P, vp]
+    L.rwmi_inject_alloc_failure.argtypes = [C.c_int64]
+    L.rwmi_inject_alloc_failure.restype = C.c_int64
+    L.rwmi_alloc_count.argtypes = []
+    L.rwmi_alloc_count.restype = C.c_int64
     for name in EXPORTED:
         fn = getattr(L, name)
         if name not in ("rwmi_config_defaults", "rwmi_last_error", "rwmi_launch_count", "rwmi_destroy",
-                        "rwmi_batch_last_error", "rwmi_batch_destroy", "rwmi_dem_defaults"):
+                        "rwmi_batch_last_error", "rwmi_batch_destroy", "rwmi_dem_defaults",
+                        "rwmi_inject_alloc_failure", "rwmi_alloc_count"):
             fn.restype = C.c_int
     _lib = L
     return L
@@ -162,6 +168,17 @@ def footprint(dims, q, storage, n_walkers, n_particles, n_centers) -> int:
     if st != 0:
         raise RwmiError(st, "rwmi_footprint: bad sizes")
     return int(out.value)
+
+
+def inject_alloc_failure(after: int) -> int:
+    """rwmi_inject_alloc_failure: the device allocation `after` allocations from now reports
+    RWMI_E_OOM without reaching the allocator (after < 0 disarms). Returns the count so far."""
+    return int(load().rwmi_inject_alloc_failure(int(after)))
+
+
+def alloc_count() -> int:
+    """rwmi_alloc_count: device allocations made (or refused by injection) in this process."""
+    return int(load().rwmi_alloc_count())
 
 
 def bin_walkers_noalloc(dims, wall_mask, pos, counts, pos_sorted=None, stream=None):
@@ -209,7 +226,11 @@ class Simulation:
         cfg.lbm_block = int(lbm_block)
         cfg.overlap = int(overlap)
         cfg.coupling = int(coupling)
-        self._check(L.rwmi_configure(self._h, C.byref(cfg)))
+        try:
+            self._check(L.rwmi_configure(self._h, C.byref(cfg)))
+        except RwmiError:
+            self.close()
+            raise
         self.q = int(q)
         _live.add(self)
         if stream is not None:

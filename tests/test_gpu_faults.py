@@ -5,6 +5,10 @@
   rwmi_sync reports RWMI_E_NONFINITE.
 - A served request cancelled while it runs is closed between chunks; the other requests finish
   with the results they have when run alone.
+- Each device allocation in turn is made to fail on the host (rwmi_inject_alloc_failure, which
+  never reaches the CUDA allocator): the call reports RWMI_E_OOM, the context is fenced (later
+  calls return RWMI_E_STATE and keep the first message), it is destroyed as far as it was
+  built, and a clean run afterwards gives the same results bit for bit.
 """
 import os
 
@@ -76,3 +80,67 @@ def test_cancelled_request_leaves_the_others_intact():
             alone = collect(s, r.workload)
         assert np.array_equal(alone["c"], rec.result["c"])
         assert np.array_equal(alone["u"], rec.result["u"])
+
+
+def _run_all(w, keep):
+    """Create, configure, particles (and free DEM), walkers, 4 steps and the outputs, one call
+    at a time; the context goes into `keep` as soon as it exists."""
+    from paper_2308_05007_gb300.rwmi import Simulation
+    s = Simulation(w.dims, w.tau, w.D, w.seed, q=w.q, storage=w.storage, wall_mask=w.wall_mask,
+                   body_force=w.body_force, force_period=w.force_period, rho0=w.rho0,
+                   init_velocity=w.init_velocity, sort_interval=4, moment_interval=4,
+                   coupling=getattr(w, "coupling", 0))
+    keep.append(s)
+    s.set_metaballs(w.metaballs)
+    if getattr(w, "dem", None) is not None:
+        s.set_dem(w.dem)
+    s.seed_walkers(w.n_walkers, *w.walker_box)
+    s.step(4)
+    s.sync()
+    pos, x0 = s.walkers_by_id()     # by walker id: the order within a cell is not fixed
+    return dict(c=s.concentration(), u=s.velocity(), f=s.populations(), x=pos, x0=x0)
+
+
+@pytest.mark.parametrize("kind", ["psm", "ibb_dem"])
+def test_every_allocation_failure_is_reported_and_fences_the_context(kind):
+    _need_gpu()
+    from paper_2308_05007_gb300 import inputs as I
+    from paper_2308_05007_gb300 import rwmi as R
+    if kind == "psm":
+        w = I.ragged(n_walkers=500)
+    else:
+        w = I.with_(I.dem_box(n_particles=3, n_walkers=500), coupling=1)
+    R.inject_alloc_failure(-1)
+    keep = []
+    n0 = R.alloc_count()
+    ref = _run_all(w, keep)
+    n_alloc = R.alloc_count() - n0
+    keep.pop().close()
+    assert n_alloc > 20
+    fenced = 0
+    for k in range(n_alloc):
+        keep = []
+        R.inject_alloc_failure(k)
+        try:
+            with pytest.raises(R.RwmiError) as e:
+                _run_all(w, keep)
+        finally:
+            R.inject_alloc_failure(-1)
+        assert e.value.status == -2, (k, str(e.value))
+        if keep:
+            s = keep[0]
+            msg = s._L.rwmi_last_error(s._h).decode()
+            assert "out of memory" in msg, msg
+            for call in (lambda: s.step(1), s.sync, s.velocity):
+                with pytest.raises(R.RwmiError) as e2:
+                    call()
+                assert e2.value.status == -6, (k, str(e2.value))
+            assert s._L.rwmi_last_error(s._h).decode() == msg
+            s.close()
+            fenced += 1
+    assert fenced > 0
+    again = []
+    res = _run_all(w, again)
+    again.pop().close()
+    for key in ref:
+        assert np.array_equal(ref[key], res[key]), key
