@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <exception>
 #include <map>
 #include <string>
 #include <vector>
@@ -138,6 +139,12 @@ rwmi_status fail(rwmi_ctx* c, rwmi_status s, const std::string& msg) {
     if (s == RWMI_E_OOM || s == RWMI_E_CUDA) c->broken = true;
   }
   return s;
+}
+
+// A C++ exception (host memory: std::bad_alloc, std::length_error) never crosses the C ABI: each
+// entry point turns it into RWMI_E_OOM, which fences the context like a device allocation failure.
+rwmi_status api_exception(rwmi_ctx* c, const char* fn, const std::exception& e) {
+  return fail(c, RWMI_E_OOM, std::string(fn) + ": host allocation failed (" + e.what() + ")");
 }
 
 // A context fenced by an earlier failure refuses the call; its message stays the first failure's.
@@ -607,7 +614,7 @@ RWMI_API void rwmi_config_defaults(rwmi_config* cfg) {
 }
 
 RWMI_API rwmi_status rwmi_create(rwmi_ctx** out, const int32_t dims[3], double tau, double D,
-                                 uint64_t seed) {
+                                 uint64_t seed) try {
   if (!out || !dims) return RWMI_E_INVALID;
   *out = nullptr;
   int64_t ncell = 1;
@@ -638,54 +645,59 @@ RWMI_API rwmi_status rwmi_create(rwmi_ctx** out, const int32_t dims[3], double t
   make_divisor(g.nxy, g.mxy, g.sxy);
   c->nbrick = (uint32_t)g.nb[0] * g.nb[1] * g.nb[2];
   update_margin(c);
-  rwmi_status st = [&]() -> rwmi_status {
-    CK(cudaGetDevice(&c->device));
-    CK(cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->device));
-    CK(cudaStreamCreate(&c->stream));
-    c->own_stream = true;
-    rwmi_status s = alloc_fluid(c);
-    if (s != RWMI_OK) return s;
-    for (int k = 0; k < 2; ++k) CK(dalloc(c, &c->u[k], sizeof(float4) * (size_t)g.ncell_pad));
-    for (int k = 0; k < 2; ++k) CK(dalloc(c, &c->solid[k], sizeof(uint16_t) * (size_t)ncell));
-    for (int k = 0; k < 2; ++k) CK(dalloc(c, &c->node[k], sizeof(uint16_t) * (size_t)ncell));
-    CK(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
-    CK(cudaStreamCreateWithFlags(&c->wst, cudaStreamNonBlocking));
-    for (cudaEvent_t* e : {&c->fork_ev, &c->join_ev, &c->fluid_ev, &c->walk_ev[0], &c->walk_ev[1]})
-      CK(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
-    CK(dalloc(c, &c->d_T, sizeof(int64_t)));
-    CK(dalloc(c, &c->wlist_n, sizeof(unsigned int) * 2 * WLIST_STRIPES));
-    CK(cudaMemsetAsync(c->wlist_n, 0, sizeof(unsigned int) * 2 * WLIST_STRIPES, c->stream));
-    CK(dalloc(c, &c->status, sizeof(unsigned long long) * ST_COUNT));
-    CK(dalloc(c, &c->macc, sizeof(double) * 12));
-    CK(dalloc(c, &c->series, sizeof(double) * (size_t)SERIES_ROWS * SERIES_COLS));
-    CK(dalloc(c, &c->mrow, sizeof(double) * SERIES_COLS));
-    CK(dalloc(c, &c->counts, sizeof(uint32_t) * (size_t)ncell));
-    for (int k = 0; k < 2; ++k) CK(dalloc(c, &c->wmask[k], sizeof(uint64_t) * c->nbrick));
-    CK(dalloc(c, &c->offsets, sizeof(uint32_t) * (size_t)ncell));
-    CK(dalloc(c, &c->bsums, sizeof(uint32_t) * scan_block_sums_size((uint32_t)ncell)));
-    for (int k = 0; k < 2; ++k) {
-      CK(dalloc(c, &c->bword[k], sizeof(uint32_t) * (c->nbrick + BWORD_EXTRA)));
-      CK(dalloc(c, &c->bcand[k], sizeof(uint16_t) * (size_t)c->nbrick * MAXC));
-      CK(dalloc(c, &c->rlist[k], sizeof(int32_t) * c->nbrick));
-      CK(dalloc(c, &c->sp[k], sizeof(StepParams)));
-      CK(cudaMemsetAsync(c->sp[k], 0, sizeof(StepParams), c->stream));
-    }
-    CK(dalloc(c, &c->desc, sizeof(ParticleDesc)));
-    CK(dalloc(c, &c->cbody, sizeof(float4)));
-    s = alloc_particles(c);
-    if (s != RWMI_OK) return s;
-    CK(cudaMemsetAsync(c->d_T, 0, sizeof(int64_t), c->stream));
-    CK(cudaMemsetAsync(c->status, 0, sizeof(unsigned long long) * ST_COUNT, c->stream));
-    CK(cudaMemsetAsync(c->macc, 0, sizeof(double) * 12, c->stream));
-    for (int k = 0; k < 2; ++k) CK(cudaMemsetAsync(c->solid[k], 0, sizeof(uint16_t) * (size_t)ncell, c->stream));
-    for (int k = 0; k < 2; ++k) CK(cudaMemsetAsync(c->node[k], 0, sizeof(uint16_t) * (size_t)ncell, c->stream));
-    s = reset_fluid(c);
-    if (s != RWMI_OK) return s;
-    s = build_current_frame(c);
-    if (s != RWMI_OK) return s;
-    CK(cudaStreamSynchronize(c->stream));
-    return RWMI_OK;
-  }();
+  rwmi_status st = RWMI_OK;
+  try {
+    st = [&]() -> rwmi_status {
+      CK(cudaGetDevice(&c->device));
+      CK(cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->device));
+      CK(cudaStreamCreate(&c->stream));
+      c->own_stream = true;
+      rwmi_status s = alloc_fluid(c);
+      if (s != RWMI_OK) return s;
+      for (int k = 0; k < 2; ++k) CK(dalloc(c, &c->u[k], sizeof(float4) * (size_t)g.ncell_pad));
+      for (int k = 0; k < 2; ++k) CK(dalloc(c, &c->solid[k], sizeof(uint16_t) * (size_t)ncell));
+      for (int k = 0; k < 2; ++k) CK(dalloc(c, &c->node[k], sizeof(uint16_t) * (size_t)ncell));
+      CK(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+      CK(cudaStreamCreateWithFlags(&c->wst, cudaStreamNonBlocking));
+      for (cudaEvent_t* e : {&c->fork_ev, &c->join_ev, &c->fluid_ev, &c->walk_ev[0], &c->walk_ev[1]})
+        CK(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+      CK(dalloc(c, &c->d_T, sizeof(int64_t)));
+      CK(dalloc(c, &c->wlist_n, sizeof(unsigned int) * 2 * WLIST_STRIPES));
+      CK(cudaMemsetAsync(c->wlist_n, 0, sizeof(unsigned int) * 2 * WLIST_STRIPES, c->stream));
+      CK(dalloc(c, &c->status, sizeof(unsigned long long) * ST_COUNT));
+      CK(dalloc(c, &c->macc, sizeof(double) * 12));
+      CK(dalloc(c, &c->series, sizeof(double) * (size_t)SERIES_ROWS * SERIES_COLS));
+      CK(dalloc(c, &c->mrow, sizeof(double) * SERIES_COLS));
+      CK(dalloc(c, &c->counts, sizeof(uint32_t) * (size_t)ncell));
+      for (int k = 0; k < 2; ++k) CK(dalloc(c, &c->wmask[k], sizeof(uint64_t) * c->nbrick));
+      CK(dalloc(c, &c->offsets, sizeof(uint32_t) * (size_t)ncell));
+      CK(dalloc(c, &c->bsums, sizeof(uint32_t) * scan_block_sums_size((uint32_t)ncell)));
+      for (int k = 0; k < 2; ++k) {
+        CK(dalloc(c, &c->bword[k], sizeof(uint32_t) * (c->nbrick + BWORD_EXTRA)));
+        CK(dalloc(c, &c->bcand[k], sizeof(uint16_t) * (size_t)c->nbrick * MAXC));
+        CK(dalloc(c, &c->rlist[k], sizeof(int32_t) * c->nbrick));
+        CK(dalloc(c, &c->sp[k], sizeof(StepParams)));
+        CK(cudaMemsetAsync(c->sp[k], 0, sizeof(StepParams), c->stream));
+      }
+      CK(dalloc(c, &c->desc, sizeof(ParticleDesc)));
+      CK(dalloc(c, &c->cbody, sizeof(float4)));
+      s = alloc_particles(c);
+      if (s != RWMI_OK) return s;
+      CK(cudaMemsetAsync(c->d_T, 0, sizeof(int64_t), c->stream));
+      CK(cudaMemsetAsync(c->status, 0, sizeof(unsigned long long) * ST_COUNT, c->stream));
+      CK(cudaMemsetAsync(c->macc, 0, sizeof(double) * 12, c->stream));
+      for (int k = 0; k < 2; ++k) CK(cudaMemsetAsync(c->solid[k], 0, sizeof(uint16_t) * (size_t)ncell, c->stream));
+      for (int k = 0; k < 2; ++k) CK(cudaMemsetAsync(c->node[k], 0, sizeof(uint16_t) * (size_t)ncell, c->stream));
+      s = reset_fluid(c);
+      if (s != RWMI_OK) return s;
+      s = build_current_frame(c);
+      if (s != RWMI_OK) return s;
+      CK(cudaStreamSynchronize(c->stream));
+      return RWMI_OK;
+    }();
+  } catch (const std::exception& e_) {
+    st = api_exception(c, "rwmi_create", e_);
+  }
   if (st != RWMI_OK) {
     const std::string msg = c->err;
     rwmi_destroy(c);
@@ -694,9 +706,11 @@ RWMI_API rwmi_status rwmi_create(rwmi_ctx** out, const int32_t dims[3], double t
   }
   *out = c;
   return RWMI_OK;
+} catch (const std::exception& e_) {
+  return RWMI_E_OOM;
 }
 
-RWMI_API rwmi_status rwmi_configure(rwmi_ctx* c, const rwmi_config* cfg) {
+RWMI_API rwmi_status rwmi_configure(rwmi_ctx* c, const rwmi_config* cfg) try {
   if (!c || !cfg) return RWMI_E_INVALID;
   GUARD(c);
   if (c->stepped) return fail(c, RWMI_E_STATE, "rwmi_configure: only before the first step");
@@ -737,9 +751,11 @@ RWMI_API rwmi_status rwmi_configure(rwmi_ctx* c, const rwmi_config* cfg) {
   if (s != RWMI_OK) return s;
   CK(cudaStreamSynchronize(c->stream));
   return RWMI_OK;
+} catch (const std::exception& e_) {
+  return api_exception(c, "rwmi_configure", e_);
 }
 
-RWMI_API rwmi_status rwmi_set_stream(rwmi_ctx* c, void* stream) {
+RWMI_API rwmi_status rwmi_set_stream(rwmi_ctx* c, void* stream) try {
   if (!c) return RWMI_E_INVALID;
   GUARD(c);
   CK(cudaStreamSynchronize(c->stream));
@@ -749,11 +765,13 @@ RWMI_API rwmi_status rwmi_set_stream(rwmi_ctx* c, void* stream) {
   c->stream = (cudaStream_t)stream;
   drop_graphs(c);
   return RWMI_OK;
+} catch (const std::exception& e_) {
+  return api_exception(c, "rwmi_set_stream", e_);
 }
 
 RWMI_API rwmi_status rwmi_set_metaballs(rwmi_ctx* c, int32_t P, const int32_t* coff, const float* cb,
                                         const float* k, const double* origin, const double* amplitude,
-                                        const double* period, const double* phase, const double* omega) {
+                                        const double* period, const double* phase, const double* omega) try {
   if (!c) return RWMI_E_INVALID;
   GUARD(c);
   if (c->stepped) return fail(c, RWMI_E_STATE, "rwmi_set_metaballs: only before the first step");
@@ -812,6 +830,8 @@ RWMI_API rwmi_status rwmi_set_metaballs(rwmi_ctx* c, int32_t P, const int32_t* c
   if (s != RWMI_OK) return s;
   CK(cudaStreamSynchronize(c->stream));
   return RWMI_OK;
+} catch (const std::exception& e_) {
+  return api_exception(c, "rwmi_set_metaballs", e_);
 }
 
 RWMI_API void rwmi_dem_defaults(rwmi_dem_config* cfg) {
@@ -823,7 +843,7 @@ RWMI_API void rwmi_dem_defaults(rwmi_dem_config* cfg) {
 }
 
 RWMI_API rwmi_status rwmi_set_dem(rwmi_ctx* c, const rwmi_dem_config* cfg, const double* density,
-                                  const double* Rs, const double* vel, const double* spin) {
+                                  const double* Rs, const double* vel, const double* spin) try {
   if (!c || !cfg) return RWMI_E_INVALID;
   GUARD(c);
   if (c->P < 1 || !density || !Rs) return fail(c, RWMI_E_INVALID, "rwmi_set_dem: no particles or null array");
@@ -916,25 +936,31 @@ RWMI_API rwmi_status rwmi_set_dem(rwmi_ctx* c, const rwmi_dem_config* cfg, const
   CK(cudaStreamSynchronize(c->stream));
   CK(cudaGetLastError());
   return RWMI_OK;
+} catch (const std::exception& e_) {
+  return api_exception(c, "rwmi_set_dem", e_);
 }
 
-RWMI_API rwmi_status rwmi_particle_mass(rwmi_ctx* c, double* out) {
+RWMI_API rwmi_status rwmi_particle_mass(rwmi_ctx* c, double* out) try {
   if (!c || !out) return RWMI_E_INVALID;
   GUARD(c);
   if (!c->dem) return fail(c, RWMI_E_STATE, "rwmi_particle_mass: no free DEM (rwmi_set_dem)");
   CK(copy_now(c, out, dem_props(c), sizeof(double) * 10 * (size_t)c->P));
   return RWMI_OK;
+} catch (const std::exception& e_) {
+  return api_exception(c, "rwmi_particle_mass", e_);
 }
 
-RWMI_API rwmi_status rwmi_particle_state(rwmi_ctx* c, double* out) {
+RWMI_API rwmi_status rwmi_particle_state(rwmi_ctx* c, double* out) try {
   if (!c || !out) return RWMI_E_INVALID;
   GUARD(c);
   if (!c->dem) return fail(c, RWMI_E_STATE, "rwmi_particle_state: no free DEM (rwmi_set_dem)");
   CK(copy_now(c, out, c->dem_d, sizeof(double) * 13 * (size_t)c->P));
   return RWMI_OK;
+} catch (const std::exception& e_) {
+  return api_exception(c, "rwmi_particle_state", e_);
 }
 
-RWMI_API rwmi_status rwmi_set_particle_state(rwmi_ctx* c, const double* state) {
+RWMI_API rwmi_status rwmi_set_particle_state(rwmi_ctx* c, const double* state) try {
   if (!c || !state) return RWMI_E_INVALID;
   GUARD(c);
   if (!c->dem) return fail(c, RWMI_E_STATE, "rwmi_set_particle_state: no free DEM (rwmi_set_dem)");
@@ -946,9 +972,11 @@ RWMI_API rwmi_status rwmi_set_particle_state(rwmi_ctx* c, const double* state) {
   if (r != RWMI_OK) return r;
   CK(cudaStreamSynchronize(c->stream));
   return RWMI_OK;
+} catch (const std::exception& e_) {
+  return api_exception(c, "rwmi_set_particle_state", e_);
 }
 
-RWMI_API rwmi_status rwmi_seed_walkers(rwmi_ctx* c, int64_t n, const double lo[3], const double hi[3]) {
+RWMI_API rwmi_status rwmi_seed_walkers(rwmi_ctx* c, int64_t n, const double lo[3], const double hi[3]) try {
   if (!c || !lo || !hi) return RWMI_E_INVALID;
   GUARD(c);
   if (n < 0 || n > 0x7fffffffLL) return fail(c, RWMI_E_INVALID, "rwmi_seed_walkers: 0 <= n < 2^31");
@@ -972,9 +1000,11 @@ RWMI_API rwmi_status rwmi_seed_walkers(rwmi_ctx* c, int64_t n, const double lo[3
   if (st[ST_SEED_FAIL] > before)
     return fail(c, RWMI_W_SEED, "rwmi_seed_walkers: some walkers found no free point in 1000 draws");
   return RWMI_OK;
+} catch (const std::exception& e_) {
+  return api_exception(c, "rwmi_seed_walkers", e_);
 }
 
-RWMI_API rwmi_status rwmi_set_walkers(rwmi_ctx* c, int64_t n, const float* pos) {
+RWMI_API rwmi_status rwmi_set_walkers(rwmi_ctx* c, int64_t n, const float* pos) try {
   if (!c || (n > 0 && !pos)) return RWMI_E_INVALID;
   GUARD(c);
   if (n < 0 || n > 0x7fffffffLL) return fail(c, RWMI_E_INVALID, "rwmi_set_walkers: 0 <= n < 2^31");
@@ -999,9 +1029,11 @@ RWMI_API rwmi_status rwmi_set_walkers(rwmi_ctx* c, int64_t n, const float* pos) 
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(c->stream));
   return RWMI_OK;
+} catch (const std::exception& e_) {
+  return api_exception(c, "rwmi_set_walkers", e_);
 }
 
-RWMI_API rwmi_status rwmi_step(rwmi_ctx* c, int32_t n) {
+RWMI_API rwmi_status rwmi_step(rwmi_ctx* c, int32_t n) try {
   if (!c || n < 0) return RWMI_E_INVALID;
   GUARD(c);
   c->stepped = true;
@@ -1040,9 +1072,11 @@ RWMI_API rwmi_status rwmi_step(rwmi_ctx* c, int32_t n) {
   }
   CK(cudaGetLastError());
   return RWMI_OK;
+} catch (const std::exception& e_) {
+  return api_exception(c, "rwmi_step", e_);
 }
 
-RWMI_API rwmi_status rwmi_step_timed(rwmi_ctx* c, int32_t n, double* phase_ms) {
+RWMI_API rwmi_status rwmi_step_timed(rwmi_ctx* c, int32_t n, double* phase_ms) try {
   if (!c || n < 0 || !phase_ms) return RWMI_E_INVALID;
   GUARD(c);
   c->stepped = true;
@@ -1065,9 +1099,11 @@ RWMI_API rwmi_status rwmi_step_timed(rwmi_ctx* c, int32_t n, double* phase_ms) {
   c->timing = false;
   CK(cudaGetLastError());
   return RWMI_OK;
+} catch (const std::exception& e_) {
+  return api_exception(c, "rwmi_step_timed", e_);
 }
 
-RWMI_API rwmi_status rwmi_autotune(rwmi_ctx* c, int32_t* chosen) {
+RWMI_API rwmi_status rwmi_autotune(rwmi_ctx* c, int32_t* chosen) try {
   if (!c) return RWMI_E_INVALID;
   GUARD(c);
   const int tp = (int)(c->t & 1);
@@ -1123,19 +1159,23 @@ RWMI_API rwmi_status rwmi_autotune(rwmi_ctx* c, int32_t* chosen) {
   drop_graphs(c);
   if (chosen) *chosen = best;
   return RWMI_OK;
+} catch (const std::exception& e_) {
+  return api_exception(c, "rwmi_autotune", e_);
 }
 
-RWMI_API rwmi_status rwmi_query(rwmi_ctx* c) {
+RWMI_API rwmi_status rwmi_query(rwmi_ctx* c) try {
   if (!c) return RWMI_E_INVALID;
   GUARD(c);
   const cudaError_t e = cudaStreamQuery(c->stream);
   if (e == cudaErrorNotReady) return RWMI_BUSY;
   CK(e);
   return RWMI_OK;
+} catch (const std::exception& e_) {
+  return api_exception(c, "rwmi_query", e_);
 }
 
 RWMI_API rwmi_status rwmi_footprint(const int32_t dims[3], int32_t q, int32_t storage, int64_t n_walkers,
-                                    int32_t n_particles, int32_t n_centers, uint64_t* bytes) {
+                                    int32_t n_particles, int32_t n_centers, uint64_t* bytes) try {
   if (!dims || !bytes || (q != 15 && q != 19) || storage < 0 || storage > 3 || n_walkers < 0 ||
       n_particles < 0 || n_centers < 0)
     return RWMI_E_INVALID;
@@ -1155,9 +1195,11 @@ RWMI_API rwmi_status rwmi_footprint(const int32_t dims[3], int32_t q, int32_t st
   b += (uint64_t)SERIES_ROWS * SERIES_COLS * 8 + 4096;         // moment series, counters
   *bytes = b;
   return RWMI_OK;
+} catch (const std::exception& e_) {
+  return RWMI_E_OOM;
 }
 
-RWMI_API rwmi_status rwmi_sync(rwmi_ctx* c) {
+RWMI_API rwmi_status rwmi_sync(rwmi_ctx* c) try {
   if (!c) return RWMI_E_INVALID;
   GUARD(c);
   CK(cudaStreamSynchronize(c->stream));
@@ -1169,24 +1211,30 @@ RWMI_API rwmi_status rwmi_sync(rwmi_ctx* c) {
     r = fail(c, RWMI_W_BISECT, "Algorithm 1 or the refill found no surface point for some walker");
   std::memcpy(c->status_seen, st, sizeof(st));
   return r;
+} catch (const std::exception& e_) {
+  return api_exception(c, "rwmi_sync", e_);
 }
 
-RWMI_API rwmi_status rwmi_time(rwmi_ctx* c, int64_t* t) {
+RWMI_API rwmi_status rwmi_time(rwmi_ctx* c, int64_t* t) try {
   if (!c || !t) return RWMI_E_INVALID;
   GUARD(c);
   *t = c->t;
   return RWMI_OK;
+} catch (const std::exception& e_) {
+  return api_exception(c, "rwmi_time", e_);
 }
 
-RWMI_API rwmi_status rwmi_info(rwmi_ctx* c, int64_t out[8]) {
+RWMI_API rwmi_status rwmi_info(rwmi_ctx* c, int64_t out[8]) try {
   if (!c || !out) return RWMI_E_INVALID;
   GUARD(c);
   const int64_t v[8] = {c->n[0], c->n[1], c->n[2], c->cfg.q, c->cfg.storage, c->nw, c->P, c->t};
   std::memcpy(out, v, sizeof(v));
   return RWMI_OK;
+} catch (const std::exception& e_) {
+  return api_exception(c, "rwmi_info", e_);
 }
 
-RWMI_API rwmi_status rwmi_concentration(rwmi_ctx* c, uint32_t* out) {
+RWMI_API rwmi_status rwmi_concentration(rwmi_ctx* c, uint32_t* out) try {
   if (!c || !out) return RWMI_E_INVALID;
   GUARD(c);
   if (c->binned_t != c->t) {
@@ -1197,18 +1245,22 @@ RWMI_API rwmi_status rwmi_concentration(rwmi_ctx* c, uint32_t* out) {
     c->binned_t = c->t;
   }
   return copy_out(c, out, c->counts, sizeof(uint32_t) * (size_t)c->ncell);
+} catch (const std::exception& e_) {
+  return api_exception(c, "rwmi_concentration", e_);
 }
 
-RWMI_API rwmi_status rwmi_walker_moments(rwmi_ctx* c, double out[13]) {
+RWMI_API rwmi_status rwmi_walker_moments(rwmi_ctx* c, double out[13]) try {
   if (!c || !out) return RWMI_E_INVALID;
   GUARD(c);
   launch_moments(c->pos[c->pcur], c->x0[c->pcur], c->nw, c->macc, c->mrow, 0, 1, c->d_T, 0, c->stream);
   c->launches += c->nw > 0 ? 2 : 1;
   CK(cudaGetLastError());
   return copy_out(c, out, c->mrow + 1, sizeof(double) * 13);
+} catch (const std::exception& e_) {
+  return api_exception(c, "rwmi_walker_moments", e_);
 }
 
-RWMI_API rwmi_status rwmi_moment_series(rwmi_ctx* c, double* out, int32_t max_rows, int32_t* n_rows) {
+RWMI_API rwmi_status rwmi_moment_series(rwmi_ctx* c, double* out, int32_t max_rows, int32_t* n_rows) try {
   if (!c || !out || !n_rows || max_rows < 0) return RWMI_E_INVALID;
   GUARD(c);
   const int64_t avail = std::min<int64_t>(c->series_rows, SERIES_ROWS);
@@ -1224,9 +1276,11 @@ RWMI_API rwmi_status rwmi_moment_series(rwmi_ctx* c, double* out, int32_t max_ro
   if (take > 0) CK(copy_now(c, out, rows.data(), sizeof(double) * rows.size()));
   *n_rows = (int32_t)take;
   return RWMI_OK;
+} catch (const std::exception& e_) {
+  return api_exception(c, "rwmi_moment_series", e_);
 }
 
-RWMI_API rwmi_status rwmi_velocity(rwmi_ctx* c, float* out) {
+RWMI_API rwmi_status rwmi_velocity(rwmi_ctx* c, float* out) try {
   if (!c || !out) return RWMI_E_INVALID;
   GUARD(c);
   rwmi_status s = ensure_scratch(c, sizeof(float) * 3 * (size_t)c->ncell);
@@ -1235,9 +1289,11 @@ RWMI_API rwmi_status rwmi_velocity(rwmi_ctx* c, float* out) {
   c->launches++;
   CK(cudaGetLastError());
   return copy_out(c, out, c->scratch, sizeof(float) * 3 * (size_t)c->ncell);
+} catch (const std::exception& e_) {
+  return api_exception(c, "rwmi_velocity", e_);
 }
 
-RWMI_API rwmi_status rwmi_density(rwmi_ctx* c, float* out) {
+RWMI_API rwmi_status rwmi_density(rwmi_ctx* c, float* out) try {
   if (!c || !out) return RWMI_E_INVALID;
   GUARD(c);
   rwmi_status s = ensure_scratch(c, sizeof(float) * (size_t)c->ncell);
@@ -1246,9 +1302,11 @@ RWMI_API rwmi_status rwmi_density(rwmi_ctx* c, float* out) {
   c->launches++;
   CK(cudaGetLastError());
   return copy_out(c, out, c->scratch, sizeof(float) * (size_t)c->ncell);
+} catch (const std::exception& e_) {
+  return api_exception(c, "rwmi_density", e_);
 }
 
-RWMI_API rwmi_status rwmi_populations(rwmi_ctx* c, double* out) {
+RWMI_API rwmi_status rwmi_populations(rwmi_ctx* c, double* out) try {
   if (!c || !out) return RWMI_E_INVALID;
   GUARD(c);
   const size_t bytes = sizeof(double) * (size_t)c->cfg.q * (size_t)c->ncell;
@@ -1259,17 +1317,21 @@ RWMI_API rwmi_status rwmi_populations(rwmi_ctx* c, double* out) {
   c->launches++;
   CK(cudaGetLastError());
   return copy_out(c, out, c->scratch, bytes);
+} catch (const std::exception& e_) {
+  return api_exception(c, "rwmi_populations", e_);
 }
 
-RWMI_API rwmi_status rwmi_lattice(rwmi_ctx* c, int32_t* e, double* w, int32_t* q) {
+RWMI_API rwmi_status rwmi_lattice(rwmi_ctx* c, int32_t* e, double* w, int32_t* q) try {
   if (!c) return RWMI_E_INVALID;
   GUARD(c);
   if (q) *q = c->cfg.q;
   if (e && w) lattice_table(c->cfg.q, e, w);
   return RWMI_OK;
+} catch (const std::exception& e_) {
+  return api_exception(c, "rwmi_lattice", e_);
 }
 
-RWMI_API rwmi_status rwmi_solid(rwmi_ctx* c, int32_t* count, int32_t* owner) {
+RWMI_API rwmi_status rwmi_solid(rwmi_ctx* c, int32_t* count, int32_t* owner) try {
   if (!c || !count || !owner) return RWMI_E_INVALID;
   GUARD(c);
   const int par = (int)(c->t & 1);
@@ -1283,9 +1345,11 @@ RWMI_API rwmi_status rwmi_solid(rwmi_ctx* c, int32_t* count, int32_t* owner) {
   s = copy_out(c, count, tmp, sizeof(int32_t) * (size_t)c->ncell);
   if (s != RWMI_OK) return s;
   return copy_out(c, owner, tmp + c->ncell, sizeof(int32_t) * (size_t)c->ncell);
+} catch (const std::exception& e_) {
+  return api_exception(c, "rwmi_solid", e_);
 }
 
-RWMI_API rwmi_status rwmi_nodes(rwmi_ctx* c, int32_t* node) {
+RWMI_API rwmi_status rwmi_nodes(rwmi_ctx* c, int32_t* node) try {
   if (!c || !node) return RWMI_E_INVALID;
   GUARD(c);
   const int par = (int)(c->t & 1);
@@ -1306,9 +1370,11 @@ RWMI_API rwmi_status rwmi_nodes(rwmi_ctx* c, int32_t* node) {
   for (size_t k = 0; k < n; ++k) o[k] = h[k];
   CK(copy_now(c, node, o.data(), sizeof(int32_t) * n));
   return RWMI_OK;
+} catch (const std::exception& e_) {
+  return api_exception(c, "rwmi_nodes", e_);
 }
 
-RWMI_API rwmi_status rwmi_mass_momentum(rwmi_ctx* c, double out[4]) {
+RWMI_API rwmi_status rwmi_mass_momentum(rwmi_ctx* c, double out[4]) try {
   if (!c || !out) return RWMI_E_INVALID;
   GUARD(c);
   double v[4] = {0.0, 0.0, 0.0, 0.0};
@@ -1323,9 +1389,11 @@ RWMI_API rwmi_status rwmi_mass_momentum(rwmi_ctx* c, double out[4]) {
   out[1] = v[1]; out[2] = v[2]; out[3] = v[3];
   if (!std::isfinite(out[0])) return fail(c, RWMI_E_NONFINITE, "non-finite mass sum");
   return RWMI_OK;
+} catch (const std::exception& e_) {
+  return api_exception(c, "rwmi_mass_momentum", e_);
 }
 
-RWMI_API rwmi_status rwmi_particle_forces(rwmi_ctx* c, double* out) {
+RWMI_API rwmi_status rwmi_particle_forces(rwmi_ctx* c, double* out) try {
   if (!c || (!out && c->P > 0)) return RWMI_E_INVALID;
   GUARD(c);
   if (c->P == 0) return RWMI_OK;
@@ -1335,9 +1403,11 @@ RWMI_API rwmi_status rwmi_particle_forces(rwmi_ctx* c, double* out) {
     return RWMI_OK;
   }
   return copy_out(c, out, c->acc[(c->t - 1) & 1], sizeof(double) * 6 * (size_t)c->P);
+} catch (const std::exception& e_) {
+  return api_exception(c, "rwmi_particle_forces", e_);
 }
 
-RWMI_API rwmi_status rwmi_walkers(rwmi_ctx* c, float* out, float* x0) {
+RWMI_API rwmi_status rwmi_walkers(rwmi_ctx* c, float* out, float* x0) try {
   if (!c || (!out && c->nw > 0)) return RWMI_E_INVALID;
   GUARD(c);
   if (c->nw == 0) return RWMI_OK;
@@ -1350,9 +1420,11 @@ RWMI_API rwmi_status rwmi_walkers(rwmi_ctx* c, float* out, float* x0) {
     CK(cudaStreamSynchronize(c->stream));
   }
   return RWMI_OK;
+} catch (const std::exception& e_) {
+  return api_exception(c, "rwmi_walkers", e_);
 }
 
-RWMI_API rwmi_status rwmi_counters(rwmi_ctx* c, int64_t out[12]) {
+RWMI_API rwmi_status rwmi_counters(rwmi_ctx* c, int64_t out[12]) try {
   if (!c || !out) return RWMI_E_INVALID;
   GUARD(c);
   CK(cudaStreamSynchronize(c->stream));
@@ -1364,9 +1436,11 @@ RWMI_API rwmi_status rwmi_counters(rwmi_ctx* c, int64_t out[12]) {
   out[10] = (int64_t)st[ST_RESOLVED];
   out[11] = (int64_t)st[ST_RASTER_QUEUED];
   return RWMI_OK;
+} catch (const std::exception& e_) {
+  return api_exception(c, "rwmi_counters", e_);
 }
 
-RWMI_API rwmi_status rwmi_save(rwmi_ctx* c, const char* path) {
+RWMI_API rwmi_status rwmi_save(rwmi_ctx* c, const char* path) try {
   if (!c || !path) return RWMI_E_INVALID;
   GUARD(c);
   CK(cudaStreamSynchronize(c->stream));
@@ -1401,9 +1475,11 @@ RWMI_API rwmi_status rwmi_save(rwmi_ctx* c, const char* path) {
   ok = (std::fclose(fp) == 0) && ok;
   if (!ok) return fail(c, RWMI_E_INVALID, "rwmi_save: write failed");
   return RWMI_OK;
+} catch (const std::exception& e_) {
+  return api_exception(c, "rwmi_save", e_);
 }
 
-RWMI_API rwmi_status rwmi_load(rwmi_ctx* c, const char* path) {
+RWMI_API rwmi_status rwmi_load(rwmi_ctx* c, const char* path) try {
   if (!c || !path) return RWMI_E_INVALID;
   GUARD(c);
   FILE* fp = std::fopen(path, "rb");
@@ -1416,8 +1492,16 @@ RWMI_API rwmi_status rwmi_load(rwmi_ctx* c, const char* path) {
     return fail(c, RWMI_E_INVALID, "rwmi_load: checkpoint does not match this context");
   }
   const size_t pop = (size_t)c->cfg.q * c->g.ncell_pad * storage_bytes(c->cfg.storage);
-  std::vector<char> f(pop);
   const int64_t nw = hdr[6];
+  // A corrupt walker count is refused before anything is allocated: the file must hold it.
+  const long here = std::ftell(fp);
+  const long size = std::fseek(fp, 0, SEEK_END) == 0 ? std::ftell(fp) : -1L;
+  if (here < 0 || size < here || std::fseek(fp, here, SEEK_SET) != 0 || nw > 0x7fffffffLL ||
+      (uint64_t)(size - here) < (uint64_t)pop + 2 * sizeof(float4) * (uint64_t)nw) {
+    std::fclose(fp);
+    return fail(c, RWMI_E_INVALID, "rwmi_load: truncated checkpoint or corrupt walker count");
+  }
+  std::vector<char> f(pop);
   std::vector<float4> p((size_t)nw), q((size_t)nw);
   bool ok = std::fread(f.data(), 1, pop, fp) == pop;
   if (nw) ok = ok && std::fread(p.data(), sizeof(float4), p.size(), fp) == p.size() &&
@@ -1467,9 +1551,11 @@ RWMI_API rwmi_status rwmi_load(rwmi_ctx* c, const char* path) {
   if (s != RWMI_OK) return s;
   CK(cudaStreamSynchronize(c->stream));
   return RWMI_OK;
+} catch (const std::exception& e_) {
+  return api_exception(c, "rwmi_load", e_);
 }
 
-RWMI_API rwmi_status rwmi_brick_stats(rwmi_ctx* c, int64_t out[4]) {
+RWMI_API rwmi_status rwmi_brick_stats(rwmi_ctx* c, int64_t out[4]) try {
   if (!c || !out) return RWMI_E_INVALID;
   GUARD(c);
   std::vector<uint32_t> w((size_t)c->nbrick + 1);
@@ -1485,6 +1571,8 @@ RWMI_API rwmi_status rwmi_brick_stats(rwmi_ctx* c, int64_t out[4]) {
   }
   out[0] = rast; out[1] = walk; out[2] = mx; out[3] = over;
   return RWMI_OK;
+} catch (const std::exception& e_) {
+  return api_exception(c, "rwmi_brick_stats", e_);
 }
 
 static rwmi_status batch_fail(rwmi_batch* b, rwmi_status s, const std::string& msg) {
@@ -1501,7 +1589,7 @@ static rwmi_status batch_fail(rwmi_batch* b, rwmi_status s, const std::string& m
 
 RWMI_API void rwmi_batch_destroy(rwmi_batch* b);
 
-RWMI_API rwmi_status rwmi_batch_create(rwmi_batch** out, rwmi_ctx* const* ctxs, int32_t n) {
+RWMI_API rwmi_status rwmi_batch_create(rwmi_batch** out, rwmi_ctx* const* ctxs, int32_t n) try {
   if (!out || !ctxs || n < 1) return RWMI_E_INVALID;
   *out = nullptr;
   rwmi_batch* b = new rwmi_batch();
@@ -1528,9 +1616,11 @@ RWMI_API rwmi_status rwmi_batch_create(rwmi_batch** out, rwmi_ctx* const* ctxs, 
   if (st != RWMI_OK) { rwmi_batch_destroy(b); return st; }
   *out = b;
   return RWMI_OK;
+} catch (const std::exception& e_) {
+  return RWMI_E_OOM;
 }
 
-RWMI_API rwmi_status rwmi_batch_step(rwmi_batch* b, int32_t nsteps) {
+RWMI_API rwmi_status rwmi_batch_step(rwmi_batch* b, int32_t nsteps) try {
   if (!b || nsteps < 0) return RWMI_E_INVALID;
   if (nsteps % b->L != 0) return batch_fail(b, RWMI_E_INVALID, "rwmi_batch_step: steps must be a multiple of the chunk");
   for (rwmi_ctx* c : b->ctxs) {
@@ -1581,9 +1671,11 @@ RWMI_API rwmi_status rwmi_batch_step(rwmi_batch* b, int32_t nsteps) {
   BCK(cudaEventRecord(b->done, b->origin));
   for (rwmi_ctx* c : b->ctxs) BCK(cudaStreamWaitEvent(c->stream, b->done, 0));
   return RWMI_OK;
+} catch (const std::exception& e_) {
+  return batch_fail(b, RWMI_E_OOM, std::string("rwmi_batch_step: ") + e_.what());
 }
 
-RWMI_API rwmi_status rwmi_batch_sync(rwmi_batch* b) {
+RWMI_API rwmi_status rwmi_batch_sync(rwmi_batch* b) try {
   if (!b) return RWMI_E_INVALID;
   BCK(cudaStreamSynchronize(b->origin));
   rwmi_status worst = RWMI_OK;
@@ -1593,6 +1685,8 @@ RWMI_API rwmi_status rwmi_batch_sync(rwmi_batch* b) {
     else if (worst == RWMI_OK && s > 0) worst = s;
   }
   return worst;
+} catch (const std::exception& e_) {
+  return batch_fail(b, RWMI_E_OOM, std::string("rwmi_batch_sync: ") + e_.what());
 }
 
 RWMI_API void rwmi_batch_destroy(rwmi_batch* b) {

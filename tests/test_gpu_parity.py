@@ -264,6 +264,45 @@ def test_checkpoint_restart_is_bit_identical():
     assert np.array_equal(c.populations(), fa)
 
 
+def test_corrupt_checkpoints_are_refused_without_side_effects():
+    """A checkpoint whose header does not match, whose walker count the file cannot hold, or
+    that is cut short is refused with RWMI_E_INVALID before anything changes; the context then
+    steps exactly like its twin."""
+    from paper_2308_05007_gb300.rwmi import RwmiError
+    w = I.ragged(n_walkers=3000)
+    twin = Sim().from_workload(w)
+    twin.step(10)
+    c = Sim().from_workload(w)
+    c.step(10)
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "ck.bin")
+        twin.save(path)
+        raw = open(path, "rb").read()
+        hdr = np.frombuffer(raw[:80], np.int64).copy()
+        bad = {}
+        for name, slot, value in (("walkers", 6, 1 << 40), ("negative", 6, -1), ("magic", 0, hdr[0] ^ 1),
+                                  ("dims", 3, hdr[3] + 1)):
+            h = hdr.copy()
+            h[slot] = value
+            bad[name] = h.tobytes() + raw[80:]
+        bad["truncated"] = raw[:-16]
+        bad["header"] = raw[:40]
+        f0 = c.populations()
+        for name, data in bad.items():
+            p = os.path.join(d, name + ".bin")
+            with open(p, "wb") as fh:
+                fh.write(data)
+            with pytest.raises(RwmiError) as e:
+                c.load(p)
+            assert e.value.status == -1, name
+            assert c.t == 10, name
+    assert np.array_equal(c.populations(), f0)
+    c.step(10)
+    twin.step(10)
+    assert np.array_equal(c.populations(), twin.populations())
+    assert np.array_equal(c.walkers_by_id()[0], twin.walkers_by_id()[0])
+
+
 def test_mass_conservation_and_walker_count_long_run():
     w = I.ragged(n_walkers=10000)
     sim = Sim().from_workload(w)
