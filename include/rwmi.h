@@ -64,11 +64,12 @@ typedef enum {
     RWMI_W_SEED = 2,         /* some walker found no free seed point (see rwmi_seed_walkers) */
     RWMI_BUSY = 3,           /* rwmi_query: GPU work of the context is still running */
     RWMI_E_INVALID = -1,     /* bad argument or size; context unchanged */
-    RWMI_E_OOM = -2,         /* device allocation failed */
-    RWMI_E_CUDA = -3,        /* a CUDA runtime call or kernel launch failed */
+    RWMI_E_OOM = -2,         /* a device (or host) allocation failed; fences the context */
+    RWMI_E_CUDA = -3,        /* a CUDA runtime call or kernel launch failed; fences the context */
     RWMI_E_NONFINITE = -4,   /* NaN/Inf in the FP64 mass sum or a walker velocity */
     RWMI_E_TIMEOUT = -5,     /* a bounded device wait gave up */
-    RWMI_E_STATE = -6        /* call out of order (e.g. stepping before configuration ends) */
+    RWMI_E_STATE = -6        /* call out of order (e.g. configuring after the first step), or
+                                any call on a context fenced by RWMI_E_OOM / RWMI_E_CUDA */
 } rwmi_status;
 
 /* Storage of the populations in HBM and the arithmetic of the LBM update. The walkers, the
