@@ -9,6 +9,10 @@ keeps every admitted context fed with chunks of steps, polls completion without 
 of the admitted contexts overlaps on the device. Every context's result is the same as when it
 runs alone, because contexts share no device state.
 
+A request whose context fails (its creation, a step, a poll or the collection raises, e.g. an
+RWMI_E_OOM the footprint did not foresee) is closed and recorded with its error; its memory
+returns to the budget and the other requests carry on untouched.
+
 The scheduler itself is plain host logic. The backend (how to make a context, its footprint, its
 chunk length, what to collect) is a parameter, so the same loop runs against a fake backend in
 CPU tests.
@@ -81,6 +85,7 @@ class Record:
     finished: float = math.nan
     cancelled: bool = False
     result: Optional[dict] = None
+    error: Optional[str] = None     # set when the request's context failed
 
     @property
     def latency(self) -> float:
@@ -118,6 +123,7 @@ class Report:
         ws = sum(r.walkers * r.steps for r in d)
         span = max(self.makespan, 1e-12)
         out = dict(requests=len(d), cancelled=sum(r.cancelled for r in self.records),
+                   failed=sum(r.error is not None for r in self.records),
                    p50_latency_s=float(np.percentile(lat, 50)), p99_latency_s=float(np.percentile(lat, 99)),
                    p50_wait_s=float(np.percentile(wait, 50)), p99_wait_s=float(np.percentile(wait, 99)),
                    makespan_s=self.makespan, mlups=cu / span / 1e6, walker_steps_per_s=ws / span,
@@ -162,7 +168,8 @@ class Server:
     def run(self, requests, time_scale: float = 1.0, on_event: Optional[Callable] = None) -> Report:
         """Serves `requests` (objects with rid, arrival in seconds, workload) and returns when
         every one has finished or was cancelled. Arrivals are replayed on the loop's clock,
-        scaled by time_scale. on_event(kind, record) is called on admit, finish and cancel."""
+        scaled by time_scale. on_event(kind, record) is called on admit, finish, cancel, reject
+        and fail."""
         be = self.backend
         pending = deque(sorted(requests, key=lambda r: r.arrival))
         queue: deque = deque()
@@ -177,6 +184,16 @@ class Server:
         def emit(kind, rec):
             if on_event is not None:
                 on_event(kind, rec)
+
+        def failed(rec, sim, exc):
+            """Closes a failed context (best effort) and records why; the caller frees its budget."""
+            rec.error = f"{type(exc).__name__}: {exc}"
+            if sim is not None:
+                try:
+                    sim.close()
+                except Exception:
+                    pass
+            emit("fail", rec)
 
         while pending or queue or active:
             progressed = False
@@ -210,7 +227,12 @@ class Server:
                 if used + rec.footprint > self.budget:
                     break
                 queue.popleft()
-                sim = be.make(w)
+                try:
+                    sim = be.make(w)
+                except Exception as exc:
+                    failed(rec, None, exc)
+                    progressed = True
+                    continue
                 rec.admitted = now()
                 used += rec.footprint
                 peak = max(peak, used)
@@ -229,17 +251,24 @@ class Server:
                     emit("cancel", s.rec)
                     progressed = True
                     continue
-                if s.sim.busy():
-                    still.append(s)
-                    continue
-                if s.left > 0:
-                    n = min(s.chunk, s.left)
-                    s.sim.step(n)
-                    s.left -= n
-                    still.append(s)
+                try:
+                    if s.sim.busy():
+                        still.append(s)
+                        continue
+                    if s.left > 0:
+                        n = min(s.chunk, s.left)
+                        s.sim.step(n)
+                        s.left -= n
+                        still.append(s)
+                        progressed = True
+                        continue
+                    result = be.collect(s.sim, s.w)
+                except Exception as exc:
+                    failed(s.rec, s.sim, exc)
+                    used -= s.rec.footprint
                     progressed = True
                     continue
-                s.rec.result = be.collect(s.sim, s.w)
+                s.rec.result = result
                 s.sim.close()
                 s.rec.finished = now()
                 used -= s.rec.footprint

@@ -161,3 +161,52 @@ def test_poisson_stream_summary_counts_work():
     for r in rep.records:
         assert r.admitted >= r.arrival
     assert all(w.workload.steps % 16 == 0 for w in reqs)
+
+
+def test_a_failing_request_is_closed_and_the_others_carry_on():
+    """One context cannot be made (an allocation failure the footprint did not foresee), another
+    fails in its second chunk and a third when its results are collected. Each is closed and
+    recorded with its error, its memory returns to the budget, and every other request runs
+    exactly its steps."""
+    clk = Clock()
+    be, log, sims = fake_backend(clk)
+    make0, collect0 = be.make, be.collect
+
+    def make(w):
+        if w.name == "r1":
+            raise RuntimeError("RWMI_E_OOM: dalloc: out of memory")
+        s = make0(w)
+        if w.name == "r2":
+            step0 = s.step
+
+            def step(n):
+                if s.steps > 0:
+                    raise RuntimeError("RWMI_E_CUDA: launch failed")
+                step0(n)
+            s.step = step
+        return s
+
+    def collect(s, w):
+        if w.name == "r4":
+            raise RuntimeError("RWMI_E_NONFINITE: non-finite walker velocity")
+        return collect0(s, w)
+
+    be.make, be.collect = make, collect
+    fp = 32 ** 3 * 100
+    events = []
+    srv = Server(be, budget_bytes=2 * fp, max_active=2, chunk_cell_updates=32 ** 3 * 16,
+                 clock=clk, sleep=clk.sleep)
+    rep = srv.run([req(i, 0.001 * i, 32, 64) for i in range(6)],
+                  on_event=lambda kind, rec: events.append((kind, rec.rid)))
+    by = {r.rid: r for r in rep.records}
+    assert "OOM" in by[1].error and "r1" not in sims
+    assert "CUDA" in by[2].error and sims["r2"].closed and sims["r2"].steps == 16
+    assert "NONFINITE" in by[4].error and sims["r4"].closed
+    for rid in (0, 3, 5):
+        assert by[rid].error is None and by[rid].result["steps"] == 64 and sims[f"r{rid}"].closed
+    for rid in (1, 2, 4):
+        assert by[rid].result is None and math.isnan(by[rid].finished) and not by[rid].cancelled
+    assert sorted(rid for k, rid in events if k == "fail") == [1, 2, 4]
+    assert rep.peak_bytes <= 2 * fp
+    s = rep.summary()
+    assert s["requests"] == 3 and s["failed"] == 3 and s["cancelled"] == 0
