@@ -55,6 +55,29 @@ def test_mean_square_displacement_is_6Dt():
         assert m[4 + a] == pytest.approx(2 * D * T, rel=5 * np.sqrt(2 / N))
 
 
+def test_reflecting_walls_keep_a_uniform_distribution_uniform():
+    """Between two no-slip walls in quiescent fluid, specular reflection leaves a uniform
+    distribution uniform: the reflected Gaussian step is symmetric. A wall that clamped or
+    absorbed walkers would heap them at the faces. Once mixed across the gap, the z
+    displacement variance of independent uniform start and end points is H^2/6."""
+    D, H, T, N = 0.2, 8, 300, 20000
+    o = Oracle((6, 6, H), D=D, seed=9, wall_mask=4)
+    o.set_walkers(np.random.default_rng(2).uniform([0, 0, 0], [6, 6, H], (N, 3)))
+    o.step(T)
+    x, x0 = o.walkers()
+    z = x[:, 2]
+    assert z.min() >= 0.0 and z.max() <= H
+    counts = np.histogram(z, bins=2 * H, range=(0, H))[0]
+    assert stats.chisquare(counts).pvalue > 1e-3, counts
+    assert counts[0] / counts.mean() == pytest.approx(1, abs=0.1)
+    assert counts[-1] / counts.mean() == pytest.approx(1, abs=0.1)
+    var_z = np.mean((z - x0[:, 2]) ** 2)
+    assert var_z == pytest.approx(H * H / 6, rel=0.04)
+    # the periodic axes still diffuse freely: 2 D t per axis
+    for a in (0, 1):
+        assert np.mean((x[:, a] - x0[:, a]) ** 2) == pytest.approx(2 * D * T, rel=5 * np.sqrt(2 / N))
+
+
 def _golden_lattice():
     g = json.load(open(os.path.join(GOLDEN, "point_source_section3_1.json")))
     n = int(round(g["domain_m"] / g["dx_m"]))
