@@ -16,7 +16,10 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "rwmi_oracle.c")
-_LIB = os.path.join(_HERE, "_liboracle.so")
+# RWMI_ORACLE_LIB names a prebuilt oracle library to load instead (mutation_check.py builds
+# deliberately broken copies elsewhere and runs the pins against them)
+_PREBUILT = os.environ.get("RWMI_ORACLE_LIB")
+_LIB = _PREBUILT or os.path.join(_HERE, "_liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
@@ -26,6 +29,8 @@ CFLAGS = ["-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-s
 
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (seconds). Rebuilt when the source is newer than the library."""
+    if _PREBUILT:
+        return _LIB
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".{os.getpid()}.tmp"
         subprocess.check_call(["gcc", *CFLAGS, "-o", tmp, _SRC, "-lm"])
@@ -95,6 +100,8 @@ def lib():
                 getattr(L, name).argtypes = [P, C.c_void_p]
             L.orc_dem_pair_geom.argtypes = [P, C.c_int, C.c_int, C.c_void_p]
             L.orc_dem_wall_geom.argtypes = [P, C.c_int, C.c_int, C.c_void_p]
+            L.orc_dem_contact_force.argtypes = [P, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
+                                                C.c_double, C.c_void_p, C.c_void_p]
             L.orc_dem_advance.argtypes = [P, C.c_longlong]
             L.orc_set_prev_nodes.argtypes = [P, C.c_longlong, C.c_void_p]
             L.orc_ibb_link.restype = C.c_double
@@ -235,6 +242,14 @@ class Oracle:
         out = np.zeros(13)
         lib().orc_dem_wall_geom(self.h, int(p), int(face), _ptr(out))
         return dict(xcm=out[0:3], xcw=out[3:6], n=out[6:9], delta=float(out[9]), xcp=out[10:13])
+
+    def dem_contact_force(self, delta, n, vi, vj, dt, xi):
+        """The contact law with this context's DEM parameters: (force on body i, updated spring)."""
+        arr = [np.ascontiguousarray(v, np.float64).reshape(3).copy() for v in (n, vi, vj, xi)]
+        F = np.zeros(3)
+        lib().orc_dem_contact_force(self.h, float(delta), _ptr(arr[0]), _ptr(arr[1]), _ptr(arr[2]),
+                                    float(dt), _ptr(arr[3]), _ptr(F))
+        return F, arr[3]
 
     def set_prev_nodes(self, t_prev, nodes):
         """IBB with the free DEM: node classes of t_prev, refilled from at the step t_prev + 1."""

@@ -2172,6 +2172,16 @@ ORC_API void orc_dem_wall_geom(void* h, int p, int f, double* out)
     free(cbuf); free(kbuf);
 }
 
+/* The contact law alone (normal spring-dashpot and Eq. 5) with the context's DEM parameters:
+ * the force on body i for overlap delta, unit normal n from i towards the other body,
+ * contact-point velocities vi, vj and DEM step dt. xi is the contact's tangential spring, read
+ * and updated in place. */
+ORC_API void orc_dem_contact_force(void* h, double delta, const double n[3], const double vi[3],
+                                   const double vj[3], double dt, double xi[3], double F[3])
+{
+    dem_contact_force((const orc_t*)h, delta, n, vi, vj, dt, xi, F);
+}
+
 /* DEM steps alone (no fluid, no walkers): the hydrodynamic force and torque are those of the
  * last LBM update when the coupling is on */
 ORC_API void orc_dem_advance(void* h, long long nsteps)

@@ -295,3 +295,100 @@ def test_fluid_drags_free_particles():
     assert np.abs(st[:, 8:10]).max() < 0.5 * st[:, 7].min()
     mass = o.density().sum()
     assert mass == pytest.approx(o.n_cells * 1.0, rel=1e-12)
+
+
+def test_contact_law_normal_clamp_coulomb_limit_and_spring_projection():
+    """The contact law on its own. At rest the force on i is -k_n delta n (away from j). It is
+    never attractive: a fast separation gives exactly zero. The tangential force is capped at
+    mu_s F_n, and the spring then holds the Coulomb force. The spring is first projected onto
+    the current tangent plane, so no normal component survives a turning contact."""
+    kn, eta_n, kt, eta_t, mu_s = 200.0, 30.0, 80.0, 2.0, 0.3
+    o, _, _ = _spheres([[10.0, 24.0, 24.0], [30.0, 24.0, 24.0]], [9.0, 9.0], kn=kn, eta_n=eta_n, kt=kt,
+                       eta_t=eta_t, mu_s=mu_s)
+    n = np.array([0.0, 0.0, 1.0])
+    z3 = np.zeros(3)
+    F, xi = o.dem_contact_force(0.05, n, z3, z3, 0.1, z3)
+    np.testing.assert_allclose(F, -kn * 0.05 * n, rtol=1e-15)
+    assert np.all(xi == 0.0)
+    # approaching at 0.1 adds damping; separating at 1.0 would pull (200*0.05 - 30*1 < 0): zero
+    F, _ = o.dem_contact_force(0.05, n, np.array([0, 0, 0.1]), z3, 0.1, z3)
+    np.testing.assert_allclose(F, -(kn * 0.05 + eta_n * 0.1) * n, rtol=1e-14)
+    F, _ = o.dem_contact_force(0.05, n, z3, np.array([0, 0, 1.0]), 0.1, z3)
+    assert np.all(F == 0.0)
+    # sliding: j moves along x relative to i; unsaturated, then saturated at mu_s F_n
+    vj = np.array([0.01, 0.0, 0.0])
+    F, xi = o.dem_contact_force(0.05, n, z3, vj, 0.1, z3)
+    Fn = kn * 0.05
+    np.testing.assert_allclose(xi, vj * 0.1, rtol=1e-15)
+    np.testing.assert_allclose(F, kt * xi + eta_t * vj - Fn * n, rtol=1e-14)
+    assert np.hypot(F[0], F[1]) < mu_s * Fn
+    vj = np.array([0.5, 0.0, 0.0])
+    F, xi = o.dem_contact_force(0.05, n, z3, vj, 0.1, np.array([0.2, 0.0, 0.0]))
+    assert np.hypot(F[0], F[1]) == pytest.approx(mu_s * Fn, rel=1e-14) and F[0] > 0
+    np.testing.assert_allclose(kt * xi + eta_t * vj, [mu_s * Fn, 0.0, 0.0], rtol=1e-13, atol=1e-15)
+    # a spring left from an earlier normal loses its component along the new normal
+    n2 = np.array([0.0, math.sqrt(0.5), math.sqrt(0.5)])
+    _, xi = o.dem_contact_force(0.05, n2, z3, z3, 0.1, np.array([0.01, 0.02, -0.03]))
+    assert abs(xi @ n2) < 1e-17
+    np.testing.assert_allclose(xi, [0.01, 0.025, -0.025], rtol=1e-14)
+
+
+def _dumbbell(spin, substeps=10, q0=None):
+    """One free two-centre particle (anisotropic inertia), no gravity, no walls, fluid force off."""
+    mb = I.Metaballs(center_offsets=np.array([0, 2], np.int32),
+                     centers_body=np.array([[-2.5, 0.5, 0.0], [2.5, -0.5, 0.3]], np.float32),
+                     k=np.array([9.0, 6.0], np.float32), origin=np.array([[24.0, 24.0, 24.0]]),
+                     amplitude=np.zeros((1, 3)), period=np.zeros(1), phase=np.zeros(1), omega=np.zeros((1, 3)))
+    dem = I.Dem(density=2.0, sphere_radius=np.array([0.5]), spin=np.asarray([spin], float),
+                velocity=np.zeros((1, 3)), substeps=substeps, hydro=0)
+    w = I.Workload(name="dumbbell", dims=(48, 48, 48), tau=0.8, D=0.0, seed=0, metaballs=mb, dem=dem)
+    o = Oracle.from_workload(w, seed_walkers=False)
+    if q0 is not None:
+        st = o.particle_state()
+        st[0, 3:7] = q0
+        o.set_particle_state(st)
+    return o
+
+
+def _rot(q):
+    w, x, y, z = q
+    return np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                     [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                     [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
+
+
+def test_torque_free_anisotropic_body_keeps_its_angular_momentum():
+    """Euler's equations without torque: the world angular momentum R I_b R^T w stays fixed while
+    w itself precesses (the gyroscopic term at work). Explicit Euler drifts by O(dt) only."""
+    o = _dumbbell([0.004, 0.009, -0.006])
+    Ib6 = o.dem_mass()[0, 4:10]
+    Ib = np.array([[Ib6[0], Ib6[3], Ib6[4]], [Ib6[3], Ib6[1], Ib6[5]], [Ib6[4], Ib6[5], Ib6[2]]])
+    assert np.ptp(np.linalg.eigvalsh(Ib)) > 0.2 * np.linalg.eigvalsh(Ib).max()   # anisotropic
+
+    def L_world():
+        st = o.particle_state()[0]
+        R = _rot(st[3:7])
+        return R @ Ib @ R.T @ st[10:13], st[10:13].copy()
+
+    L0, w0 = L_world()
+    o.dem_advance(400)
+    L1, w1 = L_world()
+    assert np.linalg.norm(w1 - w0) > 0.05 * np.linalg.norm(w0)       # w does precess
+    assert np.linalg.norm(L1 - L0) < 2e-3 * np.linalg.norm(L0)
+
+
+def test_spin_turns_the_body_in_the_world_frame():
+    """The spin is a world-frame angular velocity: from orientation R0 a constant spin w about z
+    gives R(t) = R_z(|w| t) R0, not R0 R_z(|w| t). A sphere keeps its spin (isotropic)."""
+    q0 = np.array([math.cos(math.pi / 4), math.sin(math.pi / 4), 0.0, 0.0])   # 90 degrees about x
+    w = 0.01
+    o, _, _ = _spheres([[24.0, 24.0, 24.0]], [9.0], spin=[[0.0, 0.0, w]], substeps=10)
+    st = o.particle_state()
+    st[0, 3:7] = q0
+    o.set_particle_state(st)
+    o.dem_advance(150)
+    R = _rot(o.particle_state()[0, 3:7])
+    a = w * 150
+    Rz = np.array([[math.cos(a), -math.sin(a), 0.0], [math.sin(a), math.cos(a), 0.0], [0.0, 0.0, 1.0]])
+    np.testing.assert_allclose(R, Rz @ _rot(q0), atol=2e-3)
+    assert np.abs(R - _rot(q0) @ Rz).max() > 0.5

@@ -202,6 +202,23 @@ def test_sampled_solid_fraction_equals_brute_force(t):
     assert (cnt > 0).any() and (cnt == 0).any()
 
 
+def test_owner_ties_go_to_the_lower_index():
+    """Two equal spheres mirror-symmetric about the centre plane of cell (8, 8, 8) hold equal
+    sub-sample counts there (all 64 each, evaluated exactly alike in binary32). The tie gives the
+    cell to the lower particle index, and the brute force agrees on every cell."""
+    mb = I.Metaballs(center_offsets=np.array([0, 1, 2], np.int32), centers_body=np.zeros((2, 3), np.float32),
+                     k=np.array([6.25, 6.25], np.float32),
+                     origin=np.array([[6.5, 8.5, 8.5], [10.5, 8.5, 8.5]]), amplitude=np.zeros((2, 3)),
+                     period=np.zeros(2), phase=np.zeros(2), omega=np.zeros((2, 3)))
+    dims = (17, 17, 17)
+    cnt_b, own_b, o = _brute_solid(dims, 0, mb, 0)
+    cnt, own = o.solid(0)
+    c = 8 + 17 * (8 + 17 * 8)
+    assert cnt[c] == 64 and own[c] == 0
+    assert np.array_equal(cnt, cnt_b) and np.array_equal(own, own_b)
+    assert (own == 1).any()
+
+
 def test_solid_fraction_sphere_volume():
     """Sum of epsilon over cells converges to the sphere volume (4/3) pi r^3."""
     for r, c in ((6.0, (16.0, 16.0, 16.0)), (4.5, (10.3, 11.7, 9.1))):

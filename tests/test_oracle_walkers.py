@@ -1,6 +1,7 @@
 """Pins of the oracle's random-walk step (Eq. 2), the velocity interpolation of Section 2.4.1,
 Algorithms 1 and 2, the Dirichlet refill, walls, binning (Eq. 16), moments and seeding."""
 import json
+import math
 import os
 
 import numpy as np
@@ -216,6 +217,31 @@ def test_refill_places_walker_outside_near_the_surface():
         assert 4.0 * (1 - 2.6e-4) <= r <= 4.0 + R + 2e-3
         # pushed out along the gradient: same side as the start
         assert (xn - 10.0) @ (x - 10.0) > 0
+
+
+def test_refill_is_uniform_in_the_ball_about_the_surface_point():
+    """The refilled walker lies in the ball of radius R = sqrt(2 D dt) about the surface point x_s
+    on the push-out ray. Points that fall inside the particle are mirrored across the tangent
+    plane through x_s, which keeps their distance to x_s. So |x_new - x_s| / R has the radial
+    law of a uniform ball, P(r <= s) = s^3."""
+    D = 0.5
+    R = math.sqrt(2 * D)
+    o = Oracle((20, 20, 20), D=D)
+    o.set_metaballs(I.single_sphere((10.0, 10.0, 10.0), 16.0))
+    u = np.array([0.48, -0.6, 0.64])
+    x = 10.0 + 2.5 * u                       # inside, radius 2.5; the ray leaves along u
+    xo = 10.0 + 4.5 * u                      # first outside point of the steps 1/2, 1, 2
+    assert o.inside(10.0 + 3.5 * u) == 0 and o.inside(xo) == -1
+    ok, xs = o.bisect(0, xo, x)
+    assert ok
+    r = []
+    for i in range(4000):
+        ok, xn = o.refill(0, x, i)
+        assert ok and o.inside(xn) == -1
+        r.append(np.linalg.norm(xn - xs) / R)
+    r = np.array(r)
+    assert r.max() <= 1.0 + 1e-12
+    assert stats.kstest(r, lambda s: np.clip(s, 0, 1) ** 3).pvalue > 1e-3
 
 
 @pytest.mark.parametrize("q", [15, 19])
