@@ -6,7 +6,7 @@ temporary directory with the oracle's own flags. The CPU pins (tests/test_oracle
 against it through RWMI_ORACLE_LIB. A mutation must make at least one pin fail. The real
 source and library are never touched, so an interrupted run leaves nothing behind.
 
-    python oracle/mutation_check.py              # all mutations (about 8 minutes on 8 cores)
+    python oracle/mutation_check.py              # all mutations (about 10 minutes on 8 cores)
     python oracle/mutation_check.py Guo DEM      # those whose name contains a given word
 """
 from __future__ import annotations
@@ -93,6 +93,27 @@ MUTATIONS = [
     ("IBB q <= 1/2 interpolation swapped", "Eq. 24",
      "if (qf <= 0.5) us[a] = 2.0 * qf * uf[a] + (1.0 - 2.0 * qf) * uff[a];",
      "if (qf <= 0.5) us[a] = 2.0 * qf * uff[a] + (1.0 - 2.0 * qf) * uf[a];"),
+    ("PSM force on the particle with the wrong sign", "PSM force (momentum exchange)",
+     "double Fc[3] = {-dp[0], -dp[1], -dp[2]}, r[3];", "double Fc[3] = {dp[0], dp[1], dp[2]}, r[3];"),
+    ("PSM solid velocity without the spin", "PSM solid velocity",
+     "us[0] = v[0] + w[1] * r[2] - w[2] * r[1];", "us[0] = v[0];"),
+    ("Guo source without its second-order term", "Guo forcing",
+     "S += (3.0 * (e[a] - u[a]) + 9.0 * eu * e[a]) * F[a];", "S += (3.0 * (e[a] - u[a])) * F[a];"),
+    ("body force cos, not sin", "oscillating drive (Eq. 37)",
+     "if (o->Fperiod > 0.0) s = sin(2.0 * M_PI * (double)t / o->Fperiod);",
+     "if (o->Fperiod > 0.0) s = cos(2.0 * M_PI * (double)t / o->Fperiod);"),
+    ("seeding covers half the box", "walker seeding",
+     "volatile double off = u24(r[d]) * span;", "volatile double off = u24(r[d]) * span * 0.5;"),
+    ("IBB force on the particle with the wrong sign", "momentum exchange",
+     "for (int a = 0; a < 3; ++a) o->Fp[3 * p + a] += Fl[a];", "for (int a = 0; a < 3; ++a) o->Fp[3 * p + a] -= Fl[a];"),
+    ("IBB refill at rest, not at the rigid velocity", "Eq. 27",
+     "rigid_velocity(o, &fr, nprev[c] - 1, xc, un);", "un[0] = un[1] = un[2] = 0.0;"),
+    ("DEM wall normal outward", "Eqs. 10-11",
+     "double sg = side ? -1.0 : 1.0;", "double sg = side ? 1.0 : -1.0;"),
+    ("PSM torque, x component sign", "PSM torque",
+     "o->Tp[3 * p + 0] += r[1] * Fc[2] - r[2] * Fc[1];", "o->Tp[3 * p + 0] -= r[1] * Fc[2] - r[2] * Fc[1];"),
+    ("IBB torque, x component sign", "momentum-exchange torque",
+     "o->Tp[3 * p + 0] += r[1] * Fl[2] - r[2] * Fl[1];", "o->Tp[3 * p + 0] -= r[1] * Fl[2] - r[2] * Fl[1];"),
     ("IBB moving-wall term sign", "Eq. 23",
      "return feq(q, ip, rho_f, ud) + gneq + 6.0 * lattice_weight(q, ip) * rho_f * eu;",
      "return feq(q, ip, rho_f, ud) + gneq - 6.0 * lattice_weight(q, ip) * rho_f * eu;"),
