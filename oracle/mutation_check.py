@@ -114,6 +114,20 @@ MUTATIONS = [
      "o->Tp[3 * p + 0] += r[1] * Fc[2] - r[2] * Fc[1];", "o->Tp[3 * p + 0] -= r[1] * Fc[2] - r[2] * Fc[1];"),
     ("IBB torque, x component sign", "momentum-exchange torque",
      "o->Tp[3 * p + 0] += r[1] * Fl[2] - r[2] * Fl[1];", "o->Tp[3 * p + 0] -= r[1] * Fl[2] - r[2] * Fl[1];"),
+    ("type IV keeps a reflected point inside a particle", "multiple reflections (Section 2.4.2)",
+     "if (beyond_wall(o, tr) || inside_any64(o, fr1, tr) >= 0) {", "if (beyond_wall(o, tr)) {"),
+    ("type III refilled instead of moving out", "walker types (Section 2.4.2)",
+     "        o->cnt_type[2]++;\n        for (int d = 0; d < 3; ++d) xnew[d] = xf[d];",
+     "        o->cnt_type[2]++;\n        if (!refill(o, fr1, pin, x, id, t, xnew)) o->refill_fail++;"),
+    ("Eq. 9 contact point past the overlap", "Eq. 9",
+     "for (int a = 0; a < 3; ++a) xcp[a] = xc0[a] + (Rs0 - 0.5 * delta) * nrm[a];",
+     "for (int a = 0; a < 3; ++a) xcp[a] = xc0[a] + (Rs0 + 0.5 * delta) * nrm[a];"),
+    ("DEM mass sampled at h = 1/2", "Eq. 4 mass properties",
+     "#define DEM_MASS_H 0.25", "#define DEM_MASS_H 0.5"),
+    ("IBB q bisection with 12 steps", "Eq. 25",
+     "for (int it = 0; it < 24; ++it) {", "for (int it = 0; it < 12; ++it) {"),
+    ("seeding keeps points inside particles", "initial removal (Section 2.4.2)",
+     "ok = (o->P == 0) || inside_any32(o, &fr, xs) < 0;", "ok = 1;"),
     ("IBB moving-wall term sign", "Eq. 23",
      "return feq(q, ip, rho_f, ud) + gneq + 6.0 * lattice_weight(q, ip) * rho_f * eu;",
      "return feq(q, ip, rho_f, ud) + gneq - 6.0 * lattice_weight(q, ip) * rho_f * eu;"),

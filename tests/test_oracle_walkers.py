@@ -244,6 +244,47 @@ def test_refill_is_uniform_in_the_ball_about_the_surface_point():
     assert stats.kstest(r, lambda s: np.clip(s, 0, 1) ** 3).pvalue > 1e-3
 
 
+def test_walker_type_rules_on_exact_moves():
+    """Section 2.4.2's rules on proposals made exact (D = 0, uniform u), against particle A
+    (radius 2) and a small particle B placed on the point where a reflection off A lands:
+    - type I, out to out: moves to x_p + u;
+    - type III, in to out: moves freely to x_p + u;
+    - type IV, out to in: Algorithm 1, then Algorithm 2 gives the new point;
+    - type IV whose reflected point lies inside a particle: the walker stays at x_p ("multiple
+      reflections ... returned to their original location")."""
+    u = np.array([1.2, 0.0, 0.0])
+    hit = np.array([7.3, 10.9, 10.0])                 # reaches A at x ~ 8.21, reflects to ~(8.04, 11.13)
+
+    def world(with_b):
+        cB = [8.04394206, 11.12982447, 10.0] if with_b else [3.0, 3.0, 3.0]
+        mb = I.Metaballs(center_offsets=np.array([0, 1, 2], np.int32), centers_body=np.zeros((2, 3), np.float32),
+                         k=np.array([4.0, 0.09], np.float32), origin=np.array([[10.0, 10.0, 10.0], cB]),
+                         amplitude=np.zeros((2, 3)), period=np.zeros(2), phase=np.zeros(2), omega=np.zeros((2, 3)))
+        o = Oracle((20, 20, 20), D=0.0)
+        o.set_metaballs(mb)
+        o.set_velocity(np.tile(u, (8000, 1)))
+        return o
+
+    o = world(False)
+    ok, xi = o.bisect(0, hit, hit + u, 1)
+    assert ok
+    tr = o.reflect(0, xi, hit + u, 1)
+    x = np.array([[3.0, 15.0, 15.0], [11.3, 10.0, 10.0], hit])   # types I, III, IV
+    assert [o.inside(v, 1) for v in x] == [-1, 0, -1] and o.inside(x[1] + u, 1) == -1
+    out = o.walkers_advance(x, np.arange(3, dtype=np.uint32))
+    np.testing.assert_array_equal(out[0], x[0] + u)
+    np.testing.assert_array_equal(out[1], x[1] + u)
+    np.testing.assert_array_equal(out[2], tr)
+    assert o.inside(tr, 1) == -1 and np.linalg.norm(tr - hit) > 0.5
+    c = o.counters()
+    assert (c["type_I"], c["type_II"], c["type_III"], c["type_IV"]) == (1, 0, 1, 1)
+    # the same hit with particle B sitting on the reflected point: back to x_p
+    o = world(True)
+    assert o.inside(tr, 1) == 1 and o.inside(hit, 1) == -1 and o.inside(hit + u, 1) == 0
+    out = o.walkers_advance(hit[None, :], np.array([2], np.uint32))
+    np.testing.assert_array_equal(out[0], hit)
+
+
 @pytest.mark.parametrize("q", [15, 19])
 def test_no_walker_ends_inside_a_moving_particle(q):
     w = I.ragged(q=q, n_walkers=3000)
