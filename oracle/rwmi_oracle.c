@@ -2,16 +2,20 @@
  * rwmi_oracle.c -- plain, slow FP64 CPU reference ("the oracle") for one timestep of the
  * RW-MI-DELBM fluid-solute update (arXiv 2308.05007).
  *
- * TEST INFRASTRUCTURE ONLY. The test-suite, the package smoke check and the benchmark's CPU
- * baseline leg are the only users of this library; the product path never loads it. It shares
- * no code, header, table or helper with the CUDA library: the lattice tables, the counter-based
- * generator, the metaball function and every step below are written out here on their own.
+ * TEST INFRASTRUCTURE ONLY. The test-suite (with its mutation check), the package smoke check
+ * and the benchmark's CPU baseline and reference legs are the only users of this library; the
+ * product path never loads it. It shares no code, header, table or helper with the CUDA
+ * library: the lattice tables, the counter-based generator, the metaball function and every
+ * step below are written out here on their own.
  *
  * One timestep t -> t+1, in the order the oracle runs it:
- *   1. rigid particle poses at t and t+1: the DEM of Eq. 4 is held to prescribed trajectories;
- *   2. solid fraction per cell from the metaball function of Eq. 3 (4x4x4 sub-samples);
+ *   1. rigid particle poses at t and t+1: prescribed trajectories, or the free DEM of
+ *      Eqs. 4-11 (sphero-metaball contacts, gravity, the fluid's force and torque);
+ *   2. solid fraction per cell from the metaball function of Eq. 3 (4x4x4 sub-samples), or
+ *      the solid/fluid node classes of the interpolated bounce-back;
  *   3. lattice Boltzmann pull-stream and collide, Eqs. 12-15 (D3Q19 as in Section 2.3, or
- *      D3Q15), with partially-saturated-cell solid coupling and Guo body forcing;
+ *      D3Q15), with Guo body forcing and either partially-saturated-cell solid coupling or
+ *      the paper's interpolated bounce-back, momentum exchange and refilling (Eqs. 23-27);
  *   4. random-walk advance of every solute walker, Eq. 2, with the four walker/particle
  *      relations of Section 2.4.2: free motion (I, III), Dirichlet refill (II), and the
  *      no-flux rule (IV) by Algorithm 1 (bisection) and Algorithm 2 (specular reflection);
