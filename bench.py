@@ -152,11 +152,17 @@ def measured_peaks():
 
 
 def lbm_source_digest() -> str:
-    """First 16 hex digits of the SHA-256 of the LBM kernel's sources (kernel + lattice header)."""
+    """First 16 hex digits of the SHA-256 of the LBM kernel's code (kernel + lattice header),
+    with comments, trailing blanks and blank lines removed: a comment edit keeps the digest."""
     import hashlib
+    import re
     h = hashlib.sha256()
     for name in ("rwmi_lbm.cu", "rwmi_lattice.cuh"):
-        h.update(open(os.path.join(ROOT, "paper_2308_05007_gb300", "csrc", name), "rb").read())
+        src = open(os.path.join(ROOT, "paper_2308_05007_gb300", "csrc", name)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        code = "\n".join(ln.rstrip() for ln in src.splitlines() if ln.strip())
+        h.update(code.encode())
     return h.hexdigest()[:16]
 
 

@@ -1,6 +1,8 @@
 // rwmi_lbm.cu -- the fused LBM step: pull stream (periodic wrap / half-way bounce-back) + BGK
-// collide (Eqs. 12-15) with PSM solid coupling and Guo forcing; writes the populations, the
-// velocity field and, on reduction steps, per-particle force/torque and the FP64 sums.
+// collide (Eqs. 12-15) with Guo forcing and either PSM solid coupling or the paper's
+// interpolated bounce-back (Eqs. 23-27); writes the populations, the velocity field and, on
+// reduction steps, per-particle force/torque and the FP64 sums. Also the IBB link list and its
+// q values, computed ahead of the update.
 #include "rwmi_lattice.cuh"
 
 namespace rwmi {
@@ -9,7 +11,8 @@ namespace rwmi {
 // Fused pull-stream + collide (Eqs. 12-15), partially saturated cells, Guo forcing.
 // One thread per cell, flat index c = x + nx (y + ny z); direction planes are contiguous, so
 // every pull load of a warp is one (shifted) coalesced row segment. Storage: binary32 f_i,
-// binary32 f_i - w_i rho0 ("shifted") or binary16 shifted; arithmetic binary32.
+// binary32 f_i - w_i rho0 ("shifted") or binary16 shifted, with binary32 arithmetic; or
+// binary64 shifted with binary64 arithmetic.
 // ------------------------------------------------------------------------------------------
 // Base pointers of the Q direction planes (kernel parameters: constant-bank operands, so each
 // access is one address multiply-add).
@@ -20,7 +23,8 @@ template <int Q, typename T> struct Planes {
 
 // q of Eq. 25: 24 binary32 bisection steps on Eq. 3 of one particle along x_f + s e, s in [0, 1]
 // (the CPU oracle's sequence: midpoint 0.5 (lo + hi), point x_f + mid e), q = the bracket's
-// middle. The LBM kernel calls it from one (not unrolled) loop over the warp's link table.
+// middle. ibb_q_kernel calls it once per listed link; the LBM kernel calls it only for links
+// beyond the list's capacity.
 __device__ __forceinline__ float ibb_link_q(const float4* __restrict__ cw, int c0, int c1, float x0, float y0,
                                          float z0, int ex, int ey, int ez, const Geom& g) {
   float lo = 0.0f, hi = 1.0f;
