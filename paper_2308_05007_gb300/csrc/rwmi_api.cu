@@ -1,7 +1,7 @@
 // rwmi_api.cu -- host side of the C ABI declared in include/rwmi.h: context state, device
 // memory, the per-step launch sequence (replayed from captured CUDA graphs), read-back and
-// checkpointing. Every step of the method runs in the kernels of rwmi_fluid.cu and
-// rwmi_walkers.cu; this file only sequences them.
+// checkpointing. Every step of the method runs in the kernels of rwmi_fluid.cu, rwmi_lbm.cu,
+// rwmi_walkers.cu and rwmi_dem.cu; this file only sequences them.
 #include <algorithm>
 #include <atomic>
 #include <cmath>

@@ -2,11 +2,14 @@
 // read-back (the LBM kernel itself is in rwmi_lbm.cu).
 //
 // Kernels (one timestep t):
-//   pose_bin_kernel   particle pose at a time (prescribed motion), world control points, brick
-//                     candidate lists, body force, zeroed force/momentum accumulators
+//   pose_bin_kernel   particle pose at a time (prescribed motion, or read from the free DEM's
+//                     state), world control points, brick candidate lists, body force, zeroed
+//                     force/momentum accumulators
 //   raster_kernel     solid sub-sample count + owner for every cell of bricks that touch a
 //                     particle (Eq. 3, 4x4x4 sub-samples, binary32 decisions bit-identical to
 //                     the CPU oracle's)
+//   node_kernel       with the paper's coupling: solid/fluid node classes of the flagged bricks
+//                     and the refilling of nodes uncovered since the previous step (Eq. 27)
 #include "rwmi_lattice.cuh"
 
 namespace rwmi {

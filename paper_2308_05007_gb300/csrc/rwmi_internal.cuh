@@ -3,7 +3,7 @@
 // HBM layout (one context):
 //   populations   f[2][Q][ncell_pad]      A/B ping-pong, direction-major (SoA), each direction
 //                                         plane 128-byte aligned; binary32 (optionally shifted by
-//                                         w_i rho0) or binary16 shifted
+//                                         w_i rho0), binary16 shifted or binary64 shifted
 //   velocity      u[ncell] float4          (ux, uy, uz, rho) per cell, written by the LBM kernel
 //                                         with one 16-byte store, gathered by walkers (8 loads)
 //   solid         solid[ncell]            uint16: sub-sample count (bits 0-6) | owner (bits 7-15),
