@@ -119,6 +119,8 @@ MUTATIONS = [
      "o->Tp[3 * p + 0] += r[1] * Fl[2] - r[2] * Fl[1];", "o->Tp[3 * p + 0] -= r[1] * Fl[2] - r[2] * Fl[1];"),
     ("type IV keeps a reflected point inside a particle", "multiple reflections (Section 2.4.2)",
      "if (beyond_wall(o, tr) || inside_any64(o, fr1, tr) >= 0) {", "if (beyond_wall(o, tr)) {"),
+    ("type IV keeps a reflected point beyond a wall", "multiple reflections (Section 2.4.2)",
+     "if (beyond_wall(o, tr) || inside_any64(o, fr1, tr) >= 0) {", "if (inside_any64(o, fr1, tr) >= 0) {"),
     ("type III refilled instead of moving out", "walker types (Section 2.4.2)",
      "        o->cnt_type[2]++;\n        for (int d = 0; d < 3; ++d) xnew[d] = xf[d];",
      "        o->cnt_type[2]++;\n        if (!refill(o, fr1, pin, x, id, t, xnew)) o->refill_fail++;"),

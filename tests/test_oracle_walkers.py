@@ -250,8 +250,8 @@ def test_walker_type_rules_on_exact_moves():
     - type I, out to out: moves to x_p + u;
     - type III, in to out: moves freely to x_p + u;
     - type IV, out to in: Algorithm 1, then Algorithm 2 gives the new point;
-    - type IV whose reflected point lies inside a particle: the walker stays at x_p ("multiple
-      reflections ... returned to their original location")."""
+    - type IV whose reflected point lies inside a particle or beyond a wall: the walker stays at
+      x_p ("multiple reflections ... returned to their original location")."""
     u = np.array([1.2, 0.0, 0.0])
     hit = np.array([7.3, 10.9, 10.0])                 # reaches A at x ~ 8.21, reflects to ~(8.04, 11.13)
 
@@ -283,6 +283,17 @@ def test_walker_type_rules_on_exact_moves():
     assert o.inside(tr, 1) == 1 and o.inside(hit, 1) == -1 and o.inside(hit + u, 1) == 0
     out = o.walkers_advance(hit[None, :], np.array([2], np.uint32))
     np.testing.assert_array_equal(out[0], hit)
+    # a reflection off a sphere near the z = 0 wall that would end beyond the wall: back to x_p
+    o = Oracle((20, 20, 12), D=0.0, wall_mask=4)
+    o.set_metaballs(I.single_sphere((10.0, 10.0, 2.0), 4.0))
+    o.set_velocity(np.tile([0.7, 0.0, 0.0], (20 * 20 * 12, 1)))
+    xp = np.array([8.6, 10.0, 0.5])                  # on the first node layer: u is the node value
+    xf = xp + o.trilinear(xp)
+    ok, xi = o.bisect(0, xp, xf, 1)
+    assert ok and o.inside(xp, 1) == -1 and o.inside(xf, 1) == 0
+    assert o.reflect(0, xi, xf, 1)[2] < -0.1
+    out = o.walkers_advance(xp[None, :], np.array([0], np.uint32))
+    np.testing.assert_array_equal(out[0], xp)
 
 
 @pytest.mark.parametrize("q", [15, 19])
