@@ -143,6 +143,12 @@ MUTATIONS = [
      "if (0) { if (i < 0) i = 0; if (i > o->n[a] - 1) i = o->n[a] - 1; }"),
     ("moments: mean of x, not of x - x0", "Eqs. 38-40 moments",
      "md[a] += o->x[3 * w + a] - o->x0[3 * w + a];", "md[a] += o->x[3 * w + a];"),
+    ("IBB node owner: the highest index", "node classes (Fig. 3)",
+     "                        node[c] = p + 1;\n                        break;",
+     "                        node[c] = p + 1;"),
+    ("IBB node at the cell corner", "node classes (Fig. 3)",
+     "float xs[3] = {(float)i + 0.5f, (float)j + 0.5f, (float)k + 0.5f};\n                node[c] = 0;",
+     "float xs[3] = {(float)i, (float)j, (float)k};\n                node[c] = 0;"),
     ("IBB moving-wall term sign", "Eq. 23",
      "return feq(q, ip, rho_f, ud) + gneq + 6.0 * lattice_weight(q, ip) * rho_f * eu;",
      "return feq(q, ip, rho_f, ud) + gneq - 6.0 * lattice_weight(q, ip) * rho_f * eu;"),

@@ -1,7 +1,8 @@
 """Pins for the oracle's IBB coupling (Section 2.4.3: interpolated bounce-back, Eqs. 23-25;
 Galilean-invariant momentum exchange; refilling, Eqs. 26-27), independent of the oracle itself:
-closed-form ray-sphere intersections for q, the link formula's special cases, an exact momentum
-balance for a resting particle, the rest state, and Galilean invariance of the force."""
+node classes against a brute force, closed-form ray-sphere intersections for q, the link
+formula's special cases, an exact momentum balance for a resting particle, the rest state, and
+Galilean invariance of the force."""
 import numpy as np
 import pytest
 
@@ -21,6 +22,36 @@ def _sphere_workload(n=24, center=(12.3, 11.7, 12.1), k=36.0, F=(0.0, 0.0, 0.0),
         mb.amplitude[0] = np.asarray(particle_velocity) * T / (2 * np.pi)
     return I.Workload(name="ibb_sphere", dims=(n, n, n), tau=tau, D=0.0, seed=0, q=15,
                       body_force=F, init_velocity=velocity, metaballs=mb, coupling=1, steps=1)
+
+
+def test_node_classes_are_the_binary32_inside_test_at_cell_centres():
+    """A node is solid when Eq. 3 of some particle reaches 1 at the cell centre, decided in
+    binary32 as r2 = (dx dx + dy dy) + dz dz, f = k / r2; where two particles overlap, the lower
+    index owns the node. Brute force over every cell of two overlapping spheres."""
+    n = 20
+    centres = np.array([[8.0, 10.2, 9.7], [11.0, 9.9, 10.3]])
+    ks = np.array([6.25, 5.3], np.float32)
+    mb = I.Metaballs(center_offsets=np.array([0, 1, 2], np.int32), centers_body=np.zeros((2, 3), np.float32),
+                     k=ks, origin=centres, amplitude=np.zeros((2, 3)), period=np.zeros(2),
+                     phase=np.zeros(2), omega=np.zeros((2, 3)))
+    w = I.Workload(name="ibb_two", dims=(n, n, n), tau=0.8, D=0.0, seed=0, q=15, metaballs=mb,
+                   coupling=1, steps=1)
+    o = Oracle.from_workload(w, seed_walkers=False)
+    node = o.nodes(0)
+    idx = np.arange(n ** 3)
+    x = (np.stack([idx % n, idx // n % n, idx // (n * n)], 1) + 0.5).astype(np.float32)
+    want = np.zeros(n ** 3, np.int32)
+    for p in (1, 0):                       # the lower index written last wins
+        d = x - centres[p].astype(np.float32)
+        r2 = (d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1]).astype(np.float32)
+        r2 = (r2 + d[:, 2] * d[:, 2]).astype(np.float32)
+        with np.errstate(divide="ignore"):
+            inside = (ks[p] / r2).astype(np.float32) >= np.float32(1.0)
+        want[inside] = p + 1
+    assert np.array_equal(node, want)
+    both = [c for c in range(n ** 3) if node[c] == 1
+            and np.sum((x[c] - centres[1]) ** 2) < ks[1]]
+    assert len(both) > 5                     # the overlap holds nodes, and particle 0 owns them
 
 
 def test_q_is_the_ray_sphere_intersection():
