@@ -149,6 +149,16 @@ MUTATIONS = [
     ("IBB node at the cell corner", "node classes (Fig. 3)",
      "float xs[3] = {(float)i + 0.5f, (float)j + 0.5f, (float)k + 0.5f};\n                node[c] = 0;",
      "float xs[3] = {(float)i, (float)j, (float)k};\n                node[c] = 0;"),
+    ("DEM pair without the periodic image", "DEM on periodic axes",
+     "if (!o->wall[a]) d -= (double)o->n[a] * floor(d / (double)o->n[a] + 0.5);", "(void)0;"),
+    ("walker noise not keyed by the step", "Eq. 2 (noise per step)",
+     "trilinear(o, ufield, x, u);\n    uint32_t ctr[4] = {id, t, 0u, 0u}, r[4];",
+     "trilinear(o, ufield, x, u);\n    uint32_t ctr[4] = {id, 0u, 0u, 0u}, r[4];"),
+    ("interpolation wall layer held at the node value", "Section 2.4.1 at walls",
+     "wt[1] = xa / 0.5; wt[0] = 1.0 - wt[1];", "wt[1] = 1.0; wt[0] = 0.0;"),
+    ("PSM solid velocity without the minimum image", "PSM solid velocity on periodic axes",
+     "for (int a = 0; a < 3; ++a) r[a] = min_image(o, a, xn[a] - fr->o[3 * owner + a]);",
+     "for (int a = 0; a < 3; ++a) r[a] = xn[a] - fr->o[3 * owner + a];"),
     ("IBB moving-wall term sign", "Eq. 23",
      "return feq(q, ip, rho_f, ud) + gneq + 6.0 * lattice_weight(q, ip) * rho_f * eu;",
      "return feq(q, ip, rho_f, ud) + gneq - 6.0 * lattice_weight(q, ip) * rho_f * eu;"),

@@ -179,13 +179,16 @@ def test_spinning_sphere_feels_the_stokes_rotational_drag(coupling, lo, hi):
     assert np.linalg.norm(T - ratio * want) < 1e-3 * np.linalg.norm(want)
 
 
-def test_solid_interior_moves_with_the_particle():
+@pytest.mark.parametrize("centre", [(12.0, 12.0, 12.0), (0.5, 12.0, 23.5)])
+def test_solid_interior_moves_with_the_particle(centre):
     """Inside a partially-saturated particle (B = 1 cells) the fluid takes the rigid-body
     velocity u_s = v + omega x r, up to the stencil-scale mixing with the fluid outside
-    (under 5% three cells in from the surface)."""
+    (under 5% three cells in from the surface). The second particle straddles two periodic
+    faces: r is the minimum-image offset from its centre."""
+    c = np.array(centre)
     mb = I.Metaballs(center_offsets=np.array([0, 1], np.int32),
                      centers_body=np.zeros((1, 3), np.float32), k=np.array([49.0], np.float32),
-                     origin=np.array([[12.0, 12.0, 12.0]]), amplitude=np.array([[0.0, 0.0, 0.0]]),
+                     origin=np.array([c]), amplitude=np.array([[0.0, 0.0, 0.0]]),
                      period=np.zeros(1), phase=np.zeros(1), omega=np.array([[0.0, 0.0, 0.01]]))
     o = Oracle((24, 24, 24), q=19, tau=0.8)
     o.set_metaballs(mb)
@@ -194,7 +197,8 @@ def test_solid_interior_moves_with_the_particle():
     u = o.velocity()
     idx = np.arange(24 ** 3)
     x = np.stack([idx % 24, idx // 24 % 24, idx // 576], 1) + 0.5
-    r = x - 12.0
+    r = x - c
+    r -= 24.0 * np.round(r / 24.0)
     us = np.cross(np.array([0, 0, 0.01]), r)
     deep = (np.linalg.norm(r, axis=1) < 4.0) & (cnt == 64)
     assert deep.sum() > 100
