@@ -159,6 +159,14 @@ MUTATIONS = [
     ("PSM solid velocity without the minimum image", "PSM solid velocity on periodic axes",
      "for (int a = 0; a < 3; ++a) r[a] = min_image(o, a, xn[a] - fr->o[3 * owner + a]);",
      "for (int a = 0; a < 3; ++a) r[a] = xn[a] - fr->o[3 * owner + a];"),
+    ("DEM pair torque arm from the other body", "Eq. 4 (contact torque)",
+     "double ri[3] = {xcp[0] - si[0], xcp[1] - si[1], xcp[2] - si[2]};",
+     "double ri[3] = {xcp[0] - oj[0], xcp[1] - oj[1], xcp[2] - oj[2]};"),
+    ("DEM wall torque with the wrong sign", "Eq. 4 (contact torque)",
+     "    cross3(r, Fw, Tw);\n}", "    cross3(Fw, r, Tw);\n}"),
+    ("DEM wall contact point outside the overlap", "Eq. 11",
+     "for (int d = 0; d < 3; ++d) xcp[d] = xcw[d] + 0.5 * delta * nrm[d];",
+     "for (int d = 0; d < 3; ++d) xcp[d] = xcw[d] - 0.5 * delta * nrm[d];"),
     ("IBB moving-wall term sign", "Eq. 23",
      "return feq(q, ip, rho_f, ud) + gneq + 6.0 * lattice_weight(q, ip) * rho_f * eu;",
      "return feq(q, ip, rho_f, ud) + gneq - 6.0 * lattice_weight(q, ip) * rho_f * eu;"),
