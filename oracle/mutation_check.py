@@ -6,7 +6,7 @@ temporary directory with the oracle's own flags. The CPU pins (tests/test_oracle
 against it through RWMI_ORACLE_LIB. A mutation must make at least one pin fail. The real
 source and library are never touched, so an interrupted run leaves nothing behind.
 
-    python oracle/mutation_check.py              # all mutations (about 13 minutes on 8 cores)
+    python oracle/mutation_check.py              # all mutations (about 15 minutes on 8 cores)
     python oracle/mutation_check.py Guo DEM      # those whose name contains a given word
 """
 from __future__ import annotations
