@@ -16,7 +16,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "rwmi_oracle.c")
-# RWMI_ORACLE_LIB names a prebuilt oracle library to load instead (mutation_check.py builds
+# RWMI_ORACLE_LIB names a prebuilt oracle library to load instead (tests/mutation_check.py builds
 # deliberately broken copies elsewhere and runs the pins against them)
 _PREBUILT = os.environ.get("RWMI_ORACLE_LIB")
 _LIB = _PREBUILT or os.path.join(_HERE, "_liboracle.so")

@@ -6,8 +6,8 @@ temporary directory with the oracle's own flags. The CPU pins (tests/test_oracle
 against it through RWMI_ORACLE_LIB. A mutation must make at least one pin fail. The real
 source and library are never touched, so an interrupted run leaves nothing behind.
 
-    python oracle/mutation_check.py              # all mutations (about 15 minutes on 8 cores)
-    python oracle/mutation_check.py Guo DEM      # those whose name contains a given word
+    python tests/mutation_check.py               # all mutations (about 15 minutes on 8 cores)
+    python tests/mutation_check.py Guo DEM       # those whose name contains a given word
 """
 from __future__ import annotations
 
@@ -19,16 +19,14 @@ import time
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
+ORACLE_SRC = os.path.join(ROOT, "oracle", "rwmi_oracle.c")
 sys.path.insert(0, ROOT)
 from oracle.oracle import CFLAGS  # noqa: E402
 
 PINS = ["tests/test_oracle_rng.py", "tests/test_oracle_metaball.py", "tests/test_oracle_lbm.py",
         "tests/test_oracle_walkers.py", "tests/test_oracle_ibb.py", "tests/test_oracle_dem.py"]
 
-# (name, passage it breaks, exact source text, replacement). Not listed, because no pin can
-# catch it: the plain momentum exchange in place of the Galilean-invariant one. On any closed
-# body in a uniform co-moving stream both give zero, since every lattice line crosses the
-# surface in pairs, and no closed form separates them elsewhere.
+# (name, passage it breaks, exact source text, replacement)
 MUTATIONS = [
     ("Guo prefactor 1-1/tau", "Guo forcing",
      "double guo = 1.0 - 0.5 / tau;", "double guo = 1.0 - 1.0 / tau;"),
@@ -167,6 +165,9 @@ MUTATIONS = [
     ("DEM wall contact point outside the overlap", "Eq. 11",
      "for (int d = 0; d < 3; ++d) xcp[d] = xcw[d] + 0.5 * delta * nrm[d];",
      "for (int d = 0; d < 3; ++d) xcp[d] = xcw[d] - 0.5 * delta * nrm[d];"),
+    ("momentum exchange without the wall velocity", "Galilean-invariant momentum exchange",
+     "for (int a = 0; a < 3; ++a) Fl[a] = (eip[a] - uw[a]) * Gp - (e[a] - uw[a]) * fi[m];",
+     "for (int a = 0; a < 3; ++a) Fl[a] = eip[a] * Gp - e[a] * fi[m];"),
     ("IBB moving-wall term sign", "Eq. 23",
      "return feq(q, ip, rho_f, ud) + gneq + 6.0 * lattice_weight(q, ip) * rho_f * eu;",
      "return feq(q, ip, rho_f, ud) + gneq - 6.0 * lattice_weight(q, ip) * rho_f * eu;"),
@@ -175,7 +176,7 @@ MUTATIONS = [
 
 def run(names=()) -> list:
     """Returns [(mutation, passage, caught, failing pins, seconds)]."""
-    src = open(os.path.join(HERE, "rwmi_oracle.c")).read()
+    src = open(ORACLE_SRC).read()
     out = []
     with tempfile.TemporaryDirectory() as tmp:
         for name, passage, old, new in MUTATIONS:
