@@ -311,9 +311,10 @@ RWMI_API rwmi_status rwmi_particle_forces(rwmi_ctx* ctx, double* out);
 RWMI_API rwmi_status rwmi_walkers(rwmi_ctx* ctx, float* out, float* x0);
 
 /* Device counters since creation: {type I (not counted, 0), type II, III, IV walker steps,
- * Algorithm 1 failures, refill failures, wall failures, seed failures, non-finite velocities,
- * over-long walker steps (resolved against all particles), walkers sent to the particle-resolution
- * pass, (cell, particle) pairs the rasteriser evaluated sub-sample by sub-sample}. */
+ * Algorithm 1 failures, refill failures, wall failures, seed failures, walker steps with a
+ * non-finite velocity or proposed position (that walker keeps its position), over-long walker
+ * steps (resolved against all particles), walkers sent to the particle-resolution pass,
+ * (cell, particle) pairs the rasteriser evaluated sub-sample by sub-sample}. */
 RWMI_API rwmi_status rwmi_counters(rwmi_ctx* ctx, int64_t out[12]);
 
 /* Checkpoint and restart: populations, walkers (positions, start positions), the step
@@ -358,9 +359,15 @@ RWMI_API void rwmi_batch_destroy(rwmi_batch* batch);
  * 8 MiB per GPU that loads the library, held until the process exits.
  *   dims[3], wall_mask: the box and its walled axes, as for rwmi_create / rwmi_configure.
  *   pos: device memory, n walkers of 4 floats {x, y, z, payload} (the rwmi_walkers layout).
+ *     Any float is accepted: an unwrapped coordinate of any size is wrapped exactly on a
+ *     periodic axis and clamped on a walled one; a NaN or infinite coordinate counts in cell
+ *     0 of that axis (periodic) or at the clamped end (walled). Every walker is counted in
+ *     some cell of the box, so the counts always sum to n and no write leaves the arrays.
  *   counts: device memory, dims[0]*dims[1]*dims[2] uint32, overwritten with walkers per cell.
  *   pos_sorted: device memory for n x 4 floats, or NULL: the walkers grouped by cell in
- *     ascending cell order (order within a cell unspecified).
+ *     ascending cell order (order within a cell unspecified). It must not overlap pos.
+ *   All three pointers must be device memory (host memory is not accepted here, unlike the
+ *   read-back calls of a context); the Python binding checks devices, sizes and overlap.
  *   stream: cudaStream_t for the work, or NULL for the default stream. The call is asynchronous.
  * Limits: at most 1048576 cells and 1048576 walkers; larger sizes return RWMI_E_INVALID with a
  * message from rwmi_last_error(NULL). Nothing is allocated: no cudaMalloc, no cudaFree, no

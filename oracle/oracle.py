@@ -73,6 +73,8 @@ def lib():
             L.orc_walkers_advance.argtypes = [P, C.c_longlong, C.c_void_p, C.c_void_p, C.c_void_p]
             L.orc_philox.argtypes = [C.c_uint64, C.c_void_p, C.c_void_p]
             L.orc_step_normals.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_void_p]
+            L.orc_philox_find_seed.restype = C.c_longlong
+            L.orc_philox_find_seed.argtypes = [C.c_uint64, C.c_longlong, C.c_void_p, C.c_int, C.c_uint32]
             L.orc_metaball.restype = C.c_double
             L.orc_metaball.argtypes = [P, C.c_longlong, C.c_int, C.c_void_p, C.c_void_p]
             L.orc_metaball32.restype = C.c_float
@@ -129,6 +131,13 @@ def step_normals(seed: int, walker_id: int, t: int) -> np.ndarray:
     out = np.zeros(3)
     lib().orc_step_normals(C.c_uint64(seed), C.c_uint32(walker_id), C.c_uint32(t), _ptr(out))
     return out
+
+
+def philox_find_seed(seed0: int, count: int, ctr, word: int, target: int) -> int:
+    """First seed in [seed0, seed0 + count) whose Philox word `word` for counter ctr has
+    (word >> 8) == target, or -1 (test helper)."""
+    c = np.ascontiguousarray(ctr, np.uint32)
+    return int(lib().orc_philox_find_seed(C.c_uint64(seed0), int(count), _ptr(c), int(word), C.c_uint32(target)))
 
 
 def lattice(q: int):

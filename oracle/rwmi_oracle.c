@@ -1907,6 +1907,21 @@ ORC_API void orc_step_normals(uint64_t seed, uint32_t id, uint32_t t, double z[3
     box_muller(u24(r[2]), u24(r[3]), &z[2], NULL);
 }
 
+/* Test helper (no part of the method): the first seed in [seed0, seed0 + count) whose Philox
+ * output for counter ctr has (word `word`) >> 8 == target, or -1. Tests use it to find the rare
+ * counters that put a uniform at the end of its range. */
+ORC_API long long orc_philox_find_seed(uint64_t seed0, long long count, const uint32_t ctr[4], int word,
+                                       uint32_t target)
+{
+    for (long long s = 0; s < count; ++s) {
+        uint32_t r[4];
+        uint64_t seed = seed0 + (uint64_t)s;
+        philox4x32_10((uint32_t)seed, (uint32_t)(seed >> 32), ctr, r);
+        if ((r[word & 3] >> 8) == target) return (long long)seed;
+    }
+    return -1;
+}
+
 ORC_API double orc_metaball(void* h, long long t, int p, const double x[3], double g[3])
 {
     orc_t* o = (orc_t*)h;

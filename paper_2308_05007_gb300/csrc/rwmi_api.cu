@@ -1063,10 +1063,11 @@ RWMI_API rwmi_status rwmi_step(rwmi_ctx* c, int32_t n) try {
         advance_mirrors(c, L);
       }
       n -= (int32_t)L;
-    } else {   // eager run up to the next chunk boundary (or all n without graphs)
+    } else {   // eager run up to the next chunk boundary (or all n without graphs); as in a
+               // replayed chunk, the FP64 sums only on the run's last step, the one they are read at
       int64_t k = graphs ? std::min<int64_t>(n, L - c->t % L) : n;
       n -= (int32_t)k;
-      while (k-- > 0) enqueue_step(c, true);
+      while (k-- > 0) enqueue_step(c, k == 0);
       segment_end(c);
     }
   }

@@ -172,12 +172,20 @@ __device__ __forceinline__ float metaball_value(const float4* __restrict__ cw, i
 }
 
 // Wrap a coordinate into [0, n) on a periodic axis (binary32; inv_n = 1/n rounded, the result is
-// corrected once on either side so it always lands in [0, n)).
+// corrected once on either side). Total: for every float input the result lies in [0, n), so an
+// index formed from it is always in range. Where the fast quotient is off by more than one
+// period (|x| beyond about 2^23 n) the exact binary32 remainder decides; a non-finite
+// coordinate maps to 0 (and is counted by the walker pass as a non-finite velocity or position).
 __device__ __forceinline__ float wrap_coord(float x, float n, int wall, float inv_n) {
   if (wall) return x;
   float w = x - n * floorf(x * inv_n);
   if (w >= n) w -= n;
   if (w < 0.0f) w += n;
+  if (!(w >= 0.0f && w < n)) {   // rare: huge or non-finite x
+    w = fmodf(x, n);
+    if (w < 0.0f) w += n;
+    if (!(w >= 0.0f && w < n)) w = 0.0f;
+  }
   return w;
 }
 __device__ __forceinline__ float wrap_coord(float x, float n, int wall) {

@@ -271,6 +271,18 @@ __device__ __noinline__ unsigned resolve_particles(const WalkCtx& c, const float
   return ev;
 }
 
+// -2 ln U of the 24-bit uniform U = (m + 1/2) 2^-24, m = r >> 8: the square of the Box-Muller
+// radius. The fast logarithm (absolute error about 4e-7 near 1) serves where -2 ln U > 4.8e-4,
+// so that its error moves the radius by less than 2e-5 of a step. For the top 4096 values of m
+// it would dominate the radius (and U itself rounds in binary32 once m >= 2^23), so there
+// ln U = log1p(-v) of the exact v = 1 - U = (2^24 - m - 1/2) 2^-24; the result is never negative.
+__device__ __forceinline__ float neg2_log_uniform(uint32_t r) {
+  const uint32_t m = r >> 8;
+  if (m < 16777216u - 4096u) return -2.0f * __logf(uniform24(r));
+  const float v = ((float)(16777216u - m) - 0.5f) * 5.9604644775390625e-08f;
+  return -2.0f * log1pf(-v);
+}
+
 // pass-1 grid: every block resident at once (5 blocks of 256 threads at 48 registers per SM),
 // looping over the walkers -- measured faster than one block per 256 walkers, and than grids
 // that leave SM room for the kernels beside it
@@ -318,10 +330,11 @@ __global__ void __launch_bounds__(256, 5) walker_kernel(WalkCtx c, float4* __res
       float ux, uy, uz;
       interp_velocity(u, c.g, xw, yw, zw, ux, uy, uz);
       const uint4 r = philox(make_uint4(id, (uint32_t)T, 0u, 0u), k0, k1);
-      // Box-Muller with the fast intrinsics: ln and sin/cos to ~1e-6 absolute, far below the
-      // 2e-5 per-step tolerance; angle 2 pi U = pi + theta with theta = 2 pi (U - 1/2) in (-pi, pi)
-      const float rad01 = sqrtf(-2.0f * __logf(uniform24(r.x)));
-      const float rad23 = sqrtf(-2.0f * __logf(uniform24(r.z)));
+      // Box-Muller: radius from neg2_log_uniform (accurate where U -> 1), angle with the fast
+      // sin/cos (absolute error ~4e-7, far below the 2e-5 per-step tolerance);
+      // angle 2 pi U = pi + theta with theta = 2 pi (U - 1/2) in (-pi, pi)
+      const float rad01 = sqrtf(neg2_log_uniform(r.x));
+      const float rad23 = sqrtf(neg2_log_uniform(r.z));
       float s1, c1, s3, c3;
       __sincosf(6.2831853f * (uniform24(r.y) - 0.5f), &s1, &c1);
       __sincosf(6.2831853f * (uniform24(r.w) - 0.5f), &s3, &c3);
@@ -342,8 +355,13 @@ __global__ void __launch_bounds__(256, 5) walker_kernel(WalkCtx c, float4* __res
         ev_fast = step2 > c.ps.walk_margin * c.ps.walk_margin;
         flagged = need || ev_fast;
       }
-      ev_nonfinite = !(isfinite(ux) && isfinite(uy) && isfinite(uz));
-      if (!flagged) {
+      // a non-finite velocity or position is counted (rwmi_sync reports it) and the walker keeps
+      // its position: nothing non-finite is written back, so later binning stays defined
+      ev_nonfinite = !(isfinite(ux) && isfinite(uy) && isfinite(uz)) ||
+                     !(isfinite(xf[0]) && isfinite(xf[1]) && isfinite(xf[2]));
+      if (ev_nonfinite) {
+        flagged = false;
+      } else if (!flagged) {
         pos[w] = make_float4(xf[0], xf[1], xf[2], p4.w);
       } else {
         ea = make_float4(x[0], x[1], x[2], p4.w);
@@ -448,7 +466,9 @@ __global__ void __launch_bounds__(256, 4) walker_resolve_kernel(WalkCtx c, float
           fa += __fdividef(cc.w, ax * ax + ay * ay + az * az);
           fb += __fdividef(cc.w, bx * bx + by * by + bz * bz);
         }
-        hit = fa >= 1.0f || fb >= 1.0f;
+        // the out-of-line path repeats the test with its own rounding: a 1e-3 margin sends every
+        // walker whose value is anywhere near the surface there, so the two tests never disagree
+        hit = fa >= 1.0f - 1e-3f || fb >= 1.0f - 1e-3f;
       }
     }
     unsigned ev = 0u;
@@ -548,23 +568,35 @@ void launch_set_walkers(const float* pos3, float4* pos, float4* x0, int64_t n, c
 // Eq. 16 binning and the counting sort by cell: histogram with warp-aggregated atomics (lanes
 // holding walkers of the same cell share one atomic), exclusive scan, stable-per-rank scatter.
 // ------------------------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t walker_cell(const float4& p, const Geom& g) {
-  const float x[3] = {p.x, p.y, p.z};
-  int c[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    // floor of the unwrapped coordinate, then its residue mod n (the exact integer wrap of Eq. 16)
-    int i = (int)floorf(x[a]);
-    if (g.wall[a]) {
-      i = min(max(i, 0), g.n[a] - 1);
-    } else {
-      i -= g.n[a] * (int)floorf((float)i * g.inv_n[a]);
-      if (i >= g.n[a]) i -= g.n[a];
-      if (i < 0) i += g.n[a];
-    }
-    c[a] = i;
+// Cell of one coordinate: the floor of the unwrapped coordinate, then its residue mod n on a
+// periodic axis (the exact integer wrap of Eq. 16) or clamped to [0, n-1] on a walled one. Total:
+// every float input gives an index in [0, n-1]. Below 2^22 the integer quotient path is exact
+// (the binary32 quotient is off by at most one period, corrected on either side); beyond it the
+// floor is an integer-valued float whose exact binary32 remainder (fmodf) is the residue; NaN and
+// infinities end in cell 0 (periodic) or the clamped end (walled), never outside the box.
+__device__ __forceinline__ int cell_coord(float xa, int n, int wall, float inv_n) {
+  const float fl = floorf(xa);
+  int i;
+  if (wall) {
+    i = fl >= (float)n ? n - 1 : (fl > 0.0f ? (int)fl : 0);   // NaN compares false: 0
+  } else if (fabsf(xa) < 4194304.0f) {
+    i = (int)fl;
+    i -= n * (int)floorf((float)i * inv_n);
+    if (i >= n) i -= n;
+    if (i < 0) i += n;
+  } else {
+    float r = fmodf(fl, (float)n);
+    if (r < 0.0f) r += (float)n;
+    i = r >= 0.0f && r < (float)n ? (int)r : 0;
   }
-  return ((uint32_t)c[2] * g.n[1] + c[1]) * g.n[0] + c[0];
+  return min(max(i, 0), n - 1);
+}
+
+__device__ __forceinline__ uint32_t walker_cell(const float4& p, const Geom& g) {
+  const int cx = cell_coord(p.x, g.n[0], g.wall[0], g.inv_n[0]);
+  const int cy = cell_coord(p.y, g.n[1], g.wall[1], g.inv_n[1]);
+  const int cz = cell_coord(p.z, g.n[2], g.wall[2], g.inv_n[2]);
+  return ((uint32_t)cz * g.n[1] + cy) * g.n[0] + cx;
 }
 
 __global__ void histogram_kernel(Geom g, const float4* __restrict__ pos, int64_t n,

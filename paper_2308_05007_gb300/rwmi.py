@@ -185,8 +185,36 @@ def bin_walkers_noalloc(dims, wall_mask, pos, counts, pos_sorted=None, stream=No
     """rwmi_bin_walkers_noalloc: walkers per cell (and, optionally, the walkers grouped by cell)
     for callers that cannot allocate device memory. pos, counts, pos_sorted are CUDA tensors
     (float32 [n, 4], uint32/int32 [cells], float32 [n, 4]); asynchronous on `stream`."""
+    import torch
     L = load()
-    d = (C.c_int32 * 3)(*[int(x) for x in dims])
+    dims = tuple(int(x) for x in dims)
+    if len(dims) != 3 or min(dims) < 1:
+        raise ValueError("dims must be three positive sizes")
+    n_cells = dims[0] * dims[1] * dims[2]
+    dev = torch.device("cuda", torch.cuda.current_device())
+    int32_types = {torch.int32} | ({torch.uint32} if hasattr(torch, "uint32") else set())
+
+    def _check(t, name, dtypes, min_numel):
+        if not isinstance(t, torch.Tensor) or t.device != dev:
+            raise ValueError(f"{name} must be a tensor on the current CUDA device {dev}")
+        if t.dtype not in dtypes:
+            raise ValueError(f"{name} has dtype {t.dtype}, expected one of {sorted(map(str, dtypes))}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        if t.numel() < min_numel:
+            raise ValueError(f"{name} holds {t.numel()} elements, needs {min_numel}")
+
+    _check(pos, "pos", {torch.float32}, 0)
+    if pos.numel() % 4:
+        raise ValueError("pos must hold 4 floats per walker")
+    _check(counts, "counts", int32_types, n_cells)
+    if pos_sorted is not None:
+        _check(pos_sorted, "pos_sorted", {torch.float32}, pos.numel())
+        a0, a1 = pos.data_ptr(), pos.data_ptr() + 4 * pos.numel()
+        b0, b1 = pos_sorted.data_ptr(), pos_sorted.data_ptr() + 4 * pos.numel()
+        if pos.numel() and a0 < b1 and b0 < a1:
+            raise ValueError("pos_sorted must not overlap pos")
+    d = (C.c_int32 * 3)(*dims)
     n = pos.numel() // 4
     handle = None
     if stream is not None:

@@ -114,39 +114,79 @@ def test_one_lbm_step_from_identical_populations(q, storage, walls):
 
 
 # ------------------------------------------------------------------------------- trajectories
+def _moments64(x, x0):
+    """{N, mean d, var d, mean x, var x} of positions x (N, 3), d = x - x0, in FP64."""
+    x, x0 = np.asarray(x, np.float64), np.asarray(x0, np.float64)
+    d = x - x0
+    return np.concatenate([[len(x)], d.mean(0), d.var(0), x.mean(0), x.var(0)])
+
+
 @pytest.mark.parametrize("q", [15, 19])
 def test_parity_single_full_length(q):
     """The plain-method case (32^3 periodic, tau 0.8, F = 1e-6 x, one k = 36 sphere, 1e4
-    walkers, D = 0.01, 500 steps, seed 0) against the oracle."""
+    walkers, D = 0.01, 500 steps, seed 0) against the oracle.
+
+    A walker whose GPU and oracle trajectories part at a surface test (a binary32 value within
+    ~1e-6 of f = 1 taking the other branch) ends up to a few step lengths away; every other
+    walker differs by the rounding of its binary32 position only. Those "parted" walkers
+    (|dx| > 1e-3) are counted, and the moments are compared with the oracle's moments of a
+    position set in which only the parted walkers take the GPU's positions: what remains is
+    rounding, held to 1e-5 relative (variances; means against the spread sqrt(var), since a
+    mean displacement near zero has no relative scale)."""
     w = I.parity_single(q=q)
     sim = Sim().from_workload(w)
     ora = Oracle.from_workload(w)
     sim.step(w.steps)
     assert sim.sync() >= 0
     ora.step(w.steps)
-    assert _rel(sim.velocity(), ora.velocity()) <= 1e-5
+    rel_u = _rel(sim.velocity(), ora.velocity())
+    assert rel_u <= 1e-5
     mg = sim.mass_momentum()
     mo = ora.mass_momentum()
     assert mg[0] == pytest.approx(mo[0], rel=1e-7)
     assert np.allclose(mg[1:], mo[1:], rtol=1e-4, atol=1e-6 * np.abs(mo[1:]).max())
-    xg, _ = sim.walkers_by_id()
-    xo, _ = ora.walkers()
-    cg = ora.bin_positions(xg)
-    co = ora.bin_positions(xo.astype(np.float32))
-    assert (cg != co).sum() <= 1e-3 * w.n_walkers
-    close = np.abs(xg - xo).max(1) < 1e-3
-    assert close.mean() >= 1 - 1e-3
-    assert int(sim.concentration().sum()) == w.n_walkers
-    assert np.array_equal(np.sort(sim.concentration()), np.sort(ora.concentration())) or \
-        np.abs(sim.concentration().astype(int) - ora.concentration().astype(int)).sum() <= 2 * (cg != co).sum()
-    m_g, m_o = sim.walker_moments(), ora.moments()
-    assert m_g[0] == m_o[0]
-    # up to 1e-3 N walkers may take the other branch at a surface test, each moving by at most
-    # a few step lengths (~0.2): means within 2e-4, variances within 1e-3 relative
-    assert np.allclose(m_g[[1, 2, 3, 7, 8, 9]], m_o[[1, 2, 3, 7, 8, 9]], rtol=1e-4, atol=2e-4)
-    assert np.allclose(m_g[[4, 5, 6, 10, 11, 12]], m_o[[4, 5, 6, 10, 11, 12]], rtol=1e-3)
+    xg, x0g = sim.walkers_by_id()
+    xo, x0o = ora.walkers()
+    assert np.array_equal(x0g.astype(np.float64), x0o)
+    N = w.n_walkers
+    # cells of each side's own positions (binary32 on the GPU, FP64 in the oracle): the periodic
+    # box wraps floor(x) mod n
+    dims = np.array(w.dims)
+
+    def cells(x):
+        c = np.mod(np.floor(np.asarray(x, np.float64)).astype(np.int64), dims)
+        return (c[:, 2] * dims[1] + c[:, 1]) * dims[0] + c[:, 0]
+
+    assert w.wall_mask == 0
+    cg, co = cells(xg), cells(xo)
+    mis = cg != co
+    dx = np.abs(xg - xo).max(1)
+    parted = dx > 1e-3
+    print(f"C1 D3Q{q}: rel_u {rel_u:.2e}, cells differing {int(mis.sum())}, parted {int(parted.sum())}, "
+          f"max |dx| of the rest {dx[~parted].max():.2e}")
+    assert mis.sum() <= 1e-4 * N
+    assert parted.sum() <= 1e-4 * N
+    assert dx[~parted].max() <= 1e-4
+    # concentration, cell by cell: the GPU's counts are the oracle's, moved only by the walkers
+    # whose cells differ
+    conc_g = sim.concentration().astype(np.int64)
+    conc_o = ora.concentration().astype(np.int64)
+    nc = ora.n_cells
+    assert conc_g.sum() == N
+    assert np.array_equal(conc_g - conc_o, np.bincount(cg[mis], minlength=nc) - np.bincount(co[mis], minlength=nc))
+    m_g = sim.walker_moments()
+    hybrid = np.where(parted[:, None], xg.astype(np.float64), xo)
+    m_h = _moments64(hybrid, x0o)
+    assert m_g[0] == N
+    spread = np.sqrt(np.concatenate([m_h[4:7], m_h[4:7], m_h[10:13], m_h[10:13]]))
+    err_mean = np.abs(m_g[[1, 2, 3, 7, 8, 9]] - m_h[[1, 2, 3, 7, 8, 9]]) / spread[[0, 1, 2, 6, 7, 8]]
+    err_var = np.abs(m_g[[4, 5, 6, 10, 11, 12]] / m_h[[4, 5, 6, 10, 11, 12]] - 1.0)
+    print(f"C1 D3Q{q}: moments, mean err / spread {err_mean.max():.2e}, var rel err {err_var.max():.2e}")
+    assert err_mean.max() <= 1e-5 and err_var.max() <= 1e-5
     fg, fo = sim.particle_forces(), ora.forces()
-    assert np.allclose(fg[:, :3], fo[:, :3], rtol=1e-3, atol=1e-3 * np.abs(fo[:, :3]).max())
+    rel_f = np.abs(fg[:, :3] - fo[:, :3]).max() / np.abs(fo[:, :3]).max()
+    print(f"C1 D3Q{q}: force rel err {rel_f:.2e}")
+    assert rel_f <= 1e-3
 
 
 @pytest.mark.parametrize("q,storage", [(15, 1), (19, 1), (19, 0)])
@@ -188,6 +228,30 @@ def test_one_walker_step_from_identical_inputs(wl):
     xo = ora.walkers_advance(x_prev.astype(np.float64), np.arange(len(x_prev), dtype=np.uint32))
     d = np.abs(x_next - xo).max(1)
     assert (d > 2e-5).mean() <= 1e-3, np.sort(d)[-5:]
+
+
+@pytest.mark.parametrize("word", [0, 2])
+def test_box_muller_radius_at_the_top_of_the_uniform_range(word):
+    """The largest 24-bit uniform, U = 1 - 2^-25, gives -2 ln U = 6e-8 and a Box-Muller radius of
+    2.4e-4: a fast logarithm (absolute error ~4e-7) may return either sign there, and binary32
+    rounds U itself to 1. The oracle's generator finds a seed whose noise for walker 0 at step 0
+    draws that uniform (r >> 8 = 2^24 - 1 in word 0, the radius of x and y, or word 2, the radius
+    of z); one device step of that walker must be finite and match the oracle to 2e-5."""
+    from oracle.oracle import philox, philox_find_seed
+    seed = philox_find_seed(0, 1 << 28, [0, 0, 0, 0], word, 0xFFFFFF)
+    assert seed >= 0 and philox(seed, [0, 0, 0, 0])[word] >> 8 == 0xFFFFFF
+    D = 0.02
+    x0 = np.array([[4.2, 4.3, 4.4]], np.float32)
+    sim = Sim()((8, 8, 8), 0.8, D, seed=seed, q=15)
+    sim.set_walkers(x0)
+    sim.step(1)
+    xg, _ = sim.walkers_by_id()
+    ora = Oracle((8, 8, 8), q=15, tau=0.8, D=D, seed=seed)
+    ora.set_velocity(np.zeros((512, 3)))
+    ora.set_time(0)
+    xo = ora.walkers_advance(x0.astype(np.float64), np.zeros(1, np.uint32))
+    assert np.all(np.isfinite(xg))
+    assert np.abs(xg - xo).max() <= 2e-5, (xg, xo)
 
 
 # ------------------------------------------------------------------------------- invariants
@@ -498,5 +562,5 @@ def test_precision_storages_against_the_oracle():
     # walkers) is binary32, so u carries one binary32 rounding per component
     assert errs[3]["rel_l2_f"] <= 1e-12
     assert errs[3]["rel_l2_u"] <= 2.0 ** -23
-    for st in (0, 1, 2, 3):   # walker branch flips and the velocity error both stay small
-        assert errs[st]["rel_D"] <= 1e-2, (st, errs[st])
+    for st in (0, 1, 2, 3):   # the dispersion coefficient to 1e-5 relative, every storage
+        assert errs[st]["rel_D"] <= 1e-5, (st, errs[st])

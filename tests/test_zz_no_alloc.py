@@ -69,3 +69,75 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     counts = torch.zeros(8, dtype=torch.int32, device="cuda")
     with pytest.raises(RwmiError, match="1048576"):
         bin_walkers_noalloc((128, 128, 128), 0, pos, counts)   # 2^21 cells > 2^20
+
+
+def _cell_of(v, n, walled):
+    """Exact cell of one binary32 coordinate: Python integers, no rounding."""
+    import math
+    v = float(np.float32(v))
+    if math.isnan(v):
+        return 0
+    if math.isinf(v):
+        return (n - 1 if v > 0 else 0) if walled else 0
+    i = math.floor(v)
+    return min(max(i, 0), n - 1) if walled else i % n
+
+
+def test_noalloc_counts_every_walker_inside_the_box_for_any_position():
+    """Unwrapped coordinates far outside the box (+-1e9, +-1e30, 2^40 + 4, where a binary32
+    quotient by the box size is off by many periods) and NaN or infinite ones: every walker is
+    counted in a cell of the box (its exact residue on a periodic axis, the clamped end on a
+    walled one; NaN and infinities in cell 0 of a periodic axis), so the counts sum to n and the
+    sorted copy holds every walker."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2308_05007_gb300.rwmi import bin_walkers_noalloc, load
+
+    load()
+    dims, wall_mask = (7, 5, 6), 4            # z walled, x and y periodic
+    vals = [0.5, 3.25, -0.75, 1e9, -1e9, 1e30, -1e30, 123456789.0, 2.0 ** 40 + 4, np.inf, -np.inf, np.nan]
+    rng = np.random.default_rng(5)
+    pos = []
+    for a in range(3):
+        for v in vals:
+            p = rng.uniform(0.0, 5.0, 3)
+            p[a] = v
+            pos.append(p)
+    pos = np.array(pos, np.float32)
+    n = len(pos)
+    want = np.zeros(np.prod(dims), np.int64)
+    for p in pos:
+        c = [_cell_of(p[a], dims[a], (wall_mask >> a) & 1) for a in range(3)]
+        want[(c[2] * dims[1] + c[1]) * dims[0] + c[0]] += 1
+    pos4 = np.concatenate([pos, np.arange(n, dtype=np.uint32).view(np.float32)[:, None]], axis=1)
+    posd = torch.from_numpy(np.ascontiguousarray(pos4)).cuda()
+    counts = torch.full((int(np.prod(dims)),), 9, dtype=torch.int32, device="cuda")
+    out = torch.zeros_like(posd)
+    bin_walkers_noalloc(dims, wall_mask, posd, counts, out)
+    torch.cuda.synchronize()
+    got = counts.cpu().numpy().view(np.uint32)
+    assert got.sum() == n
+    assert np.array_equal(got, want)
+    assert np.array_equal(np.sort(out.cpu().numpy()[:, 3].view(np.uint32)), np.arange(n))
+
+
+def test_noalloc_binding_refuses_bad_buffers():
+    """The Python binding checks device, dtype, contiguity, sizes and overlap before the call."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2308_05007_gb300.rwmi import bin_walkers_noalloc
+
+    pos = torch.zeros((16, 4), dtype=torch.float32, device="cuda")
+    counts = torch.zeros(64, dtype=torch.int32, device="cuda")
+    with pytest.raises(ValueError, match="counts holds"):
+        bin_walkers_noalloc((4, 4, 5), 0, pos, counts)                      # 80 cells > 64
+    with pytest.raises(ValueError, match="overlap"):
+        bin_walkers_noalloc((4, 4, 4), 0, pos, counts, pos)
+    with pytest.raises(ValueError, match="current CUDA device"):
+        bin_walkers_noalloc((4, 4, 4), 0, pos.cpu(), counts)
+    with pytest.raises(ValueError, match="4 floats"):
+        bin_walkers_noalloc((4, 4, 4), 0, pos.reshape(-1)[:30], counts)
+    with pytest.raises(ValueError, match="dtype"):
+        bin_walkers_noalloc((4, 4, 4), 0, pos, counts.to(torch.int64))
