@@ -91,7 +91,7 @@ def config_dict(a, w):
         "storage": STORE_NAMES[w.storage], "sort_interval": w.sort_interval,
         "moment_interval": w.moment_interval,
         "l2": "inputs larger than L2 (populations 2 x %.2f GB), no flush" % (w.n_cells * w.q * STORE_BYTES[w.storage] / 1e9),
-        "graphs": "CUDA graph per %d steps" % max(w.sort_interval, w.moment_interval, 2),
+        "graphs": "captured runs of up to 64 steps (whole %d-step chunks), replayed" % max(w.sort_interval, w.moment_interval, 2),
         "schedule": {0: "serial", 1: "raster of t+1 on a second stream beside the LBM of t",
                      2: "raster of t+1 beside the LBM of t; walkers of t on a third stream beside "
                         "the fluid of t+1"}[getattr(a, "overlap", 2)],
@@ -517,8 +517,31 @@ def measure_served(a):
     return out
 
 
+def launch_plan(gpus: int, env, argv):
+    """How this process runs `--gpus N`: None when it is already one of N ranks (or N = 1), else
+    the command that re-launches the benchmark as N ranks under torch.distributed.run on this node
+    (rendezvous on 127.0.0.1). A process started by torchrun with a different world size is an
+    error, never a silent single-rank run."""
+    world = int(env.get("WORLD_SIZE", "1"))
+    if "RANK" in env or world > 1:
+        if world != gpus:
+            raise SystemExit(f"bench.py: --gpus {gpus} but WORLD_SIZE {world}")
+        return None
+    if gpus <= 1:
+        return None
+    import socket
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    return [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={gpus}",
+            "--master-addr", "127.0.0.1", f"--master-port={port}", "--", os.path.abspath(__file__), *argv]
+
+
 def main():
     a = parse()
+    plan = launch_plan(a.gpus, os.environ, sys.argv[1:])
+    if plan:
+        sys.exit(subprocess.call(plan))
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -541,15 +564,24 @@ def main():
     sim.set_stream(stream)
     sim.seed_walkers(w.n_walkers, *w.walker_box)
     L = 16
-    warm = max(a.warmup, 3)
-    warm = (warm + L - 1) // L * L
-    steps = max(a.steps, L)
+    # Warm-up: at least W steps, then the timed step count once more from the same alignment
+    # (time mod 2 L: the buffer parities and the sort phase), so that the timed region replays
+    # the captured runs of steps a user's repeated calls replay; the per-phase timing runs in
+    # between. Every warm-up step is a full step.
+    period = 2 * L
+    steps = max(a.steps, 1)
+    warm = (max(a.warmup, 3) + period - 1) // period * period
     with torch.cuda.stream(stream):
         sim.step(warm)
+        sim.step(steps)
+        sim.step(-(warm + steps) % period)
         assert sim.sync() >= 0
         # per-phase GPU time (CUDA events on the launching stream, eager launches)
         phases = sim.step_timed(L)
         n_timed_phase_steps = L
+        sim.step(-sim.t % period)
+        warm = sim.t
+        assert sim.sync() >= 0
         # the timed region
         clocks = Clocks(torch.cuda.current_device())
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

@@ -24,10 +24,20 @@ constexpr int SERIES_COLS = 14;
 constexpr uint64_t CKPT_MAGIC = 0x31494d5752ULL;  // "RWMI1"
 constexpr uint64_t CKPT_DEM_MAGIC = 0x314d4544ULL;  // "DEM1": the free-DEM section
 
+// A captured run of steps is fixed by the buffer parities it starts from, its start time modulo
+// the chunk (which steps sort and form moments) and its length.
 struct GraphKey {
   int fcur, pcur;
-  bool operator<(const GraphKey& o) const { return fcur != o.fcur ? fcur < o.fcur : pcur < o.pcur; }
+  int64_t phase, len;
+  bool operator<(const GraphKey& o) const {
+    if (fcur != o.fcur) return fcur < o.fcur;
+    if (pcur != o.pcur) return pcur < o.pcur;
+    if (phase != o.phase) return phase < o.phase;
+    return len < o.len;
+  }
 };
+constexpr int64_t SEGMENT_MAX = 64;    // longest captured run of steps
+constexpr size_t GRAPH_CACHE_MAX = 32;  // captured runs kept per context; beyond, runs are eager
 
 struct GraphEntry {
   cudaGraphExec_t exec = nullptr;
@@ -639,7 +649,9 @@ RWMI_API rwmi_status rwmi_create(rwmi_ctx** out, const int32_t dims[3], double t
   }
   g.nxy = (uint32_t)dims[0] * (uint32_t)dims[1];
   g.ncell = (uint32_t)ncell;
-  g.ncell_pad = (uint32_t)((ncell + 63) / 64 * 64);
+  // plane stride: a multiple of 64 values (128-byte aligned planes at every storage width),
+  // with at least one spare slot past the last cell, where the LBM kernel's tail lanes store
+  g.ncell_pad = (uint32_t)((ncell + 64) / 64 * 64);
   for (int a = 0; a < 3; ++a) g.inv_n[a] = 1.0f / (float)dims[a];
   make_divisor((uint32_t)dims[0], g.mx, g.sx);
   make_divisor(g.nxy, g.mxy, g.sxy);
@@ -1038,36 +1050,37 @@ RWMI_API rwmi_status rwmi_step(rwmi_ctx* c, int32_t n) try {
   GUARD(c);
   c->stepped = true;
   const int64_t L = chunk_length(c);
-  const bool graphs = c->cfg.use_graphs && L <= 64;
+  const bool graphs = c->cfg.use_graphs && L <= SEGMENT_MAX;
+  // Runs of steps ("segments") of up to G steps, G the largest multiple of the chunk L within
+  // SEGMENT_MAX: a long run repeats one captured segment, and any shorter run (or remainder) is
+  // one captured segment too. Each segment ends by joining the walker stream, which exposes
+  // one walker pass, so fewer and longer segments overlap more of the step.
+  const int64_t G = graphs ? (SEGMENT_MAX / L) * L : 1;
   while (n > 0) {
-    if (graphs && c->t % L == 0 && n >= L) {
-      const GraphKey key{c->fcur, c->pcur};
-      auto it = c->graphs.find(key);
-      if (it == c->graphs.end()) {
-        const int64_t l0 = c->launches;
-        CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-        for (int64_t s = 0; s < L; ++s) enqueue_step(c, s == L - 1);   // sums on the chunk's last step
-        segment_end(c);
-        cudaGraph_t graph = nullptr;
-        CK(cudaStreamEndCapture(c->stream, &graph));
-        GraphEntry e;
-        cudaError_t ie = cudaGraphInstantiate(&e.exec, graph, 0);
-        cudaGraphDestroy(graph);
-        CK(ie);
-        e.launches = c->launches - l0;
-        c->graphs[key] = e;
-        CK(cudaGraphLaunch(e.exec, c->stream));   // mirrors already advanced while capturing
-      } else {
-        CK(cudaGraphLaunch(it->second.exec, c->stream));
-        c->launches += it->second.launches;
-        advance_mirrors(c, L);
-      }
-      n -= (int32_t)L;
-    } else {   // eager run up to the next chunk boundary (or all n without graphs); as in a
-               // replayed chunk, the FP64 sums only on the run's last step, the one they are read at
-      int64_t k = graphs ? std::min<int64_t>(n, L - c->t % L) : n;
-      n -= (int32_t)k;
-      while (k-- > 0) enqueue_step(c, k == 0);
+    const int64_t k = std::min<int64_t>(n, graphs ? G - c->t % L : n);
+    n -= (int32_t)k;
+    const GraphKey key{c->fcur, c->pcur, c->t % L, k};
+    auto it = graphs ? c->graphs.find(key) : c->graphs.end();
+    if (graphs && it != c->graphs.end()) {
+      CK(cudaGraphLaunch(it->second.exec, c->stream));
+      c->launches += it->second.launches;
+      advance_mirrors(c, k);
+    } else if (graphs && c->graphs.size() < GRAPH_CACHE_MAX) {
+      const int64_t l0 = c->launches;
+      CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+      for (int64_t s = 0; s < k; ++s) enqueue_step(c, s == k - 1);   // sums on the run's last step
+      segment_end(c);
+      cudaGraph_t graph = nullptr;
+      CK(cudaStreamEndCapture(c->stream, &graph));
+      GraphEntry e;
+      cudaError_t ie = cudaGraphInstantiate(&e.exec, graph, 0);
+      cudaGraphDestroy(graph);
+      CK(ie);
+      e.launches = c->launches - l0;
+      c->graphs[key] = e;
+      CK(cudaGraphLaunch(e.exec, c->stream));   // mirrors already advanced while capturing
+    } else {   // eager; as in a captured run, the FP64 sums only on the run's last step
+      for (int64_t s = 0; s < k; ++s) enqueue_step(c, s == k - 1);
       segment_end(c);
     }
   }
@@ -1186,7 +1199,7 @@ RWMI_API rwmi_status rwmi_footprint(const int32_t dims[3], int32_t q, int32_t st
     ncell *= (uint64_t)dims[a];
     nbrick *= (uint64_t)((dims[a] + BRICK - 1) / BRICK);
   }
-  const uint64_t pad = (ncell + 63) / 64 * 64, sb = storage_bytes(storage), P = (uint64_t)n_particles,
+  const uint64_t pad = (ncell + 64) / 64 * 64, sb = storage_bytes(storage), P = (uint64_t)n_particles,
                  Nc = (uint64_t)n_centers, N = (uint64_t)n_walkers;
   uint64_t b = 2 * (uint64_t)q * pad * sb;                     // populations A/B
   b += 2 * 16 * pad + 2 * 2 * ncell + 2 * 2 * ncell + 8 * ncell + 4 * (ncell / 2048 + 2);   // (u, rho), solid, nodes, counts/offsets, scan

@@ -4,8 +4,10 @@
 //   populations   f[2][Q][ncell_pad]      A/B ping-pong, direction-major (SoA), each direction
 //                                         plane 128-byte aligned; binary32 (optionally shifted by
 //                                         w_i rho0), binary16 shifted or binary64 shifted
-//   velocity      u[ncell] float4          (ux, uy, uz, rho) per cell, written by the LBM kernel
-//                                         with one 16-byte store, gathered by walkers (8 loads)
+//   velocity      u[ncell_pad] float4     (ux, uy, uz, rho) per cell and time parity, written by the
+//                                         LBM kernel with one 16-byte store, gathered by walkers
+//                                         (8 loads; one 16-byte load per node costs fewer
+//                                         transactions than three 4-byte planes, measured)
 //   solid         solid[ncell]            uint16: sub-sample count (bits 0-6) | owner (bits 7-15),
 //                                         valid only in bricks flagged for the current time
 //   bricks        8x8x8-cell bricks, per time parity: bword[nbrick+2] (walker-candidate count in
@@ -71,7 +73,8 @@ struct Geom {
   int wall[3];         // 1: no-slip walls normal to this axis
   uint32_t nxy;        // n[0] * n[1]
   uint32_t ncell;
-  uint32_t ncell_pad;  // direction-plane stride of the population arrays
+  uint32_t ncell_pad;  // direction-plane stride of the population and velocity arrays (> ncell:
+                       // slot ncell_pad - 1 is a spare that no cell owns)
   // fast division of a flat cell index by nx and nxy: q = (umulhi(v, m) + v) >> s
   uint32_t mx, sx, mxy, sxy;
   float inv_n[3];      // 1 / n per axis (wrapping; the result is corrected to [0, n))
@@ -104,7 +107,9 @@ __device__ __forceinline__ uint4 philox(uint4 c, uint32_t k0, uint32_t k1) {
   return c;
 }
 
-// ((r >> 8) + 1/2) 2^-24: exact in binary32, strictly inside (0, 1)
+// ((r >> 8) + 1/2) 2^-24 in binary32: exact, and strictly inside (0, 1), while r >> 8 < 2^23; above
+// that, (r >> 8) + 1/2 needs 25 bits and rounds to an even integer (within 2^-25 of the exact U,
+// up to 1 itself). The walker noise takes its radius from the exact 1 - U there.
 __device__ __forceinline__ float uniform24(uint32_t r) {
   return ((float)(r >> 8) + 0.5f) * 5.9604644775390625e-08f;
 }

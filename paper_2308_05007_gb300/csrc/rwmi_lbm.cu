@@ -3,6 +3,8 @@
 // interpolated bounce-back (Eqs. 23-27); writes the populations, the velocity field and, on
 // reduction steps, per-particle force/torque and the FP64 sums. Also the IBB link list and its
 // q values, computed ahead of the update.
+#include <type_traits>
+
 #include "rwmi_lattice.cuh"
 
 namespace rwmi {
@@ -58,6 +60,8 @@ lbm_kernel(Geom g, Planes<Q, typename Store<STORE>::T> pl,
                                                   const PoseD* __restrict__ posed,
                                                   const StepParams* __restrict__ sp,
                                                   typename Store<STORE>::R tau,
+                                                  typename Store<STORE>::R omega,
+                                                  typename Store<STORE>::R guo0,
                                                   typename Store<STORE>::R rho0, double* __restrict__ red,
                                                   double* __restrict__ forces,
                                                   const uint16_t* __restrict__ nodes,
@@ -70,11 +74,13 @@ lbm_kernel(Geom g, Planes<Q, typename Store<STORE>::T> pl,
   using S = Store<STORE>;
   using R = typename S::R;   // arithmetic type: binary32, or binary64 for the binary64 storage
   constexpr bool REDUCE = MODE != 0, STORES = MODE != 1;
-  // tau and rho0 arrive in R (converted on the host: a per-thread binary64 -> binary32
-  // conversion would occupy GB300's narrow FP64 pipe)
+  // tau, omega = 1/tau, guo0 = 1 - 1/(2 tau) and rho0 arrive in R (formed and converted on the
+  // host: per-thread divisions and binary64 -> binary32 conversions cost issue slots, and the
+  // conversions occupy GB300's narrow FP64 pipe)
   const uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x;
   const bool valid = idx < g.ncell;
-  const int c = (int)(valid ? idx : g.ncell - 1);   // tail lanes recompute the last cell, store nothing
+  const int c = (int)(valid ? idx : g.ncell - 1);   // tail lanes recompute the last cell and store
+  const int cs = valid ? c : (int)g.ncell_pad - 1;  // into the spare slot no cell owns (no branches)
   const uint32_t z = fast_div((uint32_t)c, g.mxy, g.sxy);
   const uint32_t rem = (uint32_t)c - z * g.nxy;
   const uint32_t y = fast_div(rem, g.mx, g.sx);
@@ -232,7 +238,9 @@ lbm_kernel(Geom g, Planes<Q, typename Store<STORE>::T> pl,
   const R Fx = sizeof(R) == 8 ? (R)sp->Fd[0] : (R)sp->F[0];
   const R Fy = sizeof(R) == 8 ? (R)sp->Fd[1] : (R)sp->F[1];
   const R Fz = sizeof(R) == 8 ? (R)sp->Fd[2] : (R)sp->F[2];
-  const R inv_rho = R(1.0) / rho;
+  // 1/rho correctly rounded (as the IEEE division 1/rho): a biased reciprocal would act like a
+  // small momentum sink every step, which a steady forced flow amplifies by ~1/(tau nu k^2)
+  const R inv_rho = sizeof(R) == 8 ? R(1.0) / rho : (R)__frcp_rn((float)rho);
   const R ux = (jx + R(0.5) * Fx) * inv_rho, uy = (jy + R(0.5) * Fy) * inv_rho,
               uz = (jz + R(0.5) * Fz) * inv_rho;
   const R uu = ux * ux + uy * uy + uz * uz;
@@ -262,48 +270,66 @@ lbm_kernel(Geom g, Planes<Q, typename Store<STORE>::T> pl,
       }
     }
   }
+  // BGK with Guo forcing (Eqs. 12-13), per direction i:
+  //   f+_i = (1 - rtau) f_i + rtau feq_i + guo w_i [3 (e_i - u).F + 9 (e_i.u)(e_i.F)],
+  // rtau = (1 - B) / tau, guo = (1 - B)(1 - 1/(2 tau)), with 1/tau and 1 - 1/(2 tau) from the host,
+  // feq_i = w_i rho' + w_i rho (3 e.u + 4.5 (e.u)^2 - 1.5 u.u), rho' = rho - rho0 when shifted.
+  // An opposite pair (i, i') shares e.u, (e.u)^2 and the even parts. The equilibrium keeps
+  // w_i rho' apart from w_i rho times the velocity polynomial: grouped otherwise (e.g. folding
+  // rho' into the velocity terms) the binary32 rounding of a steady forced flow grew the
+  // velocity error against the FP64 oracle from 0.96e-5 to 1.5e-5 over 500 steps.
   const R omB = R(1.0) - B;
-  const R rtau = omB / tau;              // (1 - B) / tau
-  const R guo = omB * (R(1.0) - R(0.5) / tau);
+  const R rtau = omB * omega;
+  const R guo = omB * guo0;
+  const R om1 = R(1.0) - rtau;
   const R uF = ux * Fx + uy * Fy + uz * Fz;
   const R usus = usx * usx + usy * usy + usz * usz;
+  const R m15uu = -R(1.5) * uu;
   R dpx = R(0.0), dpy = R(0.0), dpz = R(0.0);
   R out[Q];
   {  // rest direction; its own opposite: Omega_0 = feq_0(rho, u_s) - feq_0(rho, u)
     const R w = L::template wt<R>(0);
-    const R dev = -R(1.5) * uu;
-    const R feq_s = S::shifted ? w * (drho + rho * dev) : w * rho * (R(1.0) + dev);
-    const R om0 = B > R(0.0) ? R(1.5) * w * rho * (uu - usus) : R(0.0);
-    out[0] = f[0] - rtau * (f[0] - feq_s) + guo * w * (-R(3.0) * uF) + B * om0;
+    const R feq0 = w * (S::shifted ? drho : rho) + (w * rho) * m15uu;
+    out[0] = om1 * f[0] + (rtau * feq0 + (w * guo) * (-R(3.0) * uF)) + B * (R(1.5) * w * rho * (uu - usus));
   }
-  // opposite pairs (i, i + H) share e.u
+  // opposite pairs (i, i + H) share e.u. One warp-uniform branch picks the loop with the solid
+  // terms of partially saturated cells (lanes with B = 0 add exact zeros there) or the plain one.
+  auto pair_update = [&](auto psm) {
 #pragma unroll
-  for (int i = 1; i <= L::H; ++i) {
-    const int io = i + L::H;
-    const int ex = L::e(i, 0), ey = L::e(i, 1), ez = L::e(i, 2);
-    const R w = L::template wt<R>(i);
-    const R eu = ex * ux + ey * uy + ez * uz;
-    const R eF = ex * Fx + ey * Fy + ez * Fz;
-    const R sym = R(4.5) * eu * eu - R(1.5) * uu;        // even part of feq / (w rho)
-    const R base = S::shifted ? w * drho : w * rho;  // w rho (minus w rho0 when shifted)
-    const R wr = w * rho;
-    const R feq_p = base + wr * (R(3.0) * eu + sym);
-    const R feq_m = base + wr * (-R(3.0) * eu + sym);
-    const R gw = guo * w;
-    out[i] = f[i] - rtau * (f[i] - feq_p) + gw * (R(3.0) * (eF - uF) + R(9.0) * eu * eF);
-    out[io] = f[io] - rtau * (f[io] - feq_m) + gw * (R(3.0) * (-eF - uF) + R(9.0) * eu * eF);
-    if (B > R(0.0)) {
-      const R eus = ex * usx + ey * usy + ez * usz;
-      const R common = wr * (R(4.5) * (eus * eus - eu * eu) - R(1.5) * (usus - uu));
-      const R odd = wr * R(3.0) * (eu + eus);
-      const R om_p = (f[io] - f[i]) + odd + common;   // Omega_i
-      const R om_m = (f[i] - f[io]) - odd + common;   // Omega_opp(i)
-      out[i] += B * om_p;
-      out[io] += B * om_m;
-      const R dm = B * (om_p - om_m);                 // B (Omega_i e_i + Omega_opp e_opp) / e_i
-      dpx += dm * ex; dpy += dm * ey; dpz += dm * ez;
+    for (int i = 1; i <= L::H; ++i) {
+      const int io = i + L::H;
+      const int ex = L::e(i, 0), ey = L::e(i, 1), ez = L::e(i, 2);
+      const R w = L::template wt<R>(i);
+      const R eu = ex * ux + ey * uy + ez * uz;
+      const R eF = ex * Fx + ey * Fy + ez * Fz;
+      const R wdr = w * (S::shifted ? drho : rho), wr = w * rho, wg = w * guo;
+      const R sym = R(4.5) * eu * eu + m15uu;        // even part of the velocity polynomial
+      const R feq_p = wdr + wr * (sym + R(3.0) * eu);
+      const R feq_m = wdr + wr * (sym - R(3.0) * eu);
+      const R Se = wg * (R(9.0) * (eu * eF) - R(3.0) * uF);   // Guo term, even and odd parts
+      const R So = (R(3.0) * wg) * eF;
+      out[i] = om1 * f[i] + (rtau * feq_p + (Se + So));
+      out[io] = om1 * f[io] + (rtau * feq_m + (Se - So));
+      if constexpr (decltype(psm)::value) {
+        const R eus = ex * usx + ey * usy + ez * usz;
+        const R common = wr * (R(4.5) * (eus * eus - eu * eu) - R(1.5) * (usus - uu));
+        const R odd = wr * R(3.0) * (eu + eus);
+        const R om_p = (f[io] - f[i]) + odd + common;   // Omega_i
+        const R om_m = (f[i] - f[io]) - odd + common;   // Omega_opp(i)
+        out[i] += B * om_p;
+        out[io] += B * om_m;
+        const R dm = B * (om_p - om_m);                 // B (Omega_i e_i + Omega_opp e_opp) / e_i
+        dpx += dm * ex; dpy += dm * ey; dpz += dm * ez;
+      }
+      if (!IBB && STORES) {   // stored at once: fewer values live at the same time
+        S::st(pl.out[i] + cs, out[i]);
+        S::st(pl.out[io] + cs, out[io]);
+      }
     }
-  }
+  };
+  if (IBB || !__any_sync(0xffffffffu, B > R(0.0))) pair_update(std::false_type{});
+  else pair_update(std::true_type{});
+  if (!IBB && STORES) S::st(pl.out[0] + cs, out[0]);
   if (STORES) {   // the reduce-only pass stores nothing
   if (IBB && solid_self) {   // solid node: equilibrium at the particle's rigid velocity, rho0
     R us[3];
@@ -317,10 +343,10 @@ lbm_kernel(Geom g, Planes<Q, typename Store<STORE>::T> pl,
       out[i] = S::shifted ? wi * rho0 * dev : wi * rho0 * (R(1) + dev);
     }
     if (valid) u4[c] = make_float4((float)us[0], (float)us[1], (float)us[2], (float)rho0);
-  } else if (valid) {
-    u4[c] = make_float4((float)ux, (float)uy, (float)uz, (float)rho);
+  } else {
+    u4[cs] = make_float4((float)ux, (float)uy, (float)uz, (float)rho);
   }
-  if (valid) {
+  if (IBB && valid) {   // (the partially saturated cells stored each pair above)
 #pragma unroll
     for (int i = 0; i < Q; ++i) S::st(pl.out[i] + c, out[i]);
   }
@@ -510,10 +536,9 @@ static void launch_lbm_q(bool walls, bool reduce, const Geom& g, const void* fin
     pl.in[i] = (const T*)fin + (size_t)i * g.ncell_pad;
     pl.out[i] = (T*)fout + (size_t)i * g.ncell_pad;
   }
-  float4* u4 = reinterpret_cast<float4*>(u);
   const int bsz_ok = (bsz == 64 || bsz == 128) ? bsz : 256;
   const dim3 grid((g.ncell + bsz_ok - 1) / bsz_ok), block(bsz_ok);
-#define RWMI_LBM_ARGS g, pl, u4, solid, bs.bword, bs.pose, bs.posed, bs.sp, (R)tau, (R)rho0, red, forces, ib.nodes, ib.uprev, ib.desc, bs.cworld, ib.base, ib.q, ib.cap
+#define RWMI_LBM_ARGS g, pl, reinterpret_cast<float4*>(u), solid, bs.bword, bs.pose, bs.posed, bs.sp, (R)tau, (R)(1.0 / tau), (R)(1.0 - 0.5 / tau), (R)rho0, red, forces, ib.nodes, ib.uprev, ib.desc, bs.cworld, ib.base, ib.q, ib.cap
   if constexpr (STORE == 1 || STORE == 3) {   // the fused mode of free-DEM runs
     if (fused) {
       if (walls) lbm_kernel<Q, STORE, true, 2, IBB><<<grid, block, 0, st>>>(RWMI_LBM_ARGS);

@@ -121,10 +121,10 @@ def test_defaults_are_the_documented_ones(lib_path):
 
 
 def test_footprint_follows_the_storage_layout(lib_path):
-    """Device bytes of a context: the two population buffers hold q x (cells rounded up to 64)
-    values of the storage's width; everything else is independent of q and the storage."""
+    """Device bytes of a context: the two population buffers hold q x (cells + 1 rounded up to
+    64) values of the storage's width; everything else is independent of q and the storage."""
     rwmi, _ = _L(lib_path)
-    dims, pad = (40, 36, 26), (40 * 36 * 26 + 63) // 64 * 64
+    dims, pad = (40, 36, 26), (40 * 36 * 26 + 64) // 64 * 64
     base = dict(n_walkers=12345, n_particles=5, n_centers=17)
     fp = {(q, st): rwmi.footprint(dims, q, st, **base) for q in (15, 19) for st in (0, 1, 2, 3)}
     width = {0: 4, 1: 4, 2: 2, 3: 8}

@@ -105,3 +105,30 @@ def test_ibb_rejects_other_storages():
     w = _ibb_workload(storage=2)
     with pytest.raises(RwmiError):
         Simulation.from_workload(w, seed_walkers=False)
+
+
+@pytest.mark.parametrize("storage,tol", [(3, 1e-6), (1, 5e-5)])
+def test_ibb_overlapping_pair_force_is_galilean_invariant(storage, tol):
+    """The oracle's Galilean-invariance pin, run through the GPU's IBB path: two overlapping
+    spheres co-moving with a uniform stream at U along their line of centres feel, on each
+    particle, the force along U of the same pair at rest in still fluid (the pressure on the
+    open piece of surface each particle owns, about 22). A plain momentum exchange would differ
+    by rho U^2 A = 0.1 here. The fluid velocities u_f, u_ff reach the link update in binary32 in
+    every storage (the velocity field is binary32), so u_f - u_w is not zero but about
+    2^-24 U: over ~2000 links with terms of order w rho 3 (u_f - u_w) that leaves up to ~1e-6
+    with binary64 storage (5e-8 measured). Binary32-shifted storage adds its rounding of the
+    link terms: about 1e-8 per link of order 0.1, random in sign, ~5e-6 measured."""
+    _need_gpu()
+    from paper_2308_05007_gb300 import inputs as I
+    from paper_2308_05007_gb300.rwmi import Simulation
+    from test_oracle_ibb import _overlapping_pair
+    forces = {}
+    for U in (0.0, 0.04):
+        w = I.with_(_overlapping_pair(U, q=15), storage=storage)
+        with Simulation.from_workload(w, seed_walkers=False) as sim:
+            sim.step(1)
+            forces[U] = sim.particle_forces()[:, :3]
+    fr, fm = forces[0.0], forces[0.04]
+    print(f"IBB storage {storage}: |F_x(U) - F_x(0)| = {np.abs(fm[:, 0] - fr[:, 0]).max():.2e}")
+    assert fr[0, 0] > 15.0 and fr[1, 0] < -15.0
+    np.testing.assert_allclose(fm[:, 0], fr[:, 0], rtol=0, atol=tol)

@@ -126,13 +126,16 @@ def test_parity_single_full_length(q):
     """The plain-method case (32^3 periodic, tau 0.8, F = 1e-6 x, one k = 36 sphere, 1e4
     walkers, D = 0.01, 500 steps, seed 0) against the oracle.
 
-    A walker whose GPU and oracle trajectories part at a surface test (a binary32 value within
-    ~1e-6 of f = 1 taking the other branch) ends up to a few step lengths away; every other
-    walker differs by the rounding of its binary32 position only. Those "parted" walkers
-    (|dx| > 1e-3) are counted, and the moments are compared with the oracle's moments of a
-    position set in which only the parted walkers take the GPU's positions: what remains is
-    rounding, held to 1e-5 relative (variances; means against the spread sqrt(var), since a
-    mean displacement near zero has no relative scale)."""
+    A walker whose GPU and oracle trajectories part at a surface decision ends up to a few step
+    lengths away: Algorithm 1 stops at the first midpoint with |f - 1| < 1e-3, and a midpoint
+    whose binary32 value lies on the other side of that tolerance than its FP64 value makes the
+    two stop one bisection step apart (several results are correct there); an inside test
+    within ~1e-6 of f = 1 can flip likewise. Every other walker differs by the rounding of its
+    binary32 position: about 2e-6 per step over 500 steps, so up to ~2e-4 at the tail of 1e4
+    walkers. The "parted" walkers (|dx| > 1e-3) are counted and held to 1e-3 N; the moments are
+    compared with the oracle's moments of a position set in which only the parted walkers take
+    the GPU's positions. What remains is rounding, held to 1e-5 relative (variances; means
+    against the spread sqrt(var), since a mean displacement near zero has no relative scale)."""
     w = I.parity_single(q=q)
     sim = Sim().from_workload(w)
     ora = Oracle.from_workload(w)
@@ -162,11 +165,18 @@ def test_parity_single_full_length(q):
     mis = cg != co
     dx = np.abs(xg - xo).max(1)
     parted = dx > 1e-3
+    hist = np.histogram(np.log10(np.maximum(dx, 1e-12)), bins=[-13, -6, -5, -4, -3, -2, -1, 2])[0]
     print(f"C1 D3Q{q}: rel_u {rel_u:.2e}, cells differing {int(mis.sum())}, parted {int(parted.sum())}, "
-          f"max |dx| of the rest {dx[~parted].max():.2e}")
+          f"max |dx| of the rest {dx[~parted].max():.2e}, |dx| per decade from 1e-6: {hist.tolist()}")
     assert mis.sum() <= 1e-4 * N
-    assert parted.sum() <= 1e-4 * N
-    assert dx[~parted].max() <= 1e-4
+    assert parted.sum() <= 1e-3 * N
+    assert dx[~parted].max() <= 5e-4
+    # the walker-type counts of both sides (a parted walker may count differently from then on)
+    cgc, coc = sim.counters(), ora.counters()
+    print(f"C1 D3Q{q}: type II/III/IV GPU {[cgc[k] for k in ('type_II', 'type_III', 'type_IV')]}, "
+          f"oracle {[coc[k] for k in ('type_II', 'type_III', 'type_IV')]}")
+    for k in ("type_II", "type_III", "type_IV"):
+        assert abs(cgc[k] - coc[k]) <= max(3, 0.02 * coc[k]), (k, cgc[k], coc[k])
     # concentration, cell by cell: the GPU's counts are the oracle's, moved only by the walkers
     # whose cells differ
     conc_g = sim.concentration().astype(np.int64)
@@ -186,7 +196,7 @@ def test_parity_single_full_length(q):
     fg, fo = sim.particle_forces(), ora.forces()
     rel_f = np.abs(fg[:, :3] - fo[:, :3]).max() / np.abs(fo[:, :3]).max()
     print(f"C1 D3Q{q}: force rel err {rel_f:.2e}")
-    assert rel_f <= 1e-3
+    assert rel_f <= 5e-5   # 8.4e-6 measured: the velocity error (1e-5) carried into -B sum Omega e
 
 
 @pytest.mark.parametrize("q,storage", [(15, 1), (19, 1), (19, 0)])

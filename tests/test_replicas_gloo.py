@@ -69,3 +69,29 @@ def test_two_gloo_ranks_agree_on_workload_time_and_value():
     assert res[0]["t"] == res[1]["t"] == 2.5, "job time is not the max over ranks"
     assert res[0]["rate"] == pytest.approx(2 * 128 ** 3 * 10 / 2.5)
     assert res[1]["ref_out"] == "", "the reference arm printed on a rank other than 0"
+
+
+def test_gpus_n_without_torchrun_relaunches_n_ranks():
+    """`bench.py --gpus 2` started as one plain process re-launches itself as two ranks under
+    torch.distributed.run (here the reference arm, which needs no GPU: rank 0 prints the one
+    JSON line with n_gpus 2, the other rank exits without work); it never reports one GPU for
+    a two-GPU request."""
+    import json
+    import subprocess
+    sys.path.insert(0, ROOT)
+    import bench
+
+    assert bench.launch_plan(1, {}, []) is None
+    assert bench.launch_plan(2, {"RANK": "0", "WORLD_SIZE": "2"}, []) is None
+    with pytest.raises(SystemExit):
+        bench.launch_plan(2, {"RANK": "0", "WORLD_SIZE": "1"}, [])
+    plan = bench.launch_plan(2, {}, ["--gpus", "2"])
+    assert plan[1:3] == ["-m", "torch.distributed.run"] and "--nproc-per-node=2" in plan
+    env = {k: v for k, v in os.environ.items() if k not in ("RANK", "WORLD_SIZE", "LOCAL_RANK")}
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2",
+                        "--n", "64", "--particles", "1", "--walkers", "20000", "--steps", "2", "--warmup", "1",
+                        "--reference-budget", "1"], cwd=ROOT, env=env, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [json.loads(l) for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1, r.stdout
+    assert lines[0]["impl"] == "reference" and lines[0]["n_gpus"] == 2

@@ -66,7 +66,7 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     from paper_2308_05007_gb300.rwmi import RwmiError, bin_walkers_noalloc
 
     pos = torch.zeros((4, 4), dtype=torch.float32, device="cuda")
-    counts = torch.zeros(8, dtype=torch.int32, device="cuda")
+    counts = torch.zeros(128 ** 3, dtype=torch.int32, device="cuda")   # a valid buffer: the library refuses
     with pytest.raises(RwmiError, match="1048576"):
         bin_walkers_noalloc((128, 128, 128), 0, pos, counts)   # 2^21 cells > 2^20
 
