@@ -454,46 +454,64 @@ def measure_precision_case(a):
 
 
 def measure_batched(a):
-    """64 independent periodic domains (edges U{48..160}, 4-32 particles of 2-10 centres,
-    1e5-2e6 walkers, tau U[0.6, 1], D U[0.001, 0.02]) advanced together. Each context's LBM
-    block size is picked by rwmi_autotune; then one rwmi_batch graph launch per 16-step chunk
-    advances all of them ("batched"), against the same contexts each driven by its own
-    rwmi_step call on its own stream ("separate"). Whole-job MLUPS by host wall clock around
-    the launches and a final synchronisation."""
+    """Independent periodic domains advanced together, two mixes: the batched workload (64
+    domains, edges U{48..160}, 4-32 particles of 2-10 centres, 1e5-2e6 walkers, tau U[0.6, 1],
+    D U[0.001, 0.02]) and 256 small domains (edges U{16..48}, 1-4 particles of 2-4 centres,
+    2e3-4e4 walkers), where launch gaps dominate. Each mix three ways: "fused" (one launch per
+    phase for all domains, tiles picked by rwmi_batch_autotune), "branches" (one graph of
+    per-domain branches per chunk) and "separate" (each domain's own rwmi_step on its own
+    stream, LBM block size from rwmi_autotune). Whole-job MLUPS by host wall clock around the
+    launches and a final synchronisation, after a warm-up that captures every graph."""
     from paper_2308_05007_gb300 import inputs as I
-    from paper_2308_05007_gb300.rwmi import Batch, Simulation
-    ws = I.batched(n_domains=a.batch_domains, seed=3)
-    sims = [Simulation.from_workload(w) for w in ws]
-    blocks = [s.autotune() for s in sims]
-    cells = sum(w.n_cells for w in ws)
-    walkers = sum(w.n_walkers for w in ws)
-    n = max(16, a.batch_steps // 16 * 16)
-    out = {"domains": len(ws), "cells": cells, "walkers": walkers, "steps": n,
-           "lbm_block_histogram": {str(b): blocks.count(b) for b in sorted(set(blocks))}}
-    with Batch(sims) as b:
-        b.step(32)
-        b.sync()
-        t0 = time.perf_counter()
-        b.step(n)
-        assert b.sync() >= 0
-        dt = time.perf_counter() - t0
-    out["batched"] = {"mlups": cells * n / dt / 1e6, "walker_steps_per_s": walkers * n / dt,
-                      "ms_per_step": dt / n * 1e3}
-    for s in sims:
-        s.step(16)
-    for s in sims:
-        s.sync()
-    t0 = time.perf_counter()
-    for c in range(0, n, 16):
+    from paper_2308_05007_gb300.rwmi import BATCH_BRANCHES, BATCH_FUSED, Batch, Simulation
+    mixes = {
+        "domains_64": dict(n_domains=a.batch_domains, seed=3),
+        "small_256": dict(n_domains=256, seed=7, edge=(16, 48), particles=(1, 4), centers=(2, 4),
+                          walkers=(2000, 40000)),
+    }
+    out = {}
+    for label, kw in mixes.items():
+        ws = I.batched(**kw)
+        sims = [Simulation.from_workload(w) for w in ws]
+        blocks = [s.autotune() for s in sims]
+        cells = sum(w.n_cells for w in ws)
+        walkers = sum(w.n_walkers for w in ws)
+        n = max(16, a.batch_steps // 16 * 16)
+        res = {"domains": len(ws), "cells": cells, "walkers": walkers, "steps": n,
+               "edges": [min(w.dims[0] for w in ws), max(w.dims[0] for w in ws)],
+               "lbm_block_histogram": {str(b): blocks.count(b) for b in sorted(set(blocks))}}
+
+        def rate(dt):
+            return {"mlups": cells * n / dt / 1e6, "walker_steps_per_s": walkers * n / dt, "ms_per_step": dt / n * 1e3}
+
+        for mode in ("fused", "branches"):
+            with Batch(sims, mode=BATCH_FUSED if mode == "fused" else BATCH_BRANCHES) as b:
+                if mode == "fused":
+                    res["fused_tiles"] = b.autotune(16)
+                b.step(32)
+                b.sync()
+                l0 = b.launch_count
+                t0 = time.perf_counter()
+                b.step(n)
+                assert b.sync() >= 0
+                dt = time.perf_counter() - t0
+                res[mode] = rate(dt)
+                if mode == "fused":
+                    res[mode]["launches_per_step"] = (b.launch_count - l0) / n
         for s in sims:
-            s.step(16)
-    for s in sims:
-        assert s.sync() >= 0
-    dt = time.perf_counter() - t0
-    out["separate"] = {"mlups": cells * n / dt / 1e6, "walker_steps_per_s": walkers * n / dt,
-                       "ms_per_step": dt / n * 1e3}
-    for s in sims:
-        s.close()
+            s.step(32)
+        for s in sims:
+            s.sync()
+        t0 = time.perf_counter()
+        for c in range(0, n, 16):
+            for s in sims:
+                s.step(16)
+        for s in sims:
+            assert s.sync() >= 0
+        res["separate"] = rate(time.perf_counter() - t0)
+        for s in sims:
+            s.close()
+        out[label] = res
     return out
 
 

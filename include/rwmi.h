@@ -326,11 +326,12 @@ RWMI_API rwmi_status rwmi_load(rwmi_ctx* ctx, const char* path);
 
 /* ---- Batched contexts ------------------------------------------------------------------
  * Many independent simulations (each its own context: box, particles, walkers, tau, D) advanced
- * together. Each chunk of steps of every context is captured once into one CUDA graph whose
- * branches run concurrently (one per context stream); later chunks replay it, so one graph
- * launch advances all contexts. The step of each context is exactly its rwmi_step (same
- * kernels, same results bit for bit). The paper has no batching; each context follows the same
- * equations as rwmi_step. */
+ * together. Each chunk of steps of every context is captured once into one CUDA graph; later
+ * chunks replay it, so one graph launch advances all contexts. In the fused form (default where
+ * allowed, see rwmi_batch_set_mode) each phase is one launch over all contexts' work; otherwise
+ * the graph holds one concurrent branch per context. Either way the step of each context is its
+ * rwmi_step (same kernel bodies, same results bit for bit). The paper has no batching; each
+ * context follows the same equations as rwmi_step. */
 typedef struct rwmi_batch rwmi_batch;
 
 /* Groups n contexts (not owned: they must outlive the batch). All must share the chunk length
@@ -344,6 +345,48 @@ RWMI_API rwmi_status rwmi_batch_step(rwmi_batch* batch, int32_t n);
 
 /* Waits for the batch and returns the worst rwmi_sync status of its contexts. */
 RWMI_API rwmi_status rwmi_batch_sync(rwmi_batch* batch);
+
+/* Execution form of a batch. RWMI_BATCH_FUSED runs each phase of the step (poses and bricks,
+ * raster, LBM, both walker passes, the counting sort, moments) as ONE launch for all contexts:
+ * every block of the launch is mapped to (context, block of the grid that context's own launch
+ * would have) through a block map built at the first step, so the launch count per step no
+ * longer grows with the number of contexts. It needs partially saturated cells, prescribed particles, and one velocity set,
+ * storage, sort and moment interval for all contexts. Its schedule is rwmi_step's pipelined one
+ * over all contexts at once: the raster of t+1 beside the LBM of t, the walkers of t beside the
+ * fluid of t+1. Per-cell and per-walker results are those of rwmi_step bit for bit; the FP64
+ * mass/momentum sums add binary32 block partials, so another LBM block size (see the tiles)
+ * changes them at rounding level. RWMI_BATCH_BRANCHES captures the per-context steps as
+ * concurrent graph branches (any configuration). RWMI_BATCH_AUTO (the default) is FUSED where
+ * allowed and the contexts average under 2^19 cells (there launch gaps dominate), else
+ * BRANCHES (larger domains pipeline their phases better independently). */
+enum { RWMI_BATCH_AUTO = 0, RWMI_BATCH_BRANCHES = 1, RWMI_BATCH_FUSED = 2 };
+/* RWMI_E_INVALID (no change) when FUSED is asked of contexts it cannot run. */
+RWMI_API rwmi_status rwmi_batch_set_mode(rwmi_batch* batch, int32_t mode);
+
+/* Work split of the fused launches (the "tiles"): threads per LBM block (64, 128, 256; one cell
+ * per thread), 256-walker chunks per walker block (1..64), walkers per block of the particle-
+ * resolution pass (>= 256; at most the single-context grid), bricks per raster block (>= 1).
+ * Defaults {256, 1, 8192, 64}. Setting them drops the captured graphs (re-captured at the next
+ * step). Results do not depend on them. */
+typedef struct {
+  int32_t lbm_block;
+  int32_t walker_chunks_per_block;
+  int32_t resolve_walkers_per_block;
+  int32_t raster_bricks_per_block;
+} rwmi_batch_tiles;
+RWMI_API rwmi_status rwmi_batch_get_tiles(const rwmi_batch* batch, rwmi_batch_tiles* out);
+RWMI_API rwmi_status rwmi_batch_set_tiles(rwmi_batch* batch, const rwmi_batch_tiles* tiles);
+
+/* Autotuner of the fused work split: a coordinate search over the four tile parameters (LBM
+ * block 64/128/256, walker chunks per block 1/2/4/8, resolve walkers per block
+ * 2048/8192/32768, raster bricks per block 16/64/256), each candidate timed over `steps` steps (a
+ * multiple of the chunk) with CUDA events on the batch stream after one untimed chunk; keeps and
+ * returns the fastest. The timed steps are real steps: every context advances by them (about
+ * 13 (steps + chunk) steps in all). RWMI_E_STATE if the batch is not fused. */
+RWMI_API rwmi_status rwmi_batch_autotune(rwmi_batch* batch, int32_t steps, rwmi_batch_tiles* chosen);
+
+/* Kernel launches the batch has issued (captured launches count once per replay). */
+RWMI_API int64_t rwmi_batch_launch_count(const rwmi_batch* batch);
 
 RWMI_API const char* rwmi_batch_last_error(const rwmi_batch* batch);
 RWMI_API void rwmi_batch_destroy(rwmi_batch* batch);

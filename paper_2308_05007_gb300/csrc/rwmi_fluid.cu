@@ -30,12 +30,26 @@ __device__ __forceinline__ double wrap_d(double x, double n, int wall) {
   return wall ? x : __dsub_rn(x, __dmul_rn(n, floor(__ddiv_rn(x, n))));
 }
 
-// One block per particle (block 0 also writes the body force of this time).
-__global__ void pose_bin_kernel(Geom g, ParticleSet ps, BrickSet bs, const int64_t* __restrict__ d_T,
-                                int t_offset, double F0x, double F0y, double F0z, double fper,
-                                int zero_acc, double* __restrict__ acc) {
-  const int64_t t = *d_T + t_offset;
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+struct PoseArgs {
+  Geom g;
+  ParticleSet ps;
+  BrickSet bs;
+  const int64_t* d_T;
+  int t_offset, zero_acc;
+  double F0x, F0y, F0z, fper;
+  double* acc;
+};
+
+// One block per particle, blk = p of nblk = max(P, 1) blocks (block 0 also writes the body force
+// of this time).
+__device__ void pose_bin_body(const PoseArgs& A, int blk, int nblk) {
+  const Geom g = A.g;
+  const ParticleSet ps = A.ps;
+  const BrickSet bs = A.bs;
+  const double F0x = A.F0x, F0y = A.F0y, F0z = A.F0z, fper = A.fper;
+  double* __restrict__ acc = A.acc;
+  const int64_t t = *A.d_T + A.t_offset;
+  if (blk == 0 && threadIdx.x == 0) {
     const double s = fper > 0.0 ? sin(2.0 * 3.141592653589793 * (double)t / fper) : 1.0;
     bs.sp->Fd[0] = F0x * s;
     bs.sp->Fd[1] = F0y * s;
@@ -44,11 +58,11 @@ __global__ void pose_bin_kernel(Geom g, ParticleSet ps, BrickSet bs, const int64
     bs.sp->F[1] = (float)(F0y * s);
     bs.sp->F[2] = (float)(F0z * s);
   }
-  if (zero_acc) {   // force/torque [6P] + striped mass/momentum [4 RED_SLOTS] accumulators of this time
-    for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < 6 * ps.P + 4 * RED_SLOTS; m += gridDim.x * blockDim.x)
+  if (A.zero_acc) {   // force/torque [6P] + striped mass/momentum [4 RED_SLOTS] accumulators of this time
+    for (int m = blk * blockDim.x + threadIdx.x; m < 6 * ps.P + 4 * RED_SLOTS; m += nblk * blockDim.x)
       acc[m] = 0.0;
   }
-  const int p = blockIdx.x;
+  const int p = blk;
   if (p >= ps.P) return;
   __shared__ double sR[9], so[3];
   const ParticleDesc d = ps.desc[p];
@@ -199,24 +213,61 @@ __global__ void pose_bin_kernel(Geom g, ParticleSet ps, BrickSet bs, const int64
   }
 }
 
+__global__ void pose_bin_kernel(const PoseArgs a) { pose_bin_body(a, blockIdx.x, gridDim.x); }
+__global__ void pose_bin_batched(const PoseArgs* __restrict__ args, const BlockMap* __restrict__ map) {
+  const BlockMap m = map[blockIdx.x];
+  pose_bin_body(args[m.domain], m.block, m.blocks);
+}
+
 // Zeroes n words. A kernel rather than cudaMemsetAsync: inside the captured step a memset node
 // stalled the concurrent branches of the pipelined schedule (measured: 0.14 ms per step).
-__global__ void clear_u32_kernel(uint32_t* p, uint32_t n) {
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = 0u;
+struct ClearArgs {
+  uint32_t* p;
+  uint32_t n;
+};
+__device__ __forceinline__ void clear_body(const ClearArgs& a, int blk, int nblk) {
+  for (uint32_t i = blk * blockDim.x + threadIdx.x; i < a.n; i += nblk * blockDim.x) a.p[i] = 0u;
+}
+__global__ void clear_u32_kernel(const ClearArgs a) { clear_body(a, blockIdx.x, gridDim.x); }
+__global__ void clear_batched(const ClearArgs* __restrict__ args, const BlockMap* __restrict__ map) {
+  const BlockMap m = map[blockIdx.x];
+  clear_body(args[m.domain], m.block, m.blocks);
+}
+int clear_grid(uint32_t n) {
+  const uint32_t blocks = (n + 255) / 256;
+  return (int)(blocks > 152 * 8 ? 152 * 8 : blocks);
 }
 void launch_clear_u32(uint32_t* p, uint32_t n, cudaStream_t st) {
   if (n == 0) return;
-  uint32_t blocks = (n + 255) / 256;
-  if (blocks > 152 * 8) blocks = 152 * 8;
-  clear_u32_kernel<<<blocks, 256, 0, st>>>(p, n);
+  clear_u32_kernel<<<clear_grid(n), 256, 0, st>>>(ClearArgs{p, n});
+}
+size_t clear_args_size() { return sizeof(ClearArgs); }
+void clear_args(void* dst, uint32_t* p, uint32_t n) { *static_cast<ClearArgs*>(dst) = ClearArgs{p, n}; }
+void launch_clear_batched(const void* args, const BlockMap* map, int nblocks, cudaStream_t st) {
+  if (nblocks > 0) clear_batched<<<nblocks, 256, 0, st>>>(static_cast<const ClearArgs*>(args), map);
 }
 
+static PoseArgs make_pose_args(const Geom& g, const ParticleSet& ps, BrickSet bs, const int64_t* d_T,
+                               int t_offset, const double F0[3], double force_period, int zero_forces,
+                               double* acc) {
+  PoseArgs a;
+  a.g = g; a.ps = ps; a.bs = bs; a.d_T = d_T; a.t_offset = t_offset; a.zero_acc = zero_forces;
+  a.F0x = F0[0]; a.F0y = F0[1]; a.F0z = F0[2]; a.fper = force_period; a.acc = acc;
+  return a;
+}
 void launch_pose_bin(const Geom& g, const ParticleSet& ps, BrickSet bs, const int64_t* d_T,
                      int t_offset, const double F0[3], double force_period, int zero_forces,
                      double* acc, cudaStream_t st) {
   const int blocks = ps.P > 0 ? ps.P : 1;
-  pose_bin_kernel<<<blocks, 256, 0, st>>>(g, ps, bs, d_T, t_offset, F0[0], F0[1], F0[2],
-                                          force_period, zero_forces, acc);
+  pose_bin_kernel<<<blocks, 256, 0, st>>>(make_pose_args(g, ps, bs, d_T, t_offset, F0, force_period, zero_forces, acc));
+}
+size_t pose_args_size() { return sizeof(PoseArgs); }
+void pose_args(void* dst, const Geom& g, const ParticleSet& ps, BrickSet bs, const int64_t* d_T, int t_offset,
+               const double F0[3], double force_period, int zero_forces, double* acc) {
+  *static_cast<PoseArgs*>(dst) = make_pose_args(g, ps, bs, d_T, t_offset, F0, force_period, zero_forces, acc);
+}
+void launch_pose_batched(const void* args, const BlockMap* map, int nblocks, cudaStream_t st) {
+  if (nblocks > 0) pose_bin_batched<<<nblocks, 256, 0, st>>>(static_cast<const PoseArgs*>(args), map);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -366,9 +417,20 @@ struct RasterWarp {
 //     the candidate with most sub-samples, lowest index on ties.
 // All decisions use bounds with a 1e-3 margin and, within 4e-5 of f = 1, the exact binary32
 // sequence shared with the CPU oracle, so counts and owners equal the oracle's bit for bit.
-__global__ void __launch_bounds__(256, 4) raster_kernel(Geom g, ParticleSet ps, BrickSet bs,
-                                                        uint16_t* __restrict__ solid,
-                                                        unsigned long long* __restrict__ status) {
+struct RasterArgs {
+  Geom g;
+  ParticleSet ps;
+  BrickSet bs;
+  uint16_t* solid;
+  unsigned long long* status;
+};
+
+__device__ __forceinline__ void raster_body(const RasterArgs& A) {
+  const Geom g = A.g;
+  const ParticleSet ps = A.ps;
+  const BrickSet bs = A.bs;
+  uint16_t* __restrict__ solid = A.solid;
+  unsigned long long* __restrict__ status = A.status;
   __shared__ RasterWarp s_rw[RW_WARPS];
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -565,13 +627,28 @@ __global__ void __launch_bounds__(256, 4) raster_kernel(Geom g, ParticleSet ps, 
   if (lane == 0 && queued) atomicAdd(&status[ST_RASTER_QUEUED], queued);
 }
 
+__global__ void __launch_bounds__(256, 4) raster_kernel(const RasterArgs a) { raster_body(a); }
+__global__ void __launch_bounds__(256, 4) raster_batched(const RasterArgs* __restrict__ args,
+                                                         const BlockMap* __restrict__ map) {
+  raster_body(args[map[blockIdx.x].domain]);   // warps take the domain's bricks from its counter
+}
+
+// two blocks per SM: the raster runs beside the LBM, which takes the rest of each SM (four
+// blocks per SM held every register file and left the LBM to start only as they finished;
+// one block per SM made the raster itself the longer branch)
+int raster_grid(int nsm) { return nsm * 2; }
 void launch_raster(const Geom& g, const ParticleSet& ps, BrickSet bs, uint16_t* solid,
                    unsigned long long* status, int nsm, cudaStream_t st) {
   if (ps.P == 0) return;
-  // two blocks per SM: the raster runs beside the LBM, which takes the rest of each SM (four
-  // blocks per SM held every register file and left the LBM to start only as they finished;
-  // one block per SM made the raster itself the longer branch)
-  raster_kernel<<<nsm * 2, RW_WARPS * 32, 0, st>>>(g, ps, bs, solid, status);
+  raster_kernel<<<raster_grid(nsm), RW_WARPS * 32, 0, st>>>(RasterArgs{g, ps, bs, solid, status});
+}
+size_t raster_args_size() { return sizeof(RasterArgs); }
+void raster_args(void* dst, const Geom& g, const ParticleSet& ps, BrickSet bs, uint16_t* solid,
+                 unsigned long long* status) {
+  *static_cast<RasterArgs*>(dst) = RasterArgs{g, ps, bs, solid, status};
+}
+void launch_raster_batched(const void* args, const BlockMap* map, int nblocks, cudaStream_t st) {
+  if (nblocks > 0) raster_batched<<<nblocks, RW_WARPS * 32, 0, st>>>(static_cast<const RasterArgs*>(args), map);
 }
 
 // ------------------------------------------------------------------------------------------

@@ -348,4 +348,63 @@ size_t scan_block_sums_size(uint32_t n);
 const char* noalloc_last_error();
 void lattice_table(int q, int32_t* e, double* w);
 
+// ------------------------------------------------------------------------------------------
+// Batched launches: one launch runs a phase's kernel body for many contexts ("domains").
+// Every block works for one domain: map[blockIdx.x] names the domain, the block's index among
+// that domain's blocks and their number, so the body sees the grid a launch for that domain
+// alone would have. args holds one argument record per domain (the *_args functions below write
+// one with the same parameters as the matching launch_* function; *_args_size gives its
+// bytes). The single-context launch_* functions run the same bodies.
+// ------------------------------------------------------------------------------------------
+struct BlockMap {
+  int32_t domain, block, blocks, pad;
+};
+size_t clear_args_size();
+void clear_args(void* dst, uint32_t* p, uint32_t n);
+void launch_clear_batched(const void* args, const BlockMap* map, int nblocks, cudaStream_t st);
+size_t pose_args_size();
+void pose_args(void* dst, const Geom& g, const ParticleSet& ps, BrickSet bs, const int64_t* d_T, int t_offset,
+               const double F0[3], double force_period, int zero_forces, double* acc);
+void launch_pose_batched(const void* args, const BlockMap* map, int nblocks, cudaStream_t st);
+size_t raster_args_size();
+void raster_args(void* dst, const Geom& g, const ParticleSet& ps, BrickSet bs, uint16_t* solid,
+                 unsigned long long* status);
+void launch_raster_batched(const void* args, const BlockMap* map, int nblocks, cudaStream_t st);
+// LBM update (mode 0) or reduce-only pass (mode 1) of the partially saturated cells
+size_t lbm_args_size(int q, int storage);
+void lbm_args(void* dst, int q, int storage, const Geom& g, const void* fin, void* fout, float* u,
+              const uint16_t* solid, BrickSet bs, double tau, double rho0, double* red, double* forces);
+void launch_lbm_batched(int q, int storage, bool walls, int mode, const void* args, const BlockMap* map,
+                        int nblocks, int block, cudaStream_t st);
+size_t walker_args_size();
+void walker_args(void* dst, const Geom& g, const ParticleSet& ps, BrickSet bs1, float4* pos, int64_t n,
+                 const float* u, const int64_t* d_T, int toff, int toff_parity, float D, uint32_t k0,
+                 uint32_t k1, unsigned long long* status, float4* list, unsigned int* list_n);
+void launch_walker_batched(const void* args, const BlockMap* map, int nblocks, cudaStream_t st);
+void launch_resolve_batched(const void* args, const BlockMap* map, int nblocks, cudaStream_t st);
+size_t hist_args_size();
+void hist_args(void* dst, const Geom& g, const float4* pos, int64_t n, uint32_t* counts, uint32_t* rank);
+void launch_hist_batched(const void* args, const BlockMap* map, int nblocks, cudaStream_t st);
+size_t scan_args_size();
+void scan_args(void* dst, const uint32_t* counts, uint32_t* offsets, uint32_t* block_sums, uint32_t n);
+uint32_t scan_tiles(uint32_t n);   // blocks of the reduce and down-sweep passes
+void launch_scan_batched(int pass, const void* args, const BlockMap* map, int nblocks, cudaStream_t st);
+size_t scatter_args_size();
+void scatter_args(void* dst, const Geom& g, const float4* pos, const float4* x0, int64_t n,
+                  const uint32_t* offsets, const uint32_t* rank, float4* pos_out, float4* x0_out);
+void launch_scatter_batched(const void* args, const BlockMap* map, int nblocks, cudaStream_t st);
+size_t moments_args_size();
+void moments_args(void* dst, const float4* pos, const float4* x0, int64_t n, double* acc, double* base,
+                  int interval, int rows, const int64_t* d_T, int toff);
+void launch_moments_batched(bool finalize, const void* args, const BlockMap* map, int nblocks, cudaStream_t st);
+size_t advance_args_size();
+void advance_args(void* dst, int64_t* d_T, int64_t k);
+void launch_advance_batched(const void* args, const BlockMap* map, int nblocks, cudaStream_t st);
+// grids a single-context launch of these phases uses (the batched launch gives each domain the same)
+int walker_grid(int64_t n, int nsm);
+int resolve_grid(int nsm);
+int raster_grid(int nsm);
+int clear_grid(uint32_t n);
+int moments_grid(int64_t n);
+
 }  // namespace rwmi

@@ -51,8 +51,7 @@ __device__ __forceinline__ float ibb_link_q(const float4* __restrict__ cw, int c
 // reducing and non-reducing steps agree bit for bit. MODE 2: update and reduction in one pass,
 // for free-DEM runs, which read the forces on every step (so every step runs this one mode).
 template <int Q, int STORE, bool WALLS, int MODE, bool IBB>
-__global__ void __launch_bounds__(256, sizeof(typename Store<STORE>::R) == 8 ? 2 : IBB ? 4 : (Q == 19 ? 5 : 6))
-lbm_kernel(Geom g, Planes<Q, typename Store<STORE>::T> pl,
+__device__ __forceinline__ void lbm_body(Geom g, Planes<Q, typename Store<STORE>::T> pl,
                                                   float4* __restrict__ u4,
                                                   const uint16_t* __restrict__ solid,
                                                   const uint32_t* __restrict__ bword,
@@ -69,7 +68,7 @@ lbm_kernel(Geom g, Planes<Q, typename Store<STORE>::T> pl,
                                                   const ParticleDesc* __restrict__ desc,
                                                   const float4* __restrict__ cworld,
                                                   const int32_t* __restrict__ ib_base,
-                                                  const float* __restrict__ ib_q, int ib_cap) {
+                                                  const float* __restrict__ ib_q, int ib_cap, int blk) {
   using L = Lat<Q>;
   using S = Store<STORE>;
   using R = typename S::R;   // arithmetic type: binary32, or binary64 for the binary64 storage
@@ -77,7 +76,7 @@ lbm_kernel(Geom g, Planes<Q, typename Store<STORE>::T> pl,
   // tau, omega = 1/tau, guo0 = 1 - 1/(2 tau) and rho0 arrive in R (formed and converted on the
   // host: per-thread divisions and binary64 -> binary32 conversions cost issue slots, and the
   // conversions occupy GB300's narrow FP64 pipe)
-  const uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t idx = blk * blockDim.x + threadIdx.x;
   const bool valid = idx < g.ncell;
   const int c = (int)(valid ? idx : g.ncell - 1);   // tail lanes recompute the last cell and store
   const int cs = valid ? c : (int)g.ncell_pad - 1;  // into the spare slot no cell owns (no branches)
@@ -413,10 +412,55 @@ lbm_kernel(Geom g, Planes<Q, typename Store<STORE>::T> pl,
     if (threadIdx.x < 4) {   // striped slots keep the FP64 atomics of 65536 blocks uncontended
       R s = R(0.0);
       for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += s_red[w][threadIdx.x];
-      atomicAdd(&red[4 * (blockIdx.x % RED_SLOTS) + threadIdx.x], (double)s);
+      atomicAdd(&red[4 * (blk % RED_SLOTS) + threadIdx.x], (double)s);
     }
   }
 }
+
+// Arguments of one LBM launch (the partially saturated cells; the IBB inputs stay null).
+template <int Q, int STORE> struct LbmArgs {
+  using T = typename Store<STORE>::T;
+  using R = typename Store<STORE>::R;
+  Geom g;
+  Planes<Q, T> pl;
+  float4* u4;
+  const uint16_t* solid;
+  const uint32_t* bword;
+  const PoseF* pose;
+  const PoseD* posed;
+  const StepParams* sp;
+  R tau, omega, guo0, rho0;
+  double* red;
+  double* forces;
+};
+
+#define RWMI_LBM_BOUNDS __launch_bounds__(256, sizeof(typename Store<STORE>::R) == 8 ? 2 : IBB ? 4 : (Q == 19 ? 5 : 6))
+
+template <int Q, int STORE, bool WALLS, int MODE, bool IBB>
+__global__ void RWMI_LBM_BOUNDS
+lbm_kernel(Geom g, Planes<Q, typename Store<STORE>::T> pl, float4* __restrict__ u4, const uint16_t* __restrict__ solid,
+           const uint32_t* __restrict__ bword, const PoseF* __restrict__ pose, const PoseD* __restrict__ posed,
+           const StepParams* __restrict__ sp, typename Store<STORE>::R tau, typename Store<STORE>::R omega,
+           typename Store<STORE>::R guo0, typename Store<STORE>::R rho0, double* __restrict__ red,
+           double* __restrict__ forces, const uint16_t* __restrict__ nodes, const float4* __restrict__ uprev,
+           const ParticleDesc* __restrict__ desc, const float4* __restrict__ cworld,
+           const int32_t* __restrict__ ib_base, const float* __restrict__ ib_q, int ib_cap) {
+  lbm_body<Q, STORE, WALLS, MODE, IBB>(g, pl, u4, solid, bword, pose, posed, sp, tau, omega, guo0, rho0, red, forces,
+                                       nodes, uprev, desc, cworld, ib_base, ib_q, ib_cap, blockIdx.x);
+}
+
+// One launch over the cells of many domains: block -> (domain, block of that domain's grid). Its
+// plane pointers come from memory rather than the constant bank, so it gets more registers.
+template <int Q, int STORE, bool WALLS, int MODE, bool IBB>
+__global__ void __launch_bounds__(256, sizeof(typename Store<STORE>::R) == 8 ? 2 : 4) lbm_batched(const LbmArgs<Q, STORE>* __restrict__ args,
+                                            const BlockMap* __restrict__ map) {
+  const BlockMap m = map[blockIdx.x];
+  const LbmArgs<Q, STORE>& a = args[m.domain];
+  lbm_body<Q, STORE, WALLS, MODE, IBB>(a.g, a.pl, a.u4, a.solid, a.bword, a.pose, a.posed, a.sp, a.tau, a.omega,
+                                       a.guo0, a.rho0, a.red, a.forces, nullptr, nullptr, nullptr, nullptr,
+                                       nullptr, nullptr, 0, m.block);
+}
+#undef RWMI_LBM_BOUNDS
 
 // ---- IBB links (Eq. 25) ahead of the LBM update ------------------------------------------
 // Every fluid node of a flagged brick whose lattice neighbour x - e_i is a solid node owns the
@@ -584,6 +628,74 @@ void launch_lbm(int q, int storage, bool reduce, const Geom& g, const void* fin,
   }
 #undef RWMI_LBM_CASE
 #undef RWMI_LBM_PSM
+}
+
+template <int Q, int STORE>
+static void fill_lbm_args(void* dst, const Geom& g, const void* fin, void* fout, float* u, const uint16_t* solid,
+                          BrickSet bs, double tau, double rho0, double* red, double* forces) {
+  using T = typename Store<STORE>::T;
+  using R = typename Store<STORE>::R;
+  LbmArgs<Q, STORE> a;
+  a.g = g;
+  for (int i = 0; i < Q; ++i) {
+    a.pl.in[i] = (const T*)fin + (size_t)i * g.ncell_pad;
+    a.pl.out[i] = (T*)fout + (size_t)i * g.ncell_pad;
+  }
+  a.u4 = reinterpret_cast<float4*>(u);
+  a.solid = solid; a.bword = bs.bword; a.pose = bs.pose; a.posed = bs.posed; a.sp = bs.sp;
+  a.tau = (R)tau; a.omega = (R)(1.0 / tau); a.guo0 = (R)(1.0 - 0.5 / tau); a.rho0 = (R)rho0;
+  a.red = red; a.forces = forces;
+  *static_cast<LbmArgs<Q, STORE>*>(dst) = a;
+}
+
+#define RWMI_LBM_STORAGES(QQ, M)                                        \
+  (storage == 0 ? M(QQ, 0) : storage == 1 ? M(QQ, 1) : storage == 2 ? M(QQ, 2) : M(QQ, 3))
+size_t lbm_args_size(int q, int storage) {
+#define RWMI_SZ(QQ, SS) sizeof(LbmArgs<QQ, SS>)
+  return q == 15 ? RWMI_LBM_STORAGES(15, RWMI_SZ) : RWMI_LBM_STORAGES(19, RWMI_SZ);
+#undef RWMI_SZ
+}
+#undef RWMI_LBM_STORAGES
+
+void lbm_args(void* dst, int q, int storage, const Geom& g, const void* fin, void* fout, float* u,
+              const uint16_t* solid, BrickSet bs, double tau, double rho0, double* red, double* forces) {
+#define RWMI_FILL(QQ, SS) fill_lbm_args<QQ, SS>(dst, g, fin, fout, u, solid, bs, tau, rho0, red, forces)
+  if (q == 15) {
+    if (storage == 0) RWMI_FILL(15, 0); else if (storage == 1) RWMI_FILL(15, 1);
+    else if (storage == 2) RWMI_FILL(15, 2); else RWMI_FILL(15, 3);
+  } else {
+    if (storage == 0) RWMI_FILL(19, 0); else if (storage == 1) RWMI_FILL(19, 1);
+    else if (storage == 2) RWMI_FILL(19, 2); else RWMI_FILL(19, 3);
+  }
+#undef RWMI_FILL
+}
+
+template <int Q, int STORE>
+static void launch_lbm_batched_q(bool walls, int mode, const void* args, const BlockMap* map, int nblocks, int block,
+                                 cudaStream_t st) {
+  const LbmArgs<Q, STORE>* a = static_cast<const LbmArgs<Q, STORE>*>(args);
+  if (walls) {
+    if (mode == 0) lbm_batched<Q, STORE, true, 0, false><<<nblocks, block, 0, st>>>(a, map);
+    else lbm_batched<Q, STORE, true, 1, false><<<nblocks, block, 0, st>>>(a, map);
+  } else {
+    if (mode == 0) lbm_batched<Q, STORE, false, 0, false><<<nblocks, block, 0, st>>>(a, map);
+    else lbm_batched<Q, STORE, false, 1, false><<<nblocks, block, 0, st>>>(a, map);
+  }
+}
+
+void launch_lbm_batched(int q, int storage, bool walls, int mode, const void* args, const BlockMap* map,
+                        int nblocks, int block, cudaStream_t st) {
+  if (nblocks <= 0) return;
+  block = (block == 64 || block == 128) ? block : 256;
+#define RWMI_LB(QQ, SS) launch_lbm_batched_q<QQ, SS>(walls, mode, args, map, nblocks, block, st)
+  if (q == 15) {
+    if (storage == 0) RWMI_LB(15, 0); else if (storage == 1) RWMI_LB(15, 1);
+    else if (storage == 2) RWMI_LB(15, 2); else RWMI_LB(15, 3);
+  } else {
+    if (storage == 0) RWMI_LB(19, 0); else if (storage == 1) RWMI_LB(19, 1);
+    else if (storage == 2) RWMI_LB(19, 2); else RWMI_LB(19, 3);
+  }
+#undef RWMI_LB
 }
 
 }  // namespace rwmi

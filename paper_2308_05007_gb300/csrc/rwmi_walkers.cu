@@ -293,23 +293,38 @@ constexpr int WALKER_BLOCKS_PER_SM = 5;
 // walls. A walker whose mini-brick may meet a particle at t+1 (or whose list overflowed, or whose
 // step was unusually long) is appended to a compact list instead of being written back; pass 2
 // resolves those at full SIMT width, so this kernel carries none of the rare-path code.
-__global__ void __launch_bounds__(256, 5) walker_kernel(WalkCtx c, float4* __restrict__ pos, int64_t n,
-                                                        const float* __restrict__ u,
-                                                        const int64_t* __restrict__ d_T, int toff,
-                                                        float amp, uint32_t k0, uint32_t k1,
-                                                        unsigned long long* __restrict__ status,
-                                                        float4* __restrict__ list, unsigned int* list_n,
-                                                        int64_t cap) {
+// The arguments of both walker passes of one step.
+struct WalkerArgs {
+  WalkCtx c;
+  float4* pos;
+  int64_t n;
+  const float* u;
+  const int64_t* d_T;
+  int toff;
+  float amp;
+  uint32_t k0, k1;
+  unsigned long long* status;
+  float4* list;
+  unsigned int* list_n;        // this step's stripe counters
+  unsigned int* list_n_next;   // the next step's (cleared by the resolve pass)
+  int64_t cap;
+};
+
+__device__ __forceinline__ void walker_body(const WalkCtx& c, float4* __restrict__ pos, int64_t n,
+                                            const float* __restrict__ u, const int64_t* __restrict__ d_T,
+                                            int toff, float amp, uint32_t k0, uint32_t k1,
+                                            unsigned long long* __restrict__ status, float4* __restrict__ list,
+                                            unsigned int* list_n, int64_t cap, int blk, int nblk) {
   const int64_t T = *d_T + toff;
   // grid-stride over chunks of 256 walkers (block-uniform), so that a fixed grid leaves room on
   // every SM for the kernels that run beside this one
   // the next chunk's positions are loaded while this chunk's gathers are in flight
   float4 p4_next = make_float4(0.f, 0.f, 0.f, 0.f);
-  if ((int64_t)blockIdx.x * 256 + threadIdx.x < n) p4_next = pos[(int64_t)blockIdx.x * 256 + threadIdx.x];
-  for (int64_t chunk = blockIdx.x; chunk * 256 < n; chunk += gridDim.x) {
+  if ((int64_t)blk * 256 + threadIdx.x < n) p4_next = pos[(int64_t)blk * 256 + threadIdx.x];
+  for (int64_t chunk = blk; chunk * 256 < n; chunk += nblk) {
     const int64_t w = chunk * 256 + threadIdx.x;
     const float4 p4 = p4_next;
-    if (w + (int64_t)gridDim.x * 256 < n) p4_next = pos[w + (int64_t)gridDim.x * 256];
+    if (w + (int64_t)nblk * 256 < n) p4_next = pos[w + (int64_t)nblk * 256];
     bool ev_wall = false, ev_fast = false, ev_nonfinite = false, flagged = false;
     float4 ea = make_float4(0.f, 0.f, 0.f, 0.f), eb = ea;
     if (w < n) {
@@ -399,13 +414,11 @@ __global__ void __launch_bounds__(256, 5) walker_kernel(WalkCtx c, float4* __res
 // Pass 2 (fixed grid, grid-stride over the list stripes taken as one sequence): types II-IV of
 // the flagged walkers, written back to their slots. Block 0 clears the other parity's counters,
 // which the next step's pass 1 appends to.
-__global__ void __launch_bounds__(256, 4) walker_resolve_kernel(WalkCtx c, float4* __restrict__ pos,
-                                                             const float4* __restrict__ list,
-                                                             const unsigned int* list_n,
-                                                             unsigned int* list_n_next, const int64_t* d_T,
-                                                             int toff, float amp, uint32_t k0, uint32_t k1,
-                                                             unsigned long long* __restrict__ status,
-                                                             int64_t cap) {
+__device__ __forceinline__ void resolve_body(const WalkCtx& c, float4* __restrict__ pos,
+                                             const float4* __restrict__ list, const unsigned int* list_n,
+                                             unsigned int* list_n_next, const int64_t* d_T, int toff, float amp,
+                                             uint32_t k0, uint32_t k1, unsigned long long* __restrict__ status,
+                                             int64_t cap, int blk, int nblk) {
   const int64_t T = *d_T + toff;
   // the stripes as one sequence: s_pre[k] = entries in stripes before k (first warp's scan)
   __shared__ unsigned s_pre[WLIST_STRIPES + 1];
@@ -420,7 +433,7 @@ __global__ void __launch_bounds__(256, 4) walker_resolve_kernel(WalkCtx c, float
     }
     s_pre[threadIdx.x + 1] = incl;
     if (threadIdx.x == 0) s_pre[0] = 0u;
-    if (blockIdx.x == 0) {
+    if (blk == 0) {
       if (v) atomicAdd(&status[ST_RESOLVED], (unsigned long long)v);
       list_n_next[threadIdx.x] = 0u;   // the next step's counters (nobody reads them now)
     }
@@ -428,8 +441,8 @@ __global__ void __launch_bounds__(256, 4) walker_resolve_kernel(WalkCtx c, float
   __syncthreads();
   const unsigned total = s_pre[WLIST_STRIPES];
   unsigned ev_all[5] = {0u, 0u, 0u, 0u, 0u};
-  const unsigned stride = gridDim.x * blockDim.x;
-  for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += stride) {
+  const unsigned stride = nblk * blockDim.x;
+  for (unsigned e = blk * blockDim.x + threadIdx.x; e < total; e += stride) {
     int k = 0;
     while (s_pre[k + 1] <= e) ++k;   // stripe of entry e (k < WLIST_STRIPES since e < total)
     const size_t slot = (size_t)k * (size_t)cap + (e - s_pre[k]);
@@ -486,25 +499,89 @@ __global__ void __launch_bounds__(256, 4) walker_resolve_kernel(WalkCtx c, float
   }
 }
 
+__global__ void __launch_bounds__(256, 5) walker_kernel(const WalkerArgs a) {
+  walker_body(a.c, a.pos, a.n, a.u, a.d_T, a.toff, a.amp, a.k0, a.k1, a.status, a.list, a.list_n, a.cap,
+              blockIdx.x, gridDim.x);
+}
+__global__ void __launch_bounds__(256, 5) walker_batched(const WalkerArgs* __restrict__ args,
+                                                         const BlockMap* __restrict__ map) {
+  const BlockMap m = map[blockIdx.x];
+  const WalkerArgs& a = args[m.domain];
+  walker_body(a.c, a.pos, a.n, a.u, a.d_T, a.toff, a.amp, a.k0, a.k1, a.status, a.list, a.list_n, a.cap,
+              m.block, m.blocks);
+}
+__global__ void __launch_bounds__(256, 4) walker_resolve_kernel(const WalkerArgs a) {
+  resolve_body(a.c, a.pos, a.list, a.list_n, a.list_n_next, a.d_T, a.toff, a.amp, a.k0, a.k1, a.status, a.cap,
+               blockIdx.x, gridDim.x);
+}
+__global__ void __launch_bounds__(256, 4) resolve_batched(const WalkerArgs* __restrict__ args,
+                                                          const BlockMap* __restrict__ map) {
+  const BlockMap m = map[blockIdx.x];
+  const WalkerArgs& a = args[m.domain];
+  resolve_body(a.c, a.pos, a.list, a.list_n, a.list_n_next, a.d_T, a.toff, a.amp, a.k0, a.k1, a.status, a.cap,
+               m.block, m.blocks);
+}
+
+static WalkerArgs make_walker_args(const Geom& g, const ParticleSet& ps, BrickSet bs1, float4* pos, int64_t n,
+                                   const float* u, const int64_t* d_T, int toff, int toff_parity, float D,
+                                   uint32_t k0, uint32_t k1, unsigned long long* status, float4* list,
+                                   unsigned int* list_n) {
+  WalkerArgs a;
+  a.c = WalkCtx{g, ps, bs1};
+  a.pos = pos; a.n = n; a.u = u; a.d_T = d_T; a.toff = toff; a.amp = sqrtf(2.0f * D);
+  a.k0 = k0; a.k1 = k1; a.status = status; a.list = list;
+  // counters per time parity: this step appends to list_n[par], the resolve pass clears the other
+  // set for the next step (no memset launch, no completion ticket)
+  a.list_n = list_n + WLIST_STRIPES * (toff_parity & 1);
+  a.list_n_next = list_n + WLIST_STRIPES * ((toff_parity + 1) & 1);
+  a.cap = wlist_stripe_cap(n);
+  return a;
+}
+int walker_grid(int64_t n, int nsm) {
+  const int64_t blocks = (n + 255) / 256;
+  return (int)(blocks < (int64_t)nsm * WALKER_BLOCKS_PER_SM ? blocks : (int64_t)nsm * WALKER_BLOCKS_PER_SM);
+}
+int resolve_grid(int nsm) { return nsm * 8; }
+
 void launch_walkers(const Geom& g, const ParticleSet& ps, BrickSet bs1, float4* pos, int64_t n,
                     const float* u, const int64_t* d_T, int toff, int toff_parity, float D,
                     uint32_t k0, uint32_t k1, unsigned long long* status, float4* list,
                     unsigned int* list_n, int nsm, cudaStream_t st) {
-  WalkCtx c{g, ps, bs1};
-  const int64_t blocks = (n + 255) / 256;
-  const float amp = sqrtf(2.0f * D);
-  const int64_t cap = wlist_stripe_cap(n);
-  // counters per time parity: this step appends to list_n[par], the resolve pass clears the other
-  // set for the next step (no memset launch, no completion ticket)
-  unsigned int* cur = list_n + WLIST_STRIPES * (toff_parity & 1);
-  unsigned int* nxt = list_n + WLIST_STRIPES * ((toff_parity + 1) & 1);
-  const int64_t grid = blocks < (int64_t)nsm * WALKER_BLOCKS_PER_SM ? blocks : (int64_t)nsm * WALKER_BLOCKS_PER_SM;
-  walker_kernel<<<(unsigned)grid, 256, 0, st>>>(c, pos, n, u, d_T, toff, amp, k0, k1, status, list, cur, cap);
-  walker_resolve_kernel<<<nsm * 8, 256, 0, st>>>(c, pos, list, cur, nxt, d_T, toff, amp, k0, k1, status, cap);
+  const WalkerArgs a = make_walker_args(g, ps, bs1, pos, n, u, d_T, toff, toff_parity, D, k0, k1, status, list, list_n);
+  walker_kernel<<<(unsigned)walker_grid(n, nsm), 256, 0, st>>>(a);
+  walker_resolve_kernel<<<resolve_grid(nsm), 256, 0, st>>>(a);
+}
+size_t walker_args_size() { return sizeof(WalkerArgs); }
+void walker_args(void* dst, const Geom& g, const ParticleSet& ps, BrickSet bs1, float4* pos, int64_t n,
+                 const float* u, const int64_t* d_T, int toff, int toff_parity, float D, uint32_t k0,
+                 uint32_t k1, unsigned long long* status, float4* list, unsigned int* list_n) {
+  *static_cast<WalkerArgs*>(dst) =
+      make_walker_args(g, ps, bs1, pos, n, u, d_T, toff, toff_parity, D, k0, k1, status, list, list_n);
+}
+void launch_walker_batched(const void* args, const BlockMap* map, int nblocks, cudaStream_t st) {
+  if (nblocks > 0) walker_batched<<<nblocks, 256, 0, st>>>(static_cast<const WalkerArgs*>(args), map);
+}
+void launch_resolve_batched(const void* args, const BlockMap* map, int nblocks, cudaStream_t st) {
+  if (nblocks > 0) resolve_batched<<<nblocks, 256, 0, st>>>(static_cast<const WalkerArgs*>(args), map);
 }
 
+struct AdvanceArgs {
+  int64_t* d_T;
+  int64_t k;
+};
 __global__ void advance_kernel(int64_t* d_T, int64_t k) { *d_T += k; }
 void launch_advance(int64_t* d_T, int64_t k, cudaStream_t st) { advance_kernel<<<1, 1, 0, st>>>(d_T, k); }
+__global__ void advance_batched(const AdvanceArgs* __restrict__ args, const BlockMap* __restrict__ map) {
+  if (threadIdx.x == 0) {
+    const AdvanceArgs& a = args[map[blockIdx.x].domain];
+    *a.d_T += a.k;
+  }
+}
+size_t advance_args_size() { return sizeof(AdvanceArgs); }
+void advance_args(void* dst, int64_t* d_T, int64_t k) { *static_cast<AdvanceArgs*>(dst) = AdvanceArgs{d_T, k}; }
+void launch_advance_batched(const void* args, const BlockMap* map, int nblocks, cudaStream_t st) {
+  if (nblocks > 0) advance_batched<<<nblocks, 32, 0, st>>>(static_cast<const AdvanceArgs*>(args), map);
+}
 
 // ------------------------------------------------------------------------------------------
 // Seeding: walker w tries Philox counters (w, a, 2, 0); point lo + U (hi - lo) in explicitly
@@ -600,9 +677,16 @@ __device__ __forceinline__ uint32_t walker_cell(const float4& p, const Geom& g) 
   return ((uint32_t)cz * g.n[1] + cy) * g.n[0] + cx;
 }
 
-__global__ void histogram_kernel(Geom g, const float4* __restrict__ pos, int64_t n,
-                                 uint32_t* __restrict__ counts, uint32_t* __restrict__ rank) {
-  const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+struct HistArgs {
+  Geom g;
+  const float4* pos;
+  int64_t n;
+  uint32_t* counts;
+  uint32_t* rank;
+};
+__device__ __forceinline__ void histogram_body(const Geom& g, const float4* __restrict__ pos, int64_t n,
+                                               uint32_t* __restrict__ counts, uint32_t* __restrict__ rank, int blk) {
+  const int64_t w = (int64_t)blk * blockDim.x + threadIdx.x;
   const bool act = w < n;
   const unsigned amask = __ballot_sync(0xffffffffu, act);
   if (!act) return;
@@ -616,10 +700,26 @@ __global__ void histogram_kernel(Geom g, const float4* __restrict__ pos, int64_t
   if (rank) rank[w] = base + __popc(peers & ((1u << lane) - 1u));
 }
 
+__global__ void histogram_kernel(Geom g, const float4* __restrict__ pos, int64_t n,
+                                 uint32_t* __restrict__ counts, uint32_t* __restrict__ rank) {
+  histogram_body(g, pos, n, counts, rank, blockIdx.x);
+}
+__global__ void hist_batched(const HistArgs* __restrict__ args, const BlockMap* __restrict__ map) {
+  const BlockMap m = map[blockIdx.x];
+  const HistArgs& a = args[m.domain];
+  histogram_body(a.g, a.pos, a.n, a.counts, a.rank, m.block);
+}
 void launch_histogram(const Geom& g, const float4* pos, int64_t n, uint32_t* counts,
                       uint32_t* rank, cudaStream_t st) {
   if (n <= 0) return;
   histogram_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g, pos, n, counts, rank);
+}
+size_t hist_args_size() { return sizeof(HistArgs); }
+void hist_args(void* dst, const Geom& g, const float4* pos, int64_t n, uint32_t* counts, uint32_t* rank) {
+  *static_cast<HistArgs*>(dst) = HistArgs{g, pos, n, counts, rank};
+}
+void launch_hist_batched(const void* args, const BlockMap* map, int nblocks, cudaStream_t st) {
+  if (nblocks > 0) hist_batched<<<nblocks, 256, 0, st>>>(static_cast<const HistArgs*>(args), map);
 }
 
 constexpr int SCAN_THREADS = 256, SCAN_ITEMS = 8, SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
@@ -653,17 +753,27 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* t
   return wbase + incl - v;
 }
 
-__global__ void scan_reduce_kernel(const uint32_t* __restrict__ in, uint32_t n, uint32_t* __restrict__ sums) {
-  const uint32_t base = blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
+struct ScanArgs {
+  const uint32_t* in;
+  uint32_t n, nb;
+  uint32_t* sums;
+  uint32_t* out;
+};
+__device__ __forceinline__ void scan_reduce_body(const uint32_t* __restrict__ in, uint32_t n,
+                                                 uint32_t* __restrict__ sums, int blk) {
+  const uint32_t base = blk * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
   uint32_t s = 0;
 #pragma unroll
   for (int k = 0; k < SCAN_ITEMS; ++k) s += base + k < n ? in[base + k] : 0u;
   uint32_t total;
   block_exclusive_scan(s, &total);
-  if (threadIdx.x == 0) sums[blockIdx.x] = total;
+  if (threadIdx.x == 0) sums[blk] = total;
+}
+__global__ void scan_reduce_kernel(const uint32_t* __restrict__ in, uint32_t n, uint32_t* __restrict__ sums) {
+  scan_reduce_body(in, n, sums, blockIdx.x);
 }
 
-__global__ void scan_top_kernel(uint32_t* sums, uint32_t nb) {
+__device__ __forceinline__ void scan_top_body(uint32_t* sums, uint32_t nb) {
   uint32_t carry = 0;
   for (uint32_t base = 0; base < nb; base += SCAN_THREADS) {
     const uint32_t i = base + threadIdx.x;
@@ -674,19 +784,42 @@ __global__ void scan_top_kernel(uint32_t* sums, uint32_t nb) {
     carry += total;
   }
 }
+__global__ void scan_top_kernel(uint32_t* sums, uint32_t nb) { scan_top_body(sums, nb); }
 
-__global__ void scan_down_kernel(const uint32_t* __restrict__ in, uint32_t n,
-                                 const uint32_t* __restrict__ sums, uint32_t* __restrict__ out) {
-  const uint32_t base = blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
+__device__ __forceinline__ void scan_down_body(const uint32_t* __restrict__ in, uint32_t n,
+                                               const uint32_t* __restrict__ sums, uint32_t* __restrict__ out,
+                                               int blk) {
+  const uint32_t base = blk * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
   uint32_t v[SCAN_ITEMS], s = 0;
 #pragma unroll
   for (int k = 0; k < SCAN_ITEMS; ++k) { v[k] = base + k < n ? in[base + k] : 0u; s += v[k]; }
-  uint32_t run = sums[blockIdx.x] + block_exclusive_scan(s, nullptr);
+  uint32_t run = sums[blk] + block_exclusive_scan(s, nullptr);
 #pragma unroll
   for (int k = 0; k < SCAN_ITEMS; ++k) {
     if (base + k < n) out[base + k] = run;
     run += v[k];
   }
+}
+
+__global__ void scan_down_kernel(const uint32_t* __restrict__ in, uint32_t n,
+                                 const uint32_t* __restrict__ sums, uint32_t* __restrict__ out) {
+  scan_down_body(in, n, sums, out, blockIdx.x);
+}
+// pass 0: tile sums, 1: scan of the tile sums (one block per domain), 2: down-sweep
+__global__ void scan_batched(int pass, const ScanArgs* __restrict__ args, const BlockMap* __restrict__ map) {
+  const BlockMap m = map[blockIdx.x];
+  const ScanArgs& a = args[m.domain];
+  if (pass == 0) scan_reduce_body(a.in, a.n, a.sums, m.block);
+  else if (pass == 1) scan_top_body(a.sums, a.nb);
+  else scan_down_body(a.in, a.n, a.sums, a.out, m.block);
+}
+uint32_t scan_tiles(uint32_t n) { return (n + SCAN_TILE - 1) / SCAN_TILE; }
+size_t scan_args_size() { return sizeof(ScanArgs); }
+void scan_args(void* dst, const uint32_t* counts, uint32_t* offsets, uint32_t* block_sums, uint32_t n) {
+  *static_cast<ScanArgs*>(dst) = ScanArgs{counts, n, scan_tiles(n), block_sums, offsets};
+}
+void launch_scan_batched(int pass, const void* args, const BlockMap* map, int nblocks, cudaStream_t st) {
+  if (nblocks > 0) scan_batched<<<nblocks, SCAN_THREADS, 0, st>>>(pass, static_cast<const ScanArgs*>(args), map);
 }
 
 void launch_scan(const uint32_t* counts, uint32_t* offsets, uint32_t* block_sums, uint32_t n,
@@ -697,16 +830,45 @@ void launch_scan(const uint32_t* counts, uint32_t* offsets, uint32_t* block_sums
   scan_down_kernel<<<nb, SCAN_THREADS, 0, st>>>(counts, n, block_sums, offsets);
 }
 
-__global__ void scatter_kernel(Geom g, const float4* __restrict__ pos, const float4* __restrict__ x0,
-                               int64_t n, const uint32_t* __restrict__ offsets,
-                               const uint32_t* __restrict__ rank, float4* __restrict__ pos_out,
-                               float4* __restrict__ x0_out) {
-  const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+struct ScatterArgs {
+  Geom g;
+  const float4* pos;
+  const float4* x0;
+  int64_t n;
+  const uint32_t* offsets;
+  const uint32_t* rank;
+  float4* pos_out;
+  float4* x0_out;
+};
+__device__ __forceinline__ void scatter_body(const Geom& g, const float4* __restrict__ pos,
+                                             const float4* __restrict__ x0, int64_t n,
+                                             const uint32_t* __restrict__ offsets, const uint32_t* __restrict__ rank,
+                                             float4* __restrict__ pos_out, float4* __restrict__ x0_out, int blk) {
+  const int64_t w = (int64_t)blk * blockDim.x + threadIdx.x;
   if (w >= n) return;
   const float4 p = pos[w];
   const uint32_t dst = offsets[walker_cell(p, g)] + rank[w];
   pos_out[dst] = p;
   x0_out[dst] = x0[w];
+}
+__global__ void scatter_kernel(Geom g, const float4* __restrict__ pos, const float4* __restrict__ x0,
+                               int64_t n, const uint32_t* __restrict__ offsets,
+                               const uint32_t* __restrict__ rank, float4* __restrict__ pos_out,
+                               float4* __restrict__ x0_out) {
+  scatter_body(g, pos, x0, n, offsets, rank, pos_out, x0_out, blockIdx.x);
+}
+__global__ void scatter_batched(const ScatterArgs* __restrict__ args, const BlockMap* __restrict__ map) {
+  const BlockMap m = map[blockIdx.x];
+  const ScatterArgs& a = args[m.domain];
+  scatter_body(a.g, a.pos, a.x0, a.n, a.offsets, a.rank, a.pos_out, a.x0_out, m.block);
+}
+size_t scatter_args_size() { return sizeof(ScatterArgs); }
+void scatter_args(void* dst, const Geom& g, const float4* pos, const float4* x0, int64_t n,
+                  const uint32_t* offsets, const uint32_t* rank, float4* pos_out, float4* x0_out) {
+  *static_cast<ScatterArgs*>(dst) = ScatterArgs{g, pos, x0, n, offsets, rank, pos_out, x0_out};
+}
+void launch_scatter_batched(const void* args, const BlockMap* map, int nblocks, cudaStream_t st) {
+  if (nblocks > 0) scatter_batched<<<nblocks, 256, 0, st>>>(static_cast<const ScatterArgs*>(args), map);
 }
 
 __global__ void scatter_pos_kernel(Geom g, const float4* __restrict__ pos, int64_t n,
@@ -754,12 +916,22 @@ __device__ __forceinline__ void ff_acc(FF& acc, float th, float tl) {
   acc.hi = hi;
 }
 
-__global__ void moments_kernel(const float4* __restrict__ pos, const float4* __restrict__ x0, int64_t n,
-                               double* __restrict__ acc) {
+struct MomentArgs {
+  const float4* pos;
+  const float4* x0;
+  int64_t n;
+  double* acc;
+  double* base;
+  int interval, rows;
+  const int64_t* d_T;
+  int toff;
+};
+__device__ __forceinline__ void moments_body(const float4* __restrict__ pos, const float4* __restrict__ x0,
+                                             int64_t n, double* __restrict__ acc, int blk, int nblk) {
   FF a[12];
 #pragma unroll
   for (int m = 0; m < 12; ++m) a[m] = {0.0f, 0.0f};
-  for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < n; w += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t w = (int64_t)blk * blockDim.x + threadIdx.x; w < n; w += (int64_t)nblk * blockDim.x) {
     const float4 p = pos[w], q = x0[w];
     const float xs[3] = {p.x, p.y, p.z}, x0s[3] = {q.x, q.y, q.z};
 #pragma unroll
@@ -798,12 +970,16 @@ __global__ void moments_kernel(const float4* __restrict__ pos, const float4* __r
     atomicAdd(&acc[threadIdx.x], t);
   }
 }
+__global__ void moments_kernel(const float4* __restrict__ pos, const float4* __restrict__ x0, int64_t n,
+                               double* __restrict__ acc) {
+  moments_body(pos, x0, n, acc, blockIdx.x, gridDim.x);
+}
 
 // Row {t, N, mean d[3], var d[3], mean x[3], var x[3]}; clears acc for the next use. With
 // interval > 0 the row is slot (t / interval - 1) mod rows of the series at base (so a replayed
 // graph writes the row of the step it runs), otherwise base itself.
-__global__ void moments_finalize_kernel(double* acc, int64_t n, double* base, int interval, int rows,
-                                        const int64_t* d_T, int toff) {
+__device__ __forceinline__ void moments_finalize_body(double* acc, int64_t n, double* base, int interval, int rows,
+                                                      const int64_t* d_T, int toff) {
   if (threadIdx.x != 0) return;
   const double N = (double)n;
   const int64_t t = *d_T + toff;
@@ -820,15 +996,34 @@ __global__ void moments_finalize_kernel(double* acc, int64_t n, double* base, in
   }
   for (int m = 0; m < 12; ++m) acc[m] = 0.0;
 }
+__global__ void moments_finalize_kernel(double* acc, int64_t n, double* base, int interval, int rows,
+                                        const int64_t* d_T, int toff) {
+  moments_finalize_body(acc, n, base, interval, rows, d_T, toff);
+}
+__global__ void moments_batched(int finalize, const MomentArgs* __restrict__ args, const BlockMap* __restrict__ map) {
+  const BlockMap m = map[blockIdx.x];
+  const MomentArgs& a = args[m.domain];
+  if (finalize) moments_finalize_body(a.acc, a.n, a.base, a.interval, a.rows, a.d_T, a.toff);
+  else moments_body(a.pos, a.x0, a.n, a.acc, m.block, m.blocks);
+}
 
+int moments_grid(int64_t n) {
+  const int64_t blocks = (n + 255) / 256;
+  return (int)(blocks > 152 * 4 ? 152 * 4 : blocks);
+}
 void launch_moments(const float4* pos, const float4* x0, int64_t n, double* acc, double* base,
                     int interval, int rows, const int64_t* d_T, int toff, cudaStream_t st) {
-  if (n > 0) {
-    int64_t blocks = (n + 255) / 256;
-    if (blocks > 152 * 4) blocks = 152 * 4;
-    moments_kernel<<<(unsigned)blocks, 256, 0, st>>>(pos, x0, n, acc);
-  }
+  if (n > 0) moments_kernel<<<(unsigned)moments_grid(n), 256, 0, st>>>(pos, x0, n, acc);
   moments_finalize_kernel<<<1, 32, 0, st>>>(acc, n, base, interval, rows, d_T, toff);
+}
+size_t moments_args_size() { return sizeof(MomentArgs); }
+void moments_args(void* dst, const float4* pos, const float4* x0, int64_t n, double* acc, double* base,
+                  int interval, int rows, const int64_t* d_T, int toff) {
+  *static_cast<MomentArgs*>(dst) = MomentArgs{pos, x0, n, acc, base, interval, rows, d_T, toff};
+}
+void launch_moments_batched(bool finalize, const void* args, const BlockMap* map, int nblocks, cudaStream_t st) {
+  if (nblocks > 0)
+    moments_batched<<<nblocks, 256, 0, st>>>(finalize ? 1 : 0, static_cast<const MomentArgs*>(args), map);
 }
 
 // ------------------------------------------------------------------------------------------

@@ -30,7 +30,9 @@ EXPORTED = ["rwmi_config_defaults", "rwmi_create", "rwmi_configure", "rwmi_set_s
             "rwmi_launch_count", "rwmi_destroy", "rwmi_batch_create", "rwmi_batch_step", "rwmi_batch_sync",
             "rwmi_batch_last_error", "rwmi_batch_destroy", "rwmi_dem_defaults", "rwmi_set_dem",
             "rwmi_particle_state", "rwmi_set_particle_state", "rwmi_particle_mass",
-            "rwmi_inject_alloc_failure", "rwmi_alloc_count"]
+            "rwmi_inject_alloc_failure", "rwmi_alloc_count", "rwmi_batch_set_mode", "rwmi_batch_get_tiles",
+            "rwmi_batch_set_tiles", "rwmi_batch_autotune", "rwmi_batch_launch_count"]
+BATCH_AUTO, BATCH_BRANCHES, BATCH_FUSED = 0, 1, 2
 
 
 class RwmiError(RuntimeError):
@@ -49,6 +51,15 @@ class Config(C.Structure):
                 ("init_velocity", C.c_double * 3), ("sort_interval", C.c_int32),
                 ("moment_interval", C.c_int32), ("use_graphs", C.c_int32), ("lbm_block", C.c_int32),
                 ("overlap", C.c_int32), ("coupling", C.c_int32)]
+
+
+class BatchTiles(C.Structure):
+    """rwmi_batch_tiles: the work split of a fused batch's launches."""
+    _fields_ = [("lbm_block", C.c_int32), ("walker_chunks_per_block", C.c_int32),
+                ("resolve_walkers_per_block", C.c_int32), ("raster_bricks_per_block", C.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
 
 
 class DemConfig(C.Structure):
@@ -138,11 +149,17 @@ def load(build_if_missing: bool = False):
     L.rwmi_inject_alloc_failure.restype = C.c_int64
     L.rwmi_alloc_count.argtypes = []
     L.rwmi_alloc_count.restype = C.c_int64
+    L.rwmi_batch_set_mode.argtypes = [P, C.c_int32]
+    L.rwmi_batch_get_tiles.argtypes = [P, C.POINTER(BatchTiles)]
+    L.rwmi_batch_set_tiles.argtypes = [P, C.POINTER(BatchTiles)]
+    L.rwmi_batch_autotune.argtypes = [P, C.c_int32, C.POINTER(BatchTiles)]
+    L.rwmi_batch_launch_count.argtypes = [P]
+    L.rwmi_batch_launch_count.restype = C.c_int64
     for name in EXPORTED:
         fn = getattr(L, name)
         if name not in ("rwmi_config_defaults", "rwmi_last_error", "rwmi_launch_count", "rwmi_destroy",
                         "rwmi_batch_last_error", "rwmi_batch_destroy", "rwmi_dem_defaults",
-                        "rwmi_inject_alloc_failure", "rwmi_alloc_count"):
+                        "rwmi_inject_alloc_failure", "rwmi_alloc_count", "rwmi_batch_launch_count"):
             fn.restype = C.c_int
     _lib = L
     return L
@@ -527,10 +544,11 @@ class Simulation:
 
 
 class Batch:
-    """rwmi_batch: many contexts advanced by one CUDA graph launch per chunk (their steps are
-    concurrent branches). Each context must use its own stream for the branches to overlap."""
+    """rwmi_batch: many contexts advanced by one CUDA graph launch per chunk. Fused (the default
+    where allowed: one launch per phase for all contexts) or as concurrent per-context branches
+    (then each context should use its own stream for the branches to overlap)."""
 
-    def __init__(self, sims):
+    def __init__(self, sims, mode=None):
         self._L = load()
         self.sims = list(sims)
         arr = (C.c_void_p * len(self.sims))(*[s._h.value for s in self.sims])
@@ -538,6 +556,35 @@ class Batch:
         st = self._L.rwmi_batch_create(C.byref(self._h), arr, len(self.sims))
         if st != 0:
             raise RwmiError(st, "rwmi_batch_create: contexts must share the chunk length (<= 64)")
+        if mode is not None:
+            self.set_mode(mode)
+
+    def set_mode(self, mode):
+        """BATCH_AUTO, BATCH_BRANCHES or BATCH_FUSED (rwmi_batch_set_mode)."""
+        self._check(self._L.rwmi_batch_set_mode(self._h, int(mode)))
+
+    @property
+    def tiles(self) -> dict:
+        t = BatchTiles()
+        self._check(self._L.rwmi_batch_get_tiles(self._h, C.byref(t)))
+        return t.as_dict()
+
+    def set_tiles(self, **kw):
+        t = BatchTiles()
+        self._check(self._L.rwmi_batch_get_tiles(self._h, C.byref(t)))
+        for k, v in kw.items():
+            setattr(t, k, int(v))
+        self._check(self._L.rwmi_batch_set_tiles(self._h, C.byref(t)))
+
+    def autotune(self, steps=16) -> dict:
+        """rwmi_batch_autotune: picks the fused work split; advances every context."""
+        t = BatchTiles()
+        self._check(self._L.rwmi_batch_autotune(self._h, int(steps), C.byref(t)))
+        return t.as_dict()
+
+    @property
+    def launch_count(self) -> int:
+        return int(self._L.rwmi_batch_launch_count(self._h))
 
     def _check(self, st):
         if st < 0:

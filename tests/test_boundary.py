@@ -104,6 +104,11 @@ def test_null_handles_are_refused(lib_path):
     out = C.c_void_p()
     assert L.rwmi_batch_create(C.byref(out), None, 0) == -1
     assert L.rwmi_batch_step(None, 16) == -1
+    assert L.rwmi_batch_set_mode(None, 0) == -1
+    assert L.rwmi_batch_set_tiles(None, None) == -1
+    assert L.rwmi_batch_get_tiles(None, None) == -1
+    assert L.rwmi_batch_autotune(None, 16, None) == -1
+    assert L.rwmi_batch_launch_count(None) == 0
 
 
 def test_defaults_are_the_documented_ones(lib_path):

@@ -1,9 +1,13 @@
-"""Batched and served forms on the GPU: the same results as contexts stepped alone.
+"""Batched and served forms on the GPU: the same results as contexts stepped alone, and as
+the FP64 oracle.
 
-- rwmi_batch: several ragged domains advanced by one graph launch per chunk give, bit for bit,
-  the populations, velocities, walker positions and counts of the same domains stepped one by
-  one with rwmi_step. FP64 sums (moments, mass) are reductions whose order of atomic adds may
-  differ between runs, so they are compared to 1e-12 relative.
+- rwmi_batch: several ragged domains advanced by one graph launch per chunk -- fused (one launch
+  per phase for all domains) or as per-context branches -- give, bit for bit, the populations,
+  velocities, walker positions and counts of the same domains stepped one by one with
+  rwmi_step, for any work split of the fused launches. FP64 sums (moments, mass) are reductions
+  whose order of atomic adds may differ between runs, so they are compared to 1e-12 relative.
+- A batched domain and a served request against the FP64 oracle, with the single-context
+  trajectory tolerances.
 - Block-size autotuning changes no per-cell result; rwmi_query and rwmi_footprint behave.
 - The request loop: every request's result in a mix of concurrent requests equals its result
   alone.
@@ -47,9 +51,10 @@ def _same(a, b, label, regrouped=False):
     np.testing.assert_allclose(a["mm"], b["mm"], rtol=0, atol=tol, err_msg=label)
 
 
-def test_batch_equals_separate_runs():
+@pytest.mark.parametrize("mode", ["branches", "fused"])
+def test_batch_equals_separate_runs(mode):
     _need_gpu()
-    from paper_2308_05007_gb300.rwmi import Batch, RwmiError, Simulation
+    from paper_2308_05007_gb300.rwmi import BATCH_BRANCHES, BATCH_FUSED, Batch, RwmiError, Simulation
     ws = _small_domains()
     alone = []
     for w in ws:
@@ -58,7 +63,7 @@ def test_batch_equals_separate_runs():
             alone.append(_state(s))
     sims = [Simulation.from_workload(w) for w in ws]
     try:
-        with Batch(sims) as b:
+        with Batch(sims, mode=BATCH_FUSED if mode == "fused" else BATCH_BRANCHES) as b:
             with pytest.raises(RwmiError):
                 b.step(ws[0].sort_interval + 1)         # not a multiple of the chunk
             b.step(ws[0].steps // 2)                    # first chunk: captured
@@ -69,6 +74,93 @@ def test_batch_equals_separate_runs():
             # work on a context's own stream after the batch sees the batch's results
             sims[0].step(2)
             assert sims[0].t == ws[0].steps + 2
+    finally:
+        for s in sims:
+            s.close()
+
+
+def test_fused_work_split_and_autotune_change_no_result():
+    """Other tiles of the fused launches (LBM block, walker chunks per block, resolve and raster
+    split) and the autotuner's choice: the same per-cell and per-walker results as each domain
+    stepped alone (the LBM block size regroups the binary32 partial sums of mass and momentum)."""
+    _need_gpu()
+    from paper_2308_05007_gb300.rwmi import BATCH_FUSED, Batch, Simulation
+    ws = _small_domains(4, seed=8)
+    sims = [Simulation.from_workload(w) for w in ws]
+    try:
+        with Batch(sims, mode=BATCH_FUSED) as b:
+            b.set_tiles(lbm_block=128, walker_chunks_per_block=4, resolve_walkers_per_block=2048,
+                        raster_bricks_per_block=16)
+            b.step(16)
+            b.set_tiles(lbm_block=64, walker_chunks_per_block=2, resolve_walkers_per_block=32768,
+                        raster_bricks_per_block=256)
+            b.step(16)
+            chosen = b.autotune(16)
+            assert chosen["lbm_block"] in (64, 128, 256) and chosen == b.tiles
+            b.step(16)
+            assert b.sync() >= 0
+            assert b.launch_count > 0
+            for w, s in zip(ws, sims):
+                t = s.t
+                assert t % 16 == 0 and t > 48
+                with Simulation.from_workload(w) as a:
+                    a.step(t)
+                    _same(_state(a), _state(s), w.name, regrouped=True)
+    finally:
+        for s in sims:
+            s.close()
+
+
+def test_fused_batch_refuses_contexts_it_cannot_run():
+    """The paper's IBB coupling is not fused: asking for the fused form fails without side
+    effects, and the automatic form falls back to per-context branches."""
+    _need_gpu()
+    from paper_2308_05007_gb300 import inputs as I
+    from paper_2308_05007_gb300.rwmi import BATCH_AUTO, BATCH_FUSED, Batch, RwmiError, Simulation
+    ws = _small_domains(2, seed=9)
+    ws[1] = I.with_(ws[1], coupling=1)
+    sims = [Simulation.from_workload(w) for w in ws]
+    try:
+        with Batch(sims) as b:
+            with pytest.raises(RwmiError, match="fused"):
+                b.set_mode(BATCH_FUSED)
+            b.set_mode(BATCH_AUTO)
+            b.step(16)
+            assert b.sync() >= 0
+    finally:
+        for s in sims:
+            s.close()
+
+
+def _trajectory_against_the_oracle(sim_state, w, label):
+    """The single-context trajectory tolerances (shifted binary32 storage)."""
+    from oracle.oracle import Oracle
+    ora = Oracle.from_workload(w)
+    ora.step(w.steps)
+    u_o = ora.velocity()
+    rel_u = np.linalg.norm(sim_state["u"].astype(np.float64) - u_o) / np.linalg.norm(u_o)
+    assert rel_u <= 1e-5, (label, rel_u)
+    xo, _ = ora.walkers()
+    pos = sim_state["pos"]
+    cells = ora.bin_positions(pos)
+    diff = (cells != ora.bin_positions(xo.astype(np.float32))).sum()
+    assert diff <= max(2, 1e-3 * len(pos)), (label, diff)
+    assert int(sim_state["c"].sum()) == len(pos)
+    return rel_u
+
+
+def test_batched_domain_against_the_oracle():
+    """One domain of a fused batch, after two chunks, against the FP64 oracle."""
+    _need_gpu()
+    from paper_2308_05007_gb300.rwmi import BATCH_FUSED, Batch, Simulation
+    ws = _small_domains(3, seed=10)
+    sims = [Simulation.from_workload(w) for w in ws]
+    try:
+        with Batch(sims, mode=BATCH_FUSED) as b:
+            b.step(ws[0].steps)
+            assert b.sync() >= 0
+        k = int(np.argmin([w.n_cells for w in ws]))
+        print("batched domain vs oracle: rel_u", _trajectory_against_the_oracle(_state(sims[k]), ws[k], ws[k].name))
     finally:
         for s in sims:
             s.close()
@@ -190,3 +282,7 @@ def test_served_results_equal_alone_and_in_the_mix():
         np.testing.assert_allclose(alone["m"], mixed["m"], rtol=1e-12, atol=1e-12 * np.max(np.abs(alone["m"])))
     s = rep.summary()
     assert s["requests"] == len(reqs) and s["p99_latency_s"] >= s["p50_latency_s"] > 0
+    # one served request (the smallest binary32-shifted one) against the FP64 oracle
+    pick = min((r for r in reqs if r.workload.storage == 1), key=lambda r: r.workload.n_cells)
+    rec = next(x for x in rep.records if x.rid == pick.rid)
+    print("served request vs oracle: rel_u", _trajectory_against_the_oracle(rec.result, pick.workload, f"request {pick.rid}"))
