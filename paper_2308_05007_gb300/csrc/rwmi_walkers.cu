@@ -443,8 +443,13 @@ __device__ __forceinline__ void resolve_body(const WalkCtx& c, float4* __restric
   unsigned ev_all[5] = {0u, 0u, 0u, 0u, 0u};
   const unsigned stride = nblk * blockDim.x;
   for (unsigned e = blk * blockDim.x + threadIdx.x; e < total; e += stride) {
+    // stripe of entry e: the last k with s_pre[k] <= e, by bisection over the power-of-two
+    // stripe count (k < WLIST_STRIPES since e < total = s_pre[WLIST_STRIPES])
+    static_assert((WLIST_STRIPES & (WLIST_STRIPES - 1)) == 0, "stripe count must be a power of two");
     int k = 0;
-    while (s_pre[k + 1] <= e) ++k;   // stripe of entry e (k < WLIST_STRIPES since e < total)
+#pragma unroll
+    for (int half = WLIST_STRIPES / 2; half > 0; half >>= 1)
+      if (s_pre[k + half] <= e) k += half;
     const size_t slot = (size_t)k * (size_t)cap + (e - s_pre[k]);
     const float4 a = list[2 * slot], bq = list[2 * slot + 1];
     const float x[3] = {a.x, a.y, a.z}, xf[3] = {bq.x, bq.y, bq.z};
