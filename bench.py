@@ -51,6 +51,8 @@ def parse(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--overlap", type=int, default=2, choices=[0, 1, 2])
+    ap.add_argument("--lbm-staging", type=int, default=0, choices=[0, 1],
+                    help="LBM update with TMA-staged rows (1) or direct loads (0)")
     ap.add_argument("--coupling", type=int, default=0, choices=[0, 1])
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-precision", action="store_true")
@@ -92,6 +94,9 @@ def config_dict(a, w):
         "moment_interval": w.moment_interval,
         "l2": "inputs larger than L2 (populations 2 x %.2f GB), no flush" % (w.n_cells * w.q * STORE_BYTES[w.storage] / 1e9),
         "graphs": "captured runs of up to 64 steps (whole %d-step chunks), replayed" % max(w.sort_interval, w.moment_interval, 2),
+        "lbm_update": ("rows staged in shared memory by TMA tensor copies" if getattr(a, "lbm_staging", 0)
+                       and w.storage in (0, 1, 2) and a.n % (8 if w.storage == 2 else 4) == 0
+                       else "direct coalesced loads"),
         "schedule": {0: "serial", 1: "raster of t+1 on a second stream beside the LBM of t",
                      2: "raster of t+1 beside the LBM of t; walkers of t on a third stream beside "
                         "the fluid of t+1"}[getattr(a, "overlap", 2)],
@@ -323,11 +328,11 @@ def measure_variants(a, stream):
     peak = float(measured_peaks()["hbm_gbs"])
     out = {}
     for q in (15, 19):
-        for storage in (0, 1, 2, 3):
+        for storage, staging in ((0, 0), (1, 0), (2, 0), (3, 0), (0, 1), (1, 1), (2, 1)):
             b = _ap.Namespace(**vars(a))
             b.q, b.storage = q, storage
             w = workload(b)
-            sim = Simulation.from_workload(w, seed_walkers=False)
+            sim = Simulation.from_workload(w, seed_walkers=False, lbm_staging=staging)
             sim.set_stream(stream)
             sim.seed_walkers(w.n_walkers, *w.walker_box)
             sim.step(16)
@@ -337,7 +342,8 @@ def measure_variants(a, stream):
             lbm_ms = ph["lbm"] / 16
             step_ms = sum(ph.values()) / 16
             gbs = lbm_bytes_per_launch(w, w.n_cells, s_bytes) / (lbm_ms / 1e3) / 1e9
-            out[f"D3Q{q}_{STORE_NAMES[storage]}"] = {
+            name = f"D3Q{q}_{STORE_NAMES[storage]}" + ("_tma" if staging else "")
+            out[name] = {
                 "lbm_ms": lbm_ms, "lbm_gbs": gbs, "lbm_hbm_frac": gbs / peak,
                 "step_ms_eager": step_ms, "mlups_eager": w.n_cells / (step_ms / 1e3) / 1e6}
     # the paper's own coupling (IBB + momentum exchange + refilling) instead of partially
@@ -578,7 +584,7 @@ def main():
     w = workload(a)
     s_bytes = STORE_BYTES[w.storage]
     stream = torch.cuda.Stream()
-    sim = Simulation.from_workload(w, seed_walkers=False, overlap=a.overlap)
+    sim = Simulation.from_workload(w, seed_walkers=False, overlap=a.overlap, lbm_staging=a.lbm_staging)
     sim.set_stream(stream)
     sim.seed_walkers(w.n_walkers, *w.walker_box)
     L = 16

@@ -112,6 +112,12 @@ typedef struct {
                                   (Eqs. 23-25), Galilean-invariant momentum exchange for the
                                   force, refilling of uncovered nodes (Eq. 27). IBB requires
                                   storage FP32_SHIFT or FP64_SHIFT (else RWMI_E_INVALID). */
+    int32_t lbm_staging;       /* 1: the LBM update (partially saturated cells, binary32 or
+                                  binary16 storage, nx a multiple of 4 (binary32) or 8 (binary16))
+                                  stages its pulled rows through shared memory with TMA tensor
+                                  copies; 0: direct coalesced loads. Same results bit for bit.
+                                  Default 0 (direct loads measured faster on GB300); ignored where
+                                  not supported. */
 } rwmi_config;
 
 /* Fills *cfg with the defaults listed above. */

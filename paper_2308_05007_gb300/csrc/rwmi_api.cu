@@ -65,6 +65,8 @@ struct rwmi_ctx {
 
   // device state
   void* f[2] = {nullptr, nullptr};
+  CUtensorMap tmap[2];                // TMA maps of f[0], f[1] (TMA-staged LBM update)
+  bool tma_ok = false;                // both encoded for the current q, storage and buffers
   float* u[2] = {nullptr, nullptr};   // (u, rho) per time parity: the LBM of t writes u[t & 1]
   uint16_t* solid[2] = {nullptr, nullptr};   // per time parity: raster of t+1 beside the LBM of t
   uint16_t* node[2] = {nullptr, nullptr};    // IBB node classes per time parity (0 fluid, 1 + particle)
@@ -397,6 +399,13 @@ rwmi_status reset_fluid(rwmi_ctx* c) {
   return RWMI_OK;
 }
 
+// Tensor maps of the population buffers for the TMA-staged update, where it applies.
+void update_tma(rwmi_ctx* c) {
+  c->tma_ok = c->f[0] && c->f[1] && lbm_tma_supported(c->cfg.q, c->cfg.storage, c->g) &&
+              lbm_tma_encode(c->cfg.q, c->cfg.storage, c->g, c->f[0], &c->tmap[0]) &&
+              lbm_tma_encode(c->cfg.q, c->cfg.storage, c->g, c->f[1], &c->tmap[1]);
+}
+
 rwmi_status alloc_fluid(rwmi_ctx* c) {
   for (int k = 0; k < 2; ++k) {
     dfree(c, c->f[k]);
@@ -404,6 +413,7 @@ rwmi_status alloc_fluid(rwmi_ctx* c) {
   }
   const size_t pop = (size_t)c->cfg.q * c->g.ncell_pad * storage_bytes(c->cfg.storage);
   for (int k = 0; k < 2; ++k) CK(dalloc(c, &c->f[k], pop));
+  update_tma(c);
   return RWMI_OK;
 }
 
@@ -515,16 +525,24 @@ void enqueue_step(rwmi_ctx* c, bool reduce) {
       ia.nodes = c->node[tp];
       ia.uprev = reinterpret_cast<const float4*>(c->u[tn]);
       ia.desc = c->desc;
-      launch_ibb_links(c->cfg.q, c->g, brick_set(c, tp), c->node[tp], c->ibl, tp, c->desc, c->status, c->nsm,
-                       c->stream);
+      launch_ibb_links(c->cfg.q, c->cfg.storage, c->g, brick_set(c, tp), c->node[tp], c->ibl, tp, c->desc,
+                       c->f[c->fcur], c->u[tn], c->cfg.rho0, c->status, c->nsm, c->stream);
       c->launches += 2;
       ia.base = c->ibl.base;
+      ia.word = c->ibl.word;
       ia.q = c->ibl.q;
+      ia.g = c->ibl.g;
       ia.cap = c->ibl.cap;
     }
-    launch_lbm(c->cfg.q, c->cfg.storage, reduce, c->g, c->f[c->fcur], c->f[c->fcur ^ 1], c->u[tp], c->solid[tp],
-               brick_set(c, tp), c->tau, c->cfg.rho0, c->acc[tp] + 6 * c->P, c->acc[tp],
-               c->status, c->stream, c->cfg.lbm_block, ibb ? &ia : nullptr, dem);
+    // the partially saturated update through TMA-staged rows where it applies (same results)
+    const bool staged = !ibb && !dem && c->tma_ok && c->cfg.lbm_staging;
+    if (staged)
+      launch_lbm_tma(c->cfg.q, c->cfg.storage, c->tmap[c->fcur], c->g, c->f[c->fcur], c->f[c->fcur ^ 1], c->u[tp],
+                     c->solid[tp], brick_set(c, tp), c->tau, c->cfg.rho0, c->status, c->nsm, c->stream);
+    if (!staged || reduce)
+      launch_lbm(c->cfg.q, c->cfg.storage, reduce, c->g, c->f[c->fcur], c->f[c->fcur ^ 1], c->u[tp], c->solid[tp],
+                 brick_set(c, tp), c->tau, c->cfg.rho0, c->acc[tp] + 6 * c->P, c->acc[tp],
+                 c->status, c->stream, c->cfg.lbm_block, ibb ? &ia : nullptr, dem, !staged);
     c->launches += dem ? 1 : reduce ? 2 : 1;   // fused with DEM; else the reduce-only pass on reduction steps
     phase_end(c, RWMI_PHASE_LBM);
     c->fcur ^= 1;
@@ -644,6 +662,7 @@ RWMI_API void rwmi_config_defaults(rwmi_config* cfg) {
   cfg->use_graphs = 1;
   cfg->lbm_block = 256;
   cfg->overlap = 2;
+  cfg->lbm_staging = 0;
 }
 
 RWMI_API rwmi_status rwmi_create(rwmi_ctx** out, const int32_t dims[3], double tau, double D,
@@ -754,6 +773,7 @@ RWMI_API rwmi_status rwmi_configure(rwmi_ctx* c, const rwmi_config* cfg) try {
       !(cfg->force_period >= 0.0) ||
       !(cfg->lbm_block == 0 || cfg->lbm_block == 64 || cfg->lbm_block == 128 || cfg->lbm_block == 256) ||
       cfg->overlap < 0 || cfg->overlap > 2 || cfg->coupling < 0 || cfg->coupling > 1 ||
+      cfg->lbm_staging < 0 || cfg->lbm_staging > 1 ||
       (cfg->coupling == 1 && cfg->storage != RWMI_STORE_FP32_SHIFT && cfg->storage != RWMI_STORE_FP64_SHIFT))
     return fail(c, RWMI_E_INVALID, "rwmi_configure: bad q, storage, wall_mask, rho0 or interval");
   for (int a = 0; a < 3; ++a)
@@ -774,9 +794,11 @@ RWMI_API rwmi_status rwmi_configure(rwmi_ctx* c, const rwmi_config* cfg) try {
   if (cfg->coupling == 1 && !c->ibl.base) {   // IBB link list: half a link per cell (2^20 at least)
     c->ibl.cap = (int)std::min<int64_t>(std::max<int64_t>(c->ncell / 2, 1 << 20), 0x7fffffff);
     CK(dalloc(c, &c->ibl.base, sizeof(int32_t) * (size_t)c->ncell));
+    CK(dalloc(c, &c->ibl.word, sizeof(uint32_t) * (size_t)c->ncell));
     CK(dalloc(c, &c->ibl.cell, sizeof(uint32_t) * (size_t)c->ibl.cap));
     CK(dalloc(c, &c->ibl.meta, sizeof(uint32_t) * (size_t)c->ibl.cap));
     CK(dalloc(c, &c->ibl.q, sizeof(float) * (size_t)c->ibl.cap));
+    CK(dalloc(c, &c->ibl.g, sizeof(double) * (size_t)c->ibl.cap));
     CK(dalloc(c, &c->ibl.count, sizeof(unsigned int) * 2));
   }
   if (c->ibl.count) CK(cudaMemsetAsync(c->ibl.count, 0, sizeof(unsigned int) * 2, c->stream));
@@ -1162,11 +1184,13 @@ RWMI_API rwmi_status rwmi_autotune(rwmi_ctx* c, int32_t* chosen) try {
     ia.nodes = c->node[tp];
     ia.uprev = reinterpret_cast<const float4*>(c->u[tp ^ 1]);
     ia.desc = c->desc;
-    launch_ibb_links(c->cfg.q, c->g, brick_set(c, tp), c->node[tp], c->ibl, tp, c->desc, c->status, c->nsm,
-                     c->stream);
+    launch_ibb_links(c->cfg.q, c->cfg.storage, c->g, brick_set(c, tp), c->node[tp], c->ibl, tp, c->desc,
+                     c->f[c->fcur], c->u[tp ^ 1], c->cfg.rho0, c->status, c->nsm, c->stream);
     c->launches += 2;
     ia.base = c->ibl.base;
+    ia.word = c->ibl.word;
     ia.q = c->ibl.q;
+    ia.g = c->ibl.g;
     ia.cap = c->ibl.cap;
   }
   for (int k = 0; k < 3; ++k) {
@@ -1243,7 +1267,9 @@ RWMI_API rwmi_status rwmi_sync(rwmi_ctx* c) try {
   unsigned long long st[ST_COUNT];
   CK(copy_now(c, st, c->status, sizeof(st)));
   rwmi_status r = RWMI_OK;
-  if (st[ST_NONFINITE] > c->status_seen[ST_NONFINITE]) r = fail(c, RWMI_E_NONFINITE, "non-finite walker velocity");
+  if (st[ST_TMA_TIMEOUT] > c->status_seen[ST_TMA_TIMEOUT])
+    r = fail(c, RWMI_E_TIMEOUT, "a bounded wait for a TMA copy gave up (the LBM update is incomplete)");
+  else if (st[ST_NONFINITE] > c->status_seen[ST_NONFINITE]) r = fail(c, RWMI_E_NONFINITE, "non-finite walker velocity");
   else if (st[ST_BISECT_FAIL] > c->status_seen[ST_BISECT_FAIL] || st[ST_REFILL_FAIL] > c->status_seen[ST_REFILL_FAIL])
     r = fail(c, RWMI_W_BISECT, "Algorithm 1 or the refill found no surface point for some walker");
   std::memcpy(c->status_seen, st, sizeof(st));
@@ -2123,7 +2149,7 @@ RWMI_API void rwmi_destroy(rwmi_ctx* c) {
   dfree(c, c->series); dfree(c, c->mrow); dfree(c, c->desc); dfree(c, c->cbody); dfree(c, c->rank);
   dfree(c, c->counts); dfree(c, c->offsets); dfree(c, c->bsums); dfree(c, c->scratch); dfree(c, c->wmask[0]); dfree(c, c->wmask[1]);
   dfree(c, c->dem_d); dfree(c, c->dem_b);
-  dfree(c, c->ibl.base); dfree(c, c->ibl.cell); dfree(c, c->ibl.meta); dfree(c, c->ibl.q); dfree(c, c->ibl.count);
+  dfree(c, c->ibl.base); dfree(c, c->ibl.word); dfree(c, c->ibl.cell); dfree(c, c->ibl.meta); dfree(c, c->ibl.q); dfree(c, c->ibl.g); dfree(c, c->ibl.count);
   cudaStreamSynchronize(c->stream);   // the frees have returned the memory when this returns
   for (int k = 0; k < 2 * RWMI_NPHASE; ++k)
     if (c->ev[k]) cudaEventDestroy(c->ev[k]);

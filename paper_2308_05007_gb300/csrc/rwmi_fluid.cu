@@ -751,6 +751,23 @@ void launch_density(int q, int storage, const Geom& g, const void* f, double rho
   RWMI_DISPATCH(q, storage, density_kernel, g, f, rho0, out);
 }
 
+// Is (x, y, z) inside particle [c0, c1) by Eq. 3 in the CPU oracle's binary32 sequence? A fast
+// value (fast reciprocal, contraction allowed; error ~1e-6 relative) decides outside 4e-5 of 1,
+// the exact sequence inside that band, so the answer always equals the exact one.
+__device__ __forceinline__ bool inside_exact(const float4* __restrict__ cw, int c0, int c1, float x, float y,
+                                             float z, const Geom& g) {
+  float f = 0.0f;
+  for (int i = c0; i < c1; ++i) {
+    const float4 c = cw[i];
+    const float dx = min_image_rn(x - c.x, (float)g.n[0], g.wall[0]);
+    const float dy = min_image_rn(y - c.y, (float)g.n[1], g.wall[1]);
+    const float dz = min_image_rn(z - c.z, (float)g.n[2], g.wall[2]);
+    f += __fdividef(c.w, dx * dx + dy * dy + dz * dz);
+  }
+  if (fabsf(f - 1.0f) > 4e-5f) return f >= 1.0f;
+  return metaball_exact(cw, c0, c1, x, y, z, g) >= 1.0f;
+}
+
 // IBB node classes (Section 2.4.3): a cell centre is solid when Eq. 3 of some particle reaches 1
 // there (binary32, the CPU oracle's operation order), owned by the lowest such particle index.
 // Only cells of flagged bricks can be solid. With refill, a node solid in prev and fluid now gets
@@ -773,12 +790,12 @@ __global__ void node_kernel(Geom g, ParticleSet ps, BrickSet bs, const uint16_t*
     const uint32_t nc = w & 0xffffu;
     if (nc > MAXC) {
       for (int p = 0; p < ps.P && node == 0; ++p)
-        if (metaball_exact(bs.cworld, ps.desc[p].c0, ps.desc[p].c1, xs, ys, zs, g) >= 1.0f) node = p + 1;
+        if (inside_exact(bs.cworld, ps.desc[p].c0, ps.desc[p].c1, xs, ys, zs, g)) node = p + 1;
     } else {
       int best = 0x7fffffff;
       for (uint32_t m = 0; m < nc; ++m) {
         const int p = bs.bcand[b * MAXC + m] & 0x7fff;
-        if (p < best && metaball_exact(bs.cworld, ps.desc[p].c0, ps.desc[p].c1, xs, ys, zs, g) >= 1.0f) best = p;
+        if (p < best && inside_exact(bs.cworld, ps.desc[p].c0, ps.desc[p].c1, xs, ys, zs, g)) best = p;
       }
       if (best != 0x7fffffff) node = best + 1;
     }

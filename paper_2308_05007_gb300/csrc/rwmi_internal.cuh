@@ -25,6 +25,7 @@
 
 #include <cstdint>
 #include <cuda_runtime.h>
+#include <cuda.h>   // CUtensorMap (types only; the encoder is fetched through the runtime)
 
 namespace rwmi {
 
@@ -40,7 +41,8 @@ constexpr int RED_SLOTS = 256;      // mass/momentum partial sums are striped ov
 enum StatusSlot {
   ST_TYPE1 = 0, ST_TYPE2, ST_TYPE3, ST_TYPE4,
   ST_BISECT_FAIL, ST_REFILL_FAIL, ST_WALL_FAIL, ST_SEED_FAIL,
-  ST_NONFINITE, ST_BRICK_OVERFLOW, ST_FAST_SPEED, ST_RESOLVED, ST_RASTER_QUEUED, ST_IBB_OVERFLOW, ST_COUNT
+  ST_NONFINITE, ST_BRICK_OVERFLOW, ST_FAST_SPEED, ST_RESOLVED, ST_RASTER_QUEUED, ST_IBB_OVERFLOW,
+  ST_TMA_TIMEOUT, ST_COUNT
 };
 
 struct ParticleDesc {
@@ -239,27 +241,44 @@ struct IbbArgs {
   const float4* uprev = nullptr;
   const ParticleDesc* desc = nullptr;
   const int32_t* base = nullptr;   // per cell: index of its first link in q (ibb links)
+  const uint32_t* word = nullptr;  // per cell of a flagged brick: bit 0 solid node, bit i link i
   const float* q = nullptr;        // q of every link (Eq. 25)
+  const void* g = nullptr;         // G_i of every link (Eqs. 23-25), in the arithmetic type
   int cap = 0;                     // capacity of the link list
 };
-// The IBB link list of a context: per cell the index of its first link, per link the cell, the
-// direction | particle << 8, and q; two append counters (time parities).
+// The IBB link list of a context: per cell the index of its first link and its node word, per
+// link the cell, the direction | particle << 8, q and G_i (binary32 or binary64, 8 bytes
+// reserved); two append counters (time parities).
 struct IbbLinks {
   int32_t* base = nullptr;
+  uint32_t* word = nullptr;
   uint32_t *cell = nullptr, *meta = nullptr;
   float* q = nullptr;
+  void* g = nullptr;
   unsigned int* count = nullptr;
   int cap = 0;
 };
-// Links of time t (node classes nodes, bricks bs) and their q, before the LBM update of t
-void launch_ibb_links(int q, const Geom& g, BrickSet bs, const uint16_t* nodes, const IbbLinks& lk, int par,
-                      const ParticleDesc* desc, unsigned long long* status, int nsm, cudaStream_t st);
+// Links of time t (node classes nodes, bricks bs), their q and G_i from the LBM input
+// populations fin and the previous velocity uprev, before the LBM update of t.
+void launch_ibb_links(int q, int storage, const Geom& g, BrickSet bs, const uint16_t* nodes, const IbbLinks& lk,
+                      int par, const ParticleDesc* desc, const void* fin, const float* uprev, double rho0,
+                      unsigned long long* status, int nsm, cudaStream_t st);
+// TMA-staged form of the update (MODE 0, partially saturated cells; binary32 or binary16
+// storage, nx a multiple of 16 bytes): same results bit for bit as launch_lbm's update. The
+// tensor map of each population buffer is encoded once (lbm_tma_encode); false where the
+// geometry or the driver does not allow it.
+bool lbm_tma_supported(int q, int storage, const Geom& g);
+bool lbm_tma_encode(int q, int storage, const Geom& g, const void* f, CUtensorMap* map);
+size_t lbm_tma_smem(int q, int storage);
+void launch_lbm_tma(int q, int storage, const CUtensorMap& map, const Geom& g, const void* fin, void* fout, float* u,
+                    const uint16_t* solid, BrickSet bs, double tau, double rho0, unsigned long long* status, int nsm,
+                    cudaStream_t st);
 // fused: the update and the reduction in one pass (free-DEM runs, which read the forces every
 // step; binary32-shifted and binary64 storage)
 void launch_lbm(int q, int storage, bool reduce, const Geom& g, const void* fin, void* fout,
                 float* u, const uint16_t* solid, BrickSet bs, double tau, double rho0,
                 double* red, double* forces, unsigned long long* status, cudaStream_t st,
-                int block = 256, const IbbArgs* ibb = nullptr, bool fused = false);
+                int block = 256, const IbbArgs* ibb = nullptr, bool fused = false, bool update = true);
 
 // Free DEM (Section 2.2, Eqs. 4-11) of a context: contact law, state and per-pair memory. Pair
 // slots (i < j) sit at i P + j, wall slots (particle p, face 2 axis + side) at 6 p + face.

@@ -25,7 +25,7 @@ template <int Q, typename T> struct Planes {
 
 // q of Eq. 25: 24 binary32 bisection steps on Eq. 3 of one particle along x_f + s e, s in [0, 1]
 // (the CPU oracle's sequence: midpoint 0.5 (lo + hi), point x_f + mid e), q = the bracket's
-// middle. ibb_q_kernel calls it once per listed link; the LBM kernel calls it only for links
+// middle. ibb_link_kernel calls it once per listed link; the LBM kernel calls it only for links
 // beyond the list's capacity.
 __device__ __forceinline__ float ibb_link_q(const float4* __restrict__ cw, int c0, int c1, float x0, float y0,
                                          float z0, int ex, int ey, int ez, const Geom& g) {
@@ -40,6 +40,196 @@ __device__ __forceinline__ float ibb_link_q(const float4* __restrict__ cw, int c
   return __fmul_rn(0.5f, __fadd_rn(lo, hi));
 }
 
+// Row tiles of the TMA-staged update (lbm_tma_kernel): TMA_BX cells of one x-row per tile. Each
+// direction's source row is copied with a halo of 16 bytes on both sides, so that the copy
+// starts on a 16-byte boundary (x0 - halo) and covers x0 - 1 .. x0 + TMA_BX; rows sit 128-byte
+// aligned in shared memory.
+constexpr int TMA_BX = 128;
+template <int STORE> struct TmaRow {
+  static constexpr int es = (int)sizeof(typename Store<STORE>::T);
+  static constexpr int halo = 16 / es;                                  // elements
+  static constexpr int box = TMA_BX + 2 * halo;                         // elements copied per row
+  static constexpr int bytes = box * es;                                // a multiple of 16
+  static constexpr int pad = ((bytes + 127) / 128) * 128 / es;          // elements between rows
+};
+
+// Flat offset of the pull source x - e_d of cell (x, y, z) for a run-time direction d (periodic
+// wrap); false where x - e_d lies beyond a plane wall.
+template <int Q, bool WALLS>
+__device__ __forceinline__ bool pull_source(const Geom& g, uint32_t x, uint32_t y, uint32_t z, int d, int& off) {
+  using L = Lat<Q>;
+  const int ex = L::e(d, 0), ey = L::e(d, 1), ez = L::e(d, 2);
+  const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+  const int sy = nx, sz = (int)g.nxy;
+  if (WALLS && ((g.wall[0] && ((ex > 0 && x == 0) || (ex < 0 && (int)x == nx - 1))) ||
+                (g.wall[1] && ((ey > 0 && y == 0) || (ey < 0 && (int)y == ny - 1))) ||
+                (g.wall[2] && ((ez > 0 && z == 0) || (ez < 0 && (int)z == nz - 1)))))
+    return false;
+  off = (ex > 0 ? (x == 0 ? nx - 1 : -1) : ex < 0 ? ((int)x == nx - 1 ? -(nx - 1) : 1) : 0) +
+        (ey > 0 ? (y == 0 ? (ny - 1) * sy : -sy) : ey < 0 ? ((int)y == ny - 1 ? -(ny - 1) * sy : sy) : 0) +
+        (ez > 0 ? (z == 0 ? (nz - 1) * sz : -sz) : ez < 0 ? ((int)z == nz - 1 ? -(nz - 1) * sz : sz) : 0);
+  return true;
+}
+
+// One IBB link (Eqs. 23-25): fluid node x_f = cell c at (x, y, z), direction i whose source
+// x_f - e_i is a solid node of particle p, wall distance qf. rho_f and u_f are x_f's own
+// post-collision density and previous velocity. Returns G_i(x_f) = G^eq_ip(rho_f, u_d) +
+// G^neq_ip(x_f) + 6 w rho_f e_i.u_w (the storage shift cancels); Gp = G+_ip(x_f), the wall point
+// xw and its rigid velocity uw are left for the momentum exchange.
+template <int Q, int STORE, bool WALLS>
+__device__ __forceinline__ typename Store<STORE>::R
+ibb_link_value(const Geom& g, const typename Store<STORE>::T* __restrict__ in0, const float4* __restrict__ uprev,
+               const uint16_t* __restrict__ nodes, const PoseF* __restrict__ pose, const PoseD* __restrict__ posed,
+               int c, uint32_t x, uint32_t y, uint32_t z, int i, int p, typename Store<STORE>::R qf,
+               typename Store<STORE>::R rho_f, const typename Store<STORE>::R (&uf)[3],
+               typename Store<STORE>::R& Gp, typename Store<STORE>::R (&xw)[3], typename Store<STORE>::R (&uw)[3]) {
+  using L = Lat<Q>;
+  using S = Store<STORE>;
+  using R = typename S::R;
+  const int ip = L::opp(i);
+  const int ex = L::e(ip, 0), ey = L::e(ip, 1), ez = L::e(ip, 2);   // into the wall
+  xw[0] = (R)x + R(0.5) + qf * (R)ex;
+  xw[1] = (R)y + R(0.5) + qf * (R)ey;
+  xw[2] = (R)z + R(0.5) + qf * (R)ez;
+  rigid_velocity<R>(g, pose, posed, p, xw[0], xw[1], xw[2], uw);
+  R uff[3] = {uf[0], uf[1], uf[2]};
+  int off = 0;
+  if (pull_source<Q, WALLS>(g, x, y, z, ip, off)) {   // x_ff = x_f + e_i, unless solid or beyond a wall
+    const int cf = c + off;
+    if (nodes[cf] == 0) {
+      const float4 v = uprev[cf];
+      uff[0] = (R)v.x; uff[1] = (R)v.y; uff[2] = (R)v.z;
+    }
+  }
+  R ud[3];
+  for (int a = 0; a < 3; ++a) {
+    const R us1 = qf <= R(0.5) ? R(2) * qf * uf[a] + (R(1) - R(2) * qf) * uff[a]
+                               : (R(1) - qf) / qf * uf[a] + (R(2) * qf - R(1)) / qf * uw[a];
+    const R us2 = (R(1) - qf) / (R(1) + qf) * uff[a] + R(2) * qf / (R(1) + qf) * uw[a];
+    ud[a] = us1 / R(3) + R(2) * us2 / R(3);
+  }
+  const R w = L::template wt<R>(ip);
+  const R eud = (R)ex * ud[0] + (R)ey * ud[1] + (R)ez * ud[2];
+  const R euf = (R)ex * uf[0] + (R)ey * uf[1] + (R)ez * uf[2];
+  const R uud = ud[0] * ud[0] + ud[1] * ud[1] + ud[2] * ud[2];
+  const R uuf = uf[0] * uf[0] + uf[1] * uf[1] + uf[2] * uf[2];
+  const R euw = -((R)ex * uw[0] + (R)ey * uw[1] + (R)ez * uw[2]);   // e_i . u_w, e_i = -e_ip
+  Gp = S::ld(in0 + (size_t)ip * g.ncell_pad + c);
+  return Gp + w * rho_f * (R(3) * (eud - euf) + R(4.5) * (eud * eud - euf * euf) - R(1.5) * (uud - uuf)) +
+         R(6) * w * rho_f * euw;
+}
+
+// Momentum exchange of one link on its particle p (Galilean invariant, Section 2.4.3):
+// (e_ip - u_w) G+_ip - (e_i - u_w) G_i, and its torque about p's origin (minimum image).
+template <int Q, int STORE>
+__device__ __forceinline__ void ibb_link_force(const Geom& g, const PoseF* __restrict__ pose,
+                                               const PoseD* __restrict__ posed, int i, int p,
+                                               typename Store<STORE>::R rho0, typename Store<STORE>::R Gp,
+                                               typename Store<STORE>::R G, const typename Store<STORE>::R (&xw)[3],
+                                               const typename Store<STORE>::R (&uw)[3],
+                                               typename Store<STORE>::R (&Fl)[3], typename Store<STORE>::R (&Tl)[3]) {
+  using L = Lat<Q>;
+  using S = Store<STORE>;
+  using R = typename S::R;
+  const int ip = L::opp(i);
+  const R ex = (R)L::e(ip, 0), ey = (R)L::e(ip, 1), ez = (R)L::e(ip, 2);
+  const R w = L::template wt<R>(ip);
+  const R sh = S::shifted ? w * rho0 : R(0);
+  const R gp = Gp + sh, gi = G + sh;
+  Fl[0] = (ex - uw[0]) * gp - (-ex - uw[0]) * gi;
+  Fl[1] = (ey - uw[1]) * gp - (-ey - uw[1]) * gi;
+  Fl[2] = (ez - uw[2]) * gp - (-ez - uw[2]) * gi;
+  R po[3], pv[3], pw[3];
+  load_pose<R>(pose, posed, p, po, pv, pw);
+  R r[3] = {xw[0] - po[0], xw[1] - po[1], xw[2] - po[2]};
+  for (int a = 0; a < 3; ++a)
+    if (!g.wall[a]) {
+      const R na = (R)g.n[a];
+      if (r[a] > R(0.5) * na) r[a] -= na; else if (r[a] < -R(0.5) * na) r[a] += na;
+    }
+  Tl[0] = r[1] * Fl[2] - r[2] * Fl[1];
+  Tl[1] = r[2] * Fl[0] - r[0] * Fl[2];
+  Tl[2] = r[0] * Fl[1] - r[1] * Fl[0];
+}
+
+// Momentum exchange of one cell's links, in direction order (Section 2.4.3): q and G of link k
+// from the list (k < cap) or from the cell's shared rows; per-particle sums in Fib/Tib for the
+// cell's first particle, direct atomics for a second particle at one node (rare).
+template <int Q, int STORE>
+__device__ __forceinline__ void ibb_cell_force(const Geom& g, const typename Store<STORE>::T* __restrict__ in0,
+                                               const PoseF* __restrict__ pose, const PoseD* __restrict__ posed,
+                                               const uint16_t* __restrict__ nodes, int c, uint32_t x, uint32_t y,
+                                               uint32_t z, unsigned lmask, int k0, int cap,
+                                               const float* __restrict__ ib_q,
+                                               const typename Store<STORE>::R* __restrict__ ib_g, const float* qrow,
+                                               const typename Store<STORE>::R* grow, typename Store<STORE>::R rho0,
+                                               double* __restrict__ forces, int& owner,
+                                               typename Store<STORE>::R (&Fib)[3], typename Store<STORE>::R (&Tib)[3]) {
+  using L = Lat<Q>;
+  using S = Store<STORE>;
+  using R = typename S::R;
+  int k = k0;
+  for (unsigned m = lmask; m; m &= m - 1u, ++k) {
+    const int i = __ffs(m) - 1, ip = L::opp(i);
+    int off = 0;
+    pull_source<Q, true>(g, x, y, z, i, off);   // a link's source is never beyond a wall
+    const int p = (int)nodes[c + off] - 1;
+    const R qf = (R)(k < cap ? ib_q[k] : qrow[(i - 1) * 256]);
+    const R G = k < cap ? ib_g[k] : grow[(i - 1) * 256];
+    const int ex = L::e(ip, 0), ey = L::e(ip, 1), ez = L::e(ip, 2);
+    const R xw[3] = {(R)x + R(0.5) + qf * (R)ex, (R)y + R(0.5) + qf * (R)ey, (R)z + R(0.5) + qf * (R)ez};
+    R uw[3];
+    rigid_velocity<R>(g, pose, posed, p, xw[0], xw[1], xw[2], uw);
+    const R Gp = S::ld(in0 + (size_t)ip * g.ncell_pad + c);
+    R Fl[3], Tl[3];
+    ibb_link_force<Q, STORE>(g, pose, posed, i, p, rho0, Gp, G, xw, uw, Fl, Tl);
+    if (owner < 0 || owner == p) {
+      owner = p;
+      for (int a = 0; a < 3; ++a) { Fib[a] += Fl[a]; Tib[a] += Tl[a]; }
+    } else {
+      for (int a = 0; a < 3; ++a) {
+        atomicAdd(&forces[6 * p + a], (double)Fl[a]);
+        atomicAdd(&forces[6 * p + 3 + a], (double)Tl[a]);
+      }
+    }
+  }
+}
+
+// Links of one cell beyond the link list's capacity (never at its usual capacity of half a link
+// per cell): q by the same bisection and G_i into qrow / grow[(i - 1) * 256].
+template <int Q, int STORE, bool WALLS>
+__device__ __forceinline__ void ibb_overflow_links(Geom g, const typename Store<STORE>::T* __restrict__ in0,
+                                                   const float4* __restrict__ uprev,
+                                                   const uint16_t* __restrict__ nodes, const PoseF* __restrict__ pose,
+                                                   const PoseD* __restrict__ posed, const float4* __restrict__ cworld,
+                                                   const ParticleDesc* __restrict__ desc, int c, uint32_t x,
+                                                   uint32_t y, uint32_t z, unsigned lmask, int k0, int cap,
+                                                   typename Store<STORE>::R rho0, float* qrow,
+                                                   typename Store<STORE>::R* grow) {
+  using L = Lat<Q>;
+  using S = Store<STORE>;
+  using R = typename S::R;
+  R sum = R(0);   // rho_f: x_f's own post-collision populations, summed in direction order
+  for (int d = 0; d < Q; ++d) sum += S::ld(in0 + (size_t)d * g.ncell_pad + c);
+  const R rho_f = S::shifted ? rho0 + sum : sum;
+  const float4 u = uprev[c];
+  const R uf[3] = {(R)u.x, (R)u.y, (R)u.z};
+  int k = k0;
+  for (unsigned m = lmask; m; m &= m - 1u, ++k) {
+    if (k < cap) continue;
+    const int i = __ffs(m) - 1, ip = L::opp(i);
+    int off = 0;
+    pull_source<Q, WALLS>(g, x, y, z, i, off);
+    const int p = (int)nodes[c + off] - 1;
+    const float qv = ibb_link_q(cworld, desc[p].c0, desc[p].c1, (float)x + 0.5f, (float)y + 0.5f, (float)z + 0.5f,
+                                L::e(ip, 0), L::e(ip, 1), L::e(ip, 2), g);
+    R Gp, xw[3], uw[3];
+    qrow[(i - 1) * 256] = qv;
+    grow[(i - 1) * 256] = ibb_link_value<Q, STORE, WALLS>(g, in0, uprev, nodes, pose, posed, c, x, y, z, i, p,
+                                                          (R)qv, rho_f, uf, Gp, xw, uw);
+  }
+}
+
 // IBB: the paper's coupling (Section 2.4.3) instead of partially saturated cells. A cell of a
 // flagged brick reads its node class; a solid node holds the equilibrium at its particle's rigid
 // velocity; a fluid node replaces the population pulled from each solid neighbour by Eqs. 23-25
@@ -50,7 +240,7 @@ __device__ __forceinline__ float ibb_link_q(const float4* __restrict__ cw, int c
 // and stores nothing. Stored populations therefore always come from one compiled update, and the
 // reducing and non-reducing steps agree bit for bit. MODE 2: update and reduction in one pass,
 // for free-DEM runs, which read the forces on every step (so every step runs this one mode).
-template <int Q, int STORE, bool WALLS, int MODE, bool IBB>
+template <int Q, int STORE, bool WALLS, int MODE, bool IBB, bool STAGED = false>
 __device__ __forceinline__ void lbm_body(Geom g, Planes<Q, typename Store<STORE>::T> pl,
                                                   float4* __restrict__ u4,
                                                   const uint16_t* __restrict__ solid,
@@ -68,7 +258,12 @@ __device__ __forceinline__ void lbm_body(Geom g, Planes<Q, typename Store<STORE>
                                                   const ParticleDesc* __restrict__ desc,
                                                   const float4* __restrict__ cworld,
                                                   const int32_t* __restrict__ ib_base,
-                                                  const float* __restrict__ ib_q, int ib_cap, int blk) {
+                                                  const uint32_t* __restrict__ ib_word,
+                                                  const float* __restrict__ ib_q,
+                                                  const typename Store<STORE>::R* __restrict__ ib_g, int ib_cap,
+                                                  int blk, const typename Store<STORE>::T* srow = nullptr,
+                                                  uint32_t staged_idx = 0, bool staged_valid = false,
+                                                  int staged_lx = 0) {
   using L = Lat<Q>;
   using S = Store<STORE>;
   using R = typename S::R;   // arithmetic type: binary32, or binary64 for the binary64 storage
@@ -76,9 +271,12 @@ __device__ __forceinline__ void lbm_body(Geom g, Planes<Q, typename Store<STORE>
   // tau, omega = 1/tau, guo0 = 1 - 1/(2 tau) and rho0 arrive in R (formed and converted on the
   // host: per-thread divisions and binary64 -> binary32 conversions cost issue slots, and the
   // conversions occupy GB300's narrow FP64 pipe)
-  const uint32_t idx = blk * blockDim.x + threadIdx.x;
-  const bool valid = idx < g.ncell;
-  const int c = (int)(valid ? idx : g.ncell - 1);   // tail lanes recompute the last cell and store
+  // STAGED (lbm_tma_kernel): the cell and its valid flag come from the row tile, and pulls read
+  // the tile's rows in shared memory (srow: direction i at i * TmaRow<STORE>::pad elements, the
+  // cell's own source at TmaRow<STORE>::halo + staged_lx - e_x)
+  const uint32_t idx = STAGED ? staged_idx : blk * blockDim.x + threadIdx.x;
+  const bool valid = STAGED ? staged_valid : idx < g.ncell;
+  const int c = (int)(valid || STAGED ? idx : g.ncell - 1);   // tail lanes recompute the last cell and store
   const int cs = valid ? c : (int)g.ncell_pad - 1;  // into the spare slot no cell owns (no branches)
   const uint32_t z = fast_div((uint32_t)c, g.mxy, g.sxy);
   const uint32_t rem = (uint32_t)c - z * g.nxy;
@@ -99,9 +297,13 @@ __device__ __forceinline__ void lbm_body(Geom g, Planes<Q, typename Store<STORE>
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       const int ex = L::e(i, 0), ey = L::e(i, 1), ez = L::e(i, 2);
-      const int off = (ex > 0 ? ox_p : ex < 0 ? ox_m : 0) + (ey > 0 ? oy_p : ey < 0 ? oy_m : 0) +
-                      (ez > 0 ? oz_p : ez < 0 ? oz_m : 0);
-      f[i] = S::ld(pl.in[i] + (c + off));
+      if constexpr (STAGED) {
+        f[i] = S::ld(srow + i * TmaRow<STORE>::pad + (TmaRow<STORE>::halo + staged_lx - ex));
+      } else {
+        const int off = (ex > 0 ? ox_p : ex < 0 ? ox_m : 0) + (ey > 0 ? oy_p : ey < 0 ? oy_m : 0) +
+                        (ez > 0 ? oz_p : ez < 0 ? oz_m : 0);
+        f[i] = S::ld(pl.in[i] + (c + off));
+      }
     }
   } else {   // half-way bounce-back where x - e_i lies beyond a wall: f_i(x) = f+_opp(i)(x)
     const bool bx_p = g.wall[0] && x == 0, bx_m = g.wall[0] && (int)x == nx - 1;
@@ -112,116 +314,61 @@ __device__ __forceinline__ void lbm_body(Geom g, Planes<Q, typename Store<STORE>
       const int ex = L::e(i, 0), ey = L::e(i, 1), ez = L::e(i, 2);
       const int off = (ex > 0 ? ox_p : ex < 0 ? ox_m : 0) + (ey > 0 ? oy_p : ey < 0 ? oy_m : 0) +
                       (ez > 0 ? oz_p : ez < 0 ? oz_m : 0);
-      const bool blk = (ex > 0 && bx_p) || (ex < 0 && bx_m) || (ey > 0 && by_p) || (ey < 0 && by_m) ||
-                       (ez > 0 && bz_p) || (ez < 0 && bz_m);
-      f[i] = blk ? S::ld(pl.in[L::opp(i)] + c) : S::ld(pl.in[i] + (c + off));
+      const bool wb = (ex > 0 && bx_p) || (ex < 0 && bx_m) || (ey > 0 && by_p) || (ey < 0 && by_m) ||
+                      (ez > 0 && bz_p) || (ez < 0 && bz_m);
+      if constexpr (STAGED)
+        f[i] = wb ? S::ld(pl.in[L::opp(i)] + c)
+                  : S::ld(srow + i * TmaRow<STORE>::pad + (TmaRow<STORE>::halo + staged_lx - ex));
+      else
+        f[i] = wb ? S::ld(pl.in[L::opp(i)] + c) : S::ld(pl.in[i] + (c + off));
     }
   }
   // ---- the paper's coupling: IBB links of a fluid node next to solid nodes (Eqs. 23-25) ----
   bool solid_self = false;
-  R Fib[3] = {R(0), R(0), R(0)}, Tib[3] = {R(0), R(0), R(0)};
+  R Fib[3] = {R(0), R(0), R(0)}, Tib[3] = {R(0), R(0), R(0)};   // IBB: this cell's link forces
   int ib_owner = -1;
   if constexpr (IBB) {
-    // q of every link (Eq. 25) comes from ibb_q_kernel, which ran before at full occupancy: the
-    // cell's links sit at ib_base[c] in direction order (ibb_links_kernel, same rule as lmask)
-    const bool wx_p = WALLS && g.wall[0] && x == 0, wx_m = WALLS && g.wall[0] && (int)x == nx - 1;
-    const bool wy_p = WALLS && g.wall[1] && y == 0, wy_m = WALLS && g.wall[1] && (int)y == ny - 1;
-    const bool wz_p = WALLS && g.wall[2] && z == 0, wz_m = WALLS && g.wall[2] && (int)z == nz - 1;
-    auto off_of = [&](int i) {
-      const int ex = L::e(i, 0), ey = L::e(i, 1), ez = L::e(i, 2);
-      return (ex > 0 ? ox_p : ex < 0 ? ox_m : 0) + (ey > 0 ? oy_p : ey < 0 ? oy_m : 0) +
-             (ez > 0 ? oz_p : ez < 0 ? oz_m : 0);
-    };
-    auto blocked = [&](int i) {   // x - e_i beyond a plane wall
-      const int ex = L::e(i, 0), ey = L::e(i, 1), ez = L::e(i, 2);
-      return (ex > 0 && wx_p) || (ex < 0 && wx_m) || (ey > 0 && wy_p) || (ey < 0 && wy_m) ||
-             (ez > 0 && wz_p) || (ez < 0 && wz_m);
-    };
-    unsigned lmask = 0u;   // directions i whose source x - e_i is a solid node
+    // ibb_links_kernel, which ran before, left every cell of a flagged brick its node word: bit 0
+    // a solid node, bit i a link (x - e_i a solid node, not beyond a wall). The cell's links sit
+    // at ib_base[c] in direction order, and ibb_link_kernel left G_i of each in ib_g (with the
+    // momentum exchange on the steps that read forces). Cells of other bricks have no solid
+    // neighbour (the IBB brick radius is at least rb + sqrt 3).
+    unsigned lmask = 0u;
     const uint32_t bq = ((z >> 3) * (uint32_t)g.nb[1] + (y >> 3)) * (uint32_t)g.nb[0] + (x >> 3);
-    if (valid && (bword[bq] >> 16)) {   // cells of other bricks have no solid neighbour (radius >= rb + sqrt 3)
-      if (nodes[c] != 0) {
-        solid_self = true;
-      } else {
-#pragma unroll
-        for (int i = 1; i < Q; ++i)
-          if (!blocked(i) && nodes[c + off_of(i)] != 0) lmask |= 1u << i;
-      }
+    if (valid && (bword[bq] >> 16)) {
+      const uint32_t lw = ib_word[c];
+      solid_self = (lw & 1u) != 0u;
+      lmask = lw & ~1u;
     }
+    int k0 = 0;
+    bool over = false;   // links beyond the list's capacity (counted in the status): computed here
     if (lmask) {
-      R rho_f, uf[3];
-      {   // rho_f: x_f's own post-collision populations; u_f: the previous update
-        R sum = R(0);
+      k0 = ib_base[c];
+      over = k0 + __popc(lmask) > ib_cap;
+    }
+    if (__any_sync(0xffffffffu, over)) {   // never at the list's usual capacity
+      __shared__ R s_link[Q - 1][256];
+      __shared__ float s_q[Q - 1][256];
+      if (over)
+        ibb_overflow_links<Q, STORE, WALLS>(g, pl.in[0], uprev, nodes, pose, posed, cworld, desc, c, x, y, z, lmask,
+                                            k0, ib_cap, rho0, &s_q[0][threadIdx.x], &s_link[0][threadIdx.x]);
+      int k = k0;
 #pragma unroll
-        for (int j = 0; j < Q; ++j) sum += S::ld(pl.in[j] + c);
-        rho_f = S::shifted ? rho0 + sum : sum;
-        const float4 v = uprev[c];
-        uf[0] = (R)v.x; uf[1] = (R)v.y; uf[2] = (R)v.z;
-      }
-      int k = ib_base[c];
-#pragma unroll   // f[i] must stay in registers: a run-time index would put f in local memory
-      for (int i = 1; i < Q; ++i) {
-        if (!((lmask >> i) & 1u)) continue;
-        const int ip = L::opp(i), p = (int)nodes[c + off_of(i)] - 1;
-        const int ex = L::e(ip, 0), ey = L::e(ip, 1), ez = L::e(ip, 2);   // into the wall
-        // beyond the list's capacity (counted in the status) the same bisection runs here
-        const R qf = (R)(k < ib_cap ? ib_q[k] : ibb_link_q(cworld, desc[p].c0, desc[p].c1, (float)x + 0.5f,
-                                                         (float)y + 0.5f, (float)z + 0.5f, ex, ey, ez, g));
-        ++k;
-        const R xw[3] = {(R)x + R(0.5) + qf * (R)ex, (R)y + R(0.5) + qf * (R)ey, (R)z + R(0.5) + qf * (R)ez};
-        R uw[3];
-        rigid_velocity<R>(g, pose, posed, p, xw[0], xw[1], xw[2], uw);
-        R uff[3] = {uf[0], uf[1], uf[2]};
-        if (!blocked(ip)) {   // x_ff = x_f + e_i, unless solid or beyond a wall
-          const int cf = c + off_of(ip);
-          if (nodes[cf] == 0) {
-            const float4 v = uprev[cf];
-            uff[0] = (R)v.x; uff[1] = (R)v.y; uff[2] = (R)v.z;
-          }
+      for (int i = 1; i < Q; ++i)
+        if ((lmask >> i) & 1u) {
+          f[i] = k < ib_cap ? ib_g[k] : s_link[i - 1][threadIdx.x];
+          ++k;
         }
-        R ud[3];
-        for (int a = 0; a < 3; ++a) {
-          const R us1 = qf <= R(0.5) ? R(2) * qf * uf[a] + (R(1) - R(2) * qf) * uff[a]
-                                     : (R(1) - qf) / qf * uf[a] + (R(2) * qf - R(1)) / qf * uw[a];
-          const R us2 = (R(1) - qf) / (R(1) + qf) * uff[a] + R(2) * qf / (R(1) + qf) * uw[a];
-          ud[a] = us1 / R(3) + R(2) * us2 / R(3);
-        }
-        const R w = L::template wt<R>(ip);
-        const R eud = (R)ex * ud[0] + (R)ey * ud[1] + (R)ez * ud[2];
-        const R euf = (R)ex * uf[0] + (R)ey * uf[1] + (R)ez * uf[2];
-        const R uud = ud[0] * ud[0] + ud[1] * ud[1] + ud[2] * ud[2];
-        const R uuf = uf[0] * uf[0] + uf[1] * uf[1] + uf[2] * uf[2];
-        const R euw = -((R)ex * uw[0] + (R)ey * uw[1] + (R)ez * uw[2]);   // e_i . u_w, e_i = -e_ip
-        const R Gp = S::ld(pl.in[ip] + c);
-        // G^eq_ip(rho_f, u_d) + G^neq_ip(x_f) + 6 w rho_f e_i.u_w; the storage shift cancels
-        const R G = Gp + w * rho_f * (R(3) * (eud - euf) + R(4.5) * (eud * eud - euf * euf) - R(1.5) * (uud - uuf)) +
-                    R(6) * w * rho_f * euw;
-        f[i] = G;
-        if (REDUCE) {   // (e_ip - u_w) G+_ip - (e_i - u_w) G_i on particle p; torque about its origin
-          const R sh = S::shifted ? w * rho0 : R(0);
-          const R gp = Gp + sh, gi = G + sh;
-          const R Fl[3] = {((R)ex - uw[0]) * gp - (-(R)ex - uw[0]) * gi, ((R)ey - uw[1]) * gp - (-(R)ey - uw[1]) * gi,
-                           ((R)ez - uw[2]) * gp - (-(R)ez - uw[2]) * gi};
-          R po[3], pv[3], pw[3];
-          load_pose<R>(pose, posed, p, po, pv, pw);
-          R r[3] = {xw[0] - po[0], xw[1] - po[1], xw[2] - po[2]};
-          for (int a = 0; a < 3; ++a)
-            if (!g.wall[a]) {
-              const R na = (R)g.n[a];
-              if (r[a] > R(0.5) * na) r[a] -= na; else if (r[a] < -R(0.5) * na) r[a] += na;
-            }
-          const R Tl[3] = {r[1] * Fl[2] - r[2] * Fl[1], r[2] * Fl[0] - r[0] * Fl[2], r[0] * Fl[1] - r[1] * Fl[0]};
-          if (ib_owner < 0 || ib_owner == p) {
-            ib_owner = p;
-            for (int a = 0; a < 3; ++a) { Fib[a] += Fl[a]; Tib[a] += Tl[a]; }
-          } else {   // a second particle at one node: rare, direct atomics
-            for (int a = 0; a < 3; ++a) {
-              atomicAdd(&forces[6 * p + a], (double)Fl[a]);
-              atomicAdd(&forces[6 * p + 3 + a], (double)Tl[a]);
-            }
-          }
-        }
-      }
+      if (REDUCE && lmask) ibb_cell_force<Q, STORE>(g, pl.in[0], pose, posed, nodes, c, x, y, z, lmask, k0, ib_cap,
+                                                    ib_q, ib_g, &s_q[0][threadIdx.x], &s_link[0][threadIdx.x], rho0,
+                                                    forces, ib_owner, Fib, Tib);
+    } else {
+      int k = k0;
+#pragma unroll
+      for (int i = 1; i < Q; ++i)
+        if ((lmask >> i) & 1u) f[i] = ib_g[k++];
+      if (REDUCE && lmask) ibb_cell_force<Q, STORE>(g, pl.in[0], pose, posed, nodes, c, x, y, z, lmask, k0, ib_cap,
+                                                    ib_q, ib_g, nullptr, nullptr, rho0, forces, ib_owner, Fib, Tib);
     }
   }
   // moments (Eqs. 14-15); with shifted storage f holds f_i - w_i rho0
@@ -243,10 +390,17 @@ __device__ __forceinline__ void lbm_body(Geom g, Planes<Q, typename Store<STORE>
   const R ux = (jx + R(0.5) * Fx) * inv_rho, uy = (jy + R(0.5) * Fy) * inv_rho,
               uz = (jz + R(0.5) * Fz) * inv_rho;
   const R uu = ux * ux + uy * uy + uz * uz;
-  // partially saturated cell: solid word valid only in bricks flagged for this time
+  // partially saturated cell: solid word valid only in bricks flagged for this time. Under IBB
+  // (B = 0) us is a solid node's rigid velocity.
   R B = R(0.0), usx = R(0.0), usy = R(0.0), usz = R(0.0);
   int owner = -1;
-  if constexpr (!IBB) {
+  if constexpr (IBB) {
+    if (solid_self) {
+      R us[3];
+      rigid_velocity<R>(g, pose, posed, (int)nodes[c] - 1, (R)x + R(0.5), (R)y + R(0.5), (R)z + R(0.5), us);
+      usx = us[0]; usy = us[1]; usz = us[2];
+    }
+  } else {
     const uint32_t b = ((z >> 3) * (uint32_t)g.nb[1] + (y >> 3)) * (uint32_t)g.nb[0] + (x >> 3);
     if (bword[b] >> 16) {
       const uint16_t sw = solid[c];
@@ -277,6 +431,11 @@ __device__ __forceinline__ void lbm_body(Geom g, Planes<Q, typename Store<STORE>
   // w_i rho' apart from w_i rho times the velocity polynomial: grouped otherwise (e.g. folding
   // rho' into the velocity terms) the binary32 rounding of a steady forced flow grew the
   // velocity error against the FP64 oracle from 0.96e-5 to 1.5e-5 over 500 steps.
+  // a solid node (IBB) holds the equilibrium at its particle's rigid velocity and rho0
+  auto solid_eq = [&](R w, R eu, R uus) {
+    const R dev = R(3) * eu + R(4.5) * eu * eu - R(1.5) * uus;
+    return S::shifted ? w * rho0 * dev : w * rho0 * (R(1) + dev);
+  };
   const R omB = R(1.0) - B;
   const R rtau = omB * omega;
   const R guo = omB * guo0;
@@ -290,10 +449,12 @@ __device__ __forceinline__ void lbm_body(Geom g, Planes<Q, typename Store<STORE>
     const R w = L::template wt<R>(0);
     const R feq0 = w * (S::shifted ? drho : rho) + (w * rho) * m15uu;
     out[0] = om1 * f[0] + (rtau * feq0 + (w * guo) * (-R(3.0) * uF)) + B * (R(1.5) * w * rho * (uu - usus));
+    if (IBB && solid_self) out[0] = solid_eq(w, R(0), usus);
   }
   // opposite pairs (i, i + H) share e.u. One warp-uniform branch picks the loop with the solid
-  // terms of partially saturated cells (lanes with B = 0 add exact zeros there) or the plain one.
-  auto pair_update = [&](auto psm) {
+  // terms of partially saturated cells (lanes with B = 0 add exact zeros there) or the plain one;
+  // under IBB another picks the loop that gives solid nodes their rigid equilibrium.
+  auto pair_update = [&](auto psm, auto sol) {
 #pragma unroll
     for (int i = 1; i <= L::H; ++i) {
       const int io = i + L::H;
@@ -320,35 +481,31 @@ __device__ __forceinline__ void lbm_body(Geom g, Planes<Q, typename Store<STORE>
         const R dm = B * (om_p - om_m);                 // B (Omega_i e_i + Omega_opp e_opp) / e_i
         dpx += dm * ex; dpy += dm * ey; dpz += dm * ez;
       }
-      if (!IBB && STORES) {   // stored at once: fewer values live at the same time
+      if constexpr (decltype(sol)::value) {
+        if (solid_self) {
+          const R eus = (R)ex * usx + (R)ey * usy + (R)ez * usz;
+          out[i] = solid_eq(w, eus, usus);
+          out[io] = solid_eq(w, -eus, usus);
+        }
+      }
+      if (STORES) {   // stored at once: fewer values live at the same time
         S::st(pl.out[i] + cs, out[i]);
         S::st(pl.out[io] + cs, out[io]);
       }
     }
   };
-  if (IBB || !__any_sync(0xffffffffu, B > R(0.0))) pair_update(std::false_type{});
-  else pair_update(std::true_type{});
-  if (!IBB && STORES) S::st(pl.out[0] + cs, out[0]);
-  if (STORES) {   // the reduce-only pass stores nothing
-  if (IBB && solid_self) {   // solid node: equilibrium at the particle's rigid velocity, rho0
-    R us[3];
-    rigid_velocity<R>(g, pose, posed, (int)nodes[c] - 1, (R)x + R(0.5), (R)y + R(0.5), (R)z + R(0.5), us);
-    const R uus = us[0] * us[0] + us[1] * us[1] + us[2] * us[2];
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      const R eu = (R)L::e(i, 0) * us[0] + (R)L::e(i, 1) * us[1] + (R)L::e(i, 2) * us[2];
-      const R dev = R(3) * eu + R(4.5) * eu * eu - R(1.5) * uus;
-      const R wi = L::template wt<R>(i);
-      out[i] = S::shifted ? wi * rho0 * dev : wi * rho0 * (R(1) + dev);
-    }
-    if (valid) u4[c] = make_float4((float)us[0], (float)us[1], (float)us[2], (float)rho0);
+  if (IBB) {
+    if (__any_sync(0xffffffffu, solid_self)) pair_update(std::false_type{}, std::true_type{});
+    else pair_update(std::false_type{}, std::false_type{});
+  } else if (!__any_sync(0xffffffffu, B > R(0.0))) {
+    pair_update(std::false_type{}, std::false_type{});
   } else {
-    u4[cs] = make_float4((float)ux, (float)uy, (float)uz, (float)rho);
+    pair_update(std::true_type{}, std::false_type{});
   }
-  if (IBB && valid) {   // (the partially saturated cells stored each pair above)
-#pragma unroll
-    for (int i = 0; i < Q; ++i) S::st(pl.out[i] + c, out[i]);
-  }
+  if (STORES) {   // the reduce-only pass stores nothing
+    S::st(pl.out[0] + cs, out[0]);
+    if (IBB && solid_self) u4[cs] = make_float4((float)usx, (float)usy, (float)usz, (float)rho0);
+    else u4[cs] = make_float4((float)ux, (float)uy, (float)uz, (float)rho);
   }
   // hydrodynamic force on the owner particle: -B sum_i Omega_i e_i; torque about its origin.
   // Formed, like the mass/momentum sums, only on the step whose sums are read (REDUCE); the
@@ -359,7 +516,7 @@ __device__ __forceinline__ void lbm_body(Geom g, Planes<Q, typename Store<STORE>
   if (REDUCE && __any_sync(full, hasF)) {
     R Fc[3] = {-dpx, -dpy, -dpz};
     R Tc[3] = {R(0.0), R(0.0), R(0.0)};
-    if (IBB) {   // link forces and torques summed above
+    if (IBB) {   // link forces and torques of the cell
       for (int a = 0; a < 3; ++a) { Fc[a] = Fib[a]; Tc[a] = Tib[a]; }
     } else if (hasF) {
       R po[3], pv[3], pw[3];
@@ -444,9 +601,10 @@ lbm_kernel(Geom g, Planes<Q, typename Store<STORE>::T> pl, float4* __restrict__ 
            typename Store<STORE>::R guo0, typename Store<STORE>::R rho0, double* __restrict__ red,
            double* __restrict__ forces, const uint16_t* __restrict__ nodes, const float4* __restrict__ uprev,
            const ParticleDesc* __restrict__ desc, const float4* __restrict__ cworld,
-           const int32_t* __restrict__ ib_base, const float* __restrict__ ib_q, int ib_cap) {
+           const int32_t* __restrict__ ib_base, const uint32_t* __restrict__ ib_word, const float* __restrict__ ib_q,
+           const typename Store<STORE>::R* __restrict__ ib_g, int ib_cap) {
   lbm_body<Q, STORE, WALLS, MODE, IBB>(g, pl, u4, solid, bword, pose, posed, sp, tau, omega, guo0, rho0, red, forces,
-                                       nodes, uprev, desc, cworld, ib_base, ib_q, ib_cap, blockIdx.x);
+                                       nodes, uprev, desc, cworld, ib_base, ib_word, ib_q, ib_g, ib_cap, blockIdx.x);
 }
 
 // One launch over the cells of many domains: block -> (domain, block of that domain's grid). Its
@@ -458,19 +616,21 @@ __global__ void __launch_bounds__(256, sizeof(typename Store<STORE>::R) == 8 ? 2
   const LbmArgs<Q, STORE>& a = args[m.domain];
   lbm_body<Q, STORE, WALLS, MODE, IBB>(a.g, a.pl, a.u4, a.solid, a.bword, a.pose, a.posed, a.sp, a.tau, a.omega,
                                        a.guo0, a.rho0, a.red, a.forces, nullptr, nullptr, nullptr, nullptr,
-                                       nullptr, nullptr, 0, m.block);
+                                       nullptr, nullptr, nullptr, nullptr, 0, m.block);
 }
 #undef RWMI_LBM_BOUNDS
 
 // ---- IBB links (Eq. 25) ahead of the LBM update ------------------------------------------
 // Every fluid node of a flagged brick whose lattice neighbour x - e_i is a solid node owns the
-// link (x, i). ibb_links_kernel appends a node's links in direction order (warp-aggregated) and
-// keeps the index of its first one; ibb_q_kernel then runs the 24-step binary32 bisection of
-// every link at full occupancy, instead of inside the occupancy-bound LBM kernel.
+// link (x, i). ibb_links_kernel gives every cell of a flagged brick its node word (bit 0: solid
+// node; bit i: link i), appends a node's links in direction order (warp-aggregated) and keeps the
+// index of its first one; ibb_q_kernel then runs the 24-step binary32 bisection of every link at
+// full occupancy, instead of inside the occupancy-bound LBM kernel.
 template <int Q, bool WALLS>
 __global__ void __launch_bounds__(256) ibb_links_kernel(Geom g, const uint32_t* __restrict__ bword,
                                                         const uint16_t* __restrict__ nodes,
-                                                        int32_t* __restrict__ base, uint32_t* __restrict__ lcell,
+                                                        int32_t* __restrict__ base, uint32_t* __restrict__ word,
+                                                        uint32_t* __restrict__ lcell,
                                                         uint32_t* __restrict__ lmeta, unsigned int* count, int cap,
                                                         unsigned long long* __restrict__ status) {
   using L = Lat<Q>;
@@ -501,10 +661,14 @@ __global__ void __launch_bounds__(256) ibb_links_kernel(Geom g, const uint32_t* 
   };
   unsigned lmask = 0u;
   const uint32_t bq = ((z >> 3) * (uint32_t)g.nb[1] + (y >> 3)) * (uint32_t)g.nb[0] + (x >> 3);
-  if (valid && (bword[bq] >> 16) && nodes[c] == 0) {
+  if (valid && (bword[bq] >> 16)) {
+    const bool solid_node = nodes[c] != 0;
+    if (!solid_node) {
 #pragma unroll
-    for (int i = 1; i < Q; ++i)
-      if (!blocked(i) && nodes[c + off_of(i)] != 0) lmask |= 1u << i;
+      for (int i = 1; i < Q; ++i)
+        if (!blocked(i) && nodes[c + off_of(i)] != 0) lmask |= 1u << i;
+    }
+    word[c] = lmask | (solid_node ? 1u : 0u);
   }
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
@@ -533,46 +697,82 @@ __global__ void __launch_bounds__(256) ibb_links_kernel(Geom g, const uint32_t* 
   if (first + (unsigned)nl > (unsigned)cap) atomicAdd(&status[ST_IBB_OVERFLOW], 1ull);
 }
 
-template <int Q>
-__global__ void __launch_bounds__(256) ibb_q_kernel(Geom g, const float4* __restrict__ cworld,
-                                                    const ParticleDesc* __restrict__ desc,
-                                                    const uint32_t* __restrict__ lcell,
-                                                    const uint32_t* __restrict__ lmeta, const unsigned int* count,
-                                                    unsigned int* count_next, int cap, float* __restrict__ q) {
+// One thread per listed link: q by the binary32 bisection (Eq. 25), then G_i (Eqs. 23-24) from
+// the input populations and the previous velocity. The LBM kernel replaces the link's pulled
+// population by G_i and, on the steps that read forces, forms the momentum exchange from q and G
+// cell by cell in direction order.
+template <int Q, int STORE, bool WALLS>
+__global__ void __launch_bounds__(256) ibb_link_kernel(Geom g, const float4* __restrict__ cworld,
+                                                       const ParticleDesc* __restrict__ desc,
+                                                       const uint32_t* __restrict__ lcell,
+                                                       const uint32_t* __restrict__ lmeta, const unsigned int* count,
+                                                       unsigned int* count_next, int cap, float* __restrict__ qout,
+                                                       typename Store<STORE>::R* __restrict__ gout,
+                                                       const typename Store<STORE>::T* __restrict__ in0,
+                                                       const float4* __restrict__ uprev,
+                                                       const uint16_t* __restrict__ nodes,
+                                                       const PoseF* __restrict__ pose, const PoseD* __restrict__ posed,
+                                                       typename Store<STORE>::R rho0) {
   using L = Lat<Q>;
+  using S = Store<STORE>;
+  using R = typename S::R;
   if (blockIdx.x == 0 && threadIdx.x == 0) *count_next = 0u;   // the next step appends there
   const unsigned n = min(*count, (unsigned)cap);
   for (unsigned j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
-    const uint32_t c = lcell[j], meta = lmeta[j];
-    const uint32_t z = fast_div(c, g.mxy, g.sxy), r = c - z * g.nxy;
+    const int c = (int)lcell[j];
+    const uint32_t meta = lmeta[j];
+    const uint32_t z = fast_div((uint32_t)c, g.mxy, g.sxy), r = (uint32_t)c - z * g.nxy;
     const uint32_t y = fast_div(r, g.mx, g.sx), x = r - y * g.n[0];
     const int i = (int)(meta & 31u), p = (int)(meta >> 8), ip = L::opp(i);
-    q[j] = ibb_link_q(cworld, desc[p].c0, desc[p].c1, (float)x + 0.5f, (float)y + 0.5f, (float)z + 0.5f,
-                      L::e(ip, 0), L::e(ip, 1), L::e(ip, 2), g);
+    const float qv = ibb_link_q(cworld, desc[p].c0, desc[p].c1, (float)x + 0.5f, (float)y + 0.5f, (float)z + 0.5f,
+                                L::e(ip, 0), L::e(ip, 1), L::e(ip, 2), g);
+    qout[j] = qv;
+    R sum = R(0);   // rho_f: x_f's own post-collision populations, summed in direction order
+#pragma unroll
+    for (int d = 0; d < Q; ++d) sum += S::ld(in0 + (size_t)d * g.ncell_pad + c);
+    const R rho_f = S::shifted ? rho0 + sum : sum;
+    const float4 u = uprev[c];
+    const R uf[3] = {(R)u.x, (R)u.y, (R)u.z};
+    R Gp, xw[3], uw[3];
+    gout[j] = ibb_link_value<Q, STORE, WALLS>(g, in0, uprev, nodes, pose, posed, c, x, y, z, i, p, (R)qv, rho_f, uf,
+                                              Gp, xw, uw);
   }
 }
 
-void launch_ibb_links(int q, const Geom& g, BrickSet bs, const uint16_t* nodes, const IbbLinks& lk, int par,
-                      const ParticleDesc* desc, unsigned long long* status, int nsm, cudaStream_t st) {
+void launch_ibb_links(int q, int storage, const Geom& g, BrickSet bs, const uint16_t* nodes, const IbbLinks& lk,
+                      int par, const ParticleDesc* desc, const void* fin, const float* uprev, double rho0,
+                      unsigned long long* status, int nsm, cudaStream_t st) {
   const bool walls = g.wall[0] || g.wall[1] || g.wall[2];
   const unsigned blocks = (unsigned)((g.ncell + 255) / 256);
   unsigned int* cnt = lk.count + (par & 1);
   unsigned int* nxt = lk.count + ((par + 1) & 1);
+  const float4* u4 = reinterpret_cast<const float4*>(uprev);
+#define RWMI_IBB_LINKS(QQ, SS, WW)                                                                                   \
+  do {                                                                                                             \
+    using T_ = typename Store<SS>::T;                                                                              \
+    using R_ = typename Store<SS>::R;                                                                              \
+    ibb_links_kernel<QQ, WW><<<blocks, 256, 0, st>>>(g, bs.bword, nodes, lk.base, lk.word, lk.cell, lk.meta, cnt,   \
+                                                      lk.cap, status);                                             \
+    ibb_link_kernel<QQ, SS, WW><<<nsm * 8, 256, 0, st>>>(g, bs.cworld, desc, lk.cell, lk.meta, cnt, nxt, lk.cap,   \
+                                                         lk.q, static_cast<R_*>(lk.g), static_cast<const T_*>(fin),\
+                                                         u4, nodes, bs.pose, bs.posed, (R_)rho0);                  \
+  } while (0)
+#define RWMI_IBB_W(QQ, SS) \
+  if (walls) RWMI_IBB_LINKS(QQ, SS, true); else RWMI_IBB_LINKS(QQ, SS, false)
+  // IBB is built for binary32-shifted and binary64-shifted storage
   if (q == 15) {
-    if (walls) ibb_links_kernel<15, true><<<blocks, 256, 0, st>>>(g, bs.bword, nodes, lk.base, lk.cell, lk.meta, cnt, lk.cap, status);
-    else ibb_links_kernel<15, false><<<blocks, 256, 0, st>>>(g, bs.bword, nodes, lk.base, lk.cell, lk.meta, cnt, lk.cap, status);
-    ibb_q_kernel<15><<<nsm * 8, 256, 0, st>>>(g, bs.cworld, desc, lk.cell, lk.meta, cnt, nxt, lk.cap, lk.q);
+    if (storage == 3) { RWMI_IBB_W(15, 3); } else { RWMI_IBB_W(15, 1); }
   } else {
-    if (walls) ibb_links_kernel<19, true><<<blocks, 256, 0, st>>>(g, bs.bword, nodes, lk.base, lk.cell, lk.meta, cnt, lk.cap, status);
-    else ibb_links_kernel<19, false><<<blocks, 256, 0, st>>>(g, bs.bword, nodes, lk.base, lk.cell, lk.meta, cnt, lk.cap, status);
-    ibb_q_kernel<19><<<nsm * 8, 256, 0, st>>>(g, bs.cworld, desc, lk.cell, lk.meta, cnt, nxt, lk.cap, lk.q);
+    if (storage == 3) { RWMI_IBB_W(19, 3); } else { RWMI_IBB_W(19, 1); }
   }
+#undef RWMI_IBB_W
+#undef RWMI_IBB_LINKS
 }
 
 template <int Q, int STORE, bool IBB>
 static void launch_lbm_q(bool walls, bool reduce, const Geom& g, const void* fin, void* fout, float* u,
                          const uint16_t* solid, BrickSet bs, double tau, double rho0, double* red,
-                         double* forces, cudaStream_t st, int bsz, const IbbArgs& ib, bool fused) {
+                         double* forces, cudaStream_t st, int bsz, const IbbArgs& ib, bool fused, bool update) {
   using T = typename Store<STORE>::T;
   using R = typename Store<STORE>::R;
   Planes<Q, T> pl;
@@ -582,7 +782,7 @@ static void launch_lbm_q(bool walls, bool reduce, const Geom& g, const void* fin
   }
   const int bsz_ok = (bsz == 64 || bsz == 128) ? bsz : 256;
   const dim3 grid((g.ncell + bsz_ok - 1) / bsz_ok), block(bsz_ok);
-#define RWMI_LBM_ARGS g, pl, reinterpret_cast<float4*>(u), solid, bs.bword, bs.pose, bs.posed, bs.sp, (R)tau, (R)(1.0 / tau), (R)(1.0 - 0.5 / tau), (R)rho0, red, forces, ib.nodes, ib.uprev, ib.desc, bs.cworld, ib.base, ib.q, ib.cap
+#define RWMI_LBM_ARGS g, pl, reinterpret_cast<float4*>(u), solid, bs.bword, bs.pose, bs.posed, bs.sp, (R)tau, (R)(1.0 / tau), (R)(1.0 - 0.5 / tau), (R)rho0, red, forces, ib.nodes, ib.uprev, ib.desc, bs.cworld, ib.base, ib.word, ib.q, static_cast<const R*>(ib.g), ib.cap
   if constexpr (STORE == 1 || STORE == 3) {   // the fused mode of free-DEM runs
     if (fused) {
       if (walls) lbm_kernel<Q, STORE, true, 2, IBB><<<grid, block, 0, st>>>(RWMI_LBM_ARGS);
@@ -591,10 +791,10 @@ static void launch_lbm_q(bool walls, bool reduce, const Geom& g, const void* fin
     }
   }
   if (walls) {
-    lbm_kernel<Q, STORE, true, 0, IBB><<<grid, block, 0, st>>>(RWMI_LBM_ARGS);
+    if (update) lbm_kernel<Q, STORE, true, 0, IBB><<<grid, block, 0, st>>>(RWMI_LBM_ARGS);
     if (reduce) lbm_kernel<Q, STORE, true, 1, IBB><<<grid, block, 0, st>>>(RWMI_LBM_ARGS);
   } else {
-    lbm_kernel<Q, STORE, false, 0, IBB><<<grid, block, 0, st>>>(RWMI_LBM_ARGS);
+    if (update) lbm_kernel<Q, STORE, false, 0, IBB><<<grid, block, 0, st>>>(RWMI_LBM_ARGS);
     if (reduce) lbm_kernel<Q, STORE, false, 1, IBB><<<grid, block, 0, st>>>(RWMI_LBM_ARGS);
   }
 #undef RWMI_LBM_ARGS
@@ -603,7 +803,7 @@ static void launch_lbm_q(bool walls, bool reduce, const Geom& g, const void* fin
 void launch_lbm(int q, int storage, bool reduce, const Geom& g, const void* fin, void* fout,
                 float* u, const uint16_t* solid, BrickSet bs, double tau, double rho0, double* red,
                 double* forces, unsigned long long* status, cudaStream_t st, int block, const IbbArgs* ibb,
-                bool fused) {
+                bool fused, bool update) {
   (void)status;
   const bool walls = g.wall[0] || g.wall[1] || g.wall[2];
   const IbbArgs none{};
@@ -611,9 +811,9 @@ void launch_lbm(int q, int storage, bool reduce, const Geom& g, const void* fin,
   // IBB is built for binary32-shifted and binary64 storage (the configuration check refuses the
   // others); the other storages run the partially saturated cells only
 #define RWMI_LBM_PSM(QQ, SS) \
-  launch_lbm_q<QQ, SS, false>(walls, reduce, g, fin, fout, u, solid, bs, tau, rho0, red, forces, st, block, ib, fused)
+  launch_lbm_q<QQ, SS, false>(walls, reduce, g, fin, fout, u, solid, bs, tau, rho0, red, forces, st, block, ib, fused, update)
 #define RWMI_LBM_CASE(QQ, SS)                                                                           \
-  if (ibb) launch_lbm_q<QQ, SS, true>(walls, reduce, g, fin, fout, u, solid, bs, tau, rho0, red, forces, st, block, ib, fused); \
+  if (ibb) launch_lbm_q<QQ, SS, true>(walls, reduce, g, fin, fout, u, solid, bs, tau, rho0, red, forces, st, block, ib, fused, update); \
   else RWMI_LBM_PSM(QQ, SS)
   if (q == 15) {
     if (storage == 0) { RWMI_LBM_PSM(15, 0); }
@@ -628,6 +828,228 @@ void launch_lbm(int q, int storage, bool reduce, const Geom& g, const void* fin,
   }
 #undef RWMI_LBM_CASE
 #undef RWMI_LBM_PSM
+}
+
+// ---- TMA-staged update ------------------------------------------------------------------------
+// The same update (MODE 0, partially saturated cells) with the pulls staged through shared
+// memory: a resident grid walks the row tiles; per tile one thread issues Q tensor copies (one
+// source row per direction, the rows at y - e_y, z - e_z wrapped on periodic axes) into one of
+// TMA_STAGES buffers, completing on that buffer's mbarrier, TMA_STAGES - 1 tiles ahead of the
+// compute. On a periodic x axis the halo element beyond the row's end is patched in from the other
+// end; wall-blocked directions read their bounce-back population from global memory. Every wait
+// is bounded: on expiry the kernel counts ST_TMA_TIMEOUT, waits (bounded) for its copies in
+// flight and returns.
+constexpr int TMA_STAGES = 3;
+constexpr long long TMA_WAIT_CYCLES = 4000000000LL;   // about two seconds at the SM clock
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+               : "=r"(ok) : "r"(smem_addr(bar)), "r"(parity) : "memory");
+  return ok != 0u;
+}
+// Waits for the phase of parity `parity` to complete; false when TMA_WAIT_CYCLES pass first.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  for (;;) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (clock64() - t0 > TMA_WAIT_CYCLES) return false;
+  }
+}
+
+template <int Q, int STORE, bool WALLS>
+__device__ __forceinline__ void tma_issue_tile(const CUtensorMap* map, typename Store<STORE>::T* stage, uint64_t* bar,
+                                               const Geom& g, int tpr, int t) {
+  using L = Lat<Q>;
+  using TR = TmaRow<STORE>;
+  const int row = t / tpr, x0 = (t - row * tpr) * TMA_BX;
+  const int ny = g.n[1], nz = g.n[2];
+  const int y = row % ny, z = row / ny;
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+               :: "r"(smem_addr(bar)), "r"((uint32_t)(Q * TR::bytes)) : "memory");
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const int ey = L::e(i, 1), ez = L::e(i, 2);
+    // periodic axes wrap; on a wall axis a blocked source row may fall outside (zero fill) and
+    // is never read
+    int ys = y - ey, zs = z - ez;
+    if (!(WALLS && g.wall[1])) ys = ys < 0 ? ys + ny : ys >= ny ? ys - ny : ys;
+    if (!(WALLS && g.wall[2])) zs = zs < 0 ? zs + nz : zs >= nz ? zs - nz : zs;
+    const int rs = (ys < 0 || ys >= ny) ? -1 : zs * ny + ys;
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        :: "r"(smem_addr(stage + i * TR::pad)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x0 - TR::halo), "r"(rs),
+           "r"(i), "r"(smem_addr(bar))
+        : "memory");
+  }
+}
+
+template <int Q, int STORE, bool WALLS>
+__global__ void __launch_bounds__(TMA_BX, 8)
+lbm_tma_kernel(const __grid_constant__ CUtensorMap tin, Geom g, Planes<Q, typename Store<STORE>::T> pl,
+               float4* __restrict__ u4, const uint16_t* __restrict__ solid, const uint32_t* __restrict__ bword,
+               const PoseF* __restrict__ pose, const PoseD* __restrict__ posed, const StepParams* __restrict__ sp,
+               typename Store<STORE>::R tau, typename Store<STORE>::R omega, typename Store<STORE>::R guo0,
+               typename Store<STORE>::R rho0, int tpr, unsigned long long* __restrict__ status) {
+  using L = Lat<Q>;
+  using S = Store<STORE>;
+  using T = typename S::T;
+  using TR = TmaRow<STORE>;
+  extern __shared__ __align__(128) unsigned char tma_smem[];
+  __shared__ __align__(8) uint64_t bar[TMA_STAGES];
+  // stage rows start on 128-byte boundaries (the launch adds 128 bytes of slack)
+  T* stages = reinterpret_cast<T*>(tma_smem + ((128u - (smem_addr(tma_smem) & 127u)) & 127u));
+  constexpr int stage_elems = Q * TR::pad;
+  const int nx = g.n[0], ny = g.n[1];
+  const int ntiles = ny * g.n[2] * tpr;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    for (int s = 0; s < TMA_STAGES; ++s)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_addr(&bar[s])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (tid == 0)
+    for (int s = 0; s < TMA_STAGES; ++s) {
+      const int t = blockIdx.x + s * gridDim.x;
+      if (t < ntiles) tma_issue_tile<Q, STORE, WALLS>(&tin, stages + s * stage_elems, &bar[s], g, tpr, t);
+    }
+  const bool xper = !(WALLS && g.wall[0]);
+  int k = 0;
+  bool expired = false;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
+    const int s = k % TMA_STAGES;
+    const uint32_t parity = (uint32_t)(k / TMA_STAGES) & 1u;
+    T* stage = stages + s * stage_elems;
+    const bool ok = mbar_wait_bounded(&bar[s], parity);
+    if (__syncthreads_or(!ok)) { expired = true; break; }
+    const int row = t / tpr, x0 = (t - row * tpr) * TMA_BX;
+    const bool left = x0 == 0, right = x0 + TMA_BX >= nx;
+    if (xper && (left || right)) {   // tile-uniform: patch the wrapped halo elements
+      if (tid < Q) {
+        const int i = tid, ex = L::e(i, 0), ey = L::e(i, 1), ez = L::e(i, 2);
+        const int y = row % ny, z = row / ny;
+        int ys = y - ey, zs = z - ez;
+        const bool yw = WALLS && g.wall[1], zw = WALLS && g.wall[2];
+        if (!yw) ys = ys < 0 ? ys + ny : ys >= ny ? ys - ny : ys;
+        if (!zw) zs = zs < 0 ? zs + g.n[2] : zs >= g.n[2] ? zs - g.n[2] : zs;
+        if (ys >= 0 && ys < ny && zs >= 0 && zs < g.n[2]) {
+          const int rbase = (zs * ny + ys) * nx;
+          if (left && ex > 0) stage[i * TR::pad + TR::halo - 1] = pl.in[i][rbase + nx - 1];
+          if (right && ex < 0) stage[i * TR::pad + TR::halo + (nx - x0)] = pl.in[i][rbase];
+        }
+      }
+      __syncthreads();
+    }
+    const bool valid = x0 + tid < nx;
+    const int lx = valid ? tid : nx - 1 - x0;   // tail lanes recompute the row's last cell
+    const uint32_t c = (uint32_t)row * (uint32_t)nx + (uint32_t)(x0 + lx);
+    lbm_body<Q, STORE, WALLS, 0, false, true>(g, pl, u4, solid, bword, pose, posed, sp, tau, omega, guo0, rho0,
+                                              nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                              nullptr, nullptr, 0, 0, stage, c, valid, lx);
+    __syncthreads();   // every lane is done with this buffer
+    if (tid == 0) {
+      const int tn = t + TMA_STAGES * gridDim.x;
+      if (tn < ntiles) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // the halo patch before new copies
+        tma_issue_tile<Q, STORE, WALLS>(&tin, stage, &bar[s], g, tpr, tn);
+      }
+    }
+  }
+  if (expired) {   // count it; let the copies in flight land (bounded) before the block exits
+    if (tid == 0) {
+      atomicAdd(&status[ST_TMA_TIMEOUT], 1ull);
+      for (int j = 0; j < TMA_STAGES; ++j) {
+        const int kk = k + j, tt = blockIdx.x + kk * gridDim.x;
+        if (tt < ntiles) mbar_wait_bounded(&bar[kk % TMA_STAGES], (uint32_t)(kk / TMA_STAGES) & 1u);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+size_t lbm_tma_smem(int q, int storage) {
+  const int pad_bytes = storage == 2 ? TmaRow<2>::pad * 2 : TmaRow<1>::pad * 4;
+  return (size_t)TMA_STAGES * (size_t)q * (size_t)pad_bytes + 128;
+}
+
+bool lbm_tma_supported(int q, int storage, const Geom& g) {
+  if (storage < 0 || storage > 2 || (q != 15 && q != 19)) return false;
+  const int align = storage == 2 ? 8 : 4;   // row pitch a multiple of 16 bytes
+  return g.n[0] % align == 0 && (int64_t)g.n[1] * g.n[2] < (1LL << 31);
+}
+
+// Tensor map of one population buffer: dims (x, row = y + ny z, direction), pitches nx and
+// ncell_pad elements; box (TMA_BX + 2 halo, 1, 1); out-of-range elements read as zero.
+bool lbm_tma_encode(int q, int storage, const Geom& g, const void* f, CUtensorMap* map) {
+  if (!lbm_tma_supported(q, storage, g)) return false;
+  using Encode = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                              const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+  static Encode encode = nullptr;
+  if (!encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult qr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &qr) !=
+            cudaSuccess || qr != cudaDriverEntryPointSuccess || !fn)
+      return false;
+    encode = reinterpret_cast<Encode>(fn);
+  }
+  const int es = storage == 2 ? 2 : 4;
+  const cuuint64_t dims[3] = {(cuuint64_t)g.n[0], (cuuint64_t)g.n[1] * (cuuint64_t)g.n[2], (cuuint64_t)q};
+  const cuuint64_t pitch[2] = {(cuuint64_t)g.n[0] * es, (cuuint64_t)g.ncell_pad * es};
+  const cuuint32_t box[3] = {(cuuint32_t)(TMA_BX + 2 * (16 / es)), 1, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  const CUresult r = encode(map, storage == 2 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+                            const_cast<void*>(f), dims, pitch, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+template <int Q, int STORE>
+static void launch_lbm_tma_q(bool walls, const CUtensorMap& map, const Geom& g, const void* fin, void* fout, float* u,
+                             const uint16_t* solid, BrickSet bs, double tau, double rho0, unsigned long long* status,
+                             int nsm, cudaStream_t st) {
+  using T = typename Store<STORE>::T;
+  using R = typename Store<STORE>::R;
+  Planes<Q, T> pl;
+  for (int i = 0; i < Q; ++i) {
+    pl.in[i] = (const T*)fin + (size_t)i * g.ncell_pad;
+    pl.out[i] = (T*)fout + (size_t)i * g.ncell_pad;
+  }
+  const int tpr = (g.n[0] + TMA_BX - 1) / TMA_BX;
+  const size_t smem = lbm_tma_smem(Q, STORE);
+  auto kern = walls ? lbm_tma_kernel<Q, STORE, true> : lbm_tma_kernel<Q, STORE, false>;
+  static bool attr = false;   // per instantiation
+  if (!attr) {
+    cudaFuncSetAttribute(lbm_tma_kernel<Q, STORE, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(lbm_tma_kernel<Q, STORE, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr = true;
+  }
+  static int per_sm = 0;   // resident blocks per SM (shared memory bound)
+  if (per_sm == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TMA_BX, smem);
+  const int64_t ntiles = (int64_t)g.n[1] * g.n[2] * tpr;
+  const int grid = (int)std::min<int64_t>(ntiles, (int64_t)nsm * std::max(per_sm, 1));
+  kern<<<grid, TMA_BX, smem, st>>>(map, g, pl, reinterpret_cast<float4*>(u), solid, bs.bword, bs.pose, bs.posed, bs.sp,
+                                   (R)tau, (R)(1.0 / tau), (R)(1.0 - 0.5 / tau), (R)rho0, tpr, status);
+}
+
+void launch_lbm_tma(int q, int storage, const CUtensorMap& map, const Geom& g, const void* fin, void* fout, float* u,
+                    const uint16_t* solid, BrickSet bs, double tau, double rho0, unsigned long long* status, int nsm,
+                    cudaStream_t st) {
+  const bool walls = g.wall[0] || g.wall[1] || g.wall[2];
+#define RWMI_TMA(QQ, SS) launch_lbm_tma_q<QQ, SS>(walls, map, g, fin, fout, u, solid, bs, tau, rho0, status, nsm, st)
+  if (q == 15) {
+    if (storage == 0) RWMI_TMA(15, 0); else if (storage == 1) RWMI_TMA(15, 1); else RWMI_TMA(15, 2);
+  } else {
+    if (storage == 0) RWMI_TMA(19, 0); else if (storage == 1) RWMI_TMA(19, 1); else RWMI_TMA(19, 2);
+  }
+#undef RWMI_TMA
 }
 
 template <int Q, int STORE>

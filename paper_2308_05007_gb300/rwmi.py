@@ -50,7 +50,7 @@ class Config(C.Structure):
                 ("body_force", C.c_double * 3), ("force_period", C.c_double), ("rho0", C.c_double),
                 ("init_velocity", C.c_double * 3), ("sort_interval", C.c_int32),
                 ("moment_interval", C.c_int32), ("use_graphs", C.c_int32), ("lbm_block", C.c_int32),
-                ("overlap", C.c_int32), ("coupling", C.c_int32)]
+                ("overlap", C.c_int32), ("coupling", C.c_int32), ("lbm_staging", C.c_int32)]
 
 
 class BatchTiles(C.Structure):
@@ -249,7 +249,7 @@ class Simulation:
     def __init__(self, dims, tau, D, seed=0, q=19, storage=STORE_FP32_SHIFT, wall_mask=0,
                  body_force=(0.0, 0.0, 0.0), force_period=0.0, rho0=1.0, init_velocity=(0.0, 0.0, 0.0),
                  sort_interval=16, moment_interval=0, use_graphs=True, stream=None, lbm_block=256,
-                 overlap=2, coupling=0):
+                 overlap=2, coupling=0, lbm_staging=0):
         L = load()
         self._L = L
         self._h = C.c_void_p()
@@ -271,6 +271,7 @@ class Simulation:
         cfg.lbm_block = int(lbm_block)
         cfg.overlap = int(overlap)
         cfg.coupling = int(coupling)
+        cfg.lbm_staging = int(lbm_staging)
         try:
             self._check(L.rwmi_configure(self._h, C.byref(cfg)))
         except RwmiError:
