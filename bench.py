@@ -73,14 +73,15 @@ def workload(a):
 
 def bytes_per_step(w, n_cells, s):
     """Algorithmic HBM bytes of one step: populations read + written once (2 Q s per cell), the
-    (u, rho) float4 written by the LBM kernel and gathered once by the cell-sorted walkers
-    (16 + 16 B per cell), each walker's float4 read and written (32 B)."""
-    return n_cells * (2 * w.q * s + 32) + 32 * w.n_walkers
+    velocity written by the LBM kernel and gathered once by the cell-sorted walkers (12 + 12 B
+    per cell), each walker's float4 read and written (32 B). The kernels move 4 B per cell more
+    each way (rho rides along in a float4, one 16-byte gather per corner); that is not counted."""
+    return n_cells * (2 * w.q * s + 24) + 32 * w.n_walkers
 
 
 def lbm_bytes_per_launch(w, n_cells, s):
-    """Algorithmic bytes of one launch of the LBM kernel: 2 Q s per cell + 16 B of (u, rho)."""
-    return n_cells * (2 * w.q * s + 16)
+    """Algorithmic bytes of one launch of the LBM update: 2 Q s per cell + 12 B of velocity."""
+    return n_cells * (2 * w.q * s + 12)
 
 
 def config_dict(a, w):
