@@ -338,9 +338,10 @@ def measure_variants(a, stream):
             sim.seed_walkers(w.n_walkers, *w.walker_box)
             sim.step(16)
             ph = sim.step_timed(16)
+            one = sorted(sim.step_timed(1)["lbm"] for _ in range(5))[2]
             sim.close()
             s_bytes = STORE_BYTES[storage]
-            lbm_ms = ph["lbm"] / 16
+            lbm_ms = (ph["lbm"] - one) / 15   # the update alone (16 updates + 1 reduce pass)
             step_ms = sum(ph.values()) / 16
             gbs = lbm_bytes_per_launch(w, w.n_cells, s_bytes) / (lbm_ms / 1e3) / 1e9
             name = f"D3Q{q}_{STORE_NAMES[storage]}" + ("_tma" if staging else "")
@@ -604,6 +605,11 @@ def main():
         # per-phase GPU time (CUDA events on the launching stream, eager launches)
         phases = sim.step_timed(L)
         n_timed_phase_steps = L
+        # the update kernel alone: a timed run of L steps holds L updates and one reduce-only
+        # pass (on its last step), a timed single step one of each
+        one = sorted(sim.step_timed(1)["lbm"] for _ in range(7))[3]
+        lbm_update_ms = (phases["lbm"] - one) / (L - 1)
+        reduce_pass_ms = one - lbm_update_ms
         sim.step(-sim.t % period)
         warm = sim.t
         assert sim.sync() >= 0
@@ -659,7 +665,7 @@ def main():
     if rank != 0:
         return
     peaks = measured_peaks()
-    lbm_ms = phases["lbm"] / n_timed_phase_steps
+    lbm_ms = lbm_update_ms
     achieved = lbm_bytes_per_launch(w, w.n_cells, s_bytes) / (lbm_ms / 1e3) / 1e9
     peak = float(peaks["hbm_gbs"])
     traffic = profiled_traffic(a)
@@ -675,6 +681,8 @@ def main():
         "roofline": {"kernel": "lbm_kernel", "bound": "hbm", "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                      "algorithmic_bytes_per_launch": lbm_bytes_per_launch(w, w.n_cells, s_bytes),
+                     "launch_ms": lbm_update_ms, "reduce_pass_ms": reduce_pass_ms,
+                     "phase_ms": phases["lbm"] / n_timed_phase_steps,
                      "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if not peaks.get("fallback") else "fallback"},
         "phase_ms_per_step": {k: v / n_timed_phase_steps for k, v in phases.items()},
         "gpu_launches": launches,
