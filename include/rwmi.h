@@ -451,6 +451,16 @@ RWMI_API int64_t rwmi_inject_alloc_failure(int64_t after);
 /* Number of device allocations the library has made (or refused by injection) in this process. */
 RWMI_API int64_t rwmi_alloc_count(void);
 
+/* Wait-timeout injection for tests of the bounded device waits (the TMA-staged LBM update,
+ * rwmi_config.lbm_staging = 1, waits on mbarriers for its own tensor copies, at most ~2 s). The
+ * next `launches` staged updates (process-wide) leave the copies of their first tile unissued, so
+ * that tile's barrier never completes, and wait for it only about a millisecond: the block that
+ * owns the tile gives up, counts the timeout and returns after its other copies have landed;
+ * rwmi_sync then reports RWMI_E_TIMEOUT (the context stays usable; that step's update is
+ * incomplete). Nothing faults and no copy is left in flight. A captured run keeps the injected
+ * launch, so tests step with use_graphs = 0. launches <= 0 disarms. Returns the previous count. */
+RWMI_API int32_t rwmi_inject_wait_timeout(int32_t launches);
+
 /* Frees every resource of the context; NULL is allowed. A context fenced by RWMI_E_OOM or
  * RWMI_E_CUDA is freed as far as it was built. */
 RWMI_API void rwmi_destroy(rwmi_ctx* ctx);

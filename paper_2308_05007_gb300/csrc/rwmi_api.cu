@@ -6,6 +6,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <exception>
 #include <map>
@@ -791,17 +792,25 @@ RWMI_API rwmi_status rwmi_configure(rwmi_ctx* c, const rwmi_config* cfg) try {
     if (s != RWMI_OK) return s;
   }
   c->fcur = 0;
-  if (cfg->coupling == 1 && !c->ibl.base) {   // IBB link list: half a link per cell (2^20 at least)
-    c->ibl.cap = (int)std::min<int64_t>(std::max<int64_t>(c->ncell / 2, 1 << 20), 0x7fffffff);
+  if (cfg->coupling == 1 && !c->ibl.base) {
+    // IBB link list: half a link per cell (2^20 at least); overflow slots of 18 links (Q - 1 at
+    // most) for a sixteenth of the cells (2^16 at least). RWMI_IBB_LINK_CAP, if set, shrinks the
+    // list (tests use it to run the overflow slots).
+    int64_t cap = std::max<int64_t>(c->ncell / 2, 1 << 20);
+    if (const char* e = std::getenv("RWMI_IBB_LINK_CAP")) cap = std::max<int64_t>(1, std::atoll(e));
+    c->ibl.cap = (int)std::min<int64_t>(cap, 0x3fffffff);
+    c->ibl.ocap = (int)std::min<int64_t>(std::max<int64_t>(c->ncell / 16, 1 << 16), 0x3fffffff / 18);
+    const size_t nlq = (size_t)c->ibl.cap + (size_t)c->ibl.ocap * 18;
     CK(dalloc(c, &c->ibl.base, sizeof(int32_t) * (size_t)c->ncell));
     CK(dalloc(c, &c->ibl.word, sizeof(uint32_t) * (size_t)c->ncell));
     CK(dalloc(c, &c->ibl.cell, sizeof(uint32_t) * (size_t)c->ibl.cap));
     CK(dalloc(c, &c->ibl.meta, sizeof(uint32_t) * (size_t)c->ibl.cap));
-    CK(dalloc(c, &c->ibl.q, sizeof(float) * (size_t)c->ibl.cap));
-    CK(dalloc(c, &c->ibl.g, sizeof(double) * (size_t)c->ibl.cap));
-    CK(dalloc(c, &c->ibl.count, sizeof(unsigned int) * 2));
+    CK(dalloc(c, &c->ibl.q, sizeof(float) * nlq));
+    CK(dalloc(c, &c->ibl.g, sizeof(double) * nlq));
+    CK(dalloc(c, &c->ibl.ocell, sizeof(int32_t) * (size_t)c->ibl.ocap));
+    CK(dalloc(c, &c->ibl.count, sizeof(unsigned int) * 4));
   }
-  if (c->ibl.count) CK(cudaMemsetAsync(c->ibl.count, 0, sizeof(unsigned int) * 2, c->stream));
+  if (c->ibl.count) CK(cudaMemsetAsync(c->ibl.count, 0, sizeof(unsigned int) * 4, c->stream));
   rwmi_status s = reset_fluid(c);
   if (s != RWMI_OK) return s;
   s = build_current_frame(c);
@@ -1214,7 +1223,7 @@ RWMI_API rwmi_status rwmi_autotune(rwmi_ctx* c, int32_t* chosen) try {
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if (ibb) CK(cudaMemsetAsync(c->ibl.count, 0, sizeof(unsigned int) * 2, c->stream));   // the step appends anew
+  if (ibb) CK(cudaMemsetAsync(c->ibl.count, 0, sizeof(unsigned int) * 4, c->stream));   // the step appends anew
   CK(cudaGetLastError());
   c->cfg.lbm_block = best;
   drop_graphs(c);
@@ -1267,7 +1276,9 @@ RWMI_API rwmi_status rwmi_sync(rwmi_ctx* c) try {
   unsigned long long st[ST_COUNT];
   CK(copy_now(c, st, c->status, sizeof(st)));
   rwmi_status r = RWMI_OK;
-  if (st[ST_TMA_TIMEOUT] > c->status_seen[ST_TMA_TIMEOUT])
+  if (st[ST_IBB_OVERFLOW] > c->status_seen[ST_IBB_OVERFLOW])
+    r = fail(c, RWMI_E_OOM, "IBB link list and overflow slots full: a step ran with links missing");
+  else if (st[ST_TMA_TIMEOUT] > c->status_seen[ST_TMA_TIMEOUT])
     r = fail(c, RWMI_E_TIMEOUT, "a bounded wait for a TMA copy gave up (the LBM update is incomplete)");
   else if (st[ST_NONFINITE] > c->status_seen[ST_NONFINITE]) r = fail(c, RWMI_E_NONFINITE, "non-finite walker velocity");
   else if (st[ST_BISECT_FAIL] > c->status_seen[ST_BISECT_FAIL] || st[ST_REFILL_FAIL] > c->status_seen[ST_REFILL_FAIL])
@@ -1609,7 +1620,7 @@ RWMI_API rwmi_status rwmi_load(rwmi_ctx* c, const char* path) try {
   CK(copy_now(c, c->d_T, &c->t, sizeof(int64_t)));
   c->t_base = c->t;
   CK(cudaMemsetAsync(c->wlist_n, 0, sizeof(unsigned int) * 2 * WLIST_STRIPES, c->stream));
-  if (c->ibl.count) CK(cudaMemsetAsync(c->ibl.count, 0, sizeof(unsigned int) * 2, c->stream));
+  if (c->ibl.count) CK(cudaMemsetAsync(c->ibl.count, 0, sizeof(unsigned int) * 4, c->stream));
   rwmi_status s = build_current_frame(c);
   if (s != RWMI_OK) return s;
   CK(cudaStreamSynchronize(c->stream));
@@ -2131,6 +2142,8 @@ RWMI_API int64_t rwmi_inject_alloc_failure(int64_t after) {
 
 RWMI_API int64_t rwmi_alloc_count(void) { return g_alloc_count.load(); }
 
+RWMI_API int32_t rwmi_inject_wait_timeout(int32_t launches) { return tma_inject_stalls(launches); }
+
 RWMI_API void rwmi_destroy(rwmi_ctx* c) {
   if (!c) return;
   // At process teardown the CUDA runtime may already be gone: then only host memory is freed.
@@ -2149,7 +2162,7 @@ RWMI_API void rwmi_destroy(rwmi_ctx* c) {
   dfree(c, c->series); dfree(c, c->mrow); dfree(c, c->desc); dfree(c, c->cbody); dfree(c, c->rank);
   dfree(c, c->counts); dfree(c, c->offsets); dfree(c, c->bsums); dfree(c, c->scratch); dfree(c, c->wmask[0]); dfree(c, c->wmask[1]);
   dfree(c, c->dem_d); dfree(c, c->dem_b);
-  dfree(c, c->ibl.base); dfree(c, c->ibl.word); dfree(c, c->ibl.cell); dfree(c, c->ibl.meta); dfree(c, c->ibl.q); dfree(c, c->ibl.g); dfree(c, c->ibl.count);
+  dfree(c, c->ibl.base); dfree(c, c->ibl.word); dfree(c, c->ibl.cell); dfree(c, c->ibl.meta); dfree(c, c->ibl.q); dfree(c, c->ibl.g); dfree(c, c->ibl.ocell); dfree(c, c->ibl.count);
   cudaStreamSynchronize(c->stream);   // the frees have returned the memory when this returns
   for (int k = 0; k < 2 * RWMI_NPHASE; ++k)
     if (c->ev[k]) cudaEventDestroy(c->ev[k]);

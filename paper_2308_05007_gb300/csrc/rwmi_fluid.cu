@@ -772,17 +772,21 @@ __device__ __forceinline__ bool inside_exact(const float4* __restrict__ cw, int 
 // there (binary32, the CPU oracle's operation order), owned by the lowest such particle index.
 // Only cells of flagged bricks can be solid. With refill, a node solid in prev and fluid now gets
 // G^eq(rho0, u_new) with u_new its former particle's rigid velocity (Eq. 27).
+// Brick-major: block 2 b + h takes half h (z rows 4 h .. 4 h + 3) of brick b, so that a warp's
+// cells share their brick and its candidate list.
 template <int Q, int STORE>
-__global__ void node_kernel(Geom g, ParticleSet ps, BrickSet bs, const uint16_t* __restrict__ prev,
-                            uint16_t* __restrict__ cur, void* f_, double rho0_d, int refill) {
+__global__ void __launch_bounds__(256) node_kernel(Geom g, ParticleSet ps, BrickSet bs, const uint16_t* __restrict__ prev,
+                                                   uint16_t* __restrict__ cur, void* f_, double rho0_d, int refill) {
   using L = Lat<Q>;
   using S = Store<STORE>;
   using R = typename S::R;
-  const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= g.ncell) return;
-  const uint32_t z = fast_div(c, g.mxy, g.sxy), rem = c - z * g.nxy;
-  const uint32_t y = fast_div(rem, g.mx, g.sx), x = rem - y * g.n[0];
-  const uint32_t b = ((z >> 3) * (uint32_t)g.nb[1] + (y >> 3)) * (uint32_t)g.nb[0] + (x >> 3);
+  const uint32_t b = blockIdx.x >> 1;
+  const uint32_t l = threadIdx.x + ((blockIdx.x & 1u) << 8);
+  const uint32_t bi = b % (uint32_t)g.nb[0], bj = (b / (uint32_t)g.nb[0]) % (uint32_t)g.nb[1],
+                 bk = b / ((uint32_t)g.nb[0] * (uint32_t)g.nb[1]);
+  const uint32_t x = bi * BRICK + (l & 7u), y = bj * BRICK + ((l >> 3) & 7u), z = bk * BRICK + (l >> 6);
+  if (x >= (uint32_t)g.n[0] || y >= (uint32_t)g.n[1] || z >= (uint32_t)g.n[2]) return;
+  const uint32_t c = (z * (uint32_t)g.n[1] + y) * (uint32_t)g.n[0] + x;
   const uint32_t w = bs.bword[b];
   int node = 0;
   if (w >> 16) {
@@ -819,7 +823,18 @@ __global__ void node_kernel(Geom g, ParticleSet ps, BrickSet bs, const uint16_t*
 void launch_nodes(int q, int storage, const Geom& g, const ParticleSet& ps, BrickSet bs,
                   const uint16_t* prev, uint16_t* cur, void* f, double rho0, bool refill,
                   cudaStream_t st) {
-  RWMI_DISPATCH(q, storage, node_kernel, g, ps, bs, prev, cur, f, rho0, refill ? 1 : 0);
+  const dim3 grid_(2u * (uint32_t)g.nb[0] * (uint32_t)g.nb[1] * (uint32_t)g.nb[2]);   // two blocks per brick
+  if (q == 15) {
+    if (storage == 0) node_kernel<15, 0><<<grid_, 256, 0, st>>>(g, ps, bs, prev, cur, f, rho0, refill ? 1 : 0);
+    else if (storage == 1) node_kernel<15, 1><<<grid_, 256, 0, st>>>(g, ps, bs, prev, cur, f, rho0, refill ? 1 : 0);
+    else if (storage == 2) node_kernel<15, 2><<<grid_, 256, 0, st>>>(g, ps, bs, prev, cur, f, rho0, refill ? 1 : 0);
+    else node_kernel<15, 3><<<grid_, 256, 0, st>>>(g, ps, bs, prev, cur, f, rho0, refill ? 1 : 0);
+  } else {
+    if (storage == 0) node_kernel<19, 0><<<grid_, 256, 0, st>>>(g, ps, bs, prev, cur, f, rho0, refill ? 1 : 0);
+    else if (storage == 1) node_kernel<19, 1><<<grid_, 256, 0, st>>>(g, ps, bs, prev, cur, f, rho0, refill ? 1 : 0);
+    else if (storage == 2) node_kernel<19, 2><<<grid_, 256, 0, st>>>(g, ps, bs, prev, cur, f, rho0, refill ? 1 : 0);
+    else node_kernel<19, 3><<<grid_, 256, 0, st>>>(g, ps, bs, prev, cur, f, rho0, refill ? 1 : 0);
+  }
 }
 
 __global__ void unpack_solid_kernel(Geom g, const uint16_t* solid, const uint32_t* bword,

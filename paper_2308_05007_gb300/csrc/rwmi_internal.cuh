@@ -246,17 +246,20 @@ struct IbbArgs {
   const void* g = nullptr;         // G_i of every link (Eqs. 23-25), in the arithmetic type
   int cap = 0;                     // capacity of the link list
 };
-// The IBB link list of a context: per cell the index of its first link and its node word, per
-// link the cell, the direction | particle << 8, q and G_i (binary32 or binary64, 8 bytes
-// reserved); two append counters (time parities).
+// The IBB link list of a context: per cell the index of its first link (or -1 - its overflow
+// slot) and its node word; per link the cell, the direction | particle << 8, q and G_i (binary32
+// or binary64, 8 bytes reserved). q and G hold cap list entries followed by ocap overflow slots of
+// Q - 1 links each (cells whose links did not fit in the list; ocell lists them). count: list and
+// overflow append counters, two time parities each.
 struct IbbLinks {
   int32_t* base = nullptr;
   uint32_t* word = nullptr;
   uint32_t *cell = nullptr, *meta = nullptr;
   float* q = nullptr;
   void* g = nullptr;
-  unsigned int* count = nullptr;
-  int cap = 0;
+  int32_t* ocell = nullptr;
+  unsigned int* count = nullptr;   // [4]: list (parity 0, 1), overflow (parity 0, 1)
+  int cap = 0, ocap = 0;
 };
 // Links of time t (node classes nodes, bricks bs), their q and G_i from the LBM input
 // populations fin and the previous velocity uprev, before the LBM update of t.
@@ -270,6 +273,7 @@ void launch_ibb_links(int q, int storage, const Geom& g, BrickSet bs, const uint
 bool lbm_tma_supported(int q, int storage, const Geom& g);
 bool lbm_tma_encode(int q, int storage, const Geom& g, const void* f, CUtensorMap* map);
 size_t lbm_tma_smem(int q, int storage);
+int tma_inject_stalls(int n);   // rwmi_inject_wait_timeout; returns the previous count
 void launch_lbm_tma(int q, int storage, const CUtensorMap& map, const Geom& g, const void* fin, void* fout, float* u,
                     const uint16_t* solid, BrickSet bs, double tau, double rho0, unsigned long long* status, int nsm,
                     cudaStream_t st);

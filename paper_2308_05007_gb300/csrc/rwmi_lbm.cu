@@ -3,6 +3,7 @@
 // interpolated bounce-back (Eqs. 23-27); writes the populations, the velocity field and, on
 // reduction steps, per-particle force/torque and the FP64 sums. Also the IBB link list and its
 // q values, computed ahead of the update.
+#include <atomic>
 #include <type_traits>
 
 #include "rwmi_lattice.cuh"
@@ -152,30 +153,34 @@ __device__ __forceinline__ void ibb_link_force(const Geom& g, const PoseF* __res
   Tl[2] = r[0] * Fl[1] - r[1] * Fl[0];
 }
 
-// Momentum exchange of one cell's links, in direction order (Section 2.4.3): q and G of link k
-// from the list (k < cap) or from the cell's shared rows; per-particle sums in Fib/Tib for the
-// cell's first particle, direct atomics for a second particle at one node (rare).
+// Momentum exchange of one cell's links, in direction order (Section 2.4.3): q and G of each link
+// from the link list (k0 >= 0: the cell's links at k0, k0 + 1, ...) or from the overflow table
+// (k0 < 0: slot -1 - k0, link i at cap + slot (Q - 1) + i - 1); per-particle sums in Fib/Tib for
+// the cell's first particle, direct atomics for a second particle at one node (rare).
 template <int Q, int STORE>
 __device__ __forceinline__ void ibb_cell_force(const Geom& g, const typename Store<STORE>::T* __restrict__ in0,
                                                const PoseF* __restrict__ pose, const PoseD* __restrict__ posed,
                                                const uint16_t* __restrict__ nodes, int c, uint32_t x, uint32_t y,
                                                uint32_t z, unsigned lmask, int k0, int cap,
                                                const float* __restrict__ ib_q,
-                                               const typename Store<STORE>::R* __restrict__ ib_g, const float* qrow,
-                                               const typename Store<STORE>::R* grow, typename Store<STORE>::R rho0,
+                                               const typename Store<STORE>::R* __restrict__ ib_g,
+                                               typename Store<STORE>::R rho0,
                                                double* __restrict__ forces, int& owner,
                                                typename Store<STORE>::R (&Fib)[3], typename Store<STORE>::R (&Tib)[3]) {
   using L = Lat<Q>;
   using S = Store<STORE>;
   using R = typename S::R;
-  int k = k0;
+  const bool ovf = k0 < 0;
+  const int kb = ovf ? cap + (-1 - k0) * (Q - 1) : k0;
+  int k = kb;
   for (unsigned m = lmask; m; m &= m - 1u, ++k) {
     const int i = __ffs(m) - 1, ip = L::opp(i);
+    const int kk = ovf ? kb + i - 1 : k;
     int off = 0;
     pull_source<Q, true>(g, x, y, z, i, off);   // a link's source is never beyond a wall
     const int p = (int)nodes[c + off] - 1;
-    const R qf = (R)(k < cap ? ib_q[k] : qrow[(i - 1) * 256]);
-    const R G = k < cap ? ib_g[k] : grow[(i - 1) * 256];
+    const R qf = (R)ib_q[kk];
+    const R G = ib_g[kk];
     const int ex = L::e(ip, 0), ey = L::e(ip, 1), ez = L::e(ip, 2);
     const R xw[3] = {(R)x + R(0.5) + qf * (R)ex, (R)y + R(0.5) + qf * (R)ey, (R)z + R(0.5) + qf * (R)ez};
     R uw[3];
@@ -192,41 +197,6 @@ __device__ __forceinline__ void ibb_cell_force(const Geom& g, const typename Sto
         atomicAdd(&forces[6 * p + 3 + a], (double)Tl[a]);
       }
     }
-  }
-}
-
-// Links of one cell beyond the link list's capacity (never at its usual capacity of half a link
-// per cell): q by the same bisection and G_i into qrow / grow[(i - 1) * 256].
-template <int Q, int STORE, bool WALLS>
-__device__ __forceinline__ void ibb_overflow_links(Geom g, const typename Store<STORE>::T* __restrict__ in0,
-                                                   const float4* __restrict__ uprev,
-                                                   const uint16_t* __restrict__ nodes, const PoseF* __restrict__ pose,
-                                                   const PoseD* __restrict__ posed, const float4* __restrict__ cworld,
-                                                   const ParticleDesc* __restrict__ desc, int c, uint32_t x,
-                                                   uint32_t y, uint32_t z, unsigned lmask, int k0, int cap,
-                                                   typename Store<STORE>::R rho0, float* qrow,
-                                                   typename Store<STORE>::R* grow) {
-  using L = Lat<Q>;
-  using S = Store<STORE>;
-  using R = typename S::R;
-  R sum = R(0);   // rho_f: x_f's own post-collision populations, summed in direction order
-  for (int d = 0; d < Q; ++d) sum += S::ld(in0 + (size_t)d * g.ncell_pad + c);
-  const R rho_f = S::shifted ? rho0 + sum : sum;
-  const float4 u = uprev[c];
-  const R uf[3] = {(R)u.x, (R)u.y, (R)u.z};
-  int k = k0;
-  for (unsigned m = lmask; m; m &= m - 1u, ++k) {
-    if (k < cap) continue;
-    const int i = __ffs(m) - 1, ip = L::opp(i);
-    int off = 0;
-    pull_source<Q, WALLS>(g, x, y, z, i, off);
-    const int p = (int)nodes[c + off] - 1;
-    const float qv = ibb_link_q(cworld, desc[p].c0, desc[p].c1, (float)x + 0.5f, (float)y + 0.5f, (float)z + 0.5f,
-                                L::e(ip, 0), L::e(ip, 1), L::e(ip, 2), g);
-    R Gp, xw[3], uw[3];
-    qrow[(i - 1) * 256] = qv;
-    grow[(i - 1) * 256] = ibb_link_value<Q, STORE, WALLS>(g, in0, uprev, nodes, pose, posed, c, x, y, z, i, p,
-                                                          (R)qv, rho_f, uf, Gp, xw, uw);
   }
 }
 
@@ -329,10 +299,9 @@ __device__ __forceinline__ void lbm_body(Geom g, Planes<Q, typename Store<STORE>
   int ib_owner = -1;
   if constexpr (IBB) {
     // ibb_links_kernel, which ran before, left every cell of a flagged brick its node word: bit 0
-    // a solid node, bit i a link (x - e_i a solid node, not beyond a wall). The cell's links sit
-    // at ib_base[c] in direction order, and ibb_link_kernel left G_i of each in ib_g (with the
-    // momentum exchange on the steps that read forces). Cells of other bricks have no solid
-    // neighbour (the IBB brick radius is at least rb + sqrt 3).
+    // a solid node, bit i a link (x - e_i a solid node, not beyond a wall), and ibb_link_kernel
+    // left q and G_i of every link. Cells of other bricks have no solid neighbour (the IBB brick
+    // radius is at least rb + sqrt 3).
     unsigned lmask = 0u;
     const uint32_t bq = ((z >> 3) * (uint32_t)g.nb[1] + (y >> 3)) * (uint32_t)g.nb[0] + (x >> 3);
     if (valid && (bword[bq] >> 16)) {
@@ -340,35 +309,21 @@ __device__ __forceinline__ void lbm_body(Geom g, Planes<Q, typename Store<STORE>
       solid_self = (lw & 1u) != 0u;
       lmask = lw & ~1u;
     }
-    int k0 = 0;
-    bool over = false;   // links beyond the list's capacity (counted in the status): computed here
+    // the cell's links: in the list at ib_base[c] in direction order, or, for a cell whose links
+    // did not fit in the list, in its overflow slot -1 - ib_base[c] by direction
     if (lmask) {
-      k0 = ib_base[c];
-      over = k0 + __popc(lmask) > ib_cap;
-    }
-    if (__any_sync(0xffffffffu, over)) {   // never at the list's usual capacity
-      __shared__ R s_link[Q - 1][256];
-      __shared__ float s_q[Q - 1][256];
-      if (over)
-        ibb_overflow_links<Q, STORE, WALLS>(g, pl.in[0], uprev, nodes, pose, posed, cworld, desc, c, x, y, z, lmask,
-                                            k0, ib_cap, rho0, &s_q[0][threadIdx.x], &s_link[0][threadIdx.x]);
-      int k = k0;
+      const int k0 = ib_base[c];
+      const bool ovf = k0 < 0;
+      const int kb = ovf ? ib_cap + (-1 - k0) * (Q - 1) : k0;
+      int k = kb;
 #pragma unroll
       for (int i = 1; i < Q; ++i)
         if ((lmask >> i) & 1u) {
-          f[i] = k < ib_cap ? ib_g[k] : s_link[i - 1][threadIdx.x];
+          f[i] = ib_g[ovf ? kb + i - 1 : k];
           ++k;
         }
-      if (REDUCE && lmask) ibb_cell_force<Q, STORE>(g, pl.in[0], pose, posed, nodes, c, x, y, z, lmask, k0, ib_cap,
-                                                    ib_q, ib_g, &s_q[0][threadIdx.x], &s_link[0][threadIdx.x], rho0,
-                                                    forces, ib_owner, Fib, Tib);
-    } else {
-      int k = k0;
-#pragma unroll
-      for (int i = 1; i < Q; ++i)
-        if ((lmask >> i) & 1u) f[i] = ib_g[k++];
-      if (REDUCE && lmask) ibb_cell_force<Q, STORE>(g, pl.in[0], pose, posed, nodes, c, x, y, z, lmask, k0, ib_cap,
-                                                    ib_q, ib_g, nullptr, nullptr, rho0, forces, ib_owner, Fib, Tib);
+      if (REDUCE) ibb_cell_force<Q, STORE>(g, pl.in[0], pose, posed, nodes, c, x, y, z, lmask, k0, ib_cap, ib_q, ib_g,
+                                           rho0, forces, ib_owner, Fib, Tib);
     }
   }
   // moments (Eqs. 14-15); with shifted storage f holds f_i - w_i rho0
@@ -591,7 +546,7 @@ template <int Q, int STORE> struct LbmArgs {
   double* forces;
 };
 
-#define RWMI_LBM_BOUNDS __launch_bounds__(256, sizeof(typename Store<STORE>::R) == 8 ? 2 : IBB ? 4 : (Q == 19 ? 5 : 6))
+#define RWMI_LBM_BOUNDS __launch_bounds__(256, sizeof(typename Store<STORE>::R) == 8 ? 2 : IBB ? (MODE == 0 ? 6 : 4) : (Q == 19 ? 5 : 6))
 
 template <int Q, int STORE, bool WALLS, int MODE, bool IBB>
 __global__ void RWMI_LBM_BOUNDS
@@ -632,15 +587,20 @@ __global__ void __launch_bounds__(256) ibb_links_kernel(Geom g, const uint32_t* 
                                                         int32_t* __restrict__ base, uint32_t* __restrict__ word,
                                                         uint32_t* __restrict__ lcell,
                                                         uint32_t* __restrict__ lmeta, unsigned int* count, int cap,
+                                                        int32_t* __restrict__ ocell, unsigned int* ocount, int ocap,
                                                         unsigned long long* __restrict__ status) {
   using L = Lat<Q>;
-  const uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x;
-  const bool valid = idx < g.ncell;
-  const int c = (int)(valid ? idx : g.ncell - 1);
-  const uint32_t z = fast_div((uint32_t)c, g.mxy, g.sxy);
-  const uint32_t rem = (uint32_t)c - z * g.nxy;
-  const uint32_t y = fast_div(rem, g.mx, g.sx);
-  const uint32_t x = rem - y * g.n[0];
+  // brick-major (as node_kernel): block 2 b + h takes half h of brick b; bricks that hold no
+  // particle have no links and leave at once
+  const uint32_t bq = blockIdx.x >> 1;
+  if (!(bword[bq] >> 16)) return;   // block-uniform
+  const uint32_t l = threadIdx.x + ((blockIdx.x & 1u) << 8);
+  const uint32_t bi = bq % (uint32_t)g.nb[0], bj = (bq / (uint32_t)g.nb[0]) % (uint32_t)g.nb[1],
+                 bk = bq / ((uint32_t)g.nb[0] * (uint32_t)g.nb[1]);
+  uint32_t x = bi * BRICK + (l & 7u), y = bj * BRICK + ((l >> 3) & 7u), z = bk * BRICK + (l >> 6);
+  const bool valid = x < (uint32_t)g.n[0] && y < (uint32_t)g.n[1] && z < (uint32_t)g.n[2];
+  if (!valid) { x = 0; y = 0; z = 0; }   // outside the box (partial brick): no links
+  const int c = (int)((z * (uint32_t)g.n[1] + y) * (uint32_t)g.n[0] + x);
   const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
   const int sy = nx, sz = (int)g.nxy;
   const int ox_p = x == 0 ? nx - 1 : -1, ox_m = (int)x == nx - 1 ? -(nx - 1) : 1;
@@ -660,8 +620,7 @@ __global__ void __launch_bounds__(256) ibb_links_kernel(Geom g, const uint32_t* 
            (ez > 0 && wz_p) || (ez < 0 && wz_m);
   };
   unsigned lmask = 0u;
-  const uint32_t bq = ((z >> 3) * (uint32_t)g.nb[1] + (y >> 3)) * (uint32_t)g.nb[0] + (x >> 3);
-  if (valid && (bword[bq] >> 16)) {
+  if (valid) {
     const bool solid_node = nodes[c] != 0;
     if (!solid_node) {
 #pragma unroll
@@ -685,16 +644,26 @@ __global__ void __launch_bounds__(256) ibb_links_kernel(Geom g, const uint32_t* 
   if (lane == 31) first = atomicAdd(count, (unsigned)total);
   first = __shfl_sync(full, first, 31) + (unsigned)(incl - nl);
   if (!nl) return;
+  if (first + (unsigned)nl > (unsigned)cap) {   // the list is full: the cell takes an overflow slot
+    for (unsigned k = first; k < (unsigned)cap && k < first + (unsigned)nl; ++k)
+      lcell[k] = 0xffffffffu;   // its reserved list entries stay empty (ibb_link_kernel skips them)
+    const unsigned slot = atomicAdd(ocount, 1u);
+    if (slot < (unsigned)ocap) {
+      ocell[slot] = c;
+      base[c] = -1 - (int32_t)slot;
+    } else {   // both full: this step's result is incomplete (rwmi_sync reports it)
+      atomicAdd(&status[ST_IBB_OVERFLOW], 1ull);
+      word[c] = 0u;   // the cell keeps its pulled populations
+    }
+    return;
+  }
   base[c] = (int32_t)first;
   unsigned k = first;
   for (unsigned m = lmask; m; m &= m - 1u, ++k) {
     const int i = __ffs(m) - 1;
-    if (k < (unsigned)cap) {
-      lcell[k] = (uint32_t)c;
-      lmeta[k] = (uint32_t)i | ((uint32_t)(nodes[c + off_of(i)] - 1) << 8);
-    }
+    lcell[k] = (uint32_t)c;
+    lmeta[k] = (uint32_t)i | ((uint32_t)(nodes[c + off_of(i)] - 1) << 8);
   }
-  if (first + (unsigned)nl > (unsigned)cap) atomicAdd(&status[ST_IBB_OVERFLOW], 1ull);
 }
 
 // One thread per listed link: q by the binary32 bisection (Eq. 25), then G_i (Eqs. 23-24) from
@@ -712,13 +681,19 @@ __global__ void __launch_bounds__(256) ibb_link_kernel(Geom g, const float4* __r
                                                        const float4* __restrict__ uprev,
                                                        const uint16_t* __restrict__ nodes,
                                                        const PoseF* __restrict__ pose, const PoseD* __restrict__ posed,
-                                                       typename Store<STORE>::R rho0) {
+                                                       typename Store<STORE>::R rho0, const uint32_t* __restrict__ word,
+                                                       const int32_t* __restrict__ ocell, const unsigned int* ocount,
+                                                       unsigned int* ocount_next, int ocap) {
   using L = Lat<Q>;
   using S = Store<STORE>;
   using R = typename S::R;
-  if (blockIdx.x == 0 && threadIdx.x == 0) *count_next = 0u;   // the next step appends there
+  if (blockIdx.x == 0 && threadIdx.x == 0) {   // the next step appends there
+    *count_next = 0u;
+    *ocount_next = 0u;
+  }
   const unsigned n = min(*count, (unsigned)cap);
   for (unsigned j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    if (lcell[j] == 0xffffffffu) continue;   // reserved by a cell that went to the overflow slots
     const int c = (int)lcell[j];
     const uint32_t meta = lmeta[j];
     const uint32_t z = fast_div((uint32_t)c, g.mxy, g.sxy), r = (uint32_t)c - z * g.nxy;
@@ -737,25 +712,54 @@ __global__ void __launch_bounds__(256) ibb_link_kernel(Geom g, const float4* __r
     gout[j] = ibb_link_value<Q, STORE, WALLS>(g, in0, uprev, nodes, pose, posed, c, x, y, z, i, p, (R)qv, rho_f, uf,
                                               Gp, xw, uw);
   }
+  // cells whose links did not fit in the list: all their links, by direction, in their slot of
+  // the overflow table (cap + slot (Q - 1) + i - 1)
+  const unsigned no = min(*ocount, (unsigned)ocap);
+  for (unsigned s = blockIdx.x * blockDim.x + threadIdx.x; s < no; s += gridDim.x * blockDim.x) {
+    const int c = ocell[s];
+    const uint32_t z = fast_div((uint32_t)c, g.mxy, g.sxy), r = (uint32_t)c - z * g.nxy;
+    const uint32_t y = fast_div(r, g.mx, g.sx), x = r - y * g.n[0];
+    R sum = R(0);
+    for (int d = 0; d < Q; ++d) sum += S::ld(in0 + (size_t)d * g.ncell_pad + c);
+    const R rho_f = S::shifted ? rho0 + sum : sum;
+    const float4 u = uprev[c];
+    const R uf[3] = {(R)u.x, (R)u.y, (R)u.z};
+    for (unsigned m = word[c] & ~1u; m; m &= m - 1u) {
+      const int i = __ffs(m) - 1, ip = L::opp(i);
+      int off = 0;
+      pull_source<Q, WALLS>(g, x, y, z, i, off);
+      const int p = (int)nodes[c + off] - 1;
+      const float qv = ibb_link_q(cworld, desc[p].c0, desc[p].c1, (float)x + 0.5f, (float)y + 0.5f, (float)z + 0.5f,
+                                  L::e(ip, 0), L::e(ip, 1), L::e(ip, 2), g);
+      const size_t kk = (size_t)cap + (size_t)s * (Q - 1) + (size_t)(i - 1);
+      qout[kk] = qv;
+      R Gp, xw[3], uw[3];
+      gout[kk] = ibb_link_value<Q, STORE, WALLS>(g, in0, uprev, nodes, pose, posed, c, x, y, z, i, p, (R)qv, rho_f,
+                                                 uf, Gp, xw, uw);
+    }
+  }
 }
 
 void launch_ibb_links(int q, int storage, const Geom& g, BrickSet bs, const uint16_t* nodes, const IbbLinks& lk,
                       int par, const ParticleDesc* desc, const void* fin, const float* uprev, double rho0,
                       unsigned long long* status, int nsm, cudaStream_t st) {
   const bool walls = g.wall[0] || g.wall[1] || g.wall[2];
-  const unsigned blocks = (unsigned)((g.ncell + 255) / 256);
+  const unsigned blocks = 2u * (unsigned)g.nb[0] * (unsigned)g.nb[1] * (unsigned)g.nb[2];   // two per brick
   unsigned int* cnt = lk.count + (par & 1);
   unsigned int* nxt = lk.count + ((par + 1) & 1);
+  unsigned int* ocnt = lk.count + 2 + (par & 1);
+  unsigned int* onxt = lk.count + 2 + ((par + 1) & 1);
   const float4* u4 = reinterpret_cast<const float4*>(uprev);
 #define RWMI_IBB_LINKS(QQ, SS, WW)                                                                                   \
   do {                                                                                                             \
     using T_ = typename Store<SS>::T;                                                                              \
     using R_ = typename Store<SS>::R;                                                                              \
     ibb_links_kernel<QQ, WW><<<blocks, 256, 0, st>>>(g, bs.bword, nodes, lk.base, lk.word, lk.cell, lk.meta, cnt,   \
-                                                      lk.cap, status);                                             \
+                                                      lk.cap, lk.ocell, ocnt, lk.ocap, status);                    \
     ibb_link_kernel<QQ, SS, WW><<<nsm * 8, 256, 0, st>>>(g, bs.cworld, desc, lk.cell, lk.meta, cnt, nxt, lk.cap,   \
                                                          lk.q, static_cast<R_*>(lk.g), static_cast<const T_*>(fin),\
-                                                         u4, nodes, bs.pose, bs.posed, (R_)rho0);                  \
+                                                         u4, nodes, bs.pose, bs.posed, (R_)rho0, lk.word,          \
+                                                         lk.ocell, ocnt, onxt, lk.ocap);                           \
   } while (0)
 #define RWMI_IBB_W(QQ, SS) \
   if (walls) RWMI_IBB_LINKS(QQ, SS, true); else RWMI_IBB_LINKS(QQ, SS, false)
@@ -851,21 +855,22 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
                : "=r"(ok) : "r"(smem_addr(bar)), "r"(parity) : "memory");
   return ok != 0u;
 }
-// Waits for the phase of parity `parity` to complete; false when TMA_WAIT_CYCLES pass first.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+// Waits for the phase of parity `parity` to complete; false when `limit` cycles pass first.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, long long limit) {
   if (mbar_try_wait(bar, parity)) return true;
   const long long t0 = clock64();
   for (;;) {
     if (mbar_try_wait(bar, parity)) return true;
-    if (clock64() - t0 > TMA_WAIT_CYCLES) return false;
+    if (clock64() - t0 > limit) return false;
   }
 }
 
 template <int Q, int STORE, bool WALLS>
 __device__ __forceinline__ void tma_issue_tile(const CUtensorMap* map, typename Store<STORE>::T* stage, uint64_t* bar,
-                                               const Geom& g, int tpr, int t) {
+                                               const Geom& g, int tpr, int t, int stall_tile) {
   using L = Lat<Q>;
   using TR = TmaRow<STORE>;
+  if (t == stall_tile) return;   // injected (rwmi_inject_wait_timeout): this tile's barrier never completes
   const int row = t / tpr, x0 = (t - row * tpr) * TMA_BX;
   const int ny = g.n[1], nz = g.n[2];
   const int y = row % ny, z = row / ny;
@@ -894,7 +899,8 @@ lbm_tma_kernel(const __grid_constant__ CUtensorMap tin, Geom g, Planes<Q, typena
                float4* __restrict__ u4, const uint16_t* __restrict__ solid, const uint32_t* __restrict__ bword,
                const PoseF* __restrict__ pose, const PoseD* __restrict__ posed, const StepParams* __restrict__ sp,
                typename Store<STORE>::R tau, typename Store<STORE>::R omega, typename Store<STORE>::R guo0,
-               typename Store<STORE>::R rho0, int tpr, unsigned long long* __restrict__ status) {
+               typename Store<STORE>::R rho0, int tpr, unsigned long long* __restrict__ status, int stall_tile,
+               long long wait_cycles) {
   using L = Lat<Q>;
   using S = Store<STORE>;
   using T = typename S::T;
@@ -916,7 +922,7 @@ lbm_tma_kernel(const __grid_constant__ CUtensorMap tin, Geom g, Planes<Q, typena
   if (tid == 0)
     for (int s = 0; s < TMA_STAGES; ++s) {
       const int t = blockIdx.x + s * gridDim.x;
-      if (t < ntiles) tma_issue_tile<Q, STORE, WALLS>(&tin, stages + s * stage_elems, &bar[s], g, tpr, t);
+      if (t < ntiles) tma_issue_tile<Q, STORE, WALLS>(&tin, stages + s * stage_elems, &bar[s], g, tpr, t, stall_tile);
     }
   const bool xper = !(WALLS && g.wall[0]);
   int k = 0;
@@ -925,7 +931,7 @@ lbm_tma_kernel(const __grid_constant__ CUtensorMap tin, Geom g, Planes<Q, typena
     const int s = k % TMA_STAGES;
     const uint32_t parity = (uint32_t)(k / TMA_STAGES) & 1u;
     T* stage = stages + s * stage_elems;
-    const bool ok = mbar_wait_bounded(&bar[s], parity);
+    const bool ok = mbar_wait_bounded(&bar[s], parity, wait_cycles);
     if (__syncthreads_or(!ok)) { expired = true; break; }
     const int row = t / tpr, x0 = (t - row * tpr) * TMA_BX;
     const bool left = x0 == 0, right = x0 + TMA_BX >= nx;
@@ -956,7 +962,7 @@ lbm_tma_kernel(const __grid_constant__ CUtensorMap tin, Geom g, Planes<Q, typena
       const int tn = t + TMA_STAGES * gridDim.x;
       if (tn < ntiles) {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // the halo patch before new copies
-        tma_issue_tile<Q, STORE, WALLS>(&tin, stage, &bar[s], g, tpr, tn);
+        tma_issue_tile<Q, STORE, WALLS>(&tin, stage, &bar[s], g, tpr, tn, stall_tile);
       }
     }
   }
@@ -965,11 +971,22 @@ lbm_tma_kernel(const __grid_constant__ CUtensorMap tin, Geom g, Planes<Q, typena
       atomicAdd(&status[ST_TMA_TIMEOUT], 1ull);
       for (int j = 0; j < TMA_STAGES; ++j) {
         const int kk = k + j, tt = blockIdx.x + kk * gridDim.x;
-        if (tt < ntiles) mbar_wait_bounded(&bar[kk % TMA_STAGES], (uint32_t)(kk / TMA_STAGES) & 1u);
+        if (tt < ntiles && tt != stall_tile)
+          mbar_wait_bounded(&bar[kk % TMA_STAGES], (uint32_t)(kk / TMA_STAGES) & 1u, wait_cycles);
       }
     }
     __syncthreads();
   }
+}
+
+// Injected stalls (rwmi_inject_wait_timeout): the next n staged launches leave the copies of
+// their first tile unissued and wait for them about a millisecond.
+static std::atomic<int> g_tma_stalls{0};
+int tma_inject_stalls(int n) { return g_tma_stalls.exchange(n < 0 ? 0 : n); }
+static bool tma_take_stall() {
+  int n = g_tma_stalls.load();
+  while (n > 0 && !g_tma_stalls.compare_exchange_weak(n, n - 1)) {}
+  return n > 0;
 }
 
 size_t lbm_tma_smem(int q, int storage) {
@@ -1035,8 +1052,10 @@ static void launch_lbm_tma_q(bool walls, const CUtensorMap& map, const Geom& g, 
   if (per_sm == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TMA_BX, smem);
   const int64_t ntiles = (int64_t)g.n[1] * g.n[2] * tpr;
   const int grid = (int)std::min<int64_t>(ntiles, (int64_t)nsm * std::max(per_sm, 1));
+  const bool stall = tma_take_stall();
   kern<<<grid, TMA_BX, smem, st>>>(map, g, pl, reinterpret_cast<float4*>(u), solid, bs.bword, bs.pose, bs.posed, bs.sp,
-                                   (R)tau, (R)(1.0 / tau), (R)(1.0 - 0.5 / tau), (R)rho0, tpr, status);
+                                   (R)tau, (R)(1.0 / tau), (R)(1.0 - 0.5 / tau), (R)rho0, tpr, status,
+                                   stall ? 0 : -1, stall ? 2000000LL : TMA_WAIT_CYCLES);
 }
 
 void launch_lbm_tma(int q, int storage, const CUtensorMap& map, const Geom& g, const void* fin, void* fout, float* u,

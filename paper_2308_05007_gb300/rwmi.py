@@ -30,7 +30,8 @@ EXPORTED = ["rwmi_config_defaults", "rwmi_create", "rwmi_configure", "rwmi_set_s
             "rwmi_launch_count", "rwmi_destroy", "rwmi_batch_create", "rwmi_batch_step", "rwmi_batch_sync",
             "rwmi_batch_last_error", "rwmi_batch_destroy", "rwmi_dem_defaults", "rwmi_set_dem",
             "rwmi_particle_state", "rwmi_set_particle_state", "rwmi_particle_mass",
-            "rwmi_inject_alloc_failure", "rwmi_alloc_count", "rwmi_batch_set_mode", "rwmi_batch_get_tiles",
+            "rwmi_inject_alloc_failure", "rwmi_alloc_count", "rwmi_inject_wait_timeout", "rwmi_batch_set_mode",
+            "rwmi_batch_get_tiles",
             "rwmi_batch_set_tiles", "rwmi_batch_autotune", "rwmi_batch_launch_count"]
 BATCH_AUTO, BATCH_BRANCHES, BATCH_FUSED = 0, 1, 2
 
@@ -149,6 +150,8 @@ def load(build_if_missing: bool = False):
     L.rwmi_inject_alloc_failure.restype = C.c_int64
     L.rwmi_alloc_count.argtypes = []
     L.rwmi_alloc_count.restype = C.c_int64
+    L.rwmi_inject_wait_timeout.argtypes = [C.c_int32]
+    L.rwmi_inject_wait_timeout.restype = C.c_int32
     L.rwmi_batch_set_mode.argtypes = [P, C.c_int32]
     L.rwmi_batch_get_tiles.argtypes = [P, C.POINTER(BatchTiles)]
     L.rwmi_batch_set_tiles.argtypes = [P, C.POINTER(BatchTiles)]
@@ -159,7 +162,8 @@ def load(build_if_missing: bool = False):
         fn = getattr(L, name)
         if name not in ("rwmi_config_defaults", "rwmi_last_error", "rwmi_launch_count", "rwmi_destroy",
                         "rwmi_batch_last_error", "rwmi_batch_destroy", "rwmi_dem_defaults",
-                        "rwmi_inject_alloc_failure", "rwmi_alloc_count", "rwmi_batch_launch_count"):
+                        "rwmi_inject_alloc_failure", "rwmi_alloc_count", "rwmi_batch_launch_count",
+                        "rwmi_inject_wait_timeout"):
             fn.restype = C.c_int
     _lib = L
     return L
@@ -191,6 +195,12 @@ def inject_alloc_failure(after: int) -> int:
     """rwmi_inject_alloc_failure: the device allocation `after` allocations from now reports
     RWMI_E_OOM without reaching the allocator (after < 0 disarms). Returns the count so far."""
     return int(load().rwmi_inject_alloc_failure(int(after)))
+
+
+def inject_wait_timeout(launches: int) -> int:
+    """rwmi_inject_wait_timeout: the next `launches` TMA-staged LBM updates let one bounded wait
+    expire (rwmi_sync then reports RWMI_E_TIMEOUT); <= 0 disarms. Returns the previous count."""
+    return int(load().rwmi_inject_wait_timeout(int(launches)))
 
 
 def alloc_count() -> int:

@@ -99,6 +99,33 @@ def test_ibb_schedules_and_graphs_agree():
                 np.testing.assert_allclose(ref[3], st[3], rtol=1e-12, atol=1e-12 * np.abs(ref[3]).max())
 
 
+@pytest.mark.parametrize("storage,q", [(1, 15), (3, 19)])
+def test_ibb_links_beyond_the_list_capacity_give_the_same_step(storage, q, monkeypatch):
+    """A link list of 64 entries (RWMI_IBB_LINK_CAP) sends almost every link cell to the overflow
+    slots: populations, velocities and walkers stay bit-identical to the full-size list, forces
+    agree to the order of their FP64 atomics, and rwmi_sync reports no error."""
+    _need_gpu()
+    from paper_2308_05007_gb300.rwmi import Simulation
+    w = _ibb_workload(storage=storage, q=q, seed=13)
+    states = []
+    for cap in (None, "64"):
+        if cap is None:
+            monkeypatch.delenv("RWMI_IBB_LINK_CAP", raising=False)
+        else:
+            monkeypatch.setenv("RWMI_IBB_LINK_CAP", cap)
+        with Simulation.from_workload(w, seed_walkers=True) as s:
+            s.step(17)
+            pos, _ = s.walkers_by_id()
+            states.append((s.populations(), s.velocity(), pos, s.particle_forces()))
+            assert s.sync() == 0
+    monkeypatch.delenv("RWMI_IBB_LINK_CAP", raising=False)
+    for a, b in zip(states[0][:3], states[1][:3]):
+        assert np.array_equal(a, b)
+    F0, F1 = states[0][3], states[1][3]
+    assert np.abs(F0).max() > 0
+    np.testing.assert_allclose(F1, F0, rtol=1e-12, atol=1e-12 * np.abs(F0).max())
+
+
 def test_ibb_rejects_other_storages():
     _need_gpu()
     from paper_2308_05007_gb300.rwmi import RwmiError, Simulation

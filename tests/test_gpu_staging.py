@@ -82,3 +82,26 @@ def test_staged_one_step_against_the_oracle(q, walls, dims):
     assert np.abs(f_next - fo).max() <= 1e-6 * np.abs(fo).max()
     assert np.abs(u_g - uo).max() <= 1e-6 * max(np.abs(uo).max(), 1e-2)
     sim.close()
+
+
+def test_a_tma_wait_that_expires_is_reported_and_the_context_stays_usable():
+    """rwmi_inject_wait_timeout leaves one tile's copies unissued (its mbarrier never completes,
+    nothing faults): the owning block gives up after its short bound, rwmi_sync reports
+    RWMI_E_TIMEOUT, and the next steps run normally."""
+    import time
+    from paper_2308_05007_gb300 import rwmi
+    w = I.ragged(dims=(256, 24, 20), q=15, storage=1, walls=4, seed=31, n_walkers=1000)
+    sim = rwmi.Simulation.from_workload(w, seed_walkers=True, lbm_staging=1, use_graphs=False)
+    sim.step(2)
+    assert sim.sync() == 0
+    assert rwmi.inject_wait_timeout(1) == 0
+    t0 = time.perf_counter()
+    sim.step(1)
+    with pytest.raises(rwmi.RwmiError) as e:
+        sim.sync()
+    assert e.value.status == -5, str(e.value)
+    assert time.perf_counter() - t0 < 5.0
+    assert rwmi.inject_wait_timeout(0) == 0   # the one injected launch was taken
+    sim.step(3)
+    assert sim.sync() == 0
+    sim.close()
