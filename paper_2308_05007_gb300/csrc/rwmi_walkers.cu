@@ -515,7 +515,7 @@ __global__ void __launch_bounds__(256, 5) walker_batched(const WalkerArgs* __res
   walker_body(a.c, a.pos, a.n, a.u, a.d_T, a.toff, a.amp, a.k0, a.k1, a.status, a.list, a.list_n, a.cap,
               m.block, m.blocks);
 }
-__global__ void __launch_bounds__(256, 4) walker_resolve_kernel(const WalkerArgs a) {
+__global__ void __launch_bounds__(256, 8) walker_resolve_kernel(const WalkerArgs a) {
   resolve_body(a.c, a.pos, a.list, a.list_n, a.list_n_next, a.d_T, a.toff, a.amp, a.k0, a.k1, a.status, a.cap,
                blockIdx.x, gridDim.x);
 }
@@ -546,7 +546,9 @@ int walker_grid(int64_t n, int nsm) {
   const int64_t blocks = (n + 255) / 256;
   return (int)(blocks < (int64_t)nsm * WALKER_BLOCKS_PER_SM ? blocks : (int64_t)nsm * WALKER_BLOCKS_PER_SM);
 }
-int resolve_grid(int nsm) { return nsm * 8; }
+// the resolve pass is latency-bound: 8 resident blocks per SM (32 registers; the rare particle
+// path spills) and two waves of them measured best (step 0.744 against 0.754 ms at 4 per SM)
+int resolve_grid(int nsm) { return nsm * 16; }
 
 void launch_walkers(const Geom& g, const ParticleSet& ps, BrickSet bs1, float4* pos, int64_t n,
                     const float* u, const int64_t* d_T, int toff, int toff_parity, float D,
