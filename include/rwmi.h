@@ -98,8 +98,10 @@ typedef struct {
     int32_t moment_interval;   /* append FP64 walker moments to the series every this many
                                   steps (0: never). Default 0. */
     int32_t use_graphs;        /* replay captured CUDA graphs for repeated steps. Default 1. */
-    int32_t lbm_block;         /* threads per block of the LBM kernel: 64, 128 or 256 (0: 256);
-                                  rwmi_autotune picks it by timing. */
+    int32_t lbm_block;         /* threads per block of the LBM kernel: 64, 128 or 256 (0: 256).
+                                  Default 128 (in the overlapped step the smaller blocks share
+                                  the SMs with the raster better); rwmi_autotune picks it by
+                                  timing the update alone. */
     int32_t overlap;           /* step schedule, same results bit for bit in every case:
                                   0: one stream, phases one after the other;
                                   1: the raster of t+1 on a second stream while the LBM of t runs
@@ -372,7 +374,7 @@ RWMI_API rwmi_status rwmi_batch_set_mode(rwmi_batch* batch, int32_t mode);
 /* Work split of the fused launches (the "tiles"): threads per LBM block (64, 128, 256; one cell
  * per thread), 256-walker chunks per walker block (1..64), walkers per block of the particle-
  * resolution pass (>= 256; at most the single-context grid), bricks per raster block (>= 1).
- * Defaults {256, 1, 8192, 64}. Setting them drops the captured graphs (re-captured at the next
+ * Defaults {128, 1, 8192, 64}. Setting them drops the captured graphs (re-captured at the next
  * step). Results do not depend on them. */
 typedef struct {
   int32_t lbm_block;

@@ -157,7 +157,7 @@ struct rwmi_batch {
   // mapped to (context, block of that context's grid) through device block maps
   int mode = RWMI_BATCH_AUTO;
   bool fused = false;
-  rwmi_batch_tiles tiles{256, 1, 8192, 64};
+  rwmi_batch_tiles tiles{128, 1, 8192, 64};
   cudaStream_t side = nullptr;           // raster of t+1 beside the LBM of t
   cudaStream_t wst = nullptr;            // walkers of t beside the fluid of t+1
   cudaEvent_t fork2 = nullptr, join2 = nullptr, fluid_ev = nullptr, walk_ev[2] = {nullptr, nullptr};
@@ -661,7 +661,7 @@ RWMI_API void rwmi_config_defaults(rwmi_config* cfg) {
   cfg->sort_interval = 16;
   cfg->moment_interval = 0;
   cfg->use_graphs = 1;
-  cfg->lbm_block = 256;
+  cfg->lbm_block = 128;
   cfg->overlap = 2;
   cfg->lbm_staging = 0;
 }

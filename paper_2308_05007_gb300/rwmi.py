@@ -258,7 +258,7 @@ class Simulation:
 
     def __init__(self, dims, tau, D, seed=0, q=19, storage=STORE_FP32_SHIFT, wall_mask=0,
                  body_force=(0.0, 0.0, 0.0), force_period=0.0, rho0=1.0, init_velocity=(0.0, 0.0, 0.0),
-                 sort_interval=16, moment_interval=0, use_graphs=True, stream=None, lbm_block=256,
+                 sort_interval=16, moment_interval=0, use_graphs=True, stream=None, lbm_block=128,
                  overlap=2, coupling=0, lbm_staging=0):
         L = load()
         self._L = L
