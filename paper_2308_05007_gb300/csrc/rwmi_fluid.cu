@@ -64,7 +64,7 @@ __device__ void pose_bin_body(const PoseArgs& A, int blk, int nblk) {
   }
   const int p = blk;
   if (p >= ps.P) return;
-  __shared__ double sR[9], so[3];
+  __shared__ double sR[9], so[3], s_ow[3];   // rotation, origin, wrapped origin
   const ParticleDesc d = ps.desc[p];
   // Explicitly rounded FP64 operations in the oracle's order: the binary32 control points must
   // round identically on both sides, so no fused multiply-add here.
@@ -125,6 +125,7 @@ __device__ void pose_bin_body(const PoseArgs& A, int blk, int nblk) {
       pd.o[a] = wrap_d(org[a], (double)g.n[a], g.wall[a]);
       pd.v[a] = vel[a];
       pd.w[a] = spin[a];
+      s_ow[a] = pd.o[a];
     }
     pd.pad = 0.0;
     bs.posed[p] = pd;
@@ -144,9 +145,10 @@ __device__ void pose_bin_body(const PoseArgs& A, int blk, int nblk) {
     cw.x = (float)w3[0]; cw.y = (float)w3[1]; cw.z = (float)w3[2]; cw.w = cb.w;
     bs.cworld[i] = cw;
   }
-  // bricks within rb + walk_margin of the origin; raster-relevant within rb + 1
-  double ow[3];
-  for (int a = 0; a < 3; ++a) ow[a] = wrap_d(so[a], (double)g.n[a], g.wall[a]);
+  // bricks within rb + walk_margin of the origin; raster-relevant within rb + 1. The wrapped
+  // origin comes from thread 0 (an FP64 division per axis in every thread saturated the narrow
+  // FP64 pipe).
+  const double ow[3] = {s_ow[0], s_ow[1], s_ow[2]};
   // walker candidates and raster candidates coincide: the raster also writes the walkers'
   // mini-brick masks, which must cover every particle within the walker margin
   const float Rw = d.rb + ps.walk_margin, Rr = Rw;
@@ -199,15 +201,25 @@ __device__ void pose_bin_body(const PoseArgs& A, int blk, int nblk) {
       const float da = fmaxf(fabsf(delta) - h, 0.0f);
       d2 += da * da;
     }
-    if (d2 > Rw * Rw) continue;
-    const bool rr = d2 <= Rr * Rr;
-    const uint32_t b = ((uint32_t)bc[2] * g.nb[1] + bc[1]) * g.nb[0] + bc[0];
-    const uint32_t old = atomicAdd(&bs.bword[b], 1u + (rr ? 65536u : 0u));
-    const uint32_t slot = old & 0xffffu;
-    if (slot < MAXC) bs.bcand[b * MAXC + slot] = (uint16_t)(p | (rr ? 0x8000 : 0));
-    if (rr && (old >> 16) == 0u) {
-      const uint32_t li = atomicAdd(&bs.bword[nbrick], 1u);
-      bs.rlist[li] = (int32_t)b;
+    bool app = false;   // this particle is the brick's first raster candidate: list the brick
+    uint32_t b = 0;
+    if (d2 <= Rw * Rw) {
+      const bool rr = d2 <= Rr * Rr;
+      b = ((uint32_t)bc[2] * g.nb[1] + bc[1]) * g.nb[0] + bc[0];
+      const uint32_t old = atomicAdd(&bs.bword[b], 1u + (rr ? 65536u : 0u));
+      const uint32_t slot = old & 0xffffu;
+      if (slot < MAXC) bs.bcand[b * MAXC + slot] = (uint16_t)(p | (rr ? 0x8000 : 0));
+      app = rr && (old >> 16) == 0u;
+    }
+    // one append per warp: every block's raster bricks go through the single list counter
+    const unsigned am = __activemask();
+    const unsigned bal = __ballot_sync(am, app);
+    if (bal) {
+      const int lane = threadIdx.x & 31, leader = __ffs(bal) - 1;
+      uint32_t base = 0;
+      if (lane == leader) base = atomicAdd(&bs.bword[nbrick], (uint32_t)__popc(bal));
+      base = __shfl_sync(am, base, leader);
+      if (app) bs.rlist[base + __popc(bal & ((1u << lane) - 1u))] = (int32_t)b;
     }
   }
   }
