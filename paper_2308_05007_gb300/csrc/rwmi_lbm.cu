@@ -1,8 +1,12 @@
 // rwmi_lbm.cu -- the fused LBM step: pull stream (periodic wrap / half-way bounce-back) + BGK
 // collide (Eqs. 12-15) with Guo forcing and either PSM solid coupling or the paper's
 // interpolated bounce-back (Eqs. 23-27); writes the populations, the velocity field and, on
-// reduction steps, per-particle force/torque and the FP64 sums. Also the IBB link list and its
-// q values, computed ahead of the update.
+// reduction steps, per-particle force/torque and the FP64 sums.
+//   lbm_kernel        the update (one cell per thread, direct coalesced pulls), its reduce-only
+//                     pass and the fused update + reduction of free-DEM runs
+//   lbm_batched       the same update over the cells of many domains (fused batch)
+//   lbm_tma_kernel    the update with its pulled rows staged by TMA tensor copies (an option)
+//   ibb_links_kernel  IBB node words and link list; ibb_link_kernel: q and G of every link
 #include <atomic>
 #include <type_traits>
 
