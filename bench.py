@@ -373,6 +373,26 @@ def measure_variants(a, stream):
         out[f"D3Q{q}_fp32_shift_ibb"] = {
             "lbm_ms": lbm_ms, "lbm_gbs": gbs, "lbm_hbm_frac": gbs / peak,
             "step_ms": step_ms, "mlups": w.n_cells / (step_ms / 1e3) / 1e6}
+    # every particle's force and torque recorded on every step (force_interval 1): each step then
+    # runs the reduce-only LBM pass that the headline amortises over 16 steps
+    b = _ap.Namespace(**vars(a))
+    b.q, b.storage = 15, 1
+    w = workload(b)
+    sim = Simulation.from_workload(w, seed_walkers=False, force_interval=1)
+    sim.set_stream(stream)
+    sim.seed_walkers(w.n_walkers, *w.walker_box)
+    sim.step(64)
+    with torch.cuda.stream(stream):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.step(128)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    step_ms = e0.elapsed_time(e1) / 128
+    rows, _ = sim.force_series(max_rows=128)
+    sim.close()
+    out["D3Q15_fp32_shift_forces_every_step"] = {
+        "step_ms": step_ms, "mlups": w.n_cells / (step_ms / 1e3) / 1e6, "rows_recorded": int(len(rows))}
     # free particles (Eqs. 4-11) in place of the prescribed motion: the same box and particles,
     # density 2, gravity, damped frictional contacts, 10 DEM steps per LBM step; the LBM forms the
     # force in its update on every step, and the raster of t+1 follows the DEM

@@ -120,6 +120,10 @@ typedef struct {
                                   copies; 0: direct coalesced loads. Same results bit for bit.
                                   Default 0 (direct loads measured faster on GB300); ignored where
                                   not supported. */
+    int32_t force_interval;    /* record every particle's force and torque every this many steps
+                                  (0: never; rwmi_force_series reads them). A recorded step runs
+                                  the reduce-only LBM pass (or the fused one of free-DEM runs),
+                                  which the other steps skip. Default 0. */
 } rwmi_config;
 
 /* Fills *cfg with the defaults listed above. */
@@ -312,6 +316,12 @@ RWMI_API rwmi_status rwmi_mass_momentum(rwmi_ctx* ctx, double out[4]);
 /* Hydrodynamic force and torque on each particle at the last LBM step, FP64:
  * out[6 p .. 6 p + 2] = F_p, out[6 p + 3 .. 6 p + 5] = T_p about the particle origin. */
 RWMI_API rwmi_status rwmi_particle_forces(rwmi_ctx* ctx, double* out);
+
+/* The forces recorded every force_interval steps (Section 2.4.3 / PSM: the force of the LBM
+ * update of step t, labelled t + 1, the steps completed): the newest min(max_rows, recorded,
+ * 4096) rows, oldest first, each {t + 1, F_0, T_0, F_1, T_1, ...} (1 + 6 P doubles); *n_rows is
+ * set. RWMI_E_INVALID without particles or with force_interval 0. */
+RWMI_API rwmi_status rwmi_force_series(rwmi_ctx* ctx, double* out, int32_t max_rows, int32_t* n_rows);
 
 /* Walker state: out[4 w .. 4 w + 3] = {x, y, z, id} (binary32; id as a float-coded integer)
  * in the library's current (cell-sorted) order; x0 (may be NULL) receives the start

@@ -22,6 +22,7 @@ namespace {
 
 constexpr int SERIES_ROWS = 65536;
 constexpr int SERIES_COLS = 14;
+constexpr int FORCE_ROWS = 4096;    // rows of the force series ring (1 + 6 P doubles each)
 constexpr uint64_t CKPT_MAGIC = 0x31494d5752ULL;  // "RWMI1"
 constexpr uint64_t CKPT_DEM_MAGIC = 0x314d4544ULL;  // "DEM1": the free-DEM section
 
@@ -78,6 +79,8 @@ struct rwmi_ctx {
   double* macc = nullptr;                // moment accumulators [12]
   double* series = nullptr;              // [SERIES_ROWS][SERIES_COLS]
   double* mrow = nullptr;                // on-demand moments row [SERIES_COLS]
+  double* fseries = nullptr;             // force series ring [FORCE_ROWS][1 + 6 P] (force_interval > 0)
+  int fseries_p = 0;                     // particle count the ring was sized for
   // bricks per time parity (the walker masks are rewritten by every raster)
   uint64_t* wmask[2] = {nullptr, nullptr};
   uint32_t* bword[2] = {nullptr, nullptr};
@@ -121,6 +124,7 @@ struct rwmi_ctx {
   int fcur = 0, pcur = 0;
   int64_t binned_t = -1;
   int64_t series_rows = 0;
+  int64_t fseries_rows = 0;
   int64_t launches = 0;
   unsigned long long status_seen[ST_COUNT] = {0};
   std::map<GraphKey, GraphEntry> graphs;
@@ -400,6 +404,18 @@ rwmi_status reset_fluid(rwmi_ctx* c) {
   return RWMI_OK;
 }
 
+// The force series ring (force_interval > 0 with particles), sized for the current particle count.
+rwmi_status ensure_force_series(rwmi_ctx* c) {
+  if (c->cfg.force_interval <= 0 || c->P == 0) return RWMI_OK;
+  if (c->fseries && c->fseries_p == c->P) return RWMI_OK;
+  dfree(c, c->fseries);
+  c->fseries = nullptr;
+  CK(dalloc(c, &c->fseries, sizeof(double) * (size_t)FORCE_ROWS * (1 + 6 * (size_t)c->P)));
+  c->fseries_p = c->P;
+  c->fseries_rows = 0;
+  return RWMI_OK;
+}
+
 // Tensor maps of the population buffers for the TMA-staged update, where it applies.
 void update_tma(rwmi_ctx* c) {
   c->tma_ok = c->f[0] && c->f[1] && lbm_tma_supported(c->cfg.q, c->cfg.storage, c->g) &&
@@ -479,6 +495,11 @@ void phase_end(rwmi_ctx* c, int ph) {
   if (c->timing) cudaEventRecord(c->ev[2 * ph + 1], c->stream);
 }
 
+// Are the forces of the step that completes step count `done` recorded in the force series?
+bool force_recorded(const rwmi_ctx* c, int64_t done) {
+  return c->cfg.force_interval > 0 && c->P > 0 && c->fseries && done % c->cfg.force_interval == 0;
+}
+
 // One timestep t -> t+1 of a run of steps (host mirrors advance as the launches are queued).
 // Buffers are per time parity where two steps' kernels may overlap: the solid fraction of t is
 // solid[t & 1] (rasterised during step t-1, or at set-up), the LBM of t writes u[t & 1], the
@@ -494,6 +515,8 @@ void phase_end(rwmi_ctx* c, int ph) {
 // steps never race on a counter; segment_end advances d_T once per run. `reduce`: also form the
 // FP64 mass/momentum sums of this step.
 void enqueue_step(rwmi_ctx* c, bool reduce) {
+  const bool rec_f = force_recorded(c, c->t + 1);   // this step's forces go to the force series
+  reduce = reduce || rec_f;
   const int tp = (int)(c->t & 1), tn = tp ^ 1;
   const int toff = (int)(c->t - c->t_base);
   const ParticleSet ps = particle_set(c);
@@ -545,6 +568,12 @@ void enqueue_step(rwmi_ctx* c, bool reduce) {
                  brick_set(c, tp), c->tau, c->cfg.rho0, c->acc[tp] + 6 * c->P, c->acc[tp],
                  c->status, c->stream, c->cfg.lbm_block, ibb ? &ia : nullptr, dem, !staged);
     c->launches += dem ? 1 : reduce ? 2 : 1;   // fused with DEM; else the reduce-only pass on reduction steps
+    if (rec_f) {
+      launch_force_row(c->acc[tp], c->P, c->fseries, c->cfg.force_interval, FORCE_ROWS, c->d_T, toff + 1,
+                       c->stream);
+      c->launches++;
+      c->fseries_rows++;
+    }
     phase_end(c, RWMI_PHASE_LBM);
     c->fcur ^= 1;
   };
@@ -631,6 +660,7 @@ void advance_mirrors(rwmi_ctx* c, int64_t L) {
       c->binned_t = c->t;
     }
     if (c->cfg.moment_interval > 0 && c->t % c->cfg.moment_interval == 0) c->series_rows++;
+    if (force_recorded(c, c->t)) c->fseries_rows++;
   }
   c->t_base = c->t;
 }
@@ -638,7 +668,7 @@ void advance_mirrors(rwmi_ctx* c, int64_t L) {
 int64_t chunk_length(const rwmi_ctx* c) {
   auto gcd = [](int64_t a, int64_t b) { while (b) { int64_t t = a % b; a = b; b = t; } return a; };
   int64_t L = 2;
-  for (int64_t v : {(int64_t)c->cfg.sort_interval, (int64_t)c->cfg.moment_interval})
+  for (int64_t v : {(int64_t)c->cfg.sort_interval, (int64_t)c->cfg.moment_interval, (int64_t)c->cfg.force_interval})
     if (v > 0) L = L / gcd(L, v) * v;
   return L;
 }
@@ -774,7 +804,7 @@ RWMI_API rwmi_status rwmi_configure(rwmi_ctx* c, const rwmi_config* cfg) try {
       !(cfg->force_period >= 0.0) ||
       !(cfg->lbm_block == 0 || cfg->lbm_block == 64 || cfg->lbm_block == 128 || cfg->lbm_block == 256) ||
       cfg->overlap < 0 || cfg->overlap > 2 || cfg->coupling < 0 || cfg->coupling > 1 ||
-      cfg->lbm_staging < 0 || cfg->lbm_staging > 1 ||
+      cfg->lbm_staging < 0 || cfg->lbm_staging > 1 || cfg->force_interval < 0 ||
       (cfg->coupling == 1 && cfg->storage != RWMI_STORE_FP32_SHIFT && cfg->storage != RWMI_STORE_FP64_SHIFT))
     return fail(c, RWMI_E_INVALID, "rwmi_configure: bad q, storage, wall_mask, rho0 or interval");
   for (int a = 0; a < 3; ++a)
@@ -811,7 +841,9 @@ RWMI_API rwmi_status rwmi_configure(rwmi_ctx* c, const rwmi_config* cfg) try {
     CK(dalloc(c, &c->ibl.count, sizeof(unsigned int) * 4));
   }
   if (c->ibl.count) CK(cudaMemsetAsync(c->ibl.count, 0, sizeof(unsigned int) * 4, c->stream));
-  rwmi_status s = reset_fluid(c);
+  rwmi_status s = ensure_force_series(c);
+  if (s != RWMI_OK) return s;
+  s = reset_fluid(c);
   if (s != RWMI_OK) return s;
   s = build_current_frame(c);
   if (s != RWMI_OK) return s;
@@ -890,6 +922,8 @@ RWMI_API rwmi_status rwmi_set_metaballs(rwmi_ctx* c, int32_t P, const int32_t* c
   CK(copy_now(c, c->desc, desc.data(), sizeof(ParticleDesc) * desc.size()));
   CK(copy_now(c, c->cbody, body.data(), sizeof(float4) * body.size()));
   rwmi_status s = alloc_particles(c);
+  if (s != RWMI_OK) return s;
+  s = ensure_force_series(c);
   if (s != RWMI_OK) return s;
   drop_graphs(c);
   s = build_current_frame(c);
@@ -1481,6 +1515,28 @@ RWMI_API rwmi_status rwmi_particle_forces(rwmi_ctx* c, double* out) try {
   return api_exception(c, "rwmi_particle_forces", e_);
 }
 
+RWMI_API rwmi_status rwmi_force_series(rwmi_ctx* c, double* out, int32_t max_rows, int32_t* n_rows) try {
+  if (!c || !out || !n_rows || max_rows < 0) return RWMI_E_INVALID;
+  GUARD(c);
+  if (c->P == 0 || c->cfg.force_interval == 0 || !c->fseries)
+    return fail(c, RWMI_E_INVALID, "rwmi_force_series: no particles or force_interval 0");
+  const size_t cols = 1 + 6 * (size_t)c->P;
+  const int64_t avail = std::min<int64_t>(c->fseries_rows, FORCE_ROWS);
+  const int64_t take = std::min<int64_t>(avail, max_rows);
+  std::vector<double> ring((size_t)FORCE_ROWS * cols);
+  CK(cudaStreamSynchronize(c->stream));
+  CK(copy_now(c, ring.data(), c->fseries, sizeof(double) * ring.size()));
+  std::vector<double> rows((size_t)take * cols);
+  const int64_t first = c->fseries_rows - take;
+  for (int64_t r = 0; r < take; ++r)
+    std::memcpy(&rows[(size_t)r * cols], &ring[(size_t)((first + r) % FORCE_ROWS) * cols], sizeof(double) * cols);
+  if (take > 0) CK(copy_now(c, out, rows.data(), sizeof(double) * rows.size()));
+  *n_rows = (int32_t)take;
+  return RWMI_OK;
+} catch (const std::exception& e_) {
+  return api_exception(c, "rwmi_force_series", e_);
+}
+
 RWMI_API rwmi_status rwmi_walkers(rwmi_ctx* c, float* out, float* x0) try {
   if (!c || (!out && c->nw > 0)) return RWMI_E_INVALID;
   GUARD(c);
@@ -1668,8 +1724,9 @@ namespace {
 // A context runs in a fused batch when its step is the plain one of the hot path: partially
 // saturated cells, prescribed particles, and the batch's velocity set, storage and intervals.
 bool fusable(const rwmi_ctx* c, const rwmi_ctx* c0) {
-  return c->cfg.coupling == 0 && !c->dem && c->cfg.q == c0->cfg.q && c->cfg.storage == c0->cfg.storage &&
-         c->cfg.sort_interval == c0->cfg.sort_interval && c->cfg.moment_interval == c0->cfg.moment_interval;
+  return c->cfg.coupling == 0 && !c->dem && c->cfg.force_interval == 0 && c->cfg.q == c0->cfg.q &&
+         c->cfg.storage == c0->cfg.storage && c->cfg.sort_interval == c0->cfg.sort_interval &&
+         c->cfg.moment_interval == c0->cfg.moment_interval;
 }
 
 void fused_drop_graphs(rwmi_batch* b) {
@@ -2159,7 +2216,7 @@ RWMI_API void rwmi_destroy(rwmi_ctx* c) {
   }
   dfree(c, c->wlist); dfree(c, c->wlist_n);
   dfree(c, c->u[0]); dfree(c, c->u[1]); dfree(c, c->solid[0]); dfree(c, c->solid[1]); dfree(c, c->node[0]); dfree(c, c->node[1]); dfree(c, c->d_T); dfree(c, c->status); dfree(c, c->macc);
-  dfree(c, c->series); dfree(c, c->mrow); dfree(c, c->desc); dfree(c, c->cbody); dfree(c, c->rank);
+  dfree(c, c->series); dfree(c, c->mrow); dfree(c, c->fseries); dfree(c, c->desc); dfree(c, c->cbody); dfree(c, c->rank);
   dfree(c, c->counts); dfree(c, c->offsets); dfree(c, c->bsums); dfree(c, c->scratch); dfree(c, c->wmask[0]); dfree(c, c->wmask[1]);
   dfree(c, c->dem_d); dfree(c, c->dem_b);
   dfree(c, c->ibl.base); dfree(c, c->ibl.word); dfree(c, c->ibl.cell); dfree(c, c->ibl.meta); dfree(c, c->ibl.q); dfree(c, c->ibl.g); dfree(c, c->ibl.ocell); dfree(c, c->ibl.count);

@@ -231,6 +231,21 @@ __global__ void pose_bin_batched(const PoseArgs* __restrict__ args, const BlockM
   pose_bin_body(args[m.domain], m.block, m.blocks);
 }
 
+// One row {t, F_0, T_0, F_1, T_1, ...} of the force series: the forces of the LBM update just
+// done (acc), labelled with the steps completed t, read from the device counter, into slot
+// (t / interval - 1) mod rows, so that a replayed graph writes the row of the step it runs.
+__global__ void force_row_kernel(const double* __restrict__ acc, int P, double* __restrict__ base, int interval,
+                                 int rows, const int64_t* __restrict__ d_T, int toff) {
+  const int64_t t = *d_T + toff;
+  double* row = base + (size_t)(((t / interval) - 1) % rows) * (1 + 6 * (size_t)P);
+  for (int m = threadIdx.x; m < 6 * P; m += blockDim.x) row[1 + m] = acc[m];
+  if (threadIdx.x == 0) row[0] = (double)t;
+}
+void launch_force_row(const double* acc, int P, double* base, int interval, int rows, const int64_t* d_T, int toff,
+                      cudaStream_t st) {
+  force_row_kernel<<<1, 256, 0, st>>>(acc, P, base, interval, rows, d_T, toff);
+}
+
 // Zeroes n words. A kernel rather than cudaMemsetAsync: inside the captured step a memset node
 // stalled the concurrent branches of the pipelined schedule (measured: 0.14 ms per step).
 struct ClearArgs {

@@ -229,6 +229,9 @@ struct ParticleSet {
 };
 
 void launch_clear_u32(uint32_t* p, uint32_t n, cudaStream_t st);
+// row of the force series from the force accumulators of the update just done
+void launch_force_row(const double* acc, int P, double* base, int interval, int rows, const int64_t* d_T, int toff,
+                      cudaStream_t st);
 void launch_pose_bin(const Geom& g, const ParticleSet& ps, BrickSet bs, const int64_t* d_T,
                      int t_offset, const double F0[3], double force_period, int zero_forces,
                      double* forces, cudaStream_t st);

@@ -25,7 +25,8 @@ EXPORTED = ["rwmi_config_defaults", "rwmi_create", "rwmi_configure", "rwmi_set_s
             "rwmi_autotune", "rwmi_query", "rwmi_footprint", "rwmi_sync",
             "rwmi_time", "rwmi_info", "rwmi_concentration", "rwmi_walker_moments", "rwmi_moment_series",
             "rwmi_velocity", "rwmi_density", "rwmi_populations", "rwmi_lattice", "rwmi_solid", "rwmi_nodes",
-            "rwmi_mass_momentum", "rwmi_particle_forces", "rwmi_walkers", "rwmi_counters", "rwmi_save",
+            "rwmi_mass_momentum", "rwmi_particle_forces", "rwmi_force_series", "rwmi_walkers", "rwmi_counters",
+            "rwmi_save",
             "rwmi_load", "rwmi_brick_stats", "rwmi_bin_walkers_noalloc", "rwmi_last_error",
             "rwmi_launch_count", "rwmi_destroy", "rwmi_batch_create", "rwmi_batch_step", "rwmi_batch_sync",
             "rwmi_batch_last_error", "rwmi_batch_destroy", "rwmi_dem_defaults", "rwmi_set_dem",
@@ -51,7 +52,8 @@ class Config(C.Structure):
                 ("body_force", C.c_double * 3), ("force_period", C.c_double), ("rho0", C.c_double),
                 ("init_velocity", C.c_double * 3), ("sort_interval", C.c_int32),
                 ("moment_interval", C.c_int32), ("use_graphs", C.c_int32), ("lbm_block", C.c_int32),
-                ("overlap", C.c_int32), ("coupling", C.c_int32), ("lbm_staging", C.c_int32)]
+                ("overlap", C.c_int32), ("coupling", C.c_int32), ("lbm_staging", C.c_int32),
+                ("force_interval", C.c_int32)]
 
 
 class BatchTiles(C.Structure):
@@ -119,6 +121,7 @@ def load(build_if_missing: bool = False):
                  "rwmi_populations", "rwmi_mass_momentum", "rwmi_particle_forces", "rwmi_counters"):
         getattr(L, name).argtypes = [P, vp]
     L.rwmi_moment_series.argtypes = [P, vp, C.c_int32, C.POINTER(C.c_int32)]
+    L.rwmi_force_series.argtypes = [P, vp, C.c_int32, C.POINTER(C.c_int32)]
     L.rwmi_lattice.argtypes = [P, vp, vp, C.POINTER(C.c_int32)]
     L.rwmi_solid.argtypes = [P, vp, vp]
     L.rwmi_nodes.argtypes = [P, vp]
@@ -259,7 +262,7 @@ class Simulation:
     def __init__(self, dims, tau, D, seed=0, q=19, storage=STORE_FP32_SHIFT, wall_mask=0,
                  body_force=(0.0, 0.0, 0.0), force_period=0.0, rho0=1.0, init_velocity=(0.0, 0.0, 0.0),
                  sort_interval=16, moment_interval=0, use_graphs=True, stream=None, lbm_block=128,
-                 overlap=2, coupling=0, lbm_staging=0):
+                 overlap=2, coupling=0, lbm_staging=0, force_interval=0):
         L = load()
         self._L = L
         self._h = C.c_void_p()
@@ -282,6 +285,7 @@ class Simulation:
         cfg.overlap = int(overlap)
         cfg.coupling = int(coupling)
         cfg.lbm_staging = int(lbm_staging)
+        cfg.force_interval = int(force_interval)
         try:
             self._check(L.rwmi_configure(self._h, C.byref(cfg)))
         except RwmiError:
@@ -518,6 +522,16 @@ class Simulation:
         out = np.zeros((max(self.n_particles, 1), 6))
         self._check(self._L.rwmi_particle_forces(self._h, _ptr(out)))
         return out[: self.n_particles]
+
+    def force_series(self, max_rows=4096):
+        """rwmi_force_series: (steps [R] int64, forces [R, P, 6]) of the recorded rows, oldest
+        first; forces[r, p] = (F_p, T_p) of the LBM update that completed steps[r]."""
+        P = self.n_particles
+        out = np.zeros((max(int(max_rows), 1), 1 + 6 * P))
+        n = C.c_int32()
+        self._check(self._L.rwmi_force_series(self._h, _ptr(out), int(max_rows), C.byref(n)))
+        rows = out[: n.value]
+        return rows[:, 0].astype(np.int64), rows[:, 1:].reshape(n.value, P, 6)
 
     def walkers(self, with_x0=True):
         """Returns (positions [N,3] float32, ids [N] int64, start positions [N,3] or None) in the

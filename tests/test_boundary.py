@@ -109,6 +109,8 @@ def test_null_handles_are_refused(lib_path):
     assert L.rwmi_batch_get_tiles(None, None) == -1
     assert L.rwmi_batch_autotune(None, 16, None) == -1
     assert L.rwmi_batch_launch_count(None) == 0
+    n = C.c_int32()
+    assert L.rwmi_force_series(None, None, 0, C.byref(n)) == -1
 
 
 def test_defaults_are_the_documented_ones(lib_path):
@@ -118,7 +120,7 @@ def test_defaults_are_the_documented_ones(lib_path):
     L.rwmi_config_defaults(C.byref(cfg))
     assert (cfg.q, cfg.storage, cfg.wall_mask, cfg.rho0, cfg.sort_interval, cfg.moment_interval,
             cfg.use_graphs, cfg.lbm_block, cfg.overlap, cfg.coupling,
-            cfg.lbm_staging) == (19, 1, 0, 1.0, 16, 0, 1, 128, 2, 0, 0)
+            cfg.lbm_staging, cfg.force_interval) == (19, 1, 0, 1.0, 16, 0, 1, 128, 2, 0, 0, 0)
     assert list(cfg.body_force) == [0.0] * 3 and cfg.force_period == 0.0
     dem = rwmi.DemConfig()
     L.rwmi_dem_defaults(C.byref(dem))
