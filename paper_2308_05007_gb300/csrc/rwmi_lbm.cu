@@ -30,8 +30,7 @@ template <int Q, typename T> struct Planes {
 
 // q of Eq. 25: 24 binary32 bisection steps on Eq. 3 of one particle along x_f + s e, s in [0, 1]
 // (the CPU oracle's sequence: midpoint 0.5 (lo + hi), point x_f + mid e), q = the bracket's
-// middle. ibb_link_kernel calls it once per listed link; the LBM kernel calls it only for links
-// beyond the list's capacity.
+// middle. ibb_link_kernel calls it once per link (listed, or in an overflow slot).
 __device__ __forceinline__ float ibb_link_q(const float4* __restrict__ cw, int c0, int c1, float x0, float y0,
                                          float z0, int ex, int ey, int ez, const Geom& g) {
   float lo = 0.0f, hi = 1.0f;
@@ -583,8 +582,9 @@ __global__ void __launch_bounds__(256, sizeof(typename Store<STORE>::R) == 8 ? 2
 // Every fluid node of a flagged brick whose lattice neighbour x - e_i is a solid node owns the
 // link (x, i). ibb_links_kernel gives every cell of a flagged brick its node word (bit 0: solid
 // node; bit i: link i), appends a node's links in direction order (warp-aggregated) and keeps the
-// index of its first one; ibb_q_kernel then runs the 24-step binary32 bisection of every link at
-// full occupancy, instead of inside the occupancy-bound LBM kernel.
+// index of its first one (or, when the list is full, an overflow slot); ibb_link_kernel then runs
+// the 24-step binary32 bisection of every link and forms its G at full occupancy, instead of
+// inside the update.
 template <int Q, bool WALLS>
 __global__ void __launch_bounds__(256) ibb_links_kernel(Geom g, const uint32_t* __restrict__ bword,
                                                         const uint16_t* __restrict__ nodes,
