@@ -1523,14 +1523,12 @@ RWMI_API rwmi_status rwmi_force_series(rwmi_ctx* c, double* out, int32_t max_row
   const size_t cols = 1 + 6 * (size_t)c->P;
   const int64_t avail = std::min<int64_t>(c->fseries_rows, FORCE_ROWS);
   const int64_t take = std::min<int64_t>(avail, max_rows);
-  std::vector<double> ring((size_t)FORCE_ROWS * cols);
   CK(cudaStreamSynchronize(c->stream));
-  CK(copy_now(c, ring.data(), c->fseries, sizeof(double) * ring.size()));
-  std::vector<double> rows((size_t)take * cols);
-  const int64_t first = c->fseries_rows - take;
-  for (int64_t r = 0; r < take; ++r)
-    std::memcpy(&rows[(size_t)r * cols], &ring[(size_t)((first + r) % FORCE_ROWS) * cols], sizeof(double) * cols);
-  if (take > 0) CK(copy_now(c, out, rows.data(), sizeof(double) * rows.size()));
+  // the newest `take` rows of the ring, oldest first: at most two contiguous pieces
+  const int64_t first = (c->fseries_rows - take) % FORCE_ROWS;
+  const int64_t n1 = std::min<int64_t>(take, FORCE_ROWS - first);
+  if (n1 > 0) CK(copy_now(c, out, c->fseries + (size_t)first * cols, sizeof(double) * (size_t)n1 * cols));
+  if (take > n1) CK(copy_now(c, out + (size_t)n1 * cols, c->fseries, sizeof(double) * (size_t)(take - n1) * cols));
   *n_rows = (int32_t)take;
   return RWMI_OK;
 } catch (const std::exception& e_) {
