@@ -581,14 +581,14 @@ void enqueue_step(rwmi_ctx* c, bool reduce) {
     lbm();
     pose();
     phase_begin(c, RWMI_PHASE_RASTER);
-    launch_raster(c->g, ps, brick_set(c, tn), c->solid[tn], c->status, c->nsm, c->stream);
+    launch_raster(c->g, ps, brick_set(c, tn), c->solid[tn], c->status, c->nsm, c->stream, !ibb);
     c->launches++;
     phase_end(c, RWMI_PHASE_RASTER);
   } else if (fork_raster) {
     pose();
     cudaEventRecord(c->fork_ev, c->stream);
     cudaStreamWaitEvent(c->side, c->fork_ev, 0);
-    launch_raster(c->g, ps, brick_set(c, tn), c->solid[tn], c->status, c->nsm, c->side);
+    launch_raster(c->g, ps, brick_set(c, tn), c->solid[tn], c->status, c->nsm, c->side, !ibb);
     c->launches++;
     cudaEventRecord(c->join_ev, c->side);
     lbm();
@@ -598,7 +598,7 @@ void enqueue_step(rwmi_ctx* c, bool reduce) {
     pose();
     phase_begin(c, RWMI_PHASE_RASTER);
     if (c->P > 0) {
-      launch_raster(c->g, ps, brick_set(c, tn), c->solid[tn], c->status, c->nsm, c->stream);
+      launch_raster(c->g, ps, brick_set(c, tn), c->solid[tn], c->status, c->nsm, c->stream, !ibb);
       c->launches++;
     }
     phase_end(c, RWMI_PHASE_RASTER);
@@ -1447,6 +1447,14 @@ RWMI_API rwmi_status rwmi_solid(rwmi_ctx* c, int32_t* count, int32_t* owner) try
   rwmi_status s = ensure_scratch(c, bytes);
   if (s != RWMI_OK) return s;
   int32_t* tmp = (int32_t*)c->scratch;   // the current time was rasterised by the last step / set-up
+  if (c->cfg.coupling == 1 && c->P > 0) {
+    // IBB steps rasterise bricks and walker masks only: the counts of the current time are formed
+    // here, from its bricks (intact until the next step), by a full raster with a reset work
+    // counter (it rewrites the same walker masks)
+    CK(cudaMemsetAsync(c->bword[par] + c->nbrick + 1, 0, sizeof(uint32_t), c->stream));
+    launch_raster(c->g, particle_set(c), brick_set(c, par), c->solid[par], c->status, c->nsm, c->stream, true);
+    c->launches++;
+  }
   launch_unpack_solid(c->g, c->solid[par], c->bword[par], tmp, tmp + c->ncell, c->stream);
   c->launches++;
   CK(cudaGetLastError());

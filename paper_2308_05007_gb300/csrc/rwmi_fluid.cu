@@ -444,12 +444,15 @@ struct RasterWarp {
 //     the candidate with most sub-samples, lowest index on ties.
 // All decisions use bounds with a 1e-3 margin and, within 4e-5 of f = 1, the exact binary32
 // sequence shared with the CPU oracle, so counts and owners equal the oracle's bit for bit.
+// With cells = 0 a launch stops after step 2: the IBB coupling reads node classes, not counts,
+// and needs only the walkers' masks each step.
 struct RasterArgs {
   Geom g;
   ParticleSet ps;
   BrickSet bs;
   uint16_t* solid;
   unsigned long long* status;
+  int cells;
 };
 
 __device__ __forceinline__ void raster_body(const RasterArgs& A) {
@@ -567,7 +570,7 @@ __device__ __forceinline__ void raster_body(const RasterArgs& A) {
       }
     }
     // 3. cells, 32 per round
-    for (int r = 0; r < (BRICK * BRICK * BRICK) / 32; ++r) {
+    for (int r = 0; A.cells && r < (BRICK * BRICK * BRICK) / 32; ++r) {
       const int cl = r * 32 + lane;
       const int lx = cl & 7, ly = (cl >> 3) & 7, lz = cl >> 6;
       const int i = bi * BRICK + lx, j = bj * BRICK + ly, k = bk * BRICK + lz;
@@ -665,14 +668,14 @@ __global__ void __launch_bounds__(256, 4) raster_batched(const RasterArgs* __res
 // one block per SM made the raster itself the longer branch)
 int raster_grid(int nsm) { return nsm * 2; }
 void launch_raster(const Geom& g, const ParticleSet& ps, BrickSet bs, uint16_t* solid,
-                   unsigned long long* status, int nsm, cudaStream_t st) {
+                   unsigned long long* status, int nsm, cudaStream_t st, bool cells) {
   if (ps.P == 0) return;
-  raster_kernel<<<raster_grid(nsm), RW_WARPS * 32, 0, st>>>(RasterArgs{g, ps, bs, solid, status});
+  raster_kernel<<<raster_grid(nsm), RW_WARPS * 32, 0, st>>>(RasterArgs{g, ps, bs, solid, status, cells ? 1 : 0});
 }
 size_t raster_args_size() { return sizeof(RasterArgs); }
 void raster_args(void* dst, const Geom& g, const ParticleSet& ps, BrickSet bs, uint16_t* solid,
                  unsigned long long* status) {
-  *static_cast<RasterArgs*>(dst) = RasterArgs{g, ps, bs, solid, status};
+  *static_cast<RasterArgs*>(dst) = RasterArgs{g, ps, bs, solid, status, 1};
 }
 void launch_raster_batched(const void* args, const BlockMap* map, int nblocks, cudaStream_t st) {
   if (nblocks > 0) raster_batched<<<nblocks, RW_WARPS * 32, 0, st>>>(static_cast<const RasterArgs*>(args), map);

@@ -235,8 +235,9 @@ void launch_force_row(const double* acc, int P, double* base, int interval, int 
 void launch_pose_bin(const Geom& g, const ParticleSet& ps, BrickSet bs, const int64_t* d_T,
                      int t_offset, const double F0[3], double force_period, int zero_forces,
                      double* forces, cudaStream_t st);
+// cells = false: brick classes and walker masks only (no per-cell sub-sample counts)
 void launch_raster(const Geom& g, const ParticleSet& ps, BrickSet bs, uint16_t* solid,
-                   unsigned long long* status, int nsm, cudaStream_t st);
+                   unsigned long long* status, int nsm, cudaStream_t st, bool cells = true);
 // Extra inputs of the IBB coupling: node classes of this time, (u, rho) of the previous update,
 // particle descriptors (control point ranges). nullptr selects the partially saturated cells.
 struct IbbArgs {

@@ -40,6 +40,33 @@ def test_ibb_nodes_bit_exact_along_a_trajectory():
         assert (sim.nodes() > 0).sum() > 50
 
 
+def test_ibb_solid_counts_on_demand_equal_the_oracle_and_change_nothing():
+    """IBB steps rasterise only bricks and walker masks; rwmi_solid forms the sub-sample counts of
+    the current time on demand. They equal the oracle's raster bit for bit, and a run that reads
+    them after every few steps keeps the same populations and walkers as one that never does."""
+    _need_gpu()
+    from oracle.oracle import Oracle
+    from paper_2308_05007_gb300.rwmi import Simulation
+    w = _ibb_workload(seed=21)
+    ora = Oracle.from_workload(w, seed_walkers=False)
+    with Simulation.from_workload(w) as a, Simulation.from_workload(w) as b:
+        for t in (0, 3, 10, 17):
+            a.step(t - a.t)
+            b.step(t - b.t)
+            ora.step_fluid(t - ora.t)
+            cg, og = a.solid()
+            co, oo = ora.solid(t)
+            assert np.array_equal(cg, co), (t, np.flatnonzero(cg != co)[:10])
+            assert np.array_equal(og, oo), t
+            assert cg.max() == 64
+        b.step(3)
+        a.step(3)
+        assert np.array_equal(a.populations(), b.populations())
+        xa, _ = a.walkers_by_id()
+        xb, _ = b.walkers_by_id()
+        assert np.array_equal(xa, xb)
+
+
 @pytest.mark.parametrize("storage,q", [(1, 15), (1, 19), (3, 15), (3, 19)])
 def test_ibb_one_step_from_identical_state(storage, q):
     _need_gpu()
