@@ -378,14 +378,14 @@ rwmi_status build_current_frame(rwmi_ctx* c) {
     const int pp = par ^ 1;
     launch_clear_u32(c->bword[pp], c->nbrick + BWORD_EXTRA, c->stream);
     launch_pose_bin(c->g, particle_set(c), brick_set(c, pp), c->d_T, -1, c->cfg.body_force,
-                    c->cfg.force_period, 1, c->acc[pp], c->stream);
+                    c->cfg.force_period, 1, c->acc[pp], c->cfg.q, c->tau, c->stream);
     launch_nodes(c->cfg.q, c->cfg.storage, c->g, particle_set(c), brick_set(c, pp), c->node[pp], c->node[pp],
                  c->f[c->fcur], c->cfg.rho0, false, c->stream);
     c->launches += 3;
   }
   CK(cudaMemsetAsync(c->bword[par], 0, sizeof(uint32_t) * (c->nbrick + BWORD_EXTRA), c->stream));
   launch_pose_bin(c->g, particle_set(c), brick_set(c, par), c->d_T, 0, c->cfg.body_force,
-                  c->cfg.force_period, 1, c->acc[par], c->stream);
+                  c->cfg.force_period, 1, c->acc[par], c->cfg.q, c->tau, c->stream);
   c->launches++;
   if (c->P > 0) {
     launch_raster(c->g, particle_set(c), brick_set(c, par), c->solid[par], c->status, c->nsm, c->stream);
@@ -534,7 +534,7 @@ void enqueue_step(rwmi_ctx* c, bool reduce) {
     launch_clear_u32(c->bword[tn], c->nbrick + BWORD_EXTRA, c->stream);
     c->launches++;
     launch_pose_bin(c->g, ps, brick_set(c, tn), c->d_T, toff + 1, c->cfg.body_force, c->cfg.force_period, 1,
-                    c->acc[tn], c->stream);
+                    c->acc[tn], c->cfg.q, c->tau, c->stream);
     c->launches++;
     phase_end(c, RWMI_PHASE_POSE);
   };
@@ -761,8 +761,8 @@ RWMI_API rwmi_status rwmi_create(rwmi_ctx** out, const int32_t dims[3], double t
         CK(dalloc(c, &c->bword[k], sizeof(uint32_t) * (c->nbrick + BWORD_EXTRA)));
         CK(dalloc(c, &c->bcand[k], sizeof(uint16_t) * (size_t)c->nbrick * MAXC));
         CK(dalloc(c, &c->rlist[k], sizeof(int32_t) * c->nbrick));
-        CK(dalloc(c, &c->sp[k], sizeof(StepParams)));
-        CK(cudaMemsetAsync(c->sp[k], 0, sizeof(StepParams), c->stream));
+        CK(dalloc(c, &c->sp[k], sizeof(StepParams) + sizeof(GuoPairs)));   // GuoPairs follows
+        CK(cudaMemsetAsync(c->sp[k], 0, sizeof(StepParams) + sizeof(GuoPairs), c->stream));
       }
       CK(dalloc(c, &c->desc, sizeof(ParticleDesc)));
       CK(dalloc(c, &c->cbody, sizeof(float4)));
@@ -1840,7 +1840,7 @@ rwmi_status fused_capture(rwmi_batch* b, FusedGraph& fg) {
       auto rec = [&](int p) { return blob.data() + off[s][p] + sz[p] * d; };
       clear_args(rec(FP_CLEARB), c->bword[tn], c->nbrick + BWORD_EXTRA);
       pose_args(rec(FP_POSE), c->g, ps, brick_set(c, tn), c->d_T, toff + 1, c->cfg.body_force, c->cfg.force_period, 1,
-                c->acc[tn]);
+                c->acc[tn], c->cfg.q, c->tau);
       raster_args(rec(FP_RASTER), c->g, ps, brick_set(c, tn), c->solid[tn], c->status);
       lbm_args(rec(FP_LBM), q, storage, c->g, c->f[c->fcur], c->f[c->fcur ^ 1], c->u[tp], c->solid[tp],
                brick_set(c, tp), c->tau, c->cfg.rho0, c->acc[tp] + 6 * c->P, c->acc[tp]);

@@ -38,6 +38,8 @@ struct PoseArgs {
   int t_offset, zero_acc;
   double F0x, F0y, F0z, fper;
   double* acc;
+  int q;          // lattice (15 or 19) and Guo factor 1 - 1/(2 tau) of the pair constants
+  double guo0;
 };
 
 // One block per particle, blk = p of nblk = max(P, 1) blocks (block 0 also writes the body force
@@ -49,14 +51,32 @@ __device__ void pose_bin_body(const PoseArgs& A, int blk, int nblk) {
   const double F0x = A.F0x, F0y = A.F0y, F0z = A.F0z, fper = A.fper;
   double* __restrict__ acc = A.acc;
   const int64_t t = *A.d_T + A.t_offset;
-  if (blk == 0 && threadIdx.x == 0) {
-    const double s = fper > 0.0 ? sin(2.0 * 3.141592653589793 * (double)t / fper) : 1.0;
-    bs.sp->Fd[0] = F0x * s;
-    bs.sp->Fd[1] = F0y * s;
-    bs.sp->Fd[2] = F0z * s;
-    bs.sp->F[0] = (float)(F0x * s);
-    bs.sp->F[1] = (float)(F0y * s);
-    bs.sp->F[2] = (float)(F0z * s);
+  if (blk == 0) {   // block-uniform: the body force of this time and the Guo pair constants
+    __shared__ double s_F[3];
+    if (threadIdx.x == 0) {
+      const double s = fper > 0.0 ? sin(2.0 * 3.141592653589793 * (double)t / fper) : 1.0;
+      s_F[0] = F0x * s;
+      s_F[1] = F0y * s;
+      s_F[2] = F0z * s;
+      bs.sp->Fd[0] = F0x * s;
+      bs.sp->Fd[1] = F0y * s;
+      bs.sp->Fd[2] = F0z * s;
+      bs.sp->F[0] = (float)(F0x * s);
+      bs.sp->F[1] = (float)(F0y * s);
+      bs.sp->F[2] = (float)(F0z * s);
+    }
+    __syncthreads();
+    // one constant per thread (binary64 runs on a narrow pipe: a serial loop cost 4 us a step)
+    const int H = (A.q - 1) / 2, j = threadIdx.x;
+    if (j < 2 * H) {
+      const int i = 1 + (j >> 1);
+      double eF = 0.0;
+      for (int a = 0; a < 3; ++a) eF += (double)(A.q == 15 ? Lat<15>::e(i, a) : Lat<19>::e(i, a)) * s_F[a];
+      const double wg = (A.q == 15 ? Lat<15>::wt<double>(i) : Lat<19>::wt<double>(i)) * A.guo0;
+      const double k = ((j & 1) ? 3.0 : 9.0) * wg * eF;
+      guo_pairs(bs.sp)->kd[j] = k;
+      guo_pairs(bs.sp)->k[j] = (float)k;
+    }
   }
   if (A.zero_acc) {   // force/torque [6P] + striped mass/momentum [4 RED_SLOTS] accumulators of this time
     for (int m = blk * blockDim.x + threadIdx.x; m < 6 * ps.P + 4 * RED_SLOTS; m += nblk * blockDim.x)
@@ -276,22 +296,25 @@ void launch_clear_batched(const void* args, const BlockMap* map, int nblocks, cu
 
 static PoseArgs make_pose_args(const Geom& g, const ParticleSet& ps, BrickSet bs, const int64_t* d_T,
                                int t_offset, const double F0[3], double force_period, int zero_forces,
-                               double* acc) {
+                               double* acc, int q, double tau) {
   PoseArgs a;
   a.g = g; a.ps = ps; a.bs = bs; a.d_T = d_T; a.t_offset = t_offset; a.zero_acc = zero_forces;
   a.F0x = F0[0]; a.F0y = F0[1]; a.F0z = F0[2]; a.fper = force_period; a.acc = acc;
+  a.q = q; a.guo0 = 1.0 - 0.5 / tau;
   return a;
 }
 void launch_pose_bin(const Geom& g, const ParticleSet& ps, BrickSet bs, const int64_t* d_T,
                      int t_offset, const double F0[3], double force_period, int zero_forces,
-                     double* acc, cudaStream_t st) {
+                     double* acc, int q, double tau, cudaStream_t st) {
   const int blocks = ps.P > 0 ? ps.P : 1;
-  pose_bin_kernel<<<blocks, 256, 0, st>>>(make_pose_args(g, ps, bs, d_T, t_offset, F0, force_period, zero_forces, acc));
+  pose_bin_kernel<<<blocks, 256, 0, st>>>(
+      make_pose_args(g, ps, bs, d_T, t_offset, F0, force_period, zero_forces, acc, q, tau));
 }
 size_t pose_args_size() { return sizeof(PoseArgs); }
 void pose_args(void* dst, const Geom& g, const ParticleSet& ps, BrickSet bs, const int64_t* d_T, int t_offset,
-               const double F0[3], double force_period, int zero_forces, double* acc) {
-  *static_cast<PoseArgs*>(dst) = make_pose_args(g, ps, bs, d_T, t_offset, F0, force_period, zero_forces, acc);
+               const double F0[3], double force_period, int zero_forces, double* acc, int q, double tau) {
+  *static_cast<PoseArgs*>(dst) =
+      make_pose_args(g, ps, bs, d_T, t_offset, F0, force_period, zero_forces, acc, q, tau);
 }
 void launch_pose_batched(const void* args, const BlockMap* map, int nblocks, cudaStream_t st) {
   if (nblocks > 0) pose_bin_batched<<<nblocks, 256, 0, st>>>(static_cast<const PoseArgs*>(args), map);

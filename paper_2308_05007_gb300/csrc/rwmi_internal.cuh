@@ -61,12 +61,27 @@ struct PoseD {     // the same in binary64 (read by the binary64 LBM)
   double pad;
 };
 
+constexpr int GK_PAIRS = 9;   // opposite pairs of the largest lattice (D3Q19)
 struct StepParams {  // per time parity
   float F[3];      // body force density at that time (binary32)
   float pad;
   double Fd[3];    // the same in binary64 (for the binary64 LBM)
   double padd;
 };
+// Guo source constants of the opposite pairs (i, i + H), i = 1..H, formed in binary64 from F, the
+// weights and g = 1 - 1/(2 tau): k[2 (i - 1)] = 9 w_i g (e_i.F), k[2 (i - 1) + 1] = 3 w_i g (e_i.F),
+// so that the update forms a pair's source terms with one multiply-add. The block follows the
+// StepParams of its time in the same allocation (guo_pairs), so StepParams itself, and with it
+// the code of the update kernels that read F alone, stays as it is.
+struct alignas(16) GuoPairs {
+  double kd[2 * GK_PAIRS];   // read as double2
+  float k[2 * GK_PAIRS];     // read as float2
+};
+static_assert(sizeof(StepParams) % 16 == 0, "GuoPairs follows StepParams 16-byte aligned");
+__host__ __device__ inline GuoPairs* guo_pairs(StepParams* sp) { return reinterpret_cast<GuoPairs*>(sp + 1); }
+__host__ __device__ inline const GuoPairs* guo_pairs(const StepParams* sp) {
+  return reinterpret_cast<const GuoPairs*>(sp + 1);
+}
 
 // Geometry shared by all kernels (passed by value).
 struct Geom {
@@ -232,9 +247,10 @@ void launch_clear_u32(uint32_t* p, uint32_t n, cudaStream_t st);
 // row of the force series from the force accumulators of the update just done
 void launch_force_row(const double* acc, int P, double* base, int interval, int rows, const int64_t* d_T, int toff,
                       cudaStream_t st);
+// q, tau: lattice and relaxation time of the Guo pair constants written beside the body force
 void launch_pose_bin(const Geom& g, const ParticleSet& ps, BrickSet bs, const int64_t* d_T,
                      int t_offset, const double F0[3], double force_period, int zero_forces,
-                     double* forces, cudaStream_t st);
+                     double* forces, int q, double tau, cudaStream_t st);
 // cells = false: brick classes and walker masks only (no per-cell sub-sample counts)
 void launch_raster(const Geom& g, const ParticleSet& ps, BrickSet bs, uint16_t* solid,
                    unsigned long long* status, int nsm, cudaStream_t st, bool cells = true);
@@ -391,7 +407,7 @@ void clear_args(void* dst, uint32_t* p, uint32_t n);
 void launch_clear_batched(const void* args, const BlockMap* map, int nblocks, cudaStream_t st);
 size_t pose_args_size();
 void pose_args(void* dst, const Geom& g, const ParticleSet& ps, BrickSet bs, const int64_t* d_T, int t_offset,
-               const double F0[3], double force_period, int zero_forces, double* acc);
+               const double F0[3], double force_period, int zero_forces, double* acc, int q, double tau);
 void launch_pose_batched(const void* args, const BlockMap* map, int nblocks, cudaStream_t st);
 size_t raster_args_size();
 void raster_args(void* dst, const Geom& g, const ParticleSet& ps, BrickSet bs, uint16_t* solid,

@@ -44,6 +44,19 @@ __device__ __forceinline__ float ibb_link_q(const float4* __restrict__ cw, int c
   return __fmul_rn(0.5f, __fadd_rn(lo, hi));
 }
 
+// Guo pair constant j (0: 9 w_i g e_i.F, 1: 3 w_i g e_i.F) of the opposite pair (i, i + H) at the
+// update's time, in the arithmetic type (both of a pair come from one 8- or 16-byte load)
+template <typename R>
+__device__ __forceinline__ R gk_pair(const StepParams* __restrict__ sp, int i, int j) {
+  if constexpr (sizeof(R) == 8) {
+    const double2 v = reinterpret_cast<const double2*>(guo_pairs(sp)->kd)[i - 1];
+    return j ? v.y : v.x;
+  } else {
+    const float2 v = reinterpret_cast<const float2*>(guo_pairs(sp)->k)[i - 1];
+    return j ? v.y : v.x;
+  }
+}
+
 // Row tiles of the TMA-staged update (lbm_tma_kernel): TMA_BX cells of one x-row per tile. Each
 // direction's source row is copied with a halo of 16 bytes on both sides, so that the copy
 // starts on a 16-byte boundary (x0 - halo) and covers x0 - 1 .. x0 + TMA_BX; rows sit 128-byte
@@ -241,6 +254,10 @@ __device__ __forceinline__ void lbm_body(Geom g, Planes<Q, typename Store<STORE>
   using S = Store<STORE>;
   using R = typename S::R;   // arithmetic type: binary32, or binary64 for the binary64 storage
   constexpr bool REDUCE = MODE != 0, STORES = MODE != 1;
+  // Guo pair constants loaded (one multiply-add per pair) or formed from F in each thread: the
+  // loaded form measured faster for D3Q19 and binary32-shifted D3Q15, slower for binary16 and
+  // plain binary32 D3Q15 (more spilled registers at 40)
+  constexpr bool GK_CONST = !(Q == 15 && (STORE == 0 || STORE == 2));
   // tau, omega = 1/tau, guo0 = 1 - 1/(2 tau) and rho0 arrive in R (formed and converted on the
   // host: per-thread divisions and binary64 -> binary32 conversions cost issue slots, and the
   // conversions occupy GB300's narrow FP64 pipe)
@@ -339,9 +356,15 @@ __device__ __forceinline__ void lbm_body(Geom g, Planes<Q, typename Store<STORE>
     if (L::e(i, 2)) jz += L::e(i, 2) * f[i];
   }
   const R rho = S::shifted ? rho0 + drho : drho;
-  const R Fx = sizeof(R) == 8 ? (R)sp->Fd[0] : (R)sp->F[0];
-  const R Fy = sizeof(R) == 8 ? (R)sp->Fd[1] : (R)sp->F[1];
-  const R Fz = sizeof(R) == 8 ? (R)sp->Fd[2] : (R)sp->F[2];
+  R Fx, Fy, Fz;
+  if constexpr (GK_CONST && sizeof(R) == 4) {   // F and its pad as one 16-byte load (byte 0 of
+    const float4 F4 = *reinterpret_cast<const float4*>(sp->F);   // a cudaMalloc'd StepParams)
+    Fx = F4.x; Fy = F4.y; Fz = F4.z;
+  } else {
+    Fx = sizeof(R) == 8 ? (R)sp->Fd[0] : (R)sp->F[0];
+    Fy = sizeof(R) == 8 ? (R)sp->Fd[1] : (R)sp->F[1];
+    Fz = sizeof(R) == 8 ? (R)sp->Fd[2] : (R)sp->F[2];
+  }
   // 1/rho correctly rounded (as the IEEE division 1/rho): a biased reciprocal would act like a
   // small momentum sink every step, which a steady forced flow amplifies by ~1/(tau nu k^2)
   const R inv_rho = sizeof(R) == 8 ? R(1.0) / rho : (R)__frcp_rn((float)rho);
@@ -419,15 +442,34 @@ __device__ __forceinline__ void lbm_body(Geom g, Planes<Q, typename Store<STORE>
       const int ex = L::e(i, 0), ey = L::e(i, 1), ez = L::e(i, 2);
       const R w = L::template wt<R>(i);
       const R eu = ex * ux + ey * uy + ez * uz;
-      const R eF = ex * Fx + ey * Fy + ez * Fz;
-      const R wdr = w * (S::shifted ? drho : rho), wr = w * rho, wg = w * guo;
-      const R sym = R(4.5) * eu * eu + m15uu;        // even part of the velocity polynomial
-      const R feq_p = wdr + wr * (sym + R(3.0) * eu);
-      const R feq_m = wdr + wr * (sym - R(3.0) * eu);
-      const R Se = wg * (R(9.0) * (eu * eF) - R(3.0) * uF);   // Guo term, even and odd parts
-      const R So = (R(3.0) * wg) * eF;
-      out[i] = om1 * f[i] + (rtau * feq_p + (Se + So));
-      out[io] = om1 * f[io] + (rtau * feq_m + (Se - So));
+      // Guo term: even part 9 w g (e.u)(e.F) - 3 w g u.F, odd part 3 w g e.F (g = 1 - 1/(2 tau)),
+      // times 1 - B in partially saturated cells
+      if constexpr (GK_CONST) {   // from the pair constants of this time
+        const R wdr = w * (S::shifted ? drho : rho), wr = w * rho;
+        const R sym = R(4.5) * eu * eu + m15uu;        // even part of the velocity polynomial
+        const R feq_p = wdr + wr * (sym + R(3.0) * eu);
+        const R feq_m = wdr + wr * (sym - R(3.0) * eu);
+        const R k9 = gk_pair<R>(sp, i, 0), k3 = gk_pair<R>(sp, i, 1);
+        const R Se = k9 * eu + (R(-3.0) * (w * guo0)) * uF;
+        R gp = Se + k3, gm = Se - k3;
+        if constexpr (decltype(psm)::value) {
+          gp *= omB;
+          gm *= omB;
+        }
+        out[i] = om1 * f[i] + (rtau * feq_p + gp);
+        out[io] = om1 * f[io] + (rtau * feq_m + gm);
+      } else {                    // from F in every thread (the same statements, in this order)
+        const R eF = ex * Fx + ey * Fy + ez * Fz;
+        const R wdr = w * (S::shifted ? drho : rho), wr = w * rho, wg = w * guo;
+        const R sym = R(4.5) * eu * eu + m15uu;
+        const R feq_p = wdr + wr * (sym + R(3.0) * eu);
+        const R feq_m = wdr + wr * (sym - R(3.0) * eu);
+        const R Se = wg * (R(9.0) * (eu * eF) - R(3.0) * uF);
+        const R So = (R(3.0) * wg) * eF;
+        out[i] = om1 * f[i] + (rtau * feq_p + (Se + So));
+        out[io] = om1 * f[io] + (rtau * feq_m + (Se - So));
+      }
+      const R wr = w * rho;
       if constexpr (decltype(psm)::value) {
         const R eus = ex * usx + ey * usy + ez * usz;
         const R common = wr * (R(4.5) * (eus * eus - eu * eu) - R(1.5) * (usus - uu));
