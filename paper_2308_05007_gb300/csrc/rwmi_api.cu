@@ -500,6 +500,9 @@ bool force_recorded(const rwmi_ctx* c, int64_t done) {
   return c->cfg.force_interval > 0 && c->P > 0 && c->fseries && done % c->cfg.force_interval == 0;
 }
 
+// Storages with the fused update-and-reduce pass (launch_lbm's `fused`).
+static bool fused_storage(int storage) { return storage == RWMI_STORE_FP32_SHIFT || storage == RWMI_STORE_FP64_SHIFT; }
+
 // One timestep t -> t+1 of a run of steps (host mirrors advance as the launches are queued).
 // Buffers are per time parity where two steps' kernels may overlap: the solid fraction of t is
 // solid[t & 1] (rasterised during step t-1, or at set-up), the LBM of t writes u[t & 1], the
@@ -558,7 +561,11 @@ void enqueue_step(rwmi_ctx* c, bool reduce) {
       ia.g = c->ibl.g;
       ia.cap = c->ibl.cap;
     }
-    // the partially saturated update through TMA-staged rows where it applies (same results)
+    // the partially saturated update through TMA-staged rows where it applies (same results).
+    // Reduction steps run the update and the sums in one fused pass (binary32-shifted and
+    // binary64 storage): its update arithmetic is bit-identical to the plain update's, which a
+    // GPU test checks for every instantiation, so the trajectory does not depend on which steps
+    // are reduced; the other storages add the reduce-only pass.
     const bool staged = !ibb && !dem && c->tma_ok && c->cfg.lbm_staging;
     if (staged)
       launch_lbm_tma(c->cfg.q, c->cfg.storage, c->tmap[c->fcur], c->g, c->f[c->fcur], c->f[c->fcur ^ 1], c->u[tp],
@@ -566,8 +573,8 @@ void enqueue_step(rwmi_ctx* c, bool reduce) {
     if (!staged || reduce)
       launch_lbm(c->cfg.q, c->cfg.storage, reduce, c->g, c->f[c->fcur], c->f[c->fcur ^ 1], c->u[tp], c->solid[tp],
                  brick_set(c, tp), c->tau, c->cfg.rho0, c->acc[tp] + 6 * c->P, c->acc[tp],
-                 c->status, c->stream, c->cfg.lbm_block, ibb ? &ia : nullptr, dem, !staged);
-    c->launches += dem ? 1 : reduce ? 2 : 1;   // fused with DEM; else the reduce-only pass on reduction steps
+                 c->status, c->stream, c->cfg.lbm_block, ibb ? &ia : nullptr, dem || (reduce && !staged), !staged);
+    c->launches += (reduce && !staged && !fused_storage(c->cfg.storage)) ? 2 : 1;
     if (rec_f) {
       launch_force_row(c->acc[tp], c->P, c->fseries, c->cfg.force_interval, FORCE_ROWS, c->d_T, toff + 1,
                        c->stream);

@@ -297,8 +297,9 @@ int tma_inject_stalls(int n);   // rwmi_inject_wait_timeout; returns the previou
 void launch_lbm_tma(int q, int storage, const CUtensorMap& map, const Geom& g, const void* fin, void* fout, float* u,
                     const uint16_t* solid, BrickSet bs, double tau, double rho0, unsigned long long* status, int nsm,
                     cudaStream_t st);
-// fused: the update and the reduction in one pass (free-DEM runs, which read the forces every
-// step; binary32-shifted and binary64 storage)
+// fused: the update and the reduction in one pass (binary32-shifted and binary64 storage; the
+// reduction steps of every run, and every step of free-DEM runs, which read the forces each
+// step). Its update stores the same bits as the plain update's.
 void launch_lbm(int q, int storage, bool reduce, const Geom& g, const void* fin, void* fout,
                 float* u, const uint16_t* solid, BrickSet bs, double tau, double rho0,
                 double* red, double* forces, unsigned long long* status, cudaStream_t st,

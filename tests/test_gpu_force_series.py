@@ -5,8 +5,12 @@
   velocity error carried into -B sum Omega e), for PSM with moving, spinning particles between
   walls.
 - Rows recorded every 3 steps in captured graphs equal the rows of every third step recorded
-  eagerly step by step: a recorded step only adds the reduce-only pass, which stores nothing, so
-  the trajectory and the force of each step are the same whatever the cadence.
+  eagerly step by step: a recorded step runs the fused update-and-reduce pass, whose update stores
+  the same bits as the plain update, so the trajectory and the force of each step are the same
+  whatever the cadence.
+- That bit-identity, for every instantiation that takes the fused pass (D3Q15/D3Q19,
+  binary32-shifted and binary64 storage, walls or periodic, partially saturated cells or IBB):
+  a run reduced on every step equals a run reduced on its last step only.
 - The last row equals rwmi_particle_forces read after the same step.
 """
 import numpy as np
@@ -61,3 +65,21 @@ def test_force_series_cadence_and_graphs_do_not_change_the_rows():
     assert np.array_equal(every.populations(), third.populations())
     every.close()
     third.close()
+
+
+@pytest.mark.parametrize("q,storage,walls,coupling", [
+    (15, 1, 4, 0), (15, 1, 0, 0), (19, 1, 4, 0), (19, 1, 0, 0),
+    (15, 3, 4, 0), (19, 3, 0, 0), (15, 1, 4, 1), (19, 3, 4, 1)])
+def test_fused_reduction_pass_updates_bit_identically(q, storage, walls, coupling):
+    from paper_2308_05007_gb300.rwmi import Simulation
+    w = I.with_(I.ragged(q=q, storage=storage, walls=walls, seed=29, n_walkers=0), coupling=coupling)
+    every = Simulation.from_workload(w, seed_walkers=False, force_interval=1, use_graphs=False)
+    last = Simulation.from_workload(w, seed_walkers=False, use_graphs=False)
+    every.step(6)   # every step reduced: the fused pass six times
+    last.step(6)    # one eager call: only its last step reduced
+    assert np.array_equal(every.populations(), last.populations())
+    assert np.array_equal(every.velocity(), last.velocity())
+    np.testing.assert_allclose(every.force_series()[1][-1], last.particle_forces(), rtol=1e-12,
+                               atol=1e-12 * max(np.abs(last.particle_forces()).max(), 1e-300))
+    every.close()
+    last.close()
