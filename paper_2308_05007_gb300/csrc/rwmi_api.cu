@@ -1903,9 +1903,13 @@ rwmi_status fused_capture(rwmi_batch* b, FusedGraph& fg) {
     cudaStreamWaitEvent(b->side, b->fork2, 0);
     launch_raster_batched(A(s, FP_RASTER), M(FP_RASTER), N(FP_RASTER), b->side); count(FP_RASTER);
     cudaEventRecord(b->join2, b->side);
-    launch_lbm_batched(q, storage, walls, 0, A(s, FP_LBM), M(FP_LBM), N(FP_LBM), b->tiles.lbm_block, b->origin);
+    // the FP64 sums on the chunk's last step, as in rwmi_step: the fused update-and-reduce pass
+    // where the storage has one (same stored bits), else the update and a reduce-only pass
+    const bool fuse = s == L - 1 && fused_storage(storage);
+    launch_lbm_batched(q, storage, walls, fuse ? 2 : 0, A(s, FP_LBM), M(FP_LBM), N(FP_LBM), b->tiles.lbm_block,
+                       b->origin);
     count(FP_LBM);
-    if (s == L - 1) {   // the FP64 sums on the chunk's last step, as in rwmi_step
+    if (s == L - 1 && !fuse) {
       launch_lbm_batched(q, storage, walls, 1, A(s, FP_LBM), M(FP_LBM), N(FP_LBM), b->tiles.lbm_block, b->origin);
       count(FP_LBM);
     }

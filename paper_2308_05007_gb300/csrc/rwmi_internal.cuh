@@ -418,6 +418,7 @@ void launch_raster_batched(const void* args, const BlockMap* map, int nblocks, c
 size_t lbm_args_size(int q, int storage);
 void lbm_args(void* dst, int q, int storage, const Geom& g, const void* fin, void* fout, float* u,
               const uint16_t* solid, BrickSet bs, double tau, double rho0, double* red, double* forces);
+// mode 0 the update, 1 the reduce-only pass, 2 both in one pass (binary32-shifted and binary64)
 void launch_lbm_batched(int q, int storage, bool walls, int mode, const void* args, const BlockMap* map,
                         int nblocks, int block, cudaStream_t st);
 size_t walker_args_size();

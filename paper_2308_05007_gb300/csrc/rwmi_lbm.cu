@@ -1161,6 +1161,13 @@ template <int Q, int STORE>
 static void launch_lbm_batched_q(bool walls, int mode, const void* args, const BlockMap* map, int nblocks, int block,
                                  cudaStream_t st) {
   const LbmArgs<Q, STORE>* a = static_cast<const LbmArgs<Q, STORE>*>(args);
+  if constexpr (STORE == 1 || STORE == 3) {   // the fused update and reduction
+    if (mode == 2) {
+      if (walls) lbm_batched<Q, STORE, true, 2, false><<<nblocks, block, 0, st>>>(a, map);
+      else lbm_batched<Q, STORE, false, 2, false><<<nblocks, block, 0, st>>>(a, map);
+      return;
+    }
+  }
   if (walls) {
     if (mode == 0) lbm_batched<Q, STORE, true, 0, false><<<nblocks, block, 0, st>>>(a, map);
     else lbm_batched<Q, STORE, true, 1, false><<<nblocks, block, 0, st>>>(a, map);
