@@ -574,7 +574,11 @@ void enqueue_step(rwmi_ctx* c, bool reduce) {
       launch_lbm(c->cfg.q, c->cfg.storage, reduce, c->g, c->f[c->fcur], c->f[c->fcur ^ 1], c->u[tp], c->solid[tp],
                  brick_set(c, tp), c->tau, c->cfg.rho0, c->acc[tp] + 6 * c->P, c->acc[tp],
                  c->status, c->stream, c->cfg.lbm_block, ibb ? &ia : nullptr, dem || (reduce && !staged), !staged);
-    c->launches += (reduce && !staged && !fused_storage(c->cfg.storage)) ? 2 : 1;
+    // staged: the TMA update, plus the reduce-only pass on reduction steps; otherwise one pass,
+    // or the update and the reduce-only pass for storages without the fused one (free DEM runs
+    // only with storages that have it)
+    if (staged) c->launches += reduce ? 2 : 1;
+    else c->launches += (reduce && !fused_storage(c->cfg.storage)) ? 2 : 1;
     if (rec_f) {
       launch_force_row(c->acc[tp], c->P, c->fseries, c->cfg.force_interval, FORCE_ROWS, c->d_T, toff + 1,
                        c->stream);
