@@ -301,7 +301,9 @@ RWMI_API rwmi_status rwmi_lattice(rwmi_ctx* ctx, int32_t* e, double* w, int32_t*
 
 /* Solid fraction data of the current time t (rasterised by the last step or at set-up):
  * count[c] (0..64 sub-samples inside a particle, epsilon = count / 64) and owner[c] (particle
- * index, -1 if none). */
+ * index, -1 if none). With the IBB coupling the steps skip the per-cell counts (the update reads
+ * node classes), so this call rasterises the current time's cells itself: one raster launch on
+ * the context's stream, leaving the walkers' masks and the trajectory unchanged. */
 RWMI_API rwmi_status rwmi_solid(rwmi_ctx* ctx, int32_t* count, int32_t* owner);
 
 /* IBB node classes of the current time (Section 2.4.3, the coupling = 1 reading): out[c] = 0 for a
