@@ -698,13 +698,24 @@ __device__ __forceinline__ void histogram_body(const Geom& g, const float4* __re
   const unsigned amask = __ballot_sync(0xffffffffu, act);
   if (!act) return;
   const uint32_t cell = walker_cell(pos[w], g);
-  const unsigned peers = __match_any_sync(amask, cell);
+  // Walkers are sorted by cell up to their drift since the last sort, so equal cells mostly sit
+  // in runs of neighbouring lanes: each run's first lane adds the run's length and the others
+  // take their rank from it (equal cells in separate runs add separately; ranks stay a
+  // permutation of 0..count-1 per cell). The active lanes are 0..popc(amask)-1.
   const int lane = threadIdx.x & 31;
-  const int leader = __ffs(peers) - 1;
+  const uint32_t prev = __shfl_up_sync(amask, cell, 1);
+  const bool head = lane == 0 || prev != cell;
+  const unsigned heads = __ballot_sync(amask, head);
+  const unsigned upto = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);   // lanes 0..lane
+  const int first = 31 - __clz(heads & upto);                            // this lane's run head
   uint32_t base = 0;
-  if (lane == leader) base = atomicAdd(&counts[cell], (uint32_t)__popc(peers));
-  base = __shfl_sync(peers, base, leader);
-  if (rank) rank[w] = base + __popc(peers & ((1u << lane) - 1u));
+  if (head) {
+    const unsigned later = heads & ~upto;
+    const int end = later ? __ffs(later) - 1 : __popc(amask);             // one past the run
+    base = atomicAdd(&counts[cell], (uint32_t)(end - lane));
+  }
+  base = __shfl_sync(amask, base, first);
+  if (rank) rank[w] = base + (uint32_t)(lane - first);
 }
 
 __global__ void histogram_kernel(Geom g, const float4* __restrict__ pos, int64_t n,
