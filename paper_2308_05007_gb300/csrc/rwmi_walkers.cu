@@ -777,12 +777,38 @@ struct ScanArgs {
   uint32_t* sums;
   uint32_t* out;
 };
+// A thread's SCAN_ITEMS consecutive words (base is a multiple of 8): two 16-byte accesses where
+// the array is 16-byte aligned and the words lie inside it, else word by word (arrays handed in
+// by callers of the allocation-free binning may sit at any 4-byte offset).
+static_assert(SCAN_ITEMS == 8, "two uint4 per thread");
+__device__ __forceinline__ void scan_load8(const uint32_t* __restrict__ in, uint32_t base, uint32_t n, uint32_t* v) {
+  if (base + 8 <= n && (reinterpret_cast<uintptr_t>(in) & 15u) == 0) {
+    const uint4 a = *reinterpret_cast<const uint4*>(in + base);
+    const uint4 b = *reinterpret_cast<const uint4*>(in + base + 4);
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+  } else {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = base + k < n ? in[base + k] : 0u;
+  }
+}
+__device__ __forceinline__ void scan_store8(uint32_t* __restrict__ out, uint32_t base, uint32_t n, const uint32_t* v) {
+  if (base + 8 <= n && (reinterpret_cast<uintptr_t>(out) & 15u) == 0) {
+    *reinterpret_cast<uint4*>(out + base) = make_uint4(v[0], v[1], v[2], v[3]);
+    *reinterpret_cast<uint4*>(out + base + 4) = make_uint4(v[4], v[5], v[6], v[7]);
+  } else {
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      if (base + k < n) out[base + k] = v[k];
+  }
+}
+
 __device__ __forceinline__ void scan_reduce_body(const uint32_t* __restrict__ in, uint32_t n,
                                                  uint32_t* __restrict__ sums, int blk) {
   const uint32_t base = blk * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
-  uint32_t s = 0;
+  uint32_t v[SCAN_ITEMS], s = 0;
+  scan_load8(in, base, n, v);
 #pragma unroll
-  for (int k = 0; k < SCAN_ITEMS; ++k) s += base + k < n ? in[base + k] : 0u;
+  for (int k = 0; k < SCAN_ITEMS; ++k) s += v[k];
   uint32_t total;
   block_exclusive_scan(s, &total);
   if (threadIdx.x == 0) sums[blk] = total;
@@ -809,14 +835,17 @@ __device__ __forceinline__ void scan_down_body(const uint32_t* __restrict__ in, 
                                                int blk) {
   const uint32_t base = blk * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
   uint32_t v[SCAN_ITEMS], s = 0;
+  scan_load8(in, base, n, v);
 #pragma unroll
-  for (int k = 0; k < SCAN_ITEMS; ++k) { v[k] = base + k < n ? in[base + k] : 0u; s += v[k]; }
+  for (int k = 0; k < SCAN_ITEMS; ++k) s += v[k];
   uint32_t run = sums[blk] + block_exclusive_scan(s, nullptr);
+  uint32_t o[SCAN_ITEMS];
 #pragma unroll
   for (int k = 0; k < SCAN_ITEMS; ++k) {
-    if (base + k < n) out[base + k] = run;
+    o[k] = run;
     run += v[k];
   }
+  scan_store8(out, base, n, o);
 }
 
 __global__ void scan_down_kernel(const uint32_t* __restrict__ in, uint32_t n,

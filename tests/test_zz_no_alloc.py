@@ -41,7 +41,9 @@ def test_noalloc_binning_matches_the_library_twice():
         expect = sim.concentration()
         pos4 = np.concatenate([pos, ids.astype(np.uint32).view(np.float32)[:, None]], axis=1)
         posd = torch.from_numpy(np.ascontiguousarray(pos4)).cuda()
-        counts = torch.full((n_cells,), 7, dtype=torch.int32, device="cuda")   # must be overwritten
+        # must be overwritten; on the second call it starts 4 bytes into its storage, so the scan
+        # takes its word-by-word path instead of 16-byte accesses
+        counts = torch.full((n_cells + call,), 7, dtype=torch.int32, device="cuda")[call:]
         out = torch.full_like(posd, -1.0)
         with torch.cuda.stream(stream):
             bin_walkers_noalloc(w.dims, w.wall_mask, posd, counts, out, stream=stream)
