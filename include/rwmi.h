@@ -122,8 +122,10 @@ typedef struct {
                                   not supported. */
     int32_t force_interval;    /* record every particle's force and torque every this many steps
                                   (0: never; rwmi_force_series reads them). A recorded step runs
-                                  the reduce-only LBM pass (or the fused one of free-DEM runs),
-                                  which the other steps skip. Default 0. */
+                                  the fused update-and-reduce LBM pass (binary16 and plain
+                                  binary32 storage: the update and a reduce-only pass), whose
+                                  stored populations equal the plain update's, so the trajectory
+                                  does not depend on the interval. Default 0. */
 } rwmi_config;
 
 /* Fills *cfg with the defaults listed above. */

@@ -414,7 +414,8 @@ size_t raster_args_size();
 void raster_args(void* dst, const Geom& g, const ParticleSet& ps, BrickSet bs, uint16_t* solid,
                  unsigned long long* status);
 void launch_raster_batched(const void* args, const BlockMap* map, int nblocks, cudaStream_t st);
-// LBM update (mode 0) or reduce-only pass (mode 1) of the partially saturated cells
+// LBM update (mode 0), reduce-only pass (mode 1) or both in one pass (mode 2) of the partially
+// saturated cells
 size_t lbm_args_size(int q, int storage);
 void lbm_args(void* dst, int q, int storage, const Geom& g, const void* fin, void* fout, float* u,
               const uint16_t* solid, BrickSet bs, double tau, double rho0, double* red, double* forces);

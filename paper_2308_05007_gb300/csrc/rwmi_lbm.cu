@@ -2,8 +2,9 @@
 // collide (Eqs. 12-15) with Guo forcing and either PSM solid coupling or the paper's
 // interpolated bounce-back (Eqs. 23-27); writes the populations, the velocity field and, on
 // reduction steps, per-particle force/torque and the FP64 sums.
-//   lbm_kernel        the update (one cell per thread, direct coalesced pulls), its reduce-only
-//                     pass and the fused update + reduction of free-DEM runs
+//   lbm_kernel        the update (one cell per thread, direct coalesced pulls), the fused update +
+//                     reduction of reduction steps (binary32-shifted and binary64 storage, every
+//                     free-DEM step) and a reduce-only pass (the other storages, staged updates)
 //   lbm_batched       the same update over the cells of many domains (fused batch)
 //   lbm_tma_kernel    the update with its pulled rows staged by TMA tensor copies (an option)
 //   ibb_links_kernel  IBB node words and link list; ibb_link_kernel: q and G of every link
@@ -221,11 +222,12 @@ __device__ __forceinline__ void ibb_cell_force(const Geom& g, const typename Sto
 // velocity; a fluid node replaces the population pulled from each solid neighbour by Eqs. 23-25
 // (q by the same binary32 bisection as the CPU oracle) and, on reduction steps, adds the
 // Galilean-invariant momentum exchange of the link to its particle's force and torque.
-// MODE 0: the update. MODE 1: a reduce-only pass. It runs after the update on the steps whose
-// sums are read, re-pulls the same input populations and forms the FP64 sums and particle forces,
-// and stores nothing. Stored populations therefore always come from one compiled update, and the
-// reducing and non-reducing steps agree bit for bit. MODE 2: update and reduction in one pass,
-// for free-DEM runs, which read the forces on every step (so every step runs this one mode).
+// MODE 0: the update. MODE 2: update and reduction in one pass, on the steps whose sums are read
+// (binary32-shifted and binary64 storage) and on every free-DEM step. Its update arithmetic
+// stores the same bits as MODE 0 (a GPU test checks every instantiation that uses it), so
+// reducing and non-reducing steps agree bit for bit. MODE 1: a reduce-only pass for the other
+// storages and the staged update; it runs after the update, re-pulls the same input populations,
+// forms the FP64 sums and particle forces, and stores nothing.
 template <int Q, int STORE, bool WALLS, int MODE, bool IBB, bool STAGED = false>
 __device__ __forceinline__ void lbm_body(Geom g, Planes<Q, typename Store<STORE>::T> pl,
                                                   float4* __restrict__ u4,
